@@ -1,0 +1,174 @@
+"""Oracle for the edge-corrected space-time Ripley's K estimator (test infrastructure).
+
+A plain, single-threaded FP64 CPU restatement of the paper's Section 3 (Eq. 2-4 and the
+Monte Carlo CSR envelope), compiled from ``stk_oracle.c`` with gcc and loaded through
+ctypes.  Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference legs may import it; the CUDA library never calls it and shares no code with it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stk_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "stk_oracle.h"))
+    ):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+             "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i64, i32, u64, u32 = (ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                 ctypes.c_uint64, ctypes.c_uint32)
+        P = ctypes.c_void_p
+        lib.oracle_philox4x32_10.argtypes = [P, P, P]
+        lib.oracle_philox4x32_10.restype = None
+        lib.oracle_u01.argtypes = [u32, u32]
+        lib.oracle_u01.restype = d
+        lib.oracle_csr_points.argtypes = [i64, P, u64, u32, P, P, P]
+        lib.oracle_csr_points.restype = None
+        lib.oracle_spatial_weight.argtypes = [d, d, d, P]
+        lib.oracle_spatial_weight.restype = d
+        lib.oracle_temporal_weight.argtypes = [d, d, d, d]
+        lib.oracle_temporal_weight.restype = d
+        lib.oracle_pair_hist.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, P, P, P]
+        lib.oracle_pair_hist.restype = i64
+        lib.oracle_finalize.argtypes = [i64, P, P, i32, P, i32, i32, P, P, P, P, P, P]
+        lib.oracle_finalize.restype = None
+        lib.oracle_k.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, P, P, P, P]
+        lib.oracle_k.restype = i64
+        lib.oracle_envelope.argtypes = [i64, P, P, i32, P, i32, i32, i32, i32, u64, P, P, P,
+                                        P, P]
+        lib.oracle_envelope.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _box(box):
+    b = _f64(box)
+    assert b.shape == (6,)
+    return b
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block function (Salmon et al., SC'11)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def u01(w0: int, w1: int) -> float:
+    return _load().oracle_u01(w0, w1)
+
+
+def csr_points(n: int, box, seed: int, sim: int):
+    """Realization `sim` of the Monte Carlo CSR simulation (Section 3)."""
+    x = np.empty(n, np.float64)
+    y = np.empty(n, np.float64)
+    t = np.empty(n, np.float64)
+    b = _box(box)
+    _load().oracle_csr_points(n, _ptr(b), seed, sim, _ptr(x), _ptr(y), _ptr(t))
+    return x, y, t
+
+
+def spatial_weight(xi: float, yi: float, r: float, box) -> float:
+    b = _box(box)
+    return _load().oracle_spatial_weight(xi, yi, r, _ptr(b))
+
+
+def temporal_weight(ti: float, u: float, t0: float, t1: float) -> float:
+    return _load().oracle_temporal_weight(ti, u, t0, t1)
+
+
+def pair_hist(x, y, t, box, s, tt, edge_mode=1, centre_mask=None):
+    """Non-cumulative (count, weighted sum) histograms over ordered pairs (Eq. 2, 3)."""
+    x, y, t, s, tt = map(_f64, (x, y, t, s, tt))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.zeros(cs * ct, np.int64)
+    wsum = np.zeros(cs * ct, np.float64)
+    m = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    q = _load().oracle_pair_hist(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(s), cs,
+                                 _ptr(tt), ct, edge_mode, _ptr(m), _ptr(cnt), _ptr(wsum))
+    return cnt.reshape(cs, ct), wsum.reshape(cs, ct), int(q)
+
+
+def finalize(n, box, s, tt, cnt, wsum, norm=0):
+    """Cumulative C, S and K (Eq. 2), L (Eq. 4) from a non-cumulative histogram."""
+    s, tt = _f64(s), _f64(tt)
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int64).reshape(-1)
+    wsum = _f64(wsum).reshape(-1)
+    C = np.zeros(cs * ct, np.int64)
+    S, K, L = (np.zeros(cs * ct, np.float64) for _ in range(3))
+    _load().oracle_finalize(n, _ptr(b), _ptr(s), cs, _ptr(tt), ct, norm, _ptr(cnt), _ptr(wsum),
+                            _ptr(C), _ptr(S), _ptr(K), _ptr(L))
+    sh = (cs, ct)
+    return C.reshape(sh), S.reshape(sh), K.reshape(sh), L.reshape(sh)
+
+
+def k_function(x, y, t, box, s, tt, edge_mode=1, norm=0):
+    """Full estimator: returns dict with cumulative C, S, K, L and the qualifying count."""
+    x, y, t, s, tt = map(_f64, (x, y, t, s, tt))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    C = np.zeros(cs * ct, np.int64)
+    S, K, L = (np.zeros(cs * ct, np.float64) for _ in range(3))
+    q = _load().oracle_k(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(s), cs, _ptr(tt), ct,
+                         edge_mode, norm, _ptr(C), _ptr(S), _ptr(K), _ptr(L))
+    sh = (cs, ct)
+    return {"C": C.reshape(sh), "S": S.reshape(sh), "K": K.reshape(sh), "L": L.reshape(sh),
+            "pairs": int(q)}
+
+
+def envelope(n, box, s, tt, n_sims, seed, edge_mode=1, norm=0, keep_all=False):
+    """Monte Carlo CSR envelope (Section 3): min / max of K over the simulations."""
+    s, tt = _f64(s), _f64(tt)
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    K_lo, K_hi, L_lo, L_hi = (np.zeros(cs * ct, np.float64) for _ in range(4))
+    K_all = np.zeros(n_sims * cs * ct, np.float64) if keep_all else None
+    rc = _load().oracle_envelope(n, _ptr(b), _ptr(s), cs, _ptr(tt), ct, edge_mode, norm,
+                                 n_sims, seed, _ptr(K_lo), _ptr(K_hi), _ptr(L_lo), _ptr(L_hi),
+                                 _ptr(K_all))
+    if rc != 0:
+        raise ValueError("oracle_envelope: invalid arguments")
+    sh = (cs, ct)
+    out = {"K_lo": K_lo.reshape(sh), "K_hi": K_hi.reshape(sh), "L_lo": L_lo.reshape(sh),
+           "L_hi": L_hi.reshape(sh)}
+    if keep_all:
+        out["K_all"] = K_all.reshape(n_sims, cs, ct)
+    return out

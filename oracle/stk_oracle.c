@@ -1,0 +1,287 @@
+/*
+ * Oracle for the edge-corrected space-time Ripley's K estimator.
+ *
+ * TEST INFRASTRUCTURE ONLY: a plain single-threaded FP64 restatement of the
+ * paper's Section 3 (Eq. 2, 3, 4 and the Monte Carlo envelope), written for
+ * readability, not speed.  Only tests, the smoke check and the benchmark's
+ * CPU-baseline / reference legs may call it.  It shares no code with the CUDA
+ * library.  Build with -O2 -ffp-contract=off so that every floating-point
+ * operation is rounded separately, as the pair predicate below assumes.
+ */
+#include "stk_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11).  Each round multiplies words 0 and 2 by the two
+ * round multipliers, then mixes the high halves with the other words and the
+ * key; the key is advanced by the two Weyl increments between rounds.
+ * Used by the Monte Carlo CSR simulation of Section 3.
+ * ------------------------------------------------------------------------- */
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    memcpy(out, c, sizeof c);
+}
+
+double oracle_u01(uint32_t w0, uint32_t w1) {
+    const double hi = (double)(w0 >> 5); /* 27 bits */
+    const double lo = (double)(w1 >> 6); /* 26 bits */
+    return (hi * 67108864.0 + lo) * (1.0 / 9007199254740992.0);
+}
+
+/* One coordinate of point i of realization `sim`: stream 0 = x, 1 = y, 2 = t. */
+static double csr_coord(uint64_t seed, uint32_t sim, int64_t i, uint32_t stream, double lo,
+                        double hi) {
+    const uint32_t ctr[4] = {(uint32_t)i, sim, stream, (uint32_t)((uint64_t)i >> 32)};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    const double u = oracle_u01(w[0], w[1]);
+    const double span = hi - lo;
+    double v = lo + span * u;
+    if (v > hi) v = hi; /* closed box: rounding may not leave it */
+    return v;
+}
+
+/* Section 3, Monte Carlo method: points uniform in the spatio-temporal box. */
+void oracle_csr_points(int64_t n, const double box[6], uint64_t seed, uint32_t sim, double* x,
+                       double* y, double* t) {
+    for (int64_t i = 0; i < n; ++i) {
+        x[i] = csr_coord(seed, sim, i, 0u, box[0], box[1]);
+        y[i] = csr_coord(seed, sim, i, 1u, box[2], box[3]);
+        t[i] = csr_coord(seed, sim, i, 2u, box[4], box[5]);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Section 3, spatial isotropic edge correction: the weight is the proportion
+ * of the circumference of the circle centred at point i with radius d_ij that
+ * lies inside the study area.  For a rectangle, the part of the circle beyond
+ * an edge at distance e < r is the arc of half-angle acos(e/r) around that
+ * edge's outward normal.  The outside length is the measure of the union of
+ * those arcs (they can overlap near a corner), found here by sorting.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double lo, hi;
+} arc_t;
+
+static int arc_cmp(const void* a, const void* b) {
+    const double x = ((const arc_t*)a)->lo, y = ((const arc_t*)b)->lo;
+    return (x > y) - (x < y);
+}
+
+double oracle_spatial_weight(double xi, double yi, double r, const double box[6]) {
+    if (r == 0.0) return 1.0; /* coincident points: the circle degenerates */
+    /* distances to the right, top, left and bottom edges */
+    const double e[4] = {box[1] - xi, box[3] - yi, xi - box[0], yi - box[2]};
+    /* outward normals of the right, top, left and bottom edges */
+    const double normal[4] = {0.0, 0.5 * ORACLE_PI, ORACLE_PI, 1.5 * ORACLE_PI};
+    arc_t arcs[8];
+    int na = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (e[k] < r) {
+            const double alpha = acos(e[k] / r);
+            double lo = normal[k] - alpha, hi = normal[k] + alpha;
+            if (lo < 0.0) { /* wraps through angle 0: split */
+                arcs[na].lo = lo + 2.0 * ORACLE_PI;
+                arcs[na].hi = 2.0 * ORACLE_PI;
+                ++na;
+                lo = 0.0;
+            }
+            arcs[na].lo = lo;
+            arcs[na].hi = hi;
+            ++na;
+        }
+    }
+    if (na == 0) return 1.0;
+    qsort(arcs, (size_t)na, sizeof(arc_t), arc_cmp);
+    double outside = 0.0, cur_lo = arcs[0].lo, cur_hi = arcs[0].hi;
+    for (int k = 1; k < na; ++k) {
+        if (arcs[k].lo <= cur_hi) {
+            if (arcs[k].hi > cur_hi) cur_hi = arcs[k].hi;
+        } else {
+            outside += cur_hi - cur_lo;
+            cur_lo = arcs[k].lo;
+            cur_hi = arcs[k].hi;
+        }
+    }
+    outside += cur_hi - cur_lo;
+    return 1.0 - outside / (2.0 * ORACLE_PI);
+}
+
+/* Section 3, temporal edge correction: 1 if both ends of the interval of
+ * length 2u centred at t_i lie within the study period (closed), else 1/2. */
+double oracle_temporal_weight(double ti, double u, double t0, double t1) {
+    return (ti - u >= t0 && ti + u <= t1) ? 1.0 : 0.5;
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. 2 and Eq. 3: the double sum over ordered pairs i != j of
+ * I(d_ij <= s, u_ij <= t) / (w_ij v_ij), kept as a histogram over the
+ * threshold grid: pair (i, j) falls in bin (a, b) with a the first spatial
+ * threshold with d_ij <= s_a and b the first temporal threshold with
+ * u_ij <= t_b.  Cumulating the histogram gives the sum at every (s_a, t_b).
+ * ------------------------------------------------------------------------- */
+int64_t oracle_pair_hist(int64_t n, const double* x, const double* y, const double* t,
+                         const double box[6], const double* s, int cs, const double* tt,
+                         int ct, int edge_mode, const uint8_t* centre_mask, int64_t* cnt,
+                         double* wsum) {
+    const int nb = cs * ct;
+    double* s2 = (double*)malloc(sizeof(double) * (size_t)cs);
+    double* comp = (double*)calloc((size_t)nb, sizeof(double));
+    for (int a = 0; a < cs; ++a) s2[a] = s[a] * s[a];
+    for (int k = 0; k < nb; ++k) {
+        cnt[k] = 0;
+        wsum[k] = 0.0;
+    }
+    const double s2max = s2[cs - 1], tmax = tt[ct - 1];
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (centre_mask && !centre_mask[i]) continue;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = x[i] - x[j];
+            const double dy = y[i] - y[j];
+            const double d2 = dx * dx + dy * dy;
+            if (d2 > s2max) continue;
+            const double u = fabs(t[i] - t[j]);
+            if (u > tmax) continue;
+            int a = 0;
+            while (d2 > s2[a]) ++a;
+            int b = 0;
+            while (u > tt[b]) ++b;
+            double w = 1.0;
+            if (edge_mode == 1) {
+                const double om = oracle_spatial_weight(x[i], y[i], sqrt(d2), box);
+                const double v = oracle_temporal_weight(t[i], u, box[4], box[5]);
+                w = 1.0 / (om * v);
+            }
+            const int k = a * ct + b;
+            cnt[k] += 1;
+            /* compensated (Kahan) accumulation keeps the oracle's own
+             * rounding error far below the 1e-9 parity tolerance */
+            const double yk = w - comp[k];
+            const double tk = wsum[k] + yk;
+            comp[k] = (tk - wsum[k]) - yk;
+            wsum[k] = tk;
+            ++total;
+        }
+    }
+    free(s2);
+    free(comp);
+    return total;
+}
+
+/* Eq. 2 normalisation and Eq. 4 L transform over the cumulative grids. */
+void oracle_finalize(int64_t n, const double box[6], const double* s, int cs, const double* tt,
+                     int ct, int norm, const int64_t* cnt, const double* wsum, int64_t* C,
+                     double* S, double* K, double* L) {
+    const int nb = cs * ct;
+    int64_t* Cc = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
+    double* Sc = (double*)malloc(sizeof(double) * (size_t)nb);
+    for (int a = 0; a < cs; ++a) {
+        for (int b = 0; b < ct; ++b) {
+            int64_t c = 0;
+            double w = 0.0;
+            for (int a2 = 0; a2 <= a; ++a2) {
+                for (int b2 = 0; b2 <= b; ++b2) {
+                    c += cnt[a2 * ct + b2];
+                    w += wsum[a2 * ct + b2];
+                }
+            }
+            Cc[a * ct + b] = c;
+            Sc[a * ct + b] = w;
+        }
+    }
+    const double area = (box[1] - box[0]) * (box[3] - box[2]);
+    const double dur = box[5] - box[4];
+    const double nn = (double)n;
+    const double denom = (norm == 1) ? nn * nn : nn * (nn - 1.0);
+    const double coef = area * dur / denom;
+    for (int a = 0; a < cs; ++a) {
+        for (int b = 0; b < ct; ++b) {
+            const int k = a * ct + b;
+            const double kv = coef * Sc[k];
+            if (C) C[k] = Cc[k];
+            if (S) S[k] = Sc[k];
+            if (K) K[k] = kv;
+            if (L) L[k] = sqrt(kv / (2.0 * ORACLE_PI * tt[b])) - s[a];
+        }
+    }
+    free(Cc);
+    free(Sc);
+}
+
+int64_t oracle_k(int64_t n, const double* x, const double* y, const double* t,
+                 const double box[6], const double* s, int cs, const double* tt, int ct,
+                 int edge_mode, int norm, int64_t* C, double* S, double* K, double* L) {
+    const int nb = cs * ct;
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
+    double* wsum = (double*)malloc(sizeof(double) * (size_t)nb);
+    const int64_t q =
+        oracle_pair_hist(n, x, y, t, box, s, cs, tt, ct, edge_mode, NULL, cnt, wsum);
+    oracle_finalize(n, box, s, cs, tt, ct, norm, cnt, wsum, C, S, K, L);
+    free(cnt);
+    free(wsum);
+    return q;
+}
+
+/* Section 3: envelopes from the K values of simulated CSR patterns; the
+ * observed pattern is not part of the envelope. */
+int oracle_envelope(int64_t n, const double box[6], const double* s, int cs, const double* tt,
+                    int ct, int edge_mode, int norm, int n_sims, uint64_t seed, double* K_lo,
+                    double* K_hi, double* L_lo, double* L_hi, double* K_all) {
+    const int nb = cs * ct;
+    if (n_sims < 1) return 1;
+    double* x = (double*)malloc(sizeof(double) * (size_t)n);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* t = (double*)malloc(sizeof(double) * (size_t)n);
+    double* K = (double*)malloc(sizeof(double) * (size_t)nb);
+    for (int k = 0; k < n_sims; ++k) {
+        oracle_csr_points(n, box, seed, (uint32_t)k, x, y, t);
+        oracle_k(n, x, y, t, box, s, cs, tt, ct, edge_mode, norm, NULL, NULL, K, NULL);
+        for (int c = 0; c < nb; ++c) {
+            if (k == 0 || K[c] < K_lo[c]) K_lo[c] = K[c];
+            if (k == 0 || K[c] > K_hi[c]) K_hi[c] = K[c];
+        }
+        if (K_all) memcpy(K_all + (size_t)k * (size_t)nb, K, sizeof(double) * (size_t)nb);
+    }
+    for (int a = 0; a < cs; ++a) {
+        for (int b = 0; b < ct; ++b) {
+            const int c = a * ct + b;
+            if (L_lo) L_lo[c] = sqrt(K_lo[c] / (2.0 * ORACLE_PI * tt[b])) - s[a];
+            if (L_hi) L_hi[c] = sqrt(K_hi[c] / (2.0 * ORACLE_PI * tt[b])) - s[a];
+        }
+    }
+    free(x);
+    free(y);
+    free(t);
+    free(K);
+    return 0;
+}
