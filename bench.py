@@ -1,0 +1,338 @@
+"""Benchmark: observed space-time K + 99-simulation CSR envelope on the n=2,000,000 POI-shaped
+mixture (50 km x 50 km x 1095 days, timestamps in whole seconds, 25 x 25 thresholds to 2 km /
+90 days), batched FP32-guarded path, on one GB300.
+
+One step = one whole job (the observed pattern and 99 CSR realizations through generation,
+grid index, pair kernel, finalize and envelope).  The headline unit is qualifying ordered pairs
+per second (pairs with d <= s_max and u <= t_max, summed over all 100 realizations).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a bounded sample of the
+same workload (random centres of the observed pattern against all n points).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("pair evals/s & K+99-sim envelope time at n=2M (batched FP32 vs plain FP64); "
+          "serve p50/p99")
+UNIT = "qualifying ordered pairs/s"
+# per-unit instruction counts of the pair kernel's algorithm (candidate test; qualifying-pair
+# binning + histogram update), used for the ALU roofline
+OPS_PER_CANDIDATE = 8
+OPS_PER_QUALIFYING = 12
+
+
+def _workload(name):
+    from paper_1912_04753_gb300 import workloads as wl
+
+    return wl.CONFIGS[name]()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(w, target_s=15.0, seed=123):
+    """Time the FP64 oracle on random centres of the observed pattern against all n points."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n = w.n
+    # calibrate on a few centres, then size the sample for ~target_s of CPU work
+    R = 8
+    total_pairs, total_t, used = 0, 0.0, 0
+    while total_t < target_s:
+        mask = np.zeros(n, np.uint8)
+        mask[rng.choice(n, R, replace=False)] = 1
+        t0 = time.perf_counter()
+        _, _, q = oracle.pair_hist(w.x, w.y, w.t, w.box, w.s, w.tt, edge_mode=1,
+                                   centre_mask=mask)
+        dt = time.perf_counter() - t0
+        total_pairs += q
+        total_t += dt
+        used += R
+        per = dt / R
+        R = int(max(8, min(4096, (target_s - total_t) / max(per, 1e-6))))
+        if target_s - total_t < 0.5:
+            break
+    return {"value": total_pairs / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{used} random centres of the observed n={n} pattern x all n points, "
+                      f"FP64 single thread, {total_t:.1f} s", "seconds": total_t}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(args.config)
+    steps = []
+    total_pairs, total_t = 0, 0.0
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, target_s=args.ref_seconds, seed=1000 + i)
+        if i >= args.warmup:
+            steps.append(cb)
+            total_pairs += cb["value"] * cb["seconds"]
+            total_t += cb["seconds"]
+    value = total_pairs / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "sims": w.n_sims,
+                       "thresholds": [len(w.s), len(w.tt)]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": steps[-1]["sample"] if steps else ""},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1912_04753_gb300 as stk
+    from paper_1912_04753_gb300 import build as _b
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _b.build()
+    stk.load()
+    w = _workload(args.config)
+    prec = stk.STK_PREC_FP32_GUARDED if args.prec == "fp32" else stk.STK_PREC_FP64
+    exec_mode = stk.STK_EXEC_BATCHED if args.exec == "batched" else stk.STK_EXEC_PLAIN
+    seed = w.sim_seed + 7919 * rank  # independent job per rank (weak scaling)
+    stream = torch.cuda.Stream()
+    h = stk.stk_create(w.x, w.y, w.t, w.box)
+    stk.stk_set_stream(h, stream)
+
+    def job():
+        return stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
+                           exec_mode=exec_mode)
+
+    for _ in range(args.warmup):
+        job()
+    st = stk.stk_last_stats(h)
+    sampler = ClockSampler(local)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pair_ms, qual, cand, launches = 0.0, 0, 0, 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = job()
+        s = stk.stk_last_stats(h)
+        pair_ms += s["ms_pair"]
+        qual += s["qualifying_pairs"]
+        cand += s["candidate_pairs"]
+        launches += s["kernel_launches"]
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t_rank = torch.tensor([elapsed_ms, float(qual)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        tmax = t_rank.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t_rank[1:], op=torch.distributed.ReduceOp.SUM)
+        t_rank[0] = tmax[0]
+    elapsed_ms, qual_all = float(t_rank[0]), float(t_rank[1])
+    value = qual_all / (elapsed_ms / 1e3)
+
+    # end to end through the C ABI from host buffers: create (H2D of the points), job, D2H of
+    # the result grids, every step
+    e2e_ms = 0.0
+    nb = len(w.s) * len(w.tt)
+    h2d = 3 * 8 * w.n
+    d2h = nb * (8 * 4 + 8) + 4 * nb * 8
+    e2e_steps = max(1, min(args.steps, 2))
+    for _ in range(e2e_steps):
+        barrier()
+        t0 = time.perf_counter()
+        h2 = stk.stk_create(w.x, w.y, w.t, w.box)
+        stk.stk_run(h2, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec, exec_mode=exec_mode)
+        stk.stk_destroy(h2)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    e2e_ms /= e2e_steps
+    e2e_value = (qual / args.steps) / (e2e_ms / 1e3)
+
+    # plain FP64 comparison (spec pairing): one job, one launch per realization
+    plain = None
+    if args.compare_fp64 and rank == 0:
+        stk.stk_run(h, w.s, w.tt, n_sims=1, seed=seed, prec=stk.STK_PREC_FP64,
+                    exec_mode=stk.STK_EXEC_PLAIN)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=stk.STK_PREC_FP64,
+                    exec_mode=stk.STK_EXEC_PLAIN)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ps = stk.stk_last_stats(h)
+        pms = e0.elapsed_time(e1)
+        plain = {"job_s": pms / 1e3, "value": ps["qualifying_pairs"] / (pms / 1e3),
+                 "unit": UNIT, "sims_per_s": w.n_sims / (pms / 1e3),
+                 "speedup_batched_fp32": pms / (elapsed_ms / args.steps)}
+
+    if rank != 0:
+        stk.stk_destroy(h)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peaks, src = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = n_sm * 128 * mhz * 1e6  # FP32 lanes x clock = thread-instruction issue rate
+    achieved = (OPS_PER_CANDIDATE * cand + OPS_PER_QUALIFYING * qual) / (pair_ms / 1e3)
+    cb = cpu_baseline(w, target_s=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    if cb:
+        cb.pop("seconds", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (guarded, f64 ties)"
+        if prec == stk.STK_PREC_FP32_GUARDED else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "sims": w.n_sims,
+                   "thresholds": [len(w.s), len(w.tt)], "s_max_m": float(w.s[-1]),
+                   "t_max_s": float(w.tt[-1]), "exec": args.exec, "prec": args.prec,
+                   "l2": "inputs larger than L2 (100 realizations x 2M points resident)",
+                   "parallelism": f"independent jobs x{ws}"},
+        "job_s": elapsed_ms / args.steps / 1e3,
+        "sims_per_s": w.n_sims * args.steps / (elapsed_ms / 1e3),
+        "candidate_pairs_per_step": cand // args.steps,
+        "qualifying_pairs_per_step": qual // args.steps,
+        "fp64_recomputed_per_step": st["fp64_recomputed"],
+        "pair_kernel_ms_per_step": pair_ms / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "plain_fp64": plain,
+    }
+    print(json.dumps(line), flush=True)
+    stk.stk_destroy(h)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="poi_n2M")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--exec", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--compare-fp64", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * stk.h -- C ABI of the GB300 space-time Ripley's K library (libstk.so).
+ *
+ * The library computes the edge-corrected space-time K function of Wang et al.,
+ * "Optimizing and Accelerating Space-Time Ripley's K Function based on Apache
+ * Spark" (Section 3):
+ *
+ *   K(s,t) = A*D / (n(n-1)) * sum_{i} sum_{j != i} I(d_ij <= s, u_ij <= t) / (w_ij v_ij)   (Eq. 2, 3)
+ *   L(s,t) = sqrt(K(s,t) / (2 pi t)) - s                                                    (Eq. 4)
+ *
+ * over a grid of spatial thresholds s_1 < ... < s_cs and temporal thresholds
+ * t_1 < ... < t_ct, together with Monte Carlo CSR simulation envelopes
+ * (Section 3: envelopes from simulated complete spatio-temporal randomness).
+ * w_ij is the proportion of the circumference of the circle centred at i with
+ * radius d_ij that lies inside the study rectangle, v_ij is 1 when
+ * [t_i - u_ij, t_i + u_ij] lies inside the study period and 1/2 otherwise
+ * (Section 3, isotropic correction); u_ij = |t_i - t_j|.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status (enum stk_status) and never aborts.
+ *     On failure stk_last_error() describes the cause (thread-local string).
+ *   - Input arrays are read during the call and never retained: the library
+ *     copies what it needs.  Output arrays are owned by the caller.
+ *   - Grids are row-major [cs][ct] with cs, ct in [1, STK_MAX_THRESHOLDS];
+ *     entry (a, b) is cumulative: it covers every ordered pair with
+ *     d_ij <= s_a and u_ij <= t_b.
+ *   - Thresholds must be finite, > 0 and strictly increasing, and
+ *     s_cs <= min(x1-x0, y1-y0)/2 (so a circle crosses at most one x-edge and
+ *     one y-edge and 1/(w v) <= 8).  Points must be finite and inside the
+ *     closed box.  n >= 2.
+ *   - A handle is not thread-safe; distinct handles may be used from distinct
+ *     threads.  All device work of a handle runs on its stream (see
+ *     stk_set_stream); functions that return host results synchronise it.
+ *   - Parity contract with the FP64 reference definition: pair counts are
+ *     exact in both precisions; K, L and raw sums agree to relative 1e-9 in
+ *     STK_PREC_FP64 and 1e-6 in STK_PREC_FP32_GUARDED.
+ */
+#ifndef STK_H
+#define STK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STK_MAX_THRESHOLDS 64
+
+typedef struct stk_handle stk_handle;
+
+/* Study area (rectangle) and study period; a closed box with x0<x1, y0<y1, t0<t1. */
+typedef struct {
+    double x0, x1, y0, y1, t0, t1;
+} stk_box;
+
+enum stk_status {
+    STK_OK = 0,
+    STK_EINVAL = 1,   /* malformed argument (sizes, NULL, thresholds, n < 2) */
+    STK_EDOMAIN = 2,  /* a point lies outside the closed study box, or is not finite */
+    STK_ENOMEM = 3,   /* device or host allocation failed */
+    STK_ECUDA = 4,    /* a CUDA call failed; the message names it */
+    STK_ETIMEOUT = 5, /* a bounded device or host wait ran out */
+    STK_EBUSY = 6,    /* the server cannot take the request now */
+    STK_ENODEV = 7    /* no usable CUDA device */
+};
+
+enum { STK_EDGE_NONE = 0, STK_EDGE_ISOTROPIC = 1 };
+/* FP64: every pair in IEEE double, bit-compatible with the reference definition.
+ * FP32_GUARDED: pairs in FP32 with cell-relative coordinates; any pair whose
+ * bin, temporal weight or spatial-weight branch FP32 cannot decide with a
+ * proven error bound is recomputed in FP64, so counts stay exact. */
+enum { STK_PREC_FP64 = 0, STK_PREC_FP32_GUARDED = 1 };
+/* Eq. 2 prints A*D/n^2; A*D/(n(n-1)) makes E[K] = 2 pi s^2 t exact under CSR. */
+enum { STK_NORM_N_NM1 = 0, STK_NORM_N2 = 1 };
+/* Execution form for jobs with simulations. */
+enum { STK_EXEC_BATCHED = 0, STK_EXEC_PLAIN = 1 };
+
+/* Create a handle over n points (host arrays, FP64).  The points are copied to
+ * the device.  Errors: STK_EINVAL (NULL, n < 2, bad box), STK_EDOMAIN (point
+ * outside the box or not finite), STK_ENOMEM, STK_ENODEV, STK_ECUDA. */
+int stk_create(const double* x, const double* y, const double* t, int64_t n, const stk_box* box,
+               stk_handle** out);
+
+/* Same, from device-resident FP64 arrays (copied device-to-device on `stream`,
+ * a cudaStream_t or NULL for the library's own stream).  Points are validated
+ * on the device. */
+int stk_create_device(const double* d_x, const double* d_y, const double* d_t, int64_t n,
+                      const stk_box* box, void* stream, stk_handle** out);
+
+/* Run this handle's device work on `stream` (a cudaStream_t); NULL restores
+ * the handle's own stream. */
+int stk_set_stream(stk_handle* h, void* stream);
+
+/* Observed K over the threshold grid (Eq. 2-4).  Each output is a caller-owned
+ * [cs*ct] row-major array or NULL to skip it.  raw_sum is the cumulative
+ * weighted pair sum before normalisation, pair_count the cumulative number of
+ * ordered pairs. */
+int stk_k(stk_handle* h, const double* s, int cs, const double* tt, int ct, int edge_mode,
+          int prec, int norm, double* K, double* L, double* raw_sum, int64_t* pair_count);
+
+/* Monte Carlo CSR envelope (Section 3): n_sims realizations of n points,
+ * uniform in the handle's box, drawn with Philox4x32-10 under key (seed low
+ * word, seed high word) and counter (i low word, realization, stream 0/1/2 for
+ * x/y/t, i high word); u = ((w0>>5)*2^26 + (w1>>6)) * 2^-53, coordinate =
+ * min(lo + (hi-lo)*u, hi).  Outputs: element-wise min / max of K over the
+ * realizations, and L of those.  Any output may be NULL. */
+int stk_envelope(stk_handle* h, const double* s, int cs, const double* tt, int ct, int edge_mode,
+                 int prec, int norm, int n_sims, uint64_t seed, double* K_lo, double* K_hi,
+                 double* L_lo, double* L_hi);
+
+/* A whole analysis job: observed K plus an n_sims CSR envelope.
+ * exec = STK_EXEC_BATCHED runs the observed pattern and every realization
+ * through one index build and one persistent pair launch (memory permitting;
+ * otherwise in waves); STK_EXEC_PLAIN runs one launch per realization. */
+typedef struct {
+    const double* s;
+    int cs;
+    const double* tt;
+    int ct;
+    int edge_mode;
+    int prec;
+    int norm;
+    int n_sims;          /* 0 = observed K only */
+    uint64_t seed;
+    int exec;
+    const uint8_t* centre_mask; /* optional host [n]: only centres with mask != 0
+                                   contribute to the OBSERVED grids (sampled-centre
+                                   checking mode); NULL = all */
+} stk_request;
+
+typedef struct {
+    /* observed pattern, each [cs*ct] or NULL */
+    double* K;
+    double* L;
+    double* raw_sum;
+    int64_t* pair_count;
+    /* envelope, each [cs*ct] or NULL (ignored when n_sims == 0) */
+    double* K_lo;
+    double* K_hi;
+    double* L_lo;
+    double* L_hi;
+    /* optional per-realization grids [n_sims][cs*ct] */
+    double* K_sims;
+    int64_t* count_sims;
+} stk_result;
+
+/* Statistics of the last job run on a handle. */
+typedef struct {
+    int64_t qualifying_pairs;  /* ordered pairs with d <= s_cs and u <= t_ct, all realizations */
+    int64_t candidate_pairs;   /* ordered pairs examined by the pair kernel */
+    int64_t fp64_recomputed;   /* FP32_GUARDED: pairs decided in FP64 */
+    int64_t work_items;
+    int32_t realizations;
+    int32_t waves;
+    double ms_total;           /* host wall time of the job */
+    double ms_pair;            /* device time of the pair kernel launches */
+    int64_t kernel_launches;   /* CUDA kernels this library launched for the job */
+} stk_stats;
+
+int stk_run(stk_handle* h, const stk_request* req, stk_result* res);
+int stk_last_stats(const stk_handle* h, stk_stats* out);
+
+/* One CSR realization generated by the device generator that stk_envelope
+ * uses (same Philox contract), copied to caller-owned host arrays x, y, t [n].
+ * Exposes step "CSR simulation generation" for checking. */
+int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, double* x,
+                   double* y, double* t);
+
+void stk_destroy(stk_handle* h);
+const char* stk_last_error(void);
+const char* stk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STK_H */

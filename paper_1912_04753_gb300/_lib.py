@@ -1,0 +1,256 @@
+"""ctypes binding of libstk.so: the C ABI declared in include/stk.h, same names.
+
+Argument marshalling only: every step of the computation runs in the CUDA library.  There is
+no fallback: if libstk.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libstk.so")
+
+STK_OK, STK_EINVAL, STK_EDOMAIN, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_EBUSY, STK_ENODEV = range(8)
+STK_EDGE_NONE, STK_EDGE_ISOTROPIC = 0, 1
+STK_PREC_FP64, STK_PREC_FP32_GUARDED = 0, 1
+STK_NORM_N_NM1, STK_NORM_N2 = 0, 1
+STK_EXEC_BATCHED, STK_EXEC_PLAIN = 0, 1
+STK_MAX_THRESHOLDS = 64
+
+_P = ctypes.c_void_p
+
+
+class StkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[stk status {code}] {msg}")
+        self.code = code
+
+
+class stk_box(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("x0", "x1", "y0", "y1", "t0", "t1")]
+
+
+class stk_request(ctypes.Structure):
+    _fields_ = [("s", _P), ("cs", ctypes.c_int), ("tt", _P), ("ct", ctypes.c_int),
+                ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int), ("norm", ctypes.c_int),
+                ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64), ("exec", ctypes.c_int),
+                ("centre_mask", _P)]
+
+
+class stk_result(ctypes.Structure):
+    _fields_ = [(k, _P) for k in ("K", "L", "raw_sum", "pair_count", "K_lo", "K_hi", "L_lo",
+                                  "L_hi", "K_sims", "count_sims")]
+
+
+class stk_stats(ctypes.Structure):
+    _fields_ = [("qualifying_pairs", ctypes.c_int64), ("candidate_pairs", ctypes.c_int64),
+                ("fp64_recomputed", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("realizations", ctypes.c_int32), ("waves", ctypes.c_int32),
+                ("ms_total", ctypes.c_double), ("ms_pair", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """Load libstk.so (raises OSError if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if build_if_missing:
+            from . import build as _b
+
+            _b.build()
+        else:
+            raise OSError(f"libstk.so not built ({LIB_PATH}); run paper_1912_04753_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, u64, u32 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+    PP = ctypes.POINTER(_P)
+    sig = {
+        "stk_create": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), PP], i32),
+        "stk_create_device": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, PP], i32),
+        "stk_set_stream": ([_P, _P], i32),
+        "stk_k": ([_P, _P, i32, _P, i32, i32, i32, i32, _P, _P, _P, _P], i32),
+        "stk_envelope": ([_P, _P, i32, _P, i32, i32, i32, i32, i32, u64, _P, _P, _P, _P], i32),
+        "stk_run": ([_P, ctypes.POINTER(stk_request), ctypes.POINTER(stk_result)], i32),
+        "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
+        "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
+        "stk_destroy": ([_P], None),
+        "stk_last_error": ([], ctypes.c_char_p),
+        "stk_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != STK_OK:
+        raise StkError(rc, load().stk_last_error().decode())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _box(box) -> stk_box:
+    return stk_box(*[float(v) for v in box])
+
+
+def stk_version() -> str:
+    return load().stk_version().decode()
+
+
+def stk_last_error() -> str:
+    return load().stk_last_error().decode()
+
+
+def stk_create(x, y, t, box):
+    """Copy n host points into a new handle (returns an opaque handle)."""
+    x, y, t = _f64(x), _f64(y), _f64(t)
+    if not (x.shape == y.shape == t.shape and x.ndim == 1):
+        raise ValueError("x, y, t must be 1-D arrays of equal length")
+    h = _P()
+    b = _box(box)
+    _check(load().stk_create(_ptr(x), _ptr(y), _ptr(t), x.shape[0], ctypes.byref(b),
+                             ctypes.byref(h)))
+    return h
+
+
+def stk_create_device(x, y, t, box, stream=None):
+    """Create a handle from device-resident FP64 torch tensors (copied on the device)."""
+    for v in (x, y, t):
+        if not (v.is_cuda and v.dtype.is_floating_point and v.element_size() == 8
+                and v.is_contiguous()):
+            raise ValueError("device inputs must be contiguous float64 CUDA tensors")
+    h = _P()
+    b = _box(box)
+    st = None if stream is None else _P(stream.cuda_stream)
+    _check(load().stk_create_device(_P(x.data_ptr()), _P(y.data_ptr()), _P(t.data_ptr()),
+                                    x.numel(), ctypes.byref(b), st, ctypes.byref(h)))
+    return h
+
+
+def stk_set_stream(h, stream=None):
+    st = None if stream is None else _P(stream.cuda_stream)
+    _check(load().stk_set_stream(h, st))
+
+
+def stk_destroy(h):
+    if h:
+        load().stk_destroy(h)
+
+
+def stk_k(h, s, tt, edge_mode=STK_EDGE_ISOTROPIC, prec=STK_PREC_FP32_GUARDED,
+          norm=STK_NORM_N_NM1):
+    """Observed K, L, raw weighted sum and pair count grids ([cs, ct], cumulative)."""
+    s, tt = _f64(s), _f64(tt)
+    cs, ct = s.shape[0], tt.shape[0]
+    K, L, S = (np.zeros(cs * ct) for _ in range(3))
+    C = np.zeros(cs * ct, np.int64)
+    _check(load().stk_k(h, _ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, _ptr(K), _ptr(L),
+                        _ptr(S), _ptr(C)))
+    sh = (cs, ct)
+    return {"K": K.reshape(sh), "L": L.reshape(sh), "S": S.reshape(sh), "C": C.reshape(sh)}
+
+
+def stk_envelope(h, s, tt, n_sims, seed, edge_mode=STK_EDGE_ISOTROPIC,
+                 prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1):
+    s, tt = _f64(s), _f64(tt)
+    cs, ct = s.shape[0], tt.shape[0]
+    out = [np.zeros(cs * ct) for _ in range(4)]
+    _check(load().stk_envelope(h, _ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims,
+                               seed, *[_ptr(o) for o in out]))
+    sh = (cs, ct)
+    return {k: v.reshape(sh) for k, v in zip(("K_lo", "K_hi", "L_lo", "L_hi"), out)}
+
+
+def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
+            prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
+            centre_mask=None, want_sims=False):
+    """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim)."""
+    s, tt = _f64(s), _f64(tt)
+    cs, ct = s.shape[0], tt.shape[0]
+    nb = cs * ct
+    mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    q = stk_request(_ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims, seed, exec_mode,
+                    _ptr(mask))
+    o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
+    if n_sims > 0:
+        for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
+            o[k] = np.zeros(nb)
+        if want_sims:
+            o["K_sims"] = np.zeros(n_sims * nb)
+            o["C_sims"] = np.zeros(n_sims * nb, np.int64)
+    r = stk_result(_ptr(o["K"]), _ptr(o["L"]), _ptr(o["S"]), _ptr(o["C"]), _ptr(o.get("K_lo")),
+                   _ptr(o.get("K_hi")), _ptr(o.get("L_lo")), _ptr(o.get("L_hi")),
+                   _ptr(o.get("K_sims")), _ptr(o.get("C_sims")))
+    _check(load().stk_run(h, ctypes.byref(q), ctypes.byref(r)))
+    out = {}
+    for k, v in o.items():
+        out[k] = v.reshape((n_sims, cs, ct)) if k in ("K_sims", "C_sims") else v.reshape(cs, ct)
+    return out
+
+
+def stk_last_stats(h) -> dict:
+    st = stk_stats()
+    _check(load().stk_last_stats(h, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in stk_stats._fields_}
+
+
+def stk_sim_points(box, n, seed, sim):
+    """Realization `sim` of the device CSR generator, copied back to host arrays."""
+    x, y, t = (np.zeros(n) for _ in range(3))
+    b = _box(box)
+    _check(load().stk_sim_points(ctypes.byref(b), n, seed, sim, _ptr(x), _ptr(y), _ptr(t)))
+    return x, y, t
+
+
+class Pattern:
+    """Owning wrapper of a handle: ``with Pattern(x, y, t, box) as p: p.k(s, tt)``."""
+
+    def __init__(self, x, y, t, box):
+        self.box = tuple(float(v) for v in box)
+        self.n = len(x)
+        self.h = stk_create(x, y, t, box)
+
+    def k(self, s, tt, **kw):
+        return stk_k(self.h, s, tt, **kw)
+
+    def envelope(self, s, tt, n_sims, seed, **kw):
+        return stk_envelope(self.h, s, tt, n_sims, seed, **kw)
+
+    def run(self, s, tt, **kw):
+        return stk_run(self.h, s, tt, **kw)
+
+    def stats(self):
+        return stk_last_stats(self.h)
+
+    def close(self):
+        if self.h:
+            stk_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,419 @@
+// Grid index build: CSR point generation, cell keys, counting sort by cell, work list.
+//
+// Replaces the paper's R-tree / STR bulk loading (Section 4.2) and KDB-tree partitioning
+// (Section 4.4) with a uniform spatio-temporal grid whose cells are at least as large as the
+// largest thresholds, so the spatio-temporal cylinder around any point (Section 4.2) lies in
+// the 27 cells around the point's own cell.  Every kernel here is bound by HBM bandwidth.
+#include "stk_internal.h"
+
+#include <math.h>
+
+namespace stk {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon et al. (SC'11): ten rounds, each multiplying words 0 and
+// 2 by the round constants and folding the high product halves into words 1 and 3 with the
+// key; the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Uniform double in [0,1) from 27 + 26 random bits (exact in FP64).
+__device__ __forceinline__ double u01(uint32_t w0, uint32_t w1) {
+    return ((double)(w0 >> 5) * 67108864.0 + (double)(w1 >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// lo + (hi - lo) * u with each operation rounded separately, clamped into the closed box.
+__device__ __forceinline__ double csr_coord(uint64_t seed, uint32_t sim, int64_t i,
+                                            uint32_t stream, double lo, double hi) {
+    const uint4 w = philox4x32_10(
+        make_uint4((uint32_t)i, sim, stream, (uint32_t)((uint64_t)i >> 32)),
+        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double u = u01(w.x, w.y);
+    const double span = __dsub_rn(hi, lo);
+    const double v = __dadd_rn(lo, __dmul_rn(span, u));
+    return v > hi ? hi : v;
+}
+
+__device__ __forceinline__ int cell_of(double v, double v0, double inv, int nc) {
+    const double f = floor(__dmul_rn(__dsub_rn(v, v0), inv));
+    int c = (int)fmax(0.0, fmin(f, (double)(nc - 1)));
+    return c;
+}
+
+struct GridDev {
+    int nx, ny, nt;
+    double x0, y0, t0, inv_cw, inv_ch, inv_cd;
+};
+
+__host__ GridDev grid_dev(const Grid& g) {
+    GridDev d;
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.nt = g.nt;
+    d.x0 = g.x0;
+    d.y0 = g.y0;
+    d.t0 = g.t0;
+    d.inv_cw = 1.0 / g.cw;
+    d.inv_ch = 1.0 / g.ch;
+    d.inv_cd = 1.0 / g.cd;
+    return d;
+}
+
+__device__ __forceinline__ uint32_t key_of(const GridDev& g, double x, double y, double t) {
+    const int cx = cell_of(x, g.x0, g.inv_cw, g.nx);
+    const int cy = cell_of(y, g.y0, g.inv_ch, g.ny);
+    const int ct = cell_of(t, g.t0, g.inv_cd, g.nt);
+    return (uint32_t)((ct * g.ny + cy) * g.nx + cx);
+}
+
+__global__ void keys_observed_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                     const double* __restrict__ t, int64_t n, GridDev g,
+                                     double x1, double y1, double t1, uint32_t* __restrict__ key,
+                                     uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt,
+                                     int* __restrict__ bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x[i], yi = y[i], ti = t[i];
+        // inside the closed box (also rejects NaN); infinities fail the range test
+        const bool ok = (xi >= g.x0) && (xi <= x1) && (yi >= g.y0) && (yi <= y1) &&
+                        (ti >= g.t0) && (ti <= t1);
+        if (!ok) {
+            atomicOr(bad, 1);
+            key[i] = 0;
+            rank[i] = atomicAdd(&cnt[0], 1u);
+            continue;
+        }
+        const uint32_t k = key_of(g, xi, yi, ti);
+        key[i] = k;
+        rank[i] = atomicAdd(&cnt[k], 1u);
+    }
+}
+
+__global__ void validate_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                const double* __restrict__ t, int64_t n, double x0, double x1,
+                                double y0, double y1, double t0, double t1,
+                                int* __restrict__ bad) {
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x[i], yi = y[i], ti = t[i];
+        local |= !((xi >= x0) && (xi <= x1) && (yi >= y0) && (yi <= y1) && (ti >= t0) &&
+                   (ti <= t1));
+    }
+    if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+__global__ void gen_csr_kernel(int64_t n, int m, uint32_t sim0, uint64_t seed, GridDev g,
+                               double x1, double y1, double t1, int64_t ncells,
+                               double* __restrict__ x, double* __restrict__ y,
+                               double* __restrict__ t, uint32_t* __restrict__ key,
+                               uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt) {
+    const int64_t total = n * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / n);
+        const int64_t i = gi - (int64_t)k * n;
+        const uint32_t sim = sim0 + (uint32_t)k;
+        const double xi = csr_coord(seed, sim, i, 0u, g.x0, x1);
+        const double yi = csr_coord(seed, sim, i, 1u, g.y0, y1);
+        const double ti = csr_coord(seed, sim, i, 2u, g.t0, t1);
+        x[gi] = xi;
+        y[gi] = yi;
+        t[gi] = ti;
+        const uint32_t kk = key_of(g, xi, yi, ti);
+        key[gi] = kk;
+        rank[gi] = atomicAdd(&cnt[(int64_t)k * ncells + kk], 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------- scan
+// Exclusive scan of uint32 in tiles of kThreads*kItems, with the tile sums scanned
+// recursively.  tmp holds the tile sums of every level.
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += nb;
+    }
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < kThreads / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t nb = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += nb;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = (wid > 0 ? warp_sums[wid - 1] : 0u) + inc - v;
+    if (total) *total = warp_sums[kThreads / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void scan_tiles_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                  int64_t count, uint32_t* __restrict__ tile_sums) {
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    uint32_t v[kItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        v[k] = (base + k < count) ? in[base + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_scan(sum, &total);
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        if (base + k < count) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ out, int64_t count,
+                                const uint32_t* __restrict__ tile_offsets) {
+    const uint32_t add = tile_offsets[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int k = threadIdx.x; k < kTile; k += kThreads) {
+        if (base + k < count) out[base + k] += add;
+    }
+}
+
+// ---------------------------------------------------------------------------- scatter
+
+struct ScatterGrid {
+    int nx, ny;
+    double x0, y0, t0, cw, ch, cd;
+    double inv_qx, inv_qy, inv_qt;
+    double qx, qy, qt;
+};
+
+__global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
+                               const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ t, const uint32_t* __restrict__ key,
+                               const uint32_t* __restrict__ rank,
+                               const uint32_t* __restrict__ start,
+                               const uint8_t* __restrict__ mask_in, double* __restrict__ X,
+                               double* __restrict__ Y, double* __restrict__ T,
+                               float4* __restrict__ P, float2* __restrict__ Plo,
+                               uint8_t* __restrict__ mask_out) {
+    const int64_t total = n * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / n);
+        const uint32_t kk = key[gi];
+        const int64_t pos = (int64_t)start[(int64_t)k * ncells + kk] + rank[gi];
+        const double xi = x[gi], yi = y[gi], ti = t[gi];
+        X[pos] = xi;
+        Y[pos] = yi;
+        T[pos] = ti;
+        const int cx = (int)(kk % (uint32_t)g.nx);
+        const int cy = (int)((kk / (uint32_t)g.nx) % (uint32_t)g.ny);
+        const int ct = (int)(kk / ((uint32_t)g.nx * (uint32_t)g.ny));
+        // offsets from the cell origin; hi = offset rounded to the quantum (exact in FP32),
+        // lo = the exact FP64 remainder rounded to FP32
+        const double ox = __dsub_rn(xi, __dadd_rn(g.x0, __dmul_rn((double)cx, g.cw)));
+        const double oy = __dsub_rn(yi, __dadd_rn(g.y0, __dmul_rn((double)cy, g.ch)));
+        const double ot = __dsub_rn(ti, __dadd_rn(g.t0, __dmul_rn((double)ct, g.cd)));
+        const double hx = rint(ox * g.inv_qx) * g.qx;
+        const double hy = rint(oy * g.inv_qy) * g.qy;
+        const double ht = rint(ot * g.inv_qt) * g.qt;
+        const int64_t local = pos - (int64_t)k * n;
+        P[pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float((int)local));
+        Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
+        if (mask_out && k == 0) mask_out[pos] = mask_in[gi];
+    }
+}
+
+__global__ void cell_starts_kernel(int m, int64_t n, int64_t ncells,
+                                   const uint32_t* __restrict__ start,
+                                   uint32_t* __restrict__ cell_start) {
+    const int64_t total = (ncells + 1) * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / (ncells + 1));
+        const int64_t c = gi - (int64_t)k * (ncells + 1);
+        cell_start[gi] = (c == ncells) ? (uint32_t)n
+                                       : (uint32_t)((int64_t)start[(int64_t)k * ncells + c] -
+                                                    (int64_t)k * n);
+    }
+}
+
+__global__ void work_counts_kernel(int m, int64_t ncells, const uint32_t* __restrict__ cs,
+                                   uint32_t* __restrict__ chunks) {
+    const int64_t total = ncells * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / ncells);
+        const int64_t c = gi - (int64_t)k * ncells;
+        const uint32_t* s = cs + (int64_t)k * (ncells + 1);
+        const uint32_t cnt = s[c + 1] - s[c];
+        chunks[gi] = (cnt + kCentreMax - 1) / kCentreMax;
+    }
+}
+
+__global__ void work_fill_kernel(int m, int64_t ncells, const uint32_t* __restrict__ cs,
+                                 const uint32_t* __restrict__ off, WorkItem* __restrict__ items,
+                                 uint32_t* __restrict__ n_items) {
+    const int64_t total = ncells * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / ncells);
+        const int64_t c = gi - (int64_t)k * ncells;
+        const uint32_t* s = cs + (int64_t)k * (ncells + 1);
+        const uint32_t b = s[c], cnt = s[c + 1] - s[c];
+        const uint32_t parts = (cnt + kCentreMax - 1) / kCentreMax;
+        const uint32_t o = off[gi];
+        // near-equal parts of at most kCentreMax centres
+        for (uint32_t p = 0; p < parts; ++p) {
+            const uint32_t lo = (uint32_t)(((uint64_t)cnt * p) / parts);
+            const uint32_t hi = (uint32_t)(((uint64_t)cnt * (p + 1)) / parts);
+            WorkItem w;
+            w.real = (uint32_t)k;
+            w.cell = (uint32_t)c;
+            w.c_begin = b + lo;
+            w.c_count = hi - lo;
+            items[o + p] = w;
+        }
+        if (gi == total - 1) *n_items = o + parts;
+    }
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_keys_observed(const double* x, const double* y, const double* t, int64_t n,
+                                 const Grid& g, uint32_t* key, uint32_t* rank,
+                                 uint32_t* cell_count, int* bad_flag, cudaStream_t st) {
+    keys_observed_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(
+        x, y, t, n, grid_dev(g), g.x1, g.y1, g.t1, key, rank, cell_count, bad_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const double* x, const double* y, const double* t, int64_t n,
+                            const double box[6], int* bad_flag, cudaStream_t st) {
+    validate_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(x, y, t, n, box[0], box[1],
+                                                                 box[2], box[3], box[4], box[5],
+                                                                 bad_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_csr(int64_t n, int m, uint32_t sim0, uint64_t seed, const Grid& g,
+                           double* x, double* y, double* t, uint32_t* key, uint32_t* rank,
+                           uint32_t* cell_count, cudaStream_t st) {
+    gen_csr_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        n, m, sim0, seed, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, x, y, t, key, rank,
+        cell_count);
+    return cudaGetLastError();
+}
+
+int64_t scan_tmp_words(int64_t count) {
+    int64_t words = 0;
+    while (count > kTile) {
+        const int64_t tiles = (count + kTile - 1) / kTile;
+        words += 2 * tiles;  // tile sums and their scanned offsets
+        count = tiles;
+    }
+    return words + 1;
+}
+
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t count,
+                                  uint32_t* tmp, int64_t tmp_words, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t tiles = (count + kTile - 1) / kTile;
+    if (tiles == 1) {
+        scan_tiles_kernel<<<1, kThreads, 0, st>>>(in, out, count, nullptr);
+        return cudaGetLastError();
+    }
+    if (tmp_words < 2 * tiles) return cudaErrorInvalidValue;
+    uint32_t* sums = tmp;
+    uint32_t* offs = tmp + tiles;
+    scan_tiles_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(in, out, count, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_exclusive_scan(sums, offs, tiles, tmp + 2 * tiles, tmp_words - 2 * tiles, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(unsigned)tiles, kThreads, 0, st>>>(out, count, offs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, const double* y,
+                           const double* t, const uint32_t* key, const uint32_t* rank,
+                           const uint32_t* start_global, const uint8_t* mask_in, double* X,
+                           double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
+                           cudaStream_t st) {
+    ScatterGrid s;
+    s.nx = g.nx;
+    s.ny = g.ny;
+    s.x0 = g.x0;
+    s.y0 = g.y0;
+    s.t0 = g.t0;
+    s.cw = g.cw;
+    s.ch = g.ch;
+    s.cd = g.cd;
+    s.qx = g.qx;
+    s.qy = g.qy;
+    s.qt = g.qt;
+    s.inv_qx = 1.0 / (double)g.qx;
+    s.inv_qy = 1.0 / (double)g.qy;
+    s.inv_qt = 1.0 / (double)g.qt;
+    scatter_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        m, n, g.ncells, s, x, y, t, key, rank, start_global, mask_in, X, Y, T, P, Plo,
+        mask_in ? mask_out : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
+                               uint32_t* cell_start, cudaStream_t st) {
+    cell_starts_kernel<<<grid_for((ncells + 1) * m, kThreads), kThreads, 0, st>>>(
+        m, n, ncells, start_global, cell_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_work_counts(int m, int64_t ncells, const uint32_t* cell_start,
+                               uint32_t* chunks, cudaStream_t st) {
+    work_counts_kernel<<<grid_for(ncells * m, kThreads), kThreads, 0, st>>>(m, ncells,
+                                                                            cell_start, chunks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_work_fill(int m, int64_t ncells, const uint32_t* cell_start,
+                             const uint32_t* chunk_off, WorkItem* items, uint32_t* n_items,
+                             cudaStream_t st) {
+    work_fill_kernel<<<grid_for(ncells * m, kThreads), kThreads, 0, st>>>(
+        m, ncells, cell_start, chunk_off, items, n_items);
+    return cudaGetLastError();
+}
+
+}  // namespace stk

@@ -1,0 +1,197 @@
+// Host-side set-up of a job: the uniform grid and the constants of the pair kernels.
+//
+// Guard derivation for the FP32 bulk path.  Every point is stored relative to the origin of
+// its own cell as hi + lo, with hi a multiple of the quantum q = 2^-21 * P (P the smallest
+// power of two >= the cell side).  Staged into a centre cell's frame, hi parts stay exact
+// multiples of q below 2^24 q, so the FP32 difference of two hi parts is exact and differs
+// from the true coordinate difference by at most eps = 2q (+ FP64 rounding of the cell
+// origins, 2^-50 |box|).  From that:
+//   d2_hi = fl(fma(dx, dx, fl(dy*dy))) satisfies |d2_hi - d2| <= 2 r (eps_x + eps_y)
+//           + eps_x^2 + eps_y^2 + 2^-22 r^2;
+//   u_hi  = |dt_hi| satisfies |u_hi - u| <= eps_t.
+// The reference predicates compare FP64 values (d2 rounded three times, s*s rounded once),
+// which differ from the real ones by < 2^-50 of their size.  A band of twice the combined
+// bound around each threshold therefore contains every pair whose FP32 decision could differ
+// from the FP64 decision; such pairs are recomputed in FP64 by the kernel.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "stk_internal.h"
+
+namespace stk {
+
+static float round_down(double v) {
+    float f = (float)v;
+    if ((double)f > v) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+static float round_up(double v) {
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+static double pow2_at_least(double v) {
+    int e;
+    const double m = frexp(v, &e);  // v = m * 2^e, m in [0.5, 1)
+    return m == 0.5 ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+static int cells_along(double extent, double thr) {
+    // largest count whose cell side stays above the threshold with a relative margin, so
+    // that rounding in the cell assignment can never separate a qualifying pair by two cells
+    const double want = thr * (1.0 + 1e-9);
+    long long n = (long long)floor(extent / want);
+    if (n < 1) n = 1;
+    while (n > 1 && extent / (double)n < want) --n;
+    return (int)std::min<long long>(n, 1 << 20);
+}
+
+int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* err,
+               size_t errlen) {
+    memset(g, 0, sizeof(*g));
+    g->x0 = box[0];
+    g->x1 = box[1];
+    g->y0 = box[2];
+    g->y1 = box[3];
+    g->t0 = box[4];
+    g->t1 = box[5];
+    const double W = box[1] - box[0], H = box[3] - box[2], D = box[5] - box[4];
+    int nx = cells_along(W, s_max), ny = cells_along(H, s_max), nt = cells_along(D, t_max);
+    // keep the cell table modest: coarsen the largest axis until the grid fits
+    const long long kMaxCells = 1ll << 26;
+    while ((long long)nx * ny * nt > kMaxCells) {
+        if (nx >= ny && nx >= nt)
+            nx = (nx + 1) / 2;
+        else if (ny >= nt)
+            ny = (ny + 1) / 2;
+        else
+            nt = (nt + 1) / 2;
+    }
+    g->nx = nx;
+    g->ny = ny;
+    g->nt = nt;
+    g->ncells = (int64_t)nx * ny * nt;
+    g->cw = W / nx;
+    g->ch = H / ny;
+    g->cd = D / nt;
+    if (!(g->cw >= s_max && g->ch >= s_max && g->cd >= t_max)) {
+        snprintf(err, errlen, "grid cells smaller than the thresholds");
+        return 1;
+    }
+    const double px = pow2_at_least(g->cw), py = pow2_at_least(g->ch), pt = pow2_at_least(g->cd);
+    g->qx = (float)ldexp(px, -21);
+    g->qy = (float)ldexp(py, -21);
+    g->qt = (float)ldexp(pt, -21);
+    const double cwq = nearbyint(g->cw / g->qx) * g->qx;
+    const double chq = nearbyint(g->ch / g->qy) * g->qy;
+    const double cdq = nearbyint(g->cd / g->qt) * g->qt;
+    g->cwq = (float)cwq;
+    g->chq = (float)chq;
+    g->cdq = (float)cdq;
+    g->cwl = (float)(g->cw - cwq);
+    g->chl = (float)(g->ch - chq);
+    g->cdl = (float)(g->cd - cdq);
+    return 0;
+}
+
+void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
+                       int ct, int edge, PairConsts* pc) {
+    memset(pc, 0, sizeof(*pc));
+    pc->g = g;
+    pc->cs = cs;
+    pc->ct = ct;
+    pc->nbins = cs * ct;
+    pc->edge = edge;
+    pc->n = n;
+    const double ex = 2.0 * g.qx + ldexp(fabs(g.x0) + fabs(g.x1), -50);
+    const double ey = 2.0 * g.qy + ldexp(fabs(g.y0) + fabs(g.y1), -50);
+    const double et = 2.0 * g.qt + ldexp(fabs(g.t0) + fabs(g.t1), -50);
+    for (int a = 0; a < cs; ++a) {
+        const double s2 = s[a] * s[a];
+        const double sp = s[a] * (1.0 + 1e-6) + ex + ey;
+        const double G = 2.0 * (2.0 * sp * (ex + ey) + ex * ex + ey * ey + ldexp(sp * sp, -22)) +
+                         ldexp(sp * sp, -48);
+        pc->s2[a] = s2;
+        pc->s_lo[a] = s2 - G > 0.0 ? round_down(s2 - G) : -1.0f;
+        pc->s_hi[a] = round_up(s2 + G);
+    }
+    for (int b = 0; b < ct; ++b) {
+        const double G = 2.0 * et + ldexp(tt[b], -48);
+        pc->tt[b] = tt[b];
+        pc->t_lo[b] = tt[b] - G > 0.0 ? round_down(tt[b] - G) : -1.0f;
+        pc->t_hi[b] = round_up(tt[b] + G);
+    }
+    pc->s2_cut = pc->s_hi[cs - 1];
+    pc->u_cut = pc->t_hi[ct - 1];
+
+    // bin tables over r = sqrtf(d2) and over u: entry k holds the first bin any value in it
+    // can fall into, and a flag when some guard band meets the entry
+    const double rmax = sqrt((double)pc->s2_cut) * (1.0 + 1e-6);
+    pc->inv_hs = (float)(kTab / rmax);
+    const double hs = 1.0 / (double)pc->inv_hs;
+    for (int k = 0; k < kTab; ++k) {
+        const double dlo = (double)k * hs * (double)k * hs * (1.0 - ldexp(1.0, -19));
+        const double dhi = (k == kTab - 1)
+                               ? INFINITY
+                               : (double)(k + 1) * hs * (double)(k + 1) * hs * (1.0 + ldexp(1.0, -19));
+        int first = 0;
+        while (first < cs && (double)pc->s_hi[first] < dlo) ++first;
+        bool dirty = false;
+        for (int a = 0; a < cs; ++a)
+            if ((double)pc->s_lo[a] <= dhi && (double)pc->s_hi[a] >= dlo) dirty = true;
+        if (first >= cs) {
+            first = cs - 1;
+            dirty = true;
+        }
+        pc->tab_s[k] = (uint8_t)(first | (dirty ? 0x80 : 0));
+    }
+    const double umax = (double)pc->u_cut * (1.0 + 1e-6);
+    pc->inv_ht = (float)(kTab / umax);
+    const double ht = 1.0 / (double)pc->inv_ht;
+    for (int k = 0; k < kTab; ++k) {
+        const double vlo = (double)k * ht * (1.0 - ldexp(1.0, -21));
+        const double vhi = (k == kTab - 1) ? INFINITY : (double)(k + 1) * ht * (1.0 + ldexp(1.0, -21));
+        int first = 0;
+        while (first < ct && (double)pc->t_hi[first] < vlo) ++first;
+        bool dirty = false;
+        for (int b = 0; b < ct; ++b)
+            if ((double)pc->t_lo[b] <= vhi && (double)pc->t_hi[b] >= vlo) dirty = true;
+        if (first >= ct) {
+            first = ct - 1;
+            dirty = true;
+        }
+        pc->tab_t[k] = (uint8_t)(first | (dirty ? 0x80 : 0));
+    }
+
+    // weights: accurate hi + lo differences are within acc of the truth (absolute part)
+    const double acc_x = ldexp((double)g.qx, -22) + ldexp(fabs(g.x0) + fabs(g.x1), -50);
+    const double acc_y = ldexp((double)g.qy, -22) + ldexp(fabs(g.y0) + fabs(g.y1), -50);
+    pc->tan_rel = 1e-3f;
+    pc->tan_abs = round_up(4.0 * (acc_x + acc_y));
+    pc->r_acc_min = round_up(ldexp(acc_x + acc_y, 22));
+    const double rcut = sqrt((double)pc->s2_cut);
+    pc->fast_abs = round_up(3.0 * (ex + ey) + ldexp(rcut, -21));
+    pc->g_v = round_up(2.0 * (et + ldexp((double)pc->u_cut + et, -23)) +
+                       ldexp(fabs(g.t0) + fabs(g.t1), -48));
+
+    // FP64 path tables over d2 and u (start bins; exact comparisons finish the job)
+    pc->inv_hs2_64 = kTab / pc->s2[cs - 1];
+    pc->inv_ht_64 = kTab / pc->tt[ct - 1];
+    for (int k = 0; k < kTab; ++k) {
+        const double dlo = (double)k / pc->inv_hs2_64 * (1.0 - 1e-12);
+        int first = 0;
+        while (first < cs - 1 && pc->s2[first] < dlo) ++first;
+        pc->tab_s64[k] = (uint8_t)first;
+        const double vlo = (double)k / pc->inv_ht_64 * (1.0 - 1e-12);
+        first = 0;
+        while (first < ct - 1 && pc->tt[first] < vlo) ++first;
+        pc->tab_t64[k] = (uint8_t)first;
+    }
+}
+
+}  // namespace stk

@@ -1,0 +1,660 @@
+// C ABI of libstk.so: handles, argument checking and the job pipeline
+//   (observed upload) -> CSR generation -> cell keys -> counting sort -> work list
+//   -> persistent pair kernel -> finalize (K, L) -> envelope.
+// Everything after argument checking runs on the handle's CUDA stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "stk.h"
+#include "stk_internal.h"
+
+using namespace stk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear a sticky launch error where possible
+    if (e == cudaErrorMemoryAllocation)
+        return fail(STK_ENOMEM, "%s: out of device memory", what);
+    return fail(STK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                                    \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+int ensure(DevBuf& b, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return STK_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STK_ENOMEM, "cannot allocate %zu bytes of device memory for %s", bytes, what);
+    }
+    b.bytes = bytes;
+    return STK_OK;
+}
+
+template <class T>
+T* as(DevBuf& b) {
+    return reinterpret_cast<T*>(b.p);
+}
+
+}  // namespace
+
+struct stk_handle {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    double box[6] = {0, 0, 0, 0, 0, 0};
+    double* d_x = nullptr;
+    double* d_y = nullptr;
+    double* d_t = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // workspace (grow-only, resident between calls)
+    DevBuf ux, uy, ut, key, rank, counts, start, scan_tmp;
+    DevBuf X, Y, T, P, Plo, cell_start, chunks, chunk_off, items, n_items, counter;
+    DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
+    DevBuf oK, oL, oS, oC, env;
+    PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
+    stk_stats last;
+    size_t smem32 = 0, smem64 = 0;
+    int reps32 = 1, reps64 = 1;
+    int configured_nbins = -1;
+};
+
+namespace {
+
+bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
+
+int check_box(const stk_box* b) {
+    if (!b) return fail(STK_EINVAL, "box is NULL");
+    const double v[6] = {b->x0, b->x1, b->y0, b->y1, b->t0, b->t1};
+    for (double d : v)
+        if (!isfinite(d)) return fail(STK_EINVAL, "box bounds must be finite");
+    if (!(b->x0 < b->x1 && b->y0 < b->y1 && b->t0 < b->t1))
+        return fail(STK_EINVAL, "box must satisfy x0<x1, y0<y1, t0<t1");
+    return STK_OK;
+}
+
+int init_handle(stk_handle* h, int64_t n, const stk_box* box) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STK_ENODEV, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    h->device = dev;
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+    h->n = n;
+    h->box[0] = box->x0;
+    h->box[1] = box->x1;
+    h->box[2] = box->y0;
+    h->box[3] = box->y1;
+    h->box[4] = box->t0;
+    h->box[5] = box->t1;
+    CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking), "stream create");
+    h->stream = h->own_stream;
+    CK(cudaEventCreate(&h->ev0), "event create");
+    CK(cudaEventCreate(&h->ev1), "event create");
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_pc), sizeof(PairConsts)), "pinned alloc");
+    const size_t bytes = sizeof(double) * (size_t)n;
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->d_x), bytes), "point upload");
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->d_y), bytes), "point upload");
+    CK(cudaMalloc(reinterpret_cast<void**>(&h->d_t), bytes), "point upload");
+    memset(&h->last, 0, sizeof h->last);
+    return STK_OK;
+}
+
+void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int check_thresholds(const stk_handle* h, const double* s, int cs, const double* tt, int ct) {
+    if (!s || !tt) return fail(STK_EINVAL, "threshold arrays must not be NULL");
+    if (cs < 1 || cs > STK_MAX_THRESHOLDS || ct < 1 || ct > STK_MAX_THRESHOLDS)
+        return fail(STK_EINVAL, "cs and ct must be in [1, %d]", STK_MAX_THRESHOLDS);
+    for (int a = 0; a < cs; ++a) {
+        if (!isfinite(s[a]) || s[a] <= 0.0)
+            return fail(STK_EINVAL, "spatial threshold %d must be finite and > 0", a);
+        if (a > 0 && !(s[a] > s[a - 1]))
+            return fail(STK_EINVAL, "spatial thresholds must be strictly increasing");
+    }
+    for (int b = 0; b < ct; ++b) {
+        if (!isfinite(tt[b]) || tt[b] <= 0.0)
+            return fail(STK_EINVAL, "temporal threshold %d must be finite and > 0", b);
+        if (b > 0 && !(tt[b] > tt[b - 1]))
+            return fail(STK_EINVAL, "temporal thresholds must be strictly increasing");
+    }
+    const double W = h->box[1] - h->box[0], H = h->box[3] - h->box[2];
+    if (s[cs - 1] > 0.5 * (W < H ? W : H))
+        return fail(STK_EINVAL, "largest spatial threshold exceeds half the shorter box side");
+    return STK_OK;
+}
+
+int configure_kernels(stk_handle* h, int nbins) {
+    if (h->configured_nbins == nbins) return STK_OK;
+    h->smem32 = pair_fp32_smem(nbins, &h->reps32);
+    h->smem64 = pair_fp64_smem(nbins, &h->reps64);
+    CK(pair_kernels_configure(h->smem32, h->smem64), "pair kernel configuration");
+    h->configured_nbins = nbins;
+    return STK_OK;
+}
+
+// Runs observed (optional) + n_sims realizations and leaves per-realization K, L, S, C rows in
+// h->oK/oL/oS/oC ([R][nbins]) and, with n_sims > 0, the envelope in h->env ([4][nbins]).
+int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
+    using clock = std::chrono::steady_clock;
+    const auto t_start = clock::now();
+    int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
+    if (rc) return rc;
+    if (q->edge_mode != STK_EDGE_NONE && q->edge_mode != STK_EDGE_ISOTROPIC)
+        return fail(STK_EINVAL, "unknown edge_mode %d", q->edge_mode);
+    if (q->prec != STK_PREC_FP64 && q->prec != STK_PREC_FP32_GUARDED)
+        return fail(STK_EINVAL, "unknown prec %d", q->prec);
+    if (q->norm != STK_NORM_N_NM1 && q->norm != STK_NORM_N2)
+        return fail(STK_EINVAL, "unknown norm %d", q->norm);
+    if (q->exec != STK_EXEC_BATCHED && q->exec != STK_EXEC_PLAIN)
+        return fail(STK_EINVAL, "unknown exec %d", q->exec);
+    if (q->n_sims < 0 || q->n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
+    const int R = (include_obs ? 1 : 0) + q->n_sims;
+    if (R < 1) return fail(STK_EINVAL, "nothing to compute (no observed pattern, n_sims = 0)");
+    *R_out = R;
+    const int64_t n = h->n;
+    const int cs = q->cs, ct = q->ct, nbins = cs * ct;
+    char err[256];
+    Grid g;
+    if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], &g, err, sizeof err))
+        return fail(STK_EINVAL, "%s", err);
+    cudaStream_t st = h->stream;
+    CK(cudaStreamSynchronize(st), "stream sync");  // the pinned constants are reused below
+    build_pair_consts(g, n, q->s, cs, q->tt, ct, q->edge_mode, h->h_pc);
+    rc = configure_kernels(h, nbins);
+    if (rc) return rc;
+
+    // wave size: every realization of the wave is resident at once
+    const int64_t ncells = g.ncells;
+    const size_t per_real = (size_t)n * (24 + 24 + 16 + 8 + 8) + (size_t)(ncells + 1) * 4 +
+                            (size_t)ncells * 12 + ((size_t)ncells + (size_t)n / kCentreMax + 1) * 16 +
+                            (size_t)nbins * 24;
+    int m_w = 1;
+    if (q->exec == STK_EXEC_BATCHED) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b), "memory query");
+        size_t budget = (size_t)(0.6 * (double)(free_b + h->ux.bytes + h->X.bytes + h->P.bytes));
+        const char* env = getenv("STK_MEM_BUDGET_MB");
+        if (env) budget = (size_t)atoll(env) << 20;
+        int64_t fit = (int64_t)(budget / (per_real ? per_real : 1));
+        if (fit < 1) fit = 1;
+        const int64_t cap_idx = ((int64_t)1 << 31) / (n > 0 ? n : 1);  // 32-bit sorted offsets
+        m_w = (int)std::min<int64_t>(std::min<int64_t>(fit, cap_idx > 0 ? cap_idx : 1), R);
+    }
+    const int64_t mn = (int64_t)m_w * n;
+    const int64_t mc = (int64_t)m_w * ncells;
+    const size_t max_items = (size_t)m_w * ((size_t)ncells + (size_t)n / kCentreMax + 1);
+    const int64_t tmp_words = std::max(scan_tmp_words(mc), scan_tmp_words(mc));
+    if ((rc = ensure(h->ux, 8 * mn, "unsorted x")) || (rc = ensure(h->uy, 8 * mn, "unsorted y")) ||
+        (rc = ensure(h->ut, 8 * mn, "unsorted t")) || (rc = ensure(h->key, 4 * mn, "keys")) ||
+        (rc = ensure(h->rank, 4 * mn, "ranks")) || (rc = ensure(h->counts, 4 * mc, "counts")) ||
+        (rc = ensure(h->start, 4 * mc, "starts")) ||
+        (rc = ensure(h->scan_tmp, 4 * tmp_words, "scan scratch")) ||
+        (rc = ensure(h->X, 8 * mn, "sorted x")) || (rc = ensure(h->Y, 8 * mn, "sorted y")) ||
+        (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 16 * mn, "FP32 points")) ||
+        (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
+        (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
+        (rc = ensure(h->chunks, 4 * mc, "work counts")) ||
+        (rc = ensure(h->chunk_off, 4 * mc, "work offsets")) ||
+        (rc = ensure(h->items, sizeof(WorkItem) * max_items, "work items")) ||
+        (rc = ensure(h->n_items, 16, "work item count")) || (rc = ensure(h->counter, 16, "counter")) ||
+        (rc = ensure(h->acc_cnt, 8 * (size_t)m_w * nbins, "histograms")) ||
+        (rc = ensure(h->acc_lo, 8 * (size_t)m_w * nbins, "histograms")) ||
+        (rc = ensure(h->acc_hi, 8 * (size_t)m_w * nbins, "histograms")) ||
+        (rc = ensure(h->stats, 64, "statistics")) || (rc = ensure(h->pc, sizeof(PairConsts), "constants")) ||
+        (rc = ensure(h->thr, 8 * 2 * STK_MAX_THRESHOLDS, "thresholds")) ||
+        (rc = ensure(h->self_pairs, 8 * (size_t)m_w, "self pairs")) ||
+        (rc = ensure(h->oK, 8 * (size_t)R * nbins, "K grids")) ||
+        (rc = ensure(h->oL, 8 * (size_t)R * nbins, "L grids")) ||
+        (rc = ensure(h->oS, 8 * (size_t)R * nbins, "S grids")) ||
+        (rc = ensure(h->oC, 8 * (size_t)R * nbins, "C grids")) ||
+        (rc = ensure(h->env, 8 * 4 * (size_t)nbins, "envelope")))
+        return rc;
+    const bool use_mask = include_obs && q->centre_mask != nullptr;
+    int64_t masked = n;
+    if (use_mask) {
+        if ((rc = ensure(h->mask_in, (size_t)n, "centre mask")) ||
+            (rc = ensure(h->mask_sorted, (size_t)n, "centre mask")))
+            return rc;
+        CK(cudaMemcpyAsync(h->mask_in.p, q->centre_mask, (size_t)n, cudaMemcpyHostToDevice, st),
+           "mask upload");
+        masked = 0;
+        for (int64_t i = 0; i < n; ++i) masked += q->centre_mask[i] != 0;
+    }
+    CK(cudaMemcpyAsync(h->pc.p, h->h_pc, sizeof(PairConsts), cudaMemcpyHostToDevice, st),
+       "constants upload");
+    std::vector<double> thr(2 * STK_MAX_THRESHOLDS, 0.0);
+    for (int a = 0; a < cs; ++a) thr[a] = q->s[a];
+    for (int b = 0; b < ct; ++b) thr[STK_MAX_THRESHOLDS + b] = q->tt[b];
+    CK(cudaMemcpyAsync(h->thr.p, thr.data(), 8 * thr.size(), cudaMemcpyHostToDevice, st),
+       "threshold upload");
+    CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
+
+    const double area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
+    const double dur = h->box[5] - h->box[4];
+    const double nn = (double)n;
+    const double coef = area * dur / (q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0));
+    const double* d_s = as<double>(h->thr);
+    const double* d_tt = as<double>(h->thr) + STK_MAX_THRESHOLDS;
+    const bool fp32 = q->prec == STK_PREC_FP32_GUARDED;
+    const size_t smem = fp32 ? h->smem32 : h->smem64;
+    const int reps = fp32 ? h->reps32 : h->reps64;
+    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem);
+    const int grid = bps * h->num_sms;
+    std::vector<int64_t> selfp(m_w, n);
+    float ms_pair = 0.0f;
+    int waves = 0;
+    int64_t launches = 0;
+    // kernels of one exclusive scan over `count` entries (tile pass + add pass per level)
+    auto scan_launches = [](int64_t count) {
+        int64_t k = 0;
+        while (count > 2048) {
+            k += 2;
+            count = (count + 2047) / 2048;
+        }
+        return k + 1;
+    };
+    for (int r0 = 0; r0 < R; r0 += m_w) {
+        const int m = std::min(m_w, R - r0);
+        const bool obs_here = include_obs && r0 == 0;
+        const int first_sim_slot = obs_here ? 1 : 0;
+        CK(cudaMemsetAsync(h->counts.p, 0, 4 * (size_t)m * ncells, st), "memset");
+        if (obs_here) {
+            CK(cudaMemcpyAsync(h->ux.p, h->d_x, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
+            CK(cudaMemcpyAsync(h->uy.p, h->d_y, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
+            CK(cudaMemcpyAsync(h->ut.p, h->d_t, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
+            CK(launch_keys_observed(h->d_x, h->d_y, h->d_t, n, g, as<uint32_t>(h->key),
+                                    as<uint32_t>(h->rank), as<uint32_t>(h->counts),
+                                    reinterpret_cast<int*>(as<unsigned long long>(h->stats) + 3), st),
+               "cell keys");
+        }
+        if (m > first_sim_slot) {
+            const int r_first = r0 + first_sim_slot;
+            const uint32_t sim0 = (uint32_t)(r_first - (include_obs ? 1 : 0));
+            const int64_t off = (int64_t)first_sim_slot * n;
+            CK(launch_gen_csr(n, m - first_sim_slot, sim0, q->seed, g, as<double>(h->ux) + off,
+                              as<double>(h->uy) + off, as<double>(h->ut) + off,
+                              as<uint32_t>(h->key) + off, as<uint32_t>(h->rank) + off,
+                              as<uint32_t>(h->counts) + (int64_t)first_sim_slot * ncells, st),
+               "CSR generation");
+        }
+        CK(launch_exclusive_scan(as<uint32_t>(h->counts), as<uint32_t>(h->start),
+                                 (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
+           "cell scan");
+        CK(launch_scatter(m, n, g, as<double>(h->ux), as<double>(h->uy), as<double>(h->ut),
+                          as<uint32_t>(h->key), as<uint32_t>(h->rank), as<uint32_t>(h->start),
+                          (obs_here && use_mask) ? as<uint8_t>(h->mask_in) : nullptr,
+                          as<double>(h->X), as<double>(h->Y), as<double>(h->T),
+                          as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted), st),
+           "scatter");
+        CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
+                              st),
+           "cell starts");
+        CK(launch_work_counts(m, ncells, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunks), st),
+           "work counts");
+        CK(launch_exclusive_scan(as<uint32_t>(h->chunks), as<uint32_t>(h->chunk_off),
+                                 (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
+           "work scan");
+        CK(launch_work_fill(m, ncells, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunk_off),
+                            as<WorkItem>(h->items), as<uint32_t>(h->n_items), st),
+           "work fill");
+        const size_t accb = 8 * (size_t)m * nbins;
+        CK(cudaMemsetAsync(h->acc_cnt.p, 0, accb, st), "memset");
+        CK(cudaMemsetAsync(h->acc_lo.p, 0, accb, st), "memset");
+        CK(cudaMemsetAsync(h->acc_hi.p, 0, accb, st), "memset");
+        CK(cudaMemsetAsync(h->counter.p, 0, 16, st), "memset");
+        for (int k = 0; k < m; ++k) selfp[k] = (obs_here && k == 0) ? masked : n;
+        CK(cudaMemcpyAsync(h->self_pairs.p, selfp.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, st),
+           "self pairs");
+        RealBatch rb;
+        rb.P = as<float4>(h->P);
+        rb.Plo = as<float2>(h->Plo);
+        rb.X = as<double>(h->X);
+        rb.Y = as<double>(h->Y);
+        rb.T = as<double>(h->T);
+        rb.cell_start = as<uint32_t>(h->cell_start);
+        rb.mask = (obs_here && use_mask) ? as<uint8_t>(h->mask_sorted) : nullptr;
+        rb.n = n;
+        rb.ncells = ncells;
+        Accum acc;
+        acc.cnt = as<unsigned long long>(h->acc_cnt);
+        acc.exc_lo = as<unsigned long long>(h->acc_lo);
+        acc.exc_hi = as<unsigned long long>(h->acc_hi);
+        acc.stats = as<unsigned long long>(h->stats);
+        CK(cudaEventRecord(h->ev0, st), "event");
+        if (fp32)
+            CK(launch_pair_fp32(as<PairConsts>(h->pc), smem, reps, grid, rb, as<WorkItem>(h->items),
+                                as<uint32_t>(h->n_items), as<uint32_t>(h->counter), acc, st),
+               "pair kernel (FP32)");
+        else
+            CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, rb, as<WorkItem>(h->items),
+                                as<uint32_t>(h->n_items), as<uint32_t>(h->counter), acc, st),
+               "pair kernel (FP64)");
+        CK(cudaEventRecord(h->ev1, st), "event");
+        const int64_t row = (int64_t)r0 * nbins;
+        CK(launch_finalize(m, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
+                           as<double>(h->oK) + row, as<double>(h->oL) + row,
+                           as<double>(h->oS) + row, as<int64_t>(h->oC) + row, st),
+           "finalize");
+        CK(cudaEventSynchronize(h->ev1), "pair kernel");
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event timing");
+        ms_pair += ms;
+        ++waves;
+        launches += (obs_here ? 1 : 0) + (m > first_sim_slot ? 1 : 0) +
+                    2 * scan_launches((int64_t)m * ncells) + 4 /* scatter, starts, counts, fill */ +
+                    2 /* pair, finalize */;
+    }
+    const int first_sim_row = include_obs ? 1 : 0;
+    if (q->n_sims > 0) {
+        double* env = as<double>(h->env);
+        CK(launch_envelope(q->n_sims, nbins, ct, as<double>(h->oK) + (int64_t)first_sim_row * nbins,
+                           d_s, d_tt, env, env + nbins, env + 2 * nbins, env + 3 * nbins, st),
+           "envelope");
+    }
+    unsigned long long stats[8];
+    CK(cudaMemcpyAsync(stats, h->stats.p, sizeof stats, cudaMemcpyDeviceToHost, st), "stats");
+    std::vector<int64_t> lastC(R);
+    for (int r = 0; r < R; ++r)
+        CK(cudaMemcpyAsync(&lastC[r], as<int64_t>(h->oC) + (int64_t)r * nbins + nbins - 1, 8,
+                           cudaMemcpyDeviceToHost, st),
+           "counts");
+    CK(cudaStreamSynchronize(st), "job");
+    if (stats[3] != 0) return fail(STK_EDOMAIN, "a point lies outside the study box");
+    h->last.qualifying_pairs = 0;
+    for (int r = 0; r < R; ++r) h->last.qualifying_pairs += lastC[r];
+    h->last.candidate_pairs = (int64_t)stats[0];
+    h->last.fp64_recomputed = (int64_t)stats[1];
+    h->last.work_items = 0;
+    h->last.realizations = R;
+    h->last.waves = waves;
+    h->last.ms_pair = ms_pair;
+    h->last.kernel_launches = launches;
+    h->last.ms_total =
+        std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+    return STK_OK;
+}
+
+int copy_rows(stk_handle* h, DevBuf& b, int64_t row0, int rows, int nbins, void* dst) {
+    if (!dst) return STK_OK;
+    CK(cudaMemcpyAsync(dst, reinterpret_cast<char*>(b.p) + 8 * row0 * nbins,
+                       8 * (size_t)rows * nbins, cudaMemcpyDeviceToHost, h->stream),
+       "result copy");
+    return STK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stk_last_error(void) { return g_err; }
+
+const char* stk_version(void) { return "stk-gb300 0.1 (sm_103a)"; }
+
+int stk_create(const double* x, const double* y, const double* t, int64_t n, const stk_box* box,
+               stk_handle** out) {
+    if (!out) return fail(STK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!x || !y || !t) return fail(STK_EINVAL, "point arrays must not be NULL");
+    if (n < 2) return fail(STK_EINVAL, "need n >= 2 points (got %lld)", (long long)n);
+    if (n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n too large");
+    int rc = check_box(box);
+    if (rc) return rc;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!finite_in(x[i], box->x0, box->x1) || !finite_in(y[i], box->y0, box->y1) ||
+            !finite_in(t[i], box->t0, box->t1))
+            return fail(STK_EDOMAIN, "point %lld lies outside the study box or is not finite",
+                        (long long)i);
+    }
+    stk_handle* h = new stk_handle();
+    rc = init_handle(h, n, box);
+    if (rc) {
+        stk_destroy(h);
+        return rc;
+    }
+    const size_t bytes = sizeof(double) * (size_t)n;
+    cudaError_t e = cudaMemcpyAsync(h->d_x, x, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_y, y, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_t, t, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "point upload");
+        stk_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return STK_OK;
+}
+
+int stk_create_device(const double* d_x, const double* d_y, const double* d_t, int64_t n,
+                      const stk_box* box, void* stream, stk_handle** out) {
+    if (!out) return fail(STK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d_x || !d_y || !d_t) return fail(STK_EINVAL, "point arrays must not be NULL");
+    if (n < 2) return fail(STK_EINVAL, "need n >= 2 points (got %lld)", (long long)n);
+    if (n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n too large");
+    int rc = check_box(box);
+    if (rc) return rc;
+    stk_handle* h = new stk_handle();
+    rc = init_handle(h, n, box);
+    if (rc) {
+        stk_destroy(h);
+        return rc;
+    }
+    if (stream) h->stream = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(double) * (size_t)n;
+    int bad = 0;
+    cudaError_t e = cudaMemcpyAsync(h->d_x, d_x, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_y, d_y, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_t, d_t, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) {
+        rc = ensure(h->stats, 64, "statistics");
+        if (rc) {
+            stk_destroy(h);
+            return rc;
+        }
+        e = cudaMemsetAsync(h->stats.p, 0, 64, h->stream);
+    }
+    if (e == cudaSuccess) e = launch_validate(h->d_x, h->d_y, h->d_t, n, h->box,
+                                              reinterpret_cast<int*>(h->stats.p), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, h->stats.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "point copy");
+        stk_destroy(h);
+        return rc;
+    }
+    if (bad) {
+        stk_destroy(h);
+        return fail(STK_EDOMAIN, "a point lies outside the study box or is not finite");
+    }
+    *out = h;
+    return STK_OK;
+}
+
+int stk_set_stream(stk_handle* h, void* stream) {
+    if (!h) return fail(STK_EINVAL, "handle is NULL");
+    h->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : h->own_stream;
+    return STK_OK;
+}
+
+int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
+    if (!h || !req || !res) return fail(STK_EINVAL, "handle, request and result must not be NULL");
+    int R = 0;
+    int rc = run_job(h, req, true, &R);
+    if (rc) return rc;
+    const int nbins = req->cs * req->ct;
+    if ((rc = copy_rows(h, h->oK, 0, 1, nbins, res->K)) ||
+        (rc = copy_rows(h, h->oL, 0, 1, nbins, res->L)) ||
+        (rc = copy_rows(h, h->oS, 0, 1, nbins, res->raw_sum)) ||
+        (rc = copy_rows(h, h->oC, 0, 1, nbins, res->pair_count)))
+        return rc;
+    if (req->n_sims > 0) {
+        if ((rc = copy_rows(h, h->env, 0, 1, nbins, res->K_lo)) ||
+            (rc = copy_rows(h, h->env, 1, 1, nbins, res->K_hi)) ||
+            (rc = copy_rows(h, h->env, 2, 1, nbins, res->L_lo)) ||
+            (rc = copy_rows(h, h->env, 3, 1, nbins, res->L_hi)) ||
+            (rc = copy_rows(h, h->oK, 1, req->n_sims, nbins, res->K_sims)) ||
+            (rc = copy_rows(h, h->oC, 1, req->n_sims, nbins, res->count_sims)))
+            return rc;
+    }
+    CK(cudaStreamSynchronize(h->stream), "result copy");
+    return STK_OK;
+}
+
+int stk_k(stk_handle* h, const double* s, int cs, const double* tt, int ct, int edge_mode,
+          int prec, int norm, double* K, double* L, double* raw_sum, int64_t* pair_count) {
+    stk_request q;
+    memset(&q, 0, sizeof q);
+    q.s = s;
+    q.cs = cs;
+    q.tt = tt;
+    q.ct = ct;
+    q.edge_mode = edge_mode;
+    q.prec = prec;
+    q.norm = norm;
+    q.exec = STK_EXEC_BATCHED;
+    stk_result r;
+    memset(&r, 0, sizeof r);
+    r.K = K;
+    r.L = L;
+    r.raw_sum = raw_sum;
+    r.pair_count = pair_count;
+    return stk_run(h, &q, &r);
+}
+
+int stk_envelope(stk_handle* h, const double* s, int cs, const double* tt, int ct, int edge_mode,
+                 int prec, int norm, int n_sims, uint64_t seed, double* K_lo, double* K_hi,
+                 double* L_lo, double* L_hi) {
+    if (!h) return fail(STK_EINVAL, "handle is NULL");
+    if (n_sims < 1) return fail(STK_EINVAL, "n_sims must be >= 1");
+    stk_request q;
+    memset(&q, 0, sizeof q);
+    q.s = s;
+    q.cs = cs;
+    q.tt = tt;
+    q.ct = ct;
+    q.edge_mode = edge_mode;
+    q.prec = prec;
+    q.norm = norm;
+    q.n_sims = n_sims;
+    q.seed = seed;
+    q.exec = STK_EXEC_BATCHED;
+    int R = 0;
+    int rc = run_job(h, &q, false, &R);
+    if (rc) return rc;
+    const int nbins = cs * ct;
+    if ((rc = copy_rows(h, h->env, 0, 1, nbins, K_lo)) || (rc = copy_rows(h, h->env, 1, 1, nbins, K_hi)) ||
+        (rc = copy_rows(h, h->env, 2, 1, nbins, L_lo)) || (rc = copy_rows(h, h->env, 3, 1, nbins, L_hi)))
+        return rc;
+    CK(cudaStreamSynchronize(h->stream), "result copy");
+    return STK_OK;
+}
+
+int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, double* x,
+                   double* y, double* t) {
+    if (!x || !y || !t) return fail(STK_EINVAL, "output arrays must not be NULL");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n out of range");
+    int rc = check_box(box);
+    if (rc) return rc;
+    const double b6[6] = {box->x0, box->x1, box->y0, box->y1, box->t0, box->t1};
+    char err[128];
+    Grid g;
+    // one cell spanning the whole box: keys and ranks are by-products here
+    if (build_grid(b6, box->x1 - box->x0, box->t1 - box->t0, &g, err, sizeof err)) {
+        g.nx = g.ny = g.nt = 1;
+        g.ncells = 1;
+        g.cw = box->x1 - box->x0;
+        g.ch = box->y1 - box->y0;
+        g.cd = box->t1 - box->t0;
+    }
+    DevBuf bx, by, bt, bk, br, bc;
+    const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaSuccess;
+    if ((rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
+        (rc = ensure(bk, b4, "keys")) || (rc = ensure(br, b4, "ranks")) ||
+        (rc = ensure(bc, 4 * (size_t)g.ncells, "counts"))) {
+        free_buf(bx), free_buf(by), free_buf(bt), free_buf(bk), free_buf(br), free_buf(bc);
+        return rc;
+    }
+    e = cudaMemsetAsync(bc.p, 0, 4 * (size_t)g.ncells, st);
+    if (e == cudaSuccess)
+        e = launch_gen_csr(n, 1, sim, seed, g, as<double>(bx), as<double>(by), as<double>(bt),
+                           as<uint32_t>(bk), as<uint32_t>(br), as<uint32_t>(bc), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, bx.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, by.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, bt.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_buf(bx), free_buf(by), free_buf(bt), free_buf(bk), free_buf(br), free_buf(bc);
+    if (e != cudaSuccess) return cuda_fail(e, "CSR generation");
+    return STK_OK;
+}
+
+int stk_last_stats(const stk_handle* h, stk_stats* out) {
+    if (!h || !out) return fail(STK_EINVAL, "handle and out must not be NULL");
+    *out = h->last;
+    return STK_OK;
+}
+
+void stk_destroy(stk_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    DevBuf* bufs[] = {&h->ux, &h->uy, &h->ut, &h->key, &h->rank, &h->counts, &h->start,
+                      &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P, &h->Plo, &h->cell_start,
+                      &h->chunks, &h->chunk_off, &h->items, &h->n_items, &h->counter,
+                      &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
+                      &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
+                      &h->oC, &h->env};
+    for (DevBuf* b : bufs) free_buf(*b);
+    if (h->d_x) cudaFree(h->d_x);
+    if (h->d_y) cudaFree(h->d_y);
+    if (h->d_t) cudaFree(h->d_t);
+    if (h->h_pc) cudaFreeHost(h->h_pc);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+}  // extern "C"

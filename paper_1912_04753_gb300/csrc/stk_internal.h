@@ -1,0 +1,139 @@
+// Internal declarations shared by the CUDA translation units of libstk.so.
+//
+// Data layout in HBM (one "realization" = the observed pattern or one CSR simulation):
+//   - points sorted by grid cell (cell key = (ct*ny + cy)*nx + cx, x fastest), so the three
+//     x-neighbouring cells of any (cy, ct) row are one contiguous run;
+//   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps, a float4
+//     (x_hi, y_hi, t_hi, sorted index) and a float2 (x_lo, y_lo) holding the point relative to
+//     its own cell origin: hi parts are multiples of a power-of-two quantum, so differences of
+//     hi parts are exact in FP32, and hi + lo carries the offset to ~2^-45 of the cell size;
+//   - cell_start[ncells + 1] per realization (offsets into that realization's n points).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stk {
+
+constexpr int kMaxThr = 64;   // thresholds per axis
+constexpr int kTab = 256;     // bin-table entries per axis
+constexpr int kBlock = 256;   // threads per pair-kernel block
+constexpr int kStage32 = 1024;  // staged neighbour points per chunk, FP32 kernel
+constexpr int kStage64 = 512;   // staged neighbour points per chunk, FP64 kernel
+constexpr int kCentreMax = 256; // centres per work item
+
+// Uniform grid over the study box.  Cell sides are >= s_max (x, y) and >= t_max (t), so every
+// pair within the thresholds lies in the 3 x 3 x 3 block of cells around the centre's cell.
+struct Grid {
+    int nx, ny, nt;
+    int64_t ncells;
+    double x0, x1, y0, y1, t0, t1;
+    double cw, ch, cd;      // cell sides
+    float qx, qy, qt;       // quantum of the FP32 hi parts (power of two)
+    float cwq, chq, cdq;    // cell sides rounded to a multiple of the quantum (exact FP32)
+    float cwl, chl, cdl;    // cell side minus its rounded value
+};
+
+// Everything the pair kernels need for one job, built on the host (see guard derivation in
+// pair_setup.cpp) and copied into shared memory by each block.
+struct PairConsts {
+    Grid g;
+    int cs, ct, nbins, edge;
+    int64_t n;
+    // FP32 bulk path: guard bands around each threshold, in d^2 and u.
+    float s_lo[kMaxThr], s_hi[kMaxThr];
+    float t_lo[kMaxThr], t_hi[kMaxThr];
+    float s2_cut, u_cut;      // candidate filter (upper band edge of the last threshold)
+    float inv_hs, inv_ht;     // bin-table index scale over r and over u
+    float tan_rel, tan_abs;   // tangency band |r - e| <= tan_rel*r + tan_abs -> FP64
+    float fast_abs;           // interior fast path margin (hi-part error of r)
+    float g_v;                // temporal-weight decision guard
+    float r_acc_min;          // edge pairs with a smaller accurate r go to FP64
+    uint8_t tab_s[kTab], tab_t[kTab];  // bit 7: entry meets a band; bits 0-6: first bin
+    // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
+    double s2[kMaxThr], tt[kMaxThr];
+    double inv_hs2_64, inv_ht_64;
+    uint8_t tab_s64[kTab], tab_t64[kTab];
+};
+
+// One unit of pair work: the centres [c_begin, c_begin + c_count) of one cell of one
+// realization (indices local to the realization's sorted arrays).
+struct WorkItem {
+    uint32_t real;
+    uint32_t cell;
+    uint32_t c_begin;
+    uint32_t c_count;
+};
+
+// Pointers to a batch of realizations laid out back to back ([m][n] and [m][ncells + 1]).
+struct RealBatch {
+    const float4* P;
+    const float2* Plo;
+    const double* X;
+    const double* Y;
+    const double* T;
+    const uint32_t* cell_start;
+    const uint8_t* mask;    // sorted centre mask of realization 0, or null
+    int64_t n;
+    int64_t ncells;
+};
+
+// Per-realization accumulators: counts and the fixed-point (2^-32) sum of (w - 1), the latter
+// split into the sums of the low and high 32-bit halves so that both are plain integer
+// reductions without carries: excess = hi * 2^32 + lo (in units of 2^-32).
+struct Accum {
+    unsigned long long* cnt;     // [m][nbins]
+    unsigned long long* exc_lo;  // [m][nbins]
+    unsigned long long* exc_hi;  // [m][nbins]
+    unsigned long long* stats;   // [0] candidates, [1] FP64 recomputes, [3] out-of-box flag
+};
+
+// ---------------------------------------------------------------- host-side launchers
+
+cudaError_t launch_keys_observed(const double* x, const double* y, const double* t, int64_t n,
+                                 const Grid& g, uint32_t* key, uint32_t* rank,
+                                 uint32_t* cell_count, int* bad_flag, cudaStream_t st);
+cudaError_t launch_validate(const double* x, const double* y, const double* t, int64_t n,
+                            const double box[6], int* bad_flag, cudaStream_t st);
+cudaError_t launch_gen_csr(int64_t n, int m, uint32_t sim0, uint64_t seed, const Grid& g,
+                           double* x, double* y, double* t, uint32_t* key, uint32_t* rank,
+                           uint32_t* cell_count, cudaStream_t st);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t count,
+                                  uint32_t* tmp, int64_t tmp_words, cudaStream_t st);
+int64_t scan_tmp_words(int64_t count);
+cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, const double* y,
+                           const double* t, const uint32_t* key, const uint32_t* rank,
+                           const uint32_t* start_global, const uint8_t* mask_in,
+                           double* X, double* Y, double* T, float4* P, float2* Plo,
+                           uint8_t* mask_out, cudaStream_t st);
+cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
+                               uint32_t* cell_start, cudaStream_t st);
+cudaError_t launch_work_counts(int m, int64_t ncells, const uint32_t* cell_start,
+                               uint32_t* chunks, cudaStream_t st);
+cudaError_t launch_work_fill(int m, int64_t ncells, const uint32_t* cell_start,
+                             const uint32_t* chunk_off, WorkItem* items, uint32_t* n_items,
+                             cudaStream_t st);
+cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid,
+                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
+                             uint32_t* counter, Accum acc, cudaStream_t st);
+cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid,
+                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
+                             uint32_t* counter, Accum acc, cudaStream_t st);
+size_t pair_fp32_smem(int nbins, int* replicas);
+size_t pair_fp64_smem(int nbins, int* replicas);
+cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
+int pair_fp32_blocks_per_sm(size_t smem);
+int pair_fp64_blocks_per_sm(size_t smem);
+cudaError_t launch_finalize(int m, int cs, int ct, const double* s, const double* tt,
+                            double coef, const int64_t* self_pairs, Accum acc, double* K,
+                            double* L, double* S, int64_t* C, cudaStream_t st);
+cudaError_t launch_envelope(int m, int nbins, int ct, const double* K, const double* s,
+                            const double* tt, double* K_lo, double* K_hi, double* L_lo,
+                            double* L_hi, cudaStream_t st);
+
+// Host: derive grid and guard constants for one job.
+int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* err, size_t errlen);
+void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
+                       int ct, int edge, PairConsts* pc);
+
+}  // namespace stk

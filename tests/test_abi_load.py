@@ -1,0 +1,72 @@
+"""CPU-side checks of the boundary: the library builds, loads without a GPU and exports every
+entry point that include/stk.h declares; argument errors are reported without device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_04753_gb300 import build as b
+
+    b.build()
+    import paper_1912_04753_gb300 as stk
+
+    return stk.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(stk_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "stk_create" in names and "stk_run" in names
+    for nm in names:
+        assert hasattr(lib, nm), f"{nm} declared in include/ but not exported"
+
+
+def test_version_and_error_string(lib):
+    import paper_1912_04753_gb300 as stk
+
+    assert "sm_103a" in stk.stk_version()
+    assert isinstance(stk.stk_last_error(), str)
+
+
+def test_argument_errors_need_no_device(lib):
+    import paper_1912_04753_gb300 as stk
+
+    box = (0, 10, 0, 10, 0, 10)
+    x = np.array([1.0, 2.0, 3.0])
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_create(x[:1], x[:1], x[:1], box)  # n < 2
+    assert e.value.code == 1
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_create(x, x, x, (0, 10, 5, 1, 0, 10))  # y0 > y1
+    assert e.value.code == 1
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_create(x, np.array([1.0, 11.0, 2.0]), x, box)  # outside the box
+    assert e.value.code == 2
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_create(x, np.array([1.0, np.nan, 2.0]), x, box)  # not finite
+    assert e.value.code == 2
+
+
+def test_python_binding_has_no_fallback(monkeypatch, tmp_path):
+    import paper_1912_04753_gb300._lib as L
+
+    monkeypatch.setattr(L, "_lib", None)
+    monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(OSError):
+        L.load()
