@@ -36,10 +36,13 @@ OPS_PER_CANDIDATE = 8
 OPS_PER_QUALIFYING = 12
 
 
-def _workload(name):
+def _workload(name, sims=None):
     from paper_1912_04753_gb300 import workloads as wl
 
-    return wl.CONFIGS[name]()
+    w = wl.CONFIGS[name]()
+    if sims is not None:
+        w.n_sims = sims
+    return w
 
 
 def _dist():
@@ -148,7 +151,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    w = _workload(args.config)
+    w = _workload(args.config, args.sims)
     steps = []
     total_pairs, total_t = 0, 0.0
     for i in range(args.warmup + args.steps):
@@ -186,7 +189,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _b.build()
     stk.load()
-    w = _workload(args.config)
+    w = _workload(args.config, args.sims)
     prec = stk.STK_PREC_FP32_GUARDED if args.prec == "fp32" else stk.STK_PREC_FP64
     exec_mode = stk.STK_EXEC_BATCHED if args.exec == "batched" else stk.STK_EXEC_PLAIN
     seed = w.sim_seed + 7919 * rank  # independent job per rank (weak scaling)
@@ -323,6 +326,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="poi_n2M")
+    ap.add_argument("--sims", type=int, default=None, help="override the simulation count")
     ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--exec", choices=["batched", "plain"], default="batched")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -155,6 +155,7 @@ typedef struct {
     double ms_total;           /* host wall time of the job */
     double ms_pair;            /* device time of the pair kernel launches */
     int64_t kernel_launches;   /* CUDA kernels this library launched for the job */
+    int64_t internal_errors;   /* consistency checks that failed inside the kernels (0 expected) */
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);

@@ -243,8 +243,7 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         const double hx = rint(ox * g.inv_qx) * g.qx;
         const double hy = rint(oy * g.inv_qy) * g.qy;
         const double ht = rint(ot * g.inv_qt) * g.qt;
-        const int64_t local = pos - (int64_t)k * n;
-        P[pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float((int)local));
+        P[pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
         Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
         if (mask_out && k == 0) mask_out[pos] = mask_in[gi];
     }
@@ -264,43 +263,43 @@ __global__ void cell_starts_kernel(int m, int64_t n, int64_t ncells,
     }
 }
 
-__global__ void work_counts_kernel(int m, int64_t ncells, const uint32_t* __restrict__ cs,
-                                   uint32_t* __restrict__ chunks) {
-    const int64_t total = ncells * (int64_t)m;
-    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+// Work units: each (realization, grid row) is cut into groups of kUnit consecutive centres.
+__global__ void work_counts_kernel(int m, int64_t nrows, int nx, const uint32_t* __restrict__ cs,
+                                   int64_t ncells, uint32_t* __restrict__ counts) {
+    const int64_t total = nrows * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi <= total;
          gi += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(gi / ncells);
-        const int64_t c = gi - (int64_t)k * ncells;
+        if (gi == total) {
+            counts[gi] = 0u;  // slot that the exclusive scan turns into the total
+            continue;
+        }
+        const int k = (int)(gi / nrows);
+        const int64_t r = gi - (int64_t)k * nrows;
         const uint32_t* s = cs + (int64_t)k * (ncells + 1);
-        const uint32_t cnt = s[c + 1] - s[c];
-        chunks[gi] = (cnt + kCentreMax - 1) / kCentreMax;
+        const uint32_t cnt = s[(r + 1) * nx] - s[r * nx];
+        counts[gi] = (cnt + kUnit - 1) / kUnit;
     }
 }
 
-__global__ void work_fill_kernel(int m, int64_t ncells, const uint32_t* __restrict__ cs,
-                                 const uint32_t* __restrict__ off, WorkItem* __restrict__ items,
-                                 uint32_t* __restrict__ n_items) {
-    const int64_t total = ncells * (int64_t)m;
+__global__ void work_fill_kernel(int m, int64_t nrows, int nx, const uint32_t* __restrict__ cs,
+                                 int64_t ncells, const uint32_t* __restrict__ off,
+                                 WorkItem* __restrict__ units) {
+    const int64_t total = nrows * (int64_t)m;
     for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
          gi += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(gi / ncells);
-        const int64_t c = gi - (int64_t)k * ncells;
+        const int k = (int)(gi / nrows);
+        const int64_t r = gi - (int64_t)k * nrows;
         const uint32_t* s = cs + (int64_t)k * (ncells + 1);
-        const uint32_t b = s[c], cnt = s[c + 1] - s[c];
-        const uint32_t parts = (cnt + kCentreMax - 1) / kCentreMax;
+        const uint32_t b = s[r * nx], cnt = s[(r + 1) * nx] - b;
         const uint32_t o = off[gi];
-        // near-equal parts of at most kCentreMax centres
-        for (uint32_t p = 0; p < parts; ++p) {
-            const uint32_t lo = (uint32_t)(((uint64_t)cnt * p) / parts);
-            const uint32_t hi = (uint32_t)(((uint64_t)cnt * (p + 1)) / parts);
+        for (uint32_t g = 0; g * kUnit < cnt; ++g) {
             WorkItem w;
             w.real = (uint32_t)k;
-            w.cell = (uint32_t)c;
-            w.c_begin = b + lo;
-            w.c_count = hi - lo;
-            items[o + p] = w;
+            w.row = (uint32_t)r;
+            w.c_begin = b + g * kUnit;
+            w.c_count = min((uint32_t)kUnit, cnt - g * kUnit);
+            units[o + g] = w;
         }
-        if (gi == total - 1) *n_items = o + parts;
     }
 }
 
@@ -401,18 +400,19 @@ cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_work_counts(int m, int64_t ncells, const uint32_t* cell_start,
-                               uint32_t* chunks, cudaStream_t st) {
-    work_counts_kernel<<<grid_for(ncells * m, kThreads), kThreads, 0, st>>>(m, ncells,
-                                                                            cell_start, chunks);
+cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
+                               uint32_t* counts, cudaStream_t st) {
+    const int64_t nrows = (int64_t)g.ny * g.nt;
+    work_counts_kernel<<<grid_for(nrows * m + 1, kThreads), kThreads, 0, st>>>(
+        m, nrows, g.nx, cell_start, g.ncells, counts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_work_fill(int m, int64_t ncells, const uint32_t* cell_start,
-                             const uint32_t* chunk_off, WorkItem* items, uint32_t* n_items,
-                             cudaStream_t st) {
-    work_fill_kernel<<<grid_for(ncells * m, kThreads), kThreads, 0, st>>>(
-        m, ncells, cell_start, chunk_off, items, n_items);
+cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
+                             const uint32_t* unit_off, WorkItem* units, cudaStream_t st) {
+    const int64_t nrows = (int64_t)g.ny * g.nt;
+    work_fill_kernel<<<grid_for(nrows * m, kThreads), kThreads, 0, st>>>(
+        m, nrows, g.nx, cell_start, g.ncells, unit_off, units);
     return cudaGetLastError();
 }
 

@@ -1,23 +1,23 @@
 // Fused pair kernels: the hot loop of the space-time K estimator (Section 3, Eq. 2 and 3).
 //
 // Replaces the paper's per-point cylinder range query on an R-tree (Section 4.2) and its
-// 2-tier weight cache (Section 4.3): each block takes work items (up to 256 centres of one
-// grid cell of one realization), stages the 27-cell neighbourhood through shared memory in
-// chunks, evaluates every candidate pair once, and adds qualifying pairs into a block-private
-// (s_bin, t_bin) histogram.  Each pair contributes to exactly one bin: the first spatial
-// threshold s_a with d <= s_a and the first temporal threshold t_b with u <= t_b, so the
-// cumulative grid over (a, b) reproduces the indicator sum of Eq. 2 at every threshold pair.
+// 2-tier weight cache (Section 4.3): every (centre, neighbour) candidate from the grid cells
+// around a centre is evaluated once, and each qualifying ordered pair is added to a
+// block-private (s_bin, t_bin) histogram: the first spatial threshold s_a with d <= s_a and the
+// first temporal threshold t_b with u <= t_b.  Cumulating the histogram over (a, b) gives the
+// indicator sum of Eq. 2 at every threshold pair.  Weights enter as fixed-point
+// (w - 1) * 2^32, so all sums are order-independent integers.
 //
 // Two precisions:
-//   * pair_fp32: candidate filter, binning and weights in FP32 on cell-relative coordinates.
-//     Every decision that FP32 cannot make with a proven error bound (a squared distance or a
-//     time lag inside the guard band of a threshold, a temporal weight near its switch, a
-//     circle nearly tangent to an edge) is recomputed in FP64 with the reference arithmetic,
-//     so counts are exact.  Weights enter as fixed-point (w - 1) * 2^32, so sums are
-//     order-independent integers.
-//   * pair_fp64: the same tiling with every pair in FP64 (the plain comparison path).
+//   * pair_fp32: filter, bins and weights in FP32 on cell-relative coordinates.  Every decision
+//     FP32 cannot make with a proven error bound (a squared distance or a time lag inside the
+//     guard band of a threshold, a temporal weight near its switch, a circle nearly tangent
+//     to an edge) is recomputed in FP64 with the reference arithmetic, so counts are exact.
+//   * pair_fp64: the same traversal with every pair in FP64 (the plain comparison path).
 //
 // This is CUDA-core work (no dense contraction), bound by instruction issue.
+#include <stddef.h>
+
 #include "stk_internal.h"
 
 #include <math.h>
@@ -26,47 +26,6 @@ namespace stk {
 namespace {
 
 constexpr int kWarps = kBlock / 32;
-constexpr uint64_t kFlushLimit = 1ull << 28;  // candidates per histogram flush (no overflow)
-
-struct Segs {
-    int start[9];   // first sorted index of the run of up to three x-cells
-    int b1[9];      // first index of the centre column's x-cell in this row
-    int b2[9];      // one past its last index
-    int pref[10];   // prefix of run lengths (position of the run in the staged sequence)
-    int dy[9], dt[9];
-};
-
-__device__ __forceinline__ void make_segments(const Grid& g, uint32_t cell,
-                                              const uint32_t* __restrict__ cs, Segs& sg) {
-    // thread 0 builds all nine runs (dy, dt in -1..1)
-    const int cx = (int)(cell % (uint32_t)g.nx);
-    const int cy = (int)((cell / (uint32_t)g.nx) % (uint32_t)g.ny);
-    const int ct = (int)(cell / ((uint32_t)g.nx * (uint32_t)g.ny));
-    int acc = 0;
-    for (int s = 0; s < 9; ++s) {
-        const int dy = s / 3 - 1, dt = s % 3 - 1;
-        const int ry = cy + dy, rt = ct + dt;
-        sg.dy[s] = dy;
-        sg.dt[s] = dt;
-        sg.pref[s] = acc;
-        if (ry < 0 || ry >= g.ny || rt < 0 || rt >= g.nt) {
-            sg.start[s] = 0;
-            sg.b1[s] = 0;
-            sg.b2[s] = 0;
-            continue;
-        }
-        const int row = (rt * g.ny + ry) * g.nx;
-        const int lo = row + (cx > 0 ? cx - 1 : 0);
-        const int hi = row + (cx + 1 < g.nx ? cx + 1 : cx);
-        const int st = (int)cs[lo];
-        const int en = (int)cs[hi + 1];
-        sg.start[s] = st;
-        sg.b1[s] = (int)cs[row + cx];
-        sg.b2[s] = (int)cs[row + cx + 1];
-        acc += en - st;
-    }
-    sg.pref[9] = acc;
-}
 
 // ---------------------------------------------------------------- exact FP64 pair (reference)
 
@@ -111,9 +70,9 @@ __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double 
     const double u = fabs(__dsub_rn(ti, tj));
     if (u > pc.tt[pc.ct - 1]) return false;
     a = 0;
-    while (d2 > pc.s2[a]) ++a;
+    while (a < pc.cs - 1 && d2 > pc.s2[a]) ++a;
     b = 0;
-    while (u > pc.tt[b]) ++b;
+    while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
     exc = 0;
     if (pc.edge) {
         const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
@@ -125,258 +84,509 @@ __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double 
 
 // ---------------------------------------------------------------- histogram flush
 
+// Adds the block's histograms to the realization's global accumulators and clears them.
+// hh (optional) counts pairs whose excess is exactly 1, i.e. 2^32 units: they go straight to
+// the high half.
 __device__ __forceinline__ void flush_hist(int real, int nbins, int reps, uint32_t* hc,
-                                           unsigned long long* he, const Accum& acc) {
+                                           unsigned long long* he, const Accum& acc,
+                                           uint32_t* hh = nullptr) {
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += kBlock) {
-        uint32_t c = 0;
+        uint32_t c = 0, h = 0;
         unsigned long long e = 0;
         for (int r = 0; r < reps; ++r) {
             c += hc[r * nbins + b];
             e += he[r * nbins + b];
             hc[r * nbins + b] = 0;
             he[r * nbins + b] = 0;
+            if (hh) {
+                h += hh[r * nbins + b];
+                hh[r * nbins + b] = 0;
+            }
         }
         const int64_t o = (int64_t)real * nbins + b;
         if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
-        if (e) {
-            atomicAdd(&acc.exc_lo[o], e & 0xffffffffull);
-            if (e >> 32) atomicAdd(&acc.exc_hi[o], e >> 32);
-        }
+        if (e & 0xffffffffull) atomicAdd(&acc.exc_lo[o], e & 0xffffffffull);
+        if ((e >> 32) + h) atomicAdd(&acc.exc_hi[o], (e >> 32) + h);
     }
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- FP32 guarded kernel
+// A warp moves its histogram replica to the global accumulators without stopping the other
+// warps that share the replica: atomicExch takes each bin's value and zeroes it, so adds that
+// race with it either make this flush or the next one.  Called after a warp has added
+// kWarpFlush candidates, which keeps every u32 count and u64 excess of a replica far from
+// overflow (at most kWarps * kWarpFlush candidates, each excess < 2^35, reach a bin between
+// two flushes).
+constexpr uint64_t kWarpFlush = 1ull << 26;
 
-struct Smem32 {
-    PairConsts pc;
-    Segs sg;
-    float4 stage[kStage32];      // x_hi, y_hi, t_hi (centre-cell frame), sorted index bits
-    float2 stage_lo[kStage32];   // x_lo, y_lo (centre-cell frame)
-    float4 cen_a[kCentreMax];    // x_hi, y_hi, t_hi, interior fast-path bound on d2_hi
-    float4 cen_b[kCentreMax];    // x_lo, y_lo, e_x, e_y
-    float cen_te[kCentreMax];    // distance to the nearer end of the study period
-    uint8_t cen_on[kCentreMax];
-    uint32_t item;
-    // histograms follow (dynamic size)
-};
+__device__ __forceinline__ void warp_flush(int real, int nbins, uint32_t* hc, uint32_t* hh,
+                                           unsigned long long* he, const Accum& acc, int lane) {
+    for (int b = lane; b < nbins; b += 32) {
+        const uint32_t c = atomicExch(&hc[b], 0u);
+        const uint32_t h = hh ? atomicExch(&hh[b], 0u) : 0u;
+        const unsigned long long e = atomicExch(&he[b], 0ull);
+        const int64_t o = (int64_t)real * nbins + b;
+        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
+        if (e & 0xffffffffull) atomicAdd(&acc.exc_lo[o], e & 0xffffffffull);
+        if ((e >> 32) + h) atomicAdd(&acc.exc_hi[o], (e >> 32) + h);
+    }
+}
 
-__device__ __forceinline__ int bin_fp32(float v2_or_v, float key, float inv_h,
-                                        const uint8_t* tab, const float* lo, const float* hi,
-                                        int nthr, bool& amb) {
-    int k = (int)(key * inv_h);
+__device__ __forceinline__ int bin_fp32(float v, float inv_h, const uint8_t* tab,
+                                        const float* lo, const float* hi, int nthr, bool& amb) {
+    int k = (int)(v * inv_h);
     k = k < kTab - 1 ? k : kTab - 1;
     const uint32_t e = tab[k];
     int a = (int)(e & 0x7fu);
     if (e & 0x80u) {
-        while (a < nthr - 1 && v2_or_v > hi[a]) ++a;
-        if (v2_or_v >= lo[a]) amb = true;
+        while (a < nthr - 1 && v > hi[a]) ++a;
+        if (v >= lo[a]) amb = true;
     }
     return a;
 }
 
+
+// Bin of value/spacing for evenly spaced thresholds at 1, 2, ..., nthr (in spacing units):
+// ceil(t) - 1, clamped, with `amb` set when t lies within tol of a threshold.  rint is taken
+// with the 1.5 * 2^23 shift, exact for 0 <= t < 2^22.
+__device__ __forceinline__ int bin_even(float t, float tol, int nthr, bool& amb) {
+    const float kShift = 12582912.0f;
+    const float ts = t + kShift;
+    const float kf = ts - kShift;
+    const int k = __float_as_int(ts) - 0x4B400000;
+    const float fr = t - kf;
+    if ((fabsf(fr) <= tol && k >= 1) || t >= (float)nthr - tol) amb = true;
+    int a = k + (fr > 0.0f ? 1 : 0) - 1;
+    a = a < 0 ? 0 : a;
+    return a < nthr - 1 ? a : nthr - 1;
+}
+
+
+// Evaluates one queued pair in FP64.  Returns false when a full entry does not qualify.
+__device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
+                                           int& bin, bool& counts,
+                                           unsigned long long& exc) {
+    const int64_t base = (int64_t)q.z * rb.n;
+    const double xi = rb.X[base + q.x], yi = rb.Y[base + q.x], ti = rb.T[base + q.x];
+    const double xj = rb.X[base + q.y], yj = rb.Y[base + q.y], tj = rb.T[base + q.y];
+    if ((q.w & 1u) == 0u) {
+        int a, b;
+        if (!pair_exact(pc, xi, yi, ti, xj, yj, tj, a, b, exc)) return false;
+        bin = a * pc.ct + b;
+        counts = true;
+    } else {
+        const bool vhalf = (q.w >> 1) & 1u;
+        bin = (int)(q.w >> 2);
+        counts = false;
+        const double dx = __dsub_rn(xi, xj);
+        const double dy = __dsub_rn(yi, yj);
+        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
+        exc = excess_fixed64(1.0 / (om * (vhalf ? 0.5 : 1.0)));
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- FP32 guarded kernel
+//
+// One warp processes one work unit (32 consecutive centres of a grid row) at a time, in
+// three phases that keep the expensive work on full warps:
+//   A (filter): the warp walks the neighbour cells of its centres (reading the sorted points
+//     straight from L2 / L1, every lane the same address), moves its centres into each
+//     neighbour cell's frame, and tests every (centre, neighbour) candidate with paired FP32
+//     arithmetic.  Candidates inside the s_max / t_max bands are appended, with their d2 and
+//     u, to a per-warp queue by ballot compaction.
+//   B (bin): 64 queued pairs at a time (two per lane): spatial and temporal bins, the count,
+//     the temporal weight and the interior test.  Pairs whose spatial weight is not 1 go to
+//     queue 2; pairs FP32 cannot decide go to the global FP64 queue.
+//   C (weight): 32 pairs of queue 2 at a time: accurate distance from the hi + lo parts and
+//     the isotropic weight of the (at most two) cutting edges; near-tangent circles go to
+//     the FP64 queue.
+// Pairs in the FP64 queue are evaluated with the reference arithmetic by exact_kernel.  FP64
+// runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this kernel
+// would hold a whole warp for thousands of cycles.
+
+constexpr int kRing = 128;   // per-warp queue of candidate pairs (linear, compacted on drain)
+constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
+constexpr int kQ2 = 64;      // per-warp queue of pairs needing the spatial weight
+static_assert(kDrain - 1 + 2 * 32 <= kRing, "queue must hold a batch plus one step");
+
+struct WarpSm {
+    float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2_hi
+    float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
+    float cen_te[32];   // distance to the nearer end of the study period
+    uint4 ring[kRing];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 | dcy << 8
+    uint4 q2[kQ2];      // (meta | vhalf << 11 | bin << 12, neighbour, -, -)
+};
+
+struct Smem32 {
+    PairConsts pc;      // only the part before `s2` is copied
+    WarpSm w[kWarps];
+    // histograms follow (dynamic size)
+};
+
+struct WarpCtx {
+    uint32_t* hc;             // this warp's histogram replica: counts
+    uint32_t* hh;             //   pairs whose weight is exactly 2 (excess 1)
+    unsigned long long* he;   //   other excess, 2^-32 units
+    int64_t base;             // realization offset into the sorted arrays
+    uint32_t real;
+    uint32_t c_begin;
+    int q2n;                  // queue 2 fill (warp-uniform)
+};
+
+// Appends the flagged lanes' pairs to the global FP64 queue.  If the queue is full the pair
+// is evaluated here instead (correct, only slower).
+__device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
+                                           const ExactQueue& xq, bool flag, uint4 entry,
+                                           int lane, WarpCtx& w) {
+    const uint32_t m = __ballot_sync(0xffffffffu, flag);
+    if (m == 0u) return;
+    unsigned int pos = 0;
+    if (lane == 0) pos = atomicAdd(xq.count, (unsigned int)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (!flag) return;
+    const unsigned int idx = pos + (unsigned int)__popc(m & ((1u << lane) - 1u));
+    if (idx < xq.cap) {
+        xq.e[idx] = entry;
+        return;
+    }
+    int bin;
+    bool counts;
+    unsigned long long exc;
+    if (exact_eval(*gpc, rb, entry, bin, counts, exc)) {
+        if (counts) atomicAdd(&w.hc[bin], 1u);
+        if (exc) atomicAdd(&w.he[bin], exc);
+    }
+}
+
+// Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.
+__device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairConsts* gpc,
+                                              WarpSm& ws, const RealBatch& rb,
+                                              const ExactQueue& xq, int cnt, int lane,
+                                              WarpCtx& w) {
+    bool exact = false;
+    uint4 xe = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < cnt) {
+        const uint4 e = ws.q2[lane];
+        const uint32_t meta = e.x, j = e.y;
+        const int cl = (int)(meta & 31u);
+        const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
+        const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
+        const bool vhalf = (meta >> 11) & 1u;
+        const int bin = (int)(meta >> 12);
+        const float4 ca = ws.cen_a[cl];
+        const float4 cb = ws.cen_b[cl];
+        const float4 p = rb.P[w.base + j];
+        const float2 lo = rb.Plo[w.base + j];
+        // centre in the neighbour's cell frame: hi part exact, lo part carries the remainder
+        const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+        const float ra = sqrtf(fmaf(dxa, dxa, dya * dya));
+        const float e1 = fminf(cb.z, cb.w), e2 = fmaxf(cb.z, cb.w);
+        const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
+        if (ra < pc.r_acc_min || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
+            exact = true;  // nearly tangent to an edge, or too short to resolve
+            xe = make_uint4(w.c_begin + (uint32_t)cl, j, w.real,
+                            1u | ((uint32_t)vhalf << 1) | ((uint32_t)bin << 2));
+        } else {
+            float a1 = 0.0f, a2 = 0.0f;
+            if (e1 < ra) a1 = atan2f(sqrtf((ra - e1) * (ra + e1)), e1);
+            if (e2 < ra) a2 = atan2f(sqrtf((ra - e2) * (ra + e2)), e2);
+            const float A = (fmaf(e1, e1, e2 * e2) < ra * ra)
+                                ? (a1 + a2 + 1.57079632679f) * 0.159154943092f
+                                : (a1 + a2) * 0.318309886184f;
+            const float xs = vhalf ? (1.0f + A) / (1.0f - A) : A / (1.0f - A);
+            const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
+            if (exc) atomicAdd(&w.he[bin], exc);
+        }
+    }
+    push_exact(gpc, rb, xq, exact, xe, lane, w);
+}
+
+// Phase B for `cnt` (<= 64) ring entries starting at index 0.
+__device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
+                                            WarpSm& ws, const RealBatch& rb,
+                                            const ExactQueue& xq, int cnt, int lane,
+                                            WarpCtx& w) {
+    const bool edge = pc.edge != 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int idx = r * 32 + lane;
+        const bool has = idx < cnt;
+        const uint4 e = ws.ring[has ? idx : 0];
+        const float d2 = __uint_as_float(e.x), u = __uint_as_float(e.y);
+        const uint32_t meta = e.z;
+        const int cl = (int)(meta & 31u);
+        bool amb = false;
+        int a, b;
+        if (pc.even_s)
+            a = bin_even(d2 * rsqrtf(fmaxf(d2, 1e-30f)) * pc.inv_ds, pc.tol_s, pc.cs, amb);
+        else
+            a = bin_fp32(d2, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, amb);
+        if (pc.even_t)
+            b = bin_even(u * pc.inv_dt, pc.tol_t, pc.ct, amb);
+        else
+            b = bin_fp32(u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, amb);
+        bool vhalf = false, interior = true;
+        if (edge) {
+            const float te = ws.cen_te[cl];
+            vhalf = u > te + pc.g_v;
+            amb |= (u > te - pc.g_v) & !vhalf;
+            interior = d2 <= ws.cen_a[cl].w;
+        }
+        const int bin = a * pc.ct + b;
+        const bool counted = has & !amb;
+        const bool defer = counted & !interior;
+        if (counted) atomicAdd(&w.hc[bin], 1u);
+        if (counted & vhalf & interior) atomicAdd(&w.hh[bin], 1u);
+        const uint32_t m = __ballot_sync(0xffffffffu, defer);
+        if (m) {
+            if (defer)
+                ws.q2[w.q2n + __popc(m & ((1u << lane) - 1u))] =
+                    make_uint4(meta | ((uint32_t)vhalf << 11) | ((uint32_t)bin << 12), e.w, 0u, 0u);
+            w.q2n += __popc(m);
+            if (w.q2n >= 32) {
+                __syncwarp();
+                drain_weights(pc, gpc, ws, rb, xq, 32, lane, w);
+                __syncwarp();
+                if (lane < w.q2n - 32) ws.q2[lane] = ws.q2[32 + lane];
+                __syncwarp();
+                w.q2n -= 32;
+            }
+        }
+        push_exact(gpc, rb, xq, has & amb,
+                   make_uint4(w.c_begin + (uint32_t)cl, e.w, w.real, 0u), lane, w);
+    }
+}
+
+// Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
+__device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
+                                          WarpSm& ws, const RealBatch& rb,
+                                          const ExactQueue& xq, uint32_t& tail, int lane,
+                                          WarpCtx& w) {
+    while (tail > 0) {
+        const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
+        __syncwarp();
+        drain_pairs(pc, gpc, ws, rb, xq, cnt, lane, w);
+        __syncwarp();
+        const uint32_t rest = tail - (uint32_t)cnt;
+        for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
+        tail = rest;
+    }
+    __syncwarp();
+    if (w.q2n > 0) {
+        drain_weights(pc, gpc, ws, rb, xq, w.q2n, lane, w);
+        w.q2n = 0;
+    }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kBlock, 3)
-pair_fp32_kernel(const PairConsts* __restrict__ gpc, RealBatch rb,
-                 const WorkItem* __restrict__ items, const uint32_t* __restrict__ n_items_p,
-                 uint32_t* __restrict__ counter, Accum acc, int reps) {
+pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
+                 const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
+                 uint32_t* __restrict__ counters, Accum acc, ExactQueue xq, int reps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem32& sm = *reinterpret_cast<Smem32*>(smem_raw);
     const PairConsts& pc = sm.pc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
-        const int words = (int)(sizeof(PairConsts) / 4);
+        const int words = (int)(offsetof(PairConsts, s2) / 4);
         const int* src = reinterpret_cast<const int*>(gpc);
         int* dst = reinterpret_cast<int*>(&sm.pc);
         for (int i = tid; i < words; i += kBlock) dst[i] = src[i];
     }
     __syncthreads();
+    WarpSm& ws = sm.w[warp];
     const int nbins = pc.nbins;
     const size_t hist_off = (sizeof(Smem32) + 15) & ~size_t(15);
     unsigned long long* he = reinterpret_cast<unsigned long long*>(smem_raw + hist_off);
     uint32_t* hc = reinterpret_cast<uint32_t*>(he + (size_t)reps * nbins);
+    uint32_t* hh = hc + (size_t)reps * nbins;
     for (int i = tid; i < reps * nbins; i += kBlock) {
         hc[i] = 0;
+        hh[i] = 0;
         he[i] = 0;
     }
-    uint32_t* my_hc = hc + (warp % reps) * nbins;
-    unsigned long long* my_he = he + (warp % reps) * nbins;
-
-    const uint32_t n_items = *n_items_p;
+    WarpCtx w;
+    w.hc = hc + (warp % reps) * nbins;
+    w.hh = hh + (warp % reps) * nbins;
+    w.he = he + (warp % reps) * nbins;
+    w.q2n = 0;
     const int64_t n = rb.n;
-    int cur_real = -1;
-    uint64_t since_flush = 0;
-    unsigned long long n_cand = 0, n_exact = 0;
+    const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
+    const int64_t nrows = (int64_t)ny * nt;
+    const uint32_t lt = (1u << lane) - 1u;
+    unsigned long long n_cand = 0;
+    uint64_t since_flush = 0;  // candidates this warp added since it last flushed (uniform)
     __syncthreads();
 
-    for (;;) {
-        if (tid == 0) sm.item = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t it = sm.item;
-        if (it >= n_items) break;
-        const WorkItem w = items[it];
-        if ((int)w.real != cur_real) {
-            if (cur_real >= 0) flush_hist(cur_real, nbins, reps, hc, he, acc);
-            cur_real = (int)w.real;
-            since_flush = 0;
-        }
-        const int64_t base = (int64_t)w.real * n;
-        const uint32_t* cs = rb.cell_start + (int64_t)w.real * (rb.ncells + 1);
-        const int C = (int)w.c_count;
-        if (tid < C) {
-            const int64_t ci = base + w.c_begin + tid;
+    for (int k = 0; k < m; ++k) {
+        const uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        const int64_t base = (int64_t)k * n;
+        const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
+        w.base = base;
+        w.real = (uint32_t)k;
+        for (;;) {
+            uint32_t u = 0;
+            if (lane == 0) u = atomicAdd(&counters[k], 1u);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (ubeg + u >= uend) break;
+            const WorkItem wi = units[ubeg + u];
+            w.c_begin = wi.c_begin;
+            const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
+            // centres: one per lane
+            const bool valid = lane < (int)wi.c_count;
+            const int64_t ci = base + wi.c_begin + (valid ? lane : 0);
             const float4 p = rb.P[ci];
-            const float2 lo = rb.Plo[ci];
+            const float2 plo = rb.Plo[ci];
             const double xi = rb.X[ci], yi = rb.Y[ci], ti = rb.T[ci];
             const float ex = (float)fmin(xi - pc.g.x0, pc.g.x1 - xi);
             const float ey = (float)fmin(yi - pc.g.y0, pc.g.y1 - yi);
             const float te = (float)fmin(ti - pc.g.t0, pc.g.t1 - ti);
             const float em = fminf(ex, ey);
             // interior: r_true < e_min * (1 - tan_rel) - tan_abs, so omega = 1 exactly
-            float rin = em * (1.0f - pc.tan_rel) - pc.tan_abs - pc.fast_abs -
-                        em * 4.76837158e-7f;
+            float rin = em * (1.0f - pc.tan_rel) - pc.tan_abs - pc.fast_abs - em * 4.76837158e-7f;
             rin = fmaxf(rin, 0.0f);
-            sm.cen_a[tid] = make_float4(p.x, p.y, p.z, rin * rin * 0.99999f);
-            sm.cen_b[tid] = make_float4(lo.x, lo.y, ex, ey);
-            sm.cen_te[tid] = te;
-            sm.cen_on[tid] =
-                (rb.mask != nullptr && w.real == 0) ? rb.mask[w.c_begin + tid] : (uint8_t)1;
-        }
-        if (tid == 0) make_segments(pc.g, w.cell, cs, sm.sg);
-        __syncthreads();
-        const int M = sm.sg.pref[9];
-        for (int cb = 0; cb < M; cb += kStage32) {
-            const int mlen = min(kStage32, M - cb);
-            if (since_flush + (uint64_t)C * (uint64_t)mlen > kFlushLimit) {
-                flush_hist(cur_real, nbins, reps, hc, he, acc);
-                since_flush = 0;
-            }
-            since_flush += (uint64_t)C * (uint64_t)mlen;
-            // stage the chunk, moving each point into the centre cell's frame
-            for (int e = tid; e < mlen; e += kBlock) {
-                const int gp = cb + e;
-                int s = 0;
-                while (s < 8 && gp >= sm.sg.pref[s + 1]) ++s;
-                const int idx = sm.sg.start[s] + (gp - sm.sg.pref[s]);
-                float4 p = rb.P[base + idx];
-                float2 lo = rb.Plo[base + idx];
-                const float sx = (float)(-1 + (idx >= sm.sg.b1[s]) + (idx >= sm.sg.b2[s]));
-                const float sy = (float)sm.sg.dy[s], st = (float)sm.sg.dt[s];
-                p.x += sx * pc.g.cwq;
-                p.y += sy * pc.g.chq;
-                p.z += st * pc.g.cdq;
-                lo.x += sx * pc.g.cwl;
-                lo.y += sy * pc.g.chl;
-                sm.stage[e] = p;
-                sm.stage_lo[e] = lo;
-            }
-            __syncthreads();
-            // warp units: 32 consecutive centres x one slice of the staged chunk
-            const int G = (C + 31) >> 5;
-            int S = (2 * kWarps + G - 1) / G;
-            const int smax = mlen / 64 > 1 ? mlen / 64 : 1;
-            S = S < smax ? S : smax;
-            const int units = G * S;
-            for (int un = warp; un < units; un += kWarps) {
-                const int g = un % G, sl = un / G;
-                const int c = g * 32 + lane;
-                const bool on = c < C && sm.cen_on[c];
-                const int cc = c < C ? c : 0;
-                const float4 ca = sm.cen_a[cc];
-                const float4 cbv = sm.cen_b[cc];
-                const float te = sm.cen_te[cc];
-                const int j0 = (int)(((int64_t)mlen * sl) / S);
-                const int j1 = (int)(((int64_t)mlen * (sl + 1)) / S);
-                if (on) n_cand += (unsigned long long)(j1 - j0);
-                for (int j = j0; j < j1; ++j) {
-                    const float4 p = sm.stage[j];
-                    const float dx = ca.x - p.x;
-                    const float dy = ca.y - p.y;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    const float u = fabsf(ca.z - p.z);
-                    if (!(on && d2 <= pc.s2_cut && u <= pc.u_cut)) continue;
-                    bool amb = false;
-                    const float r = sqrtf(d2);
-                    int a = bin_fp32(d2, r, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, amb);
-                    int b = bin_fp32(u, u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, amb);
-                    unsigned long long exc = 0;
-                    if (pc.edge && !amb) {
-                        bool vhalf = false;
-                        if (u > te - pc.g_v) {
-                            if (u > te + pc.g_v)
-                                vhalf = true;
-                            else
-                                amb = true;
-                        }
-                        float A = 0.0f;
-                        if (!amb && d2 > ca.w) {
-                            const float2 lo = sm.stage_lo[j];
-                            const float dxa = dx + (cbv.x - lo.x);
-                            const float dya = dy + (cbv.y - lo.y);
-                            const float ra = sqrtf(fmaf(dxa, dxa, dya * dya));
-                            const float ex = cbv.z, ey = cbv.w;
-                            const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
-                            if (ra < pc.r_acc_min || fabsf(ra - ex) <= band ||
-                                fabsf(ra - ey) <= band) {
-                                amb = true;
-                            } else {
-                                float ax = 0.0f, ay = 0.0f;
-                                if (ex < ra) ax = atan2f(sqrtf((ra - ex) * (ra + ex)), ex);
-                                if (ey < ra) ay = atan2f(sqrtf((ra - ey) * (ra + ey)), ey);
-                                if (fmaf(ex, ex, ey * ey) < ra * ra)
-                                    A = (ax + ay + 1.57079632679f) * 0.159154943092f;
-                                else
-                                    A = (ax + ay) * 0.318309886184f;
+            const int cx = __float_as_int(p.w);
+            ws.cen_a[lane] = make_float4(p.x, p.y, p.z, rin * rin * 0.99999f);
+            ws.cen_b[lane] = make_float4(plo.x, plo.y, ex, ey);
+            ws.cen_te[lane] = te;
+            const bool on = valid && (rb.mask == nullptr || k != 0 || rb.mask[wi.c_begin + lane]);
+            const float cut2 = on ? pc.s2_cut : -1.0f;  // inactive lanes never qualify
+            const float ucut = pc.u_cut;
+            const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
+            const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
+            const int wa = max(0, cxa - fs), wb = min(nx - 1, cxb + fs);
+            __syncwarp();
+            uint32_t tail = 0;
+            for (int dt = -ft; dt <= ft; ++dt) {
+                const int rt = ct + dt;
+                if (rt < 0 || rt >= nt) continue;
+                const float tc = fmaf((float)(-dt), pc.g.cdq, p.z);
+                for (int dy = -fs; dy <= fs; ++dy) {
+                    const int ry = cy + dy;
+                    if (ry < 0 || ry >= ny) continue;
+                    const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
+                    const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
+                    const uint32_t mrow = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
+                    for (int cxj = wa; cxj <= wb; ++cxj) {
+                        const uint32_t j0 = cs[rowkey + cxj], j1 = cs[rowkey + cxj + 1];
+                        if (j0 == j1) continue;
+                        const int dcx = cx - cxj;
+                        const float xc = fmaf((float)dcx, pc.g.cwq, p.x);
+                        const uint32_t meta =
+                            mrow | ((uint32_t)min(max(dcx + fs, 0), 7) << 5);
+                        const float2 xc2 = make_float2(xc, xc), yc2 = make_float2(yc, yc);
+                        const float2 tc2 = make_float2(tc, tc);
+                        if (on) n_cand += j1 - j0;
+                        since_flush += 32ull * (j1 - j0);
+                        for (uint32_t j = j0; j < j1; j += 2) {
+                            const bool two = j + 1 < j1;
+                            const float4 q0 = rb.P[base + j];
+                            const float4 q1 = rb.P[base + (two ? j + 1 : j)];
+                            const float2 dx = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
+                            const float2 dy2 = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
+                            const float2 dtt = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
+                            const float2 d2 = __ffma2_rn(dx, dx, __fmul2_rn(dy2, dy2));
+                            const bool k0 = (d2.x <= cut2) & (fabsf(dtt.x) <= ucut);
+                            const bool k1 = (d2.y <= cut2) & (fabsf(dtt.y) <= ucut) & two;
+                            const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
+                            if (k0)
+                                ws.ring[tail + __popc(m0 & lt)] =
+                                    make_uint4(__float_as_uint(d2.x), __float_as_uint(fabsf(dtt.x)),
+                                               meta, j);
+                            tail += __popc(m0);
+                            const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
+                            if (k1)
+                                ws.ring[tail + __popc(m1 & lt)] =
+                                    make_uint4(__float_as_uint(d2.y), __float_as_uint(fabsf(dtt.y)),
+                                               meta, j + 1);
+                            tail += __popc(m1);
+                            if (tail >= (uint32_t)kDrain) {
+                                __syncwarp();
+                                drain_pairs(pc, gpc, ws, rb, xq, kDrain, lane, w);
+                                __syncwarp();
+                                const uint32_t rest = tail - kDrain;
+                                if ((uint32_t)lane < rest) ws.ring[lane] = ws.ring[kDrain + lane];
+                                if ((uint32_t)lane + 32 < rest)
+                                    ws.ring[32 + lane] = ws.ring[kDrain + 32 + lane];
+                                __syncwarp();
+                                tail = rest;
                             }
                         }
-                        if (!amb) {
-                            const float xs = vhalf ? (1.0f + A) / (1.0f - A) : A / (1.0f - A);
-                            if (xs > 0.0f) exc = __float2ull_rn(xs * 4294967296.0f);
-                        }
                     }
-                    if (amb) {
-                        ++n_exact;
-                        const int64_t ci = base + w.c_begin + c;
-                        const int64_t cj = base + __float_as_int(p.w);
-                        if (!pair_exact(pc, rb.X[ci], rb.Y[ci], rb.T[ci], rb.X[cj], rb.Y[cj],
-                                        rb.T[cj], a, b, exc))
-                            continue;
-                    }
-                    const int bin = a * pc.ct + b;
-                    atomicAdd(&my_hc[bin], 1u);
-                    if (exc) atomicAdd(&my_he[bin], exc);
                 }
             }
-            __syncthreads();
+            drain_all(pc, gpc, ws, rb, xq, tail, lane, w);
+            if (since_flush >= kWarpFlush) {
+                warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
+                since_flush = 0;
+            }
         }
+        // every warp of the block is done with realization k: add its histograms
+        flush_hist(k, nbins, reps, hc, he, acc, hh);
+        since_flush = 0;
     }
-    if (cur_real >= 0) flush_hist(cur_real, nbins, reps, hc, he, acc);
-    // block totals of the statistics
-    for (int o = 16; o > 0; o >>= 1) {
-        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
-        n_exact += __shfl_xor_sync(0xffffffffu, n_exact, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&acc.stats[0], n_cand);
-        atomicAdd(&acc.stats[1], n_exact);
-    }
+    for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
+    if (lane == 0) atomicAdd(&acc.stats[0], n_cand);
 }
 
 // ---------------------------------------------------------------- FP64 plain kernel
+//
+// The comparison path: the same unit traversal with every pair in FP64 and the reference
+// rounding, candidates compacted per warp and evaluated 32 at a time.
+
+struct WarpSm64 {
+    double cx[32], cy[32], ct[32];
+    uint2 ring[kRing];   // (lane, neighbour)
+};
 
 struct Smem64 {
     PairConsts pc;
-    Segs sg;
-    double sx[kStage64], sy[kStage64], st[kStage64];
-    double cx[kCentreMax], cy[kCentreMax], ct[kCentreMax];
-    uint8_t cen_on[kCentreMax];
-    uint32_t item;
+    WarpSm64 w[kWarps];
 };
 
+// Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
+__device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
+                                          int lane, const double* X, const double* Y,
+                                          const double* T, uint32_t* hc,
+                                          unsigned long long* he, unsigned long long* stats) {
+    if (lane >= cnt) return;
+    const uint2 e = ws.ring[lane];
+    const double xi = ws.cx[e.x], yi = ws.cy[e.x], ti = ws.ct[e.x];
+    const double xj = X[e.y], yj = Y[e.y], tj = T[e.y];
+    const double dx = __dsub_rn(xi, xj);
+    const double dy = __dsub_rn(yi, yj);
+    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    const double u = fabs(__dsub_rn(ti, tj));
+    if (!(d2 <= pc.s2[pc.cs - 1] && u <= pc.tt[pc.ct - 1])) {
+        atomicAdd(&stats[2], 1ull);  // cannot happen: the filter used the same arithmetic
+        return;
+    }
+    int ks = (int)(d2 * pc.inv_hs2_64);
+    ks = ks < kTab - 1 ? ks : kTab - 1;
+    int a = pc.tab_s64[ks];
+    while (a < pc.cs - 1 && d2 > pc.s2[a]) ++a;
+    int kt = (int)(u * pc.inv_ht_64);
+    kt = kt < kTab - 1 ? kt : kTab - 1;
+    int b = pc.tab_t64[kt];
+    while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
+    unsigned long long exc = 0;
+    if (pc.edge) {
+        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
+        exc = excess_fixed64(1.0 / (om * v64(pc, ti, u)));
+    }
+    const int bin = a * pc.ct + b;
+    atomicAdd(&hc[bin], 1u);
+    if (exc) atomicAdd(&he[bin], exc);
+}
+
 __global__ void __launch_bounds__(kBlock, 2)
-pair_fp64_kernel(const PairConsts* __restrict__ gpc, RealBatch rb,
-                 const WorkItem* __restrict__ items, const uint32_t* __restrict__ n_items_p,
-                 uint32_t* __restrict__ counter, Accum acc, int reps) {
+pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
+                 const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
+                 uint32_t* __restrict__ counters, Accum acc, int reps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem64& sm = *reinterpret_cast<Smem64*>(smem_raw);
     const PairConsts& pc = sm.pc;
@@ -388,6 +598,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, RealBatch rb,
         for (int i = tid; i < words; i += kBlock) dst[i] = src[i];
     }
     __syncthreads();
+    WarpSm64& ws = sm.w[warp];
     const int nbins = pc.nbins;
     const size_t hist_off = (sizeof(Smem64) + 15) & ~size_t(15);
     unsigned long long* he = reinterpret_cast<unsigned long long*>(smem_raw + hist_off);
@@ -398,100 +609,109 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, RealBatch rb,
     }
     uint32_t* my_hc = hc + (warp % reps) * nbins;
     unsigned long long* my_he = he + (warp % reps) * nbins;
-    const uint32_t n_items = *n_items_p;
     const int64_t n = rb.n;
-    int cur_real = -1;
-    uint64_t since_flush = 0;
-    unsigned long long n_cand = 0;
+    const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
+    const int64_t nrows = (int64_t)ny * nt;
+    const uint32_t lt = (1u << lane) - 1u;
     const double s2max = pc.s2[pc.cs - 1], tmax = pc.tt[pc.ct - 1];
+    unsigned long long n_cand = 0;
+    uint64_t since_flush = 0;
     __syncthreads();
 
-    for (;;) {
-        if (tid == 0) sm.item = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t it = sm.item;
-        if (it >= n_items) break;
-        const WorkItem w = items[it];
-        if ((int)w.real != cur_real) {
-            if (cur_real >= 0) flush_hist(cur_real, nbins, reps, hc, he, acc);
-            cur_real = (int)w.real;
-            since_flush = 0;
-        }
-        const int64_t base = (int64_t)w.real * n;
-        const uint32_t* cs = rb.cell_start + (int64_t)w.real * (rb.ncells + 1);
-        const int C = (int)w.c_count;
-        if (tid < C) {
-            const int64_t ci = base + w.c_begin + tid;
-            sm.cx[tid] = rb.X[ci];
-            sm.cy[tid] = rb.Y[ci];
-            sm.ct[tid] = rb.T[ci];
-            sm.cen_on[tid] =
-                (rb.mask != nullptr && w.real == 0) ? rb.mask[w.c_begin + tid] : (uint8_t)1;
-        }
-        if (tid == 0) make_segments(pc.g, w.cell, cs, sm.sg);
-        __syncthreads();
-        const int M = sm.sg.pref[9];
-        for (int cb = 0; cb < M; cb += kStage64) {
-            const int mlen = min(kStage64, M - cb);
-            if (since_flush + (uint64_t)C * (uint64_t)mlen > kFlushLimit) {
-                flush_hist(cur_real, nbins, reps, hc, he, acc);
-                since_flush = 0;
-            }
-            since_flush += (uint64_t)C * (uint64_t)mlen;
-            for (int e = tid; e < mlen; e += kBlock) {
-                const int gp = cb + e;
-                int s = 0;
-                while (s < 8 && gp >= sm.sg.pref[s + 1]) ++s;
-                const int64_t idx = base + sm.sg.start[s] + (gp - sm.sg.pref[s]);
-                sm.sx[e] = rb.X[idx];
-                sm.sy[e] = rb.Y[idx];
-                sm.st[e] = rb.T[idx];
-            }
-            __syncthreads();
-            const int G = (C + 31) >> 5;
-            int S = (2 * kWarps + G - 1) / G;
-            const int smax = mlen / 64 > 1 ? mlen / 64 : 1;
-            S = S < smax ? S : smax;
-            const int units = G * S;
-            for (int un = warp; un < units; un += kWarps) {
-                const int g = un % G, sl = un / G;
-                const int c = g * 32 + lane;
-                const bool on = c < C && sm.cen_on[c];
-                const int cc = c < C ? c : 0;
-                const double xi = sm.cx[cc], yi = sm.cy[cc], ti = sm.ct[cc];
-                const int j0 = (int)(((int64_t)mlen * sl) / S);
-                const int j1 = (int)(((int64_t)mlen * (sl + 1)) / S);
-                if (on) n_cand += (unsigned long long)(j1 - j0);
-                for (int j = j0; j < j1; ++j) {
-                    const double dx = __dsub_rn(xi, sm.sx[j]);
-                    const double dy = __dsub_rn(yi, sm.sy[j]);
-                    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                    const double u = fabs(__dsub_rn(ti, sm.st[j]));
-                    if (!(on && d2 <= s2max && u <= tmax)) continue;
-                    int ks = (int)(d2 * pc.inv_hs2_64);
-                    ks = ks < kTab - 1 ? ks : kTab - 1;
-                    int a = pc.tab_s64[ks];
-                    while (d2 > pc.s2[a]) ++a;
-                    int kt = (int)(u * pc.inv_ht_64);
-                    kt = kt < kTab - 1 ? kt : kTab - 1;
-                    int b = pc.tab_t64[kt];
-                    while (u > pc.tt[b]) ++b;
-                    unsigned long long exc = 0;
-                    if (pc.edge) {
-                        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
-                        exc = excess_fixed64(1.0 / (om * v64(pc, ti, u)));
+    for (int k = 0; k < m; ++k) {
+        const uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        const int64_t base = (int64_t)k * n;
+        const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
+        const double* X = rb.X + base;
+        const double* Y = rb.Y + base;
+        const double* T = rb.T + base;
+        for (;;) {
+            uint32_t u = 0;
+            if (lane == 0) u = atomicAdd(&counters[k], 1u);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (ubeg + u >= uend) break;
+            const WorkItem wi = units[ubeg + u];
+            const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
+            const bool valid = lane < (int)wi.c_count;
+            const uint32_t ci = wi.c_begin + (valid ? lane : 0);
+            const double xi = X[ci], yi = Y[ci], ti = T[ci];
+            ws.cx[lane] = xi;
+            ws.cy[lane] = yi;
+            ws.ct[lane] = ti;
+            const int cx = __float_as_int(rb.P[base + ci].w);
+            const bool on = valid && (rb.mask == nullptr || k != 0 || rb.mask[ci]);
+            const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
+            const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
+            const int wa = max(0, cxa - fs), wb = min(nx - 1, cxb + fs);
+            __syncwarp();
+            uint32_t tail = 0;
+            for (int dt = -ft; dt <= ft; ++dt) {
+                const int rt = ct + dt;
+                if (rt < 0 || rt >= nt) continue;
+                for (int dy = -fs; dy <= fs; ++dy) {
+                    const int ry = cy + dy;
+                    if (ry < 0 || ry >= ny) continue;
+                    const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
+                    const uint32_t j0 = cs[rowkey + wa], j1 = cs[rowkey + wb + 1];
+                    if (on) n_cand += j1 - j0;
+                    since_flush += 32ull * (j1 - j0);
+                    for (uint32_t j = j0; j < j1; ++j) {
+                        const double dx = __dsub_rn(xi, X[j]);
+                        const double dy2 = __dsub_rn(yi, Y[j]);
+                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2));
+                        const double uu = fabs(__dsub_rn(ti, T[j]));
+                        const bool q = on && d2 <= s2max && uu <= tmax;
+                        const uint32_t mq = __ballot_sync(0xffffffffu, q);
+                        if (q) ws.ring[tail + __popc(mq & lt)] = make_uint2((uint32_t)lane, j);
+                        tail += __popc(mq);
+                        if (tail >= 32u) {
+                            __syncwarp();
+                            process64(pc, ws, 32, lane, X, Y, T, my_hc, my_he, acc.stats);
+                            __syncwarp();
+                            if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
+                            __syncwarp();
+                            tail -= 32;
+                        }
                     }
-                    const int bin = a * pc.ct + b;
-                    atomicAdd(&my_hc[bin], 1u);
-                    if (exc) atomicAdd(&my_he[bin], exc);
                 }
             }
-            __syncthreads();
+            __syncwarp();
+            if (tail > 0) process64(pc, ws, (int)tail, lane, X, Y, T, my_hc, my_he, acc.stats);
+            __syncwarp();
+            if (since_flush >= kWarpFlush) {
+                warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);
+                since_flush = 0;
+            }
         }
+        flush_hist(k, nbins, reps, hc, he, acc);
+        since_flush = 0;
     }
-    if (cur_real >= 0) flush_hist(cur_real, nbins, reps, hc, he, acc);
     for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
     if (lane == 0) atomicAdd(&acc.stats[0], n_cand);
+}
+
+// ---------------------------------------------------------------- FP64 queue kernel
+
+// Evaluates the pairs the FP32 kernel queued, 32 per warp, and adds them to the global
+// accumulators (integer atomics, so the order does not matter).
+__global__ void __launch_bounds__(256)
+exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQueue xq) {
+    const unsigned int pushed = *xq.count;
+    const unsigned int total = min(pushed, xq.cap);
+    const PairConsts& pc = *gpc;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&acc.stats[1], (unsigned long long)pushed);
+    for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        const uint4 q = xq.e[i];
+        int bin;
+        bool counts;
+        unsigned long long exc;
+        if (!exact_eval(pc, rb, q, bin, counts, exc)) continue;
+        const int64_t o = (int64_t)q.z * pc.nbins + bin;
+        if (counts) atomicAdd(&acc.cnt[o], 1ull);
+        if (exc & 0xffffffffull) atomicAdd(&acc.exc_lo[o], exc & 0xffffffffull);
+        if (exc >> 32) atomicAdd(&acc.exc_hi[o], exc >> 32);
+    }
 }
 
 // ---------------------------------------------------------------- finalize / envelope
@@ -564,7 +784,7 @@ __global__ void envelope_kernel(int m, int nbins, int ct, const double* __restri
     L_hi[i] = sqrt(hi / den) - s[a];
 }
 
-size_t hist_bytes(int nbins, int reps) { return (size_t)reps * nbins * 12; }
+size_t hist_bytes(int nbins, int reps) { return (size_t)reps * nbins * 16; }
 
 size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
     const size_t b = (base + 15) & ~size_t(15);
@@ -580,7 +800,7 @@ size_t pair_fp32_smem(int nbins, int* reps) {
     return smem_with_reps(sizeof(Smem32), nbins, reps, 72 * 1024);
 }
 size_t pair_fp64_smem(int nbins, int* reps) {
-    return smem_with_reps(sizeof(Smem64), nbins, reps, 100 * 1024);
+    return smem_with_reps(sizeof(Smem64), nbins, reps, 72 * 1024);
 }
 
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
@@ -612,17 +832,25 @@ int pair_fp64_blocks_per_sm(size_t smem) {
     return b > 0 ? b : 1;
 }
 
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid,
-                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
-                             uint32_t* counter, Accum acc, cudaStream_t st) {
-    pair_fp32_kernel<<<grid, kBlock, smem, st>>>(d_pc, rb, items, n_items, counter, acc, reps);
+cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
+                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
+                             uint32_t* counters, Accum acc, ExactQueue xq, cudaStream_t st) {
+    pair_fp32_kernel<<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters, acc, xq,
+                                                 reps);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid,
-                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
-                             uint32_t* counter, Accum acc, cudaStream_t st) {
-    pair_fp64_kernel<<<grid, kBlock, smem, st>>>(d_pc, rb, items, n_items, counter, acc, reps);
+cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
+                         ExactQueue xq, cudaStream_t st) {
+    exact_kernel<<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
+                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
+                             uint32_t* counters, Accum acc, cudaStream_t st) {
+    pair_fp64_kernel<<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters, acc,
+                                                 reps);
     return cudaGetLastError();
 }
 

@@ -1,9 +1,10 @@
 // Host-side set-up of a job: the uniform grid and the constants of the pair kernels.
 //
 // Guard derivation for the FP32 bulk path.  Every point is stored relative to the origin of
-// its own cell as hi + lo, with hi a multiple of the quantum q = 2^-21 * P (P the smallest
-// power of two >= the cell side).  Staged into a centre cell's frame, hi parts stay exact
-// multiples of q below 2^24 q, so the FP32 difference of two hi parts is exact and differs
+// its own cell as hi + lo, with hi a multiple of the quantum q = 2^-22 * P (P the smallest
+// power of two >= the cell side).  The centre is moved into each neighbour cell's frame
+// (at most fs <= 2 cells away), so it lies in [-2P, 3P]: hi parts stay exact multiples of q
+// below 2^24 q = 4P and the FP32 difference of two hi parts is exact; it differs
 // from the true coordinate difference by at most eps = 2q (+ FP64 rounding of the cell
 // origins, 2^-50 |box|).  From that:
 //   d2_hi = fl(fma(dx, dx, fl(dy*dy))) satisfies |d2_hi - d2| <= 2 r (eps_x + eps_y)
@@ -42,8 +43,8 @@ static double pow2_at_least(double v) {
 }
 
 static int cells_along(double extent, double thr) {
-    // largest count whose cell side stays above the threshold with a relative margin, so
-    // that rounding in the cell assignment can never separate a qualifying pair by two cells
+    // largest count whose cell side stays above thr with a relative margin, so that rounding
+    // in the cell assignment can never put a qualifying pair one cell too far apart
     const double want = thr * (1.0 + 1e-9);
     long long n = (long long)floor(extent / want);
     if (n < 1) n = 1;
@@ -51,8 +52,25 @@ static int cells_along(double extent, double thr) {
     return (int)std::min<long long>(n, 1 << 20);
 }
 
-int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* err,
-               size_t errlen) {
+static void grid_counts(double W, double H, double D, double s_max, double t_max, int f,
+                        int* nx, int* ny, int* nt) {
+    *nx = cells_along(W, s_max / f);
+    *ny = cells_along(H, s_max / f);
+    *nt = cells_along(D, t_max / f);
+    // keep the cell table modest: coarsen the largest axis until the grid fits
+    const long long kMaxCells = 1ll << 26;
+    while ((long long)*nx * *ny * *nt > kMaxCells) {
+        if (*nx >= *ny && *nx >= *nt)
+            *nx = (*nx + 1) / 2;
+        else if (*ny >= *nt)
+            *ny = (*ny + 1) / 2;
+        else
+            *nt = (*nt + 1) / 2;
+    }
+}
+
+int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f_req, Grid* g,
+               char* err, size_t errlen) {
     memset(g, 0, sizeof(*g));
     g->x0 = box[0];
     g->x1 = box[1];
@@ -61,17 +79,20 @@ int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* e
     g->t0 = box[4];
     g->t1 = box[5];
     const double W = box[1] - box[0], H = box[3] - box[2], D = box[5] - box[4];
-    int nx = cells_along(W, s_max), ny = cells_along(H, s_max), nt = cells_along(D, t_max);
-    // keep the cell table modest: coarsen the largest axis until the grid fits
-    const long long kMaxCells = 1ll << 26;
-    while ((long long)nx * ny * nt > kMaxCells) {
-        if (nx >= ny && nx >= nt)
-            nx = (nx + 1) / 2;
-        else if (ny >= nt)
-            ny = (ny + 1) / 2;
-        else
-            nt = (nt + 1) / 2;
+    // Refinement: cells of s_max/2 and t_max/2 shrink the examined neighbourhood from 27 to
+    // 15.6 threshold-cells per centre, but visit 125 cells instead of 27; worth it once a
+    // refined cell holds a few points.
+    int f = f_req;
+    if (f != 1 && f != 2) {
+        int nx2, ny2, nt2;
+        grid_counts(W, H, D, s_max, t_max, 2, &nx2, &ny2, &nt2);
+        const double per_cell = (double)n / ((double)nx2 * ny2 * nt2);
+        f = per_cell >= 8.0 ? 2 : 1;
     }
+    int nx, ny, nt;
+    grid_counts(W, H, D, s_max, t_max, f, &nx, &ny, &nt);
+    g->fs = f;
+    g->ft = f;
     g->nx = nx;
     g->ny = ny;
     g->nt = nt;
@@ -79,14 +100,14 @@ int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* e
     g->cw = W / nx;
     g->ch = H / ny;
     g->cd = D / nt;
-    if (!(g->cw >= s_max && g->ch >= s_max && g->cd >= t_max)) {
+    if (!(g->cw * f >= s_max && g->ch * f >= s_max && g->cd * f >= t_max)) {
         snprintf(err, errlen, "grid cells smaller than the thresholds");
         return 1;
     }
     const double px = pow2_at_least(g->cw), py = pow2_at_least(g->ch), pt = pow2_at_least(g->cd);
-    g->qx = (float)ldexp(px, -21);
-    g->qy = (float)ldexp(py, -21);
-    g->qt = (float)ldexp(pt, -21);
+    g->qx = (float)ldexp(px, -22);
+    g->qy = (float)ldexp(py, -22);
+    g->qt = (float)ldexp(pt, -22);
     const double cwq = nearbyint(g->cw / g->qx) * g->qx;
     const double chq = nearbyint(g->ch / g->qy) * g->qy;
     const double cdq = nearbyint(g->cd / g->qt) * g->qt;
@@ -129,16 +150,15 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
     pc->s2_cut = pc->s_hi[cs - 1];
     pc->u_cut = pc->t_hi[ct - 1];
 
-    // bin tables over r = sqrtf(d2) and over u: entry k holds the first bin any value in it
-    // can fall into, and a flag when some guard band meets the entry
-    const double rmax = sqrt((double)pc->s2_cut) * (1.0 + 1e-6);
-    pc->inv_hs = (float)(kTab / rmax);
+    // bin tables over d2 and over u: entry k holds the first bin any value in it can fall
+    // into, and a flag when some guard band meets the entry.  The index (int)(v * inv_h) is
+    // computed in FP32, so each entry is widened by a relative 2^-21 on both sides.
+    const double dmax = (double)pc->s2_cut * (1.0 + 1e-6);
+    pc->inv_hs = (float)(kTab / dmax);
     const double hs = 1.0 / (double)pc->inv_hs;
     for (int k = 0; k < kTab; ++k) {
-        const double dlo = (double)k * hs * (double)k * hs * (1.0 - ldexp(1.0, -19));
-        const double dhi = (k == kTab - 1)
-                               ? INFINITY
-                               : (double)(k + 1) * hs * (double)(k + 1) * hs * (1.0 + ldexp(1.0, -19));
+        const double dlo = (double)k * hs * (1.0 - ldexp(1.0, -21));
+        const double dhi = (k == kTab - 1) ? INFINITY : (double)(k + 1) * hs * (1.0 + ldexp(1.0, -21));
         int first = 0;
         while (first < cs && (double)pc->s_hi[first] < dlo) ++first;
         bool dirty = false;
@@ -166,6 +186,28 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
             dirty = true;
         }
         pc->tab_t[k] = (uint8_t)(first | (dirty ? 0x80 : 0));
+    }
+
+    // evenly spaced thresholds (s_a ~ a * ds): bin = ceil(r / ds) - 1, decided in FP32 unless
+    // r / ds lies within tol of an integer.  tol covers the d2 error above (divided by the
+    // distance), the rsqrt / multiply rounding (5 * 2^-24 relative), and the largest deviation
+    // of a threshold from its grid value.
+    {
+        const double ds = s[cs - 1] / cs;
+        double dev = 0.0;
+        for (int a = 0; a < cs; ++a) dev = std::max(dev, fabs(s[a] - (a + 1) * ds));
+        const double tol = 2.0 * ((ex + ey) / ds + (ex * ex + ey * ey) / (ds * ds)) +
+                           ldexp((double)(cs + 1), -19) + dev / ds + 1e-9 * cs;
+        pc->even_s = tol < 1e-3;
+        pc->inv_ds = (float)(1.0 / ds);
+        pc->tol_s = round_up(tol);
+        const double dt = tt[ct - 1] / ct;
+        double devt = 0.0;
+        for (int b = 0; b < ct; ++b) devt = std::max(devt, fabs(tt[b] - (b + 1) * dt));
+        const double tolt = 2.0 * et / dt + ldexp((double)(ct + 1), -20) + devt / dt + 1e-9 * ct;
+        pc->even_t = tolt < 1e-3;
+        pc->inv_dt = (float)(1.0 / dt);
+        pc->tol_t = round_up(tolt);
     }
 
     // weights: accurate hi + lo differences are within acc of the truth (absolute part)

@@ -82,9 +82,9 @@ struct stk_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // workspace (grow-only, resident between calls)
     DevBuf ux, uy, ut, key, rank, counts, start, scan_tmp;
-    DevBuf X, Y, T, P, Plo, cell_start, chunks, chunk_off, items, n_items, counter;
+    DevBuf X, Y, T, P, Plo, cell_start, chunks, chunk_off, items, counter;
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
-    DevBuf oK, oL, oS, oC, env;
+    DevBuf oK, oL, oS, oC, env, xq_e, xq_count;
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     stk_stats last;
     size_t smem32 = 0, smem64 = 0;
@@ -95,6 +95,8 @@ struct stk_handle {
 namespace {
 
 bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
+
+bool fp32_path(const stk_request* q) { return q->prec == STK_PREC_FP32_GUARDED; }
 
 int check_box(const stk_box* b) {
     if (!b) return fail(STK_EINVAL, "box is NULL");
@@ -195,7 +197,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     const int cs = q->cs, ct = q->ct, nbins = cs * ct;
     char err[256];
     Grid g;
-    if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], &g, err, sizeof err))
+    int f_req = 0;  // grid refinement: chosen from the density unless STK_GRID_F is set
+    if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+    if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
     cudaStream_t st = h->stream;
     CK(cudaStreamSynchronize(st), "stream sync");  // the pinned constants are reused below
@@ -205,8 +209,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
 
     // wave size: every realization of the wave is resident at once
     const int64_t ncells = g.ncells;
+    const int64_t nrows = (int64_t)g.ny * g.nt;
     const size_t per_real = (size_t)n * (24 + 24 + 16 + 8 + 8) + (size_t)(ncells + 1) * 4 +
-                            (size_t)ncells * 12 + ((size_t)ncells + (size_t)n / kCentreMax + 1) * 16 +
+                            (size_t)ncells * 12 + ((size_t)nrows + (size_t)n / kUnit + 1) * 16 +
                             (size_t)nbins * 24;
     int m_w = 1;
     if (q->exec == STK_EXEC_BATCHED) {
@@ -222,8 +227,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     }
     const int64_t mn = (int64_t)m_w * n;
     const int64_t mc = (int64_t)m_w * ncells;
-    const size_t max_items = (size_t)m_w * ((size_t)ncells + (size_t)n / kCentreMax + 1);
-    const int64_t tmp_words = std::max(scan_tmp_words(mc), scan_tmp_words(mc));
+    const int64_t mr = (int64_t)m_w * nrows + 1;
+    const size_t max_items = (size_t)m_w * ((size_t)nrows + (size_t)n / kUnit + 1);
+    const int64_t tmp_words = std::max(scan_tmp_words(mc), scan_tmp_words(mr));
     if ((rc = ensure(h->ux, 8 * mn, "unsorted x")) || (rc = ensure(h->uy, 8 * mn, "unsorted y")) ||
         (rc = ensure(h->ut, 8 * mn, "unsorted t")) || (rc = ensure(h->key, 4 * mn, "keys")) ||
         (rc = ensure(h->rank, 4 * mn, "ranks")) || (rc = ensure(h->counts, 4 * mc, "counts")) ||
@@ -233,10 +239,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 16 * mn, "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
-        (rc = ensure(h->chunks, 4 * mc, "work counts")) ||
-        (rc = ensure(h->chunk_off, 4 * mc, "work offsets")) ||
-        (rc = ensure(h->items, sizeof(WorkItem) * max_items, "work items")) ||
-        (rc = ensure(h->n_items, 16, "work item count")) || (rc = ensure(h->counter, 16, "counter")) ||
+        (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
+        (rc = ensure(h->chunk_off, 4 * mr, "work offsets")) ||
+        (rc = ensure(h->items, sizeof(WorkItem) * max_items, "work units")) ||
+        (rc = ensure(h->counter, 4 * (size_t)m_w + 16, "unit counters")) ||
         (rc = ensure(h->acc_cnt, 8 * (size_t)m_w * nbins, "histograms")) ||
         (rc = ensure(h->acc_lo, 8 * (size_t)m_w * nbins, "histograms")) ||
         (rc = ensure(h->acc_hi, 8 * (size_t)m_w * nbins, "histograms")) ||
@@ -248,6 +254,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         (rc = ensure(h->oS, 8 * (size_t)R * nbins, "S grids")) ||
         (rc = ensure(h->oC, 8 * (size_t)R * nbins, "C grids")) ||
         (rc = ensure(h->env, 8 * 4 * (size_t)nbins, "envelope")))
+        return rc;
+    // FP64 queue: pairs the FP32 kernel cannot decide (well under 0.1% of pairs in practice);
+    // overflow is still exact, evaluated inside the pair kernel
+    const unsigned int xq_cap = 1u << 24;
+    if (fp32_path(q) && ((rc = ensure(h->xq_e, sizeof(uint4) * (size_t)xq_cap, "FP64 queue")) ||
+                         (rc = ensure(h->xq_count, 16, "FP64 queue"))))
         return rc;
     const bool use_mask = include_obs && q->centre_mask != nullptr;
     int64_t masked = n;
@@ -329,19 +341,20 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
            "cell starts");
-        CK(launch_work_counts(m, ncells, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunks), st),
+        CK(launch_work_counts(m, g, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunks), st),
            "work counts");
         CK(launch_exclusive_scan(as<uint32_t>(h->chunks), as<uint32_t>(h->chunk_off),
-                                 (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
+                                 (int64_t)m * nrows + 1, as<uint32_t>(h->scan_tmp), tmp_words, st),
            "work scan");
-        CK(launch_work_fill(m, ncells, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunk_off),
-                            as<WorkItem>(h->items), as<uint32_t>(h->n_items), st),
+        CK(launch_work_fill(m, g, as<uint32_t>(h->cell_start), as<uint32_t>(h->chunk_off),
+                            as<WorkItem>(h->items), st),
            "work fill");
         const size_t accb = 8 * (size_t)m * nbins;
         CK(cudaMemsetAsync(h->acc_cnt.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->acc_lo.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->acc_hi.p, 0, accb, st), "memset");
-        CK(cudaMemsetAsync(h->counter.p, 0, 16, st), "memset");
+        CK(cudaMemsetAsync(h->counter.p, 0, 4 * (size_t)m, st), "memset");
+        if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
         for (int k = 0; k < m; ++k) selfp[k] = (obs_here && k == 0) ? masked : n;
         CK(cudaMemcpyAsync(h->self_pairs.p, selfp.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, st),
            "self pairs");
@@ -361,15 +374,24 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         acc.exc_hi = as<unsigned long long>(h->acc_hi);
         acc.stats = as<unsigned long long>(h->stats);
         CK(cudaEventRecord(h->ev0, st), "event");
+        ExactQueue xq;
+        xq.e = as<uint4>(h->xq_e);
+        xq.count = as<unsigned int>(h->xq_count);
+        xq.cap = xq_cap;
         if (fp32)
-            CK(launch_pair_fp32(as<PairConsts>(h->pc), smem, reps, grid, rb, as<WorkItem>(h->items),
-                                as<uint32_t>(h->n_items), as<uint32_t>(h->counter), acc, st),
+            CK(launch_pair_fp32(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
+                                as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
+                                as<uint32_t>(h->counter), acc, xq, st),
                "pair kernel (FP32)");
         else
-            CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, rb, as<WorkItem>(h->items),
-                                as<uint32_t>(h->n_items), as<uint32_t>(h->counter), acc, st),
+            CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
+                                as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
+                                as<uint32_t>(h->counter), acc, st),
                "pair kernel (FP64)");
         CK(cudaEventRecord(h->ev1, st), "event");
+        if (fp32) {
+            CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st), "FP64 queue");
+        }
         const int64_t row = (int64_t)r0 * nbins;
         CK(launch_finalize(m, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
                            as<double>(h->oK) + row, as<double>(h->oL) + row,
@@ -381,8 +403,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         ms_pair += ms;
         ++waves;
         launches += (obs_here ? 1 : 0) + (m > first_sim_slot ? 1 : 0) +
-                    2 * scan_launches((int64_t)m * ncells) + 4 /* scatter, starts, counts, fill */ +
-                    2 /* pair, finalize */;
+                    scan_launches((int64_t)m * ncells) + scan_launches((int64_t)m * nrows + 1) +
+                    4 /* scatter, starts, counts, fill */ +
+                    2 /* pair, finalize */ + (fp32 ? 1 : 0) /* FP64 queue */;
     }
     const int first_sim_row = include_obs ? 1 : 0;
     if (q->n_sims > 0) {
@@ -409,6 +432,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     h->last.waves = waves;
     h->last.ms_pair = ms_pair;
     h->last.kernel_launches = launches;
+    h->last.internal_errors = (int64_t)stats[2];
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     return STK_OK;
@@ -601,7 +625,7 @@ int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, d
     char err[128];
     Grid g;
     // one cell spanning the whole box: keys and ranks are by-products here
-    if (build_grid(b6, box->x1 - box->x0, box->t1 - box->t0, &g, err, sizeof err)) {
+    if (build_grid(b6, box->x1 - box->x0, box->t1 - box->t0, n, 1, &g, err, sizeof err)) {
         g.nx = g.ny = g.nt = 1;
         g.ncells = 1;
         g.cw = box->x1 - box->x0;
@@ -640,9 +664,9 @@ int stk_last_stats(const stk_handle* h, stk_stats* out) {
 void stk_destroy(stk_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    DevBuf* bufs[] = {&h->ux, &h->uy, &h->ut, &h->key, &h->rank, &h->counts, &h->start,
+    DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank, &h->counts, &h->start,
                       &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P, &h->Plo, &h->cell_start,
-                      &h->chunks, &h->chunk_off, &h->items, &h->n_items, &h->counter,
+                      &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
                       &h->oC, &h->env};

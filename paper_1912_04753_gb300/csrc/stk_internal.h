@@ -1,13 +1,14 @@
 // Internal declarations shared by the CUDA translation units of libstk.so.
 //
 // Data layout in HBM (one "realization" = the observed pattern or one CSR simulation):
-//   - points sorted by grid cell (cell key = (ct*ny + cy)*nx + cx, x fastest), so the three
-//     x-neighbouring cells of any (cy, ct) row are one contiguous run;
+//   - points sorted by grid cell (cell key = (ct*ny + cy)*nx + cx, x fastest), so the cells of
+//     one (cy, ct) row are one contiguous run;
 //   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps, a float4
-//     (x_hi, y_hi, t_hi, sorted index) and a float2 (x_lo, y_lo) holding the point relative to
+//     (x_hi, y_hi, t_hi, cell x index) and a float2 (x_lo, y_lo) holding the point relative to
 //     its own cell origin: hi parts are multiples of a power-of-two quantum, so differences of
 //     hi parts are exact in FP32, and hi + lo carries the offset to ~2^-45 of the cell size;
 //   - cell_start[ncells + 1] per realization (offsets into that realization's n points).
+//   - work units: 32 consecutive centres of one (cy, ct) row, in realization order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,26 +17,26 @@
 namespace stk {
 
 constexpr int kMaxThr = 64;   // thresholds per axis
-constexpr int kTab = 256;     // bin-table entries per axis
+constexpr int kTab = 1024;    // bin-table entries per axis
 constexpr int kBlock = 256;   // threads per pair-kernel block
-constexpr int kStage32 = 1024;  // staged neighbour points per chunk, FP32 kernel
-constexpr int kStage64 = 512;   // staged neighbour points per chunk, FP64 kernel
-constexpr int kCentreMax = 256; // centres per work item
+constexpr int kUnit = 32;      // centres per work unit (one warp)
 
-// Uniform grid over the study box.  Cell sides are >= s_max (x, y) and >= t_max (t), so every
-// pair within the thresholds lies in the 3 x 3 x 3 block of cells around the centre's cell.
+// Uniform grid over the study box.  Cell sides are >= s_max / fs (x, y) and >= t_max / ft (t)
+// with fs, ft in {1, 2}, so every pair within the thresholds lies in the block of
+// (2fs+1) x (2fs+1) x (2ft+1) cells around the centre's cell.
 struct Grid {
     int nx, ny, nt;
+    int fs, ft;
     int64_t ncells;
     double x0, x1, y0, y1, t0, t1;
     double cw, ch, cd;      // cell sides
-    float qx, qy, qt;       // quantum of the FP32 hi parts (power of two)
+    float qx, qy, qt;       // quantum of the FP32 hi parts (2^-22 x a power of two >= side)
     float cwq, chq, cdq;    // cell sides rounded to a multiple of the quantum (exact FP32)
     float cwl, chl, cdl;    // cell side minus its rounded value
 };
 
 // Everything the pair kernels need for one job, built on the host (see guard derivation in
-// pair_setup.cpp) and copied into shared memory by each block.
+// pair_setup.cpp).  The FP32 kernel copies the part before `s2` into shared memory.
 struct PairConsts {
     Grid g;
     int cs, ct, nbins, edge;
@@ -44,23 +45,26 @@ struct PairConsts {
     float s_lo[kMaxThr], s_hi[kMaxThr];
     float t_lo[kMaxThr], t_hi[kMaxThr];
     float s2_cut, u_cut;      // candidate filter (upper band edge of the last threshold)
-    float inv_hs, inv_ht;     // bin-table index scale over r and over u
+    float inv_hs, inv_ht;     // bin-table index scale over d^2 and over u
     float tan_rel, tan_abs;   // tangency band |r - e| <= tan_rel*r + tan_abs -> FP64
     float fast_abs;           // interior fast path margin (hi-part error of r)
     float g_v;                // temporal-weight decision guard
     float r_acc_min;          // edge pairs with a smaller accurate r go to FP64
     uint8_t tab_s[kTab], tab_t[kTab];  // bit 7: entry meets a band; bits 0-6: first bin
+    // evenly spaced thresholds: bins from value / spacing, exact outside +-tol of an integer
+    int even_s, even_t;
+    float inv_ds, inv_dt, tol_s, tol_t;
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
     uint8_t tab_s64[kTab], tab_t64[kTab];
 };
 
-// One unit of pair work: the centres [c_begin, c_begin + c_count) of one cell of one
-// realization (indices local to the realization's sorted arrays).
+// One unit of pair work for one warp: the centres [c_begin, c_begin + c_count) (at most 32,
+// consecutive in sorted order, all in grid row `row` = ct * ny + cy) of realization `real`.
 struct WorkItem {
     uint32_t real;
-    uint32_t cell;
+    uint32_t row;
     uint32_t c_begin;
     uint32_t c_count;
 };
@@ -85,7 +89,17 @@ struct Accum {
     unsigned long long* cnt;     // [m][nbins]
     unsigned long long* exc_lo;  // [m][nbins]
     unsigned long long* exc_hi;  // [m][nbins]
-    unsigned long long* stats;   // [0] candidates, [1] FP64 recomputes, [3] out-of-box flag
+    unsigned long long* stats;   // [0] candidates, [1] FP64 recomputes, [2] internal check
+                                 // failures, [3] out-of-box flag
+};
+
+// Pairs the FP32 kernel hands to FP64: x = centre, y = neighbour (sorted indices local to the
+// realization), z = realization, w = info: bit 0 = weight only (bins already counted),
+// bit 1 = temporal weight 1/2, bits 2.. = bin (weight-only entries).
+struct ExactQueue {
+    uint4* e;
+    unsigned int* count;  // entries pushed (may exceed cap; the excess ran in the pair kernel)
+    unsigned int cap;
 };
 
 // ---------------------------------------------------------------- host-side launchers
@@ -108,17 +122,20 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            uint8_t* mask_out, cudaStream_t st);
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
-cudaError_t launch_work_counts(int m, int64_t ncells, const uint32_t* cell_start,
-                               uint32_t* chunks, cudaStream_t st);
-cudaError_t launch_work_fill(int m, int64_t ncells, const uint32_t* cell_start,
-                             const uint32_t* chunk_off, WorkItem* items, uint32_t* n_items,
-                             cudaStream_t st);
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid,
-                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
-                             uint32_t* counter, Accum acc, cudaStream_t st);
-cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid,
-                             RealBatch rb, const WorkItem* items, const uint32_t* n_items,
-                             uint32_t* counter, Accum acc, cudaStream_t st);
+// units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)
+cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
+                               uint32_t* counts, cudaStream_t st);
+// units[unit_off[k*nrows + r] ...] for every (k, r); unit_off has m * nrows + 1 entries
+cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
+                             const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
+cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
+                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
+                             uint32_t* counters, Accum acc, ExactQueue xq, cudaStream_t st);
+cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
+                         ExactQueue xq, cudaStream_t st);
+cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
+                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
+                             uint32_t* counters, Accum acc, cudaStream_t st);
 size_t pair_fp32_smem(int nbins, int* replicas);
 size_t pair_fp64_smem(int nbins, int* replicas);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
@@ -131,8 +148,10 @@ cudaError_t launch_envelope(int m, int nbins, int ct, const double* K, const dou
                             const double* tt, double* K_lo, double* K_hi, double* L_lo,
                             double* L_hi, cudaStream_t st);
 
-// Host: derive grid and guard constants for one job.
-int build_grid(const double box[6], double s_max, double t_max, Grid* g, char* err, size_t errlen);
+// Host: derive grid and guard constants for one job.  f_req = 0 lets the planner choose the
+// refinement factor from the point density; 1 or 2 forces it.
+int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f_req, Grid* g,
+               char* err, size_t errlen);
 void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
                        int ct, int edge, PairConsts* pc);
 

@@ -89,6 +89,7 @@ def test_csr_small_config(stk, orc, wl, prec):
         assert_grids(got, want, prec, "csr n=2000")
         st = p.stats()
         assert st["qualifying_pairs"] == int(want["C"][-1, -1])
+        assert st["internal_errors"] == 0
 
 
 @pytest.mark.parametrize("prec", [0, 1])
