@@ -150,18 +150,17 @@ __device__ __forceinline__ int bin_fp32(float v, float inv_h, const uint8_t* tab
 // Bin of value/spacing for evenly spaced thresholds at 1, 2, ..., nthr (in spacing units):
 // ceil(t) - 1, clamped, with `amb` set when t lies within tol of a threshold.  rint is taken
 // with the 1.5 * 2^23 shift, exact for 0 <= t < 2^22.
-__device__ __forceinline__ int bin_even(float t, float tol, int nthr, bool& amb) {
+__device__ __forceinline__ int bin_even(float t, float tol, float top, int nthr, bool& amb) {
     const float kShift = 12582912.0f;
     const float ts = t + kShift;
     const float kf = ts - kShift;
     const int k = __float_as_int(ts) - 0x4B400000;
     const float fr = t - kf;
-    if ((fabsf(fr) <= tol && k >= 1) || t >= (float)nthr - tol) amb = true;
+    amb |= (fabsf(fr) <= tol && k >= 1) || t >= top;
     int a = k + (fr > 0.0f ? 1 : 0) - 1;
     a = a < 0 ? 0 : a;
     return a < nthr - 1 ? a : nthr - 1;
 }
-
 
 // Evaluates one queued pair in FP64.  Returns false when a full entry does not qualify.
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
@@ -216,13 +215,15 @@ struct WarpSm {
     float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2_hi
     float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
-    uint4 ring[kRing];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 | dcy << 8
+    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 | dcy << 8;
+                            // the extra slot takes the stores of lanes with nothing to queue
     uint4 q2[kQ2];      // (meta | vhalf << 11 | bin << 12, neighbour, -, -)
 };
 
 struct Smem32 {
     PairConsts pc;      // only the part before `s2` is copied
     WarpSm w[kWarps];
+    uint32_t tile;
     // histograms follow (dynamic size)
 };
 
@@ -305,47 +306,55 @@ __device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairCo
     push_exact(gpc, rb, xq, exact, xe, lane, w);
 }
 
-// Phase B for `cnt` (<= 64) ring entries starting at index 0.
+// Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
+template <bool EVEN, bool EDGE>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
-                                            WarpCtx& w) {
-    const bool edge = pc.edge != 0;
+                                            uint32_t lt, WarpCtx& w) {
+    uint4 e[2];
+    e[0] = ws.ring[lane];
+    e[1] = ws.ring[32 + lane];
+    bool amb[2], defer[2], vhalf[2];
+    int bin[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const int idx = r * 32 + lane;
-        const bool has = idx < cnt;
-        const uint4 e = ws.ring[has ? idx : 0];
-        const float d2 = __uint_as_float(e.x), u = __uint_as_float(e.y);
-        const uint32_t meta = e.z;
-        const int cl = (int)(meta & 31u);
-        bool amb = false;
+        const bool has = r * 32 + lane < cnt;
+        const float d2 = __uint_as_float(e[r].x), u = __uint_as_float(e[r].y);
+        const int cl = (int)(e[r].z & 31u);
+        bool am = false;
         int a, b;
-        if (pc.even_s)
-            a = bin_even(d2 * rsqrtf(fmaxf(d2, 1e-30f)) * pc.inv_ds, pc.tol_s, pc.cs, amb);
-        else
-            a = bin_fp32(d2, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, amb);
-        if (pc.even_t)
-            b = bin_even(u * pc.inv_dt, pc.tol_t, pc.ct, amb);
-        else
-            b = bin_fp32(u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, amb);
-        bool vhalf = false, interior = true;
-        if (edge) {
+        if (EVEN) {
+            a = bin_even(d2 * rsqrtf(fmaxf(d2, 1e-30f)) * pc.inv_ds, pc.tol_s, pc.top_s, pc.cs, am);
+            b = bin_even(u * pc.inv_dt, pc.tol_t, pc.top_t, pc.ct, am);
+        } else {
+            a = bin_fp32(d2, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, am);
+            b = bin_fp32(u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, am);
+        }
+        bool vh = false, interior = true;
+        if (EDGE) {
             const float te = ws.cen_te[cl];
-            vhalf = u > te + pc.g_v;
-            amb |= (u > te - pc.g_v) & !vhalf;
+            vh = u > te + pc.g_v;
+            am |= (u > te - pc.g_v) & !vh;
             interior = d2 <= ws.cen_a[cl].w;
         }
-        const int bin = a * pc.ct + b;
-        const bool counted = has & !amb;
-        const bool defer = counted & !interior;
-        if (counted) atomicAdd(&w.hc[bin], 1u);
-        if (counted & vhalf & interior) atomicAdd(&w.hh[bin], 1u);
-        const uint32_t m = __ballot_sync(0xffffffffu, defer);
+        bin[r] = a * pc.ct + b;  // always a valid bin, also for lanes without an entry
+        const bool counted = has & !am;
+        atomicAdd(&w.hc[bin[r]], counted ? 1u : 0u);
+        if (EDGE && counted & vh & interior) atomicAdd(&w.hh[bin[r]], 1u);
+        amb[r] = has & am;
+        defer[r] = counted & !interior;
+        vhalf[r] = vh;
+    }
+    if (!__any_sync(0xffffffffu, defer[0] | defer[1] | amb[0] | amb[1])) return;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const uint32_t m = __ballot_sync(0xffffffffu, defer[r]);
         if (m) {
-            if (defer)
-                ws.q2[w.q2n + __popc(m & ((1u << lane) - 1u))] =
-                    make_uint4(meta | ((uint32_t)vhalf << 11) | ((uint32_t)bin << 12), e.w, 0u, 0u);
+            if (defer[r])
+                ws.q2[w.q2n + __popc(m & lt)] =
+                    make_uint4(e[r].z | ((uint32_t)vhalf[r] << 11) | ((uint32_t)bin[r] << 12),
+                               e[r].w, 0u, 0u);
             w.q2n += __popc(m);
             if (w.q2n >= 32) {
                 __syncwarp();
@@ -356,20 +365,21 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                 w.q2n -= 32;
             }
         }
-        push_exact(gpc, rb, xq, has & amb,
-                   make_uint4(w.c_begin + (uint32_t)cl, e.w, w.real, 0u), lane, w);
+        push_exact(gpc, rb, xq, amb[r],
+                   make_uint4(w.c_begin + (e[r].z & 31u), e[r].w, w.real, 0u), lane, w);
     }
 }
 
 // Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
+template <bool EVEN, bool EDGE>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
                                           const ExactQueue& xq, uint32_t& tail, int lane,
-                                          WarpCtx& w) {
+                                          uint32_t lt, WarpCtx& w) {
     while (tail > 0) {
         const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs(pc, gpc, ws, rb, xq, cnt, lane, w);
+        drain_pairs<EVEN, EDGE>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
         for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
@@ -383,6 +393,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
 }
 
+template <bool EVEN, bool EDGE>
 __global__ void __launch_bounds__(kBlock, 3)
 pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
@@ -428,12 +439,20 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         w.base = base;
         w.real = (uint32_t)k;
+        // the block takes tiles of kWarps consecutive units (neighbouring centres of one row),
+        // so its warps walk the same neighbour cells together and share them in L1
+        const float4* Pk = rb.P + base;
         for (;;) {
-            uint32_t u = 0;
-            if (lane == 0) u = atomicAdd(&counters[k], 1u);
-            u = __shfl_sync(0xffffffffu, u, 0);
-            if (ubeg + u >= uend) break;
-            const WorkItem wi = units[ubeg + u];
+            if (tid == 0) sm.tile = atomicAdd(&counters[k], 1u);
+            __syncthreads();
+            const uint32_t first = ubeg + sm.tile * (uint32_t)kWarps;
+            if (first >= uend) break;  // uniform: every thread read the same tile
+            const uint32_t ui = first + (uint32_t)warp;
+            if (ui >= uend) {
+                __syncthreads();
+                continue;
+            }
+            const WorkItem wi = units[ui];
             w.c_begin = wi.c_begin;
             const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
             // centres: one per lane
@@ -484,8 +503,8 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         since_flush += 32ull * (j1 - j0);
                         for (uint32_t j = j0; j < j1; j += 2) {
                             const bool two = j + 1 < j1;
-                            const float4 q0 = rb.P[base + j];
-                            const float4 q1 = rb.P[base + (two ? j + 1 : j)];
+                            const float4 q0 = Pk[j];
+                            const float4 q1 = Pk[j + 1];  // P has padding after the last point
                             const float2 dx = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
                             const float2 dy2 = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
                             const float2 dtt = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
@@ -493,20 +512,18 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                             const bool k0 = (d2.x <= cut2) & (fabsf(dtt.x) <= ucut);
                             const bool k1 = (d2.y <= cut2) & (fabsf(dtt.y) <= ucut) & two;
                             const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
-                            if (k0)
-                                ws.ring[tail + __popc(m0 & lt)] =
-                                    make_uint4(__float_as_uint(d2.x), __float_as_uint(fabsf(dtt.x)),
-                                               meta, j);
-                            tail += __popc(m0);
                             const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
-                            if (k1)
-                                ws.ring[tail + __popc(m1 & lt)] =
-                                    make_uint4(__float_as_uint(d2.y), __float_as_uint(fabsf(dtt.y)),
-                                               meta, j + 1);
-                            tail += __popc(m1);
+                            const uint32_t n0 = (uint32_t)__popc(m0);
+                            ws.ring[k0 ? tail + __popc(m0 & lt) : (uint32_t)kRing] =
+                                make_uint4(__float_as_uint(d2.x), __float_as_uint(fabsf(dtt.x)),
+                                           meta, j);
+                            ws.ring[k1 ? tail + n0 + __popc(m1 & lt) : (uint32_t)kRing] =
+                                make_uint4(__float_as_uint(d2.y), __float_as_uint(fabsf(dtt.y)),
+                                           meta, j + 1);
+                            tail += n0 + (uint32_t)__popc(m1);
                             if (tail >= (uint32_t)kDrain) {
                                 __syncwarp();
-                                drain_pairs(pc, gpc, ws, rb, xq, kDrain, lane, w);
+                                drain_pairs<EVEN, EDGE>(pc, gpc, ws, rb, xq, kDrain, lane, lt, w);
                                 __syncwarp();
                                 const uint32_t rest = tail - kDrain;
                                 if ((uint32_t)lane < rest) ws.ring[lane] = ws.ring[kDrain + lane];
@@ -519,12 +536,14 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                     }
                 }
             }
-            drain_all(pc, gpc, ws, rb, xq, tail, lane, w);
+            drain_all<EVEN, EDGE>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
                 since_flush = 0;
             }
+            __syncthreads();  // tile done: sm.tile may be replaced
         }
+        __syncthreads();
         // every warp of the block is done with realization k: add its histograms
         flush_hist(k, nbins, reps, hc, he, acc, hh);
         since_flush = 0;
@@ -808,17 +827,22 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(pair_fp32_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem32);
-    if (e != cudaSuccess) return e;
+    const void* k32[4] = {(const void*)pair_fp32_kernel<false, false>,
+                          (const void*)pair_fp32_kernel<false, true>,
+                          (const void*)pair_fp32_kernel<true, false>,
+                          (const void*)pair_fp32_kernel<true, true>};
+    for (const void* f : k32) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem64);
 }
 
 int pair_fp32_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel, kBlock, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true>, kBlock,
+                                                      smem) !=
         cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
@@ -832,11 +856,22 @@ int pair_fp64_blocks_per_sm(size_t smem) {
     return b > 0 ? b : 1;
 }
 
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
-                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, ExactQueue xq, cudaStream_t st) {
-    pair_fp32_kernel<<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters, acc, xq,
-                                                 reps);
+cudaError_t launch_pair_fp32(const PairConsts* d_pc, bool even, bool edge, size_t smem, int reps,
+                             int grid, int m, RealBatch rb, const WorkItem* units,
+                             const uint32_t* unit_off, uint32_t* counters, Accum acc,
+                             ExactQueue xq, cudaStream_t st) {
+    if (even && edge)
+        pair_fp32_kernel<true, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                 counters, acc, xq, reps);
+    else if (even)
+        pair_fp32_kernel<true, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                  counters, acc, xq, reps);
+    else if (edge)
+        pair_fp32_kernel<false, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                  counters, acc, xq, reps);
+    else
+        pair_fp32_kernel<false, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                   counters, acc, xq, reps);
     return cudaGetLastError();
 }
 

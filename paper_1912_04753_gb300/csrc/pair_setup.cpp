@@ -208,6 +208,8 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
         pc->even_t = tolt < 1e-3;
         pc->inv_dt = (float)(1.0 / dt);
         pc->tol_t = round_up(tolt);
+        pc->top_s = round_down((double)cs - (double)pc->tol_s);
+        pc->top_t = round_down((double)ct - (double)pc->tol_t);
     }
 
     // weights: accurate hi + lo differences are within acc of the truth (absolute part)

@@ -236,7 +236,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         (rc = ensure(h->start, 4 * mc, "starts")) ||
         (rc = ensure(h->scan_tmp, 4 * tmp_words, "scan scratch")) ||
         (rc = ensure(h->X, 8 * mn, "sorted x")) || (rc = ensure(h->Y, 8 * mn, "sorted y")) ||
-        (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 16 * mn, "FP32 points")) ||
+        (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 16 * (mn + 8), "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
         (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
@@ -379,7 +379,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         xq.count = as<unsigned int>(h->xq_count);
         xq.cap = xq_cap;
         if (fp32)
-            CK(launch_pair_fp32(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
+            CK(launch_pair_fp32(as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
+                                h->h_pc->edge != 0, smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
                                 as<uint32_t>(h->counter), acc, xq, st),
                "pair kernel (FP32)");

@@ -54,6 +54,7 @@ struct PairConsts {
     // evenly spaced thresholds: bins from value / spacing, exact outside +-tol of an integer
     int even_s, even_t;
     float inv_ds, inv_dt, tol_s, tol_t;
+    float top_s, top_t;       // cs - tol_s, ct - tol_t: values at or above need FP64
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
@@ -128,9 +129,10 @@ cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
 // units[unit_off[k*nrows + r] ...] for every (k, r); unit_off has m * nrows + 1 entries
 cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
                              const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
-                             RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, ExactQueue xq, cudaStream_t st);
+cudaError_t launch_pair_fp32(const PairConsts* d_pc, bool even, bool edge, size_t smem, int reps,
+                             int grid, int m, RealBatch rb, const WorkItem* units,
+                             const uint32_t* unit_off, uint32_t* counters, Accum acc,
+                             ExactQueue xq, cudaStream_t st);
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
                          ExactQueue xq, cudaStream_t st);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
