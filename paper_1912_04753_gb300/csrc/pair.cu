@@ -237,6 +237,18 @@ struct WarpCtx {
     int q2n;                  // queue 2 fill (warp-uniform)
 };
 
+// Evaluates a pair in FP64 inside the pair kernel (only when the FP64 queue is full).
+__device__ __noinline__ void exact_inline(const PairConsts* gpc, const RealBatch& rb, uint4 entry,
+                                          uint32_t* hc, unsigned long long* he) {
+    int bin;
+    bool counts;
+    unsigned long long exc;
+    if (exact_eval(*gpc, rb, entry, bin, counts, exc)) {
+        if (counts) atomicAdd(&hc[bin], 1u);
+        if (exc) atomicAdd(&he[bin], exc);
+    }
+}
+
 // Appends the flagged lanes' pairs to the global FP64 queue.  If the queue is full the pair
 // is evaluated here instead (correct, only slower).
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
@@ -249,24 +261,23 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
     pos = __shfl_sync(0xffffffffu, pos, 0);
     if (!flag) return;
     const unsigned int idx = pos + (unsigned int)__popc(m & ((1u << lane) - 1u));
-    if (idx < xq.cap) {
+    if (idx < xq.cap)
         xq.e[idx] = entry;
-        return;
-    }
-    int bin;
-    bool counts;
-    unsigned long long exc;
-    if (exact_eval(*gpc, rb, entry, bin, counts, exc)) {
-        if (counts) atomicAdd(&w.hc[bin], 1u);
-        if (exc) atomicAdd(&w.he[bin], exc);
-    }
+    else
+        exact_inline(gpc, rb, entry, w.hc, w.he);
 }
 
-// Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.
-__device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairConsts* gpc,
-                                              WarpSm& ws, const RealBatch& rb,
-                                              const ExactQueue& xq, int cnt, int lane,
-                                              WarpCtx& w) {
+// Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.  Out of line (it
+// runs once per 32 deferred pairs) with scalar arguments, so that neither its registers nor
+// an address-taken copy of the warp state weigh on the filter loop.
+__device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
+                                           WarpSm* wsp, const float4* __restrict__ Pk,
+                                           const float2* __restrict__ Plok, RealBatch rb,
+                                           ExactQueue xq, int cnt, int lane,
+                                           unsigned long long* he, uint32_t* hc,
+                                           uint32_t real, uint32_t c_begin) {
+    const PairConsts& pc = *pcs;
+    WarpSm& ws = *wsp;
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
@@ -279,8 +290,8 @@ __device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairCo
         const int bin = (int)(meta >> 12);
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        const float4 p = rb.P[w.base + j];
-        const float2 lo = rb.Plo[w.base + j];
+        const float4 p = Pk[j];
+        const float2 lo = Plok[j];
         // centre in the neighbour's cell frame: hi part exact, lo part carries the remainder
         const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
         const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
@@ -289,7 +300,7 @@ __device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairCo
         const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
         if (ra < pc.r_acc_min || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
             exact = true;  // nearly tangent to an edge, or too short to resolve
-            xe = make_uint4(w.c_begin + (uint32_t)cl, j, w.real,
+            xe = make_uint4(c_begin + (uint32_t)cl, j, real,
                             1u | ((uint32_t)vhalf << 1) | ((uint32_t)bin << 2));
         } else {
             float a1 = 0.0f, a2 = 0.0f;
@@ -300,10 +311,20 @@ __device__ __forceinline__ void drain_weights(const PairConsts& pc, const PairCo
                                 : (a1 + a2) * 0.318309886184f;
             const float xs = vhalf ? (1.0f + A) / (1.0f - A) : A / (1.0f - A);
             const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
-            if (exc) atomicAdd(&w.he[bin], exc);
+            if (exc) atomicAdd(&he[bin], exc);
         }
     }
-    push_exact(gpc, rb, xq, exact, xe, lane, w);
+    const uint32_t m = __ballot_sync(0xffffffffu, exact);
+    if (m == 0u) return;
+    unsigned int pos = 0;
+    if (lane == 0) pos = atomicAdd(xq.count, (unsigned int)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (!exact) return;
+    const unsigned int idx = pos + (unsigned int)__popc(m & ((1u << lane) - 1u));
+    if (idx < xq.cap)
+        xq.e[idx] = xe;
+    else
+        exact_inline(gpc, rb, xe, hc, he);
 }
 
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
@@ -358,7 +379,8 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             w.q2n += __popc(m);
             if (w.q2n >= 32) {
                 __syncwarp();
-                drain_weights(pc, gpc, ws, rb, xq, 32, lane, w);
+                drain_weights(&pc, gpc, &ws, rb.P + w.base, rb.Plo + w.base, rb, xq, 32, lane,
+                              w.he, w.hc, w.real, w.c_begin);
                 __syncwarp();
                 if (lane < w.q2n - 32) ws.q2[lane] = ws.q2[32 + lane];
                 __syncwarp();
@@ -387,7 +409,8 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     }
     __syncwarp();
     if (w.q2n > 0) {
-        drain_weights(pc, gpc, ws, rb, xq, w.q2n, lane, w);
+        drain_weights(&pc, gpc, &ws, rb.P + w.base, rb.Plo + w.base, rb, xq, w.q2n, lane, w.he,
+                      w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
