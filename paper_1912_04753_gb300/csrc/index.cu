@@ -208,9 +208,10 @@ __global__ void scan_add_kernel(uint32_t* __restrict__ out, int64_t count,
 
 struct ScatterGrid {
     int nx, ny;
-    double x0, y0, t0, cw, ch, cd;
+    double x0, y0, t0, x1, y1, t1, cw, ch, cd;
     double inv_qx, inv_qy, inv_qt;
     double qx, qy, qt;
+    float tan_rel, tan_abs, fast_abs;
 };
 
 __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
@@ -222,6 +223,9 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
                                double* __restrict__ Y, double* __restrict__ T,
                                float4* __restrict__ P, float2* __restrict__ Plo,
                                uint8_t* __restrict__ mask_out) {
+    // P holds two float4 per point: (x_hi, y_hi, t_hi, cell x) and (e_x, e_y, e_t, rin2):
+    // distances to the nearer x edge, y edge and end of the period, and a bound on d2 below
+    // which the circle around the point stays clear of every edge (interior: weight 1)
     const int64_t total = n * (int64_t)m;
     for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
          gi += (int64_t)gridDim.x * blockDim.x) {
@@ -243,7 +247,15 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         const double hx = rint(ox * g.inv_qx) * g.qx;
         const double hy = rint(oy * g.inv_qy) * g.qy;
         const double ht = rint(ot * g.inv_qt) * g.qt;
-        P[pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
+        P[2 * pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
+        const float ex = (float)fmin(__dsub_rn(xi, g.x0), __dsub_rn(g.x1, xi));
+        const float ey = (float)fmin(__dsub_rn(yi, g.y0), __dsub_rn(g.y1, yi));
+        const float te = (float)fmin(__dsub_rn(ti, g.t0), __dsub_rn(g.t1, ti));
+        // interior: r_true < e_min * (1 - tan_rel) - tan_abs, so omega = 1 exactly
+        const float em = fminf(ex, ey);
+        float rin = em * (1.0f - g.tan_rel) - g.tan_abs - g.fast_abs - em * 4.76837158e-7f;
+        rin = fmaxf(rin, 0.0f);
+        P[2 * pos + 1] = make_float4(ex, ey, te, rin * rin * 0.99999f);
         Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
         if (mask_out && k == 0) mask_out[pos] = mask_in[gi];
     }
@@ -371,8 +383,14 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const double* t, const uint32_t* key, const uint32_t* rank,
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
-                           cudaStream_t st) {
+                           float tan_rel, float tan_abs, float fast_abs, cudaStream_t st) {
     ScatterGrid s;
+    s.x1 = g.x1;
+    s.y1 = g.y1;
+    s.t1 = g.t1;
+    s.tan_rel = tan_rel;
+    s.tan_abs = tan_abs;
+    s.fast_abs = fast_abs;
     s.nx = g.nx;
     s.ny = g.ny;
     s.x0 = g.x0;

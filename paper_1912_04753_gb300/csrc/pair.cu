@@ -58,11 +58,14 @@ __device__ __forceinline__ unsigned long long excess_fixed64(double w) {
     return e > 0.0 ? __double2ull_rn(e * 4294967296.0) : 0ull;
 }
 
-// Exact pair evaluation with the reference rounding (every operation rounded separately).
-// Returns false when the pair does not qualify.
+// Exact evaluation of the unordered pair {i, j} with the reference rounding (every operation
+// rounded separately): its bin and the fixed-point excess of both ordered pairs (i, j), with
+// centre i, and (j, i), with centre j.  d2 and u are the same for both orders (the FP64
+// difference of two numbers is exactly the negation of the reversed difference).  Returns
+// false when the pair does not qualify.
 __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double yi, double ti,
                                         double xj, double yj, double tj, int& a, int& b,
-                                        unsigned long long& exc) {
+                                        unsigned long long& exc_i, unsigned long long& exc_j) {
     const double dx = __dsub_rn(xi, xj);
     const double dy = __dsub_rn(yi, yj);
     const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
@@ -73,11 +76,12 @@ __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double 
     while (a < pc.cs - 1 && d2 > pc.s2[a]) ++a;
     b = 0;
     while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
-    exc = 0;
+    exc_i = 0;
+    exc_j = 0;
     if (pc.edge) {
-        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
-        const double w = 1.0 / (om * v64(pc, ti, u));
-        exc = excess_fixed64(w);
+        const double r = __dsqrt_rn(d2);
+        exc_i = excess_fixed64(1.0 / (omega64(pc, xi, yi, r) * v64(pc, ti, u)));
+        exc_j = excess_fixed64(1.0 / (omega64(pc, xj, yj, r) * v64(pc, tj, u)));
     }
     return true;
 }
@@ -137,6 +141,7 @@ __device__ __forceinline__ int bin_fp32(float v, float inv_h, const uint8_t* tab
                                         const float* lo, const float* hi, int nthr, bool& amb) {
     int k = (int)(v * inv_h);
     k = k < kTab - 1 ? k : kTab - 1;
+    k = k > 0 ? k : 0;  // also keeps lanes without an entry inside the table
     const uint32_t e = tab[k];
     int a = (int)(e & 0x7fu);
     if (e & 0x80u) {
@@ -162,62 +167,72 @@ __device__ __forceinline__ int bin_even(float t, float tol, float top, int nthr,
     return a < nthr - 1 ? a : nthr - 1;
 }
 
-// Evaluates one queued pair in FP64.  Returns false when a full entry does not qualify.
+// Evaluates one queued entry in FP64.  Full entries (w bit 0 clear) are unordered pairs
+// {x, y}: bins, a count of (w bit 1) + (w bit 2) ordered pairs (the centre of each order may
+// be masked out) and the excess of those orders.  Weight-only entries (w bit 0 set) carry the
+// bin in w >> 2 and add the excess of the single ordered pair with centre x.
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
-                                           int& bin, bool& counts,
+                                           int& bin, uint32_t& counts,
                                            unsigned long long& exc) {
     const int64_t base = (int64_t)q.z * rb.n;
     const double xi = rb.X[base + q.x], yi = rb.Y[base + q.x], ti = rb.T[base + q.x];
     const double xj = rb.X[base + q.y], yj = rb.Y[base + q.y], tj = rb.T[base + q.y];
     if ((q.w & 1u) == 0u) {
         int a, b;
-        if (!pair_exact(pc, xi, yi, ti, xj, yj, tj, a, b, exc)) return false;
+        unsigned long long ei, ej;
+        if (!pair_exact(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
+        const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
         bin = a * pc.ct + b;
-        counts = true;
+        counts = (uint32_t)act_i + (uint32_t)act_j;
+        exc = (act_i ? ei : 0ull) + (act_j ? ej : 0ull);
     } else {
-        const bool vhalf = (q.w >> 1) & 1u;
         bin = (int)(q.w >> 2);
-        counts = false;
+        counts = 0;
         const double dx = __dsub_rn(xi, xj);
         const double dy = __dsub_rn(yi, yj);
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
-        exc = excess_fixed64(1.0 / (om * (vhalf ? 0.5 : 1.0)));
+        const double u = fabs(__dsub_rn(ti, tj));
+        exc = excess_fixed64(1.0 / (omega64(pc, xi, yi, __dsqrt_rn(d2)) * v64(pc, ti, u)));
     }
     return true;
 }
 
 // ---------------------------------------------------------------- FP32 guarded kernel
 //
-// One warp processes one work unit (32 consecutive centres of a grid row) at a time, in
-// three phases that keep the expensive work on full warps:
+// Each unordered pair {i, j} is evaluated once: a centre i only scans neighbours j with a
+// larger sorted index (rows of the grid before i's row are skipped; within i's own row, a
+// single index compare), the pair's bin is found once, and both ordered pairs (i, j) and
+// (j, i) are added: the count by 2, the weight excess of each order with its own centre.
+//
+// One warp processes one work unit (32 consecutive centres of a grid row) at a time, in three
+// phases that keep the expensive work on full warps:
 //   A (filter): the warp walks the neighbour cells of its centres (reading the sorted points
-//     straight from L2 / L1, every lane the same address), moves its centres into each
-//     neighbour cell's frame, and tests every (centre, neighbour) candidate with paired FP32
-//     arithmetic.  Candidates inside the s_max / t_max bands are appended, with their d2 and
-//     u, to a per-warp queue by ballot compaction.
-//   B (bin): 64 queued pairs at a time (two per lane): spatial and temporal bins, the count,
-//     the temporal weight and the interior test.  Pairs whose spatial weight is not 1 go to
-//     queue 2; pairs FP32 cannot decide go to the global FP64 queue.
-//   C (weight): 32 pairs of queue 2 at a time: accurate distance from the hi + lo parts and
+//     from L2 / L1, every lane the same address), moves its centres into each neighbour
+//     cell's frame, and tests every candidate with paired FP32 arithmetic.  Candidates inside
+//     the s_max / t_max bands are appended, with their d2 and u, to a per-warp queue by ballot
+//     compaction.
+//   B (bin): 64 queued pairs at a time (two per lane): spatial and temporal bins, the counts,
+//     the temporal weights and the interior tests of both orders.  Orders whose spatial weight
+//     is not 1 go to queue 2; pairs or orders FP32 cannot decide go to the global FP64 queue.
+//   C (weight): 32 orders of queue 2 at a time: accurate distance from the hi + lo parts and
 //     the isotropic weight of the (at most two) cutting edges; near-tangent circles go to
 //     the FP64 queue.
-// Pairs in the FP64 queue are evaluated with the reference arithmetic by exact_kernel.  FP64
-// runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this kernel
-// would hold a whole warp for thousands of cycles.
+// Entries of the FP64 queue are evaluated with the reference arithmetic by exact_kernel.
+// FP64 runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this
+// kernel would hold a whole warp for thousands of cycles.
 
 constexpr int kRing = 128;   // per-warp queue of candidate pairs (linear, compacted on drain)
 constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
-constexpr int kQ2 = 64;      // per-warp queue of pairs needing the spatial weight
+constexpr int kQ2 = 64;      // per-warp queue of orders needing the spatial weight
 static_assert(kDrain - 1 + 2 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
-    float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2_hi
+    float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2
     float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
-    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 | dcy << 8;
-                            // the extra slot takes the stores of lanes with nothing to queue
-    uint4 q2[kQ2];      // (meta | vhalf << 11 | bin << 12, neighbour, -, -)
+    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 |
+                            // dcy << 8; the extra slot takes the stores of idle lanes
+    uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
 };
 
 struct Smem32 {
@@ -229,46 +244,49 @@ struct Smem32 {
 
 struct WarpCtx {
     uint32_t* hc;             // this warp's histogram replica: counts
-    uint32_t* hh;             //   pairs whose weight is exactly 2 (excess 1)
+    uint32_t* hh;             //   orders whose weight is exactly 2 (excess 1)
     unsigned long long* he;   //   other excess, 2^-32 units
-    int64_t base;             // realization offset into the sorted arrays
+    const float4* Pk;         // point records of the current realization
+    const uint8_t* mk;        // centre mask of the current realization, or null
     uint32_t real;
     uint32_t c_begin;
+    uint32_t onmask;          // lanes whose centre is active (mask mode)
     int q2n;                  // queue 2 fill (warp-uniform)
 };
 
-// Evaluates a pair in FP64 inside the pair kernel (only when the FP64 queue is full).
-__device__ __noinline__ void exact_inline(const PairConsts* gpc, const RealBatch& rb, uint4 entry,
+// Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
+__device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, uint4 entry,
                                           uint32_t* hc, unsigned long long* he) {
     int bin;
-    bool counts;
+    uint32_t counts;
     unsigned long long exc;
     if (exact_eval(*gpc, rb, entry, bin, counts, exc)) {
-        if (counts) atomicAdd(&hc[bin], 1u);
+        if (counts) atomicAdd(&hc[bin], counts);
         if (exc) atomicAdd(&he[bin], exc);
     }
 }
 
-// Appends the flagged lanes' pairs to the global FP64 queue.  If the queue is full the pair
+// Appends the flagged lanes' entries to the global FP64 queue.  If the queue is full the entry
 // is evaluated here instead (correct, only slower).
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
                                            const ExactQueue& xq, bool flag, uint4 entry,
-                                           int lane, WarpCtx& w) {
+                                           int lane, uint32_t lt, uint32_t* hc,
+                                           unsigned long long* he) {
     const uint32_t m = __ballot_sync(0xffffffffu, flag);
     if (m == 0u) return;
     unsigned int pos = 0;
     if (lane == 0) pos = atomicAdd(xq.count, (unsigned int)__popc(m));
     pos = __shfl_sync(0xffffffffu, pos, 0);
     if (!flag) return;
-    const unsigned int idx = pos + (unsigned int)__popc(m & ((1u << lane) - 1u));
+    const unsigned int idx = pos + (unsigned int)__popc(m & lt);
     if (idx < xq.cap)
         xq.e[idx] = entry;
     else
-        exact_inline(gpc, rb, entry, w.hc, w.he);
+        exact_inline(gpc, rb, entry, hc, he);
 }
 
 // Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.  Out of line (it
-// runs once per 32 deferred pairs) with scalar arguments, so that neither its registers nor
+// runs once per 32 deferred orders) with scalar arguments, so that neither its registers nor
 // an address-taken copy of the warp state weigh on the filter loop.
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
                                            WarpSm* wsp, const float4* __restrict__ Pk,
@@ -281,27 +299,35 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint4 e = ws.q2[lane];
+        const uint2 e = ws.q2[lane];
         const uint32_t meta = e.x, j = e.y;
         const int cl = (int)(meta & 31u);
         const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
         const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
-        const bool vhalf = (meta >> 11) & 1u;
-        const int bin = (int)(meta >> 12);
+        const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
+        const bool vhalf = (meta >> 12) & 1u;
+        const int bin = (int)(meta >> 13);
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        const float4 p = Pk[j];
+        const float4 p = Pk[2 * j];
         const float2 lo = Plok[j];
-        // centre in the neighbour's cell frame: hi part exact, lo part carries the remainder
+        // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
+        // distance is the same for both orders
         const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
         const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
         const float ra = sqrtf(fmaf(dxa, dxa, dya * dya));
-        const float e1 = fminf(cb.z, cb.w), e2 = fmaxf(cb.z, cb.w);
+        float ex = cb.z, ey = cb.w;
+        if (other) {
+            const float4 pb = Pk[2 * j + 1];
+            ex = pb.x;
+            ey = pb.y;
+        }
+        const float e1 = fminf(ex, ey), e2 = fmaxf(ex, ey);
         const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
         if (ra < pc.r_acc_min || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
             exact = true;  // nearly tangent to an edge, or too short to resolve
-            xe = make_uint4(c_begin + (uint32_t)cl, j, real,
-                            1u | ((uint32_t)vhalf << 1) | ((uint32_t)bin << 2));
+            const uint32_t ci = c_begin + (uint32_t)cl;
+            xe = make_uint4(other ? j : ci, other ? ci : j, real, 1u | ((uint32_t)bin << 2));
         } else {
             float a1 = 0.0f, a2 = 0.0f;
             if (e1 < ra) a1 = atan2f(sqrtf((ra - e1) * (ra + e1)), e1);
@@ -314,17 +340,26 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
             if (exc) atomicAdd(&he[bin], exc);
         }
     }
-    const uint32_t m = __ballot_sync(0xffffffffu, exact);
+    push_exact(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
+}
+
+__device__ __forceinline__ void push_weight(WarpSm& ws, const PairConsts& pc,
+                                            const PairConsts* gpc, const RealBatch& rb,
+                                            const ExactQueue& xq, bool flag, uint2 entry,
+                                            int lane, uint32_t lt, WarpCtx& w) {
+    const uint32_t m = __ballot_sync(0xffffffffu, flag);
     if (m == 0u) return;
-    unsigned int pos = 0;
-    if (lane == 0) pos = atomicAdd(xq.count, (unsigned int)__popc(m));
-    pos = __shfl_sync(0xffffffffu, pos, 0);
-    if (!exact) return;
-    const unsigned int idx = pos + (unsigned int)__popc(m & ((1u << lane) - 1u));
-    if (idx < xq.cap)
-        xq.e[idx] = xe;
-    else
-        exact_inline(gpc, rb, xe, hc, he);
+    if (flag) ws.q2[w.q2n + __popc(m & lt)] = entry;
+    w.q2n += __popc(m);
+    if (w.q2n >= 32) {
+        __syncwarp();
+        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 32, lane,
+                      w.he, w.hc, w.real, w.c_begin);
+        __syncwarp();
+        if (lane < w.q2n - 32) ws.q2[lane] = ws.q2[32 + lane];
+        __syncwarp();
+        w.q2n -= 32;
+    }
 }
 
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
@@ -336,7 +371,14 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
     uint4 e[2];
     e[0] = ws.ring[lane];
     e[1] = ws.ring[32 + lane];
-    bool amb[2], defer[2], vhalf[2];
+    if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
+    float4 pj[2];
+    if (EDGE) {  // neighbour's edge record: same 32-byte sector the filter just read
+        pj[0] = w.Pk[2 * (size_t)(lane < cnt ? e[0].w : 0u) + 1];
+        pj[1] = w.Pk[2 * (size_t)(32 + lane < cnt ? e[1].w : 0u) + 1];
+    }
+    bool rare = false;
+    bool full[2], di[2], dj[2], wi[2], wj[2], vi[2], vj[2], aj[2], ai[2];
     int bin[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -352,43 +394,51 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             a = bin_fp32(d2, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, am);
             b = bin_fp32(u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, am);
         }
-        bool vh = false, interior = true;
-        if (EDGE) {
-            const float te = ws.cen_te[cl];
-            vh = u > te + pc.g_v;
-            am |= (u > te - pc.g_v) & !vh;
-            interior = d2 <= ws.cen_a[cl].w;
-        }
         bin[r] = a * pc.ct + b;  // always a valid bin, also for lanes without an entry
+        const bool act_i = w.mk == nullptr || ((w.onmask >> cl) & 1u);
+        const bool act_j = w.mk == nullptr || (has && w.mk[e[r].w] != 0);
+        ai[r] = act_i;
+        aj[r] = act_j;
         const bool counted = has & !am;
-        atomicAdd(&w.hc[bin[r]], counted ? 1u : 0u);
-        if (EDGE && counted & vh & interior) atomicAdd(&w.hh[bin[r]], 1u);
-        amb[r] = has & am;
-        defer[r] = counted & !interior;
-        vhalf[r] = vh;
+        full[r] = has & am;
+        atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
+        di[r] = dj[r] = wi[r] = wj[r] = false;
+        if (EDGE) {
+            const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
+            const float te_j = pj[r].z, rin_j = pj[r].w;
+            const bool vhi = u > te_i + pc.g_v, vhj = u > te_j + pc.g_v;
+            const bool vai = (u > te_i - pc.g_v) & !vhi, vaj = (u > te_j - pc.g_v) & !vhj;
+            const bool ini = d2 <= rin_i, inj = d2 <= rin_j;
+            const bool ci = counted & act_i, cj = counted & act_j;
+            const uint32_t half = (uint32_t)(ci & vhi & !vai & ini) + (uint32_t)(cj & vhj & !vaj & inj);
+            if (half) atomicAdd(&w.hh[bin[r]], half);
+            wi[r] = ci & vai;         // temporal weight undecided: FP64 weight of order (i, j)
+            wj[r] = cj & vaj;
+            di[r] = ci & !vai & !ini;  // spatial weight needed
+            dj[r] = cj & !vaj & !inj;
+            vi[r] = vhi;
+            vj[r] = vhj;
+        }
+        rare |= full[r] | wi[r] | wj[r] | di[r] | dj[r];
     }
-    if (!__any_sync(0xffffffffu, defer[0] | defer[1] | amb[0] | amb[1])) return;
+    if (!__any_sync(0xffffffffu, rare)) return;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const uint32_t m = __ballot_sync(0xffffffffu, defer[r]);
-        if (m) {
-            if (defer[r])
-                ws.q2[w.q2n + __popc(m & lt)] =
-                    make_uint4(e[r].z | ((uint32_t)vhalf[r] << 11) | ((uint32_t)bin[r] << 12),
-                               e[r].w, 0u, 0u);
-            w.q2n += __popc(m);
-            if (w.q2n >= 32) {
-                __syncwarp();
-                drain_weights(&pc, gpc, &ws, rb.P + w.base, rb.Plo + w.base, rb, xq, 32, lane,
-                              w.he, w.hc, w.real, w.c_begin);
-                __syncwarp();
-                if (lane < w.q2n - 32) ws.q2[lane] = ws.q2[32 + lane];
-                __syncwarp();
-                w.q2n -= 32;
-            }
+        const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
+        if (EDGE) {
+            const uint32_t mb = e[r].z | ((uint32_t)bin[r] << 13);
+            push_weight(ws, pc, gpc, rb, xq, di[r], make_uint2(mb | ((uint32_t)vi[r] << 12), j),
+                        lane, lt, w);
+            push_weight(ws, pc, gpc, rb, xq, dj[r],
+                        make_uint2(mb | (1u << 11) | ((uint32_t)vj[r] << 12), j), lane, lt, w);
+            push_exact(gpc, rb, xq, wi[r], make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)),
+                       lane, lt, w.hc, w.he);
+            push_exact(gpc, rb, xq, wj[r], make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)),
+                       lane, lt, w.hc, w.he);
         }
-        push_exact(gpc, rb, xq, amb[r],
-                   make_uint4(w.c_begin + (e[r].z & 31u), e[r].w, w.real, 0u), lane, w);
+        push_exact(gpc, rb, xq, full[r],
+                   make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
+                   lane, lt, w.hc, w.he);
     }
 }
 
@@ -409,8 +459,8 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     }
     __syncwarp();
     if (w.q2n > 0) {
-        drain_weights(&pc, gpc, &ws, rb.P + w.base, rb.Plo + w.base, rb, xq, w.q2n, lane, w.he,
-                      w.hc, w.real, w.c_begin);
+        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, w.q2n, lane,
+                      w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
@@ -460,11 +510,12 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         const uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
         const int64_t base = (int64_t)k * n;
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
-        w.base = base;
+        const float4* Pk = rb.P + 2 * base;
+        w.Pk = Pk;
         w.real = (uint32_t)k;
+        w.mk = (rb.mask != nullptr && k == 0) ? rb.mask : nullptr;
         // the block takes tiles of kWarps consecutive units (neighbouring centres of one row),
         // so its warps walk the same neighbour cells together and share them in L1
-        const float4* Pk = rb.P + base;
         for (;;) {
             if (tid == 0) sm.tile = atomicAdd(&counters[k], 1u);
             __syncthreads();
@@ -480,36 +531,35 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
             // centres: one per lane
             const bool valid = lane < (int)wi.c_count;
-            const int64_t ci = base + wi.c_begin + (valid ? lane : 0);
-            const float4 p = rb.P[ci];
-            const float2 plo = rb.Plo[ci];
-            const double xi = rb.X[ci], yi = rb.Y[ci], ti = rb.T[ci];
-            const float ex = (float)fmin(xi - pc.g.x0, pc.g.x1 - xi);
-            const float ey = (float)fmin(yi - pc.g.y0, pc.g.y1 - yi);
-            const float te = (float)fmin(ti - pc.g.t0, pc.g.t1 - ti);
-            const float em = fminf(ex, ey);
-            // interior: r_true < e_min * (1 - tan_rel) - tan_abs, so omega = 1 exactly
-            float rin = em * (1.0f - pc.tan_rel) - pc.tan_abs - pc.fast_abs - em * 4.76837158e-7f;
-            rin = fmaxf(rin, 0.0f);
+            const uint32_t myi = wi.c_begin + (valid ? lane : 0);
+            const float4 p = Pk[2 * (size_t)myi];
+            const float4 pe = Pk[2 * (size_t)myi + 1];
+            const float2 plo = rb.Plo[base + myi];
             const int cx = __float_as_int(p.w);
-            ws.cen_a[lane] = make_float4(p.x, p.y, p.z, rin * rin * 0.99999f);
-            ws.cen_b[lane] = make_float4(plo.x, plo.y, ex, ey);
-            ws.cen_te[lane] = te;
-            const bool on = valid && (rb.mask == nullptr || k != 0 || rb.mask[wi.c_begin + lane]);
-            const float cut2 = on ? pc.s2_cut : -1.0f;  // inactive lanes never qualify
+            ws.cen_a[lane] = make_float4(p.x, p.y, p.z, pe.w);
+            ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
+            ws.cen_te[lane] = pe.z;
+            w.onmask = __ballot_sync(0xffffffffu, valid && (w.mk == nullptr || w.mk[myi] != 0));
+            const float cut2 = valid ? pc.s2_cut : -1.0f;  // idle lanes never qualify
             const float ucut = pc.u_cut;
             const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
             const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
-            const int wa = max(0, cxa - fs), wb = min(nx - 1, cxb + fs);
+            const int wb = min(nx - 1, cxb + fs);
             __syncwarp();
             uint32_t tail = 0;
-            for (int dt = -ft; dt <= ft; ++dt) {
+            // rows from the centres' own row onward in key order (t major, y minor)
+            for (int dt = 0; dt <= ft; ++dt) {
                 const int rt = ct + dt;
-                if (rt < 0 || rt >= nt) continue;
+                if (rt >= nt) break;
                 const float tc = fmaf((float)(-dt), pc.g.cdq, p.z);
-                for (int dy = -fs; dy <= fs; ++dy) {
+                for (int dy = (dt == 0 ? 0 : -fs); dy <= fs; ++dy) {
                     const int ry = cy + dy;
                     if (ry < 0 || ry >= ny) continue;
+                    const bool own = (dt == 0) & (dy == 0);
+                    // in the own row only neighbours after the centre (sorted index > myi);
+                    // cells left of the first centre's cell hold none of them
+                    const int jlo = own ? (int)myi : -1;
+                    const int wa = own ? cxa : max(0, cxa - fs);
                     const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
                     const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
                     const uint32_t mrow = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
@@ -522,18 +572,18 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                             mrow | ((uint32_t)min(max(dcx + fs, 0), 7) << 5);
                         const float2 xc2 = make_float2(xc, xc), yc2 = make_float2(yc, yc);
                         const float2 tc2 = make_float2(tc, tc);
-                        if (on) n_cand += j1 - j0;
+                        if (valid) n_cand += j1 - j0;
                         since_flush += 32ull * (j1 - j0);
                         for (uint32_t j = j0; j < j1; j += 2) {
-                            const bool two = j + 1 < j1;
-                            const float4 q0 = Pk[j];
-                            const float4 q1 = Pk[j + 1];  // P has padding after the last point
+                            const float4 q0 = Pk[2 * (size_t)j];
+                            const float4 q1 = Pk[2 * (size_t)j + 2];  // records are padded
                             const float2 dx = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
                             const float2 dy2 = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
                             const float2 dtt = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
                             const float2 d2 = __ffma2_rn(dx, dx, __fmul2_rn(dy2, dy2));
-                            const bool k0 = (d2.x <= cut2) & (fabsf(dtt.x) <= ucut);
-                            const bool k1 = (d2.y <= cut2) & (fabsf(dtt.y) <= ucut) & two;
+                            const bool k0 = (d2.x <= cut2) & (fabsf(dtt.x) <= ucut) & ((int)j > jlo);
+                            const bool k1 = (d2.y <= cut2) & (fabsf(dtt.y) <= ucut) &
+                                            ((int)j + 1 > jlo) & (j + 1 < j1);
                             const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
                             const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
                             const uint32_t n0 = (uint32_t)__popc(m0);
@@ -577,8 +627,8 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
 
 // ---------------------------------------------------------------- FP64 plain kernel
 //
-// The comparison path: the same unit traversal with every pair in FP64 and the reference
-// rounding, candidates compacted per warp and evaluated 32 at a time.
+// The comparison path: the same traversal (each unordered pair once) with every pair in FP64
+// and the reference rounding; candidates are compacted per warp and evaluated 32 at a time.
 
 struct WarpSm64 {
     double cx[32], cy[32], ct[32];
@@ -593,8 +643,9 @@ struct Smem64 {
 // Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
 __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
                                           int lane, const double* X, const double* Y,
-                                          const double* T, uint32_t* hc,
-                                          unsigned long long* he, unsigned long long* stats) {
+                                          const double* T, const uint8_t* mk, uint32_t onmask,
+                                          uint32_t* hc, unsigned long long* he,
+                                          unsigned long long* stats) {
     if (lane >= cnt) return;
     const uint2 e = ws.ring[lane];
     const double xi = ws.cx[e.x], yi = ws.cy[e.x], ti = ws.ct[e.x];
@@ -615,13 +666,16 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     kt = kt < kTab - 1 ? kt : kTab - 1;
     int b = pc.tab_t64[kt];
     while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
+    const bool act_i = mk == nullptr || ((onmask >> e.x) & 1u);
+    const bool act_j = mk == nullptr || mk[e.y] != 0;
     unsigned long long exc = 0;
     if (pc.edge) {
-        const double om = omega64(pc, xi, yi, __dsqrt_rn(d2));
-        exc = excess_fixed64(1.0 / (om * v64(pc, ti, u)));
+        const double r = __dsqrt_rn(d2);
+        if (act_i) exc += excess_fixed64(1.0 / (omega64(pc, xi, yi, r) * v64(pc, ti, u)));
+        if (act_j) exc += excess_fixed64(1.0 / (omega64(pc, xj, yj, r) * v64(pc, tj, u)));
     }
     const int bin = a * pc.ct + b;
-    atomicAdd(&hc[bin], 1u);
+    atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
     if (exc) atomicAdd(&he[bin], exc);
 }
 
@@ -667,6 +721,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         const double* X = rb.X + base;
         const double* Y = rb.Y + base;
         const double* T = rb.T + base;
+        const uint8_t* mk = (rb.mask != nullptr && k == 0) ? rb.mask : nullptr;
         for (;;) {
             uint32_t u = 0;
             if (lane == 0) u = atomicAdd(&counters[k], 1u);
@@ -680,35 +735,39 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             ws.cx[lane] = xi;
             ws.cy[lane] = yi;
             ws.ct[lane] = ti;
-            const int cx = __float_as_int(rb.P[base + ci].w);
-            const bool on = valid && (rb.mask == nullptr || k != 0 || rb.mask[ci]);
+            const int cx = __float_as_int(rb.P[2 * (base + ci)].w);
+            const uint32_t onmask = __ballot_sync(0xffffffffu, valid && (mk == nullptr || mk[ci]));
             const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
             const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
-            const int wa = max(0, cxa - fs), wb = min(nx - 1, cxb + fs);
+            const int wb = min(nx - 1, cxb + fs);
             __syncwarp();
             uint32_t tail = 0;
-            for (int dt = -ft; dt <= ft; ++dt) {
+            for (int dt = 0; dt <= ft; ++dt) {
                 const int rt = ct + dt;
-                if (rt < 0 || rt >= nt) continue;
-                for (int dy = -fs; dy <= fs; ++dy) {
+                if (rt >= nt) break;
+                for (int dy = (dt == 0 ? 0 : -fs); dy <= fs; ++dy) {
                     const int ry = cy + dy;
                     if (ry < 0 || ry >= ny) continue;
+                    const bool own = (dt == 0) & (dy == 0);
+                    const int jlo = own ? (int)ci : -1;
+                    const int wa = own ? cxa : max(0, cxa - fs);
                     const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
                     const uint32_t j0 = cs[rowkey + wa], j1 = cs[rowkey + wb + 1];
-                    if (on) n_cand += j1 - j0;
+                    if (valid) n_cand += j1 - j0;
                     since_flush += 32ull * (j1 - j0);
                     for (uint32_t j = j0; j < j1; ++j) {
                         const double dx = __dsub_rn(xi, X[j]);
                         const double dy2 = __dsub_rn(yi, Y[j]);
                         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy2, dy2));
                         const double uu = fabs(__dsub_rn(ti, T[j]));
-                        const bool q = on && d2 <= s2max && uu <= tmax;
+                        const bool q = valid && (int)j > jlo && d2 <= s2max && uu <= tmax;
                         const uint32_t mq = __ballot_sync(0xffffffffu, q);
                         if (q) ws.ring[tail + __popc(mq & lt)] = make_uint2((uint32_t)lane, j);
                         tail += __popc(mq);
                         if (tail >= 32u) {
                             __syncwarp();
-                            process64(pc, ws, 32, lane, X, Y, T, my_hc, my_he, acc.stats);
+                            process64(pc, ws, 32, lane, X, Y, T, mk, onmask, my_hc, my_he,
+                                      acc.stats);
                             __syncwarp();
                             if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
                             __syncwarp();
@@ -718,7 +777,8 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                 }
             }
             __syncwarp();
-            if (tail > 0) process64(pc, ws, (int)tail, lane, X, Y, T, my_hc, my_he, acc.stats);
+            if (tail > 0)
+                process64(pc, ws, (int)tail, lane, X, Y, T, mk, onmask, my_hc, my_he, acc.stats);
             __syncwarp();
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);
@@ -746,11 +806,11 @@ exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQ
          i += gridDim.x * blockDim.x) {
         const uint4 q = xq.e[i];
         int bin;
-        bool counts;
+        uint32_t counts;
         unsigned long long exc;
         if (!exact_eval(pc, rb, q, bin, counts, exc)) continue;
         const int64_t o = (int64_t)q.z * pc.nbins + bin;
-        if (counts) atomicAdd(&acc.cnt[o], 1ull);
+        if (counts) atomicAdd(&acc.cnt[o], (unsigned long long)counts);
         if (exc & 0xffffffffull) atomicAdd(&acc.exc_lo[o], exc & 0xffffffffull);
         if (exc >> 32) atomicAdd(&acc.exc_hi[o], exc >> 32);
     }

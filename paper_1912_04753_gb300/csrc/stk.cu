@@ -210,7 +210,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     // wave size: every realization of the wave is resident at once
     const int64_t ncells = g.ncells;
     const int64_t nrows = (int64_t)g.ny * g.nt;
-    const size_t per_real = (size_t)n * (24 + 24 + 16 + 8 + 8) + (size_t)(ncells + 1) * 4 +
+    const size_t per_real = (size_t)n * (24 + 24 + 32 + 8 + 8) + (size_t)(ncells + 1) * 4 +
                             (size_t)ncells * 12 + ((size_t)nrows + (size_t)n / kUnit + 1) * 16 +
                             (size_t)nbins * 24;
     int m_w = 1;
@@ -236,7 +236,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         (rc = ensure(h->start, 4 * mc, "starts")) ||
         (rc = ensure(h->scan_tmp, 4 * tmp_words, "scan scratch")) ||
         (rc = ensure(h->X, 8 * mn, "sorted x")) || (rc = ensure(h->Y, 8 * mn, "sorted y")) ||
-        (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 16 * (mn + 8), "FP32 points")) ||
+        (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 32 * (mn + 8), "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
         (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
@@ -336,7 +336,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
                           as<uint32_t>(h->key), as<uint32_t>(h->rank), as<uint32_t>(h->start),
                           (obs_here && use_mask) ? as<uint8_t>(h->mask_in) : nullptr,
                           as<double>(h->X), as<double>(h->Y), as<double>(h->T),
-                          as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted), st),
+                          as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
+                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st),
            "scatter");
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
@@ -355,7 +356,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         CK(cudaMemsetAsync(h->acc_hi.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->counter.p, 0, 4 * (size_t)m, st), "memset");
         if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
-        for (int k = 0; k < m; ++k) selfp[k] = (obs_here && k == 0) ? masked : n;
+        // each unordered pair is evaluated once, never a point with itself
+        for (int k = 0; k < m; ++k) selfp[k] = 0;
         CK(cudaMemcpyAsync(h->self_pairs.p, selfp.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, st),
            "self pairs");
         RealBatch rb;

@@ -3,10 +3,11 @@
 // Data layout in HBM (one "realization" = the observed pattern or one CSR simulation):
 //   - points sorted by grid cell (cell key = (ct*ny + cy)*nx + cx, x fastest), so the cells of
 //     one (cy, ct) row are one contiguous run;
-//   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps, a float4
-//     (x_hi, y_hi, t_hi, cell x index) and a float2 (x_lo, y_lo) holding the point relative to
-//     its own cell origin: hi parts are multiples of a power-of-two quantum, so differences of
-//     hi parts are exact in FP32, and hi + lo carries the offset to ~2^-45 of the cell size;
+//   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps; two float4,
+//     (x_hi, y_hi, t_hi, cell x index) and (e_x, e_y, e_t, interior bound on d2), and a float2
+//     (x_lo, y_lo); the point is stored relative to its own cell origin: hi parts are multiples
+//     of a power-of-two quantum, so differences of hi parts are exact in FP32, and hi + lo
+//     carries the offset to ~2^-45 of the cell size;
 //   - cell_start[ncells + 1] per realization (offsets into that realization's n points).
 //   - work units: 32 consecutive centres of one (cy, ct) row, in realization order.
 #pragma once
@@ -72,7 +73,7 @@ struct WorkItem {
 
 // Pointers to a batch of realizations laid out back to back ([m][n] and [m][ncells + 1]).
 struct RealBatch {
-    const float4* P;
+    const float4* P;        // [2 * (realization * n + i)] and [... + 1], see above
     const float2* Plo;
     const double* X;
     const double* Y;
@@ -120,7 +121,8 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const double* t, const uint32_t* key, const uint32_t* rank,
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
-                           uint8_t* mask_out, cudaStream_t st);
+                           uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
+                           cudaStream_t st);
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
 // units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)
