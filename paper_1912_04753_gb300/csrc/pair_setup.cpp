@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "stk_internal.h"
 
@@ -117,6 +118,44 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
     g->cwl = (float)(g->cw - cwq);
     g->chl = (float)(g->ch - chq);
     g->cdl = (float)(g->cd - cdq);
+    return 0;
+}
+
+int validate_thresholds(const double box[6], const double* s, int cs, const double* tt, int ct,
+                        char* err, size_t errlen) {
+    if (!s || !tt) {
+        snprintf(err, errlen, "threshold arrays must not be NULL");
+        return 1;
+    }
+    if (cs < 1 || cs > kMaxThr || ct < 1 || ct > kMaxThr) {
+        snprintf(err, errlen, "cs and ct must be in [1, %d]", kMaxThr);
+        return 1;
+    }
+    for (int a = 0; a < cs; ++a) {
+        if (!std::isfinite(s[a]) || s[a] <= 0.0) {
+            snprintf(err, errlen, "spatial threshold %d must be finite and > 0", a);
+            return 1;
+        }
+        if (a > 0 && !(s[a] > s[a - 1])) {
+            snprintf(err, errlen, "spatial thresholds must be strictly increasing");
+            return 1;
+        }
+    }
+    for (int b = 0; b < ct; ++b) {
+        if (!std::isfinite(tt[b]) || tt[b] <= 0.0) {
+            snprintf(err, errlen, "temporal threshold %d must be finite and > 0", b);
+            return 1;
+        }
+        if (b > 0 && !(tt[b] > tt[b - 1])) {
+            snprintf(err, errlen, "temporal thresholds must be strictly increasing");
+            return 1;
+        }
+    }
+    const double W = box[1] - box[0], H = box[3] - box[2];
+    if (s[cs - 1] > 0.5 * (W < H ? W : H)) {
+        snprintf(err, errlen, "largest spatial threshold exceeds half the shorter box side");
+        return 1;
+    }
     return 0;
 }
 

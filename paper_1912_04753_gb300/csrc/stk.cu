@@ -69,6 +69,13 @@ T* as(DevBuf& b) {
 
 }  // namespace
 
+namespace stk {
+void stk_note_error(int code, const char* msg) {
+    (void)code;
+    snprintf(g_err, sizeof g_err, "%s", msg);
+}
+}  // namespace stk
+
 struct stk_handle {
     int device = 0;
     int num_sms = 0;
@@ -144,24 +151,8 @@ void free_buf(DevBuf& b) {
 }
 
 int check_thresholds(const stk_handle* h, const double* s, int cs, const double* tt, int ct) {
-    if (!s || !tt) return fail(STK_EINVAL, "threshold arrays must not be NULL");
-    if (cs < 1 || cs > STK_MAX_THRESHOLDS || ct < 1 || ct > STK_MAX_THRESHOLDS)
-        return fail(STK_EINVAL, "cs and ct must be in [1, %d]", STK_MAX_THRESHOLDS);
-    for (int a = 0; a < cs; ++a) {
-        if (!isfinite(s[a]) || s[a] <= 0.0)
-            return fail(STK_EINVAL, "spatial threshold %d must be finite and > 0", a);
-        if (a > 0 && !(s[a] > s[a - 1]))
-            return fail(STK_EINVAL, "spatial thresholds must be strictly increasing");
-    }
-    for (int b = 0; b < ct; ++b) {
-        if (!isfinite(tt[b]) || tt[b] <= 0.0)
-            return fail(STK_EINVAL, "temporal threshold %d must be finite and > 0", b);
-        if (b > 0 && !(tt[b] > tt[b - 1]))
-            return fail(STK_EINVAL, "temporal thresholds must be strictly increasing");
-    }
-    const double W = h->box[1] - h->box[0], H = h->box[3] - h->box[2];
-    if (s[cs - 1] > 0.5 * (W < H ? W : H))
-        return fail(STK_EINVAL, "largest spatial threshold exceeds half the shorter box side");
+    char err[256];
+    if (validate_thresholds(h->box, s, cs, tt, ct, err, sizeof err)) return fail(STK_EINVAL, "%s", err);
     return STK_OK;
 }
 

@@ -158,5 +158,11 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
                char* err, size_t errlen);
 void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
                        int ct, int edge, PairConsts* pc);
+// Records `msg` as the calling thread's stk_last_error() text.
+void stk_note_error(int code, const char* msg);
+
+// Threshold rules of the C ABI (finite, > 0, strictly increasing, s_cs <= min(W, H) / 2).
+int validate_thresholds(const double box[6], const double* s, int cs, const double* tt, int ct,
+                        char* err, size_t errlen);
 
 }  // namespace stk
