@@ -167,6 +167,24 @@ int stk_last_stats(const stk_handle* h, stk_stats* out);
 int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, double* x,
                    double* y, double* t);
 
+/* Observed K of one pattern without allocating memory.  Not part of the paper's method: an
+ * interface for callers that cannot call cudaMalloc where they need K (a region where
+ * cudaMalloc / cudaFree would synchronise the device and stall pipelined work, a caching
+ * allocator's reserved pool, an embedding that owns every buffer).  Inputs d_x, d_y, d_t
+ * [n] and outputs d_K, d_L, d_S (double) and d_C (int64) [cs*ct] are caller-owned DEVICE
+ * arrays; thresholds are host arrays; FP32_GUARDED precision, A*D/(n(n-1)) normalisation.
+ * Every intermediate buffer lives in one static device array of 64 MiB inside the library,
+ * held on every GPU that loads it until the process exits; patterns up to 262,144 points
+ * and grids up to 2^20 cells are accepted, larger ones fail with STK_EINVAL.  The first call
+ * on a device looks up the array's address (once per device): make it before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race; the caller
+ * serialises them.  `stream` is a cudaStream_t or NULL; the call synchronises it.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+int stk_k_noalloc(const double* d_x, const double* d_y, const double* d_t, int64_t n,
+                  const stk_box* box, const double* s, int cs, const double* tt, int ct,
+                  int edge_mode, double* d_K, double* d_L, double* d_S, int64_t* d_C,
+                  void* stream);
+
 void stk_destroy(stk_handle* h);
 const char* stk_last_error(void);
 const char* stk_version(void);

@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
     stk_destroy,
     stk_envelope,
     stk_k,
+    stk_k_noalloc,
     stk_last_error,
     stk_last_stats,
     stk_run,

@@ -80,6 +80,8 @@ def load(build_if_missing: bool = False):
         "stk_run": ([_P, ctypes.POINTER(stk_request), ctypes.POINTER(stk_result)], i32),
         "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
         "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
+        "stk_k_noalloc": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, i32, _P, i32, i32, _P,
+                           _P, _P, _P, _P], i32),
         "stk_destroy": ([_P], None),
         "stk_last_error": ([], ctypes.c_char_p),
         "stk_version": ([], ctypes.c_char_p),
@@ -216,6 +218,18 @@ def stk_sim_points(box, n, seed, sim):
     b = _box(box)
     _check(load().stk_sim_points(ctypes.byref(b), n, seed, sim, _ptr(x), _ptr(y), _ptr(t)))
     return x, y, t
+
+
+def stk_k_noalloc(x, y, t, box, s, tt, K, L, S, C, edge_mode=STK_EDGE_ISOTROPIC, stream=None):
+    """K of one pattern with no allocation inside the library.  x, y, t and the outputs K, L,
+    S (float64) and C (int64), each [cs, ct], are caller-owned contiguous CUDA tensors."""
+    s, tt = _f64(s), _f64(tt)
+    b = _box(box)
+    st = None if stream is None else _P(stream.cuda_stream)
+    _check(load().stk_k_noalloc(_P(x.data_ptr()), _P(y.data_ptr()), _P(t.data_ptr()), x.numel(),
+                                ctypes.byref(b), _ptr(s), s.shape[0], _ptr(tt), tt.shape[0],
+                                edge_mode, _P(K.data_ptr()), _P(L.data_ptr()), _P(S.data_ptr()),
+                                _P(C.data_ptr()), st))
 
 
 class Pattern:

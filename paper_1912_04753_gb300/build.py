@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libstk.so")
 
-SOURCES = ["index.cu", "pair.cu", "pair_setup.cpp", "stk.cu", "serve.cpp"]
+SOURCES = ["index.cu", "pair.cu", "pair_setup.cpp", "stk.cu", "noalloc.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
