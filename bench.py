@@ -254,7 +254,8 @@ def run_ours(args):
     e2e_ms /= e2e_steps
     e2e_value = (qual / args.steps) / (e2e_ms / 1e3)
 
-    # plain FP64 comparison (spec pairing): one job, one launch per realization
+    # plain FP64 comparison (spec pairing): one job, one launch per realization, and the
+    # per-cell error of the FP32-guarded grids against it on the same realizations
     plain = None
     if args.compare_fp64 and rank == 0:
         stk.stk_run(h, w.s, w.tt, n_sims=1, seed=seed, prec=stk.STK_PREC_FP64,
@@ -262,15 +263,26 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=stk.STK_PREC_FP64,
-                    exec_mode=stk.STK_EXEC_PLAIN)
+        ref = stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=stk.STK_PREC_FP64,
+                          exec_mode=stk.STK_EXEC_PLAIN, want_sims=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ps = stk.stk_last_stats(h)
         pms = e0.elapsed_time(e1)
+        f32 = stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
+                          exec_mode=exec_mode, want_sims=True)
+        ka = np.concatenate([f32["K"][None], f32["K_sims"]])
+        kb = np.concatenate([ref["K"][None], ref["K_sims"]])
+        rel = np.abs(ka - kb) / np.where(kb == 0, 1.0, np.abs(kb))
+        same_counts = bool(np.array_equal(f32["C"], ref["C"]) and
+                           np.array_equal(f32["C_sims"], ref["C_sims"]))
         plain = {"job_s": pms / 1e3, "value": ps["qualifying_pairs"] / (pms / 1e3),
                  "unit": UNIT, "sims_per_s": w.n_sims / (pms / 1e3),
-                 "speedup_batched_fp32": pms / (elapsed_ms / args.steps)}
+                 "speedup_batched_fp32": pms / (elapsed_ms / args.steps),
+                 "fp32_vs_fp64": {"cells": int(rel.size), "counts_identical": same_counts,
+                                  "max_rel_err_K": float(rel.max()),
+                                  "p99_rel_err_K": float(np.quantile(rel, 0.99)),
+                                  "median_rel_err_K": float(np.median(rel))}}
 
     if rank != 0:
         stk.stk_destroy(h)
