@@ -185,6 +185,92 @@ int stk_k_noalloc(const double* d_x, const double* d_y, const double* d_t, int64
                   int edge_mode, double* d_K, double* d_L, double* d_S, int64_t* d_C,
                   void* stream);
 
+/* ---- Serving loop ---------------------------------------------------------------------
+ * The paper serves K and envelope jobs to a web front end through a job-submission tier
+ * (Section 5); this is the single-GPU counterpart.  A server keeps registered point sets
+ * resident on one device and runs jobs submitted from any thread:
+ *   - `slots` worker threads, each driving its own CUDA stream, take queued jobs in arrival
+ *     order; a job whose point set is busy in another slot waits for it, later jobs on other
+ *     point sets go ahead, so the work of different requests overlaps on the GPU;
+ *   - admission by device memory: point sets plus the workspaces of running and idle jobs
+ *     stay within mem_budget_bytes; a job starts when its minimum footprint (one realization
+ *     resident at a time) fits, after idle workspaces have been released if needed, and
+ *     runs its realizations in waves sized to what it was granted;
+ *   - continuous batching: when a slot takes a job it also takes every queued job on the
+ *     same point set with the same thresholds, edge mode, precision and normalisation (up to
+ *     max_batch_sims simulations in total).  The observed pattern is computed once and all
+ *     their simulations go through the same launches, each job's under its own seed:
+ *     realization k of a job is Philox realization k under the job's seed, exactly as in
+ *     stk_envelope, and every realization is accumulated on its own, so a job's results do
+ *     not depend on the jobs it ran with.
+ * A server is thread-safe; handles created with stk_create are unaffected by it. */
+typedef struct stk_server stk_server;
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    int slots;                /* concurrent jobs (worker threads, one stream each); 0 = 4 */
+    int64_t mem_budget_bytes; /* device bytes for point sets and job workspaces;
+                                 0 = 80% of the device's free memory at creation */
+    int max_batch_sims;       /* most simulations merged into one batched job; 0 = 8192 */
+    int max_queue;            /* queued jobs beyond which stk_submit returns STK_EBUSY;
+                                 0 = 65536 */
+    int no_merge;             /* 1: run every job on its own (no continuous batching) */
+} stk_server_config;
+
+typedef struct {
+    uint64_t dataset;    /* from stk_server_register */
+    const double* s;     /* thresholds, copied at submission (same rules as stk_k) */
+    int cs;
+    const double* tt;
+    int ct;
+    int edge_mode;
+    int prec;
+    int norm;
+    int n_sims;          /* 0 = observed K only */
+    uint64_t seed;
+    int want_sims;       /* 1: keep per-realization K and counts for stk_poll */
+} stk_job;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t queued, running;      /* now */
+    int64_t max_queue_depth;
+    int64_t batches;              /* batched jobs run on the device */
+    int64_t merged_jobs;          /* jobs that shared their batch with another job */
+    int64_t simulations;          /* realizations of completed jobs, observed excluded */
+    int64_t qualifying_pairs;     /* over all completed batches and realizations */
+    double p50_ms, p99_ms, max_ms, mean_ms; /* submission -> result ready, completed jobs */
+    double wall_s;                /* first submission -> last completion */
+    double jobs_per_s, sims_per_s;
+    int64_t resident_bytes;       /* point sets + workspaces held now */
+    int64_t peak_bytes;           /* most held (accounted) at once */
+    int64_t budget_bytes;
+} stk_serve_stats;
+
+/* Errors: STK_EINVAL (bad config), STK_ENODEV, STK_ECUDA, STK_ENOMEM. */
+int stk_server_create(const stk_server_config* cfg, stk_server** out);
+/* Copies a point set to the device and keeps it there until stk_server_unregister or
+ * stk_server_destroy.  Same argument rules and errors as stk_create; STK_ENOMEM when the
+ * point set does not fit the server's budget. */
+int stk_server_register(stk_server* sv, const double* x, const double* y, const double* t,
+                        int64_t n, const stk_box* box, uint64_t* dataset);
+/* Releases a point set; STK_EBUSY while jobs on it are queued or running. */
+int stk_server_unregister(stk_server* sv, uint64_t dataset);
+/* Queues a job; its thresholds are checked and copied here.  Errors: STK_EINVAL (unknown
+ * dataset, bad thresholds or modes, n_sims < 0), STK_EBUSY (queue full). */
+int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket);
+/* Waits up to wait_ms milliseconds (< 0: without limit) for a job.  STK_OK: the result is
+ * copied into `res` (its pointers as in stk_run; K_sims / count_sims need want_sims) and the
+ * ticket is released; latency_ms (may be NULL) receives submission -> completion time.
+ * STK_ETIMEOUT: not finished yet, the ticket stays valid.  The job's own error code when it
+ * failed (ticket released, message in stk_last_error).  STK_EINVAL: unknown ticket. */
+int stk_poll(stk_server* sv, uint64_t ticket, stk_result* res, int wait_ms, double* latency_ms);
+int stk_server_stats(stk_server* sv, stk_serve_stats* out);
+/* Clears latency and throughput counters (not the queue). */
+int stk_server_reset_stats(stk_server* sv);
+/* Finishes running jobs, fails queued ones with STK_EBUSY, frees everything. */
+void stk_server_destroy(stk_server* sv);
+
 void stk_destroy(stk_handle* h);
 const char* stk_last_error(void);
 const char* stk_version(void);

@@ -53,6 +53,28 @@ class stk_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("internal_errors", ctypes.c_int64)]
 
 
+class stk_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int),
+                ("mem_budget_bytes", ctypes.c_int64), ("max_batch_sims", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("no_merge", ctypes.c_int)]
+
+
+class stk_job(ctypes.Structure):
+    _fields_ = [("dataset", ctypes.c_uint64), ("s", _P), ("cs", ctypes.c_int), ("tt", _P),
+                ("ct", ctypes.c_int), ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int),
+                ("norm", ctypes.c_int), ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("want_sims", ctypes.c_int)]
+
+
+class stk_serve_stats(ctypes.Structure):
+    _fields_ = ([(k, ctypes.c_int64) for k in (
+        "submitted", "completed", "failed", "queued", "running", "max_queue_depth", "batches",
+        "merged_jobs", "simulations", "qualifying_pairs")] +
+        [(k, ctypes.c_double) for k in (
+            "p50_ms", "p99_ms", "max_ms", "mean_ms", "wall_s", "jobs_per_s", "sims_per_s")] +
+        [(k, ctypes.c_int64) for k in ("resident_bytes", "peak_bytes", "budget_bytes")])
+
+
 _lib = None
 
 
@@ -82,6 +104,16 @@ def load(build_if_missing: bool = False):
         "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
         "stk_k_noalloc": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, i32, _P, i32, i32, _P,
                            _P, _P, _P, _P], i32),
+        "stk_server_create": ([ctypes.POINTER(stk_server_config), PP], i32),
+        "stk_server_register": ([_P, _P, _P, _P, i64, ctypes.POINTER(stk_box),
+                                 ctypes.POINTER(u64)], i32),
+        "stk_server_unregister": ([_P, u64], i32),
+        "stk_submit": ([_P, ctypes.POINTER(stk_job), ctypes.POINTER(u64)], i32),
+        "stk_poll": ([_P, u64, ctypes.POINTER(stk_result), i32, ctypes.POINTER(ctypes.c_double)],
+                     i32),
+        "stk_server_stats": ([_P, ctypes.POINTER(stk_serve_stats)], i32),
+        "stk_server_reset_stats": ([_P], i32),
+        "stk_server_destroy": ([_P], None),
         "stk_destroy": ([_P], None),
         "stk_last_error": ([], ctypes.c_char_p),
         "stk_version": ([], ctypes.c_char_p),
@@ -230,6 +262,133 @@ def stk_k_noalloc(x, y, t, box, s, tt, K, L, S, C, edge_mode=STK_EDGE_ISOTROPIC,
                                 ctypes.byref(b), _ptr(s), s.shape[0], _ptr(tt), tt.shape[0],
                                 edge_mode, _P(K.data_ptr()), _P(L.data_ptr()), _P(S.data_ptr()),
                                 _P(C.data_ptr()), st))
+
+
+def stk_server_create(device=0, slots=0, mem_budget_bytes=0, max_batch_sims=0, max_queue=0,
+                      no_merge=False):
+    """Start a serving loop on `device` (returns an opaque server)."""
+    cfg = stk_server_config(device, slots, int(mem_budget_bytes), max_batch_sims, max_queue,
+                            1 if no_merge else 0)
+    sv = _P()
+    _check(load().stk_server_create(ctypes.byref(cfg), ctypes.byref(sv)))
+    return sv
+
+
+def stk_server_register(sv, x, y, t, box) -> int:
+    """Make a point set resident on the server's device; returns its dataset id."""
+    x, y, t = _f64(x), _f64(y), _f64(t)
+    if not (x.shape == y.shape == t.shape and x.ndim == 1):
+        raise ValueError("x, y, t must be 1-D arrays of equal length")
+    b = _box(box)
+    d = ctypes.c_uint64()
+    _check(load().stk_server_register(sv, _ptr(x), _ptr(y), _ptr(t), x.shape[0],
+                                      ctypes.byref(b), ctypes.byref(d)))
+    return d.value
+
+
+def stk_server_unregister(sv, dataset: int):
+    _check(load().stk_server_unregister(sv, dataset))
+
+
+def stk_submit(sv, dataset, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
+               prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, want_sims=False) -> int:
+    """Queue a K / envelope job on a registered point set; returns its ticket."""
+    s, tt = _f64(s), _f64(tt)
+    j = stk_job(dataset, _ptr(s), s.shape[0], _ptr(tt), tt.shape[0], edge_mode, prec, norm,
+                n_sims, seed, 1 if want_sims else 0)
+    tk = ctypes.c_uint64()
+    _check(load().stk_submit(sv, ctypes.byref(j), ctypes.byref(tk)))
+    return tk.value
+
+
+def stk_poll(sv, ticket, cs, ct, n_sims=0, want_sims=False, wait_ms=-1):
+    """Wait for a job.  Returns (grids, latency_ms), or None while it is still running after
+    wait_ms; raises StkError if the job failed."""
+    nb = cs * ct
+    o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
+    if n_sims > 0:
+        for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
+            o[k] = np.zeros(nb)
+        if want_sims:
+            o["K_sims"] = np.zeros(n_sims * nb)
+            o["C_sims"] = np.zeros(n_sims * nb, np.int64)
+    r = stk_result(_ptr(o["K"]), _ptr(o["L"]), _ptr(o["S"]), _ptr(o["C"]), _ptr(o.get("K_lo")),
+                   _ptr(o.get("K_hi")), _ptr(o.get("L_lo")), _ptr(o.get("L_hi")),
+                   _ptr(o.get("K_sims")), _ptr(o.get("C_sims")))
+    lat = ctypes.c_double()
+    rc = load().stk_poll(sv, ticket, ctypes.byref(r), wait_ms, ctypes.byref(lat))
+    if rc == STK_ETIMEOUT:
+        return None
+    _check(rc)
+    out = {}
+    for k, v in o.items():
+        out[k] = v.reshape((n_sims, cs, ct)) if k in ("K_sims", "C_sims") else v.reshape(cs, ct)
+    return out, lat.value
+
+
+def stk_server_stats(sv) -> dict:
+    st = stk_serve_stats()
+    _check(load().stk_server_stats(sv, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in stk_serve_stats._fields_}
+
+
+def stk_server_reset_stats(sv):
+    _check(load().stk_server_reset_stats(sv))
+
+
+def stk_server_destroy(sv):
+    if sv:
+        load().stk_server_destroy(sv)
+
+
+class Server:
+    """Owning wrapper of a serving loop; remembers each ticket's grid shape for poll()."""
+
+    def __init__(self, **cfg):
+        self.sv = stk_server_create(**cfg)
+        self._shape = {}
+
+    def register(self, x, y, t, box) -> int:
+        return stk_server_register(self.sv, x, y, t, box)
+
+    def unregister(self, dataset):
+        stk_server_unregister(self.sv, dataset)
+
+    def submit(self, dataset, s, tt, n_sims=0, seed=0, want_sims=False, **kw) -> int:
+        tk = stk_submit(self.sv, dataset, s, tt, n_sims=n_sims, seed=seed, want_sims=want_sims,
+                        **kw)
+        self._shape[tk] = (len(s), len(tt), n_sims, want_sims)
+        return tk
+
+    def poll(self, ticket, wait_ms=-1):
+        cs, ct, n_sims, want = self._shape[ticket]
+        r = stk_poll(self.sv, ticket, cs, ct, n_sims, want, wait_ms)
+        if r is not None:
+            del self._shape[ticket]
+        return r
+
+    def stats(self):
+        return stk_server_stats(self.sv)
+
+    def reset_stats(self):
+        stk_server_reset_stats(self.sv)
+
+    def close(self):
+        if self.sv:
+            stk_server_destroy(self.sv)
+            self.sv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Pattern:

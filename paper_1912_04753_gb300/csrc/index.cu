@@ -119,7 +119,8 @@ __global__ void validate_kernel(const double* __restrict__ x, const double* __re
     if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
-__global__ void gen_csr_kernel(int64_t n, int m, uint32_t sim0, uint64_t seed, GridDev g,
+__global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ seeds,
+                               const uint32_t* __restrict__ sims, GridDev g,
                                double x1, double y1, double t1, int64_t ncells,
                                double* __restrict__ x, double* __restrict__ y,
                                double* __restrict__ t, uint32_t* __restrict__ key,
@@ -129,7 +130,8 @@ __global__ void gen_csr_kernel(int64_t n, int m, uint32_t sim0, uint64_t seed, G
          gi += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(gi / n);
         const int64_t i = gi - (int64_t)k * n;
-        const uint32_t sim = sim0 + (uint32_t)k;
+        const uint32_t sim = sims[k];
+        const uint64_t seed = seeds[k];
         const double xi = csr_coord(seed, sim, i, 0u, g.x0, x1);
         const double yi = csr_coord(seed, sim, i, 1u, g.y0, y1);
         const double ti = csr_coord(seed, sim, i, 2u, g.t0, t1);
@@ -340,11 +342,11 @@ cudaError_t launch_validate(const double* x, const double* y, const double* t, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_csr(int64_t n, int m, uint32_t sim0, uint64_t seed, const Grid& g,
-                           double* x, double* y, double* t, uint32_t* key, uint32_t* rank,
-                           uint32_t* cell_count, cudaStream_t st) {
+cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
+                           const Grid& g, double* x, double* y, double* t, uint32_t* key,
+                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st) {
     gen_csr_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
-        n, m, sim0, seed, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, x, y, t, key, rank,
+        n, m, seeds, sims, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, x, y, t, key, rank,
         cell_count);
     return cudaGetLastError();
 }

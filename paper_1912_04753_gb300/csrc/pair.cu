@@ -17,6 +17,7 @@
 //
 // This is CUDA-core work (no dense contraction), bound by instruction issue.
 #include <stddef.h>
+#include <algorithm>
 
 #include "stk_internal.h"
 
@@ -905,7 +906,17 @@ size_t pair_fp64_smem(int nbins, int* reps) {
     return smem_with_reps(sizeof(Smem64), nbins, reps, 72 * 1024);
 }
 
+// Largest dynamic shared memory a pair kernel can ask for (any threshold grid).
+size_t smem_cap(size_t base) {
+    const size_t one = ((base + 15) & ~size_t(15)) + hist_bytes(kMaxThr * kMaxThr, 1);
+    return std::max<size_t>(72 * 1024, one);
+}
+
+// The attributes are process-wide and jobs on other threads may launch at any time, so they
+// are set to one fixed cap that covers every grid, never lowered.
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
+    smem32 = std::max(smem32, smem_cap(sizeof(Smem32)));
+    smem64 = std::max(smem64, smem_cap(sizeof(Smem64)));
     cudaError_t e = cudaFuncSetAttribute(finalize_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));

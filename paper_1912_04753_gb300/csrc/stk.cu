@@ -91,12 +91,13 @@ struct stk_handle {
     DevBuf ux, uy, ut, key, rank, counts, start, scan_tmp;
     DevBuf X, Y, T, P, Plo, cell_start, chunks, chunk_off, items, counter;
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
-    DevBuf oK, oL, oS, oC, env, xq_e, xq_count;
+    DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     stk_stats last;
     size_t smem32 = 0, smem64 = 0;
     int reps32 = 1, reps64 = 1;
     int configured_nbins = -1;
+    size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
 };
 
 namespace {
@@ -165,9 +166,47 @@ int configure_kernels(stk_handle* h, int nbins) {
     return STK_OK;
 }
 
-// Runs observed (optional) + n_sims realizations and leaves per-realization K, L, S, C rows in
-// h->oK/oL/oS/oC ([R][nbins]) and, with n_sims > 0, the envelope in h->env ([4][nbins]).
-int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
+// FP64 queue entries for a wave of `points` points (about one undecided pair per point is the
+// worst seen; an overflow is still evaluated exactly, inside the pair kernel)
+unsigned int exact_queue_cap(int64_t points) {
+    int64_t c = 1 << 16;
+    while (c < points && c < (int64_t(1) << 24)) c <<= 1;
+    return (unsigned int)c;
+}
+
+// Device bytes of a job: `per_real` for every realization resident in a wave, `fixed` for the
+// job's output rows and constants.
+Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool fp32) {
+    const size_t ncells = (size_t)g.ncells, nrows = (size_t)g.ny * g.nt, un = (size_t)n;
+    Footprint f;
+    // unsorted + keys/ranks + sorted FP64 + FP32 records + low parts; counts, starts, cell
+    // starts, scan scratch; work counts/offsets and units; histograms; seeds; FP64 queue
+    f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
+                 (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
+                 8 + 12 + (fp32 ? 16 * un : 0);
+    f.fixed = 32 * 8 + 32 * (size_t)R * nbins +
+              32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
+              16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
+    return f;
+}
+
+size_t workspace_bytes(const stk_handle* h) {
+    const DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank,
+                            &h->counts, &h->start, &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P,
+                            &h->Plo, &h->cell_start, &h->chunks, &h->chunk_off, &h->items,
+                            &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
+                            &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
+                            &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid};
+    size_t b = 0;
+    for (const DevBuf* d : bufs) b += d->bytes;
+    return b;
+}
+
+// Runs the observed pattern (optional) and the simulations of `plan`; leaves per-realization
+// K, L, S, C rows in h->oK/oL/oS/oC ([R][nbins], observed first) and one envelope per group of
+// the plan in h->env ([groups][4][nbins]).
+int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
+            int* R_out) {
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
     int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
@@ -180,8 +219,14 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         return fail(STK_EINVAL, "unknown norm %d", q->norm);
     if (q->exec != STK_EXEC_BATCHED && q->exec != STK_EXEC_PLAIN)
         return fail(STK_EINVAL, "unknown exec %d", q->exec);
-    if (q->n_sims < 0 || q->n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
-    const int R = (include_obs ? 1 : 0) + q->n_sims;
+    const int n_sims = (int)plan.seed.size();
+    if (n_sims > (1 << 24) || plan.id.size() != plan.seed.size())
+        return fail(STK_EINVAL, "n_sims out of range");
+    const int n_groups = (int)plan.groups.size();
+    for (const auto& gr : plan.groups)
+        if (gr.second <= 0 || gr.first < 0 || gr.first + gr.second > n_sims)
+            return fail(STK_EINVAL, "bad envelope group");
+    const int R = (include_obs ? 1 : 0) + n_sims;
     if (R < 1) return fail(STK_EINVAL, "nothing to compute (no observed pattern, n_sims = 0)");
     *R_out = R;
     const int64_t n = h->n;
@@ -201,17 +246,18 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     // wave size: every realization of the wave is resident at once
     const int64_t ncells = g.ncells;
     const int64_t nrows = (int64_t)g.ny * g.nt;
-    const size_t per_real = (size_t)n * (24 + 24 + 32 + 8 + 8) + (size_t)(ncells + 1) * 4 +
-                            (size_t)ncells * 12 + ((size_t)nrows + (size_t)n / kUnit + 1) * 16 +
-                            (size_t)nbins * 24;
+    const Footprint fp = footprint(n, g, nbins, R, n_groups, fp32_path(q));
     int m_w = 1;
     if (q->exec == STK_EXEC_BATCHED) {
-        size_t free_b = 0, total_b = 0;
-        CK(cudaMemGetInfo(&free_b, &total_b), "memory query");
-        size_t budget = (size_t)(0.6 * (double)(free_b + h->ux.bytes + h->X.bytes + h->P.bytes));
-        const char* env = getenv("STK_MEM_BUDGET_MB");
-        if (env) budget = (size_t)atoll(env) << 20;
-        int64_t fit = (int64_t)(budget / (per_real ? per_real : 1));
+        size_t budget = h->wave_budget;
+        if (budget == 0) {
+            size_t free_b = 0, total_b = 0;
+            CK(cudaMemGetInfo(&free_b, &total_b), "memory query");
+            budget = (size_t)(0.6 * (double)(free_b + workspace_bytes(h)));
+            const char* env = getenv("STK_MEM_BUDGET_MB");
+            if (env) budget = (size_t)atoll(env) << 20;
+        }
+        int64_t fit = budget > fp.fixed ? (int64_t)((budget - fp.fixed) / fp.per_real) : 1;
         if (fit < 1) fit = 1;
         const int64_t cap_idx = ((int64_t)1 << 31) / (n > 0 ? n : 1);  // 32-bit sorted offsets
         m_w = (int)std::min<int64_t>(std::min<int64_t>(fit, cap_idx > 0 ? cap_idx : 1), R);
@@ -244,11 +290,14 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         (rc = ensure(h->oL, 8 * (size_t)R * nbins, "L grids")) ||
         (rc = ensure(h->oS, 8 * (size_t)R * nbins, "S grids")) ||
         (rc = ensure(h->oC, 8 * (size_t)R * nbins, "C grids")) ||
-        (rc = ensure(h->env, 8 * 4 * (size_t)nbins, "envelope")))
+        (rc = ensure(h->env, 8 * 4 * (size_t)nbins * (size_t)(n_groups > 0 ? n_groups : 1),
+                     "envelope")) ||
+        (rc = ensure(h->simseed, 8 * (size_t)m_w, "simulation seeds")) ||
+        (rc = ensure(h->simid, 4 * (size_t)m_w, "simulation ids")))
         return rc;
     // FP64 queue: pairs the FP32 kernel cannot decide (well under 0.1% of pairs in practice);
     // overflow is still exact, evaluated inside the pair kernel
-    const unsigned int xq_cap = 1u << 24;
+    const unsigned int xq_cap = exact_queue_cap((int64_t)m_w * n);
     if (fp32_path(q) && ((rc = ensure(h->xq_e, sizeof(uint4) * (size_t)xq_cap, "FP64 queue")) ||
                          (rc = ensure(h->xq_count, 16, "FP64 queue"))))
         return rc;
@@ -312,10 +361,17 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
         }
         if (m > first_sim_slot) {
             const int r_first = r0 + first_sim_slot;
-            const uint32_t sim0 = (uint32_t)(r_first - (include_obs ? 1 : 0));
+            const int s_first = r_first - (include_obs ? 1 : 0);
+            const int ms = m - first_sim_slot;
+            // pageable sources: staged before the calls return
+            CK(cudaMemcpyAsync(h->simseed.p, plan.seed.data() + s_first, 8 * (size_t)ms,
+                               cudaMemcpyHostToDevice, st), "seeds");
+            CK(cudaMemcpyAsync(h->simid.p, plan.id.data() + s_first, 4 * (size_t)ms,
+                               cudaMemcpyHostToDevice, st), "seeds");
             const int64_t off = (int64_t)first_sim_slot * n;
-            CK(launch_gen_csr(n, m - first_sim_slot, sim0, q->seed, g, as<double>(h->ux) + off,
-                              as<double>(h->uy) + off, as<double>(h->ut) + off,
+            CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
+                              as<double>(h->ux) + off, as<double>(h->uy) + off,
+                              as<double>(h->ut) + off,
                               as<uint32_t>(h->key) + off, as<uint32_t>(h->rank) + off,
                               as<uint32_t>(h->counts) + (int64_t)first_sim_slot * ncells, st),
                "CSR generation");
@@ -402,10 +458,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
                     2 /* pair, finalize */ + (fp32 ? 1 : 0) /* FP64 queue */;
     }
     const int first_sim_row = include_obs ? 1 : 0;
-    if (q->n_sims > 0) {
-        double* env = as<double>(h->env);
-        CK(launch_envelope(q->n_sims, nbins, ct, as<double>(h->oK) + (int64_t)first_sim_row * nbins,
-                           d_s, d_tt, env, env + nbins, env + 2 * nbins, env + 3 * nbins, st),
+    for (int gi = 0; gi < n_groups; ++gi) {
+        const int g0 = plan.groups[gi].first, gn = plan.groups[gi].second;
+        double* env = as<double>(h->env) + (size_t)gi * 4 * nbins;
+        CK(launch_envelope(gn, nbins, ct,
+                           as<double>(h->oK) + (int64_t)(first_sim_row + g0) * nbins, d_s, d_tt,
+                           env, env + nbins, env + 2 * nbins, env + 3 * nbins, st),
            "envelope");
     }
     unsigned long long stats[8];
@@ -432,6 +490,16 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, int* R_out) {
     return STK_OK;
 }
 
+SimPlan default_plan(const stk_request* q) {
+    SimPlan p;
+    const int ns = q->n_sims > 0 ? q->n_sims : 0;
+    p.seed.assign((size_t)ns, q->seed);
+    p.id.resize((size_t)ns);
+    for (int k = 0; k < ns; ++k) p.id[(size_t)k] = (uint32_t)k;
+    if (ns > 0) p.groups.push_back({0, ns});
+    return p;
+}
+
 int copy_rows(stk_handle* h, DevBuf& b, int64_t row0, int rows, int nbins, void* dst) {
     if (!dst) return STK_OK;
     CK(cudaMemcpyAsync(dst, reinterpret_cast<char*>(b.p) + 8 * row0 * nbins,
@@ -441,6 +509,59 @@ int copy_rows(stk_handle* h, DevBuf& b, int64_t row0, int rows, int nbins, void*
 }
 
 }  // namespace
+
+namespace stk {
+
+int run_plan(stk_handle* h, const stk_request* q, const SimPlan& plan, bool include_obs) {
+    int R = 0;
+    return run_job(h, q, include_obs, plan, &R);
+}
+
+int fetch_rows(stk_handle* h, int what, int row0, int rows, void* dst) {
+    DevBuf* b = what == 0   ? &h->oK
+                : what == 1 ? &h->oL
+                : what == 2 ? &h->oS
+                : what == 3 ? &h->oC
+                            : &h->env;
+    return copy_rows(h, *b, row0, rows, h->configured_nbins, dst);
+}
+
+int handle_sync(stk_handle* h) {
+    CK(cudaStreamSynchronize(h->stream), "synchronise");
+    return STK_OK;
+}
+
+int job_footprint(stk_handle* h, const stk_request* q, int R, int groups, Footprint* out) {
+    int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
+    if (rc) return rc;
+    char err[256];
+    Grid g;
+    int f_req = 0;
+    if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+    if (build_grid(h->box, q->s[q->cs - 1], q->tt[q->ct - 1], h->n, f_req, &g, err, sizeof err))
+        return fail(STK_EINVAL, "%s", err);
+    *out = footprint(h->n, g, q->cs * q->ct, R, groups, fp32_path(q));
+    return STK_OK;
+}
+
+size_t handle_workspace_bytes(const stk_handle* h) { return workspace_bytes(h); }
+
+void handle_trim(stk_handle* h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank,
+                      &h->counts, &h->start, &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P,
+                      &h->Plo, &h->cell_start, &h->chunks, &h->chunk_off, &h->items,
+                      &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
+                      &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL,
+                      &h->oS, &h->oC, &h->env, &h->simseed, &h->simid};
+    for (DevBuf* b : bufs) free_buf(*b);
+}
+
+void handle_set_wave_budget(stk_handle* h, size_t bytes) { h->wave_budget = bytes; }
+
+int64_t handle_points(const stk_handle* h) { return h->n; }
+
+}  // namespace stk
 
 extern "C" {
 
@@ -538,8 +659,9 @@ int stk_set_stream(stk_handle* h, void* stream) {
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
     if (!h || !req || !res) return fail(STK_EINVAL, "handle, request and result must not be NULL");
+    if (req->n_sims < 0 || req->n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
     int R = 0;
-    int rc = run_job(h, req, true, &R);
+    int rc = run_job(h, req, true, default_plan(req), &R);
     if (rc) return rc;
     const int nbins = req->cs * req->ct;
     if ((rc = copy_rows(h, h->oK, 0, 1, nbins, res->K)) ||
@@ -598,8 +720,9 @@ int stk_envelope(stk_handle* h, const double* s, int cs, const double* tt, int c
     q.n_sims = n_sims;
     q.seed = seed;
     q.exec = STK_EXEC_BATCHED;
+    if (n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
     int R = 0;
-    int rc = run_job(h, &q, false, &R);
+    int rc = run_job(h, &q, false, default_plan(&q), &R);
     if (rc) return rc;
     const int nbins = cs * ct;
     if ((rc = copy_rows(h, h->env, 0, 1, nbins, K_lo)) || (rc = copy_rows(h, h->env, 1, 1, nbins, K_hi)) ||
@@ -626,25 +749,34 @@ int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, d
         g.ch = box->y1 - box->y0;
         g.cd = box->t1 - box->t0;
     }
-    DevBuf bx, by, bt, bk, br, bc;
+    DevBuf bx, by, bt, bk, br, bc, bs;
     const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
     cudaStream_t st = nullptr;
     cudaError_t e = cudaSuccess;
     if ((rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
         (rc = ensure(bk, b4, "keys")) || (rc = ensure(br, b4, "ranks")) ||
-        (rc = ensure(bc, 4 * (size_t)g.ncells, "counts"))) {
+        (rc = ensure(bc, 4 * (size_t)g.ncells, "counts")) || (rc = ensure(bs, 16, "seed"))) {
         free_buf(bx), free_buf(by), free_buf(bt), free_buf(bk), free_buf(br), free_buf(bc);
+        free_buf(bs);
         return rc;
     }
+    struct {
+        uint64_t seed;
+        uint32_t sim, pad;
+    } key_sim = {seed, sim, 0};
     e = cudaMemsetAsync(bc.p, 0, 4 * (size_t)g.ncells, st);
     if (e == cudaSuccess)
-        e = launch_gen_csr(n, 1, sim, seed, g, as<double>(bx), as<double>(by), as<double>(bt),
-                           as<uint32_t>(bk), as<uint32_t>(br), as<uint32_t>(bc), st);
+        e = cudaMemcpyAsync(bs.p, &key_sim, sizeof key_sim, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_gen_csr(n, 1, as<uint64_t>(bs),
+                           reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(bs.p) + 8), g, as<double>(bx), as<double>(by), as<double>(bt), as<uint32_t>(bk),
+                           as<uint32_t>(br), as<uint32_t>(bc), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(x, bx.p, b8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, by.p, b8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(t, bt.p, b8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     free_buf(bx), free_buf(by), free_buf(bt), free_buf(bk), free_buf(br), free_buf(bc);
+    free_buf(bs);
     if (e != cudaSuccess) return cuda_fail(e, "CSR generation");
     return STK_OK;
 }
@@ -663,7 +795,7 @@ void stk_destroy(stk_handle* h) {
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
-                      &h->oC, &h->env};
+                      &h->oC, &h->env, &h->simseed, &h->simid};
     for (DevBuf* b : bufs) free_buf(*b);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_y) cudaFree(h->d_y);

@@ -111,9 +111,10 @@ cudaError_t launch_keys_observed(const double* x, const double* y, const double*
                                  uint32_t* cell_count, int* bad_flag, cudaStream_t st);
 cudaError_t launch_validate(const double* x, const double* y, const double* t, int64_t n,
                             const double box[6], int* bad_flag, cudaStream_t st);
-cudaError_t launch_gen_csr(int64_t n, int m, uint32_t sim0, uint64_t seed, const Grid& g,
-                           double* x, double* y, double* t, uint32_t* key, uint32_t* rank,
-                           uint32_t* cell_count, cudaStream_t st);
+// realization slot k (0..m-1) is Philox realization sims[k] under key seeds[k] (device arrays)
+cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
+                           const Grid& g, double* x, double* y, double* t, uint32_t* key,
+                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t count,
                                   uint32_t* tmp, int64_t tmp_words, cudaStream_t st);
 int64_t scan_tmp_words(int64_t count);
@@ -164,5 +165,43 @@ void stk_note_error(int code, const char* msg);
 // Threshold rules of the C ABI (finite, > 0, strictly increasing, s_cs <= min(W, H) / 2).
 int validate_thresholds(const double box[6], const double* s, int cs, const double* tt, int ct,
                         char* err, size_t errlen);
+
+}  // namespace stk
+
+#include <utility>
+#include <vector>
+
+#include "stk.h"
+
+namespace stk {
+
+// Device bytes of a job: `per_real` for every realization resident in one wave, `fixed`
+// for the rest (output rows, constants).
+struct Footprint {
+    size_t per_real = 0;
+    size_t fixed = 0;
+};
+
+// Simulations of a job: realization r of the job is Philox realization id[r] under key
+// seed[r]; groups are consecutive runs of realizations that form one envelope each.
+struct SimPlan {
+    std::vector<uint64_t> seed;
+    std::vector<uint32_t> id;
+    std::vector<std::pair<int, int>> groups;  // (first simulation, count)
+};
+
+// Runs the observed pattern (when include_obs) and the simulations of `plan` on h's stream.
+int run_plan(stk_handle* h, const stk_request* q, const SimPlan& plan, bool include_obs);
+// Copies rows of the last job's grids to host: what = 0 K, 1 L, 2 raw sum, 3 count (int64),
+// 4 envelope rows (K_lo, K_hi, L_lo, L_hi of each group, 4 rows per group).
+int fetch_rows(stk_handle* h, int what, int row0, int rows, void* dst);
+int handle_sync(stk_handle* h);
+// Footprint of a job of R realizations and `groups` envelopes on h (builds the job's grid).
+int job_footprint(stk_handle* h, const stk_request* q, int R, int groups, Footprint* out);
+size_t handle_workspace_bytes(const stk_handle* h);
+void handle_trim(stk_handle* h);  // frees the job workspace; the point set stays resident
+// Device bytes the next jobs on h may hold (waves are sized to fit); 0 = a share of free memory.
+void handle_set_wave_budget(stk_handle* h, size_t bytes);
+int64_t handle_points(const stk_handle* h);
 
 }  // namespace stk

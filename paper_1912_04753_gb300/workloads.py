@@ -160,39 +160,56 @@ def config_large(seed: int = 0, n: int = 10_000_000) -> Workload:
                      "cluster_frac": 0.7})
 
 
-def serving_requests(count: int, seed: int = 0, n_lo: int = 1000, n_hi: int = 1_000_000,
-                     max_sims: int = 199, rate_hz: float = 20.0):
-    """Poisson arrivals of K / envelope requests for the serving loop.
+def serving_stream(count: int, seed: int = 0, n_datasets: int = 12, presets: int = 2,
+                   n_lo: int = 1000, n_hi: int = 1_000_000, max_sims: int = 199,
+                   rate_hz: float = 50.0, neighbours: float = 300.0):
+    """Synthetic request stream for the serving loop (Poisson arrivals of K / envelope jobs).
 
-    n is log-uniform in [n_lo, n_hi]; the pattern is drawn from the CSR, Thomas or POI-mixture
-    generator; 5-50 thresholds per axis; 0..max_sims simulations.  Returns a list of dicts with
-    the arrival offset (s) and a Workload.
+    A pool of `n_datasets` point sets stays registered with the server (the analyst's layers):
+    n log-uniform in [n_lo, n_hi], drawn from the CSR, Thomas or POI-mixture generator, at a
+    fixed density of one point per 500 m^2 over 365 days.  Each dataset carries `presets`
+    threshold grids (5-50 thresholds per axis, evenly spaced) whose largest spatial threshold
+    gives about `neighbours` CSR neighbours per point at a 60-day window, capped at a quarter
+    of the side.  Each request picks a dataset, one of its grids, 0..max_sims simulations and
+    its own simulation seed; arrivals are exponential with mean 1/rate_hz.
+
+    Returns (datasets, requests): datasets is a list of Workload (n_sims 0), requests a list of
+    dicts {arrival_s, dataset, s, tt, n_sims, seed}.
     """
     rng = np.random.default_rng(seed)
-    out = []
-    clock = 0.0
-    for k in range(count):
-        clock += float(rng.exponential(1.0 / rate_hz))
+    datasets, grids = [], []
+    for d in range(n_datasets):
         n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
-        kind = int(rng.integers(0, 3))
-        cs = int(rng.integers(5, 51))
-        ct = int(rng.integers(5, 51))
-        sims = int(rng.integers(0, max_sims + 1))
-        sub = int(rng.integers(0, 2**31))
-        side = 1000.0 * np.sqrt(n / 2000.0)  # keep CSR density near the small config's
+        kind = d % 3
+        side = float(np.sqrt(500.0 * n))
         box = (0.0, side, 0.0, side, 0.0, 365.0)
+        sub = int(rng.integers(0, 2**31))
         r = np.random.default_rng(sub)
         if kind == 0:
             x, y, t = csr(n, box, sub)
         elif kind == 1:
-            x, y, t = thomas(n, box, max(1, n // 500), 0.015 * side, 10.0, r)
+            x, y, t = thomas(n, box, max(1, n // 500), 150.0, 10.0, r)
         else:
-            x, y, t = poi_mixture(n, box, max(1, n // 1000), r, sigma_s=0.015 * side,
-                                  sigma_t_s=10.0)
-        w = Workload(f"req{k}", x, y, t, box, even_thresholds(0.1 * side, cs),
-                     even_thresholds(30.0, ct), sims, sub, {"kind": kind})
-        out.append({"arrival_s": clock, "workload": w})
-    return out
+            x, y, t = poi_mixture(n, box, max(1, n // 1000), r, sigma_s=150.0, sigma_t_s=10.0)
+        s_max = min(0.25 * side, float(np.sqrt(neighbours * 500.0 * 365.0 / (60.0 * np.pi))))
+        mine = []
+        for _ in range(presets):
+            cs = int(rng.integers(5, 51))
+            ct = int(rng.integers(5, 51))
+            mine.append((even_thresholds(s_max, cs), even_thresholds(30.0, ct)))
+        grids.append(mine)
+        datasets.append(Workload(f"layer{d}", x, y, t, box, mine[0][0], mine[0][1], 0, 0,
+                                 {"kind": ("csr", "thomas", "poi_mixture")[kind]}))
+    requests = []
+    clock = 0.0
+    for _ in range(count):
+        clock += float(rng.exponential(1.0 / rate_hz))
+        d = int(rng.integers(0, n_datasets))
+        s_, tt_ = grids[d][int(rng.integers(0, presets))]
+        requests.append({"arrival_s": clock, "dataset": d, "s": s_, "tt": tt_,
+                         "n_sims": int(rng.integers(0, max_sims + 1)),
+                         "seed": int(rng.integers(0, 2**63))})
+    return datasets, requests
 
 
 CONFIGS = {

@@ -70,3 +70,20 @@ def test_python_binding_has_no_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(OSError):
         L.load()
+
+
+def test_server_argument_errors(lib):
+    import torch
+
+    import paper_1912_04753_gb300 as stk
+
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_server_create(slots=100)
+    assert e.value.code == stk.STK_EINVAL
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_server_create(mem_budget_bytes=-1)
+    assert e.value.code == stk.STK_EINVAL
+    if not torch.cuda.is_available():
+        with pytest.raises(stk.StkError) as e:
+            stk.stk_server_create()
+        assert e.value.code == 7  # STK_ENODEV
