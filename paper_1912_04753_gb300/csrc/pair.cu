@@ -239,9 +239,61 @@ struct WarpSm {
 struct Smem32 {
     PairConsts pc;      // only the part before `s2` is copied
     WarpSm w[kWarps];
-    uint32_t tile;
+    unsigned long long cursor;  // (tile << 32) | next index in the tile, see next_unit
     // histograms follow (dynamic size)
 };
+
+constexpr uint32_t kTileUnits = 2 * kWarps;  // consecutive units a block claims at once
+constexpr uint32_t kNoUnit = 0xffffffffu;
+constexpr int kSpinLimit = 1 << 20;
+
+// Next work unit of the current realization for the calling warp, or kNoUnit when none is
+// left.  The block claims tiles of kTileUnits consecutive units (neighbouring centres of one
+// row, so its warps walk the same neighbour cells and share them in L1) from the
+// realization's global counter; its warps draw units from the current tile through a shared
+// cursor, with no block barrier, so a warp with a cheap unit never waits for one with a dear
+// unit.  The warp that draws index kTileUnits claims the next tile; warps that draw past it
+// wait (bounded) for the new tile.  Lane 0 works, the result is broadcast.
+__device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32_t* counter,
+                                              uint32_t ubeg, uint32_t uend, int lane,
+                                              unsigned long long* stats) {
+    uint32_t ui = kNoUnit;
+    if (lane == 0) {
+        const uint32_t ntiles = (uend - ubeg + kTileUnits - 1) / kTileUnits;
+        int spin = 0;
+        bool stuck = false;
+        while (!stuck) {
+            const unsigned long long old = atomicAdd(cursor, 1ull);
+            const uint32_t tile = (uint32_t)(old >> 32), idx = (uint32_t)old;
+            if (tile >= ntiles) break;
+            if (idx < kTileUnits) {
+                const uint32_t u = ubeg + tile * kTileUnits + idx;
+                if (u < uend) {
+                    ui = u;
+                    break;
+                }
+                continue;  // past the end of the last tile: draw until someone claims anew
+            }
+            if (idx == kTileUnits) {
+                const uint32_t nt = atomicAdd(counter, 1u);
+                atomicExch(cursor, ((unsigned long long)nt << 32) | 1ull);  // index 0 is ours
+                if (nt >= ntiles) break;
+                ui = ubeg + nt * kTileUnits;  // < uend: nt < ntiles
+                break;
+            }
+            while ((uint32_t)(*reinterpret_cast<volatile unsigned long long*>(cursor) >> 32) ==
+                   tile) {
+                if (++spin > kSpinLimit) {
+                    atomicAdd(&stats[2], 1ull);  // never expected: the claimer is resident
+                    stuck = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, ui, 0);
+}
 
 struct WarpCtx {
     uint32_t* hc;             // this warp's histogram replica: counts
@@ -468,7 +520,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
 }
 
 template <bool EVEN, bool EDGE>
-__global__ void __launch_bounds__(kBlock, 3)
+__global__ void __launch_bounds__(kBlock, 2)
 pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
                  uint32_t* __restrict__ counters, Accum acc, ExactQueue xq, int reps) {
@@ -515,18 +567,11 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         w.Pk = Pk;
         w.real = (uint32_t)k;
         w.mk = (rb.mask != nullptr && k == 0) ? rb.mask : nullptr;
-        // the block takes tiles of kWarps consecutive units (neighbouring centres of one row),
-        // so its warps walk the same neighbour cells together and share them in L1
+        if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
+        __syncthreads();
         for (;;) {
-            if (tid == 0) sm.tile = atomicAdd(&counters[k], 1u);
-            __syncthreads();
-            const uint32_t first = ubeg + sm.tile * (uint32_t)kWarps;
-            if (first >= uend) break;  // uniform: every thread read the same tile
-            const uint32_t ui = first + (uint32_t)warp;
-            if (ui >= uend) {
-                __syncthreads();
-                continue;
-            }
+            const uint32_t ui = next_unit(&sm.cursor, &counters[k], ubeg, uend, lane, acc.stats);
+            if (ui == kNoUnit) break;
             const WorkItem wi = units[ui];
             w.c_begin = wi.c_begin;
             const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
@@ -615,7 +660,6 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                 warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
                 since_flush = 0;
             }
-            __syncthreads();  // tile done: sm.tile may be replaced
         }
         __syncthreads();
         // every warp of the block is done with realization k: add its histograms
