@@ -305,6 +305,7 @@ struct WarpCtx {
     uint32_t c_begin;
     uint32_t onmask;          // lanes whose centre is active (mask mode)
     int q2n;                  // queue 2 fill (warp-uniform)
+    bool deep;                // every point the unit meets has w = v = 1 for counted pairs
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
@@ -421,12 +422,13 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
                                             uint32_t lt, WarpCtx& w) {
+    const bool edge = EDGE && !w.deep;  // uniform
     uint4 e[2];
     e[0] = ws.ring[lane];
     e[1] = ws.ring[32 + lane];
     if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
     float4 pj[2];
-    if (EDGE) {  // neighbour's edge record: same 32-byte sector the filter just read
+    if (edge) {  // neighbour's edge record: same 32-byte sector the filter just read
         pj[0] = w.Pk[2 * (size_t)(lane < cnt ? e[0].w : 0u) + 1];
         pj[1] = w.Pk[2 * (size_t)(32 + lane < cnt ? e[1].w : 0u) + 1];
     }
@@ -456,7 +458,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         full[r] = has & am;
         atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
         di[r] = dj[r] = wi[r] = wj[r] = false;
-        if (EDGE) {
+        if (edge) {
             const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
             const float te_j = pj[r].z, rin_j = pj[r].w;
             const bool vhi = u > te_i + pc.g_v, vhj = u > te_j + pc.g_v;
@@ -478,7 +480,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
-        if (EDGE) {
+        if (edge) {
             const uint32_t mb = e[r].z | ((uint32_t)bin[r] << 13);
             push_weight(ws, pc, gpc, rb, xq, di[r], make_uint2(mb | ((uint32_t)vi[r] << 12), j),
                         lane, lt, w);
@@ -551,6 +553,7 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
     w.hh = hh + (warp % reps) * nbins;
     w.he = he + (warp % reps) * nbins;
     w.q2n = 0;
+    w.deep = false;
     const int64_t n = rb.n;
     const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
     const int64_t nrows = (int64_t)ny * nt;
@@ -591,6 +594,10 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
             const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
             const int wb = min(nx - 1, cxb + fs);
+            // units whose whole neighbourhood is deep inside the box skip the weight logic
+            w.deep = EDGE && max(0, cxa - fs) >= pc.deep_x[0] && wb <= pc.deep_x[1] &&
+                     cy - fs >= pc.deep_y[0] && cy + fs <= pc.deep_y[1] &&
+                     ct >= pc.deep_t[0] && ct + ft <= pc.deep_t[1];
             __syncwarp();
             uint32_t tail = 0;
             // rows from the centres' own row onward in key order (t major, y minor)

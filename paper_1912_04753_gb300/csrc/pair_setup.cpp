@@ -159,6 +159,20 @@ int validate_thresholds(const double box[6], const double* s, int cs, const doub
     return 0;
 }
 
+// Cells c of an axis (side `w`, nc cells from the box's lower bound) whose points lie at
+// least `req` from both ends of the axis.  A point of cell c has v - v0 >= c*w and
+// v1 - v >= (v1 - v0) - (c+1)*w up to the rounding of its cell index (a relative 2^-50 at
+// most, covered by the 1e-12 factors); the last cell also takes clamped points and is never
+// deep.  Returns lo > hi when no cell qualifies.
+void deep_range(double w, int nc, double extent, double req, int out[2]) {
+    int lo = 0;
+    while (lo < nc && (double)lo * w * (1.0 - 1e-12) < req) ++lo;
+    int hi = nc - 2;
+    while (hi >= 0 && extent - (double)(hi + 1) * w * (1.0 + 1e-12) < req) --hi;
+    out[0] = lo;
+    out[1] = hi;
+}
+
 void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
                        int ct, int edge, PairConsts* pc) {
     memset(pc, 0, sizeof(*pc));
@@ -188,6 +202,12 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
     }
     pc->s2_cut = pc->s_hi[cs - 1];
     pc->u_cut = pc->t_hi[ct - 1];
+    {
+        const double sreq = s[cs - 1] * (1.0 + 1e-9), treq = tt[ct - 1] * (1.0 + 1e-9);
+        deep_range(g.cw, g.nx, g.x1 - g.x0, sreq, pc->deep_x);
+        deep_range(g.ch, g.ny, g.y1 - g.y0, sreq, pc->deep_y);
+        deep_range(g.cd, g.nt, g.t1 - g.t0, treq, pc->deep_t);
+    }
 
     // bin tables over d2 and over u: entry k holds the first bin any value in it can fall
     // into, and a flag when some guard band meets the entry.  The index (int)(v * inv_h) is

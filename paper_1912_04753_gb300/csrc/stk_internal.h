@@ -56,6 +56,9 @@ struct PairConsts {
     int even_s, even_t;
     float inv_ds, inv_dt, tol_s, tol_t;
     float top_s, top_t;       // cs - tol_s, ct - tol_t: values at or above need FP64
+    // cell index ranges [lo, hi] of points at least s_max from every spatial edge (x, y) and
+    // t_max from both ends of the period (t): a pair of two such points has w = v = 1
+    int deep_x[2], deep_y[2], deep_t[2];
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
