@@ -224,7 +224,8 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
 
 constexpr int kRing = 128;   // per-warp queue of candidate pairs (linear, compacted on drain)
 constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
-constexpr int kQ2 = 64;      // per-warp queue of orders needing the spatial weight
+constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders needing the spatial weight:
+                                  // under 32 left over + up to 4 orders per lane of a pass
 static_assert(kDrain - 1 + 2 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
@@ -345,7 +346,7 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
                                            WarpSm* wsp, const float4* __restrict__ Pk,
                                            const float2* __restrict__ Plok, RealBatch rb,
-                                           ExactQueue xq, int cnt, int lane,
+                                           ExactQueue xq, int off, int cnt, int lane,
                                            unsigned long long* he, uint32_t* hc,
                                            uint32_t real, uint32_t c_begin) {
     const PairConsts& pc = *pcs;
@@ -353,7 +354,7 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint2 e = ws.q2[lane];
+        const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
         const int cl = (int)(meta & 31u);
         const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
@@ -397,23 +398,25 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
     push_exact(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
 }
 
-__device__ __forceinline__ void push_weight(WarpSm& ws, const PairConsts& pc,
-                                            const PairConsts* gpc, const RealBatch& rb,
-                                            const ExactQueue& xq, bool flag, uint2 entry,
-                                            int lane, uint32_t lt, WarpCtx& w) {
-    const uint32_t m = __ballot_sync(0xffffffffu, flag);
-    if (m == 0u) return;
-    if (flag) ws.q2[w.q2n + __popc(m & lt)] = entry;
-    w.q2n += __popc(m);
-    if (w.q2n >= 32) {
-        __syncwarp();
-        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 32, lane,
-                      w.he, w.hc, w.real, w.c_begin);
-        __syncwarp();
-        if (lane < w.q2n - 32) ws.q2[lane] = ws.q2[32 + lane];
-        __syncwarp();
-        w.q2n -= 32;
+// Evaluates queue 2 in batches of 32 while it holds that many, and moves the rest (fewer than
+// 32) to its front.
+__device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
+                                              const PairConsts* gpc, const RealBatch& rb,
+                                              const ExactQueue& xq, int lane, WarpCtx& w) {
+    int off = 0;
+    __syncwarp();
+    while (w.q2n - off >= 32) {
+        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, off, 32,
+                      lane, w.he, w.hc, w.real, w.c_begin);
+        off += 32;
     }
+    const int rest = w.q2n - off;
+    uint2 v = make_uint2(0u, 0u);
+    if (lane < rest) v = ws.q2[off + lane];
+    __syncwarp();
+    if (lane < rest) ws.q2[lane] = v;
+    __syncwarp();
+    w.q2n = rest;
 }
 
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
@@ -477,23 +480,47 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         rare |= full[r] | wi[r] | wj[r] | di[r] | dj[r];
     }
     if (!__any_sync(0xffffffffu, rare)) return;
+    // FP64 entries: rare enough that one vote usually skips them all
+    const bool xflag = full[0] | full[1] | wi[0] | wj[0] | wi[1] | wj[1];
+    if (__any_sync(0xffffffffu, xflag)) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
-        if (edge) {
-            const uint32_t mb = e[r].z | ((uint32_t)bin[r] << 13);
-            push_weight(ws, pc, gpc, rb, xq, di[r], make_uint2(mb | ((uint32_t)vi[r] << 12), j),
-                        lane, lt, w);
-            push_weight(ws, pc, gpc, rb, xq, dj[r],
-                        make_uint2(mb | (1u << 11) | ((uint32_t)vj[r] << 12), j), lane, lt, w);
-            push_exact(gpc, rb, xq, wi[r], make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)),
-                       lane, lt, w.hc, w.he);
-            push_exact(gpc, rb, xq, wj[r], make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)),
+        for (int r = 0; r < 2; ++r) {
+            const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
+            if (edge) {
+                push_exact(gpc, rb, xq, wi[r],
+                           make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
+                           w.hc, w.he);
+                push_exact(gpc, rb, xq, wj[r],
+                           make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
+                           w.hc, w.he);
+            }
+            push_exact(gpc, rb, xq, full[r],
+                       make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
                        lane, lt, w.hc, w.he);
         }
-        push_exact(gpc, rb, xq, full[r],
-                   make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
-                   lane, lt, w.hc, w.he);
+    }
+    if (edge) {
+        // spatial weights: up to four orders per lane join queue 2 in one compaction
+        const uint32_t b0 = __ballot_sync(0xffffffffu, di[0]);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, dj[0]);
+        const uint32_t b2 = __ballot_sync(0xffffffffu, di[1]);
+        const uint32_t b3 = __ballot_sync(0xffffffffu, dj[1]);
+        if ((b0 | b1 | b2 | b3) != 0u) {
+            const int o0 = w.q2n, o1 = o0 + __popc(b0), o2 = o1 + __popc(b1),
+                      o3 = o2 + __popc(b2);
+            const uint32_t m0 = e[0].z | ((uint32_t)bin[0] << 13);
+            const uint32_t m1 = e[1].z | ((uint32_t)bin[1] << 13);
+            if (di[0]) ws.q2[o0 + __popc(b0 & lt)] = make_uint2(m0 | ((uint32_t)vi[0] << 12), e[0].w);
+            if (dj[0])
+                ws.q2[o1 + __popc(b1 & lt)] =
+                    make_uint2(m0 | (1u << 11) | ((uint32_t)vj[0] << 12), e[0].w);
+            if (di[1]) ws.q2[o2 + __popc(b2 & lt)] = make_uint2(m1 | ((uint32_t)vi[1] << 12), e[1].w);
+            if (dj[1])
+                ws.q2[o3 + __popc(b3 & lt)] =
+                    make_uint2(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w);
+            w.q2n = o3 + __popc(b3);
+            if (w.q2n >= 32) flush_weights(ws, pc, gpc, rb, xq, lane, w);
+        }
     }
 }
 
@@ -514,8 +541,8 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     }
     __syncwarp();
     if (w.q2n > 0) {
-        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, w.q2n, lane,
-                      w.he, w.hc, w.real, w.c_begin);
+        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 0, w.q2n,
+                      lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
