@@ -222,11 +222,11 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
 // FP64 runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this
 // kernel would hold a whole warp for thousands of cycles.
 
-constexpr int kRing = 128;   // per-warp queue of candidate pairs (linear, compacted on drain)
+constexpr int kRing = 192;   // per-warp queue of candidate pairs (linear, compacted on drain)
 constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
 constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders needing the spatial weight:
                                   // under 32 left over + up to 4 orders per lane of a pass
-static_assert(kDrain - 1 + 2 * 32 <= kRing, "queue must hold a batch plus one step");
+static_assert(kDrain - 1 + 4 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
     float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2
@@ -654,34 +654,61 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         const float2 tc2 = make_float2(tc, tc);
                         if (valid) n_cand += j1 - j0;
                         since_flush += 32ull * (j1 - j0);
-                        for (uint32_t j = j0; j < j1; j += 2) {
+                        for (uint32_t j = j0; j < j1; j += 4) {
+                            // four neighbours per step (records are padded by 8)
                             const float4 q0 = Pk[2 * (size_t)j];
-                            const float4 q1 = Pk[2 * (size_t)j + 2];  // records are padded
-                            const float2 dx = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
-                            const float2 dy2 = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
-                            const float2 dtt = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
-                            const float2 d2 = __ffma2_rn(dx, dx, __fmul2_rn(dy2, dy2));
-                            const bool k0 = (d2.x <= cut2) & (fabsf(dtt.x) <= ucut) & ((int)j > jlo);
-                            const bool k1 = (d2.y <= cut2) & (fabsf(dtt.y) <= ucut) &
+                            const float4 q1 = Pk[2 * (size_t)j + 2];
+                            const float4 q2 = Pk[2 * (size_t)j + 4];
+                            const float4 q3 = Pk[2 * (size_t)j + 6];
+                            const float2 dxa = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
+                            const float2 dxb = __fadd2_rn(xc2, make_float2(-q2.x, -q3.x));
+                            const float2 dya = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
+                            const float2 dyb = __fadd2_rn(yc2, make_float2(-q2.y, -q3.y));
+                            const float2 dta = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
+                            const float2 dtb = __fadd2_rn(tc2, make_float2(-q2.z, -q3.z));
+                            const float2 d2a = __ffma2_rn(dxa, dxa, __fmul2_rn(dya, dya));
+                            const float2 d2b = __ffma2_rn(dxb, dxb, __fmul2_rn(dyb, dyb));
+                            const bool k0 = (d2a.x <= cut2) & (fabsf(dta.x) <= ucut) & ((int)j > jlo);
+                            const bool k1 = (d2a.y <= cut2) & (fabsf(dta.y) <= ucut) &
                                             ((int)j + 1 > jlo) & (j + 1 < j1);
+                            const bool k2 = (d2b.x <= cut2) & (fabsf(dtb.x) <= ucut) &
+                                            ((int)j + 2 > jlo) & (j + 2 < j1);
+                            const bool k3 = (d2b.y <= cut2) & (fabsf(dtb.y) <= ucut) &
+                                            ((int)j + 3 > jlo) & (j + 3 < j1);
                             const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
                             const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
-                            const uint32_t n0 = (uint32_t)__popc(m0);
+                            const uint32_t m2 = __ballot_sync(0xffffffffu, k2);
+                            const uint32_t m3 = __ballot_sync(0xffffffffu, k3);
+                            const uint32_t t1 = tail + (uint32_t)__popc(m0);
+                            const uint32_t t2 = t1 + (uint32_t)__popc(m1);
+                            const uint32_t t3 = t2 + (uint32_t)__popc(m2);
                             ws.ring[k0 ? tail + __popc(m0 & lt) : (uint32_t)kRing] =
-                                make_uint4(__float_as_uint(d2.x), __float_as_uint(fabsf(dtt.x)),
+                                make_uint4(__float_as_uint(d2a.x), __float_as_uint(fabsf(dta.x)),
                                            meta, j);
-                            ws.ring[k1 ? tail + n0 + __popc(m1 & lt) : (uint32_t)kRing] =
-                                make_uint4(__float_as_uint(d2.y), __float_as_uint(fabsf(dtt.y)),
+                            ws.ring[k1 ? t1 + __popc(m1 & lt) : (uint32_t)kRing] =
+                                make_uint4(__float_as_uint(d2a.y), __float_as_uint(fabsf(dta.y)),
                                            meta, j + 1);
-                            tail += n0 + (uint32_t)__popc(m1);
-                            if (tail >= (uint32_t)kDrain) {
+                            ws.ring[k2 ? t2 + __popc(m2 & lt) : (uint32_t)kRing] =
+                                make_uint4(__float_as_uint(d2b.x), __float_as_uint(fabsf(dtb.x)),
+                                           meta, j + 2);
+                            ws.ring[k3 ? t3 + __popc(m3 & lt) : (uint32_t)kRing] =
+                                make_uint4(__float_as_uint(d2b.y), __float_as_uint(fabsf(dtb.y)),
+                                           meta, j + 3);
+                            tail = t3 + (uint32_t)__popc(m3);
+                            while (tail >= (uint32_t)kDrain) {
                                 __syncwarp();
                                 drain_pairs<EVEN, EDGE>(pc, gpc, ws, rb, xq, kDrain, lane, lt, w);
                                 __syncwarp();
                                 const uint32_t rest = tail - kDrain;
-                                if ((uint32_t)lane < rest) ws.ring[lane] = ws.ring[kDrain + lane];
-                                if ((uint32_t)lane + 32 < rest)
-                                    ws.ring[32 + lane] = ws.ring[kDrain + 32 + lane];
+                                uint4 v[4];
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if ((uint32_t)(lane + 32 * c) < rest)
+                                        v[c] = ws.ring[kDrain + lane + 32 * c];
+                                __syncwarp();
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
                                 __syncwarp();
                                 tail = rest;
                             }
@@ -978,7 +1005,7 @@ size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
 }  // namespace
 
 size_t pair_fp32_smem(int nbins, int* reps) {
-    return smem_with_reps(sizeof(Smem32), nbins, reps, 72 * 1024);
+    return smem_with_reps(sizeof(Smem32), nbins, reps, 56 * 1024);
 }
 size_t pair_fp64_smem(int nbins, int* reps) {
     return smem_with_reps(sizeof(Smem64), nbins, reps, 72 * 1024);
