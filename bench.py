@@ -175,6 +175,78 @@ def run_reference(args):
     return 0
 
 
+def serve_bench(args, stk, seed=0):
+    """Serving loop on a synthetic request stream (Poisson arrivals, n log-uniform in
+    [1e3, 1e6], CSR / Thomas / POI-mixture point sets kept resident, 5-50 thresholds per axis,
+    0-199 simulations, own seed per request): p50 / p99 latency from submission to result and
+    jobs/s, FP32-guarded continuous batching vs a single FIFO queue running each job as the
+    plain FP64 path (one launch per realization)."""
+    from paper_1912_04753_gb300 import workloads as wl
+
+    datasets, reqs = wl.serving_stream(args.serve_requests, seed=seed, rate_hz=args.serve_rate)
+    out = {"requests": len(reqs), "datasets": len(datasets),
+           "n_range": [min(d.n for d in datasets), max(d.n for d in datasets)],
+           "rate_hz": args.serve_rate, "sims_total": int(sum(r["n_sims"] for r in reqs))}
+    with stk.Server(slots=args.serve_slots) as sv:
+        ids = [sv.register(d.x, d.y, d.t, d.box) for d in datasets]
+        # warm-up: one small job per point set (workspaces, kernel attributes)
+        for k, d in enumerate(datasets):
+            sv.poll(sv.submit(ids[k], d.s, d.tt, n_sims=1, seed=1))
+        sv.reset_stats()
+        tickets = [None] * len(reqs)
+
+        def submit_all():
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                dt = r["arrival_s"] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = sv.submit(ids[r["dataset"]], r["s"], r["tt"], n_sims=r["n_sims"],
+                                       seed=r["seed"], want_sims=False)
+
+        th = threading.Thread(target=submit_all)
+        th.start()
+        th.join()
+        served = [sv.poll(tk) for tk in tickets]
+        st = sv.stats()
+    out["fp32_served"] = {
+        "slots": args.serve_slots, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "max_ms": st["max_ms"], "jobs_per_s": st["jobs_per_s"], "sims_per_s": st["sims_per_s"],
+        "batches": st["batches"], "merged_jobs": st["merged_jobs"],
+        "max_queue_depth": st["max_queue_depth"], "peak_device_bytes": st["peak_bytes"]}
+    # a few results against the same job run alone (must be identical)
+    same = True
+    for i in range(min(3, len(reqs))):
+        r, d = reqs[i], datasets[reqs[i]["dataset"]]
+        with stk.Pattern(d.x, d.y, d.t, d.box) as p:
+            alone = p.run(r["s"], r["tt"], n_sims=r["n_sims"], seed=r["seed"])
+        same = same and all(np.array_equal(served[i][0][k], alone[k]) for k in alone)
+    out["served_equals_alone"] = same
+    if args.serve_fp64:
+        handles = [stk.Pattern(d.x, d.y, d.t, d.box) for d in datasets]
+        for k, d in enumerate(datasets):  # warm-up as above
+            handles[k].run(d.s, d.tt, n_sims=1, seed=1, prec=stk.STK_PREC_FP64,
+                           exec_mode=stk.STK_EXEC_PLAIN)
+        lat = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            wait = r["arrival_s"] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            handles[r["dataset"]].run(r["s"], r["tt"], n_sims=r["n_sims"], seed=r["seed"],
+                                      prec=stk.STK_PREC_FP64, exec_mode=stk.STK_EXEC_PLAIN)
+            lat.append(1e3 * (time.perf_counter() - t0 - r["arrival_s"]))
+        wall = time.perf_counter() - t0 - reqs[0]["arrival_s"]
+        for hd in handles:
+            hd.close()
+        lat = np.sort(np.array(lat))
+        q = lambda p: float(lat[max(0, int(np.ceil(p / 100 * len(lat))) - 1)])
+        out["fp64_plain_fifo"] = {"p50_ms": q(50), "p99_ms": q(99), "max_ms": float(lat[-1]),
+                                  "jobs_per_s": len(reqs) / wall,
+                                  "sims_per_s": out["sims_total"] / wall}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -284,6 +356,8 @@ def run_ours(args):
                                   "p99_rel_err_K": float(np.quantile(rel, 0.99)),
                                   "median_rel_err_K": float(np.median(rel))}}
 
+    serve = serve_bench(args, stk) if (args.serve_requests > 0 and rank == 0) else None
+
     if rank != 0:
         stk.stk_destroy(h)
         if ws > 1:
@@ -323,6 +397,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "plain_fp64": plain,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
     stk.stk_destroy(h)
@@ -344,6 +419,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--compare-fp64", type=int, default=1)
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests in the serving-loop measurement (0: skip it)")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-fp64", type=int, default=1,
+                    help="also replay the stream through a FIFO of plain FP64 jobs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
