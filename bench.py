@@ -45,6 +45,25 @@ def _workload(name, sims=None):
     return w
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Simulation seed of a rank: every rank runs its own independent job (weak scaling)."""
+    return base + 7919 * rank
+
+
+def reduce_over_ranks(elapsed_ms: float, qual: float, device):
+    """(max elapsed over ranks, sum of qualifying pairs over ranks); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return float(elapsed_ms), float(qual)
+    tmax = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(qual)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -264,7 +283,7 @@ def run_ours(args):
     w = _workload(args.config, args.sims)
     prec = stk.STK_PREC_FP32_GUARDED if args.prec == "fp32" else stk.STK_PREC_FP64
     exec_mode = stk.STK_EXEC_BATCHED if args.exec == "batched" else stk.STK_EXEC_PLAIN
-    seed = w.sim_seed + 7919 * rank  # independent job per rank (weak scaling)
+    seed = rank_seed(w.sim_seed, rank)
     stream = torch.cuda.Stream()
     h = stk.stk_create(w.x, w.y, w.t, w.box)
     stk.stk_set_stream(h, stream)
@@ -299,13 +318,7 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     elapsed_ms = ev0.elapsed_time(ev1)
-    t_rank = torch.tensor([elapsed_ms, float(qual)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        tmax = t_rank.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t_rank[1:], op=torch.distributed.ReduceOp.SUM)
-        t_rank[0] = tmax[0]
-    elapsed_ms, qual_all = float(t_rank[0]), float(t_rank[1])
+    elapsed_ms, qual_all = reduce_over_ranks(elapsed_ms, qual, torch.device("cuda", local))
     value = qual_all / (elapsed_ms / 1e3)
 
     # end to end through the C ABI from host buffers: create (H2D of the points), job, D2H of
@@ -406,7 +419,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -425,7 +438,11 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-fp64", type=int, default=1,
                     help="also replay the stream through a FIFO of plain FP64 jobs")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
