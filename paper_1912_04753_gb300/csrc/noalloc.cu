@@ -201,8 +201,9 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
     xq.count = xq_count;
     xq.cap = kExactCap;
     const int grid = pair_fp32_blocks_per_sm(smem) * sms;
-    NK(launch_pair_fp32(d_pc, pc.even_s && pc.even_t, edge_mode != 0, smem, reps, grid, 1, rb, units,
-                        uoff, counter, acc, xq, st), "pair kernel");
+    NK(launch_pair_fp32(pc, d_pc, pc.even_s && pc.even_t, edge_mode != 0, smem, reps, grid, 1, rb,
+                        units, uoff, counter, acc, xq, st),
+       "pair kernel");
     NK(launch_exact(d_pc, 4 * sms, rb, acc, xq, st), "FP64 queue");
     const double area = (box->x1 - box->x0) * (box->y1 - box->y0);
     const double nn = (double)n;

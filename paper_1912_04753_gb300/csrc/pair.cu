@@ -307,6 +307,7 @@ struct WarpCtx {
     uint32_t onmask;          // lanes whose centre is active (mask mode)
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
+    const PairConsts* pa;     // shared-memory copy (indexed tables and bands)
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
@@ -449,8 +450,9 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             a = bin_even(d2 * rsqrtf(fmaxf(d2, 1e-30f)) * pc.inv_ds, pc.tol_s, pc.top_s, pc.cs, am);
             b = bin_even(u * pc.inv_dt, pc.tol_t, pc.top_t, pc.ct, am);
         } else {
-            a = bin_fp32(d2, pc.inv_hs, pc.tab_s, pc.s_lo, pc.s_hi, pc.cs, am);
-            b = bin_fp32(u, pc.inv_ht, pc.tab_t, pc.t_lo, pc.t_hi, pc.ct, am);
+            const PairConsts& pa = *w.pa;  // tables and bands: shared memory
+            a = bin_fp32(d2, pc.inv_hs, pa.tab_s, pa.s_lo, pa.s_hi, pc.cs, am);
+            b = bin_fp32(u, pc.inv_ht, pa.tab_t, pa.t_lo, pa.t_hi, pc.ct, am);
         }
         bin[r] = a * pc.ct + b;  // always a valid bin, also for lanes without an entry
         const bool act_i = w.mk == nullptr || ((w.onmask >> cl) & 1u);
@@ -550,12 +552,13 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
 
 template <bool EVEN, bool EDGE>
 __global__ void __launch_bounds__(kBlock, 2)
-pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
+pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
+                 int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
                  uint32_t* __restrict__ counters, Accum acc, ExactQueue xq, int reps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem32& sm = *reinterpret_cast<Smem32*>(smem_raw);
-    const PairConsts& pc = sm.pc;
+    const PairConsts& pc = pk;  // scalars: kernel parameters (constant bank)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const int words = (int)(offsetof(PairConsts, s2) / 4);
@@ -581,6 +584,7 @@ pair_fp32_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
     w.he = he + (warp % reps) * nbins;
     w.q2n = 0;
     w.deep = false;
+    w.pa = &sm.pc;
     const int64_t n = rb.n;
     const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
     const int64_t nrows = (int64_t)ny * nt;
@@ -1055,21 +1059,22 @@ int pair_fp64_blocks_per_sm(size_t smem) {
     return b > 0 ? b : 1;
 }
 
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, bool even, bool edge, size_t smem, int reps,
+cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool even, bool edge,
+                             size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st) {
     if (even && edge)
-        pair_fp32_kernel<true, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+        pair_fp32_kernel<true, true><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
                                                                  counters, acc, xq, reps);
     else if (even)
-        pair_fp32_kernel<true, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+        pair_fp32_kernel<true, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
                                                                   counters, acc, xq, reps);
     else if (edge)
-        pair_fp32_kernel<false, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+        pair_fp32_kernel<false, true><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
                                                                   counters, acc, xq, reps);
     else
-        pair_fp32_kernel<false, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+        pair_fp32_kernel<false, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
                                                                    counters, acc, xq, reps);
     return cudaGetLastError();
 }

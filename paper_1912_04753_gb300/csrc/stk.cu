@@ -428,7 +428,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         xq.count = as<unsigned int>(h->xq_count);
         xq.cap = xq_cap;
         if (fp32)
-            CK(launch_pair_fp32(as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
+            CK(launch_pair_fp32(*h->h_pc, as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
                                 h->h_pc->edge != 0, smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
                                 as<uint32_t>(h->counter), acc, xq, st),

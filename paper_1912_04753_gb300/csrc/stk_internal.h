@@ -135,7 +135,9 @@ cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
 // units[unit_off[k*nrows + r] ...] for every (k, r); unit_off has m * nrows + 1 entries
 cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
                              const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
-cudaError_t launch_pair_fp32(const PairConsts* d_pc, bool even, bool edge, size_t smem, int reps,
+// hpc: host copy of *d_pc, passed by value (its scalars are read from the constant bank)
+cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool even, bool edge,
+                             size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st);
