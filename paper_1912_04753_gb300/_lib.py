@@ -50,7 +50,8 @@ class stk_stats(ctypes.Structure):
                 ("fp64_recomputed", ctypes.c_int64), ("work_items", ctypes.c_int64),
                 ("realizations", ctypes.c_int32), ("waves", ctypes.c_int32),
                 ("ms_total", ctypes.c_double), ("ms_pair", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("internal_errors", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("internal_errors", ctypes.c_int64),
+                ("grid_refinement", ctypes.c_int32), ("graph_replays", ctypes.c_int32)]
 
 
 class stk_server_config(ctypes.Structure):

@@ -80,11 +80,13 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
     g->t0 = box[4];
     g->t1 = box[5];
     const double W = box[1] - box[0], H = box[3] - box[2], D = box[5] - box[4];
-    // Refinement: cells of s_max/2 and t_max/2 shrink the examined neighbourhood from 27 to
-    // 15.6 threshold-cells per centre, but visit 125 cells instead of 27; worth it once a
-    // refined cell holds a few points.
+    // Refinement f (1..3): cells of s_max/f and t_max/f shrink the examined neighbourhood
+    // ((2f+1)^2 (f+1) cells of volume 1/f^3 threshold-cells: 18, 9.4, 7.3 for f = 1, 2, 3) but
+    // visit more, smaller cells.  Without a request (f_req outside 1..3) the planner takes
+    // f = 2 once a cell of s_max/2 holds a few points, else 1; the job runner's tuner
+    // requests the f it measured fastest.
     int f = f_req;
-    if (f != 1 && f != 2) {
+    if (f < 1 || f > 3) {
         int nx2, ny2, nt2;
         grid_counts(W, H, D, s_max, t_max, 2, &nx2, &ny2, &nt2);
         const double per_cell = (double)n / ((double)nx2 * ny2 * nt2);

@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "stk.h"
@@ -206,7 +208,63 @@ size_t workspace_bytes(const stk_handle* h) {
 // K, L, S, C rows in h->oK/oL/oS/oC ([R][nbins], observed first) and one envelope per group of
 // the plan in h->env ([groups][4][nbins]).
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
-            int* R_out) {
+            int* R_out, int f_force = 0);
+
+// Grid refinement tuner: for batched jobs large enough to amortise it, times the pair kernel
+// on one CSR realization for f = 1, 2, 3 and keeps the fastest per problem shape (n, box,
+// largest thresholds, precision, edge mode) for the life of the process.
+struct TuneKey {
+    int64_t n;
+    double box[6], s_max, t_max;
+    int prec, edge;
+    bool operator<(const TuneKey& o) const {
+        return memcmp(this, &o, sizeof(TuneKey)) < 0;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
+    TuneKey key;
+    memset(&key, 0, sizeof key);
+    key.n = h->n;
+    memcpy(key.box, h->box, sizeof key.box);
+    key.s_max = q->s[q->cs - 1];
+    key.t_max = q->tt[q->ct - 1];
+    key.prec = q->prec;
+    key.edge = q->edge_mode;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *f_out = it->second;
+            return STK_OK;
+        }
+    }
+    SimPlan trial;
+    trial.seed.push_back(0x9E3779B97F4A7C15ull);
+    trial.id.push_back(0u);
+    stk_request tq = *q;
+    tq.centre_mask = nullptr;
+    float best = 0.0f;
+    int best_f = 0;
+    for (int f = 1; f <= 3; ++f) {
+        int R = 0;
+        const int rc = run_job(h, &tq, false, trial, &R, f);
+        if (rc == STK_ENOMEM) continue;  // a finer grid that does not fit is no candidate
+        if (rc) return rc;
+        const float ms = (float)h->last.ms_pair;
+        if (best_f == 0 || ms < best) best = ms, best_f = f;
+    }
+    if (best_f == 0) best_f = 1;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best_f;
+    *f_out = best_f;
+    return STK_OK;
+}
+
+int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
+            int* R_out, int f_force) {
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
     int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
@@ -233,8 +291,19 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const int cs = q->cs, ct = q->ct, nbins = cs * ct;
     char err[256];
     Grid g;
-    int f_req = 0;  // grid refinement: chosen from the density unless STK_GRID_F is set
-    if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+    // grid refinement: forced (tuner trials), STK_GRID_F, the tuner (STK_TUNE=0 disables it)
+    // or the density planner
+    int f_req = f_force;
+    if (f_req == 0) {
+        if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+    }
+    const char* tune_env = getenv("STK_TUNE");
+    const bool tune = f_req == 0 && q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0) &&
+                      (double)n * (double)R >= 2.0e7;
+    if (tune) {
+        rc = tuned_refinement(h, q, &f_req);
+        if (rc) return rc;
+    }
     if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
     cudaStream_t st = h->stream;
@@ -485,6 +554,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.ms_pair = ms_pair;
     h->last.kernel_launches = launches;
     h->last.internal_errors = (int64_t)stats[2];
+    h->last.grid_refinement = g.fs;
+    h->last.graph_replays = 0;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     return STK_OK;

@@ -181,6 +181,45 @@ def test_degenerate_patterns(stk, orc, prec):
     np.testing.assert_allclose(got["L"], -np.repeat(s[:, None], 2, axis=1), rtol=0, atol=0)
 
 
+@pytest.mark.parametrize("f", [1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_grid_refinement(stk, orc, wl, prec, f, monkeypatch):
+    # cells of s_max/f: each refinement walks a different neighbourhood in a different cell
+    # frame and must give the same grids (clustered data near the edges and the period's end)
+    monkeypatch.setenv("STK_GRID_F", str(f))
+    rng = np.random.default_rng(31)
+    box = (0.0, 6000.0, 0.0, 5000.0, 0.0, 300.0)
+    x, y, t = wl.thomas(12000, box, 30, 150.0, 8.0, rng)
+    s = wl.even_thresholds(450.0, 9)
+    tt = wl.even_thresholds(24.0, 8)
+    want = oracle_k(orc, x, y, t, box, s, tt)
+    with stk.Pattern(x, y, t, box) as p:
+        assert_grids(p.k(s, tt, prec=prec), want, prec, f"f={f}")
+        st = p.stats()
+        assert st["grid_refinement"] == f and st["internal_errors"] == 0
+
+
+def test_tuned_refinement_gives_the_same_job(stk, wl, monkeypatch):
+    # a batched job large enough to be tuned: the tuner's choice (1..3) must not change counts,
+    # and K stays within the FP32 tolerance of the planner's grid
+    rng = np.random.default_rng(8)
+    box = (0.0, 20000.0, 0.0, 20000.0, 0.0, 365.0)
+    x, y, t = wl.thomas(300000, box, 300, 150.0, 10.0, rng)
+    s, tt = wl.even_thresholds(600.0, 10), wl.even_thresholds(30.0, 10)
+    with stk.Pattern(x, y, t, box) as p:
+        monkeypatch.setenv("STK_TUNE", "0")
+        ref = p.run(s, tt, n_sims=80, seed=5, want_sims=True)
+        f_plan = p.stats()["grid_refinement"]
+        monkeypatch.setenv("STK_TUNE", "1")
+        got = p.run(s, tt, n_sims=80, seed=5, want_sims=True)
+        st = p.stats()
+    assert st["grid_refinement"] in (1, 2, 3) and f_plan in (1, 2)
+    np.testing.assert_array_equal(got["C"], ref["C"])
+    np.testing.assert_array_equal(got["C_sims"], ref["C_sims"])
+    assert rel_err(got["K_sims"], ref["K_sims"]).max() <= 1e-6
+    assert rel_err(got["K"], ref["K"]).max() <= 1e-6
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_grid_shapes_and_modes(stk, orc, wl, prec):
     w = wl.config_csr_small(seed=4, n=1500)
