@@ -95,6 +95,14 @@ struct stk_handle {
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
+    // pinned staging of the other per-job host inputs (graph-capturable copies)
+    double* h_thr = nullptr;     // [2][STK_MAX_THRESHOLDS]
+    uint64_t* h_seed = nullptr;  // [h_sim_cap]
+    uint32_t* h_id = nullptr;
+    size_t h_sim_cap = 0;
+    // the last single-wave job, captured as a CUDA graph, and what it was captured for
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
     stk_stats last;
     size_t smem32 = 0, smem64 = 0;
     int reps32 = 1, reps64 = 1;
@@ -139,6 +147,8 @@ int init_handle(stk_handle* h, int64_t n, const stk_box* box) {
     CK(cudaEventCreate(&h->ev0), "event create");
     CK(cudaEventCreate(&h->ev1), "event create");
     CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_pc), sizeof(PairConsts)), "pinned alloc");
+    CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_thr), 16 * STK_MAX_THRESHOLDS),
+       "pinned alloc");
     const size_t bytes = sizeof(double) * (size_t)n;
     CK(cudaMalloc(reinterpret_cast<void**>(&h->d_x), bytes), "point upload");
     CK(cudaMalloc(reinterpret_cast<void**>(&h->d_y), bytes), "point upload");
@@ -383,11 +393,26 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     }
     CK(cudaMemcpyAsync(h->pc.p, h->h_pc, sizeof(PairConsts), cudaMemcpyHostToDevice, st),
        "constants upload");
-    std::vector<double> thr(2 * STK_MAX_THRESHOLDS, 0.0);
-    for (int a = 0; a < cs; ++a) thr[a] = q->s[a];
-    for (int b = 0; b < ct; ++b) thr[STK_MAX_THRESHOLDS + b] = q->tt[b];
-    CK(cudaMemcpyAsync(h->thr.p, thr.data(), 8 * thr.size(), cudaMemcpyHostToDevice, st),
+    for (int a = 0; a < 2 * STK_MAX_THRESHOLDS; ++a) h->h_thr[a] = 0.0;
+    for (int a = 0; a < cs; ++a) h->h_thr[a] = q->s[a];
+    for (int b = 0; b < ct; ++b) h->h_thr[STK_MAX_THRESHOLDS + b] = q->tt[b];
+    CK(cudaMemcpyAsync(h->thr.p, h->h_thr, 16 * STK_MAX_THRESHOLDS, cudaMemcpyHostToDevice, st),
        "threshold upload");
+    // simulation keys and indices: pinned staging (the stream was idle at the start)
+    if ((size_t)n_sims > h->h_sim_cap) {
+        if (h->h_seed) cudaFreeHost(h->h_seed);
+        if (h->h_id) cudaFreeHost(h->h_id);
+        h->h_seed = nullptr;
+        h->h_id = nullptr;
+        h->h_sim_cap = 0;
+        CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_seed), 8 * (size_t)n_sims), "pinned alloc");
+        CK(cudaMallocHost(reinterpret_cast<void**>(&h->h_id), 4 * (size_t)n_sims), "pinned alloc");
+        h->h_sim_cap = (size_t)n_sims;
+    }
+    for (int k = 0; k < n_sims; ++k) {
+        h->h_seed[k] = plan.seed[(size_t)k];
+        h->h_id[k] = plan.id[(size_t)k];
+    }
     CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
 
     const double area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
@@ -401,7 +426,6 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const int reps = fp32 ? h->reps32 : h->reps64;
     const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem);
     const int grid = bps * h->num_sms;
-    std::vector<int64_t> selfp(m_w, n);
     float ms_pair = 0.0f;
     int waves = 0;
     int64_t launches = 0;
@@ -414,8 +438,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         }
         return k + 1;
     };
-    for (int r0 = 0; r0 < R; r0 += m_w) {
-        const int m = std::min(m_w, R - r0);
+    // every stream operation of the wave holding realizations r0 .. r0+m-1
+    // (in_graph: being captured; the events then bracket the whole graph launch instead)
+    auto issue_wave = [&](int r0, int m, bool in_graph) -> int {
         const bool obs_here = include_obs && r0 == 0;
         const int first_sim_slot = obs_here ? 1 : 0;
         CK(cudaMemsetAsync(h->counts.p, 0, 4 * (size_t)m * ncells, st), "memset");
@@ -432,10 +457,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             const int r_first = r0 + first_sim_slot;
             const int s_first = r_first - (include_obs ? 1 : 0);
             const int ms = m - first_sim_slot;
-            // pageable sources: staged before the calls return
-            CK(cudaMemcpyAsync(h->simseed.p, plan.seed.data() + s_first, 8 * (size_t)ms,
+            CK(cudaMemcpyAsync(h->simseed.p, h->h_seed + s_first, 8 * (size_t)ms,
                                cudaMemcpyHostToDevice, st), "seeds");
-            CK(cudaMemcpyAsync(h->simid.p, plan.id.data() + s_first, 4 * (size_t)ms,
+            CK(cudaMemcpyAsync(h->simid.p, h->h_id + s_first, 4 * (size_t)ms,
                                cudaMemcpyHostToDevice, st), "seeds");
             const int64_t off = (int64_t)first_sim_slot * n;
             CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
@@ -473,9 +497,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         CK(cudaMemsetAsync(h->counter.p, 0, 4 * (size_t)m, st), "memset");
         if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
         // each unordered pair is evaluated once, never a point with itself
-        for (int k = 0; k < m; ++k) selfp[k] = 0;
-        CK(cudaMemcpyAsync(h->self_pairs.p, selfp.data(), 8 * (size_t)m, cudaMemcpyHostToDevice, st),
-           "self pairs");
+        CK(cudaMemsetAsync(h->self_pairs.p, 0, 8 * (size_t)m, st), "memset");
         RealBatch rb;
         rb.P = as<float4>(h->P);
         rb.Plo = as<float2>(h->Plo);
@@ -491,7 +513,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         acc.exc_lo = as<unsigned long long>(h->acc_lo);
         acc.exc_hi = as<unsigned long long>(h->acc_hi);
         acc.stats = as<unsigned long long>(h->stats);
-        CK(cudaEventRecord(h->ev0, st), "event");
+        if (!in_graph) CK(cudaEventRecord(h->ev0, st), "event");
         ExactQueue xq;
         xq.e = as<uint4>(h->xq_e);
         xq.count = as<unsigned int>(h->xq_count);
@@ -507,7 +529,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
                                 as<uint32_t>(h->counter), acc, st),
                "pair kernel (FP64)");
-        CK(cudaEventRecord(h->ev1, st), "event");
+        if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
         if (fp32) {
             CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st), "FP64 queue");
         }
@@ -516,6 +538,73 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                            as<double>(h->oK) + row, as<double>(h->oL) + row,
                            as<double>(h->oS) + row, as<int64_t>(h->oC) + row, st),
            "finalize");
+        return STK_OK;
+    };
+    // A small single-wave job without a centre mask (launch overhead matters there) is captured
+    // as a CUDA graph and replayed while the next jobs have the same shape, constants and
+    // buffers (STK_GRAPHS=0 disables it, 1 forces it for any single-wave job).  The pair-kernel
+    // time of a graph job is that of the whole graph.
+    const char* graphs_env = getenv("STK_GRAPHS");
+    const int graphs = graphs_env ? atoi(graphs_env) : -1;
+    const bool use_graph = R <= m_w && !use_mask && graphs != 0 &&
+                           (graphs == 1 || (double)n * (double)R <= 1.6e7);
+    std::vector<unsigned char> key;
+    if (use_graph) {
+        auto put = [&key](const void* p, size_t b) {
+            const unsigned char* c = reinterpret_cast<const unsigned char*>(p);
+            key.insert(key.end(), c, c + b);
+        };
+        const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
+                              (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows};
+        put(sc, sizeof sc);
+        put(&coef, sizeof coef);
+        put(h->h_pc, sizeof(PairConsts));
+        const void* ptrs[] = {h->ux.p, h->uy.p, h->ut.p, h->key.p, h->rank.p, h->counts.p,
+                              h->start.p, h->scan_tmp.p, h->X.p, h->Y.p, h->T.p, h->P.p,
+                              h->Plo.p, h->cell_start.p, h->chunks.p, h->chunk_off.p,
+                              h->items.p, h->counter.p, h->acc_cnt.p, h->acc_lo.p, h->acc_hi.p,
+                              h->stats.p, h->pc.p, h->thr.p, h->self_pairs.p, h->oK.p, h->oL.p,
+                              h->oS.p, h->oC.p, h->xq_e.p, h->xq_count.p, h->simseed.p,
+                              h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
+                              (void*)h->ev0, (void*)h->ev1, (void*)st};
+        put(ptrs, sizeof ptrs);
+    }
+    int replays = 0;
+    for (int r0 = 0; r0 < R; r0 += m_w) {
+        const int m = std::min(m_w, R - r0);
+        const bool obs_here = include_obs && r0 == 0;
+        const int first_sim_slot = obs_here ? 1 : 0;
+        if (use_graph && h->gexec && key == h->gkey) {
+            CK(cudaEventRecord(h->ev0, st), "event");
+            CK(cudaGraphLaunch(h->gexec, st), "graph launch");
+            CK(cudaEventRecord(h->ev1, st), "event");
+            ++replays;
+        } else if (use_graph) {
+            if (h->gexec) cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+            h->gkey.clear();
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture");
+            const int irc = issue_wave(r0, m, true);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+            if (irc) {
+                if (graph) cudaGraphDestroy(graph);
+                return irc;
+            }
+            CK(ec, "graph capture");
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ei, "graph instantiate");
+            h->gexec = ex;
+            h->gkey = key;
+            CK(cudaEventRecord(h->ev0, st), "event");
+            CK(cudaGraphLaunch(h->gexec, st), "graph launch");
+            CK(cudaEventRecord(h->ev1, st), "event");
+        } else {
+            rc = issue_wave(r0, m, false);
+            if (rc) return rc;
+        }
         CK(cudaEventSynchronize(h->ev1), "pair kernel");
         float ms = 0.0f;
         CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event timing");
@@ -555,7 +644,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.kernel_launches = launches;
     h->last.internal_errors = (int64_t)stats[2];
     h->last.grid_refinement = g.fs;
-    h->last.graph_replays = 0;
+    h->last.graph_replays = replays;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     return STK_OK;
@@ -872,6 +961,10 @@ void stk_destroy(stk_handle* h) {
     if (h->d_y) cudaFree(h->d_y);
     if (h->d_t) cudaFree(h->d_t);
     if (h->h_pc) cudaFreeHost(h->h_pc);
+    if (h->h_thr) cudaFreeHost(h->h_thr);
+    if (h->h_seed) cudaFreeHost(h->h_seed);
+    if (h->h_id) cudaFreeHost(h->h_id);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);

@@ -1,0 +1,52 @@
+"""CUDA-graph replay of single-wave jobs: a job whose shape, constants and buffers match the
+last captured one is replayed from the graph (new simulation seeds reach it through the pinned
+staging copies) and gives exactly the grids of the same job issued launch by launch."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stk():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1912_04753_gb300 import build as b
+
+    b.build()
+    import paper_1912_04753_gb300 as m
+
+    m.load()
+    return m
+
+
+def test_graph_replay_equals_direct_issue(stk, monkeypatch):
+    from paper_1912_04753_gb300 import workloads as wl
+
+    rng = np.random.default_rng(2)
+    box = (0.0, 3000.0, 0.0, 3000.0, 0.0, 365.0)
+    x, y, t = wl.thomas(6000, box, 20, 100.0, 6.0, rng)
+    s, tt = wl.even_thresholds(200.0, 8), wl.even_thresholds(20.0, 6)
+    for prec in (stk.STK_PREC_FP32_GUARDED, stk.STK_PREC_FP64):
+        with stk.Pattern(x, y, t, box) as p:
+            monkeypatch.setenv("STK_GRAPHS", "1")
+            first = p.run(s, tt, n_sims=7, seed=11, prec=prec, want_sims=True)
+            assert p.stats()["graph_replays"] == 0  # captured, launched once
+            runs = {}
+            for seed in (11, 12, 13):
+                runs[seed] = p.run(s, tt, n_sims=7, seed=seed, prec=prec, want_sims=True)
+                assert p.stats()["graph_replays"] == 1
+            monkeypatch.setenv("STK_GRAPHS", "0")
+            for seed in (11, 12, 13):
+                direct = p.run(s, tt, n_sims=7, seed=seed, prec=prec, want_sims=True)
+                assert p.stats()["graph_replays"] == 0
+                for k in direct:
+                    np.testing.assert_array_equal(runs[seed][k], direct[k], err_msg=k)
+            for k in first:
+                np.testing.assert_array_equal(first[k], runs[11][k], err_msg=k)
+            # a different shape is captured anew, never replayed from the old graph
+            monkeypatch.setenv("STK_GRAPHS", "1")
+            p.run(s, tt, n_sims=5, seed=1, prec=prec)
+            assert p.stats()["graph_replays"] == 0
