@@ -156,8 +156,9 @@ typedef struct {
     double ms_pair;            /* device time of the pair kernel launches */
     int64_t kernel_launches;   /* CUDA kernels this library launched for the job */
     int64_t internal_errors;   /* consistency checks that failed inside the kernels (0 expected) */
-    int32_t grid_refinement;   /* f: grid cells of s_max/f x s_max/f x t_max/f (1..3) */
+    int32_t grid_refinement;   /* fs: grid cells of s_max/fs x s_max/fs (1..3) */
     int32_t graph_replays;     /* waves replayed from a captured CUDA graph */
+    int32_t grid_refinement_t; /* ft: grid cells of t_max/ft in time (1..3) */
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);

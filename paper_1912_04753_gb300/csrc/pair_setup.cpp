@@ -53,11 +53,11 @@ static int cells_along(double extent, double thr) {
     return (int)std::min<long long>(n, 1 << 20);
 }
 
-static void grid_counts(double W, double H, double D, double s_max, double t_max, int f,
+static void grid_counts(double W, double H, double D, double s_max, double t_max, int fs, int ft,
                         int* nx, int* ny, int* nt) {
-    *nx = cells_along(W, s_max / f);
-    *ny = cells_along(H, s_max / f);
-    *nt = cells_along(D, t_max / f);
+    *nx = cells_along(W, s_max / fs);
+    *ny = cells_along(H, s_max / fs);
+    *nt = cells_along(D, t_max / ft);
     // keep the cell table modest: coarsen the largest axis until the grid fits
     const long long kMaxCells = 1ll << 26;
     while ((long long)*nx * *ny * *nt > kMaxCells) {
@@ -80,22 +80,29 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
     g->t0 = box[4];
     g->t1 = box[5];
     const double W = box[1] - box[0], H = box[3] - box[2], D = box[5] - box[4];
-    // Refinement f (1..3): cells of s_max/f and t_max/f shrink the examined neighbourhood
-    // ((2f+1)^2 (f+1) cells of volume 1/f^3 threshold-cells: 18, 9.4, 7.3 for f = 1, 2, 3) but
-    // visit more, smaller cells.  Without a request (f_req outside 1..3) the planner takes
-    // f = 2 once a cell of s_max/2 holds a few points, else 1; the job runner's tuner
-    // requests the f it measured fastest.
-    int f = f_req;
-    if (f < 1 || f > 3) {
+    // Refinement fs (space) and ft (time), each 1..3: cells of s_max/fs and t_max/ft shrink
+    // the examined neighbourhood ((2fs+1)^2 (ft+1) cells of volume 1/(fs^2 ft) threshold-cells:
+    // 18, 9.4, 7.3 for fs = ft = 1, 2, 3) but visit more, smaller cells.  f_req = fs | ft << 8
+    // (ft = 0: ft = fs).  Without a request (fs outside 1..3) the planner takes fs = ft = 2
+    // once a cell of s_max/2 holds a few points, else 1; the job runner's tuner requests the
+    // pair it measured fastest.  Up to 3 keeps hi-part differences exact (centre coordinates in
+    // a neighbour's cell frame stay below 4 cells < 2^24 quanta).
+    int fs = f_req & 0xff, ft = (f_req >> 8) & 0xff;
+    if (fs < 1 || fs > 3) {
         int nx2, ny2, nt2;
-        grid_counts(W, H, D, s_max, t_max, 2, &nx2, &ny2, &nt2);
+        grid_counts(W, H, D, s_max, t_max, 2, 2, &nx2, &ny2, &nt2);
         const double per_cell = (double)n / ((double)nx2 * ny2 * nt2);
-        f = per_cell >= 8.0 ? 2 : 1;
+        fs = ft = per_cell >= 8.0 ? 2 : 1;
+    }
+    if (ft == 0) ft = fs;
+    if (ft < 1 || ft > 3) {
+        snprintf(err, errlen, "temporal grid refinement must be 1..3");
+        return 1;
     }
     int nx, ny, nt;
-    grid_counts(W, H, D, s_max, t_max, f, &nx, &ny, &nt);
-    g->fs = f;
-    g->ft = f;
+    grid_counts(W, H, D, s_max, t_max, fs, ft, &nx, &ny, &nt);
+    g->fs = fs;
+    g->ft = ft;
     g->nx = nx;
     g->ny = ny;
     g->nt = nt;
@@ -103,7 +110,7 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
     g->cw = W / nx;
     g->ch = H / ny;
     g->cd = D / nt;
-    if (!(g->cw * f >= s_max && g->ch * f >= s_max && g->cd * f >= t_max)) {
+    if (!(g->cw * fs >= s_max && g->ch * fs >= s_max && g->cd * ft >= t_max)) {
         snprintf(err, errlen, "grid cells smaller than the thresholds");
         return 1;
     }

@@ -221,8 +221,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             int* R_out, int f_force = 0);
 
 // Grid refinement tuner: for batched jobs large enough to amortise it, times the pair kernel
-// on one CSR realization for f = 1, 2, 3 and keeps the fastest per problem shape (n, box,
-// largest thresholds, precision, edge mode) for the life of the process.
+// on a few CSR realizations for (fs, ft) = (f, f), f = 1..3, then the best fs with ft one step
+// finer and coarser, and keeps the fastest per problem shape (n, box, largest thresholds,
+// precision, edge mode) for the life of the process.
 struct TuneKey {
     int64_t n;
     double box[6], s_max, t_max;
@@ -251,22 +252,39 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
             return STK_OK;
         }
     }
+    // a few realizations (about 4e6 point-realizations, at most 4) so that the timing is stable
     SimPlan trial;
-    trial.seed.push_back(0x9E3779B97F4A7C15ull);
-    trial.id.push_back(0u);
+    const int k_trial = (int)std::min<int64_t>(4, std::max<int64_t>(1, 4000000 / h->n));
+    for (int k = 0; k < k_trial; ++k) {
+        trial.seed.push_back(0x9E3779B97F4A7C15ull);
+        trial.id.push_back((uint32_t)k);
+    }
     stk_request tq = *q;
     tq.centre_mask = nullptr;
     float best = 0.0f;
     int best_f = 0;
-    for (int f = 1; f <= 3; ++f) {
+    auto trial_run = [&](int fs, int ft) -> int {
         int R = 0;
+        const int f = fs | (ft << 8);
         const int rc = run_job(h, &tq, false, trial, &R, f);
-        if (rc == STK_ENOMEM) continue;  // a finer grid that does not fit is no candidate
+        if (rc == STK_ENOMEM) return STK_OK;  // a finer grid that does not fit is no candidate
         if (rc) return rc;
         const float ms = (float)h->last.ms_pair;
         if (best_f == 0 || ms < best) best = ms, best_f = f;
+        return STK_OK;
+    };
+    // the same refinement on both axes first, then the time axis one step either side
+    for (int f = 1; f <= 3; ++f) {
+        const int rc = trial_run(f, f);
+        if (rc) return rc;
     }
-    if (best_f == 0) best_f = 1;
+    if (best_f == 0) best_f = 1 | (1 << 8);
+    const int fs0 = best_f & 0xff;
+    for (int ft = fs0 - 1; ft <= fs0 + 1; ft += 2) {
+        if (ft < 1 || ft > 3) continue;
+        const int rc = trial_run(fs0, ft);
+        if (rc) return rc;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tuned[key] = best_f;
     *f_out = best_f;
@@ -301,11 +319,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const int cs = q->cs, ct = q->ct, nbins = cs * ct;
     char err[256];
     Grid g;
-    // grid refinement: forced (tuner trials), STK_GRID_F, the tuner (STK_TUNE=0 disables it)
-    // or the density planner
+    // grid refinement: forced (tuner trials), STK_GRID_F (and STK_GRID_FT for the time axis),
+    // the tuner (STK_TUNE=0 disables it) or the density planner
     int f_req = f_force;
     if (f_req == 0) {
         if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+        if (const char* ft = getenv("STK_GRID_FT")) f_req |= atoi(ft) << 8;
     }
     const char* tune_env = getenv("STK_TUNE");
     const bool tune = f_req == 0 && q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0) &&
@@ -644,6 +663,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.kernel_launches = launches;
     h->last.internal_errors = (int64_t)stats[2];
     h->last.grid_refinement = g.fs;
+    h->last.grid_refinement_t = g.ft;
     h->last.graph_replays = replays;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
@@ -696,8 +716,10 @@ int job_footprint(stk_handle* h, const stk_request* q, int R, int groups, Footpr
     if (rc) return rc;
     char err[256];
     Grid g;
-    int f_req = 0;
+    // the finest refinement the tuner may pick bounds the cell-dependent part
+    int f_req = 3 | (3 << 8);
     if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
+    if (const char* ft = getenv("STK_GRID_FT")) f_req = (f_req & 0xff) | (atoi(ft) << 8);
     if (build_grid(h->box, q->s[q->cs - 1], q->tt[q->ct - 1], h->n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
     *out = footprint(h->n, g, q->cs * q->ct, R, groups, fp32_path(q));

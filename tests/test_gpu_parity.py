@@ -181,22 +181,35 @@ def test_degenerate_patterns(stk, orc, prec):
     np.testing.assert_allclose(got["L"], -np.repeat(s[:, None], 2, axis=1), rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("f", [1, 2, 3])
+_REFINE_CASE = {}
+
+
+def _refine_case(orc, wl):
+    # clustered data near the edges and the period's end, computed once for all refinements
+    if not _REFINE_CASE:
+        rng = np.random.default_rng(31)
+        box = (0.0, 6000.0, 0.0, 5000.0, 0.0, 300.0)
+        x, y, t = wl.thomas(12000, box, 30, 150.0, 8.0, rng)
+        s = wl.even_thresholds(450.0, 9)
+        tt = wl.even_thresholds(24.0, 8)
+        _REFINE_CASE.update(x=x, y=y, t=t, box=box, s=s, tt=tt,
+                            want=oracle_k(orc, x, y, t, box, s, tt))
+    return _REFINE_CASE
+
+
+@pytest.mark.parametrize("fs,ft", [(1, 1), (2, 2), (3, 3), (2, 3), (3, 1), (1, 2)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_every_grid_refinement(stk, orc, wl, prec, f, monkeypatch):
-    # cells of s_max/f: each refinement walks a different neighbourhood in a different cell
-    # frame and must give the same grids (clustered data near the edges and the period's end)
-    monkeypatch.setenv("STK_GRID_F", str(f))
-    rng = np.random.default_rng(31)
-    box = (0.0, 6000.0, 0.0, 5000.0, 0.0, 300.0)
-    x, y, t = wl.thomas(12000, box, 30, 150.0, 8.0, rng)
-    s = wl.even_thresholds(450.0, 9)
-    tt = wl.even_thresholds(24.0, 8)
-    want = oracle_k(orc, x, y, t, box, s, tt)
-    with stk.Pattern(x, y, t, box) as p:
-        assert_grids(p.k(s, tt, prec=prec), want, prec, f"f={f}")
+def test_every_grid_refinement(stk, orc, wl, prec, fs, ft, monkeypatch):
+    # cells of s_max/fs x t_max/ft: each refinement walks a different neighbourhood in a
+    # different cell frame and must give the same grids
+    monkeypatch.setenv("STK_GRID_F", str(fs))
+    monkeypatch.setenv("STK_GRID_FT", str(ft))
+    c = _refine_case(orc, wl)
+    with stk.Pattern(c["x"], c["y"], c["t"], c["box"]) as p:
+        assert_grids(p.k(c["s"], c["tt"], prec=prec), c["want"], prec, f"f={fs},{ft}")
         st = p.stats()
-        assert st["grid_refinement"] == f and st["internal_errors"] == 0
+        assert (st["grid_refinement"], st["grid_refinement_t"]) == (fs, ft)
+        assert st["internal_errors"] == 0
 
 
 def test_tuned_refinement_gives_the_same_job(stk, wl, monkeypatch):
@@ -213,7 +226,8 @@ def test_tuned_refinement_gives_the_same_job(stk, wl, monkeypatch):
         monkeypatch.setenv("STK_TUNE", "1")
         got = p.run(s, tt, n_sims=80, seed=5, want_sims=True)
         st = p.stats()
-    assert st["grid_refinement"] in (1, 2, 3) and f_plan in (1, 2)
+    assert st["grid_refinement"] in (1, 2, 3) and st["grid_refinement_t"] in (1, 2, 3)
+    assert f_plan in (1, 2)
     np.testing.assert_array_equal(got["C"], ref["C"])
     np.testing.assert_array_equal(got["C_sims"], ref["C_sims"])
     assert rel_err(got["K_sims"], ref["K_sims"]).max() <= 1e-6
