@@ -34,6 +34,9 @@ UNIT = "qualifying ordered pairs/s"
 # binning + histogram update), used for the ALU roofline
 OPS_PER_CANDIDATE = 8
 OPS_PER_QUALIFYING = 12
+# DRAM bytes (read + write) of the pair kernel per realization of the 2M-point mixture, from
+# the ncu capture in profiles/pair_fp32_poi_n2M.md (2 realizations per launch there)
+PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 99.8e6}
 
 
 def _workload(name, sims=None):
@@ -381,6 +384,11 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak_ops = n_sm * 128 * mhz * 1e6  # FP32 lanes x clock = thread-instruction issue rate
     achieved = (OPS_PER_CANDIDATE * cand + OPS_PER_QUALIFYING * qual) / (pair_ms / 1e3)
+    per_real = PAIR_DRAM_BYTES_PER_REALIZATION.get(w.name)
+    waves = max(1, st.get("waves", 1))
+    # bytes per pair launch (a job of R realizations runs in `waves` launches)
+    fp32_job = prec == stk.STK_PREC_FP32_GUARDED
+    traffic = per_real * st["realizations"] / waves if (per_real and fp32_job) else None
     cb = cpu_baseline(w, target_s=args.cpu_seconds) if args.cpu_seconds > 0 else None
     if cb:
         cb.pop("seconds", None)
@@ -402,7 +410,7 @@ def run_ours(args):
         "fp64_recomputed_per_step": st["fp64_recomputed"],
         "pair_kernel_ms_per_step": pair_ms / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
