@@ -1,7 +1,7 @@
 """Oracle for the edge-corrected space-time Ripley's K estimator (test infrastructure).
 
 A plain, single-threaded FP64 CPU restatement of the paper's Section 3 (Eq. 2-4 and the
-Monte Carlo CSR envelope), compiled from ``stk_oracle.c`` with gcc and loaded through
+simulation envelopes: Monte Carlo CSR, bootstrapping, random permutation), compiled from ``stk_oracle.c`` with gcc and loaded through
 ctypes.  Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
 reference legs may import it; the CUDA library never calls it and shares no code with it.
 """
@@ -62,6 +62,18 @@ def _load():
         lib.oracle_envelope.argtypes = [i64, P, P, i32, P, i32, i32, i32, i32, u64, P, P, P,
                                         P, P]
         lib.oracle_envelope.restype = ctypes.c_int
+        lib.oracle_bootstrap_index.argtypes = [i64, u64, u32, i64]
+        lib.oracle_bootstrap_index.restype = i64
+        lib.oracle_bootstrap_points.argtypes = [P, P, P, i64, u64, u32, P, P, P]
+        lib.oracle_bootstrap_points.restype = None
+        lib.oracle_feistel_bits.argtypes = [i64]
+        lib.oracle_feistel_bits.restype = ctypes.c_int
+        lib.oracle_feistel.argtypes = [u64, ctypes.c_int, u64, u32]
+        lib.oracle_feistel.restype = u64
+        lib.oracle_permutation_index.argtypes = [i64, u64, u32, i64]
+        lib.oracle_permutation_index.restype = i64
+        lib.oracle_permutation_points.argtypes = [P, P, P, i64, u64, u32, P, P, P]
+        lib.oracle_permutation_points.restype = None
         _lib = lib
     return _lib
 
@@ -172,3 +184,71 @@ def envelope(n, box, s, tt, n_sims, seed, edge_mode=1, norm=0, keep_all=False):
     if keep_all:
         out["K_all"] = K_all.reshape(n_sims, cs, ct)
     return out
+
+
+SIM_CSR, SIM_PERMUTATION, SIM_BOOTSTRAP = 0, 1, 2
+
+
+def bootstrap_index(n: int, seed: int, sim: int, i: int) -> int:
+    return int(_load().oracle_bootstrap_index(n, seed, sim, i))
+
+
+def bootstrap_points(x, y, t, seed: int, sim: int):
+    """Realization `sim` of the bootstrapping simulation (Section 3): n draws with
+    replacement from the observed points."""
+    x, y, t = _f64(x), _f64(y), _f64(t)
+    n = len(x)
+    ox, oy, ot = (np.empty(n, np.float64) for _ in range(3))
+    _load().oracle_bootstrap_points(_ptr(x), _ptr(y), _ptr(t), n, seed, sim, _ptr(ox),
+                                    _ptr(oy), _ptr(ot))
+    return ox, oy, ot
+
+
+def feistel_bits(n: int) -> int:
+    return int(_load().oracle_feistel_bits(n))
+
+
+def feistel(v: int, b: int, seed: int, sim: int) -> int:
+    return int(_load().oracle_feistel(v, b, seed, sim))
+
+
+def permutation_index(n: int, seed: int, sim: int, i: int) -> int:
+    return int(_load().oracle_permutation_index(n, seed, sim, i))
+
+
+def permutation_points(x, y, t, seed: int, sim: int):
+    """Realization `sim` of the random-permutation simulation (Section 3): the observed
+    points with their timestamps exchanged by a pseudo-random bijection."""
+    x, y, t = _f64(x), _f64(y), _f64(t)
+    n = len(x)
+    ox, oy, ot = (np.empty(n, np.float64) for _ in range(3))
+    _load().oracle_permutation_points(_ptr(x), _ptr(y), _ptr(t), n, seed, sim, _ptr(ox),
+                                      _ptr(oy), _ptr(ot))
+    return ox, oy, ot
+
+
+def simulation_points(method: int, x, y, t, box, seed: int, sim: int):
+    """Realization `sim` of the given simulation method (Section 3)."""
+    if method == SIM_CSR:
+        return csr_points(len(x), box, seed, sim)
+    if method == SIM_PERMUTATION:
+        return permutation_points(x, y, t, seed, sim)
+    if method == SIM_BOOTSTRAP:
+        return bootstrap_points(x, y, t, seed, sim)
+    raise ValueError(f"unknown simulation method {method}")
+
+
+def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, norm=0):
+    """Envelope (Section 3) over n_sims realizations of any simulation method: the
+    element-wise min / max of K (and L of those), plus every realization's K."""
+    Ks = []
+    for k in range(n_sims):
+        px, py, pt = simulation_points(method, x, y, t, box, seed, k)
+        Ks.append(k_function(px, py, pt, box, s, tt, edge_mode=edge_mode, norm=norm)["K"])
+    Ks = np.stack(Ks)
+    s, tt = _f64(s), _f64(tt)
+    lo, hi = Ks.min(axis=0), Ks.max(axis=0)
+    den = 2.0 * np.pi * tt[None, :]
+    return {"K_lo": lo, "K_hi": hi, "L_lo": np.sqrt(lo / den) - s[:, None],
+            "L_hi": np.sqrt(hi / den) - s[:, None], "K_all": Ks}
+

@@ -79,6 +79,78 @@ void oracle_csr_points(int64_t n, const double box[6], uint64_t seed, uint32_t s
     }
 }
 
+/* Section 3, bootstrapping: point i of realization `sim` is observed point
+ * src = floor(u * n), u the 53-bit uniform of Philox block (i, sim, 4, i>>32)
+ * under key (seed lo, seed hi); the product is rounded once and a result that
+ * rounds up to n is taken as n - 1. */
+int64_t oracle_bootstrap_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i) {
+    const uint32_t ctr[4] = {(uint32_t)i, sim, 4u, (uint32_t)((uint64_t)i >> 32)};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    const double u = oracle_u01(w[0], w[1]);
+    int64_t src = (int64_t)(u * (double)n);
+    if (src >= n) src = n - 1;
+    return src;
+}
+
+void oracle_bootstrap_points(const double* x, const double* y, const double* t, int64_t n,
+                             uint64_t seed, uint32_t sim, double* ox, double* oy, double* ot) {
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t src = oracle_bootstrap_index(n, seed, sim, i);
+        ox[i] = x[src];
+        oy[i] = y[src];
+        ot[i] = t[src];
+    }
+}
+
+/* Section 3, random permutation: the timestamps are exchanged among the points
+ * by a pseudo-random bijection pi of [0, n) (t_i <- t_pi(i), x and y kept).
+ * pi is a balanced 4-round Feistel network on b-bit values (b the smallest even
+ * number >= 2 with 2^b >= n), round r mixing the right half into the left with
+ * the low half-width bits of word 0 of Philox block (right, sim, 16 + r, 0)
+ * under key (seed lo, seed hi) (Luby-Rackoff construction), restricted to
+ * [0, n) by cycle walking: apply the network again until the value is below n
+ * (Black and Rogaway, "Ciphers with arbitrary finite domains", 2002). */
+int oracle_feistel_bits(int64_t n) {
+    int b = 2;
+    while (((int64_t)1 << b) < n) b += 2;
+    return b;
+}
+
+uint64_t oracle_feistel(uint64_t v, int b, uint64_t seed, uint32_t sim) {
+    const int half = b / 2;
+    const uint64_t mask = ((uint64_t)1 << half) - 1;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint64_t left = v >> half, right = v & mask;
+    for (uint32_t r = 0; r < 4; ++r) {
+        const uint32_t ctr[4] = {(uint32_t)right, sim, 16u + r, 0u};
+        uint32_t w[4];
+        oracle_philox4x32_10(ctr, key, w);
+        const uint64_t f = (uint64_t)w[0] & mask;
+        const uint64_t next_right = left ^ f;
+        left = right;
+        right = next_right;
+    }
+    return (left << half) | right;
+}
+
+int64_t oracle_permutation_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i) {
+    const int b = oracle_feistel_bits(n);
+    uint64_t v = oracle_feistel((uint64_t)i, b, seed, sim);
+    while (v >= (uint64_t)n) v = oracle_feistel(v, b, seed, sim);
+    return (int64_t)v;
+}
+
+void oracle_permutation_points(const double* x, const double* y, const double* t, int64_t n,
+                               uint64_t seed, uint32_t sim, double* ox, double* oy, double* ot) {
+    for (int64_t i = 0; i < n; ++i) {
+        ox[i] = x[i];
+        oy[i] = y[i];
+        ot[i] = t[oracle_permutation_index(n, seed, sim, i)];
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * Section 3, spatial isotropic edge correction: the weight is the proportion
  * of the circumference of the circle centred at point i with radius d_ij that

@@ -22,7 +22,9 @@
  *   - L = sqrt(K / (2 pi t)) - s (Eq. 4);
  *   - CSR simulations: n points uniform in the box and window, drawn with
  *     Philox4x32-10 (Salmon et al., SC'11) under counter (i, sim, stream, 0),
- *     key (seed lo, seed hi) (Section 3, Monte Carlo simulation).
+ *     key (seed lo, seed hi) (Section 3, Monte Carlo simulation);
+ *   - bootstrap and random-permutation simulations (Section 3) draw from the
+ *     same generator (streams 4 and 16..19), see their declarations.
  *
  * Grids are row-major [cs][ct]; bins are non-cumulative in *_hist and
  * cumulative (d <= s_a and u <= t_b) everywhere else.
@@ -44,6 +46,21 @@ double oracle_u01(uint32_t w0, uint32_t w1);
 /* One CSR realization `sim` of n points in box[6] = {x0,x1,y0,y1,t0,t1}. */
 void oracle_csr_points(int64_t n, const double box[6], uint64_t seed, uint32_t sim,
                        double* x, double* y, double* t);
+
+/* Bootstrapping (Section 3): source index of point i of realization `sim`
+ * (uniform draw with replacement), and the whole resampled realization. */
+int64_t oracle_bootstrap_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i);
+void oracle_bootstrap_points(const double* x, const double* y, const double* t, int64_t n,
+                             uint64_t seed, uint32_t sim, double* ox, double* oy, double* ot);
+
+/* Random permutation (Section 3): pi(i) of realization `sim`, the keyed Feistel
+ * bijection on b = oracle_feistel_bits(n) bits it is built from, and the
+ * realization (x, y kept, t_i <- t_pi(i)). */
+int oracle_feistel_bits(int64_t n);
+uint64_t oracle_feistel(uint64_t v, int b, uint64_t seed, uint32_t sim);
+int64_t oracle_permutation_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i);
+void oracle_permutation_points(const double* x, const double* y, const double* t, int64_t n,
+                               uint64_t seed, uint32_t sim, double* ox, double* oy, double* ot);
 
 /* Spatial isotropic weight: proportion of the circumference of the circle of
  * radius r centred at (xi, yi) that lies inside the rectangle.  Computed as

@@ -315,3 +315,106 @@ def test_envelope_is_min_max_of_simulations(orc):
         x, y, t = orc.csr_points(300, box, 42, k)
         np.testing.assert_array_equal(orc.k_function(x, y, t, box, s, tt)["K"], Ka[k])
     assert (env["L_lo"] <= env["L_hi"]).all()
+
+
+# ----------------------------------------------------------- bootstrap / permutation (Sec. 3)
+
+
+@pytest.mark.parametrize("b", [2, 4, 6, 10])
+def test_feistel_network_is_a_bijection(orc, b):
+    for seed, sim in ((0, 0), (12345, 7), (2**63 + 5, 99)):
+        out = sorted(orc.feistel(v, b, seed, sim) for v in range(1 << b))
+        assert out == list(range(1 << b))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 17, 1000, 4097])
+def test_permutation_is_a_permutation(orc, n):
+    assert orc.feistel_bits(n) % 2 == 0 and (1 << orc.feistel_bits(n)) >= n
+    for sim in (0, 1, 2):
+        p = [orc.permutation_index(n, 42, sim, i) for i in range(n)]
+        assert sorted(p) == list(range(n))
+    if n >= 17:  # distinct realizations differ
+        assert [orc.permutation_index(n, 42, 0, i) for i in range(n)] != \
+               [orc.permutation_index(n, 42, 1, i) for i in range(n)]
+
+
+def test_permutation_exchanges_only_the_timestamps(orc):
+    rng = np.random.default_rng(3)
+    x, y, t = rng.uniform(0, 100, 300), rng.uniform(0, 50, 300), rng.uniform(0, 9, 300)
+    px, py, pt = orc.permutation_points(x, y, t, 7, 4)
+    np.testing.assert_array_equal(px, x)
+    np.testing.assert_array_equal(py, y)
+    np.testing.assert_array_equal(np.sort(pt), np.sort(t))
+    assert not np.array_equal(pt, t)
+
+
+def test_permutation_is_uniform_on_small_sets(orc):
+    # all 6 orders of 3 points, and every (position, source) pair of 10 points, come out with
+    # equal frequency (chi-square far inside a 1e-6 tail)
+    import itertools
+
+    sims = 6000
+    orders = {p: 0 for p in itertools.permutations(range(3))}
+    for k in range(sims):
+        orders[tuple(orc.permutation_index(3, 11, k, i) for i in range(3))] += 1
+    e = sims / 6
+    chi2 = sum((c - e) ** 2 / e for c in orders.values())
+    assert chi2 < 35.9, orders  # 5 dof
+    sims = 3000
+    cnt = np.zeros((10, 10))
+    for k in range(sims):
+        for i in range(10):
+            cnt[i, orc.permutation_index(10, 5, k, i)] += 1
+    e = sims / 10
+    chi2 = ((cnt - e) ** 2 / e).sum()
+    assert chi2 < 81 + 6 * math.sqrt(2 * 81)  # 81 dof
+
+
+def test_permutation_keeps_spatial_pair_counts(orc):
+    # exchanging timestamps leaves every spatial distance as it is: with a temporal threshold
+    # that spans the whole period, the cumulative counts equal the observed ones
+    rng = np.random.default_rng(8)
+    box = (0.0, 400.0, 0.0, 300.0, 0.0, 50.0)
+    x, y, t = rng.uniform(0, 400, 250), rng.uniform(0, 300, 250), rng.uniform(0, 50, 250)
+    s, tt = np.array([20.0, 45.0, 90.0]), np.array([5.0, 50.0])
+    obs = orc.k_function(x, y, t, box, s, tt)
+    for sim in range(3):
+        px, py, pt = orc.permutation_points(x, y, t, 99, sim)
+        got = orc.k_function(px, py, pt, box, s, tt)
+        np.testing.assert_array_equal(got["C"][:, -1], obs["C"][:, -1])
+
+
+def test_bootstrap_draws_are_observed_points_uniformly(orc):
+    rng = np.random.default_rng(4)
+    n = 500
+    x, y, t = rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.uniform(0, 1, n)
+    counts = np.zeros(n)
+    sims = 200
+    for k in range(sims):
+        bx, by, bt = orc.bootstrap_points(x, y, t, 77, k)
+        idx = np.array([orc.bootstrap_index(n, 77, k, i) for i in range(n)])
+        assert idx.min() >= 0 and idx.max() < n
+        np.testing.assert_array_equal(bx, x[idx])
+        np.testing.assert_array_equal(by, y[idx])
+        np.testing.assert_array_equal(bt, t[idx])
+        counts += np.bincount(idx, minlength=n)
+    e = sims
+    chi2 = ((counts - e) ** 2 / e).sum()
+    assert abs(chi2 - (n - 1)) < 6 * math.sqrt(2 * (n - 1))
+    assert orc.bootstrap_index(1, 3, 0, 0) == 0
+
+
+def test_bootstrap_duplicates_are_zero_distance_pairs(orc):
+    # a realization that repeats a point pairs the copies at d = 0, u = 0, weight 1: the
+    # first bin counts exactly the ordered pairs of copies of the same observed point
+    rng = np.random.default_rng(6)
+    box = (0.0, 1000.0, 0.0, 1000.0, 0.0, 100.0)
+    n = 200
+    x, y, t = rng.uniform(0, 1000, n), rng.uniform(0, 1000, n), rng.uniform(0, 100, n)
+    bx, by, bt = orc.bootstrap_points(x, y, t, 5, 0)
+    idx = np.array([orc.bootstrap_index(n, 5, 0, i) for i in range(n)])
+    mult = np.bincount(idx, minlength=n)
+    s, tt = np.array([1e-9, 10.0]), np.array([1e-9, 5.0])
+    got = orc.k_function(bx, by, bt, box, s, tt)
+    assert got["C"][0, 0] == int((mult * (mult - 1)).sum())
+    assert got["S"][0, 0] == got["C"][0, 0]  # interior duplicates: weight exactly 1
