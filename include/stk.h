@@ -74,6 +74,12 @@ enum { STK_PREC_FP64 = 0, STK_PREC_FP32_GUARDED = 1 };
 enum { STK_NORM_N_NM1 = 0, STK_NORM_N2 = 1 };
 /* Execution form for jobs with simulations. */
 enum { STK_EXEC_BATCHED = 0, STK_EXEC_PLAIN = 1 };
+/* Simulation method (Section 3): Monte Carlo CSR (points uniform in the box and period),
+ * random permutation (the observed points with their timestamps exchanged by a keyed
+ * pseudo-random bijection: a 4-round Feistel network on Philox round functions, streams
+ * 16-19, restricted to [0, n) by cycle walking), bootstrapping (n draws with replacement from
+ * the observed points: source floor(u n), u the 53-bit uniform of Philox stream 4). */
+enum { STK_SIM_CSR = 0, STK_SIM_PERMUTATION = 1, STK_SIM_BOOTSTRAP = 2 };
 
 /* Create a handle over n points (host arrays, FP64).  The points are copied to
  * the device.  Errors: STK_EINVAL (NULL, n < 2, bad box), STK_EDOMAIN (point
@@ -126,6 +132,7 @@ typedef struct {
     const uint8_t* centre_mask; /* optional host [n]: only centres with mask != 0
                                    contribute to the OBSERVED grids (sampled-centre
                                    checking mode); NULL = all */
+    int sim_method;      /* STK_SIM_*; the envelope is over realizations of this method */
 } stk_request;
 
 typedef struct {
@@ -169,6 +176,13 @@ int stk_last_stats(const stk_handle* h, stk_stats* out);
  * Exposes step "CSR simulation generation" for checking. */
 int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, double* x,
                    double* y, double* t);
+
+/* One random-permutation or bootstrap realization (method STK_SIM_PERMUTATION or
+ * STK_SIM_BOOTSTRAP, Section 3) of the observed host points x0, y0, t0 [n], generated by
+ * the device generator the jobs use, copied to caller-owned host arrays x, y, t [n].
+ * Exposes step "simulation generation" for checking.  Errors: STK_EINVAL. */
+int stk_sim_resample(const double* x0, const double* y0, const double* t0, int64_t n,
+                     int method, uint64_t seed, uint32_t sim, double* x, double* y, double* t);
 
 /* Observed K of one pattern without allocating memory.  Not part of the paper's method: an
  * interface for callers that cannot call cudaMalloc where they need K (a region where
@@ -232,6 +246,7 @@ typedef struct {
     int n_sims;          /* 0 = observed K only */
     uint64_t seed;
     int want_sims;       /* 1: keep per-realization K and counts for stk_poll */
+    int sim_method;      /* STK_SIM_* */
 } stk_job;
 
 typedef struct {

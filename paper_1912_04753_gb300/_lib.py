@@ -18,6 +18,7 @@ STK_EDGE_NONE, STK_EDGE_ISOTROPIC = 0, 1
 STK_PREC_FP64, STK_PREC_FP32_GUARDED = 0, 1
 STK_NORM_N_NM1, STK_NORM_N2 = 0, 1
 STK_EXEC_BATCHED, STK_EXEC_PLAIN = 0, 1
+STK_SIM_CSR, STK_SIM_PERMUTATION, STK_SIM_BOOTSTRAP = 0, 1, 2
 STK_MAX_THRESHOLDS = 64
 
 _P = ctypes.c_void_p
@@ -37,7 +38,7 @@ class stk_request(ctypes.Structure):
     _fields_ = [("s", _P), ("cs", ctypes.c_int), ("tt", _P), ("ct", ctypes.c_int),
                 ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int), ("norm", ctypes.c_int),
                 ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64), ("exec", ctypes.c_int),
-                ("centre_mask", _P)]
+                ("centre_mask", _P), ("sim_method", ctypes.c_int)]
 
 
 class stk_result(ctypes.Structure):
@@ -65,7 +66,7 @@ class stk_job(ctypes.Structure):
     _fields_ = [("dataset", ctypes.c_uint64), ("s", _P), ("cs", ctypes.c_int), ("tt", _P),
                 ("ct", ctypes.c_int), ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int),
                 ("norm", ctypes.c_int), ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("want_sims", ctypes.c_int)]
+                ("want_sims", ctypes.c_int), ("sim_method", ctypes.c_int)]
 
 
 class stk_serve_stats(ctypes.Structure):
@@ -104,6 +105,7 @@ def load(build_if_missing: bool = False):
         "stk_run": ([_P, ctypes.POINTER(stk_request), ctypes.POINTER(stk_result)], i32),
         "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
         "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
+        "stk_sim_resample": ([_P, _P, _P, i64, i32, u64, u32, _P, _P, _P], i32),
         "stk_k_noalloc": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, i32, _P, i32, i32, _P,
                            _P, _P, _P, _P], i32),
         "stk_server_create": ([ctypes.POINTER(stk_server_config), PP], i32),
@@ -215,14 +217,14 @@ def stk_envelope(h, s, tt, n_sims, seed, edge_mode=STK_EDGE_ISOTROPIC,
 
 def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
             prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
-            centre_mask=None, want_sims=False):
+            centre_mask=None, want_sims=False, sim_method=STK_SIM_CSR):
     """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim)."""
     s, tt = _f64(s), _f64(tt)
     cs, ct = s.shape[0], tt.shape[0]
     nb = cs * ct
     mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
     q = stk_request(_ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims, seed, exec_mode,
-                    _ptr(mask))
+                    _ptr(mask), sim_method)
     o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
     if n_sims > 0:
         for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
@@ -252,6 +254,17 @@ def stk_sim_points(box, n, seed, sim):
     b = _box(box)
     _check(load().stk_sim_points(ctypes.byref(b), n, seed, sim, _ptr(x), _ptr(y), _ptr(t)))
     return x, y, t
+
+
+def stk_sim_resample(x, y, t, method, seed, sim):
+    """Realization `sim` of the device permutation / bootstrap generator (Section 3) of the
+    host points x, y, t, copied back to host arrays."""
+    x, y, t = _f64(x), _f64(y), _f64(t)
+    n = x.shape[0]
+    ox, oy, ot = (np.zeros(n) for _ in range(3))
+    _check(load().stk_sim_resample(_ptr(x), _ptr(y), _ptr(t), n, method, seed, sim, _ptr(ox),
+                                   _ptr(oy), _ptr(ot)))
+    return ox, oy, ot
 
 
 def stk_k_noalloc(x, y, t, box, s, tt, K, L, S, C, edge_mode=STK_EDGE_ISOTROPIC, stream=None):
@@ -293,11 +306,12 @@ def stk_server_unregister(sv, dataset: int):
 
 
 def stk_submit(sv, dataset, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
-               prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, want_sims=False) -> int:
+               prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, want_sims=False,
+               sim_method=STK_SIM_CSR) -> int:
     """Queue a K / envelope job on a registered point set; returns its ticket."""
     s, tt = _f64(s), _f64(tt)
     j = stk_job(dataset, _ptr(s), s.shape[0], _ptr(tt), tt.shape[0], edge_mode, prec, norm,
-                n_sims, seed, 1 if want_sims else 0)
+                n_sims, seed, 1 if want_sims else 0, sim_method)
     tk = ctypes.c_uint64()
     _check(load().stk_submit(sv, ctypes.byref(j), ctypes.byref(tk)))
     return tk.value

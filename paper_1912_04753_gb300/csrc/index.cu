@@ -144,6 +144,84 @@ __global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ se
     }
 }
 
+// ---------------------------------------------------------------------------- resampling
+// Bootstrapping (Section 3): point i of a realization is observed point floor(u n), u the
+// 53-bit uniform of Philox block (i, sim, 4, i >> 32), a product that rounds up to n taken
+// as n - 1.
+__device__ __forceinline__ int64_t bootstrap_src(uint64_t seed, uint32_t sim, int64_t i,
+                                                 int64_t n) {
+    const uint4 w = philox4x32_10(
+        make_uint4((uint32_t)i, sim, 4u, (uint32_t)((uint64_t)i >> 32)),
+        make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    int64_t src = (int64_t)__dmul_rn(u01(w.x, w.y), (double)n);
+    return src < n ? src : n - 1;
+}
+
+// Random permutation (Section 3): a balanced 4-round Feistel network on b-bit values whose
+// round r mixes the right half into the left with the low half-width bits of word 0 of
+// Philox block (right, sim, 16 + r, 0) (Luby-Rackoff), restricted to [0, n) by cycle walking
+// (Black and Rogaway, 2002).
+__device__ __forceinline__ uint64_t feistel(uint64_t v, int b, uint64_t seed, uint32_t sim) {
+    const int half = b >> 1;
+    const uint64_t mask = (1ull << half) - 1ull;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    uint64_t left = v >> half, right = v & mask;
+#pragma unroll
+    for (uint32_t r = 0; r < 4; ++r) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)right, sim, 16u + r, 0u), key);
+        const uint64_t nr = left ^ ((uint64_t)w.x & mask);
+        left = right;
+        right = nr;
+    }
+    return (left << half) | right;
+}
+
+constexpr int kWalkLimit = 1 << 16;  // cycle-walk steps (the expected number is below 4)
+
+__global__ void gen_resample_kernel(int method, int64_t n, int m, int bits,
+                                    const uint64_t* __restrict__ seeds,
+                                    const uint32_t* __restrict__ sims, GridDev g,
+                                    int64_t ncells, const double* __restrict__ x0,
+                                    const double* __restrict__ y0,
+                                    const double* __restrict__ t0, double* __restrict__ x,
+                                    double* __restrict__ y, double* __restrict__ t,
+                                    uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
+                                    uint32_t* __restrict__ cnt,
+                                    unsigned long long* __restrict__ err) {
+    const int64_t total = n * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / n);
+        const int64_t i = gi - (int64_t)k * n;
+        const uint32_t sim = sims[k];
+        const uint64_t seed = seeds[k];
+        double xi, yi, ti;
+        if (method == STK_SIM_BOOTSTRAP) {
+            const int64_t src = bootstrap_src(seed, sim, i, n);
+            xi = x0[src];
+            yi = y0[src];
+            ti = t0[src];
+        } else {
+            uint64_t v = feistel((uint64_t)i, bits, seed, sim);
+            int steps = 0;
+            while (v >= (uint64_t)n && ++steps < kWalkLimit) v = feistel(v, bits, seed, sim);
+            if (v >= (uint64_t)n) {  // never expected; keep the index valid and report it
+                atomicAdd(err, 1ull);
+                v = (uint64_t)i;
+            }
+            xi = x0[i];
+            yi = y0[i];
+            ti = t0[v];
+        }
+        x[gi] = xi;
+        y[gi] = yi;
+        t[gi] = ti;
+        const uint32_t kk = key_of(g, xi, yi, ti);
+        key[gi] = kk;
+        rank[gi] = atomicAdd(&cnt[(int64_t)k * ncells + kk], 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------- scan
 // Exclusive scan of uint32 in tiles of kThreads*kItems, with the tile sums scanned
 // recursively.  tmp holds the tile sums of every level.
@@ -348,6 +426,23 @@ cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32
     gen_csr_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
         n, m, seeds, sims, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, x, y, t, key, rank,
         cell_count);
+    return cudaGetLastError();
+}
+
+int feistel_bits(int64_t n) {
+    int b = 2;
+    while (((int64_t)1 << b) < n) b += 2;
+    return b;
+}
+
+cudaError_t launch_gen_resample(int method, int64_t n, int m, const uint64_t* seeds,
+                                const uint32_t* sims, const Grid& g, const double* x0,
+                                const double* y0, const double* t0, double* x, double* y,
+                                double* t, uint32_t* key, uint32_t* rank, uint32_t* cell_count,
+                                unsigned long long* err, cudaStream_t st) {
+    gen_resample_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        method, n, m, feistel_bits(n), seeds, sims, grid_dev(g), g.ncells, x0, y0, t0, x, y, t,
+        key, rank, cell_count, err);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ struct Job {
     uint64_t ticket = 0;
     uint64_t dataset = 0;
     std::vector<double> s, tt;
-    int edge_mode = 0, prec = 0, norm = 0, n_sims = 0, want_sims = 0;
+    int edge_mode = 0, prec = 0, norm = 0, n_sims = 0, want_sims = 0, sim_method = 0;
     uint64_t seed = 0;
     JobState state = JobState::Queued;
     int rc = STK_OK;
@@ -72,7 +72,7 @@ struct Dataset {
 
 bool same_params(const Job& a, const Job& b) {
     return a.dataset == b.dataset && a.s == b.s && a.tt == b.tt && a.edge_mode == b.edge_mode &&
-           a.prec == b.prec && a.norm == b.norm;
+           a.prec == b.prec && a.norm == b.norm && a.sim_method == b.sim_method;
 }
 
 }  // namespace
@@ -232,6 +232,7 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual) {
     q.prec = head.prec;
     q.norm = head.norm;
     q.exec = STK_EXEC_BATCHED;
+    q.sim_method = head.sim_method;
     stk::SimPlan plan;
     std::vector<int> group_of(b.jobs.size(), -1), first_row(b.jobs.size(), 0);
     bool any_sims = false;
@@ -455,6 +456,8 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
         return note(STK_EINVAL, "unknown prec");
     if (job->norm != STK_NORM_N_NM1 && job->norm != STK_NORM_N2)
         return note(STK_EINVAL, "unknown norm");
+    if (job->sim_method < STK_SIM_CSR || job->sim_method > STK_SIM_BOOTSTRAP)
+        return note(STK_EINVAL, "unknown sim_method");
     auto j = std::make_shared<Job>();
     j->dataset = job->dataset;
     j->s.assign(job->s, job->s + job->cs);
@@ -465,6 +468,7 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
     j->n_sims = job->n_sims;
     j->seed = job->seed;
     j->want_sims = job->want_sims;
+    j->sim_method = job->sim_method;
     std::lock_guard<std::mutex> lock(sv->mu);
     auto it = sv->datasets.find(job->dataset);
     if (it == sv->datasets.end()) return note(STK_EINVAL, "unknown dataset");

@@ -227,7 +227,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
 struct TuneKey {
     int64_t n;
     double box[6], s_max, t_max;
-    int prec, edge;
+    int prec, edge, method;
     bool operator<(const TuneKey& o) const {
         return memcmp(this, &o, sizeof(TuneKey)) < 0;
     }
@@ -244,6 +244,7 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
     key.t_max = q->tt[q->ct - 1];
     key.prec = q->prec;
     key.edge = q->edge_mode;
+    key.method = q->sim_method;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -313,6 +314,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         return fail(STK_EINVAL, "unknown norm %d", q->norm);
     if (q->exec != STK_EXEC_BATCHED && q->exec != STK_EXEC_PLAIN)
         return fail(STK_EINVAL, "unknown exec %d", q->exec);
+    if (q->sim_method < STK_SIM_CSR || q->sim_method > STK_SIM_BOOTSTRAP)
+        return fail(STK_EINVAL, "unknown sim_method %d", q->sim_method);
     const int n_sims = (int)plan.seed.size();
     if (n_sims > (1 << 24) || plan.id.size() != plan.seed.size())
         return fail(STK_EINVAL, "n_sims out of range");
@@ -489,12 +492,21 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             CK(cudaMemcpyAsync(h->simid.p, h->h_id + s_first, 4 * (size_t)ms,
                                cudaMemcpyHostToDevice, st), "seeds");
             const int64_t off = (int64_t)first_sim_slot * n;
-            CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
-                              as<double>(h->ux) + off, as<double>(h->uy) + off,
-                              as<double>(h->ut) + off,
-                              as<uint32_t>(h->key) + off, as<uint32_t>(h->rank) + off,
-                              as<uint32_t>(h->counts) + (int64_t)first_sim_slot * ncells, st),
-               "CSR generation");
+            uint32_t* cnt0 = as<uint32_t>(h->counts) + (int64_t)first_sim_slot * ncells;
+            if (q->sim_method == STK_SIM_CSR)
+                CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
+                                  as<double>(h->ux) + off, as<double>(h->uy) + off,
+                                  as<double>(h->ut) + off, as<uint32_t>(h->key) + off,
+                                  as<uint32_t>(h->rank) + off, cnt0, st),
+                   "CSR generation");
+            else
+                CK(launch_gen_resample(q->sim_method, n, ms, as<uint64_t>(h->simseed),
+                                       as<uint32_t>(h->simid), g, h->d_x, h->d_y, h->d_t,
+                                       as<double>(h->ux) + off, as<double>(h->uy) + off,
+                                       as<double>(h->ut) + off, as<uint32_t>(h->key) + off,
+                                       as<uint32_t>(h->rank) + off, cnt0,
+                                       as<unsigned long long>(h->stats) + 2, st),
+                   "resampling");
         }
         CK(launch_exclusive_scan(as<uint32_t>(h->counts), as<uint32_t>(h->start),
                                  (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
@@ -582,7 +594,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             key.insert(key.end(), c, c + b);
         };
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
-                              (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows};
+                              (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
+                              q->sim_method};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -919,6 +932,64 @@ int stk_envelope(stk_handle* h, const double* s, int cs, const double* tt, int c
         (rc = copy_rows(h, h->env, 2, 1, nbins, L_lo)) || (rc = copy_rows(h, h->env, 3, 1, nbins, L_hi)))
         return rc;
     CK(cudaStreamSynchronize(h->stream), "result copy");
+    return STK_OK;
+}
+
+int stk_sim_resample(const double* x0, const double* y0, const double* t0, int64_t n,
+                     int method, uint64_t seed, uint32_t sim, double* x, double* y, double* t) {
+    if (!x0 || !y0 || !t0 || !x || !y || !t) return fail(STK_EINVAL, "arrays must not be NULL");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n out of range");
+    if (method != STK_SIM_PERMUTATION && method != STK_SIM_BOOTSTRAP)
+        return fail(STK_EINVAL, "method must be STK_SIM_PERMUTATION or STK_SIM_BOOTSTRAP");
+    // one cell holding everything: keys and ranks are by-products here
+    Grid g;
+    memset(&g, 0, sizeof g);
+    g.nx = g.ny = g.nt = 1;
+    g.ncells = 1;
+    g.cw = g.ch = g.cd = 1.0;
+    DevBuf bx0, by0, bt0, bx, by, bt, bk, br, bc, bs, be;
+    const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+    DevBuf* all[] = {&bx0, &by0, &bt0, &bx, &by, &bt, &bk, &br, &bc, &bs, &be};
+    auto release = [&]() {
+        for (DevBuf* b : all) free_buf(*b);
+    };
+    int rc;
+    if ((rc = ensure(bx0, b8, "x")) || (rc = ensure(by0, b8, "y")) || (rc = ensure(bt0, b8, "t")) ||
+        (rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
+        (rc = ensure(bk, b4, "keys")) || (rc = ensure(br, b4, "ranks")) ||
+        (rc = ensure(bc, 16, "counts")) || (rc = ensure(bs, 16, "seed")) ||
+        (rc = ensure(be, 16, "status"))) {
+        release();
+        return rc;
+    }
+    struct {
+        uint64_t seed;
+        uint32_t sim, pad;
+    } key_sim = {seed, sim, 0};
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMemcpyAsync(bx0.p, x0, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(by0.p, y0, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bt0.p, t0, b8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bc.p, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(be.p, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bs.p, &key_sim, sizeof key_sim, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_gen_resample(method, n, 1, as<uint64_t>(bs),
+                                reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(bs.p) + 8),
+                                g, as<double>(bx0), as<double>(by0), as<double>(bt0),
+                                as<double>(bx), as<double>(by), as<double>(bt), as<uint32_t>(bk),
+                                as<uint32_t>(br), as<uint32_t>(bc), as<unsigned long long>(be),
+                                st);
+    unsigned long long walk_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, bx.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, by.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, bt.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&walk_err, be.p, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "resampling");
+    if (walk_err) return fail(STK_ECUDA, "internal consistency check failed (cycle walk)");
     return STK_OK;
 }
 

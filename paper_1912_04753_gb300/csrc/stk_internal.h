@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "stk.h"
+
 namespace stk {
 
 constexpr int kMaxThr = 64;   // thresholds per axis
@@ -114,6 +116,14 @@ cudaError_t launch_keys_observed(const double* x, const double* y, const double*
                                  uint32_t* cell_count, int* bad_flag, cudaStream_t st);
 cudaError_t launch_validate(const double* x, const double* y, const double* t, int64_t n,
                             const double box[6], int* bad_flag, cudaStream_t st);
+// Realization slot k (0..m-1) from the observed points x0, y0, t0 [n] (device): a random
+// permutation of the timestamps or a bootstrap resample, keyed like the CSR generator;
+// err counts cycle walks that ran out (never expected).
+cudaError_t launch_gen_resample(int method, int64_t n, int m, const uint64_t* seeds,
+                                const uint32_t* sims, const Grid& g, const double* x0,
+                                const double* y0, const double* t0, double* x, double* y,
+                                double* t, uint32_t* key, uint32_t* rank, uint32_t* cell_count,
+                                unsigned long long* err, cudaStream_t st);
 // realization slot k (0..m-1) is Philox realization sims[k] under key seeds[k] (device arrays)
 cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
                            const Grid& g, double* x, double* y, double* t, uint32_t* key,
@@ -175,8 +185,6 @@ int validate_thresholds(const double box[6], const double* s, int cs, const doub
 
 #include <utility>
 #include <vector>
-
-#include "stk.h"
 
 namespace stk {
 
