@@ -374,6 +374,27 @@ def run_ours(args):
 
     serve = serve_bench(args, stk) if (args.serve_requests > 0 and rank == 0) else None
 
+    # the other two simulation methods of Section 3 on the same job shape
+    methods = None
+    if args.methods and rank == 0:
+        methods = {}
+        for name, mth in (("permutation", stk.STK_SIM_PERMUTATION),
+                          ("bootstrap", stk.STK_SIM_BOOTSTRAP)):
+            stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
+                        exec_mode=exec_mode, sim_method=mth)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
+                        exec_mode=exec_mode, sim_method=mth)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_m = e0.elapsed_time(e1)
+            sm = stk.stk_last_stats(h)
+            methods[name] = {"job_s": ms_m / 1e3, "sims_per_s": w.n_sims / (ms_m / 1e3),
+                             "value": sm["qualifying_pairs"] / (ms_m / 1e3), "unit": UNIT,
+                             "qualifying_pairs": sm["qualifying_pairs"]}
+
     if rank != 0:
         stk.stk_destroy(h)
         if ws > 1:
@@ -419,6 +440,7 @@ def run_ours(args):
         "clocks": clocks,
         "plain_fp64": plain,
         "serve": serve,
+        "sim_methods": methods,
     }
     print(json.dumps(line), flush=True)
     stk.stk_destroy(h)
@@ -446,6 +468,8 @@ def build_parser():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-fp64", type=int, default=1,
                     help="also replay the stream through a FIFO of plain FP64 jobs")
+    ap.add_argument("--methods", type=int, default=1,
+                    help="also time the job with permutation and bootstrap simulations")
     return ap
 
 
