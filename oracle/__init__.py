@@ -74,6 +74,19 @@ def _load():
         lib.oracle_permutation_index.restype = i64
         lib.oracle_permutation_points.argtypes = [P, P, P, i64, u64, u32, P, P, P]
         lib.oracle_permutation_points.restype = None
+        lib.oracle_finalize_area.argtypes = [i64, d, d, P, i32, P, i32, i32, P, P, P, P, P, P]
+        lib.oracle_finalize_area.restype = None
+        lib.oracle_polygon_area.argtypes = [P, P, i32]
+        lib.oracle_polygon_area.restype = d
+        lib.oracle_point_in_polygon.argtypes = [d, d, P, P, i32]
+        lib.oracle_point_in_polygon.restype = i32
+        lib.oracle_polygon_weight.argtypes = [d, d, d, P, P, i32]
+        lib.oracle_polygon_weight.restype = d
+        lib.oracle_pair_hist_polygon.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, P, i32,
+                                                 i32, P, P]
+        lib.oracle_pair_hist_polygon.restype = i64
+        lib.oracle_csr_polygon_points.argtypes = [i64, P, P, P, i32, u64, u32, i32, P, P, P]
+        lib.oracle_csr_polygon_points.restype = i32
         _lib = lib
     return _lib
 
@@ -227,8 +240,59 @@ def permutation_points(x, y, t, seed: int, sim: int):
     return ox, oy, ot
 
 
-def simulation_points(method: int, x, y, t, box, seed: int, sim: int):
+def polygon_area(vx, vy) -> float:
+    vx, vy = _f64(vx), _f64(vy)
+    return _load().oracle_polygon_area(_ptr(vx), _ptr(vy), len(vx))
+
+
+def point_in_polygon(px: float, py: float, vx, vy) -> bool:
+    vx, vy = _f64(vx), _f64(vy)
+    return bool(_load().oracle_point_in_polygon(px, py, _ptr(vx), _ptr(vy), len(vx)))
+
+
+def polygon_weight(xi: float, yi: float, r: float, vx, vy) -> float:
+    """Proportion of the circle's circumference inside the polygon (isotropic weight)."""
+    vx, vy = _f64(vx), _f64(vy)
+    return _load().oracle_polygon_weight(xi, yi, r, _ptr(vx), _ptr(vy), len(vx))
+
+
+def k_function_polygon(x, y, t, box, vx, vy, s, tt, edge_mode=1, norm=0):
+    """The estimator over a polygon study area (A = polygon area, period box[4..5])."""
+    x, y, t, s, tt, vx, vy = map(_f64, (x, y, t, s, tt, vx, vy))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.zeros(cs * ct, np.int64)
+    wsum = np.zeros(cs * ct, np.float64)
+    lib = _load()
+    q = lib.oracle_pair_hist_polygon(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(vx),
+                                     _ptr(vy), len(vx), _ptr(s), cs, _ptr(tt), ct, edge_mode,
+                                     _ptr(cnt), _ptr(wsum))
+    C = np.zeros(cs * ct, np.int64)
+    S, K, L = (np.zeros(cs * ct, np.float64) for _ in range(3))
+    lib.oracle_finalize_area(len(x), polygon_area(vx, vy), b[5] - b[4], _ptr(s), cs, _ptr(tt),
+                             ct, norm, _ptr(cnt), _ptr(wsum), _ptr(C), _ptr(S), _ptr(K),
+                             _ptr(L))
+    sh = (cs, ct)
+    return {"C": C.reshape(sh), "S": S.reshape(sh), "K": K.reshape(sh), "L": L.reshape(sh),
+            "pairs": int(q)}
+
+
+def csr_polygon_points(n: int, box, vx, vy, seed: int, sim: int, max_attempts: int = 4096):
+    """Realization `sim` of CSR in a polygon (rejection from the bounding rectangle)."""
+    vx, vy = _f64(vx), _f64(vy)
+    b = _box(box)
+    x, y, t = (np.empty(n, np.float64) for _ in range(3))
+    rc = _load().oracle_csr_polygon_points(n, _ptr(b), _ptr(vx), _ptr(vy), len(vx), seed, sim,
+                                           max_attempts, _ptr(x), _ptr(y), _ptr(t))
+    if rc != 0:
+        raise ValueError("a point found no position inside the polygon")
+    return x, y, t
+
+
+def simulation_points(method: int, x, y, t, box, seed: int, sim: int, polygon=None):
     """Realization `sim` of the given simulation method (Section 3)."""
+    if method == SIM_CSR and polygon is not None:
+        return csr_polygon_points(len(x), box, polygon[0], polygon[1], seed, sim)
     if method == SIM_CSR:
         return csr_points(len(x), box, seed, sim)
     if method == SIM_PERMUTATION:
@@ -238,13 +302,20 @@ def simulation_points(method: int, x, y, t, box, seed: int, sim: int):
     raise ValueError(f"unknown simulation method {method}")
 
 
-def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, norm=0):
-    """Envelope (Section 3) over n_sims realizations of any simulation method: the
-    element-wise min / max of K (and L of those), plus every realization's K."""
+def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, norm=0,
+                polygon=None):
+    """Envelope (Section 3) over n_sims realizations of any simulation method (optionally in
+    a polygon study area): the element-wise min / max of K (and L of those), plus every
+    realization's K."""
     Ks = []
     for k in range(n_sims):
-        px, py, pt = simulation_points(method, x, y, t, box, seed, k)
-        Ks.append(k_function(px, py, pt, box, s, tt, edge_mode=edge_mode, norm=norm)["K"])
+        px, py, pt = simulation_points(method, x, y, t, box, seed, k, polygon)
+        if polygon is None:
+            r = k_function(px, py, pt, box, s, tt, edge_mode=edge_mode, norm=norm)
+        else:
+            r = k_function_polygon(px, py, pt, box, polygon[0], polygon[1], s, tt,
+                                   edge_mode=edge_mode, norm=norm)
+        Ks.append(r["K"])
     Ks = np.stack(Ks)
     s, tt = _f64(s), _f64(tt)
     lo, hi = Ks.min(axis=0), Ks.max(axis=0)

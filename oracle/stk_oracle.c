@@ -274,6 +274,13 @@ int64_t oracle_pair_hist(int64_t n, const double* x, const double* y, const doub
 void oracle_finalize(int64_t n, const double box[6], const double* s, int cs, const double* tt,
                      int ct, int norm, const int64_t* cnt, const double* wsum, int64_t* C,
                      double* S, double* K, double* L) {
+    const double area = (box[1] - box[0]) * (box[3] - box[2]);
+    oracle_finalize_area(n, area, box[5] - box[4], s, cs, tt, ct, norm, cnt, wsum, C, S, K, L);
+}
+
+void oracle_finalize_area(int64_t n, double area, double dur, const double* s, int cs,
+                          const double* tt, int ct, int norm, const int64_t* cnt,
+                          const double* wsum, int64_t* C, double* S, double* K, double* L) {
     const int nb = cs * ct;
     int64_t* Cc = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
     double* Sc = (double*)malloc(sizeof(double) * (size_t)nb);
@@ -291,8 +298,6 @@ void oracle_finalize(int64_t n, const double box[6], const double* s, int cs, co
             Sc[a * ct + b] = w;
         }
     }
-    const double area = (box[1] - box[0]) * (box[3] - box[2]);
-    const double dur = box[5] - box[4];
     const double nn = (double)n;
     const double denom = (norm == 1) ? nn * nn : nn * (nn - 1.0);
     const double coef = area * dur / denom;
@@ -357,3 +362,181 @@ int oracle_envelope(int64_t n, const double box[6], const double* s, int cs, con
     free(K);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Polygon study areas (the paper's experiments use an 85-vertex outline,
+ * Sections 3 and 6): a simple polygon of nv vertices in either orientation,
+ * closed (its boundary belongs to it).
+ * ------------------------------------------------------------------------- */
+
+/* Shoelace formula, absolute value. */
+double oracle_polygon_area(const double* vx, const double* vy, int nv) {
+    double a = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = (k + 1) % nv;
+        a += vx[k] * vy[k1] - vx[k1] * vy[k];
+    }
+    return fabs(a) * 0.5;
+}
+
+/* 1 if (px, py) lies on the segment a-b: zero cross product and inside the
+ * segment's bounding box. */
+static int on_segment(double px, double py, double ax, double ay, double bx, double by) {
+    const double cross = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+    if (cross != 0.0) return 0;
+    return px >= fmin(ax, bx) && px <= fmax(ax, bx) && py >= fmin(ay, by) && py <= fmax(ay, by);
+}
+
+/* Closed point-in-polygon: boundary points are inside; otherwise the parity of
+ * the crossings of the ray from (px, py) towards +x with the edges, an edge
+ * counting when it straddles the ray's height (upper end exclusive). */
+int oracle_point_in_polygon(double px, double py, const double* vx, const double* vy, int nv) {
+    int inside = 0;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = (k + 1) % nv;
+        const double ax = vx[k], ay = vy[k], bx = vx[k1], by = vy[k1];
+        if (on_segment(px, py, ax, ay, bx, by)) return 1;
+        if ((ay > py) != (by > py)) {
+            const double xc = ax + (py - ay) * (bx - ax) / (by - ay);
+            if (px < xc) inside = !inside;
+        }
+    }
+    return inside;
+}
+
+static int cmp_double(const void* a, const void* b) {
+    const double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : x > y ? 1 : 0;
+}
+
+/* Isotropic spatial weight for a polygon: proportion of the circumference of
+ * the circle of radius r centred at (xi, yi) inside the polygon.  The circle
+ * meets the edges at the roots of |a + s (b - a) - c|^2 = r^2, 0 <= s <= 1;
+ * between consecutive crossing angles an arc is wholly inside or outside, and
+ * its midpoint decides which. */
+double oracle_polygon_weight(double xi, double yi, double r, const double* vx, const double* vy,
+                             int nv) {
+    if (r <= 0.0) return 1.0;
+    double* ang = (double*)malloc(sizeof(double) * (size_t)(2 * nv + 1));
+    int na = 0;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = (k + 1) % nv;
+        const double ax = vx[k], ay = vy[k];
+        const double dx = vx[k1] - ax, dy = vy[k1] - ay;
+        const double fx = ax - xi, fy = ay - yi;
+        const double A = dx * dx + dy * dy;
+        if (A == 0.0) continue;
+        const double B = 2.0 * (fx * dx + fy * dy);
+        const double C = fx * fx + fy * fy - r * r;
+        const double disc = B * B - 4.0 * A * C;
+        if (disc < 0.0) continue;
+        const double sq = sqrt(disc);
+        const double roots[2] = {(-B - sq) / (2.0 * A), (-B + sq) / (2.0 * A)};
+        for (int q = 0; q < 2; ++q) {
+            const double sr = roots[q];
+            if (sr < 0.0 || sr > 1.0) continue;
+            ang[na++] = atan2(fy + sr * dy, fx + sr * dx);
+        }
+    }
+    double w;
+    if (na == 0) {
+        w = oracle_point_in_polygon(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
+    } else {
+        qsort(ang, (size_t)na, sizeof(double), cmp_double);
+        double inside = 0.0;
+        for (int k = 0; k < na; ++k) {
+            const double a0 = ang[k];
+            const double a1 = (k + 1 < na) ? ang[k + 1] : ang[0] + 2.0 * ORACLE_PI;
+            if (!(a1 > a0)) continue;
+            const double mid = 0.5 * (a0 + a1);
+            if (oracle_point_in_polygon(xi + r * cos(mid), yi + r * sin(mid), vx, vy, nv))
+                inside += a1 - a0;
+        }
+        w = inside / (2.0 * ORACLE_PI);
+    }
+    free(ang);
+    return w;
+}
+
+/* Pair histogram with the polygon weight (otherwise as oracle_pair_hist); the
+ * temporal window is box[4]..box[5]. */
+int64_t oracle_pair_hist_polygon(int64_t n, const double* x, const double* y, const double* t,
+                                 const double box[6], const double* vx, const double* vy,
+                                 int nv, const double* s, int cs, const double* tt, int ct,
+                                 int edge_mode, int64_t* cnt, double* wsum) {
+    const int nb = cs * ct;
+    double* s2 = (double*)malloc(sizeof(double) * (size_t)cs);
+    double* comp = (double*)calloc((size_t)nb, sizeof(double));
+    for (int a = 0; a < cs; ++a) s2[a] = s[a] * s[a];
+    for (int k = 0; k < nb; ++k) {
+        cnt[k] = 0;
+        wsum[k] = 0.0;
+    }
+    const double s2max = s2[cs - 1], tmax = tt[ct - 1];
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = x[i] - x[j];
+            const double dy = y[i] - y[j];
+            const double d2 = dx * dx + dy * dy;
+            if (d2 > s2max) continue;
+            const double u = fabs(t[i] - t[j]);
+            if (u > tmax) continue;
+            int a = 0;
+            while (d2 > s2[a]) ++a;
+            int b = 0;
+            while (u > tt[b]) ++b;
+            double w = 1.0;
+            if (edge_mode == 1) {
+                const double om = oracle_polygon_weight(x[i], y[i], sqrt(d2), vx, vy, nv);
+                const double v = oracle_temporal_weight(t[i], u, box[4], box[5]);
+                w = 1.0 / (om * v);
+            }
+            const int k = a * ct + b;
+            cnt[k] += 1;
+            const double yk = w - comp[k];
+            const double tk = wsum[k] + yk;
+            comp[k] = (tk - wsum[k]) - yk;
+            wsum[k] = tk;
+            ++total;
+        }
+    }
+    free(s2);
+    free(comp);
+    return total;
+}
+
+/* CSR in a polygon (Section 3, Monte Carlo method): point i of realization
+ * `sim` takes the first of the attempts k = 0, 1, ... whose position lies in
+ * the polygon, attempt k drawing x from words 0-1 and y from words 2-3 of
+ * Philox block (i, sim, 32 + k, i >> 32) uniformly in the bounding rectangle
+ * box[0..3]; t as for the box (stream 2).  Returns 0, or -1 when some point
+ * found no position in max_attempts attempts. */
+int oracle_csr_polygon_points(int64_t n, const double box[6], const double* vx,
+                              const double* vy, int nv, uint64_t seed, uint32_t sim,
+                              int max_attempts, double* x, double* y, double* t) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) {
+        int found = 0;
+        for (int k = 0; k < max_attempts && !found; ++k) {
+            const uint32_t ctr[4] = {(uint32_t)i, sim, 32u + (uint32_t)k,
+                                     (uint32_t)((uint64_t)i >> 32)};
+            uint32_t w[4];
+            oracle_philox4x32_10(ctr, key, w);
+            double px = box[0] + (box[1] - box[0]) * oracle_u01(w[0], w[1]);
+            double py = box[2] + (box[3] - box[2]) * oracle_u01(w[2], w[3]);
+            if (px > box[1]) px = box[1];
+            if (py > box[3]) py = box[3];
+            if (oracle_point_in_polygon(px, py, vx, vy, nv)) {
+                x[i] = px;
+                y[i] = py;
+                found = 1;
+            }
+        }
+        if (!found) return -1;
+        t[i] = csr_coord(seed, sim, i, 2u, box[4], box[5]);
+    }
+    return 0;
+}
+

@@ -47,6 +47,24 @@ double oracle_u01(uint32_t w0, uint32_t w1);
 void oracle_csr_points(int64_t n, const double box[6], uint64_t seed, uint32_t sim,
                        double* x, double* y, double* t);
 
+/* Finalize with an explicit study-area measure A and period length D. */
+void oracle_finalize_area(int64_t n, double area, double dur, const double* s, int cs,
+                          const double* tt, int ct, int norm, const int64_t* cnt,
+                          const double* wsum, int64_t* C, double* S, double* K, double* L);
+
+/* Polygon study areas (simple polygon, either orientation, closed). */
+double oracle_polygon_area(const double* vx, const double* vy, int nv);
+int oracle_point_in_polygon(double px, double py, const double* vx, const double* vy, int nv);
+double oracle_polygon_weight(double xi, double yi, double r, const double* vx, const double* vy,
+                             int nv);
+int64_t oracle_pair_hist_polygon(int64_t n, const double* x, const double* y, const double* t,
+                                 const double box[6], const double* vx, const double* vy,
+                                 int nv, const double* s, int cs, const double* tt, int ct,
+                                 int edge_mode, int64_t* cnt, double* wsum);
+int oracle_csr_polygon_points(int64_t n, const double box[6], const double* vx,
+                              const double* vy, int nv, uint64_t seed, uint32_t sim,
+                              int max_attempts, double* x, double* y, double* t);
+
 /* Bootstrapping (Section 3): source index of point i of realization `sim`
  * (uniform draw with replacement), and the whole resampled realization. */
 int64_t oracle_bootstrap_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i);

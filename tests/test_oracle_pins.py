@@ -418,3 +418,104 @@ def test_bootstrap_duplicates_are_zero_distance_pairs(orc):
     got = orc.k_function(bx, by, bt, box, s, tt)
     assert got["C"][0, 0] == int((mult * (mult - 1)).sum())
     assert got["S"][0, 0] == got["C"][0, 0]  # interior duplicates: weight exactly 1
+
+
+# ---------------------------------------------------------------- polygon study areas
+
+
+def _star(nv, r0, r1, cx, cy, seed):
+    rng = np.random.default_rng(seed)
+    th = np.sort(rng.uniform(0, 2 * np.pi, nv))
+    rad = np.where(np.arange(nv) % 2 == 0, r0, r1) * rng.uniform(0.85, 1.0, nv)
+    return cx + rad * np.cos(th), cy + rad * np.sin(th)
+
+
+def test_polygon_area_and_orientation(orc):
+    tri = ([0.0, 4.0, 0.0], [0.0, 0.0, 3.0])
+    assert orc.polygon_area(*tri) == 6.0
+    ell = ([0, 4, 4, 1, 1, 0], [0, 0, 1, 1, 3, 3])  # L shape: 4x1 + 1x2
+    assert orc.polygon_area(*ell) == 6.0
+    assert orc.polygon_area(ell[0][::-1], ell[1][::-1]) == 6.0
+
+
+def test_point_in_polygon_closed(orc):
+    ell = ([0, 4, 4, 1, 1, 0], [0, 0, 1, 1, 3, 3])
+    assert orc.point_in_polygon(0.5, 2.5, *ell)
+    assert not orc.point_in_polygon(2.0, 2.0, *ell)      # in the notch
+    assert orc.point_in_polygon(4.0, 0.5, *ell)          # on an edge
+    assert orc.point_in_polygon(1.0, 1.0, *ell)          # the reflex vertex
+    assert orc.point_in_polygon(0.0, 3.0, *ell)          # a convex vertex
+    assert not orc.point_in_polygon(4.0 + 1e-12, 0.5, *ell)
+
+
+def test_rectangle_polygon_equals_box_weight(orc):
+    # two independent constructions: arc union over the four edge half-planes (box) and
+    # crossing angles with midpoint tests (polygon)
+    rng = np.random.default_rng(2)
+    box = (-3.0, 7.0, 1.0, 6.0, 0.0, 1.0)
+    vx, vy = [-3.0, 7.0, 7.0, -3.0], [1.0, 1.0, 6.0, 6.0]
+    for _ in range(400):
+        x, y = rng.uniform(-3, 7), rng.uniform(1, 6)
+        r = rng.uniform(0, 2.5)
+        assert abs(orc.polygon_weight(x, y, r, vx, vy) - orc.spatial_weight(x, y, r, box)) < 1e-12
+
+
+def test_polygon_weight_closed_forms(orc):
+    sq = ([0.0, 2.0, 2.0, 0.0], [0.0, 0.0, 2.0, 2.0])
+    assert orc.polygon_weight(1.0, 1.0, 0.9, *sq) == 1.0   # clear of the edges
+    assert abs(orc.polygon_weight(0.0, 0.0, 1.0, *sq) - 0.25) < 1e-15  # at a corner
+    assert abs(orc.polygon_weight(1.0, 0.0, 0.5, *sq) - 0.5) < 1e-15   # on an edge
+    # at the reflex vertex of an L: three quarters of a small circle are inside
+    ell = ([0, 4, 4, 1, 1, 0], [0, 0, 1, 1, 3, 3])
+    assert abs(orc.polygon_weight(1.0, 1.0, 0.5, *ell) - 0.75) < 1e-15
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_polygon_weight_matches_angular_sampling(orc, seed):
+    vx, vy = _star(24, 100.0, 55.0, 0.0, 0.0, seed)
+    rng = np.random.default_rng(seed + 10)
+    th = (np.arange(200000) + 0.5) * (2 * np.pi / 200000)
+    for _ in range(4):
+        while True:
+            x, y = rng.uniform(-80, 80), rng.uniform(-80, 80)
+            if orc.point_in_polygon(x, y, vx, vy):
+                break
+        r = rng.uniform(5, 60)
+        # fraction of 200,000 evenly spaced points of the circle inside the polygon,
+        # by a vectorised crossing-number test
+        px, py = x + r * np.cos(th), y + r * np.sin(th)
+        inside = np.zeros(px.shape, bool)
+        for k in range(len(vx)):
+            ax, ay, bx, by = vx[k], vy[k], vx[(k + 1) % len(vx)], vy[(k + 1) % len(vx)]
+            straddle = (ay > py) != (by > py)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                xc = ax + (py - ay) * (bx - ax) / (by - ay)
+            inside ^= straddle & (px < xc)
+        assert abs(orc.polygon_weight(x, y, r, vx, vy) - inside.mean()) < 5e-5
+
+
+def test_rectangle_polygon_gives_the_box_estimator(orc):
+    rng = np.random.default_rng(5)
+    box = (0.0, 300.0, 0.0, 200.0, 0.0, 30.0)
+    x, y, t = rng.uniform(0, 300, 400), rng.uniform(0, 200, 400), rng.uniform(0, 30, 400)
+    s, tt = np.array([10.0, 40.0, 90.0]), np.array([2.0, 7.0])
+    a = orc.k_function(x, y, t, box, s, tt)
+    b = orc.k_function_polygon(x, y, t, box, [0, 300, 300, 0], [0, 0, 200, 200], s, tt)
+    np.testing.assert_array_equal(a["C"], b["C"])
+    np.testing.assert_allclose(b["K"], a["K"], rtol=1e-12)
+
+
+def test_csr_in_polygon_inside_and_uniform(orc):
+    ell = ([0, 4, 4, 1, 1, 0], [0, 0, 1, 1, 3, 3])
+    box = (0.0, 4.0, 0.0, 3.0, 10.0, 20.0)
+    n = 60000
+    x, y, t = orc.csr_polygon_points(n, box, *ell, 9, 2)
+    assert all(orc.point_in_polygon(a, b, *ell) for a, b in zip(x[:2000], y[:2000]))
+    assert ((x <= 1) | (y <= 1)).all()
+    # the leg x <= 1, y > 1 holds 2 of the 6 area units
+    frac = np.mean((x <= 1) & (y > 1))
+    assert abs(frac - 2 / 6) < 6 * np.sqrt((1 / 3) * (2 / 3) / n)
+    assert t.min() >= 10.0 and t.max() <= 20.0
+    x2, y2, t2 = orc.csr_polygon_points(n, box, *ell, 9, 2)
+    np.testing.assert_array_equal(x, x2)
+
