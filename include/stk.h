@@ -93,6 +93,18 @@ int stk_create(const double* x, const double* y, const double* t, int64_t n, con
 int stk_create_device(const double* d_x, const double* d_y, const double* d_t, int64_t n,
                       const stk_box* box, void* stream, stk_handle** out);
 
+/* Polygon study area (the paper's experiments use an 85-vertex outline, Sections 3 and 6):
+ * subsequent jobs on h take the closed simple polygon of nv vertices (vx[k], vy[k]), either
+ * orientation, as the study region: A in Eq. 2 is its area, the spatial weight is the
+ * proportion of the circle's circumference inside it (computed in FP64 whenever the circle
+ * reaches the boundary), and CSR simulations are uniform in it (each point the first of its
+ * draws in the bounding box, Philox streams 32, 33, ..., that falls inside).  The period stays
+ * the box's.  Requires 3 <= nv <= 128, every vertex inside the handle's box, an area of at
+ * least 1/64 of the box's, and every point of the handle inside the polygon (else
+ * STK_EDOMAIN, the study area unchanged).  nv = 0 restores the box.  Errors: STK_EINVAL,
+ * STK_EDOMAIN, STK_ENOMEM, STK_ECUDA. */
+int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv);
+
 /* Run this handle's device work on `stream` (a cudaStream_t); NULL restores
  * the handle's own stream. */
 int stk_set_stream(stk_handle* h, void* stream);
@@ -176,6 +188,13 @@ int stk_last_stats(const stk_handle* h, stk_stats* out);
  * Exposes step "CSR simulation generation" for checking. */
 int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, double* x,
                    double* y, double* t);
+
+/* One CSR realization in the polygon (vx, vy, nv) (as in jobs after stk_set_polygon), with
+ * the period of `box`, whose x/y range is the rectangle the draws are taken in; copied to
+ * caller-owned host arrays x, y, t [n].  Errors: STK_EINVAL. */
+int stk_sim_points_polygon(const stk_box* box, const double* vx, const double* vy, int nv,
+                           int64_t n, uint64_t seed, uint32_t sim, double* x, double* y,
+                           double* t);
 
 /* One random-permutation or bootstrap realization (method STK_SIM_PERMUTATION or
  * STK_SIM_BOOTSTRAP, Section 3) of the observed host points x0, y0, t0 [n], generated by

@@ -106,6 +106,9 @@ def load(build_if_missing: bool = False):
         "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
         "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
         "stk_sim_resample": ([_P, _P, _P, i64, i32, u64, u32, _P, _P, _P], i32),
+        "stk_sim_points_polygon": ([ctypes.POINTER(stk_box), _P, _P, i32, i64, u64, u32, _P, _P,
+                                    _P], i32),
+        "stk_set_polygon": ([_P, _P, _P, i32], i32),
         "stk_k_noalloc": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, i32, _P, i32, i32, _P,
                            _P, _P, _P, _P], i32),
         "stk_server_create": ([ctypes.POINTER(stk_server_config), PP], i32),
@@ -253,6 +256,25 @@ def stk_sim_points(box, n, seed, sim):
     x, y, t = (np.zeros(n) for _ in range(3))
     b = _box(box)
     _check(load().stk_sim_points(ctypes.byref(b), n, seed, sim, _ptr(x), _ptr(y), _ptr(t)))
+    return x, y, t
+
+
+def stk_set_polygon(h, vx=None, vy=None):
+    """Make the polygon (vx, vy) the study area of later jobs on h (None: back to the box)."""
+    if vx is None:
+        _check(load().stk_set_polygon(h, None, None, 0))
+        return
+    vx, vy = _f64(vx), _f64(vy)
+    _check(load().stk_set_polygon(h, _ptr(vx), _ptr(vy), vx.shape[0]))
+
+
+def stk_sim_points_polygon(box, vx, vy, n, seed, sim):
+    """Realization `sim` of CSR in the polygon (device generator), copied back to the host."""
+    vx, vy = _f64(vx), _f64(vy)
+    x, y, t = (np.zeros(n) for _ in range(3))
+    b = _box(box)
+    _check(load().stk_sim_points_polygon(ctypes.byref(b), _ptr(vx), _ptr(vy), vx.shape[0], n,
+                                         seed, sim, _ptr(x), _ptr(y), _ptr(t)))
     return x, y, t
 
 
@@ -426,6 +448,9 @@ class Pattern:
 
     def stats(self):
         return stk_last_stats(self.h)
+
+    def set_polygon(self, vx=None, vy=None):
+        stk_set_polygon(self.h, vx, vy)
 
     def close(self):
         if self.h:

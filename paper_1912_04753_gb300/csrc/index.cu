@@ -8,6 +8,8 @@
 
 #include <math.h>
 
+#include "poly.cuh"
+
 namespace stk {
 namespace {
 
@@ -119,12 +121,15 @@ __global__ void validate_kernel(const double* __restrict__ x, const double* __re
     if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
 }
 
+constexpr int kPolyAttempts = 4096;  // CSR draws per point in a polygon (area >= box / 64)
+
 __global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ seeds,
                                const uint32_t* __restrict__ sims, GridDev g,
                                double x1, double y1, double t1, int64_t ncells,
                                double* __restrict__ x, double* __restrict__ y,
                                double* __restrict__ t, uint32_t* __restrict__ key,
-                               uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt) {
+                               uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt,
+                               Polygon poly, unsigned long long* __restrict__ err) {
     const int64_t total = n * (int64_t)m;
     for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
          gi += (int64_t)gridDim.x * blockDim.x) {
@@ -132,8 +137,34 @@ __global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ se
         const int64_t i = gi - (int64_t)k * n;
         const uint32_t sim = sims[k];
         const uint64_t seed = seeds[k];
-        const double xi = csr_coord(seed, sim, i, 0u, g.x0, x1);
-        const double yi = csr_coord(seed, sim, i, 1u, g.y0, y1);
+        double xi, yi;
+        if (poly.nv == 0) {
+            xi = csr_coord(seed, sim, i, 0u, g.x0, x1);
+            yi = csr_coord(seed, sim, i, 1u, g.y0, y1);
+        } else {
+            // uniform in the polygon: the first attempt inside, x from words 0-1 and y from
+            // words 2-3 of Philox block (i, sim, 32 + attempt, i >> 32) in the bounding box
+            const uint2 kk2 = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+            const double sx = __dsub_rn(x1, g.x0), sy = __dsub_rn(y1, g.y0);
+            bool found = false;
+            xi = g.x0;
+            yi = g.y0;
+            for (int a = 0; a < kPolyAttempts && !found; ++a) {
+                const uint4 w = philox4x32_10(
+                    make_uint4((uint32_t)i, sim, 32u + (uint32_t)a, (uint32_t)((uint64_t)i >> 32)),
+                    kk2);
+                double px = __dadd_rn(g.x0, __dmul_rn(sx, u01(w.x, w.y)));
+                double py = __dadd_rn(g.y0, __dmul_rn(sy, u01(w.z, w.w)));
+                px = px > x1 ? x1 : px;
+                py = py > y1 ? y1 : py;
+                if (poly_contains(px, py, poly.vx, poly.vy, poly.nv)) {
+                    xi = px;
+                    yi = py;
+                    found = true;
+                }
+            }
+            if (!found && err) atomicAdd(err, 1ull);  // never expected: area >= box / 64
+        }
         const double ti = csr_coord(seed, sim, i, 2u, g.t0, t1);
         x[gi] = xi;
         y[gi] = yi;
@@ -292,6 +323,7 @@ struct ScatterGrid {
     double inv_qx, inv_qy, inv_qt;
     double qx, qy, qt;
     float tan_rel, tan_abs, fast_abs;
+    Polygon poly;
 };
 
 __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
@@ -328,11 +360,16 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         const double hy = rint(oy * g.inv_qy) * g.qy;
         const double ht = rint(ot * g.inv_qt) * g.qt;
         P[2 * pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
-        const float ex = (float)fmin(__dsub_rn(xi, g.x0), __dsub_rn(g.x1, xi));
-        const float ey = (float)fmin(__dsub_rn(yi, g.y0), __dsub_rn(g.y1, yi));
+        float ex = (float)fmin(__dsub_rn(xi, g.x0), __dsub_rn(g.x1, xi));
+        float ey = (float)fmin(__dsub_rn(yi, g.y0), __dsub_rn(g.y1, yi));
         const float te = (float)fmin(__dsub_rn(ti, g.t0), __dsub_rn(g.t1, ti));
-        // interior: r_true < e_min * (1 - tan_rel) - tan_abs, so omega = 1 exactly
-        const float em = fminf(ex, ey);
+        // interior: r_true < e_min * (1 - tan_rel) - tan_abs, so omega = 1 exactly; in a
+        // polygon e_min is the distance to its boundary (its weights are all taken in FP64)
+        float em = fminf(ex, ey);
+        if (g.poly.nv > 0) {
+            em = (float)poly_boundary_distance(xi, yi, g.poly.vx, g.poly.vy, g.poly.nv);
+            ex = ey = 3.0e38f;
+        }
         float rin = em * (1.0f - g.tan_rel) - g.tan_abs - g.fast_abs - em * 4.76837158e-7f;
         rin = fmaxf(rin, 0.0f);
         P[2 * pos + 1] = make_float4(ex, ey, te, rin * rin * 0.99999f);
@@ -422,10 +459,26 @@ cudaError_t launch_validate(const double* x, const double* y, const double* t, i
 
 cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
                            const Grid& g, double* x, double* y, double* t, uint32_t* key,
-                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st) {
+                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st, Polygon poly,
+                           unsigned long long* err) {
     gen_csr_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
         n, m, seeds, sims, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, x, y, t, key, rank,
-        cell_count);
+        cell_count, poly, err);
+    return cudaGetLastError();
+}
+
+__global__ void poly_validate_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                     int64_t n, Polygon poly, int* __restrict__ bad) {
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        local |= !poly_contains(x[i], y[i], poly.vx, poly.vy, poly.nv);
+    if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+cudaError_t launch_poly_validate(const double* x, const double* y, int64_t n, Polygon poly,
+                                 int* bad, cudaStream_t st) {
+    poly_validate_kernel<<<grid_for(n, kThreads), kThreads, 0, st>>>(x, y, n, poly, bad);
     return cudaGetLastError();
 }
 
@@ -480,8 +533,10 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const double* t, const uint32_t* key, const uint32_t* rank,
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
-                           float tan_rel, float tan_abs, float fast_abs, cudaStream_t st) {
+                           float tan_rel, float tan_abs, float fast_abs, cudaStream_t st,
+                           Polygon poly) {
     ScatterGrid s;
+    s.poly = poly;
     s.x1 = g.x1;
     s.y1 = g.y1;
     s.t1 = g.t1;

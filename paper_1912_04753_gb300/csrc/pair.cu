@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "stk_internal.h"
+#include "poly.cuh"
 
 #include <math.h>
 
@@ -37,6 +38,7 @@ constexpr int kWarps = kBlock / 32;
 __device__ __forceinline__ double omega64(const PairConsts& pc, double xi, double yi,
                                           double r) {
     if (r == 0.0) return 1.0;
+    if (pc.nv > 0) return poly_weight(xi, yi, r, pc.pvx, pc.pvy, pc.nv);
     const double ex = fmin(__dsub_rn(xi, pc.g.x0), __dsub_rn(pc.g.x1, xi));
     const double ey = fmin(__dsub_rn(yi, pc.g.y0), __dsub_rn(pc.g.y1, yi));
     const double ax = ex < r ? acos(ex / r) : 0.0;
@@ -476,6 +478,11 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             wj[r] = cj & vaj;
             di[r] = ci & !vai & !ini;  // spatial weight needed
             dj[r] = cj & !vaj & !inj;
+            if (pc.nv > 0) {  // polygon: every weight that is not 1 is taken in FP64
+                wi[r] |= di[r];
+                wj[r] |= dj[r];
+                di[r] = dj[r] = false;
+            }
             vi[r] = vhi;
             vj[r] = vhj;
         }

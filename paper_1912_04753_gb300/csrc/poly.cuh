@@ -1,0 +1,113 @@
+// Polygon study areas on the device: closed point-in-polygon, distance to the boundary and the
+// isotropic circumference weight, all in FP64 with every operation rounded separately (the
+// point-in-polygon decisions decide which CSR draws are kept, so they are reproducible).
+// A polygon is nv vertices (vx[k], vy[k]) in either orientation, simple, closed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "stk_internal.h"
+
+namespace stk {
+
+// (px, py) on the segment a-b: zero cross product and inside the segment's bounding box.
+static __device__ __forceinline__ bool poly_on_segment(double px, double py, double ax,
+                                                       double ay, double bx, double by) {
+    const double cross = __dsub_rn(__dmul_rn(__dsub_rn(bx, ax), __dsub_rn(py, ay)),
+                                   __dmul_rn(__dsub_rn(by, ay), __dsub_rn(px, ax)));
+    if (cross != 0.0) return false;
+    return px >= fmin(ax, bx) && px <= fmax(ax, bx) && py >= fmin(ay, by) && py <= fmax(ay, by);
+}
+
+// Boundary points are inside; otherwise the parity of the crossings of the ray towards +x
+// with the edges that straddle the ray's height (upper end exclusive).
+static __device__ __forceinline__ bool poly_contains(double px, double py, const double* vx,
+                                                     const double* vy, int nv) {
+    bool inside = false;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = k + 1 < nv ? k + 1 : 0;
+        const double ax = vx[k], ay = vy[k], bx = vx[k1], by = vy[k1];
+        if (poly_on_segment(px, py, ax, ay, bx, by)) return true;
+        if ((ay > py) != (by > py)) {
+            const double xc = __dadd_rn(
+                ax, __ddiv_rn(__dmul_rn(__dsub_rn(py, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
+            if (px < xc) inside = !inside;
+        }
+    }
+    return inside;
+}
+
+// Distance from (px, py) to the polygon's boundary.
+static __device__ __forceinline__ double poly_boundary_distance(double px, double py,
+                                                                const double* vx,
+                                                                const double* vy, int nv) {
+    double best = INFINITY;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = k + 1 < nv ? k + 1 : 0;
+        const double ax = vx[k], ay = vy[k];
+        const double dx = vx[k1] - ax, dy = vy[k1] - ay;
+        const double fx = px - ax, fy = py - ay;
+        const double len2 = dx * dx + dy * dy;
+        double s = len2 > 0.0 ? (fx * dx + fy * dy) / len2 : 0.0;
+        s = fmin(1.0, fmax(0.0, s));
+        const double ex = fx - s * dx, ey = fy - s * dy;
+        best = fmin(best, sqrt(ex * ex + ey * ey));
+    }
+    return best;
+}
+
+
+// Proportion of the circumference of the circle of radius r centred at (xi, yi) inside the
+// polygon: the crossings with the edges (edges whose bounding box misses the circle's are
+// skipped) split the circle into arcs that are wholly inside or outside; a midpoint test
+// decides each.
+static __device__ __noinline__ double poly_weight(double xi, double yi, double r,
+                                                  const double* vx, const double* vy, int nv) {
+    if (r <= 0.0) return 1.0;
+    double ang[2 * kMaxPolyVertices];
+    int na = 0;
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = k + 1 < nv ? k + 1 : 0;
+        const double ax = vx[k], ay = vy[k], bx = vx[k1], by = vy[k1];
+        if (fmin(ax, bx) > xi + r || fmax(ax, bx) < xi - r || fmin(ay, by) > yi + r ||
+            fmax(ay, by) < yi - r)
+            continue;
+        const double dx = bx - ax, dy = by - ay;
+        const double fx = ax - xi, fy = ay - yi;
+        const double A = dx * dx + dy * dy;
+        if (A == 0.0) continue;
+        const double B = 2.0 * (fx * dx + fy * dy);
+        const double C = fx * fx + fy * fy - r * r;
+        const double disc = B * B - 4.0 * A * C;
+        if (disc < 0.0) continue;
+        const double sq = sqrt(disc);
+        const double r0 = (-B - sq) / (2.0 * A), r1 = (-B + sq) / (2.0 * A);
+        if (r0 >= 0.0 && r0 <= 1.0 && na < 2 * kMaxPolyVertices)
+            ang[na++] = atan2(fy + r0 * dy, fx + r0 * dx);
+        if (r1 >= 0.0 && r1 <= 1.0 && na < 2 * kMaxPolyVertices)
+            ang[na++] = atan2(fy + r1 * dy, fx + r1 * dx);
+    }
+    if (na == 0) return poly_contains(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
+    for (int a = 1; a < na; ++a) {  // insertion sort: a handful of crossings in practice
+        const double v = ang[a];
+        int b = a - 1;
+        while (b >= 0 && ang[b] > v) {
+            ang[b + 1] = ang[b];
+            --b;
+        }
+        ang[b + 1] = v;
+    }
+    const double two_pi = 6.283185307179586;
+    double inside = 0.0;
+    for (int k = 0; k < na; ++k) {
+        const double a0 = ang[k];
+        const double a1 = k + 1 < na ? ang[k + 1] : ang[0] + two_pi;
+        if (!(a1 > a0)) continue;
+        const double mid = 0.5 * (a0 + a1);
+        if (poly_contains(xi + r * cos(mid), yi + r * sin(mid), vx, vy, nv)) inside += a1 - a0;
+    }
+    return inside / two_pi;
+}
+
+}  // namespace stk

@@ -108,6 +108,10 @@ struct stk_handle {
     int reps32 = 1, reps64 = 1;
     int configured_nbins = -1;
     size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
+    // polygon study area (nv = 0: the box), vertices in device memory, and the area A of Eq. 2
+    DevBuf poly;
+    int nv = 0;
+    double area = 0.0;
 };
 
 namespace {
@@ -142,6 +146,7 @@ int init_handle(stk_handle* h, int64_t n, const stk_box* box) {
     h->box[3] = box->y1;
     h->box[4] = box->t0;
     h->box[5] = box->t1;
+    h->area = (box->x1 - box->x0) * (box->y1 - box->y0);
     CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking), "stream create");
     h->stream = h->own_stream;
     CK(cudaEventCreate(&h->ev0), "event create");
@@ -349,6 +354,20 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     cudaStream_t st = h->stream;
     CK(cudaStreamSynchronize(st), "stream sync");  // the pinned constants are reused below
     build_pair_consts(g, n, q->s, cs, q->tt, ct, q->edge_mode, h->h_pc);
+    Polygon poly;
+    if (h->nv > 0) {
+        poly.vx = as<double>(h->poly);
+        poly.vy = as<double>(h->poly) + h->nv;
+        poly.nv = h->nv;
+        h->h_pc->nv = h->nv;
+        h->h_pc->pvx = poly.vx;
+        h->h_pc->pvy = poly.vy;
+        // the deep-unit shortcut is derived for the rectangle: none in a polygon
+        for (int a = 0; a < 2; ++a) {
+            h->h_pc->deep_x[a] = 1 - a;
+            h->h_pc->deep_y[a] = 1 - a;
+        }
+    }
     rc = configure_kernels(h, nbins);
     if (rc) return rc;
 
@@ -445,7 +464,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     }
     CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
 
-    const double area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
+    const double area = h->area;
     const double dur = h->box[5] - h->box[4];
     const double nn = (double)n;
     const double coef = area * dur / (q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0));
@@ -497,7 +516,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                 CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
                                   as<double>(h->ux) + off, as<double>(h->uy) + off,
                                   as<double>(h->ut) + off, as<uint32_t>(h->key) + off,
-                                  as<uint32_t>(h->rank) + off, cnt0, st),
+                                  as<uint32_t>(h->rank) + off, cnt0, st, poly,
+                                  as<unsigned long long>(h->stats) + 2),
                    "CSR generation");
             else
                 CK(launch_gen_resample(q->sim_method, n, ms, as<uint64_t>(h->simseed),
@@ -516,7 +536,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                           (obs_here && use_mask) ? as<uint8_t>(h->mask_in) : nullptr,
                           as<double>(h->X), as<double>(h->Y), as<double>(h->T),
                           as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
-                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st),
+                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st, poly),
            "scatter");
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
@@ -935,6 +955,69 @@ int stk_envelope(stk_handle* h, const double* s, int cs, const double* tt, int c
     return STK_OK;
 }
 
+int stk_sim_points_polygon(const stk_box* box, const double* vx, const double* vy, int nv,
+                           int64_t n, uint64_t seed, uint32_t sim, double* x, double* y,
+                           double* t) {
+    if (!x || !y || !t || !vx || !vy) return fail(STK_EINVAL, "arrays must not be NULL");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n out of range");
+    if (nv < 3 || nv > kMaxPolyVertices)
+        return fail(STK_EINVAL, "a polygon needs 3..%d vertices", kMaxPolyVertices);
+    int rc = check_box(box);
+    if (rc) return rc;
+    Grid g;
+    memset(&g, 0, sizeof g);
+    g.nx = g.ny = g.nt = 1;
+    g.ncells = 1;
+    g.x0 = box->x0, g.x1 = box->x1, g.y0 = box->y0, g.y1 = box->y1, g.t0 = box->t0,
+    g.t1 = box->t1;
+    g.cw = box->x1 - box->x0, g.ch = box->y1 - box->y0, g.cd = box->t1 - box->t0;
+    DevBuf bx, by, bt, bk, br, bc, bs, bp, be;
+    DevBuf* all[] = {&bx, &by, &bt, &bk, &br, &bc, &bs, &bp, &be};
+    auto release = [&]() {
+        for (DevBuf* b : all) free_buf(*b);
+    };
+    const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+    if ((rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
+        (rc = ensure(bk, b4, "keys")) || (rc = ensure(br, b4, "ranks")) ||
+        (rc = ensure(bc, 16, "counts")) || (rc = ensure(bs, 16, "seed")) ||
+        (rc = ensure(bp, 16 * (size_t)nv, "polygon")) || (rc = ensure(be, 16, "status"))) {
+        release();
+        return rc;
+    }
+    struct {
+        uint64_t seed;
+        uint32_t sim, pad;
+    } key_sim = {seed, sim, 0};
+    Polygon poly;
+    poly.vx = as<double>(bp);
+    poly.vy = as<double>(bp) + nv;
+    poly.nv = nv;
+    cudaStream_t st = nullptr;
+    unsigned long long miss = 0;
+    cudaError_t e = cudaMemcpyAsync(bp.p, vx, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(as<double>(bp) + nv, vy, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bc.p, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(be.p, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bs.p, &key_sim, sizeof key_sim, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_gen_csr(n, 1, as<uint64_t>(bs),
+                           reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(bs.p) + 8),
+                           g, as<double>(bx), as<double>(by), as<double>(bt), as<uint32_t>(bk),
+                           as<uint32_t>(br), as<uint32_t>(bc), st, poly,
+                           as<unsigned long long>(be));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, bx.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, by.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, bt.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&miss, be.p, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "CSR generation");
+    if (miss) return fail(STK_EINVAL, "%llu points found no position inside the polygon", miss);
+    return STK_OK;
+}
+
 int stk_sim_resample(const double* x0, const double* y0, const double* t0, int64_t n,
                      int method, uint64_t seed, uint32_t sim, double* x, double* y, double* t) {
     if (!x0 || !y0 || !t0 || !x || !y || !t) return fail(STK_EINVAL, "arrays must not be NULL");
@@ -1042,6 +1125,65 @@ int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, d
     return STK_OK;
 }
 
+int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
+    if (!h) return fail(STK_EINVAL, "handle is NULL");
+    if (nv == 0) {  // back to the rectangle
+        free_buf(h->poly);
+        h->nv = 0;
+        h->area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
+        return STK_OK;
+    }
+    if (!vx || !vy) return fail(STK_EINVAL, "vertex arrays must not be NULL");
+    if (nv < 3 || nv > kMaxPolyVertices)
+        return fail(STK_EINVAL, "a polygon needs 3..%d vertices", kMaxPolyVertices);
+    double area2 = 0.0;
+    for (int k = 0; k < nv; ++k) {
+        if (!(vx[k] >= h->box[0] && vx[k] <= h->box[1] && vy[k] >= h->box[2] && vy[k] <= h->box[3]))
+            return fail(STK_EINVAL, "polygon vertex %d is outside the handle's box", k);
+        const int k1 = (k + 1) % nv;
+        area2 += vx[k] * vy[k1] - vx[k1] * vy[k];
+    }
+    const double area = fabs(area2) * 0.5;
+    const double box_area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
+    if (!(area > 0.0) || area * 64.0 < box_area)
+        return fail(STK_EINVAL, "polygon area must be at least 1/64 of the box's");
+    int rc;
+    DevBuf pv;
+    if ((rc = ensure(pv, 16 * (size_t)nv, "polygon"))) return rc;
+    cudaStream_t st = h->stream;
+    int bad = 0;
+    DevBuf flag;
+    if ((rc = ensure(flag, 16, "status"))) {
+        free_buf(pv);
+        return rc;
+    }
+    Polygon poly;
+    poly.vx = as<double>(pv);
+    poly.vy = as<double>(pv) + nv;
+    poly.nv = nv;
+    cudaError_t e = cudaMemcpyAsync(pv.p, vx, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(as<double>(pv) + nv, vy, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 4, st);
+    if (e == cudaSuccess) e = launch_poly_validate(h->d_x, h->d_y, h->n, poly, as<int>(flag), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag.p, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_buf(flag);
+    if (e != cudaSuccess) {
+        free_buf(pv);
+        return cuda_fail(e, "polygon upload");
+    }
+    if (bad) {
+        free_buf(pv);
+        return fail(STK_EDOMAIN, "a point lies outside the polygon");
+    }
+    free_buf(h->poly);
+    h->poly = pv;
+    h->nv = nv;
+    h->area = area;
+    return STK_OK;
+}
+
 int stk_last_stats(const stk_handle* h, stk_stats* out) {
     if (!h || !out) return fail(STK_EINVAL, "handle and out must not be NULL");
     *out = h->last;
@@ -1051,6 +1193,7 @@ int stk_last_stats(const stk_handle* h, stk_stats* out) {
 void stk_destroy(stk_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    free_buf(h->poly);
     DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank, &h->counts, &h->start,
                       &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P, &h->Plo, &h->cell_start,
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,

@@ -20,6 +20,7 @@
 namespace stk {
 
 constexpr int kMaxThr = 64;   // thresholds per axis
+constexpr int kMaxPolyVertices = 128;  // vertices of a polygon study area
 constexpr int kTab = 1024;    // bin-table entries per axis
 constexpr int kBlock = 256;   // threads per pair-kernel block
 constexpr int kUnit = 32;      // centres per work unit (one warp)
@@ -61,6 +62,10 @@ struct PairConsts {
     // cell index ranges [lo, hi] of points at least s_max from every spatial edge (x, y) and
     // t_max from both ends of the period (t): a pair of two such points has w = v = 1
     int deep_x[2], deep_y[2], deep_t[2];
+    // polygon study area (nv = 0: the rectangle); vertex arrays in device memory
+    int nv;
+    const double* pvx;
+    const double* pvy;
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
@@ -124,10 +129,22 @@ cudaError_t launch_gen_resample(int method, int64_t n, int m, const uint64_t* se
                                 const double* y0, const double* t0, double* x, double* y,
                                 double* t, uint32_t* key, uint32_t* rank, uint32_t* cell_count,
                                 unsigned long long* err, cudaStream_t st);
-// realization slot k (0..m-1) is Philox realization sims[k] under key seeds[k] (device arrays)
+// A polygon study area: nv vertices in device memory (nv = 0: the grid's rectangle).
+struct Polygon {
+    const double* vx = nullptr;
+    const double* vy = nullptr;
+    int nv = 0;
+};
+// realization slot k (0..m-1) is Philox realization sims[k] under key seeds[k] (device arrays);
+// in a polygon, point i keeps the first of its attempts (Philox streams 32, 33, ...) that lies
+// inside (err counts points that found none in the attempt limit)
 cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
                            const Grid& g, double* x, double* y, double* t, uint32_t* key,
-                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st);
+                           uint32_t* rank, uint32_t* cell_count, cudaStream_t st,
+                           Polygon poly = Polygon(), unsigned long long* err = nullptr);
+// flags (bad = 1) any of the n points outside the polygon (closed)
+cudaError_t launch_poly_validate(const double* x, const double* y, int64_t n, Polygon poly,
+                                 int* bad, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t count,
                                   uint32_t* tmp, int64_t tmp_words, cudaStream_t st);
 int64_t scan_tmp_words(int64_t count);
@@ -136,7 +153,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
-                           cudaStream_t st);
+                           cudaStream_t st, Polygon poly = Polygon());
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
 // units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)
