@@ -395,6 +395,29 @@ def run_ours(args):
                              "value": sm["qualifying_pairs"] / (ms_m / 1e3), "unit": UNIT,
                              "qualifying_pairs": sm["qualifying_pairs"]}
 
+    # a polygon study area (85-vertex outline, Thomas process, CSR simulations in it); its
+    # weights near the boundary are all FP64, so the job is kept to 9 simulations
+    polygon = None
+    if args.polygon and rank == 0:
+        wp = _workload("thomas_polygon85_n200k", sims=9)
+        with stk.Pattern(wp.x, wp.y, wp.t, wp.box) as pp:
+            pp.set_polygon(*wp.meta["polygon"])
+            stk.stk_set_stream(pp.h, stream)
+            pp.run(wp.s, wp.tt, n_sims=wp.n_sims, seed=seed, prec=prec, exec_mode=exec_mode)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pp.run(wp.s, wp.tt, n_sims=wp.n_sims, seed=seed, prec=prec, exec_mode=exec_mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_p = e0.elapsed_time(e1)
+            sp = pp.stats()
+        polygon = {"workload": wp.name, "n": wp.n, "vertices": len(wp.meta["polygon"][0]),
+                   "sims": wp.n_sims, "job_s": ms_p / 1e3,
+                   "sims_per_s": wp.n_sims / (ms_p / 1e3),
+                   "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
+                   "fp64_weights_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
+
     if rank != 0:
         stk.stk_destroy(h)
         if ws > 1:
@@ -441,6 +464,7 @@ def run_ours(args):
         "plain_fp64": plain,
         "serve": serve,
         "sim_methods": methods,
+        "polygon": polygon,
     }
     print(json.dumps(line), flush=True)
     stk.stk_destroy(h)
@@ -470,6 +494,8 @@ def build_parser():
                     help="also replay the stream through a FIFO of plain FP64 jobs")
     ap.add_argument("--methods", type=int, default=1,
                     help="also time the job with permutation and bootstrap simulations")
+    ap.add_argument("--polygon", type=int, default=1,
+                    help="also time a job over an 85-vertex polygon study area")
     return ap
 
 

@@ -35,10 +35,16 @@ constexpr int kWarps = kBlock / 32;
 // at most one x-edge and one y-edge cut the circle.  An edge at distance e < r removes an arc
 // of half-angle acos(e/r) around its normal; when the corner lies inside the circle the two
 // arcs overlap and the outside part is alpha_x + alpha_y + pi/2 (out of 2 pi).
+// POLY: the study area may be a polygon (pc.nv > 0); kernels for the rectangle are compiled
+// without the polygon code so that it costs them no registers.
+template <bool POLY>
 __device__ __forceinline__ double omega64(const PairConsts& pc, double xi, double yi,
                                           double r) {
     if (r == 0.0) return 1.0;
-    if (pc.nv > 0) return poly_weight(xi, yi, r, pc.pvx, pc.pvy, pc.nv);
+    if (POLY && pc.nv > 0) {
+        const double w = poly_weight_fast(xi, yi, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        return w >= 0.0 ? w : poly_weight(xi, yi, r, pc.pvx, pc.pvy, pc.nv);
+    }
     const double ex = fmin(__dsub_rn(xi, pc.g.x0), __dsub_rn(pc.g.x1, xi));
     const double ey = fmin(__dsub_rn(yi, pc.g.y0), __dsub_rn(pc.g.y1, yi));
     const double ax = ex < r ? acos(ex / r) : 0.0;
@@ -66,6 +72,7 @@ __device__ __forceinline__ unsigned long long excess_fixed64(double w) {
 // centre i, and (j, i), with centre j.  d2 and u are the same for both orders (the FP64
 // difference of two numbers is exactly the negation of the reversed difference).  Returns
 // false when the pair does not qualify.
+template <bool POLY>
 __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double yi, double ti,
                                         double xj, double yj, double tj, int& a, int& b,
                                         unsigned long long& exc_i, unsigned long long& exc_j) {
@@ -83,8 +90,8 @@ __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double 
     exc_j = 0;
     if (pc.edge) {
         const double r = __dsqrt_rn(d2);
-        exc_i = excess_fixed64(1.0 / (omega64(pc, xi, yi, r) * v64(pc, ti, u)));
-        exc_j = excess_fixed64(1.0 / (omega64(pc, xj, yj, r) * v64(pc, tj, u)));
+        exc_i = excess_fixed64(1.0 / (omega64<POLY>(pc, xi, yi, r) * v64(pc, ti, u)));
+        exc_j = excess_fixed64(1.0 / (omega64<POLY>(pc, xj, yj, r) * v64(pc, tj, u)));
     }
     return true;
 }
@@ -174,6 +181,7 @@ __device__ __forceinline__ int bin_even(float t, float tol, float top, int nthr,
 // {x, y}: bins, a count of (w bit 1) + (w bit 2) ordered pairs (the centre of each order may
 // be masked out) and the excess of those orders.  Weight-only entries (w bit 0 set) carry the
 // bin in w >> 2 and add the excess of the single ordered pair with centre x.
+template <bool POLY>
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
                                            int& bin, uint32_t& counts,
                                            unsigned long long& exc) {
@@ -183,7 +191,7 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
     if ((q.w & 1u) == 0u) {
         int a, b;
         unsigned long long ei, ej;
-        if (!pair_exact(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
+        if (!pair_exact<POLY>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
         const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
         bin = a * pc.ct + b;
         counts = (uint32_t)act_i + (uint32_t)act_j;
@@ -195,7 +203,7 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
         const double dy = __dsub_rn(yi, yj);
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
         const double u = fabs(__dsub_rn(ti, tj));
-        exc = excess_fixed64(1.0 / (omega64(pc, xi, yi, __dsqrt_rn(d2)) * v64(pc, ti, u)));
+        exc = excess_fixed64(1.0 / (omega64<POLY>(pc, xi, yi, __dsqrt_rn(d2)) * v64(pc, ti, u)));
     }
     return true;
 }
@@ -313,12 +321,13 @@ struct WarpCtx {
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
+template <bool POLY>
 __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, uint4 entry,
                                           uint32_t* hc, unsigned long long* he) {
     int bin;
     uint32_t counts;
     unsigned long long exc;
-    if (exact_eval(*gpc, rb, entry, bin, counts, exc)) {
+    if (exact_eval<POLY>(*gpc, rb, entry, bin, counts, exc)) {
         if (counts) atomicAdd(&hc[bin], counts);
         if (exc) atomicAdd(&he[bin], exc);
     }
@@ -326,6 +335,7 @@ __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, u
 
 // Appends the flagged lanes' entries to the global FP64 queue.  If the queue is full the entry
 // is evaluated here instead (correct, only slower).
+template <bool POLY>
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
                                            const ExactQueue& xq, bool flag, uint4 entry,
                                            int lane, uint32_t lt, uint32_t* hc,
@@ -340,7 +350,46 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
     if (idx < xq.cap)
         xq.e[idx] = entry;
     else
-        exact_inline(gpc, rb, entry, hc, he);
+        exact_inline<POLY>(gpc, rb, entry, hc, he);
+}
+
+// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
+// one per lane (crossings with the boundary, poly_weight_fast).  Out of line like the
+// rectangle's version, so that the rectangle path does not carry its registers.
+__device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const PairConsts* gpc,
+                                                WarpSm* wsp, RealBatch rb, ExactQueue xq,
+                                                int off, int cnt, int lane,
+                                                unsigned long long* he, uint32_t* hc,
+                                                uint32_t real, uint32_t c_begin) {
+    const PairConsts& pc = *pcs;
+    WarpSm& ws = *wsp;
+    bool exact = false;
+    uint4 xe = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < cnt) {
+        const uint2 e = ws.q2[off + lane];
+        const uint32_t meta = e.x, j = e.y;
+        const uint32_t ci = c_begin + (meta & 31u);
+        const bool other = (meta >> 11) & 1u;
+        const bool vhalf = (meta >> 12) & 1u;
+        const int bin = (int)(meta >> 13);
+        const uint32_t a = other ? j : ci, b = other ? ci : j;  // centre, neighbour
+        const int64_t base = (int64_t)real * rb.n;
+        const double xa = rb.X[base + a], ya = rb.Y[base + a];
+        const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
+        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        const double om = poly_weight_fast(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        const double w = om > 0.0 ? 1.0 / (om * (vhalf ? 0.5 : 1.0)) : 0.0;
+        // undecided crossings, and weights above 8 (beyond the shared accumulators' bound),
+        // go to the FP64 queue
+        if (!(om > 0.0) || w > 8.0) {
+            exact = true;
+            xe = make_uint4(a, b, real, 1u | ((uint32_t)bin << 2));
+        } else {
+            const unsigned long long exc = excess_fixed64(w);
+            if (exc) atomicAdd(&he[bin], exc);
+        }
+    }
+    push_exact<true>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
 }
 
 // Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.  Out of line (it
@@ -398,19 +447,24 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
             if (exc) atomicAdd(&he[bin], exc);
         }
     }
-    push_exact(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
+    push_exact<false>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
 }
 
 // Evaluates queue 2 in batches of 32 while it holds that many, and moves the rest (fewer than
 // 32) to its front.
+template <bool POLY>
 __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
                                               const PairConsts* gpc, const RealBatch& rb,
                                               const ExactQueue& xq, int lane, WarpCtx& w) {
     int off = 0;
     __syncwarp();
     while (w.q2n - off >= 32) {
-        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, off, 32,
-                      lane, w.he, w.hc, w.real, w.c_begin);
+        if (POLY)
+            drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
+                               w.c_begin);
+        else
+            drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, off, 32,
+                          lane, w.he, w.hc, w.real, w.c_begin);
         off += 32;
     }
     const int rest = w.q2n - off;
@@ -423,7 +477,7 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
 }
 
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
-template <bool EVEN, bool EDGE>
+template <bool EVEN, bool EDGE, bool POLY>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
@@ -478,11 +532,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             wj[r] = cj & vaj;
             di[r] = ci & !vai & !ini;  // spatial weight needed
             dj[r] = cj & !vaj & !inj;
-            if (pc.nv > 0) {  // polygon: every weight that is not 1 is taken in FP64
-                wi[r] |= di[r];
-                wj[r] |= dj[r];
-                di[r] = dj[r] = false;
-            }
+
             vi[r] = vhi;
             vj[r] = vhj;
         }
@@ -496,14 +546,14 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         for (int r = 0; r < 2; ++r) {
             const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
             if (edge) {
-                push_exact(gpc, rb, xq, wi[r],
+                push_exact<POLY>(gpc, rb, xq, wi[r],
                            make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
                            w.hc, w.he);
-                push_exact(gpc, rb, xq, wj[r],
+                push_exact<POLY>(gpc, rb, xq, wj[r],
                            make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
                            w.hc, w.he);
             }
-            push_exact(gpc, rb, xq, full[r],
+            push_exact<POLY>(gpc, rb, xq, full[r],
                        make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
                        lane, lt, w.hc, w.he);
         }
@@ -528,13 +578,13 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                 ws.q2[o3 + __popc(b3 & lt)] =
                     make_uint2(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w);
             w.q2n = o3 + __popc(b3);
-            if (w.q2n >= 32) flush_weights(ws, pc, gpc, rb, xq, lane, w);
+            if (w.q2n >= 32) flush_weights<POLY>(ws, pc, gpc, rb, xq, lane, w);
         }
     }
 }
 
 // Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
-template <bool EVEN, bool EDGE>
+template <bool EVEN, bool EDGE, bool POLY>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
                                           const ExactQueue& xq, uint32_t& tail, int lane,
@@ -542,7 +592,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     while (tail > 0) {
         const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs<EVEN, EDGE>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
+        drain_pairs<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
         for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
@@ -550,14 +600,18 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     }
     __syncwarp();
     if (w.q2n > 0) {
-        drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 0, w.q2n,
-                      lane, w.he, w.hc, w.real, w.c_begin);
+        if (POLY)
+            drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
+                               w.c_begin);
+        else
+            drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 0,
+                          w.q2n, lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
 }
 
-template <bool EVEN, bool EDGE>
+template <bool EVEN, bool EDGE, bool POLY>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
                  int m, RealBatch rb,
@@ -708,7 +762,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                             tail = t3 + (uint32_t)__popc(m3);
                             while (tail >= (uint32_t)kDrain) {
                                 __syncwarp();
-                                drain_pairs<EVEN, EDGE>(pc, gpc, ws, rb, xq, kDrain, lane, lt, w);
+                                drain_pairs<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, kDrain, lane, lt, w);
                                 __syncwarp();
                                 const uint32_t rest = tail - kDrain;
                                 uint4 v[4];
@@ -727,7 +781,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                     }
                 }
             }
-            drain_all<EVEN, EDGE>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
+            drain_all<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
                 since_flush = 0;
@@ -758,6 +812,7 @@ struct Smem64 {
 };
 
 // Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
+template <bool POLY>
 __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
                                           int lane, const double* X, const double* Y,
                                           const double* T, const uint8_t* mk, uint32_t onmask,
@@ -788,14 +843,15 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     unsigned long long exc = 0;
     if (pc.edge) {
         const double r = __dsqrt_rn(d2);
-        if (act_i) exc += excess_fixed64(1.0 / (omega64(pc, xi, yi, r) * v64(pc, ti, u)));
-        if (act_j) exc += excess_fixed64(1.0 / (omega64(pc, xj, yj, r) * v64(pc, tj, u)));
+        if (act_i) exc += excess_fixed64(1.0 / (omega64<POLY>(pc, xi, yi, r) * v64(pc, ti, u)));
+        if (act_j) exc += excess_fixed64(1.0 / (omega64<POLY>(pc, xj, yj, r) * v64(pc, tj, u)));
     }
     const int bin = a * pc.ct + b;
     atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
     if (exc) atomicAdd(&he[bin], exc);
 }
 
+template <bool POLY>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
@@ -883,7 +939,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         tail += __popc(mq);
                         if (tail >= 32u) {
                             __syncwarp();
-                            process64(pc, ws, 32, lane, X, Y, T, mk, onmask, my_hc, my_he,
+                            process64<POLY>(pc, ws, 32, lane, X, Y, T, mk, onmask, my_hc, my_he,
                                       acc.stats);
                             __syncwarp();
                             if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
@@ -895,7 +951,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             }
             __syncwarp();
             if (tail > 0)
-                process64(pc, ws, (int)tail, lane, X, Y, T, mk, onmask, my_hc, my_he, acc.stats);
+                process64<POLY>(pc, ws, (int)tail, lane, X, Y, T, mk, onmask, my_hc, my_he, acc.stats);
             __syncwarp();
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);
@@ -913,6 +969,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
 
 // Evaluates the pairs the FP32 kernel queued, 32 per warp, and adds them to the global
 // accumulators (integer atomics, so the order does not matter).
+template <bool POLY>
 __global__ void __launch_bounds__(256)
 exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQueue xq) {
     const unsigned int pushed = *xq.count;
@@ -925,7 +982,7 @@ exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQ
         int bin;
         uint32_t counts;
         unsigned long long exc;
-        if (!exact_eval(pc, rb, q, bin, counts, exc)) continue;
+        if (!exact_eval<POLY>(pc, rb, q, bin, counts, exc)) continue;
         const int64_t o = (int64_t)q.z * pc.nbins + bin;
         if (counts) atomicAdd(&acc.cnt[o], (unsigned long long)counts);
         if (exc & 0xffffffffull) atomicAdd(&acc.exc_lo[o], exc & 0xffffffffull);
@@ -1037,22 +1094,27 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));
     if (e != cudaSuccess) return e;
-    const void* k32[4] = {(const void*)pair_fp32_kernel<false, false>,
-                          (const void*)pair_fp32_kernel<false, true>,
-                          (const void*)pair_fp32_kernel<true, false>,
-                          (const void*)pair_fp32_kernel<true, true>};
+    const void* k32[6] = {(const void*)pair_fp32_kernel<false, false, false>,
+                          (const void*)pair_fp32_kernel<false, true, false>,
+                          (const void*)pair_fp32_kernel<true, false, false>,
+                          (const void*)pair_fp32_kernel<true, true, false>,
+                          (const void*)pair_fp32_kernel<false, true, true>,
+                          (const void*)pair_fp32_kernel<true, true, true>};
     for (const void* f : k32) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem64);
+    e = cudaFuncSetAttribute(pair_fp64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem64);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pair_fp64_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
 }
 
 int pair_fp32_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true>, kBlock,
-                                                      smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false>,
+                                                      kBlock, smem) !=
         cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
@@ -1060,7 +1122,8 @@ int pair_fp32_blocks_per_sm(size_t smem) {
 
 int pair_fp64_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel, kBlock, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false>, kBlock,
+                                                      smem) !=
         cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
@@ -1071,32 +1134,44 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st) {
-    if (even && edge)
-        pair_fp32_kernel<true, true><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
-                                                                 counters, acc, xq, reps);
+    const bool poly = edge && hpc.nv > 0;
+#define STK_PAIR32(E, D, P)                                                                  \
+    pair_fp32_kernel<E, D, P><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off, \
+                                                          counters, acc, xq, reps)
+    if (poly && even)
+        STK_PAIR32(true, true, true);
+    else if (poly)
+        STK_PAIR32(false, true, true);
+    else if (even && edge)
+        STK_PAIR32(true, true, false);
     else if (even)
-        pair_fp32_kernel<true, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
-                                                                  counters, acc, xq, reps);
+        STK_PAIR32(true, false, false);
     else if (edge)
-        pair_fp32_kernel<false, true><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
-                                                                  counters, acc, xq, reps);
+        STK_PAIR32(false, true, false);
     else
-        pair_fp32_kernel<false, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off,
-                                                                   counters, acc, xq, reps);
+        STK_PAIR32(false, false, false);
+#undef STK_PAIR32
     return cudaGetLastError();
 }
 
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
-                         ExactQueue xq, cudaStream_t st) {
-    exact_kernel<<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+                         ExactQueue xq, cudaStream_t st, bool poly) {
+    if (poly)
+        exact_kernel<true><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+    else
+        exact_kernel<false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, cudaStream_t st) {
-    pair_fp64_kernel<<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters, acc,
-                                                 reps);
+                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly) {
+    if (poly)
+        pair_fp64_kernel<true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters,
+                                                           acc, reps);
+    else
+        pair_fp64_kernel<false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                            counters, acc, reps);
     return cudaGetLastError();
 }
 

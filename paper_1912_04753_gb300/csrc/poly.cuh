@@ -62,10 +62,12 @@ static __device__ __forceinline__ double poly_boundary_distance(double px, doubl
 // polygon: the crossings with the edges (edges whose bounding box misses the circle's are
 // skipped) split the circle into arcs that are wholly inside or outside; a midpoint test
 // decides each.
+constexpr int kMaxCross = 32;  // crossings of one circle with the boundary
+
 static __device__ __noinline__ double poly_weight(double xi, double yi, double r,
                                                   const double* vx, const double* vy, int nv) {
     if (r <= 0.0) return 1.0;
-    double ang[2 * kMaxPolyVertices];
+    double ang[kMaxCross];
     int na = 0;
     for (int k = 0; k < nv; ++k) {
         const int k1 = k + 1 < nv ? k + 1 : 0;
@@ -83,10 +85,12 @@ static __device__ __noinline__ double poly_weight(double xi, double yi, double r
         if (disc < 0.0) continue;
         const double sq = sqrt(disc);
         const double r0 = (-B - sq) / (2.0 * A), r1 = (-B + sq) / (2.0 * A);
-        if (r0 >= 0.0 && r0 <= 1.0 && na < 2 * kMaxPolyVertices)
-            ang[na++] = atan2(fy + r0 * dy, fx + r0 * dx);
-        if (r1 >= 0.0 && r1 <= 1.0 && na < 2 * kMaxPolyVertices)
-            ang[na++] = atan2(fy + r1 * dy, fx + r1 * dx);
+        for (int q = 0; q < 2; ++q) {
+            const double sr = q ? r1 : r0;
+            if (sr < 0.0 || sr > 1.0) continue;
+            if (na == kMaxCross) return -2.0;  // more crossings than supported
+            ang[na++] = atan2(fy + sr * dy, fx + sr * dx);
+        }
     }
     if (na == 0) return poly_contains(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
     for (int a = 1; a < na; ++a) {  // insertion sort: a handful of crossings in practice
@@ -106,6 +110,75 @@ static __device__ __noinline__ double poly_weight(double xi, double yi, double r
         if (!(a1 > a0)) continue;
         const double mid = 0.5 * (a0 + a1);
         if (poly_contains(xi + r * cos(mid), yi + r * sin(mid), vx, vy, nv)) inside += a1 - a0;
+    }
+    return inside / two_pi;
+}
+
+// The same weight from the crossings' directions (no point-in-polygon test per arc): along a
+// crossed edge a -> b the segment enters the disc at the smaller root of
+// |a + s (b - a) - c|^2 = r^2 and leaves it at the larger, and at the larger root the circle,
+// run counter-clockwise, passes to the left of the edge, i.e. into the polygon when its
+// vertices run counter-clockwise (ccw = 1; the other way round for ccw = 0).  Crossings are
+// taken for 0 <= s < 1 (a vertex belongs to the edge it starts).  Inside arcs run from an
+// entering crossing to the next.  ebox[k] is edge k's bounding box in FP32 rounded outwards
+// (x_min, x_max, y_min, y_max), for culling.  Returns -1 when a crossing is too close to a
+// tangency to call or the crossings do not alternate (a vertex on the circle): the caller
+// then uses poly_weight.
+static __device__ __noinline__ double poly_weight_fast(double xi, double yi, double r,
+                                                       const double* vx, const double* vy,
+                                                       const float4* ebox, int nv, int ccw) {
+    if (r <= 0.0) return 1.0;
+    double ang[kMaxCross];
+    bool enter[kMaxCross];
+    int na = 0;
+    const float m = (float)(r * 1e-4) + 1e-6f * (fabsf((float)xi) + fabsf((float)yi)) + 1e-30f;
+    const float x0 = (float)(xi - r) - m, x1 = (float)(xi + r) + m;
+    const float y0 = (float)(yi - r) - m, y1 = (float)(yi + r) + m;
+    const double r2 = r * r;
+    for (int k = 0; k < nv; ++k) {
+        const float4 eb = ebox[k];
+        if (eb.x > x1 || eb.y < x0 || eb.z > y1 || eb.w < y0) continue;
+        const int k1 = k + 1 < nv ? k + 1 : 0;
+        const double ax = vx[k], ay = vy[k];
+        const double dx = vx[k1] - ax, dy = vy[k1] - ay;
+        const double fx = ax - xi, fy = ay - yi;
+        const double A = dx * dx + dy * dy;
+        if (A == 0.0) continue;
+        const double hb = fx * dx + fy * dy;  // B / 2
+        const double C = fx * fx + fy * fy - r2;
+        const double disc = hb * hb - A * C;   // (B^2 - 4AC) / 4
+        if (disc <= 0.0) continue;             // no crossing, or a touching
+        const double sq = sqrt(disc);
+        if (sq <= 1e-9 * A * r) return -1.0;   // nearly tangent: direction too close to call
+        const double s0 = (-hb - sq) / A, s1 = (-hb + sq) / A;
+        for (int q = 0; q < 2; ++q) {
+            const double sr = q ? s1 : s0;
+            if (sr < 0.0 || sr >= 1.0) continue;
+            if (na == kMaxCross) return -2.0;  // more crossings than supported
+            ang[na] = atan2(fy + sr * dy, fx + sr * dx);
+            enter[na++] = (q == 1) == (ccw != 0);
+        }
+    }
+    if (na == 0) return poly_contains(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
+    for (int a = 1; a < na; ++a) {
+        const double v = ang[a];
+        const bool e = enter[a];
+        int b = a - 1;
+        while (b >= 0 && ang[b] > v) {
+            ang[b + 1] = ang[b];
+            enter[b + 1] = enter[b];
+            --b;
+        }
+        ang[b + 1] = v;
+        enter[b + 1] = e;
+    }
+    if (na & 1) return -1.0;
+    const double two_pi = 6.283185307179586;
+    double inside = 0.0;
+    for (int k = 0; k < na; ++k) {
+        const bool next = enter[k + 1 < na ? k + 1 : 0];
+        if (enter[k] == next) return -1.0;  // crossings must alternate
+        if (enter[k]) inside += (k + 1 < na ? ang[k + 1] : ang[0] + two_pi) - ang[k];
     }
     return inside / two_pi;
 }

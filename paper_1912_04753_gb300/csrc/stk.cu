@@ -109,8 +109,9 @@ struct stk_handle {
     int configured_nbins = -1;
     size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
     // polygon study area (nv = 0: the box), vertices in device memory, and the area A of Eq. 2
-    DevBuf poly;
+    DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4)
     int nv = 0;
+    int poly_ccw = 1;
     double area = 0.0;
 };
 
@@ -360,8 +361,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         poly.vy = as<double>(h->poly) + h->nv;
         poly.nv = h->nv;
         h->h_pc->nv = h->nv;
+        h->h_pc->pccw = h->poly_ccw;
         h->h_pc->pvx = poly.vx;
         h->h_pc->pvy = poly.vy;
+        h->h_pc->pebox = reinterpret_cast<const float4*>(as<double>(h->poly) + 2 * h->nv);
         // the deep-unit shortcut is derived for the rectangle: none in a polygon
         for (int a = 0; a < 2; ++a) {
             h->h_pc->deep_x[a] = 1 - a;
@@ -586,11 +589,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, st),
+                                as<uint32_t>(h->counter), acc, st, h->nv > 0),
                "pair kernel (FP64)");
         if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
         if (fp32) {
-            CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st), "FP64 queue");
+            CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st, h->nv > 0),
+               "FP64 queue");
         }
         const int64_t row = (int64_t)r0 * nbins;
         CK(launch_finalize(m, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
@@ -1147,9 +1151,23 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     const double box_area = (h->box[1] - h->box[0]) * (h->box[3] - h->box[2]);
     if (!(area > 0.0) || area * 64.0 < box_area)
         return fail(STK_EINVAL, "polygon area must be at least 1/64 of the box's");
+    // edge bounding boxes in FP32 rounded outwards, for culling
+    std::vector<float> ebox(4 * (size_t)nv);
+    for (int k = 0; k < nv; ++k) {
+        const int k1 = (k + 1) % nv;
+        const double lo[2] = {fmin(vx[k], vx[k1]), fmin(vy[k], vy[k1])};
+        const double hi[2] = {fmax(vx[k], vx[k1]), fmax(vy[k], vy[k1])};
+        for (int c = 0; c < 2; ++c) {
+            float l = (float)lo[c], u = (float)hi[c];
+            if ((double)l > lo[c]) l = nextafterf(l, -INFINITY);
+            if ((double)u < hi[c]) u = nextafterf(u, INFINITY);
+            ebox[4 * (size_t)k + 2 * c] = l;
+            ebox[4 * (size_t)k + 2 * c + 1] = u;
+        }
+    }
     int rc;
     DevBuf pv;
-    if ((rc = ensure(pv, 16 * (size_t)nv, "polygon"))) return rc;
+    if ((rc = ensure(pv, 32 * (size_t)nv, "polygon"))) return rc;
     cudaStream_t st = h->stream;
     int bad = 0;
     DevBuf flag;
@@ -1164,7 +1182,11 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     cudaError_t e = cudaMemcpyAsync(pv.p, vx, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(as<double>(pv) + nv, vy, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(as<double>(pv) + 2 * nv, ebox.data(), 16 * (size_t)nv,
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ebox (pageable) is read
     if (e == cudaSuccess) e = launch_poly_validate(h->d_x, h->d_y, h->n, poly, as<int>(flag), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag.p, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1180,6 +1202,7 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     free_buf(h->poly);
     h->poly = pv;
     h->nv = nv;
+    h->poly_ccw = area2 > 0.0 ? 1 : 0;
     h->area = area;
     return STK_OK;
 }

@@ -64,8 +64,10 @@ struct PairConsts {
     int deep_x[2], deep_y[2], deep_t[2];
     // polygon study area (nv = 0: the rectangle); vertex arrays in device memory
     int nv;
+    int pccw;                 // 1: vertices run counter-clockwise
     const double* pvx;
     const double* pvy;
+    const float4* pebox;      // per-edge bounding boxes, FP32 rounded outwards
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
@@ -169,10 +171,10 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st);
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
-                         ExactQueue xq, cudaStream_t st);
+                         ExactQueue xq, cudaStream_t st, bool poly = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, cudaStream_t st);
+                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false);
 size_t pair_fp32_smem(int nbins, int* replicas);
 size_t pair_fp64_smem(int nbins, int* replicas);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);

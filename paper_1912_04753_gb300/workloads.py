@@ -212,9 +212,53 @@ def serving_stream(count: int, seed: int = 0, n_datasets: int = 12, presets: int
     return datasets, requests
 
 
+def star_polygon(nv: int, r_out: float, r_in: float, cx: float, cy: float, seed: int):
+    """A simple star-shaped polygon of nv vertices (alternating outer / inner radius with
+    jitter, sorted angles): a stand-in for an irregular administrative outline."""
+    rng = np.random.default_rng(seed)
+    th = np.sort(rng.uniform(0.0, 2.0 * np.pi, nv))
+    rad = np.where(np.arange(nv) % 2 == 0, r_out, r_in) * rng.uniform(0.85, 1.0, nv)
+    return cx + rad * np.cos(th), cy + rad * np.sin(th)
+
+
+def inside_polygon(px, py, vx, vy):
+    """Vectorised even-odd test (input generation only; boundary cases are immaterial)."""
+    inside = np.zeros(np.shape(px), bool)
+    n = len(vx)
+    for k in range(n):
+        ax, ay, bx, by = vx[k], vy[k], vx[(k + 1) % n], vy[(k + 1) % n]
+        straddle = (ay > py) != (by > py)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xc = ax + (py - ay) * (bx - ax) / (by - ay)
+        inside ^= straddle & (px < xc)
+    return inside
+
+
+def config_polygon(seed: int = 0, n: int = 200_000) -> Workload:
+    """The Thomas configuration (10 km x 10 km x 730 d, sigma 150 m / 10 d) inside an
+    85-vertex star polygon (the paper's experiments use an 85-vertex outline): n points drawn
+    from the Thomas process and kept when inside; 20 x 20 thresholds to 1 km / 60 d; 99 CSR
+    simulations in the polygon.  meta["polygon"] holds (vx, vy)."""
+    rng = np.random.default_rng(seed)
+    box = (0.0, 10_000.0, 0.0, 10_000.0, 0.0, 730.0)
+    vx, vy = star_polygon(85, 5000.0, 3400.0, 5000.0, 5000.0, seed + 1)
+    xs, ys, ts = [], [], []
+    have = 0
+    while have < n:
+        x, y, t = thomas(n, box, 400, 150.0, 10.0, rng)
+        keep = inside_polygon(x, y, vx, vy)
+        xs.append(x[keep]), ys.append(y[keep]), ts.append(t[keep])
+        have += int(keep.sum())
+    x, y, t = (np.concatenate(a)[:n] for a in (xs, ys, ts))
+    return Workload("thomas_polygon85_n200k", x, y, t, box, even_thresholds(1000.0, 20),
+                    even_thresholds(60.0, 20), 99, seed,
+                    {"time_unit": "day", "polygon": (vx, vy)})
+
+
 CONFIGS = {
     "csr_n2000": config_csr_small,
     "thomas_n200k": config_thomas,
     "poi_n2M": config_poi,
     "poi_n10M": config_large,
+    "thomas_polygon85_n200k": config_polygon,
 }
