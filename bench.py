@@ -416,7 +416,7 @@ def run_ours(args):
                    "sims": wp.n_sims, "job_s": ms_p / 1e3,
                    "sims_per_s": wp.n_sims / (ms_p / 1e3),
                    "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
-                   "fp64_weights_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
+                   "fp64_queue_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
 
     if rank != 0:
         stk.stk_destroy(h)

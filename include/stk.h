@@ -145,6 +145,10 @@ typedef struct {
                                    contribute to the OBSERVED grids (sampled-centre
                                    checking mode); NULL = all */
     int sim_method;      /* STK_SIM_*; the envelope is over realizations of this method */
+    uint32_t first_sim;  /* simulations are realizations first_sim .. first_sim+n_sims-1 of
+                            the counter-based generator, so a long envelope job can run (or
+                            resume after an interruption) in chunks: the union of the chunks'
+                            realizations equals the whole job's, bit for bit */
 } stk_request;
 
 typedef struct {

@@ -720,7 +720,7 @@ SimPlan default_plan(const stk_request* q) {
     const int ns = q->n_sims > 0 ? q->n_sims : 0;
     p.seed.assign((size_t)ns, q->seed);
     p.id.resize((size_t)ns);
-    for (int k = 0; k < ns; ++k) p.id[(size_t)k] = (uint32_t)k;
+    for (int k = 0; k < ns; ++k) p.id[(size_t)k] = q->first_sim + (uint32_t)k;
     if (ns > 0) p.groups.push_back({0, ns});
     return p;
 }
