@@ -87,6 +87,9 @@ def _load():
         lib.oracle_pair_hist_polygon.restype = i64
         lib.oracle_csr_polygon_points.argtypes = [i64, P, P, P, i32, u64, u32, i32, P, P, P]
         lib.oracle_csr_polygon_points.restype = i32
+        lib.oracle_k_cross.argtypes = [i64, P, P, P, P, i32, i32, P, P, i32, P, i32, i32, i32,
+                                       P, P, P, P]
+        lib.oracle_k_cross.restype = i64
         _lib = lib
     return _lib
 
@@ -322,4 +325,20 @@ def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, nor
     den = 2.0 * np.pi * tt[None, :]
     return {"K_lo": lo, "K_hi": hi, "L_lo": np.sqrt(lo / den) - s[:, None],
             "L_hi": np.sqrt(hi / den) - s[:, None], "K_all": Ks}
+
+
+def k_cross(x, y, t, labels, a, b, box, s, tt, edge_mode=1, norm=0):
+    """Bivariate (cross) K between centres labelled a and neighbours labelled b."""
+    x, y, t, s, tt = map(_f64, (x, y, t, s, tt))
+    lab = np.ascontiguousarray(labels, dtype=np.uint8)
+    bx = _box(box)
+    cs, ct = len(s), len(tt)
+    C = np.zeros(cs * ct, np.int64)
+    S, K, L = (np.zeros(cs * ct, np.float64) for _ in range(3))
+    q = _load().oracle_k_cross(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(lab), a, b, _ptr(bx),
+                               _ptr(s), cs, _ptr(tt), ct, edge_mode, norm, _ptr(C), _ptr(S),
+                               _ptr(K), _ptr(L))
+    sh = (cs, ct)
+    return {"C": C.reshape(sh), "S": S.reshape(sh), "K": K.reshape(sh), "L": L.reshape(sh),
+            "pairs": int(q)}
 

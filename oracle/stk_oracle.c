@@ -540,3 +540,84 @@ int oracle_csr_polygon_points(int64_t n, const double box[6], const double* vx,
     return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * Bivariate (cross) K between the points labelled a (centres) and the points
+ * labelled b (neighbours), the bivariate variant the paper names as future
+ * work: ordered pairs (i, j), i != j, labels[i] == a, labels[j] == b, weights
+ * centred at i; K = A*D/(n_a n_b) * sum (a != b), and for a == b the
+ * univariate estimator of that subset (n_a (n_a - 1), or n_a^2 with norm 1).
+ * ------------------------------------------------------------------------- */
+int64_t oracle_k_cross(int64_t n, const double* x, const double* y, const double* t,
+                       const uint8_t* labels, int a, int b, const double box[6], const double* s,
+                       int cs, const double* tt, int ct, int edge_mode, int norm, int64_t* C,
+                       double* S, double* K, double* L) {
+    const int nb = cs * ct;
+    int64_t* cnt = (int64_t*)calloc((size_t)nb, sizeof(int64_t));
+    double* wsum = (double*)calloc((size_t)nb, sizeof(double));
+    double* comp = (double*)calloc((size_t)nb, sizeof(double));
+    double* s2 = (double*)malloc(sizeof(double) * (size_t)cs);
+    for (int q = 0; q < cs; ++q) s2[q] = s[q] * s[q];
+    const double s2max = s2[cs - 1], tmax = tt[ct - 1];
+    int64_t na = 0, nbb = 0, total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        na += labels[i] == a;
+        nbb += labels[i] == b;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (labels[i] != a) continue;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i || labels[j] != b) continue;
+            const double dx = x[i] - x[j];
+            const double dy = y[i] - y[j];
+            const double d2 = dx * dx + dy * dy;
+            if (d2 > s2max) continue;
+            const double u = fabs(t[i] - t[j]);
+            if (u > tmax) continue;
+            int ai = 0;
+            while (d2 > s2[ai]) ++ai;
+            int bi = 0;
+            while (u > tt[bi]) ++bi;
+            double w = 1.0;
+            if (edge_mode == 1) {
+                const double om = oracle_spatial_weight(x[i], y[i], sqrt(d2), box);
+                const double v = oracle_temporal_weight(t[i], u, box[4], box[5]);
+                w = 1.0 / (om * v);
+            }
+            const int k = ai * ct + bi;
+            cnt[k] += 1;
+            const double yk = w - comp[k];
+            const double tk = wsum[k] + yk;
+            comp[k] = (tk - wsum[k]) - yk;
+            wsum[k] = tk;
+            ++total;
+        }
+    }
+    /* cumulative grids and the normalisation of Eq. 2 with the cross denominator */
+    const double area = (box[1] - box[0]) * (box[3] - box[2]);
+    const double dur = box[5] - box[4];
+    const double fa = (double)na, fb = (double)nbb;
+    const double denom = (a != b) ? fa * fb : (norm == 1 ? fa * fa : fa * (fa - 1.0));
+    for (int p = 0; p < cs; ++p) {
+        for (int q = 0; q < ct; ++q) {
+            int64_t c = 0;
+            double wsumc = 0.0;
+            for (int p2 = 0; p2 <= p; ++p2)
+                for (int q2 = 0; q2 <= q; ++q2) {
+                    c += cnt[p2 * ct + q2];
+                    wsumc += wsum[p2 * ct + q2];
+                }
+            const int k = p * ct + q;
+            const double kv = area * dur / denom * wsumc;
+            if (C) C[k] = c;
+            if (S) S[k] = wsumc;
+            if (K) K[k] = kv;
+            if (L) L[k] = sqrt(kv / (2.0 * ORACLE_PI * tt[q])) - s[p];
+        }
+    }
+    free(cnt);
+    free(wsum);
+    free(comp);
+    free(s2);
+    return total;
+}
+

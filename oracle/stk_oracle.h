@@ -65,6 +65,12 @@ int oracle_csr_polygon_points(int64_t n, const double box[6], const double* vx,
                               const double* vy, int nv, uint64_t seed, uint32_t sim,
                               int max_attempts, double* x, double* y, double* t);
 
+/* Bivariate (cross) K: centres labelled a, neighbours labelled b (see the source). */
+int64_t oracle_k_cross(int64_t n, const double* x, const double* y, const double* t,
+                       const uint8_t* labels, int a, int b, const double box[6], const double* s,
+                       int cs, const double* tt, int ct, int edge_mode, int norm, int64_t* C,
+                       double* S, double* K, double* L);
+
 /* Bootstrapping (Section 3): source index of point i of realization `sim`
  * (uniform draw with replacement), and the whole resampled realization. */
 int64_t oracle_bootstrap_index(int64_t n, uint64_t seed, uint32_t sim, int64_t i);

@@ -519,3 +519,37 @@ def test_csr_in_polygon_inside_and_uniform(orc):
     x2, y2, t2 = orc.csr_polygon_points(n, box, *ell, 9, 2)
     np.testing.assert_array_equal(x, x2)
 
+
+
+# ------------------------------------------------------------------- bivariate (cross) K
+
+
+def _two_types(seed, n=500):
+    rng = np.random.default_rng(seed)
+    box = (0.0, 500.0, 0.0, 400.0, 0.0, 60.0)
+    x, y, t = rng.uniform(0, 500, n), rng.uniform(0, 400, n), rng.uniform(0, 60, n)
+    lab = (rng.uniform(size=n) < 0.35).astype(np.uint8)
+    return x, y, t, lab, box
+
+
+def test_cross_k_same_label_is_the_subset_estimator(orc):
+    x, y, t, lab, box = _two_types(1)
+    s, tt = np.array([15.0, 40.0, 90.0]), np.array([3.0, 10.0])
+    for a in (0, 1):
+        sel = lab == a
+        want = orc.k_function(x[sel], y[sel], t[sel], box, s, tt)
+        got = orc.k_cross(x, y, t, lab, a, a, box, s, tt)
+        np.testing.assert_array_equal(got["C"], want["C"])
+        np.testing.assert_allclose(got["K"], want["K"], rtol=1e-13)
+
+
+def test_cross_counts_partition_all_pairs_and_are_symmetric(orc):
+    x, y, t, lab, box = _two_types(2)
+    s, tt = np.array([20.0, 60.0]), np.array([5.0, 20.0])
+    allc = orc.k_function(x, y, t, box, s, tt)["C"]
+    c = {(a, b): orc.k_cross(x, y, t, lab, a, b, box, s, tt)["C"] for a in (0, 1)
+         for b in (0, 1)}
+    np.testing.assert_array_equal(sum(c.values()), allc)
+    np.testing.assert_array_equal(c[(0, 1)], c[(1, 0)])
+    none = orc.k_cross(x, y, t, lab, 0, 1, box, s, tt, edge_mode=0)
+    np.testing.assert_array_equal(none["S"], none["C"].astype(float))
