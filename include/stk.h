@@ -149,6 +149,15 @@ typedef struct {
                             the counter-based generator, so a long envelope job can run (or
                             resume after an interruption) in chunks: the union of the chunks'
                             realizations equals the whole job's, bit for bit */
+    /* Bivariate (cross) K, the variant the paper names as future work: with labels (host
+     * [n], copied) every grid is over ordered pairs from centres labelled cross_a to
+     * neighbours labelled cross_b, weights centred at the centre, normalised by
+     * n_a * n_b (the subset's univariate normalisation when cross_a == cross_b).  Simulated
+     * point i keeps the label of observed point i (CSR and permutation; not bootstrap).
+     * NULL = univariate.  Not combined with centre_mask. */
+    const uint8_t* labels;
+    int cross_a;
+    int cross_b;
 } stk_request;
 
 typedef struct {

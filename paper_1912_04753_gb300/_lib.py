@@ -38,7 +38,8 @@ class stk_request(ctypes.Structure):
     _fields_ = [("s", _P), ("cs", ctypes.c_int), ("tt", _P), ("ct", ctypes.c_int),
                 ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int), ("norm", ctypes.c_int),
                 ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64), ("exec", ctypes.c_int),
-                ("centre_mask", _P), ("sim_method", ctypes.c_int), ("first_sim", ctypes.c_uint32)]
+                ("centre_mask", _P), ("sim_method", ctypes.c_int), ("first_sim", ctypes.c_uint32),
+                ("labels", _P), ("cross_a", ctypes.c_int), ("cross_b", ctypes.c_int)]
 
 
 class stk_result(ctypes.Structure):
@@ -220,14 +221,16 @@ def stk_envelope(h, s, tt, n_sims, seed, edge_mode=STK_EDGE_ISOTROPIC,
 
 def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
             prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
-            centre_mask=None, want_sims=False, sim_method=STK_SIM_CSR, first_sim=0):
+            centre_mask=None, want_sims=False, sim_method=STK_SIM_CSR, first_sim=0,
+            labels=None, cross=(0, 0)):
     """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim)."""
     s, tt = _f64(s), _f64(tt)
     cs, ct = s.shape[0], tt.shape[0]
     nb = cs * ct
     mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
     q = stk_request(_ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims, seed, exec_mode,
-                    _ptr(mask), sim_method, first_sim)
+                    _ptr(mask), sim_method, first_sim, _ptr(lab), int(cross[0]), int(cross[1]))
     o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
     if n_sims > 0:
         for k in ("K_lo", "K_hi", "L_lo", "L_hi"):

@@ -324,6 +324,7 @@ struct ScatterGrid {
     double qx, qy, qt;
     float tan_rel, tan_abs, fast_abs;
     Polygon poly;
+    int mask_all;  // role flags for every realization (indexed by the point's index in it)
 };
 
 __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
@@ -374,7 +375,7 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         rin = fmaxf(rin, 0.0f);
         P[2 * pos + 1] = make_float4(ex, ey, te, rin * rin * 0.99999f);
         Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
-        if (mask_out && k == 0) mask_out[pos] = mask_in[gi];
+        if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)k * n];
     }
 }
 
@@ -534,9 +535,10 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
                            float tan_rel, float tan_abs, float fast_abs, cudaStream_t st,
-                           Polygon poly) {
+                           Polygon poly, bool mask_all) {
     ScatterGrid s;
     s.poly = poly;
+    s.mask_all = mask_all ? 1 : 0;
     s.x1 = g.x1;
     s.y1 = g.y1;
     s.t1 = g.t1;

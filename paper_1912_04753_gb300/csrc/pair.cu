@@ -314,7 +314,7 @@ struct WarpCtx {
     const uint8_t* mk;        // centre mask of the current realization, or null
     uint32_t real;
     uint32_t c_begin;
-    uint32_t onmask;          // lanes whose centre is active (mask mode)
+    uint32_t onA, onB;        // lanes whose centre counts as a centre / as a neighbour
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
     const PairConsts* pa;     // shared-memory copy (indexed tables and bands)
@@ -511,8 +511,11 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             b = bin_fp32(u, pc.inv_ht, pa.tab_t, pa.t_lo, pa.t_hi, pc.ct, am);
         }
         bin[r] = a * pc.ct + b;  // always a valid bin, also for lanes without an entry
-        const bool act_i = w.mk == nullptr || ((w.onmask >> cl) & 1u);
-        const bool act_j = w.mk == nullptr || (has && w.mk[e[r].w] != 0);
+        // order (i, j) counts when i is a centre and j a neighbour (role flags), (j, i) the
+        // other way round
+        const uint32_t fj = w.mk == nullptr ? 3u : (has ? (uint32_t)w.mk[e[r].w] : 0u);
+        const bool act_i = w.mk == nullptr || (((w.onA >> cl) & 1u) && (fj & 2u));
+        const bool act_j = w.mk == nullptr || ((fj & 1u) && ((w.onB >> cl) & 1u));
         ai[r] = act_i;
         aj[r] = act_j;
         const bool counted = has & !am;
@@ -661,7 +664,9 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         const float4* Pk = rb.P + 2 * base;
         w.Pk = Pk;
         w.real = (uint32_t)k;
-        w.mk = (rb.mask != nullptr && k == 0) ? rb.mask : nullptr;
+        w.mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
+                   ? rb.mask + (rb.mask_all ? base : 0)
+                   : nullptr;
         if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
         __syncthreads();
         for (;;) {
@@ -680,7 +685,9 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             ws.cen_a[lane] = make_float4(p.x, p.y, p.z, pe.w);
             ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
             ws.cen_te[lane] = pe.z;
-            w.onmask = __ballot_sync(0xffffffffu, valid && (w.mk == nullptr || w.mk[myi] != 0));
+            const uint32_t fl = w.mk == nullptr ? 3u : (uint32_t)w.mk[myi];
+            w.onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
+            w.onB = __ballot_sync(0xffffffffu, valid && (fl & 2u));
             const float cut2 = valid ? pc.s2_cut : -1.0f;  // idle lanes never qualify
             const float ucut = pc.u_cut;
             const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
@@ -815,7 +822,8 @@ struct Smem64 {
 template <bool POLY>
 __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
                                           int lane, const double* X, const double* Y,
-                                          const double* T, const uint8_t* mk, uint32_t onmask,
+                                          const double* T, const uint8_t* mk, uint32_t onA,
+                                          uint32_t onB,
                                           uint32_t* hc, unsigned long long* he,
                                           unsigned long long* stats) {
     if (lane >= cnt) return;
@@ -838,8 +846,9 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     kt = kt < kTab - 1 ? kt : kTab - 1;
     int b = pc.tab_t64[kt];
     while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
-    const bool act_i = mk == nullptr || ((onmask >> e.x) & 1u);
-    const bool act_j = mk == nullptr || mk[e.y] != 0;
+    const uint32_t fj = mk == nullptr ? 3u : (uint32_t)mk[e.y];
+    const bool act_i = mk == nullptr || (((onA >> e.x) & 1u) && (fj & 2u));
+    const bool act_j = mk == nullptr || ((fj & 1u) && ((onB >> e.x) & 1u));
     unsigned long long exc = 0;
     if (pc.edge) {
         const double r = __dsqrt_rn(d2);
@@ -894,7 +903,9 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         const double* X = rb.X + base;
         const double* Y = rb.Y + base;
         const double* T = rb.T + base;
-        const uint8_t* mk = (rb.mask != nullptr && k == 0) ? rb.mask : nullptr;
+        const uint8_t* mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
+                                ? rb.mask + (rb.mask_all ? (int64_t)k * rb.n : 0)
+                                : nullptr;
         for (;;) {
             uint32_t u = 0;
             if (lane == 0) u = atomicAdd(&counters[k], 1u);
@@ -909,7 +920,9 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             ws.cy[lane] = yi;
             ws.ct[lane] = ti;
             const int cx = __float_as_int(rb.P[2 * (base + ci)].w);
-            const uint32_t onmask = __ballot_sync(0xffffffffu, valid && (mk == nullptr || mk[ci]));
+            const uint32_t fl = mk == nullptr ? 3u : (uint32_t)mk[ci];
+            const uint32_t onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
+            const uint32_t onB = __ballot_sync(0xffffffffu, valid && (fl & 2u));
             const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
             const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
             const int wb = min(nx - 1, cxb + fs);
@@ -939,7 +952,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         tail += __popc(mq);
                         if (tail >= 32u) {
                             __syncwarp();
-                            process64<POLY>(pc, ws, 32, lane, X, Y, T, mk, onmask, my_hc, my_he,
+                            process64<POLY>(pc, ws, 32, lane, X, Y, T, mk, onA, onB, my_hc, my_he,
                                       acc.stats);
                             __syncwarp();
                             if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
@@ -951,7 +964,8 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             }
             __syncwarp();
             if (tail > 0)
-                process64<POLY>(pc, ws, (int)tail, lane, X, Y, T, mk, onmask, my_hc, my_he, acc.stats);
+                process64<POLY>(pc, ws, (int)tail, lane, X, Y, T, mk, onA, onB, my_hc, my_he,
+                                acc.stats);
             __syncwarp();
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);

@@ -201,7 +201,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
     // starts, scan scratch; work counts/offsets and units; histograms; seeds; FP64 queue
     f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
-                 8 + 12 + (fp32 ? 16 * un : 0);
+                 8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */;
     f.fixed = 32 * 8 + 32 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
               16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
@@ -322,6 +322,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         return fail(STK_EINVAL, "unknown exec %d", q->exec);
     if (q->sim_method < STK_SIM_CSR || q->sim_method > STK_SIM_BOOTSTRAP)
         return fail(STK_EINVAL, "unknown sim_method %d", q->sim_method);
+    if (q->labels && q->centre_mask)
+        return fail(STK_EINVAL, "labels (cross K) and centre_mask cannot be combined");
+    if (q->labels && q->sim_method == STK_SIM_BOOTSTRAP)
+        return fail(STK_EINVAL, "cross K takes CSR or permutation simulations");
+    if (q->labels && (q->cross_a < 0 || q->cross_a > 255 || q->cross_b < 0 || q->cross_b > 255))
+        return fail(STK_EINVAL, "cross labels must be in 0..255");
     const int n_sims = (int)plan.seed.size();
     if (n_sims > (1 << 24) || plan.id.size() != plan.seed.size())
         return fail(STK_EINVAL, "n_sims out of range");
@@ -432,16 +438,33 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     if (fp32_path(q) && ((rc = ensure(h->xq_e, sizeof(uint4) * (size_t)xq_cap, "FP64 queue")) ||
                          (rc = ensure(h->xq_count, 16, "FP64 queue"))))
         return rc;
-    const bool use_mask = include_obs && q->centre_mask != nullptr;
-    int64_t masked = n;
+    // per-point role flags (bit 0 centre, bit 1 neighbour): the sampled-centre mask of the
+    // observed pattern, or the labels of a cross K for every realization
+    const bool cross = q->labels != nullptr;
+    const bool centre_mode = include_obs && q->centre_mask != nullptr;
+    const bool use_mask = centre_mode || cross;
+    int64_t n_a = n, n_b = n;
     if (use_mask) {
-        if ((rc = ensure(h->mask_in, (size_t)n, "centre mask")) ||
-            (rc = ensure(h->mask_sorted, (size_t)n, "centre mask")))
+        if ((rc = ensure(h->mask_in, (size_t)n, "role flags")) ||
+            (rc = ensure(h->mask_sorted, (size_t)n * (cross ? (size_t)m_w : 1), "role flags")))
             return rc;
-        CK(cudaMemcpyAsync(h->mask_in.p, q->centre_mask, (size_t)n, cudaMemcpyHostToDevice, st),
-           "mask upload");
-        masked = 0;
-        for (int64_t i = 0; i < n; ++i) masked += q->centre_mask[i] != 0;
+        std::vector<uint8_t> flags((size_t)n);
+        n_a = n_b = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (cross) {
+                const bool fa = q->labels[i] == q->cross_a, fb = q->labels[i] == q->cross_b;
+                flags[(size_t)i] = (uint8_t)((fa ? 1 : 0) | (fb ? 2 : 0));
+                n_a += fa;
+                n_b += fb;
+            } else {
+                flags[(size_t)i] = (uint8_t)((q->centre_mask[i] != 0 ? 1 : 0) | 2);
+            }
+        }
+        if (cross && (n_a < 1 || n_b < 1 || (q->cross_a == q->cross_b && n_a < 2)))
+            return fail(STK_EINVAL, "cross K needs points of both labels");
+        // pageable source: staged before the call returns
+        CK(cudaMemcpyAsync(h->mask_in.p, flags.data(), (size_t)n, cudaMemcpyHostToDevice, st),
+           "role flags upload");
     }
     CK(cudaMemcpyAsync(h->pc.p, h->h_pc, sizeof(PairConsts), cudaMemcpyHostToDevice, st),
        "constants upload");
@@ -470,7 +493,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const double area = h->area;
     const double dur = h->box[5] - h->box[4];
     const double nn = (double)n;
-    const double coef = area * dur / (q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0));
+    double denom = q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0);
+    if (cross) {
+        const double fa = (double)n_a, fb = (double)n_b;
+        denom = q->cross_a != q->cross_b ? fa * fb
+                                         : (q->norm == STK_NORM_N2 ? fa * fa : fa * (fa - 1.0));
+    }
+    const double coef = area * dur / denom;
     const double* d_s = as<double>(h->thr);
     const double* d_tt = as<double>(h->thr) + STK_MAX_THRESHOLDS;
     const bool fp32 = q->prec == STK_PREC_FP32_GUARDED;
@@ -536,10 +565,12 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
            "cell scan");
         CK(launch_scatter(m, n, g, as<double>(h->ux), as<double>(h->uy), as<double>(h->ut),
                           as<uint32_t>(h->key), as<uint32_t>(h->rank), as<uint32_t>(h->start),
-                          (obs_here && use_mask) ? as<uint8_t>(h->mask_in) : nullptr,
+                          (cross || (obs_here && centre_mode)) ? as<uint8_t>(h->mask_in)
+                                                               : nullptr,
                           as<double>(h->X), as<double>(h->Y), as<double>(h->T),
                           as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
-                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st, poly),
+                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st, poly,
+                          cross),
            "scatter");
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
@@ -567,7 +598,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         rb.Y = as<double>(h->Y);
         rb.T = as<double>(h->T);
         rb.cell_start = as<uint32_t>(h->cell_start);
-        rb.mask = (obs_here && use_mask) ? as<uint8_t>(h->mask_sorted) : nullptr;
+        rb.mask = (cross || (obs_here && centre_mode)) ? as<uint8_t>(h->mask_sorted) : nullptr;
+        rb.mask_all = cross ? 1 : 0;
         rb.n = n;
         rb.ncells = ncells;
         Accum acc;

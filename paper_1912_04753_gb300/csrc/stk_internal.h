@@ -91,9 +91,13 @@ struct RealBatch {
     const double* Y;
     const double* T;
     const uint32_t* cell_start;
-    const uint8_t* mask;    // sorted centre mask of realization 0, or null
+    // sorted per-point role flags (bit 0: counts as a centre, bit 1: counts as a neighbour;
+    // order (i, j) counts when i has bit 0 and j bit 1), or null (every order counts); of
+    // realization 0 only, or of every realization (mask + k * n) when mask_all
+    const uint8_t* mask;
     int64_t n;
     int64_t ncells;
+    int mask_all = 0;
 };
 
 // Per-realization accumulators: counts and the fixed-point (2^-32) sum of (w - 1), the latter
@@ -155,7 +159,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
-                           cudaStream_t st, Polygon poly = Polygon());
+                           cudaStream_t st, Polygon poly = Polygon(), bool mask_all = false);
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
 // units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)
