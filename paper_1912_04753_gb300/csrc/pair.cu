@@ -42,7 +42,8 @@ __device__ __forceinline__ double omega64(const PairConsts& pc, double xi, doubl
                                           double r) {
     if (r == 0.0) return 1.0;
     if (POLY && pc.nv > 0) {
-        const double w = poly_weight_fast(xi, yi, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        const double w =
+            poly_weight_fast<true>(xi, yi, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
         return w >= 0.0 ? w : poly_weight(xi, yi, r, pc.pvx, pc.pvy, pc.nv);
     }
     const double ex = fmin(__dsub_rn(xi, pc.g.x0), __dsub_rn(pc.g.x1, xi));
@@ -377,7 +378,8 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
         const double xa = rb.X[base + a], ya = rb.Y[base + a];
         const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
         const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-        const double om = poly_weight_fast(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        const double om =
+            poly_weight_fast<false>(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
         const double w = om > 0.0 ? 1.0 / (om * (vhalf ? 0.5 : 1.0)) : 0.0;
         // undecided crossings, and weights above 8 (beyond the shared accumulators' bound),
         // go to the FP64 queue

@@ -114,7 +114,8 @@ static __device__ __noinline__ double poly_weight(double xi, double yi, double r
     return inside / two_pi;
 }
 
-// The same weight from the crossings' directions (no point-in-polygon test per arc): along a
+// The same weight from the crossings' directions (no point-in-polygon test per arc, one FP32
+// arctangent per inside arc): along a
 // crossed edge a -> b the segment enters the disc at the smaller root of
 // |a + s (b - a) - c|^2 = r^2 and leaves it at the larger, and at the larger root the circle,
 // run counter-clockwise, passes to the left of the edge, i.e. into the polygon when its
@@ -124,11 +125,17 @@ static __device__ __noinline__ double poly_weight(double xi, double yi, double r
 // (x_min, x_max, y_min, y_max), for culling.  Returns -1 when a crossing is too close to a
 // tangency to call or the crossings do not alternate (a vertex on the circle): the caller
 // then uses poly_weight.
+// F64: arc lengths in FP64 (the FP64 paths); else in FP32 from FP64 end vectors (relative
+// error ~1e-7 of each arc: the FP32-guarded path).
+template <bool F64>
 static __device__ __noinline__ double poly_weight_fast(double xi, double yi, double r,
                                                        const double* vx, const double* vy,
                                                        const float4* ebox, int nv, int ccw) {
     if (r <= 0.0) return 1.0;
-    double ang[kMaxCross];
+    // crossing points relative to the centre (FP64), an FP32 angle to sort them by, and
+    // whether the circle enters the polygon there
+    double cpx[kMaxCross], cpy[kMaxCross];
+    float key[kMaxCross];
     bool enter[kMaxCross];
     int na = 0;
     const float m = (float)(r * 1e-4) + 1e-6f * (fabsf((float)xi) + fabsf((float)yi)) + 1e-30f;
@@ -155,30 +162,45 @@ static __device__ __noinline__ double poly_weight_fast(double xi, double yi, dou
             const double sr = q ? s1 : s0;
             if (sr < 0.0 || sr >= 1.0) continue;
             if (na == kMaxCross) return -2.0;  // more crossings than supported
-            ang[na] = atan2(fy + sr * dy, fx + sr * dx);
+            cpx[na] = fx + sr * dx;
+            cpy[na] = fy + sr * dy;
+            key[na] = atan2f((float)cpy[na], (float)cpx[na]);
             enter[na++] = (q == 1) == (ccw != 0);
         }
     }
     if (na == 0) return poly_contains(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
-    for (int a = 1; a < na; ++a) {
-        const double v = ang[a];
+    if (na & 1) return -1.0;
+    for (int a = 1; a < na; ++a) {  // insertion sort by angle: a handful of crossings
+        const float kv = key[a];
+        const double px = cpx[a], py = cpy[a];
         const bool e = enter[a];
         int b = a - 1;
-        while (b >= 0 && ang[b] > v) {
-            ang[b + 1] = ang[b];
+        while (b >= 0 && key[b] > kv) {
+            key[b + 1] = key[b];
+            cpx[b + 1] = cpx[b];
+            cpy[b + 1] = cpy[b];
             enter[b + 1] = enter[b];
             --b;
         }
-        ang[b + 1] = v;
+        key[b + 1] = kv;
+        cpx[b + 1] = px;
+        cpy[b + 1] = py;
         enter[b + 1] = e;
     }
-    if (na & 1) return -1.0;
+    // inside arcs run from an entering crossing to the next one, counter-clockwise; each
+    // length is the angle between its end vectors, from their cross and dot products in FP64
+    // (relative accuracy of the short arcs), then atan2 in FP32
     const double two_pi = 6.283185307179586;
     double inside = 0.0;
     for (int k = 0; k < na; ++k) {
-        const bool next = enter[k + 1 < na ? k + 1 : 0];
-        if (enter[k] == next) return -1.0;  // crossings must alternate
-        if (enter[k]) inside += (k + 1 < na ? ang[k + 1] : ang[0] + two_pi) - ang[k];
+        const int k1 = k + 1 < na ? k + 1 : 0;
+        if (enter[k] == enter[k1]) return -1.0;  // crossings must alternate
+        if (!enter[k]) continue;
+        const double cr = cpx[k] * cpy[k1] - cpy[k] * cpx[k1];
+        const double dt = cpx[k] * cpx[k1] + cpy[k] * cpy[k1];
+        double da = F64 ? atan2(cr, dt) : (double)atan2f((float)cr, (float)dt);
+        if (da < 0.0 || (da == 0.0 && dt < 0.0)) da += two_pi;
+        inside += da;
     }
     return inside / two_pi;
 }

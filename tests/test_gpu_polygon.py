@@ -94,8 +94,10 @@ def test_envelope_in_polygon(stk, orc, method):
         got = p.run(s, tt, n_sims=sims, seed=seed, sim_method=method, want_sims=True)
     for k in range(sims):
         assert _rel(got["K_sims"][k], want["K_all"][k]).max() <= TOL[1]
-    for key in ("K_lo", "K_hi", "L_lo", "L_hi"):
+    for key in ("K_lo", "K_hi"):
         assert _rel(got[key], want[key]).max() <= TOL[1], key
+    for key in ("L_lo", "L_hi"):  # L through L + s = sqrt(K / (2 pi t)), as K
+        assert _rel(got[key] + s[:, None], want[key] + s[:, None]).max() <= TOL[1], key
 
 
 def test_polygon_arguments_checked(stk, orc):
