@@ -66,3 +66,54 @@ def test_full_size_job_sampled_centres_and_simulations(stk, orc):
     # envelope = element-wise min / max of the realizations
     np.testing.assert_array_equal(got["K_lo"], Ks.min(axis=0))
     np.testing.assert_array_equal(got["K_hi"], Ks.max(axis=0))
+
+
+def test_thomas_config_batched_fp64_equals_plain(stk, orc):
+    # the Thomas configuration (n = 200,000, 99 simulations, FP64): one batched launch and one
+    # launch per realization give the same grids bit for bit; sampled observed centres match
+    # the oracle
+    from paper_1912_04753_gb300 import workloads as wl
+
+    w = wl.config_thomas()
+    rng = np.random.default_rng(5)
+    mask = np.zeros(w.n, np.uint8)
+    mask[rng.choice(w.n, 64, replace=False)] = 1
+    with stk.Pattern(w.x, w.y, w.t, w.box) as p:
+        b = p.run(w.s, w.tt, n_sims=w.n_sims, seed=w.sim_seed, prec=stk.STK_PREC_FP64,
+                  want_sims=True)
+        q = p.run(w.s, w.tt, n_sims=w.n_sims, seed=w.sim_seed, prec=stk.STK_PREC_FP64,
+                  exec_mode=stk.STK_EXEC_PLAIN, want_sims=True)
+        m = p.run(w.s, w.tt, prec=stk.STK_PREC_FP64, centre_mask=mask)
+        assert p.stats()["internal_errors"] == 0
+    for k in b:
+        np.testing.assert_array_equal(b[k], q[k], err_msg=k)
+    cnt, wsum, _ = orc.pair_hist(w.x, w.y, w.t, w.box, w.s, w.tt, centre_mask=mask)
+    C, S, K, L = orc.finalize(w.n, w.box, w.s, w.tt, cnt, wsum)
+    np.testing.assert_array_equal(m["C"], C)
+    assert _rel(m["K"], K).max() <= 1e-9
+
+
+def test_large_config_in_waves(stk, orc):
+    # n = 10^7 and 199 simulations do not fit at once: the job runs in waves; sampled observed
+    # centres match the oracle and every realization satisfies the invariants
+    from paper_1912_04753_gb300 import workloads as wl
+
+    w = wl.config_large()
+    rng = np.random.default_rng(9)
+    mask = np.zeros(w.n, np.uint8)
+    mask[rng.choice(w.n, 48, replace=False)] = 1
+    with stk.Pattern(w.x, w.y, w.t, w.box) as p:
+        got = p.run(w.s, w.tt, n_sims=w.n_sims, seed=w.sim_seed, centre_mask=mask,
+                    want_sims=True)
+        st = p.stats()
+    assert st["internal_errors"] == 0 and st["realizations"] == 200
+    assert st["waves"] >= 2
+    cnt, wsum, _ = orc.pair_hist(w.x, w.y, w.t, w.box, w.s, w.tt, centre_mask=mask)
+    C, S, K, L = orc.finalize(w.n, w.box, w.s, w.tt, cnt, wsum)
+    np.testing.assert_array_equal(got["C"], C)
+    assert _rel(got["K"], K).max() <= 1e-6
+    Cs, Ks = got["C_sims"], got["K_sims"]
+    assert (np.diff(Cs, axis=1) >= 0).all() and (np.diff(Cs, axis=2) >= 0).all()
+    assert (Cs % 2 == 0).all()
+    np.testing.assert_array_equal(got["K_lo"], Ks.min(axis=0))
+    np.testing.assert_array_equal(got["K_hi"], Ks.max(axis=0))
