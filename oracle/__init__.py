@@ -90,6 +90,17 @@ def _load():
         lib.oracle_k_cross.argtypes = [i64, P, P, P, P, i32, i32, P, P, i32, P, i32, i32, i32,
                                        P, P, P, P]
         lib.oracle_k_cross.restype = i64
+        lib.oracle_intensity_cell.argtypes = [P, i32, i32, i32, d, d, d]
+        lib.oracle_intensity_cell.restype = i32
+        lib.oracle_intensity_lambda.argtypes = [P, i32, i32, i32, P, i64, P]
+        lib.oracle_intensity_lambda.restype = None
+        lib.oracle_inhom_points.argtypes = [i64, P, P, i32, i32, i32, u64, u32, P, P, P, P]
+        lib.oracle_inhom_points.restype = None
+        lib.oracle_pair_hist_inhom.argtypes = [i64, P, P, P, P, P, P, i32, P, i32, i32, P, P,
+                                               P]
+        lib.oracle_pair_hist_inhom.restype = i64
+        lib.oracle_finalize_inhom.argtypes = [i64, P, P, i32, P, i32, i32, P, P, P, P, P, P]
+        lib.oracle_finalize_inhom.restype = None
         _lib = lib
     return _lib
 
@@ -292,6 +303,66 @@ def csr_polygon_points(n: int, box, vx, vy, seed: int, sim: int, max_attempts: i
     return x, y, t
 
 
+def _rho(rho):
+    r = _f64(rho)
+    assert r.ndim == 3, "rho is indexed [t][y][x]"
+    return np.ascontiguousarray(r), r.shape[2], r.shape[1], r.shape[0]
+
+
+def intensity_cell(box, rho_shape, x: float, y: float, t: float) -> int:
+    """Cell of the intensity grid (shape [nit, niy, nix]) holding the point (x, y, t)."""
+    nit, niy, nix = rho_shape
+    return int(_load().oracle_intensity_cell(_ptr(_box(box)), nix, niy, nit, x, y, t))
+
+
+def intensity_lambda(rho, box, n: int):
+    """Intensity per cell: rho scaled to integrate to n over the box."""
+    r, nix, niy, nit = _rho(rho)
+    lam = np.empty(r.size, np.float64)
+    _load().oracle_intensity_lambda(_ptr(r), nix, niy, nit, _ptr(_box(box)), n, _ptr(lam))
+    return lam
+
+
+def intensity_at(x, y, t, box, rho):
+    """Intensity at each point: lambda of the cell that holds it."""
+    lam = intensity_lambda(rho, box, len(x))
+    cells = np.array([intensity_cell(box, np.shape(rho), float(a), float(b), float(c))
+                      for a, b, c in zip(x, y, t)], dtype=np.int64)
+    return lam[cells] if len(cells) else np.zeros(0)
+
+
+def inhom_points(n: int, box, rho, seed: int, sim: int):
+    """Realization `sim` of n points drawn with density proportional to rho, and the cell of
+    each point."""
+    r, nix, niy, nit = _rho(rho)
+    x, y, t = (np.empty(n, np.float64) for _ in range(3))
+    cell = np.empty(n, np.int32)
+    _load().oracle_inhom_points(n, _ptr(_box(box)), _ptr(r), nix, niy, nit, seed, sim, _ptr(x),
+                                _ptr(y), _ptr(t), _ptr(cell))
+    return x, y, t, cell
+
+
+def k_function_inhom(x, y, t, box, s, tt, lam, edge_mode=1, norm=0, centre_mask=None):
+    """Inhomogeneous estimator with the intensity lam[i] at each point (see stk_oracle.c)."""
+    x, y, t, s, tt, lam = map(_f64, (x, y, t, s, tt, lam))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.zeros(cs * ct, np.int64)
+    wsum = np.zeros(cs * ct, np.float64)
+    m = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    lib = _load()
+    q = lib.oracle_pair_hist_inhom(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(lam), _ptr(b),
+                                   _ptr(s), cs, _ptr(tt), ct, edge_mode, _ptr(m), _ptr(cnt),
+                                   _ptr(wsum))
+    C = np.zeros(cs * ct, np.int64)
+    S, K, L = (np.zeros(cs * ct, np.float64) for _ in range(3))
+    lib.oracle_finalize_inhom(len(x), _ptr(b), _ptr(s), cs, _ptr(tt), ct, norm, _ptr(cnt),
+                              _ptr(wsum), _ptr(C), _ptr(S), _ptr(K), _ptr(L))
+    sh = (cs, ct)
+    return {"C": C.reshape(sh), "S": S.reshape(sh), "K": K.reshape(sh), "L": L.reshape(sh),
+            "pairs": int(q)}
+
+
 def simulation_points(method: int, x, y, t, box, seed: int, sim: int, polygon=None):
     """Realization `sim` of the given simulation method (Section 3)."""
     if method == SIM_CSR and polygon is not None:
@@ -306,12 +377,23 @@ def simulation_points(method: int, x, y, t, box, seed: int, sim: int, polygon=No
 
 
 def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, norm=0,
-                polygon=None):
+                polygon=None, rho=None):
     """Envelope (Section 3) over n_sims realizations of any simulation method (optionally in
-    a polygon study area): the element-wise min / max of K (and L of those), plus every
-    realization's K."""
+    a polygon study area, or of the inhomogeneous K with relative intensity rho, whose CSR
+    realizations are then drawn with density proportional to rho): the element-wise min /
+    max of K (and L of those), plus every realization's K."""
     Ks = []
     for k in range(n_sims):
+        if rho is not None:
+            if method == SIM_CSR:
+                px, py, pt, cell = inhom_points(len(x), box, rho, seed, k)
+                lam = intensity_lambda(rho, box, len(x))[cell]
+            else:
+                px, py, pt = simulation_points(method, x, y, t, box, seed, k)
+                lam = intensity_at(px, py, pt, box, rho)
+            r = k_function_inhom(px, py, pt, box, s, tt, lam, edge_mode=edge_mode, norm=norm)
+            Ks.append(r["K"])
+            continue
         px, py, pt = simulation_points(method, x, y, t, box, seed, k, polygon)
         if polygon is None:
             r = k_function(px, py, pt, box, s, tt, edge_mode=edge_mode, norm=norm)

@@ -621,3 +621,179 @@ int64_t oracle_k_cross(int64_t n, const double* x, const double* y, const double
     return total;
 }
 
+
+/* ---------------------------------------------------------------------------
+ * Inhomogeneous K, the variant Section 7 names as future work, in the
+ * second-order intensity-reweighted form: every ordered pair is divided by the
+ * product of the intensities at its two points.
+ *
+ * The caller gives a relative intensity rho, piecewise constant on
+ * nix x niy x nit equal cells of the box (row-major [nit][niy][nix], x
+ * fastest).  The intensity is rho scaled to integrate to n over the box:
+ * lambda_c = n rho_c / sum_c (rho_c V), V = A D / (nix niy nit).
+ *   K_I(s, t) = n / ((n - 1) A D) * sum_{i != j} I(d <= s, u <= t) / (w v lambda_i lambda_j)
+ * (1 / (A D) with norm 1).  With rho constant, lambda = n / (A D) and K_I is
+ * Eq. 2; for n points drawn independently with density proportional to rho
+ * (rho > 0 everywhere) its expectation is 2 pi s^2 t, as for Eq. 2 under CSR.
+ * The raw sum S reported beside K is sum I / (w v lambda_i lambda_j) times
+ * (n / (A D))^2, so that K = S * A D / (n (n - 1)) in both modes.
+ * ------------------------------------------------------------------------- */
+
+/* Cell of v along one axis of the intensity grid: floor(((v - lo) / (hi - lo)) * nc),
+ * each operation rounded separately, clamped into [0, nc - 1]. */
+static int axis_cell(double v, double lo, double hi, int nc) {
+    double f = floor(((v - lo) / (hi - lo)) * (double)nc);
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(nc - 1)) f = (double)(nc - 1);
+    return (int)f;
+}
+
+int oracle_intensity_cell(const double box[6], int nix, int niy, int nit, double x, double y,
+                          double t) {
+    const int ix = axis_cell(x, box[0], box[1], nix);
+    const int iy = axis_cell(y, box[2], box[3], niy);
+    const int it = axis_cell(t, box[4], box[5], nit);
+    return (it * niy + iy) * nix + ix;
+}
+
+void oracle_intensity_lambda(const double* rho, int nix, int niy, int nit, const double box[6],
+                             int64_t n, double* lam_cell) {
+    const int nc = nix * niy * nit;
+    const double vol = (box[1] - box[0]) * (box[3] - box[2]) * (box[5] - box[4]) / (double)nc;
+    double mass = 0.0;
+    for (int c = 0; c < nc; ++c) mass += rho[c] * vol;
+    for (int c = 0; c < nc; ++c) lam_cell[c] = (double)n * rho[c] / mass;
+}
+
+/* Realization `sim` of n points drawn independently with density proportional
+ * to rho.  Point i: a cell with probability rho_c / sum rho (cells have equal
+ * volumes), then a uniform position inside it.  The cell is the first c whose
+ * running sum cum_c = rho_0 + ... + rho_c (added in cell order) exceeds
+ * u * cum_last, u the 53-bit uniform of Philox block (i, sim, 40, i >> 32); if
+ * rounding leaves no such c, the last cell with rho > 0.  Inside cell
+ * (ix, iy, it): x = x0 + (x1 - x0) * ((ix + u_x) / nix), clamped to x1, u_x
+ * the uniform of stream 0 (y: stream 1, t: stream 2), as the CSR coordinates.
+ * With one cell this is exactly the CSR realization. */
+void oracle_inhom_points(int64_t n, const double box[6], const double* rho, int nix, int niy,
+                         int nit, uint64_t seed, uint32_t sim, double* x, double* y, double* t,
+                         int32_t* cell) {
+    const int nc = nix * niy * nit;
+    double* cum = (double*)malloc(sizeof(double) * (size_t)nc);
+    double run = 0.0;
+    int last_pos = 0;
+    for (int c = 0; c < nc; ++c) {
+        run += rho[c];
+        cum[c] = run;
+        if (rho[c] > 0.0) last_pos = c;
+    }
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t w[4];
+        const uint32_t ctr[4] = {(uint32_t)i, sim, 40u, (uint32_t)((uint64_t)i >> 32)};
+        oracle_philox4x32_10(ctr, key, w);
+        const double target = oracle_u01(w[0], w[1]) * cum[nc - 1];
+        int c = last_pos;
+        for (int q = 0; q < nc; ++q) {
+            if (cum[q] > target) {
+                c = q;
+                break;
+            }
+        }
+        const int ix = c % nix, iy = (c / nix) % niy, it = c / (nix * niy);
+        const double lo[3] = {box[0], box[2], box[4]}, hi[3] = {box[1], box[3], box[5]};
+        const int idx[3] = {ix, iy, it}, cnt[3] = {nix, niy, nit};
+        double out[3];
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t ctr2[4] = {(uint32_t)i, sim, (uint32_t)a, (uint32_t)((uint64_t)i >> 32)};
+            oracle_philox4x32_10(ctr2, key, w);
+            const double u = oracle_u01(w[0], w[1]);
+            double v = lo[a] + (hi[a] - lo[a]) * (((double)idx[a] + u) / (double)cnt[a]);
+            if (v > hi[a]) v = hi[a];
+            out[a] = v;
+        }
+        x[i] = out[0];
+        y[i] = out[1];
+        t[i] = out[2];
+        if (cell) cell[i] = c;
+    }
+    free(cum);
+}
+
+/* Non-cumulative histograms of the inhomogeneous double sum: cnt as in
+ * oracle_pair_hist, wsum of I / (w v lambda_i lambda_j) with lam[i] the
+ * intensity at point i.  centre_mask as in oracle_pair_hist. */
+int64_t oracle_pair_hist_inhom(int64_t n, const double* x, const double* y, const double* t,
+                               const double* lam, const double box[6], const double* s, int cs,
+                               const double* tt, int ct, int edge_mode,
+                               const uint8_t* centre_mask, int64_t* cnt, double* wsum) {
+    const int nb = cs * ct;
+    double* s2 = (double*)malloc(sizeof(double) * (size_t)cs);
+    double* comp = (double*)calloc((size_t)nb, sizeof(double));
+    for (int a = 0; a < cs; ++a) s2[a] = s[a] * s[a];
+    for (int k = 0; k < nb; ++k) {
+        cnt[k] = 0;
+        wsum[k] = 0.0;
+    }
+    const double s2max = s2[cs - 1], tmax = tt[ct - 1];
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (centre_mask && !centre_mask[i]) continue;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = x[i] - x[j];
+            const double dy = y[i] - y[j];
+            const double d2 = dx * dx + dy * dy;
+            if (d2 > s2max) continue;
+            const double u = fabs(t[i] - t[j]);
+            if (u > tmax) continue;
+            int a = 0;
+            while (d2 > s2[a]) ++a;
+            int b = 0;
+            while (u > tt[b]) ++b;
+            double om = 1.0, v = 1.0;
+            if (edge_mode == 1) {
+                om = oracle_spatial_weight(x[i], y[i], sqrt(d2), box);
+                v = oracle_temporal_weight(t[i], u, box[4], box[5]);
+            }
+            const double w = 1.0 / (om * v * lam[i] * lam[j]);
+            const int k = a * ct + b;
+            cnt[k] += 1;
+            const double yk = w - comp[k];
+            const double tk = wsum[k] + yk;
+            comp[k] = (tk - wsum[k]) - yk;
+            wsum[k] = tk;
+            ++total;
+        }
+    }
+    free(s2);
+    free(comp);
+    return total;
+}
+
+/* Cumulative grids of the inhomogeneous estimator from its non-cumulative
+ * histograms; S and K as described above, L by Eq. 4. */
+void oracle_finalize_inhom(int64_t n, const double box[6], const double* s, int cs,
+                           const double* tt, int ct, int norm, const int64_t* cnt,
+                           const double* wsum, int64_t* C, double* S, double* K, double* L) {
+    const double ad = (box[1] - box[0]) * (box[3] - box[2]) * (box[5] - box[4]);
+    const double nn = (double)n;
+    const double kcoef = (norm == 1) ? 1.0 / ad : nn / ((nn - 1.0) * ad);
+    const double lbar = nn / ad;
+    for (int a = 0; a < cs; ++a) {
+        for (int b = 0; b < ct; ++b) {
+            int64_t c = 0;
+            double w = 0.0;
+            for (int a2 = 0; a2 <= a; ++a2)
+                for (int b2 = 0; b2 <= b; ++b2) {
+                    c += cnt[a2 * ct + b2];
+                    w += wsum[a2 * ct + b2];
+                }
+            const int k = a * ct + b;
+            const double kv = kcoef * w;
+            if (C) C[k] = c;
+            if (S) S[k] = w * lbar * lbar;
+            if (K) K[k] = kv;
+            if (L) L[k] = sqrt(kv / (2.0 * ORACLE_PI * tt[b])) - s[a];
+        }
+    }
+}

@@ -123,6 +123,24 @@ int oracle_envelope(int64_t n, const double box[6], const double* s, int cs,
                     uint64_t seed, double* K_lo, double* K_hi, double* L_lo,
                     double* L_hi, double* K_all);
 
+/* Inhomogeneous K (Section 7 future work): relative intensity rho on
+ * nix x niy x nit equal cells of the box ([nit][niy][nix], x fastest), scaled
+ * to integrate to n; see the source for the estimator and its readings. */
+int oracle_intensity_cell(const double box[6], int nix, int niy, int nit, double x, double y,
+                          double t);
+void oracle_intensity_lambda(const double* rho, int nix, int niy, int nit, const double box[6],
+                             int64_t n, double* lam_cell);
+void oracle_inhom_points(int64_t n, const double box[6], const double* rho, int nix, int niy,
+                         int nit, uint64_t seed, uint32_t sim, double* x, double* y, double* t,
+                         int32_t* cell);
+int64_t oracle_pair_hist_inhom(int64_t n, const double* x, const double* y, const double* t,
+                               const double* lam, const double box[6], const double* s, int cs,
+                               const double* tt, int ct, int edge_mode,
+                               const uint8_t* centre_mask, int64_t* cnt, double* wsum);
+void oracle_finalize_inhom(int64_t n, const double box[6], const double* s, int cs,
+                           const double* tt, int ct, int norm, const int64_t* cnt,
+                           const double* wsum, int64_t* C, double* S, double* K, double* L);
+
 #ifdef __cplusplus
 }
 #endif
