@@ -418,6 +418,29 @@ def run_ours(args):
                    "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
                    "fp64_queue_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
 
+    # the inhomogeneous K (intensity-weighted pairs, FP64 throughout) on the Thomas pattern with
+    # a histogram intensity, observed + 99 intensity-weighted simulations
+    inhom = None
+    if args.inhom and rank == 0:
+        wi = _workload("thomas_inhom_n200k")
+        with stk.Pattern(wi.x, wi.y, wi.t, wi.box) as pi_:
+            pi_.set_intensity(wi.meta["rho"])
+            stk.stk_set_stream(pi_.h, stream)
+            pi_.run(wi.s, wi.tt, n_sims=wi.n_sims, seed=seed, exec_mode=exec_mode)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pi_.run(wi.s, wi.tt, n_sims=wi.n_sims, seed=seed, exec_mode=exec_mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_i = e0.elapsed_time(e1)
+            si = pi_.stats()
+        inhom = {"workload": wi.name, "n": wi.n, "intensity_cells": list(wi.meta["rho"].shape),
+                 "sims": wi.n_sims, "dtype": "f64", "job_s": ms_i / 1e3,
+                 "sims_per_s": wi.n_sims / (ms_i / 1e3),
+                 "value": si["qualifying_pairs"] / (ms_i / 1e3), "unit": UNIT,
+                 "pair_kernel_s": si["ms_pair"] / 1e3}
+
     if rank != 0:
         stk.stk_destroy(h)
         if ws > 1:
@@ -465,6 +488,7 @@ def run_ours(args):
         "serve": serve,
         "sim_methods": methods,
         "polygon": polygon,
+        "inhomogeneous": inhom,
     }
     print(json.dumps(line), flush=True)
     stk.stk_destroy(h)
@@ -496,6 +520,8 @@ def build_parser():
                     help="also time the job with permutation and bootstrap simulations")
     ap.add_argument("--polygon", type=int, default=1,
                     help="also time a job over an 85-vertex polygon study area")
+    ap.add_argument("--inhom", type=int, default=1,
+                    help="also time an inhomogeneous-K job (intensity-weighted, FP64)")
     return ap
 
 

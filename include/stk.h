@@ -105,6 +105,31 @@ int stk_create_device(const double* d_x, const double* d_y, const double* d_t, i
  * STK_EDOMAIN, STK_ENOMEM, STK_ECUDA. */
 int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv);
 
+/* Inhomogeneous K (the variant Section 7 lists as future work): subsequent jobs on h divide
+ * every ordered pair by the intensities at both of its points.  rho is a caller-owned host
+ * array of nix * niy * nit relative intensities, piecewise constant on that many equal cells
+ * of the box, row-major [nit][niy][nix] (x fastest); only its shape matters: the intensity is
+ * lambda_c = n rho_c / sum_c(rho_c V), V the cell volume, so that it integrates to n.  A
+ * point (x, y, t) lies in cell floor(((x - x0) / (x1 - x0)) * nix) (each operation rounded
+ * separately, clamped to [0, nix - 1]), and likewise along y and t.  The estimator is
+ *   K_I(s, t) = n / ((n - 1) A D) * sum_{i != j} I(d_ij <= s, u_ij <= t) / (w_ij v_ij lambda_i lambda_j)
+ * (1 / (A D) with STK_NORM_N2), Eq. 2 when rho is constant; raw_sum reports that sum times
+ * (n / (A D))^2, so K = raw_sum * A D / (n (n - 1)) as in Eq. 2, and L follows Eq. 4.  Every
+ * pair is evaluated in FP64 whatever `prec` asks (the K tolerance is that of STK_PREC_FP64;
+ * counts are exact).  Simulations: STK_SIM_CSR draws n points independently with density
+ * proportional to rho (cell i of a point: the first whose running sum of rho exceeds u times
+ * the total, u from Philox block (i, sim, 40, i >> 32); the position inside the cell from the
+ * CSR streams 0, 1, 2: x = x0 + (x1 - x0) * ((cell x index + u_x) / nix)), and each point
+ * takes the intensity of its cell; with one cell this is the CSR realization.  Bootstrap and
+ * permutation realizations take the intensity of the cell each point lies in; permutations
+ * need rho > 0 in every cell.  Requires rho finite and >= 0 with a positive sum, every
+ * positive rho_c within 2^14 times the mean of rho either way, 1 <= cells <= 2^22, and every
+ * observed point in a cell with rho > 0 (else STK_EDOMAIN, the handle unchanged).  Cannot be
+ * combined with a polygon study area or with labels (cross K).  rho = NULL or nix = 0
+ * restores the homogeneous estimator.  Errors: STK_EINVAL, STK_EDOMAIN, STK_ENOMEM,
+ * STK_ECUDA. */
+int stk_set_intensity(stk_handle* h, const double* rho, int nix, int niy, int nit);
+
 /* Run this handle's device work on `stream` (a cudaStream_t); NULL restores
  * the handle's own stream. */
 int stk_set_stream(stk_handle* h, void* stream);
@@ -208,6 +233,13 @@ int stk_sim_points(const stk_box* box, int64_t n, uint64_t seed, uint32_t sim, d
 int stk_sim_points_polygon(const stk_box* box, const double* vx, const double* vy, int nv,
                            int64_t n, uint64_t seed, uint32_t sim, double* x, double* y,
                            double* t);
+
+/* One realization of the intensity-weighted simulation of stk_set_intensity (n points with
+ * density proportional to rho over `box`), generated by the device generator the jobs use,
+ * copied to caller-owned host arrays x, y, t [n].  Errors: STK_EINVAL. */
+int stk_sim_points_inhom(const stk_box* box, const double* rho, int nix, int niy, int nit,
+                         int64_t n, uint64_t seed, uint32_t sim, double* x, double* y,
+                         double* t);
 
 /* One random-permutation or bootstrap realization (method STK_SIM_PERMUTATION or
  * STK_SIM_BOOTSTRAP, Section 3) of the observed host points x0, y0, t0 [n], generated by

@@ -110,6 +110,9 @@ def load(build_if_missing: bool = False):
         "stk_sim_points_polygon": ([ctypes.POINTER(stk_box), _P, _P, i32, i64, u64, u32, _P, _P,
                                     _P], i32),
         "stk_set_polygon": ([_P, _P, _P, i32], i32),
+        "stk_set_intensity": ([_P, _P, i32, i32, i32], i32),
+        "stk_sim_points_inhom": ([ctypes.POINTER(stk_box), _P, i32, i32, i32, i64, u64, u32,
+                                  _P, _P, _P], i32),
         "stk_k_noalloc": ([_P, _P, _P, i64, ctypes.POINTER(stk_box), _P, i32, _P, i32, i32, _P,
                            _P, _P, _P, _P], i32),
         "stk_server_create": ([ctypes.POINTER(stk_server_config), PP], i32),
@@ -269,6 +272,34 @@ def stk_set_polygon(h, vx=None, vy=None):
         return
     vx, vy = _f64(vx), _f64(vy)
     _check(load().stk_set_polygon(h, _ptr(vx), _ptr(vy), vx.shape[0]))
+
+
+def _rho3(rho):
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    if r.ndim != 3:
+        raise ValueError("rho must be a 3-D array indexed [t][y][x]")
+    return r
+
+
+def stk_set_intensity(h, rho=None):
+    """Relative intensity rho[nit, niy, nix] over the box for the inhomogeneous K of later jobs
+    on h (None: back to the homogeneous estimator)."""
+    if rho is None:
+        _check(load().stk_set_intensity(h, None, 0, 0, 0))
+        return
+    r = _rho3(rho)
+    _check(load().stk_set_intensity(h, _ptr(r), r.shape[2], r.shape[1], r.shape[0]))
+
+
+def stk_sim_points_inhom(box, rho, n, seed, sim):
+    """Realization `sim` of the intensity-weighted simulation (device generator), copied back
+    to the host."""
+    r = _rho3(rho)
+    x, y, t = (np.zeros(n) for _ in range(3))
+    b = _box(box)
+    _check(load().stk_sim_points_inhom(ctypes.byref(b), _ptr(r), r.shape[2], r.shape[1],
+                                       r.shape[0], n, seed, sim, _ptr(x), _ptr(y), _ptr(t)))
+    return x, y, t
 
 
 def stk_sim_points_polygon(box, vx, vy, n, seed, sim):
@@ -454,6 +485,10 @@ class Pattern:
 
     def set_polygon(self, vx=None, vy=None):
         stk_set_polygon(self.h, vx, vy)
+
+    def set_intensity(self, rho=None):
+        """Inhomogeneous K from now on, with relative intensity rho[nit, niy, nix]."""
+        stk_set_intensity(self.h, rho)
 
     def close(self):
         if self.h:

@@ -175,6 +175,89 @@ __global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ se
     }
 }
 
+// ---------------------------------------------------------------------------- intensity
+// Inhomogeneous K (Section 7 future work): the relative intensity rho is piecewise constant on
+// nix x niy x nit equal cells of the box.  Cell of v along one axis:
+// floor(((v - lo) / (hi - lo)) * nc), each operation rounded separately, clamped to the axis.
+__device__ __forceinline__ int intensity_axis(double v, double lo, double hi, int nc) {
+    const double f = floor(__dmul_rn(__ddiv_rn(__dsub_rn(v, lo), __dsub_rn(hi, lo)), (double)nc));
+    return (int)fmax(0.0, fmin(f, (double)(nc - 1)));
+}
+
+struct IntensityBox {
+    double x0, x1, y0, y1, t0, t1;
+};
+
+__global__ void intensity_lookup_kernel(const double* __restrict__ x,
+                                        const double* __restrict__ y,
+                                        const double* __restrict__ t, int64_t count,
+                                        IntensityBox b, Intensity in, double* __restrict__ h,
+                                        unsigned long long* __restrict__ zero) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = intensity_axis(x[i], b.x0, b.x1, in.nix);
+        const int iy = intensity_axis(y[i], b.y0, b.y1, in.niy);
+        const int it = intensity_axis(t[i], b.t0, b.t1, in.nit);
+        const double v = in.hcell[((int64_t)it * in.niy + iy) * in.nix + ix];
+        h[i] = v;
+        if (v == 0.0) atomicAdd(zero, 1ull);
+    }
+}
+
+// Point i of a realization: cell c = the first whose running sum of rho exceeds u * total
+// (u from Philox block (i, sim, 40, i >> 32); the last cell with rho > 0 when rounding leaves
+// none), then lo + (hi - lo) * ((cell index + u_axis) / cells on the axis), u_axis the uniform
+// of the CSR coordinate stream of that axis.  One cell gives exactly the CSR realization.
+__global__ void gen_inhom_kernel(int64_t n, int m, const uint64_t* __restrict__ seeds,
+                                 const uint32_t* __restrict__ sims, GridDev g, double x1,
+                                 double y1, double t1, int64_t ncells, Intensity in,
+                                 double* __restrict__ x, double* __restrict__ y,
+                                 double* __restrict__ t, double* __restrict__ h,
+                                 uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
+                                 uint32_t* __restrict__ cnt) {
+    const int64_t total = n * (int64_t)m;
+    const int cells = in.nix * in.niy * in.nit;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / n);
+        const int64_t i = gi - (int64_t)k * n;
+        const uint32_t sim = sims[k];
+        const uint64_t seed = seeds[k];
+        const uint2 kk2 = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)i, sim, 40u, (uint32_t)((uint64_t)i >> 32)), kk2);
+        const double target = __dmul_rn(u01(w.x, w.y), in.total);
+        int lo = 0, hi = cells;  // first c with cum[c] > target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (in.cum[mid] > target)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const int c = lo < cells ? lo : in.last_pos;
+        const int ix = c % in.nix, iy = (c / in.nix) % in.niy, it = c / (in.nix * in.niy);
+        const double b0[3] = {g.x0, g.y0, g.t0}, b1[3] = {x1, y1, t1};
+        const int idx[3] = {ix, iy, it}, nc[3] = {in.nix, in.niy, in.nit};
+        double v[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const uint4 wa = philox4x32_10(
+                make_uint4((uint32_t)i, sim, (uint32_t)a, (uint32_t)((uint64_t)i >> 32)), kk2);
+            const double q = __ddiv_rn(__dadd_rn((double)idx[a], u01(wa.x, wa.y)), (double)nc[a]);
+            const double c1 = __dadd_rn(b0[a], __dmul_rn(__dsub_rn(b1[a], b0[a]), q));
+            v[a] = c1 > b1[a] ? b1[a] : c1;
+        }
+        x[gi] = v[0];
+        y[gi] = v[1];
+        t[gi] = v[2];
+        h[gi] = in.hcell[c];
+        const uint32_t kk = key_of(g, v[0], v[1], v[2]);
+        key[gi] = kk;
+        rank[gi] = atomicAdd(&cnt[(int64_t)k * ncells + kk], 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------- resampling
 // Bootstrapping (Section 3): point i of a realization is observed point floor(u n), u the
 // 53-bit uniform of Philox block (i, sim, 4, i >> 32), a product that rounds up to n taken
@@ -335,7 +418,8 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
                                const uint8_t* __restrict__ mask_in, double* __restrict__ X,
                                double* __restrict__ Y, double* __restrict__ T,
                                float4* __restrict__ P, float2* __restrict__ Plo,
-                               uint8_t* __restrict__ mask_out) {
+                               uint8_t* __restrict__ mask_out,
+                               const double* __restrict__ h_in, double* __restrict__ H) {
     // P holds two float4 per point: (x_hi, y_hi, t_hi, cell x) and (e_x, e_y, e_t, rin2):
     // distances to the nearer x edge, y edge and end of the period, and a bound on d2 below
     // which the circle around the point stays clear of every edge (interior: weight 1)
@@ -376,6 +460,7 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         P[2 * pos + 1] = make_float4(ex, ey, te, rin * rin * 0.99999f);
         Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
         if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)k * n];
+        if (H) H[pos] = h_in[gi];
     }
 }
 
@@ -535,7 +620,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
                            float tan_rel, float tan_abs, float fast_abs, cudaStream_t st,
-                           Polygon poly, bool mask_all) {
+                           Polygon poly, bool mask_all, const double* h_in, double* H) {
     ScatterGrid s;
     s.poly = poly;
     s.mask_all = mask_all ? 1 : 0;
@@ -561,7 +646,33 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
     s.inv_qt = 1.0 / (double)g.qt;
     scatter_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
         m, n, g.ncells, s, x, y, t, key, rank, start_global, mask_in, X, Y, T, P, Plo,
-        mask_in ? mask_out : nullptr);
+        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_lookup(const double* x, const double* y, const double* t,
+                                    int64_t count, const double box[6], Intensity in, double* h,
+                                    unsigned long long* zero, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    IntensityBox b;
+    b.x0 = box[0];
+    b.x1 = box[1];
+    b.y0 = box[2];
+    b.y1 = box[3];
+    b.t0 = box[4];
+    b.t1 = box[5];
+    intensity_lookup_kernel<<<grid_for(count, kThreads), kThreads, 0, st>>>(x, y, t, count, b,
+                                                                            in, h, zero);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_inhom(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
+                             const Grid& g, Intensity in, double* x, double* y, double* t,
+                             double* h, uint32_t* key, uint32_t* rank, uint32_t* cell_count,
+                             cudaStream_t st) {
+    gen_inhom_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        n, m, seeds, sims, grid_dev(g), g.x1, g.y1, g.t1, g.ncells, in, x, y, t, h, key, rank,
+        cell_count);
     return cudaGetLastError();
 }
 

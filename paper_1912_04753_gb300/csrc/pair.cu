@@ -812,8 +812,38 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
 
 struct WarpSm64 {
     double cx[32], cy[32], ct[32];
+    double ch[32];       // inhomogeneous K: h of the centres
     uint2 ring[kRing];   // (lane, neighbour)
 };
+
+// Inhomogeneous K: a pair weight W = h_i h_j / (w v) in fixed point, split so that every part is
+// a plain integer sum: the whole part, and the fraction in units of 2^-64 as two 32-bit halves.
+// W < 2^32 (h is at most 2^14 and 1 / (w v) at most 8).
+struct Fix96 {
+    unsigned long long whole = 0, lo = 0, hi = 0;
+};
+
+__device__ __forceinline__ void add_fix96(double W, Fix96& f) {
+    const double wh = floor(W);
+    const unsigned long long m = __double2ull_rn(__dsub_rn(W, wh) * 18446744073709551616.0);
+    f.whole += (unsigned long long)wh;
+    f.lo += m & 0xffffffffull;
+    f.hi += m >> 32;
+}
+
+// Adds a replica's sums to the global accumulators: lo (2^-64 units) and hi (2^-32 units) are
+// re-split so that each global add is below 2^32 (no overflow however many flushes).
+__device__ __forceinline__ void add_fix96_global(const Accum& acc, int64_t o,
+                                                 unsigned long long whole,
+                                                 unsigned long long lo,
+                                                 unsigned long long hi) {
+    const unsigned long long g_lo = lo & 0xffffffffull;
+    const unsigned long long g_hi = (lo >> 32) + (hi & 0xffffffffull);
+    const unsigned long long g_whole = whole + (hi >> 32);
+    if (g_lo) atomicAdd(&acc.exc_lo[o], g_lo);
+    if (g_hi) atomicAdd(&acc.exc_hi[o], g_hi);
+    if (g_whole) atomicAdd(&acc.whole[o], g_whole);
+}
 
 struct Smem64 {
     PairConsts pc;
@@ -821,12 +851,13 @@ struct Smem64 {
 };
 
 // Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
-template <bool POLY>
+template <bool POLY, bool INH>
 __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
                                           int lane, const double* X, const double* Y,
-                                          const double* T, const uint8_t* mk, uint32_t onA,
-                                          uint32_t onB,
+                                          const double* T, const double* H, const uint8_t* mk,
+                                          uint32_t onA, uint32_t onB,
                                           uint32_t* hc, unsigned long long* he,
+                                          unsigned long long* hf, unsigned long long* hw,
                                           unsigned long long* stats) {
     if (lane >= cnt) return;
     const uint2 e = ws.ring[lane];
@@ -851,18 +882,77 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     const uint32_t fj = mk == nullptr ? 3u : (uint32_t)mk[e.y];
     const bool act_i = mk == nullptr || (((onA >> e.x) & 1u) && (fj & 2u));
     const bool act_j = mk == nullptr || ((fj & 1u) && ((onB >> e.x) & 1u));
+    const int bin = a * pc.ct + b;
+    if (INH) {
+        // Section 7 inhomogeneous variant: each order weighted by h_i h_j / (w v)
+        const double hh = __dmul_rn(ws.ch[e.x], H[e.y]);
+        double wi = 1.0, wj = 1.0;
+        if (pc.edge) {
+            const double r = __dsqrt_rn(d2);
+            wi = 1.0 / (omega64<POLY>(pc, xi, yi, r) * v64(pc, ti, u));
+            wj = 1.0 / (omega64<POLY>(pc, xj, yj, r) * v64(pc, tj, u));
+        }
+        Fix96 f;
+        if (act_i) add_fix96(__dmul_rn(wi, hh), f);
+        if (act_j) add_fix96(__dmul_rn(wj, hh), f);
+        atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
+        if (f.lo) atomicAdd(&he[bin], f.lo);
+        if (f.hi) atomicAdd(&hf[bin], f.hi);
+        if (f.whole) atomicAdd(&hw[bin], f.whole);
+        return;
+    }
     unsigned long long exc = 0;
     if (pc.edge) {
         const double r = __dsqrt_rn(d2);
         if (act_i) exc += excess_fixed64(1.0 / (omega64<POLY>(pc, xi, yi, r) * v64(pc, ti, u)));
         if (act_j) exc += excess_fixed64(1.0 / (omega64<POLY>(pc, xj, yj, r) * v64(pc, tj, u)));
     }
-    const int bin = a * pc.ct + b;
     atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
     if (exc) atomicAdd(&he[bin], exc);
 }
 
-template <bool POLY>
+// Inhomogeneous K: flushes of the three fixed-point sums (see flush_hist and warp_flush).
+__device__ __forceinline__ void flush_hist_inh(int real, int nbins, int reps, uint32_t* hc,
+                                               unsigned long long* he, unsigned long long* hf,
+                                               unsigned long long* hw, const Accum& acc) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += kBlock) {
+        uint32_t c = 0;
+        unsigned long long lo = 0, hi = 0, wh = 0;
+        for (int r = 0; r < reps; ++r) {
+            const int i = r * nbins + b;
+            c += hc[i];
+            lo += he[i];
+            hi += hf[i];
+            wh += hw[i];
+            hc[i] = 0;
+            he[i] = 0;
+            hf[i] = 0;
+            hw[i] = 0;
+        }
+        const int64_t o = (int64_t)real * nbins + b;
+        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
+        add_fix96_global(acc, o, wh, lo, hi);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void warp_flush_inh(int real, int nbins, uint32_t* hc,
+                                               unsigned long long* he, unsigned long long* hf,
+                                               unsigned long long* hw, const Accum& acc,
+                                               int lane) {
+    for (int b = lane; b < nbins; b += 32) {
+        const uint32_t c = atomicExch(&hc[b], 0u);
+        const unsigned long long lo = atomicExch(&he[b], 0ull);
+        const unsigned long long hi = atomicExch(&hf[b], 0ull);
+        const unsigned long long wh = atomicExch(&hw[b], 0ull);
+        const int64_t o = (int64_t)real * nbins + b;
+        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
+        add_fix96_global(acc, o, wh, lo, hi);
+    }
+}
+
+template <bool POLY, bool INH>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
@@ -881,14 +971,24 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
     WarpSm64& ws = sm.w[warp];
     const int nbins = pc.nbins;
     const size_t hist_off = (sizeof(Smem64) + 15) & ~size_t(15);
+    // per replica: he [nbins] u64 (excess; inhomogeneous: fraction low halves), then for the
+    // inhomogeneous K hf (fraction high halves) and hw (whole parts), then hc [nbins] u32
     unsigned long long* he = reinterpret_cast<unsigned long long*>(smem_raw + hist_off);
-    uint32_t* hc = reinterpret_cast<uint32_t*>(he + (size_t)reps * nbins);
+    unsigned long long* hf = he + (size_t)reps * nbins;
+    unsigned long long* hw = hf + (size_t)reps * nbins;
+    uint32_t* hc = reinterpret_cast<uint32_t*>(INH ? hw + (size_t)reps * nbins : hf);
     for (int i = tid; i < reps * nbins; i += kBlock) {
         hc[i] = 0;
         he[i] = 0;
+        if (INH) {
+            hf[i] = 0;
+            hw[i] = 0;
+        }
     }
     uint32_t* my_hc = hc + (warp % reps) * nbins;
     unsigned long long* my_he = he + (warp % reps) * nbins;
+    unsigned long long* my_hf = hf + (warp % reps) * nbins;
+    unsigned long long* my_hw = hw + (warp % reps) * nbins;
     const int64_t n = rb.n;
     const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
     const int64_t nrows = (int64_t)ny * nt;
@@ -905,6 +1005,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
         const double* X = rb.X + base;
         const double* Y = rb.Y + base;
         const double* T = rb.T + base;
+        const double* H = INH ? rb.H + base : nullptr;
         const uint8_t* mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
                                 ? rb.mask + (rb.mask_all ? (int64_t)k * rb.n : 0)
                                 : nullptr;
@@ -921,6 +1022,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             ws.cx[lane] = xi;
             ws.cy[lane] = yi;
             ws.ct[lane] = ti;
+            if (INH) ws.ch[lane] = H[ci];
             const int cx = __float_as_int(rb.P[2 * (base + ci)].w);
             const uint32_t fl = mk == nullptr ? 3u : (uint32_t)mk[ci];
             const uint32_t onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
@@ -954,8 +1056,8 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         tail += __popc(mq);
                         if (tail >= 32u) {
                             __syncwarp();
-                            process64<POLY>(pc, ws, 32, lane, X, Y, T, mk, onA, onB, my_hc, my_he,
-                                      acc.stats);
+                            process64<POLY, INH>(pc, ws, 32, lane, X, Y, T, H, mk, onA, onB,
+                                                 my_hc, my_he, my_hf, my_hw, acc.stats);
                             __syncwarp();
                             if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
                             __syncwarp();
@@ -966,15 +1068,21 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             }
             __syncwarp();
             if (tail > 0)
-                process64<POLY>(pc, ws, (int)tail, lane, X, Y, T, mk, onA, onB, my_hc, my_he,
-                                acc.stats);
+                process64<POLY, INH>(pc, ws, (int)tail, lane, X, Y, T, H, mk, onA, onB, my_hc,
+                                     my_he, my_hf, my_hw, acc.stats);
             __syncwarp();
             if (since_flush >= kWarpFlush) {
-                warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);
+                if (INH)
+                    warp_flush_inh(k, nbins, my_hc, my_he, my_hf, my_hw, acc, lane);
+                else
+                    warp_flush(k, nbins, my_hc, nullptr, my_he, acc, lane);
                 since_flush = 0;
             }
         }
-        flush_hist(k, nbins, reps, hc, he, acc);
+        if (INH)
+            flush_hist_inh(k, nbins, reps, hc, he, hf, hw, acc);
+        else
+            flush_hist(k, nbins, reps, hc, he, acc);
         since_flush = 0;
     }
     for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
@@ -1024,6 +1132,7 @@ __global__ void finalize_kernel(int cs, int ct, const double* __restrict__ s,
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         cc[i] = acc.cnt[o + i];
         ee[i] = ((unsigned __int128)acc.exc_hi[o + i] << 32) + (unsigned __int128)acc.exc_lo[o + i];
+        if (acc.whole) ee[i] += (unsigned __int128)acc.whole[o + i] << 64;
     }
     __syncthreads();
     if (threadIdx.x == 0) cc[0] -= (unsigned long long)self_pairs[k];  // (i, i) lands in bin (0, 0)
@@ -1045,9 +1154,15 @@ __global__ void finalize_kernel(int cs, int ct, const double* __restrict__ s,
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         const int a = i / ct, b = i - (i / ct) * ct;
         const unsigned __int128 e = ee[i];
-        const double ed = (double)(unsigned long long)(e >> 64) * 18446744073709551616.0 +
-                          (double)(unsigned long long)e;
-        const double sv = (double)cc[i] + ed * (1.0 / 4294967296.0);
+        double sv;
+        if (acc.whole) {  // inhomogeneous K: the weights themselves, in units of 2^-64
+            sv = (double)(unsigned long long)(e >> 64) +
+                 (double)(unsigned long long)e * (1.0 / 18446744073709551616.0);
+        } else {
+            const double ed = (double)(unsigned long long)(e >> 64) * 18446744073709551616.0 +
+                              (double)(unsigned long long)e;
+            sv = (double)cc[i] + ed * (1.0 / 4294967296.0);
+        }
         const double kv = coef * sv;
         if (K) K[o + i] = kv;
         if (L) L[o + i] = sqrt(kv / (2.0 * 3.141592653589793 * tt[b])) - s[a];
@@ -1091,7 +1206,14 @@ size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
 size_t pair_fp32_smem(int nbins, int* reps) {
     return smem_with_reps(sizeof(Smem32), nbins, reps, 56 * 1024);
 }
-size_t pair_fp64_smem(int nbins, int* reps) {
+size_t pair_fp64_smem(int nbins, int* reps, bool inh) {
+    if (inh) {  // three u64 sums and a u32 count per bin and replica
+        const size_t b = (sizeof(Smem64) + 15) & ~size_t(15);
+        int r = 8;
+        while (r > 1 && b + (size_t)r * nbins * 32 > 72 * 1024) --r;
+        *reps = r;
+        return b + (size_t)r * nbins * 32;
+    }
     return smem_with_reps(sizeof(Smem64), nbins, reps, 72 * 1024);
 }
 
@@ -1120,11 +1242,16 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(pair_fp64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem64);
+    e = cudaFuncSetAttribute(pair_fp64_kernel<true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pair_fp64_kernel<false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+    e = cudaFuncSetAttribute(pair_fp64_kernel<false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+    if (e != cudaSuccess) return e;
+    const size_t smem_inh = std::max<size_t>(
+        72 * 1024, ((sizeof(Smem64) + 15) & ~size_t(15)) + (size_t)kMaxThr * kMaxThr * 32);
+    return cudaFuncSetAttribute(pair_fp64_kernel<false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inh);
 }
 
 int pair_fp32_blocks_per_sm(size_t smem) {
@@ -1136,12 +1263,14 @@ int pair_fp32_blocks_per_sm(size_t smem) {
     return b > 0 ? b : 1;
 }
 
-int pair_fp64_blocks_per_sm(size_t smem) {
+int pair_fp64_blocks_per_sm(size_t smem, bool inh) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false>, kBlock,
-                                                      smem) !=
-        cudaSuccess)
-        return 1;
+    const cudaError_t e =
+        inh ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false, true>,
+                                                            kBlock, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false, false>,
+                                                            kBlock, smem);
+    if (e != cudaSuccess) return 1;
     return b > 0 ? b : 1;
 }
 
@@ -1181,13 +1310,18 @@ cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum a
 
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly) {
-    if (poly)
-        pair_fp64_kernel<true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters,
-                                                           acc, reps);
+                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly,
+                             bool inh) {
+    if (inh && (poly || rb.H == nullptr || acc.whole == nullptr)) return cudaErrorInvalidValue;
+    if (inh)
+        pair_fp64_kernel<false, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                  counters, acc, reps);
+    else if (poly)
+        pair_fp64_kernel<true, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                  counters, acc, reps);
     else
-        pair_fp64_kernel<false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
-                                                            counters, acc, reps);
+        pair_fp64_kernel<false, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
+                                                                   counters, acc, reps);
     return cudaGetLastError();
 }
 

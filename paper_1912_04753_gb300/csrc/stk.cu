@@ -113,13 +113,23 @@ struct stk_handle {
     int nv = 0;
     int poly_ccw = 1;
     double area = 0.0;
+    // inhomogeneous K: the relative intensity (device tables hcell and cum, [2][cells]), h of
+    // the observed points in input order, and the per-wave h arrays (unsorted, sorted) and
+    // whole-part accumulators
+    DevBuf inh, inh_obs, uh, Hs, acc_whole;
+    Intensity inten;    // inten.nix = 0: none
+    int inh_zero = 0;   // some cell has rho = 0
+    uint64_t inh_gen = 0;
 };
 
 namespace {
 
 bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
 
-bool fp32_path(const stk_request* q) { return q->prec == STK_PREC_FP32_GUARDED; }
+// The FP32-guarded pair kernel, unless the job is an inhomogeneous K (always FP64).
+bool fp32_path(const stk_handle* h, const stk_request* q) {
+    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0;
+}
 
 int check_box(const stk_box* b) {
     if (!b) return fail(STK_EINVAL, "box is NULL");
@@ -194,14 +204,16 @@ unsigned int exact_queue_cap(int64_t points) {
 
 // Device bytes of a job: `per_real` for every realization resident in a wave, `fixed` for the
 // job's output rows and constants.
-Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool fp32) {
+Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool fp32,
+                    bool inh = false) {
     const size_t ncells = (size_t)g.ncells, nrows = (size_t)g.ny * g.nt, un = (size_t)n;
     Footprint f;
     // unsorted + keys/ranks + sorted FP64 + FP32 records + low parts; counts, starts, cell
     // starts, scan scratch; work counts/offsets and units; histograms; seeds; FP64 queue
     f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
-                 8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */;
+                 8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
+                 (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 32 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
               16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
@@ -214,7 +226,8 @@ size_t workspace_bytes(const stk_handle* h) {
                             &h->Plo, &h->cell_start, &h->chunks, &h->chunk_off, &h->items,
                             &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                             &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
-                            &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid};
+                            &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh,
+                            &h->Hs, &h->acc_whole};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     return b;
@@ -328,6 +341,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         return fail(STK_EINVAL, "cross K takes CSR or permutation simulations");
     if (q->labels && (q->cross_a < 0 || q->cross_a > 255 || q->cross_b < 0 || q->cross_b > 255))
         return fail(STK_EINVAL, "cross labels must be in 0..255");
+    if (h->inten.nix > 0 && q->labels)
+        return fail(STK_EINVAL, "the inhomogeneous K takes no labels (cross K)");
+    if (h->inten.nix > 0 && h->inh_zero && q->sim_method == STK_SIM_PERMUTATION &&
+        plan.seed.size() > 0)
+        return fail(STK_EINVAL,
+                    "permutation simulations need rho > 0 in every cell (a permuted point "
+                    "may fall in a cell with rho = 0)");
     const int n_sims = (int)plan.seed.size();
     if (n_sims > (1 << 24) || plan.id.size() != plan.seed.size())
         return fail(STK_EINVAL, "n_sims out of range");
@@ -383,7 +403,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     // wave size: every realization of the wave is resident at once
     const int64_t ncells = g.ncells;
     const int64_t nrows = (int64_t)g.ny * g.nt;
-    const Footprint fp = footprint(n, g, nbins, R, n_groups, fp32_path(q));
+    const bool inh = h->inten.nix > 0;
+    const Footprint fp = footprint(n, g, nbins, R, n_groups, fp32_path(h, q), inh);
     int m_w = 1;
     if (q->exec == STK_EXEC_BATCHED) {
         size_t budget = h->wave_budget;
@@ -435,7 +456,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     // FP64 queue: pairs the FP32 kernel cannot decide (well under 0.1% of pairs in practice);
     // overflow is still exact, evaluated inside the pair kernel
     const unsigned int xq_cap = exact_queue_cap((int64_t)m_w * n);
-    if (fp32_path(q) && ((rc = ensure(h->xq_e, sizeof(uint4) * (size_t)xq_cap, "FP64 queue")) ||
+    if (inh && ((rc = ensure(h->uh, 8 * mn, "intensity ratios")) ||
+                (rc = ensure(h->Hs, 8 * mn, "intensity ratios")) ||
+                (rc = ensure(h->acc_whole, 8 * (size_t)m_w * nbins, "histograms"))))
+        return rc;
+    if (fp32_path(h, q) && ((rc = ensure(h->xq_e, sizeof(uint4) * (size_t)xq_cap, "FP64 queue")) ||
                          (rc = ensure(h->xq_count, 16, "FP64 queue"))))
         return rc;
     // per-point role flags (bit 0 centre, bit 1 neighbour): the sampled-centre mask of the
@@ -502,10 +527,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const double coef = area * dur / denom;
     const double* d_s = as<double>(h->thr);
     const double* d_tt = as<double>(h->thr) + STK_MAX_THRESHOLDS;
-    const bool fp32 = q->prec == STK_PREC_FP32_GUARDED;
-    const size_t smem = fp32 ? h->smem32 : h->smem64;
-    const int reps = fp32 ? h->reps32 : h->reps64;
-    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem);
+    const bool fp32 = fp32_path(h, q);
+    int reps = fp32 ? h->reps32 : h->reps64;
+    size_t smem = fp32 ? h->smem32 : h->smem64;
+    if (inh) smem = pair_fp64_smem(nbins, &reps, true);
+    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem, inh);
     const int grid = bps * h->num_sms;
     float ms_pair = 0.0f;
     int waves = 0;
@@ -529,6 +555,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             CK(cudaMemcpyAsync(h->ux.p, h->d_x, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
             CK(cudaMemcpyAsync(h->uy.p, h->d_y, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
             CK(cudaMemcpyAsync(h->ut.p, h->d_t, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
+            if (inh)
+                CK(cudaMemcpyAsync(h->uh.p, h->inh_obs.p, 8 * n, cudaMemcpyDeviceToDevice, st),
+                   "copy");
             CK(launch_keys_observed(h->d_x, h->d_y, h->d_t, n, g, as<uint32_t>(h->key),
                                     as<uint32_t>(h->rank), as<uint32_t>(h->counts),
                                     reinterpret_cast<int*>(as<unsigned long long>(h->stats) + 3), st),
@@ -544,7 +573,14 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                cudaMemcpyHostToDevice, st), "seeds");
             const int64_t off = (int64_t)first_sim_slot * n;
             uint32_t* cnt0 = as<uint32_t>(h->counts) + (int64_t)first_sim_slot * ncells;
-            if (q->sim_method == STK_SIM_CSR)
+            if (q->sim_method == STK_SIM_CSR && inh)
+                CK(launch_gen_inhom(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
+                                    h->inten, as<double>(h->ux) + off, as<double>(h->uy) + off,
+                                    as<double>(h->ut) + off, as<double>(h->uh) + off,
+                                    as<uint32_t>(h->key) + off, as<uint32_t>(h->rank) + off,
+                                    cnt0, st),
+                   "intensity-weighted generation");
+            else if (q->sim_method == STK_SIM_CSR)
                 CK(launch_gen_csr(n, ms, as<uint64_t>(h->simseed), as<uint32_t>(h->simid), g,
                                   as<double>(h->ux) + off, as<double>(h->uy) + off,
                                   as<double>(h->ut) + off, as<uint32_t>(h->key) + off,
@@ -559,6 +595,14 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                        as<uint32_t>(h->rank) + off, cnt0,
                                        as<unsigned long long>(h->stats) + 2, st),
                    "resampling");
+            // resampled points take h from the cell they lie in (rho > 0 there: a bootstrap
+            // point is an observed one; permutations need rho > 0 everywhere)
+            if (inh && q->sim_method != STK_SIM_CSR)
+                CK(launch_intensity_lookup(as<double>(h->ux) + off, as<double>(h->uy) + off,
+                                           as<double>(h->ut) + off, (int64_t)ms * n, h->box,
+                                           h->inten, as<double>(h->uh) + off,
+                                           as<unsigned long long>(h->stats) + 2, st),
+                   "intensity lookup");
         }
         CK(launch_exclusive_scan(as<uint32_t>(h->counts), as<uint32_t>(h->start),
                                  (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
@@ -570,7 +614,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                           as<double>(h->X), as<double>(h->Y), as<double>(h->T),
                           as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
                           h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st, poly,
-                          cross),
+                          cross, inh ? as<double>(h->uh) : nullptr,
+                          inh ? as<double>(h->Hs) : nullptr),
            "scatter");
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
@@ -587,6 +632,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         CK(cudaMemsetAsync(h->acc_cnt.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->acc_lo.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->acc_hi.p, 0, accb, st), "memset");
+        if (inh) CK(cudaMemsetAsync(h->acc_whole.p, 0, accb, st), "memset");
         CK(cudaMemsetAsync(h->counter.p, 0, 4 * (size_t)m, st), "memset");
         if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
         // each unordered pair is evaluated once, never a point with itself
@@ -602,11 +648,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         rb.mask_all = cross ? 1 : 0;
         rb.n = n;
         rb.ncells = ncells;
+        rb.H = inh ? as<double>(h->Hs) : nullptr;
         Accum acc;
         acc.cnt = as<unsigned long long>(h->acc_cnt);
         acc.exc_lo = as<unsigned long long>(h->acc_lo);
         acc.exc_hi = as<unsigned long long>(h->acc_hi);
         acc.stats = as<unsigned long long>(h->stats);
+        acc.whole = inh ? as<unsigned long long>(h->acc_whole) : nullptr;
         if (!in_graph) CK(cudaEventRecord(h->ev0, st), "event");
         ExactQueue xq;
         xq.e = as<uint4>(h->xq_e);
@@ -621,7 +669,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, st, h->nv > 0),
+                                as<uint32_t>(h->counter), acc, st, h->nv > 0, inh),
                "pair kernel (FP64)");
         if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
         if (fp32) {
@@ -651,7 +699,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         };
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
-                              q->sim_method};
+                              q->sim_method, inh, (int64_t)h->inh_gen};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -662,7 +710,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               h->stats.p, h->pc.p, h->thr.p, h->self_pairs.p, h->oK.p, h->oL.p,
                               h->oS.p, h->oC.p, h->xq_e.p, h->xq_count.p, h->simseed.p,
                               h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
-                              (void*)h->ev0, (void*)h->ev1, (void*)st};
+                              (void*)h->ev0, (void*)h->ev1, (void*)st, h->uh.p, h->Hs.p,
+                              h->acc_whole.p, h->inh.p, h->inh_obs.p};
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
@@ -799,7 +848,7 @@ int job_footprint(stk_handle* h, const stk_request* q, int R, int groups, Footpr
     if (const char* ft = getenv("STK_GRID_FT")) f_req = (f_req & 0xff) | (atoi(ft) << 8);
     if (build_grid(h->box, q->s[q->cs - 1], q->tt[q->ct - 1], h->n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
-    *out = footprint(h->n, g, q->cs * q->ct, R, groups, fp32_path(q));
+    *out = footprint(h->n, g, q->cs * q->ct, R, groups, fp32_path(h, q), h->inten.nix > 0);
     return STK_OK;
 }
 
@@ -812,7 +861,8 @@ void handle_trim(stk_handle* h) {
                       &h->Plo, &h->cell_start, &h->chunks, &h->chunk_off, &h->items,
                       &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                       &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL,
-                      &h->oS, &h->oC, &h->env, &h->simseed, &h->simid};
+                      &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh, &h->Hs,
+                      &h->acc_whole};
     for (DevBuf* b : bufs) free_buf(*b);
 }
 
@@ -1170,6 +1220,8 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
         return STK_OK;
     }
     if (!vx || !vy) return fail(STK_EINVAL, "vertex arrays must not be NULL");
+    if (h->inten.nix > 0)
+        return fail(STK_EINVAL, "a polygon study area and an intensity cannot be combined");
     if (nv < 3 || nv > kMaxPolyVertices)
         return fail(STK_EINVAL, "a polygon needs 3..%d vertices", kMaxPolyVertices);
     double area2 = 0.0;
@@ -1239,6 +1291,173 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     return STK_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Host tables of a relative intensity: tab[0 .. cells) = mean(rho) / rho_c (0 where rho_c = 0)
+// and tab[cells .. 2 cells) = rho_0 + ... + rho_c, added in cell order.  Checks the values and
+// the range rule (every rho_c > 0 within 2^14 of the mean either way, which keeps a pair
+// weight below 2^31).
+int intensity_tables(const double* rho, int nix, int niy, int nit, std::vector<double>& tab,
+                     Intensity* in, int* zero) {
+    if (!rho) return fail(STK_EINVAL, "rho must not be NULL");
+    if (nix < 1 || niy < 1 || nit < 1 || (int64_t)nix * niy * nit > ((int64_t)1 << 22))
+        return fail(STK_EINVAL, "intensity grid must have 1..2^22 cells (nix, niy, nit >= 1)");
+    const int cells = nix * niy * nit;
+    double sum = 0.0;
+    int last = -1;
+    *zero = 0;
+    tab.assign(2 * (size_t)cells, 0.0);
+    for (int c = 0; c < cells; ++c) {
+        const double r = rho[c];
+        if (!(r >= 0.0) || !isfinite(r))
+            return fail(STK_EINVAL, "rho[%d] must be finite and >= 0", c);
+        sum += r;
+        tab[(size_t)cells + c] = sum;
+        if (r > 0.0)
+            last = c;
+        else
+            *zero = 1;
+    }
+    if (last < 0 || !isfinite(sum)) return fail(STK_EINVAL, "rho must have a positive, finite sum");
+    const double mean = sum / (double)cells;
+    for (int c = 0; c < cells; ++c) {
+        if (rho[c] == 0.0) continue;
+        const double hc = mean / rho[c];
+        if (!(hc <= 16384.0 && hc >= 1.0 / 16384.0))
+            return fail(STK_EINVAL,
+                        "rho[%d] is more than 2^14 times below or above the mean of rho", c);
+        tab[(size_t)c] = hc;
+    }
+    in->nix = nix;
+    in->niy = niy;
+    in->nit = nit;
+    in->total = tab[2 * (size_t)cells - 1];
+    in->last_pos = last;
+    return STK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stk_set_intensity(stk_handle* h, const double* rho, int nix, int niy, int nit) {
+    if (!h) return fail(STK_EINVAL, "handle is NULL");
+    cudaStream_t st = h->stream;
+    CK(cudaStreamSynchronize(st), "stream sync");  // no running job reads the old tables
+    if (rho == nullptr || nix == 0) {  // back to the homogeneous estimator
+        free_buf(h->inh);
+        free_buf(h->inh_obs);
+        h->inten = Intensity();
+        h->inh_zero = 0;
+        ++h->inh_gen;
+        return STK_OK;
+    }
+    if (h->nv > 0)
+        return fail(STK_EINVAL, "a polygon study area and an intensity cannot be combined");
+    std::vector<double> tab;
+    Intensity in;
+    int zero = 0;
+    int rc = intensity_tables(rho, nix, niy, nit, tab, &in, &zero);
+    if (rc) return rc;
+    const int cells = nix * niy * nit;
+    DevBuf tb, ob, flag;
+    if ((rc = ensure(tb, 16 * (size_t)cells, "intensity")) ||
+        (rc = ensure(ob, 8 * (size_t)h->n, "intensity")) || (rc = ensure(flag, 16, "status"))) {
+        free_buf(tb), free_buf(ob), free_buf(flag);
+        return rc;
+    }
+    in.hcell = as<double>(tb);
+    in.cum = as<double>(tb) + cells;
+    unsigned long long bad = 0;
+    cudaError_t e = cudaMemcpyAsync(tb.p, tab.data(), 16 * (size_t)cells, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 8, st);
+    if (e == cudaSuccess)
+        e = launch_intensity_lookup(h->d_x, h->d_y, h->d_t, h->n, h->box, in, as<double>(ob),
+                                    as<unsigned long long>(flag), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag.p, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // also: tab (pageable) was read
+    free_buf(flag);
+    if (e != cudaSuccess) {
+        free_buf(tb), free_buf(ob);
+        return cuda_fail(e, "intensity upload");
+    }
+    if (bad) {
+        free_buf(tb), free_buf(ob);
+        return fail(STK_EDOMAIN, "%llu observed points lie in cells with rho = 0", bad);
+    }
+    free_buf(h->inh);
+    free_buf(h->inh_obs);
+    h->inh = tb;
+    h->inh_obs = ob;
+    h->inten = in;
+    h->inh_zero = zero;
+    ++h->inh_gen;
+    return STK_OK;
+}
+
+int stk_sim_points_inhom(const stk_box* box, const double* rho, int nix, int niy, int nit,
+                         int64_t n, uint64_t seed, uint32_t sim, double* x, double* y,
+                         double* t) {
+    if (!x || !y || !t) return fail(STK_EINVAL, "output arrays must not be NULL");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) return fail(STK_EINVAL, "n out of range");
+    int rc = check_box(box);
+    if (rc) return rc;
+    std::vector<double> tab;
+    Intensity in;
+    int zero = 0;
+    if ((rc = intensity_tables(rho, nix, niy, nit, tab, &in, &zero))) return rc;
+    const int cells = nix * niy * nit;
+    Grid g;  // one neighbour-grid cell: keys and ranks are by-products here
+    memset(&g, 0, sizeof g);
+    g.nx = g.ny = g.nt = 1;
+    g.ncells = 1;
+    g.x0 = box->x0, g.x1 = box->x1, g.y0 = box->y0, g.y1 = box->y1, g.t0 = box->t0,
+    g.t1 = box->t1;
+    g.cw = box->x1 - box->x0;
+    g.ch = box->y1 - box->y0;
+    g.cd = box->t1 - box->t0;
+    DevBuf bx, by, bt, bh, bk, br, bc, bs, tb;
+    const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+    auto release = [&]() {
+        free_buf(bx), free_buf(by), free_buf(bt), free_buf(bh), free_buf(bk), free_buf(br);
+        free_buf(bc), free_buf(bs), free_buf(tb);
+    };
+    if ((rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
+        (rc = ensure(bh, b8, "h")) || (rc = ensure(bk, b4, "keys")) ||
+        (rc = ensure(br, b4, "ranks")) || (rc = ensure(bc, 16, "counts")) ||
+        (rc = ensure(bs, 16, "seed")) || (rc = ensure(tb, 16 * (size_t)cells, "intensity"))) {
+        release();
+        return rc;
+    }
+    in.hcell = as<double>(tb);
+    in.cum = as<double>(tb) + cells;
+    struct {
+        uint64_t seed;
+        uint32_t sim, pad;
+    } key_sim = {seed, sim, 0};
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMemsetAsync(bc.p, 0, 16, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bs.p, &key_sim, sizeof key_sim, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb.p, tab.data(), 16 * (size_t)cells, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_gen_inhom(n, 1, as<uint64_t>(bs),
+                             reinterpret_cast<const uint32_t*>(reinterpret_cast<char*>(bs.p) + 8),
+                             g, in, as<double>(bx), as<double>(by), as<double>(bt),
+                             as<double>(bh), as<uint32_t>(bk), as<uint32_t>(br),
+                             as<uint32_t>(bc), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, bx.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, by.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t, bt.p, b8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "intensity-weighted generation");
+    return STK_OK;
+}
+
 int stk_last_stats(const stk_handle* h, stk_stats* out) {
     if (!h || !out) return fail(STK_EINVAL, "handle and out must not be NULL");
     *out = h->last;
@@ -1249,6 +1468,11 @@ void stk_destroy(stk_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_buf(h->poly);
+    free_buf(h->inh);
+    free_buf(h->inh_obs);
+    free_buf(h->uh);
+    free_buf(h->Hs);
+    free_buf(h->acc_whole);
     DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank, &h->counts, &h->start,
                       &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P, &h->Plo, &h->cell_start,
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,

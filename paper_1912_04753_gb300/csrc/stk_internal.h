@@ -98,6 +98,9 @@ struct RealBatch {
     int64_t n;
     int64_t ncells;
     int mask_all = 0;
+    // inhomogeneous K: per sorted point h = mean(rho) / rho(cell of the point), [m][n]; null
+    // for the homogeneous estimator
+    const double* H = nullptr;
 };
 
 // Per-realization accumulators: counts and the fixed-point (2^-32) sum of (w - 1), the latter
@@ -109,6 +112,9 @@ struct Accum {
     unsigned long long* exc_hi;  // [m][nbins]
     unsigned long long* stats;   // [0] candidates, [1] FP64 recomputes, [2] internal check
                                  // failures, [3] out-of-box flag
+    // inhomogeneous K only (null otherwise): the pair weights themselves are accumulated, in
+    // units of 2^-64: sum = whole * 2^64 + exc_hi * 2^32 + exc_lo; cnt still counts pairs
+    unsigned long long* whole = nullptr;  // [m][nbins]
 };
 
 // Pairs the FP32 kernel hands to FP64: x = centre, y = neighbour (sorted indices local to the
@@ -141,6 +147,26 @@ struct Polygon {
     const double* vy = nullptr;
     int nv = 0;
 };
+// Relative intensity of the inhomogeneous K: rho on nix x niy x nit equal cells of the box
+// ([nit][niy][nix], x fastest), in device memory.
+struct Intensity {
+    int nix = 0, niy = 0, nit = 0;  // 0: none
+    const double* hcell = nullptr;  // [cells] mean(rho) / rho_c, 0 where rho_c = 0
+    const double* cum = nullptr;    // [cells] rho_0 + ... + rho_c, added in cell order
+    double total = 0.0;             // cum[cells - 1]
+    int last_pos = 0;               // last cell with rho_c > 0
+};
+// h[i] = in.hcell[cell of (x[i], y[i], t[i])] for `count` points in the box; points in a cell
+// with rho = 0 get 0 and are counted in *zero
+cudaError_t launch_intensity_lookup(const double* x, const double* y, const double* t,
+                                    int64_t count, const double box[6], Intensity in, double* h,
+                                    unsigned long long* zero, cudaStream_t st);
+// realization slot k (0..m-1): n points drawn with density proportional to rho (Philox
+// realization sims[k] under key seeds[k]), h of each point from the cell it was drawn in
+cudaError_t launch_gen_inhom(int64_t n, int m, const uint64_t* seeds, const uint32_t* sims,
+                             const Grid& g, Intensity in, double* x, double* y, double* t,
+                             double* h, uint32_t* key, uint32_t* rank, uint32_t* cell_count,
+                             cudaStream_t st);
 // realization slot k (0..m-1) is Philox realization sims[k] under key seeds[k] (device arrays);
 // in a polygon, point i keeps the first of its attempts (Philox streams 32, 33, ...) that lies
 // inside (err counts points that found none in the attempt limit)
@@ -159,7 +185,8 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
-                           cudaStream_t st, Polygon poly = Polygon(), bool mask_all = false);
+                           cudaStream_t st, Polygon poly = Polygon(), bool mask_all = false,
+                           const double* h_in = nullptr, double* H = nullptr);
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
 // units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)
@@ -178,12 +205,13 @@ cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum a
                          ExactQueue xq, cudaStream_t st, bool poly = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
-                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false);
+                             uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false,
+                             bool inh = false);
 size_t pair_fp32_smem(int nbins, int* replicas);
-size_t pair_fp64_smem(int nbins, int* replicas);
+size_t pair_fp64_smem(int nbins, int* replicas, bool inh = false);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
 int pair_fp32_blocks_per_sm(size_t smem);
-int pair_fp64_blocks_per_sm(size_t smem);
+int pair_fp64_blocks_per_sm(size_t smem, bool inh = false);
 cudaError_t launch_finalize(int m, int cs, int ct, const double* s, const double* tt,
                             double coef, const int64_t* self_pairs, Accum acc, double* K,
                             double* L, double* S, int64_t* C, cudaStream_t st);

@@ -255,10 +255,34 @@ def config_polygon(seed: int = 0, n: int = 200_000) -> Workload:
                     {"time_unit": "day", "polygon": (vx, vy)})
 
 
+def histogram_intensity(x, y, t, box, shape, floor: float = 0.05) -> np.ndarray:
+    """A relative intensity for the inhomogeneous K: the point counts on `shape` = (nit, niy,
+    nix) equal cells of the box plus `floor` times the mean count, so that every cell is
+    positive (a stand-in for a smoothed estimate of the first-order intensity)."""
+    nit, niy, nix = shape
+    x0, x1, y0, y1, t0, t1 = box
+    ix = np.clip(((np.asarray(x) - x0) / (x1 - x0) * nix).astype(np.int64), 0, nix - 1)
+    iy = np.clip(((np.asarray(y) - y0) / (y1 - y0) * niy).astype(np.int64), 0, niy - 1)
+    it = np.clip(((np.asarray(t) - t0) / (t1 - t0) * nit).astype(np.int64), 0, nit - 1)
+    counts = np.bincount((it * niy + iy) * nix + ix, minlength=nit * niy * nix).astype(float)
+    return (counts + floor * counts.mean()).reshape(nit, niy, nix)
+
+
+def config_inhom(seed: int = 0, n: int = 200_000) -> Workload:
+    """The Thomas configuration with a relative intensity for the inhomogeneous K: point
+    counts on 10 x 10 x 8 cells (1 km x 1 km x 91.25 d) plus 5 % of the mean count;
+    meta["rho"] holds it ([nit][niy][nix]).  99 intensity-weighted simulations."""
+    w = config_thomas(seed, n)
+    rho = histogram_intensity(w.x, w.y, w.t, w.box, (8, 10, 10))
+    return Workload("thomas_inhom_n200k", w.x, w.y, w.t, w.box, w.s, w.tt, w.n_sims,
+                    w.sim_seed, dict(w.meta, rho=rho))
+
+
 CONFIGS = {
     "csr_n2000": config_csr_small,
     "thomas_n200k": config_thomas,
     "poi_n2M": config_poi,
     "poi_n10M": config_large,
     "thomas_polygon85_n200k": config_polygon,
+    "thomas_inhom_n200k": config_inhom,
 }

@@ -87,3 +87,25 @@ def test_server_argument_errors(lib):
         with pytest.raises(stk.StkError) as e:
             stk.stk_server_create()
         assert e.value.code == 7  # STK_ENODEV
+
+
+def test_intensity_argument_errors_need_no_device(lib):
+    """The relative intensity is checked on the host before any device call."""
+    import paper_1912_04753_gb300 as stk
+
+    box = (0, 10, 0, 10, 0, 10)
+    good = np.ones((2, 2, 2))
+    for bad in (good * -1.0, np.full((2, 2, 2), np.nan), np.zeros((2, 2, 2))):
+        with pytest.raises(stk.StkError) as e:
+            stk.stk_sim_points_inhom(box, bad, 10, 1, 0)
+        assert e.value.code == 1
+    wide = np.ones((1, 1, 4))
+    wide[0, 0, 0] = 1e-6  # 2^14 below the mean
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_sim_points_inhom(box, wide, 10, 1, 0)
+    assert e.value.code == 1 and "2^14" in str(e.value)
+    with pytest.raises(ValueError):
+        stk.stk_sim_points_inhom(box, np.ones((2, 2)), 10, 1, 0)
+    with pytest.raises(stk.StkError) as e:
+        stk.stk_set_intensity(None, good)
+    assert e.value.code == 1
