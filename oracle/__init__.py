@@ -101,6 +101,13 @@ def _load():
         lib.oracle_pair_hist_inhom.restype = i64
         lib.oracle_finalize_inhom.argtypes = [i64, P, P, i32, P, i32, i32, P, P, P, P, P, P]
         lib.oracle_finalize_inhom.restype = None
+        lib.oracle_translation_weight.argtypes = [d, d, d, P]
+        lib.oracle_translation_weight.restype = d
+        lib.oracle_sector.argtypes = [d, d, i32]
+        lib.oracle_sector.restype = i32
+        lib.oracle_pair_hist_dir.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, P, P,
+                                             P]
+        lib.oracle_pair_hist_dir.restype = i64
         _lib = lib
     return _lib
 
@@ -363,6 +370,43 @@ def k_function_inhom(x, y, t, box, s, tt, lam, edge_mode=1, norm=0, centre_mask=
             "pairs": int(q)}
 
 
+def translation_weight(dx: float, dy: float, u: float, box) -> float:
+    """Translation edge correction of a pair at offset (dx, dy) and time lag u."""
+    return _load().oracle_translation_weight(dx, dy, u, _ptr(_box(box)))
+
+
+def sector(dx: float, dy: float, n_sec: int) -> int:
+    """Axial-direction sector of the offset (dx, dy) among n_sec equal sectors of [0, pi)."""
+    return int(_load().oracle_sector(dx, dy, n_sec))
+
+
+def k_function_dir(x, y, t, box, s, tt, n_sec, edge_mode=2, norm=0, centre_mask=None):
+    """Directional (sector) K, translation-corrected with edge_mode 2 (see stk_oracle.c):
+    cumulative C, S, K and L per sector, arrays [n_sec, cs, ct].  L of a sector is
+    sqrt(n_sec K / (2 pi t)) - s, zero in expectation under CSR like Eq. 4."""
+    x, y, t, s, tt = map(_f64, (x, y, t, s, tt))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.zeros(n_sec * cs * ct, np.int64)
+    wsum = np.zeros(n_sec * cs * ct, np.float64)
+    m = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    q = _load().oracle_pair_hist_dir(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(s), cs,
+                                     _ptr(tt), ct, n_sec, edge_mode, _ptr(m), _ptr(cnt),
+                                     _ptr(wsum))
+    out = {k: [] for k in ("C", "S", "K", "L")}
+    nb = cs * ct
+    for k in range(n_sec):
+        C, S_, K, _ = finalize(len(x), box, s, tt, cnt[k * nb:(k + 1) * nb],
+                               wsum[k * nb:(k + 1) * nb], norm=norm)
+        out["C"].append(C)
+        out["S"].append(S_)
+        out["K"].append(K)
+        out["L"].append(np.sqrt(n_sec * K / (2.0 * np.pi * tt[None, :])) - s[:, None])
+    res = {k: np.stack(v) for k, v in out.items()}
+    res["pairs"] = int(q)
+    return res
+
+
 def simulation_points(method: int, x, y, t, box, seed: int, sim: int, polygon=None):
     """Realization `sim` of the given simulation method (Section 3)."""
     if method == SIM_CSR and polygon is not None:
@@ -377,13 +421,18 @@ def simulation_points(method: int, x, y, t, box, seed: int, sim: int, polygon=No
 
 
 def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, norm=0,
-                polygon=None, rho=None):
+                polygon=None, rho=None, n_sec=0):
     """Envelope (Section 3) over n_sims realizations of any simulation method (optionally in
     a polygon study area, or of the inhomogeneous K with relative intensity rho, whose CSR
     realizations are then drawn with density proportional to rho): the element-wise min /
     max of K (and L of those), plus every realization's K."""
     Ks = []
     for k in range(n_sims):
+        if n_sec > 0:
+            px, py, pt = simulation_points(method, x, y, t, box, seed, k)
+            Ks.append(k_function_dir(px, py, pt, box, s, tt, n_sec, edge_mode=edge_mode,
+                                     norm=norm)["K"])
+            continue
         if rho is not None:
             if method == SIM_CSR:
                 px, py, pt, cell = inhom_points(len(x), box, rho, seed, k)
@@ -404,7 +453,7 @@ def envelope_of(method: int, x, y, t, box, s, tt, n_sims, seed, edge_mode=1, nor
     Ks = np.stack(Ks)
     s, tt = _f64(s), _f64(tt)
     lo, hi = Ks.min(axis=0), Ks.max(axis=0)
-    den = 2.0 * np.pi * tt[None, :]
+    den = 2.0 * np.pi * tt[None, :] / max(1, n_sec)
     return {"K_lo": lo, "K_hi": hi, "L_lo": np.sqrt(lo / den) - s[:, None],
             "L_hi": np.sqrt(hi / den) - s[:, None], "K_all": Ks}
 

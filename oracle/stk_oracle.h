@@ -141,6 +141,15 @@ void oracle_finalize_inhom(int64_t n, const double box[6], const double* s, int 
                            const double* tt, int ct, int norm, const int64_t* cnt,
                            const double* wsum, int64_t* C, double* S, double* K, double* L);
 
+/* Directional (sector) K with translation edge correction (Section 7 future
+ * work, anisotropic analysis); see the source for the estimator. */
+double oracle_translation_weight(double dx, double dy, double u, const double box[6]);
+int oracle_sector(double dx, double dy, int n_sec);
+int64_t oracle_pair_hist_dir(int64_t n, const double* x, const double* y, const double* t,
+                             const double box[6], const double* s, int cs, const double* tt,
+                             int ct, int n_sec, int edge_mode, const uint8_t* centre_mask,
+                             int64_t* cnt, double* wsum);
+
 #ifdef __cplusplus
 }
 #endif
