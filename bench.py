@@ -441,6 +441,30 @@ def run_ours(args):
                  "value": si["qualifying_pairs"] / (ms_i / 1e3), "unit": UNIT,
                  "pair_kernel_s": si["ms_pair"] / 1e3}
 
+    # the directional K (8 axial sectors, translation correction, FP64) on the Thomas pattern,
+    # observed + 99 CSR simulations
+    directional = None
+    if args.directional and rank == 0:
+        wd = _workload("thomas_n200k")
+        with stk.Pattern(wd.x, wd.y, wd.t, wd.box) as pd:
+            stk.stk_set_stream(pd.h, stream)
+            kw = dict(n_sims=wd.n_sims, seed=seed, exec_mode=exec_mode,
+                      edge_mode=stk.STK_EDGE_TRANSLATION, n_sectors=8)
+            pd.run(wd.s, wd.tt, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pd.run(wd.s, wd.tt, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_d = e0.elapsed_time(e1)
+            sd = pd.stats()
+        directional = {"workload": wd.name, "n": wd.n, "sectors": 8, "edge": "translation",
+                       "sims": wd.n_sims, "dtype": "f64", "job_s": ms_d / 1e3,
+                       "sims_per_s": wd.n_sims / (ms_d / 1e3),
+                       "value": sd["qualifying_pairs"] / (ms_d / 1e3), "unit": UNIT,
+                       "pair_kernel_s": sd["ms_pair"] / 1e3}
+
     if rank != 0:
         stk.stk_destroy(h)
         if ws > 1:
@@ -489,6 +513,7 @@ def run_ours(args):
         "sim_methods": methods,
         "polygon": polygon,
         "inhomogeneous": inhom,
+        "directional": directional,
     }
     print(json.dumps(line), flush=True)
     stk.stk_destroy(h)
@@ -522,6 +547,8 @@ def build_parser():
                     help="also time a job over an 85-vertex polygon study area")
     ap.add_argument("--inhom", type=int, default=1,
                     help="also time an inhomogeneous-K job (intensity-weighted, FP64)")
+    ap.add_argument("--directional", type=int, default=1,
+                    help="also time a directional-K job (8 sectors, translation correction)")
     return ap
 
 

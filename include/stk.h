@@ -64,7 +64,12 @@ enum stk_status {
     STK_ENODEV = 7    /* no usable CUDA device */
 };
 
-enum { STK_EDGE_NONE = 0, STK_EDGE_ISOTROPIC = 1 };
+/* NONE: weight 1.  ISOTROPIC: Section 3 (proportion of the circle's circumference inside the
+ * study area, temporal weight 1 or 1/2).  TRANSLATION: the translation correction, pair weight
+ * W H / ((W - |dx|)(H - |dy|)) * D / (D - u) (|A| over the area of the box intersected with
+ * its copy shifted by the pair's offset, likewise in time; rectangle only, always in FP64):
+ * unbiased for every direction, so the one the directional K (n_sectors > 1) takes. */
+enum { STK_EDGE_NONE = 0, STK_EDGE_ISOTROPIC = 1, STK_EDGE_TRANSLATION = 2 };
 /* FP64: every pair in IEEE double, bit-compatible with the reference definition.
  * FP32_GUARDED: pairs in FP32 with cell-relative coordinates; any pair whose
  * bin, temporal weight or spatial-weight branch FP32 cannot decide with a
@@ -183,10 +188,21 @@ typedef struct {
     const uint8_t* labels;
     int cross_a;
     int cross_b;
+    /* Directional (sector) K, the anisotropic analysis the paper names as future work:
+     * n_sectors in 2..64 splits the pairs by the axial direction of their offset into
+     * n_sectors equal sectors of [0, pi) (sector k: angles [k pi / n, (k + 1) pi / n); the
+     * offset turned into the upper half plane, then counted against the boundaries
+     * (cos(m pi / n), sin(m pi / n)) by the sign of b_x d_y - b_y d_x >= 0, each operation
+     * rounded separately; coincident points in sector 0).  Every grid output then holds
+     * n_sectors grids, [n_sectors][cs][ct], with n_sectors * cs * ct <= 4096; L of a sector is
+     * sqrt(n_sectors K / (2 pi t)) - s (zero in expectation under CSR, like Eq. 4).  Needs
+     * edge_mode NONE or TRANSLATION, the rectangle, no intensity and no labels; runs in FP64.
+     * 0 or 1: no split. */
+    int n_sectors;
 } stk_request;
 
 typedef struct {
-    /* observed pattern, each [cs*ct] or NULL */
+    /* observed pattern, each [cs*ct] (times n_sectors for a directional K) or NULL */
     double* K;
     double* L;
     double* raw_sum;

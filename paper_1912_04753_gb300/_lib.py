@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libstk.so")
 
 STK_OK, STK_EINVAL, STK_EDOMAIN, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_EBUSY, STK_ENODEV = range(8)
-STK_EDGE_NONE, STK_EDGE_ISOTROPIC = 0, 1
+STK_EDGE_NONE, STK_EDGE_ISOTROPIC, STK_EDGE_TRANSLATION = 0, 1, 2
 STK_PREC_FP64, STK_PREC_FP32_GUARDED = 0, 1
 STK_NORM_N_NM1, STK_NORM_N2 = 0, 1
 STK_EXEC_BATCHED, STK_EXEC_PLAIN = 0, 1
@@ -39,7 +39,8 @@ class stk_request(ctypes.Structure):
                 ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int), ("norm", ctypes.c_int),
                 ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64), ("exec", ctypes.c_int),
                 ("centre_mask", _P), ("sim_method", ctypes.c_int), ("first_sim", ctypes.c_uint32),
-                ("labels", _P), ("cross_a", ctypes.c_int), ("cross_b", ctypes.c_int)]
+                ("labels", _P), ("cross_a", ctypes.c_int), ("cross_b", ctypes.c_int),
+                ("n_sectors", ctypes.c_int)]
 
 
 class stk_result(ctypes.Structure):
@@ -225,15 +226,18 @@ def stk_envelope(h, s, tt, n_sims, seed, edge_mode=STK_EDGE_ISOTROPIC,
 def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
             prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
             centre_mask=None, want_sims=False, sim_method=STK_SIM_CSR, first_sim=0,
-            labels=None, cross=(0, 0)):
-    """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim)."""
+            labels=None, cross=(0, 0), n_sectors=0):
+    """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim).
+    With n_sectors > 1 (directional K) every grid is [n_sectors, cs, ct]."""
     s, tt = _f64(s), _f64(tt)
     cs, ct = s.shape[0], tt.shape[0]
-    nb = cs * ct
+    grid = (n_sectors, cs, ct) if n_sectors > 1 else (cs, ct)
+    nb = int(np.prod(grid))
     mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
     lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
     q = stk_request(_ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims, seed, exec_mode,
-                    _ptr(mask), sim_method, first_sim, _ptr(lab), int(cross[0]), int(cross[1]))
+                    _ptr(mask), sim_method, first_sim, _ptr(lab), int(cross[0]), int(cross[1]),
+                    int(n_sectors))
     o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
     if n_sims > 0:
         for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
@@ -247,7 +251,7 @@ def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
     _check(load().stk_run(h, ctypes.byref(q), ctypes.byref(r)))
     out = {}
     for k, v in o.items():
-        out[k] = v.reshape((n_sims, cs, ct)) if k in ("K_sims", "C_sims") else v.reshape(cs, ct)
+        out[k] = v.reshape((n_sims,) + grid) if k in ("K_sims", "C_sims") else v.reshape(grid)
     return out
 
 

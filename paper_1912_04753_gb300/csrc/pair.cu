@@ -850,8 +850,33 @@ struct Smem64 {
     WarpSm64 w[kWarps];
 };
 
+// Directional K: sector of the pair offset (dx, dy) among pc.nsec equal axial sectors of
+// [0, pi): the offset turned into the upper half plane (both orders of a pair agree), then the
+// number of boundaries b with b_x d_y - b_y d_x >= 0, each operation rounded separately;
+// coincident points in sector 0.
+__device__ __forceinline__ int sector_of(const PairConsts& pc, double dx, double dy) {
+    if (dx == 0.0 && dy == 0.0) return 0;
+    if (!(dy > 0.0 || (dy == 0.0 && dx > 0.0))) {
+        dx = -dx;
+        dy = -dy;
+    }
+    int k = 0;
+    for (int m = 0; m < pc.nsec - 1; ++m)
+        k += __dsub_rn(__dmul_rn(pc.sec_bx[m], dy), __dmul_rn(pc.sec_by[m], dx)) >= 0.0 ? 1 : 0;
+    return k;
+}
+
+// Translation correction of a pair at offset (dx, dy) and lag u: |A| / |A intersected with A
+// shifted by (dx, dy)| in space times D / (D - u) in time (at most 4 * 2 for thresholds within
+// half the sides and half the period).
+__device__ __forceinline__ double translation_weight(const PairConsts& pc, double dx, double dy,
+                                                     double u) {
+    const double es = (pc.tw * pc.th) / ((pc.tw - fabs(dx)) * (pc.th - fabs(dy)));
+    return es * (pc.td / (pc.td - u));
+}
+
 // Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
-template <bool POLY, bool INH>
+template <bool POLY, bool INH, bool DIR>
 __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& ws, int cnt,
                                           int lane, const double* X, const double* Y,
                                           const double* T, const double* H, const uint8_t* mk,
@@ -882,6 +907,16 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     const uint32_t fj = mk == nullptr ? 3u : (uint32_t)mk[e.y];
     const bool act_i = mk == nullptr || (((onA >> e.x) & 1u) && (fj & 2u));
     const bool act_j = mk == nullptr || ((fj & 1u) && ((onB >> e.x) & 1u));
+    if (DIR) {  // directional / translation-corrected K: one weight for both orders
+        const int bin = (sector_of(pc, dx, dy) * pc.cs + a) * pc.ct + b;
+        const unsigned long long e =
+            pc.edge == STK_EDGE_TRANSLATION ? excess_fixed64(translation_weight(pc, dx, dy, u))
+                                            : 0ull;
+        atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
+        const unsigned long long exc = (act_i ? e : 0ull) + (act_j ? e : 0ull);
+        if (exc) atomicAdd(&he[bin], exc);
+        return;
+    }
     const int bin = a * pc.ct + b;
     if (INH) {
         // Section 7 inhomogeneous variant: each order weighted by h_i h_j / (w v)
@@ -952,7 +987,7 @@ __device__ __forceinline__ void warp_flush_inh(int real, int nbins, uint32_t* hc
     }
 }
 
-template <bool POLY, bool INH>
+template <bool POLY, bool INH, bool DIR>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
@@ -1056,7 +1091,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
                         tail += __popc(mq);
                         if (tail >= 32u) {
                             __syncwarp();
-                            process64<POLY, INH>(pc, ws, 32, lane, X, Y, T, H, mk, onA, onB,
+                            process64<POLY, INH, DIR>(pc, ws, 32, lane, X, Y, T, H, mk, onA, onB,
                                                  my_hc, my_he, my_hf, my_hw, acc.stats);
                             __syncwarp();
                             if ((uint32_t)lane < tail - 32) ws.ring[lane] = ws.ring[32 + lane];
@@ -1068,7 +1103,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             }
             __syncwarp();
             if (tail > 0)
-                process64<POLY, INH>(pc, ws, (int)tail, lane, X, Y, T, H, mk, onA, onB, my_hc,
+                process64<POLY, INH, DIR>(pc, ws, (int)tail, lane, X, Y, T, H, mk, onA, onB, my_hc,
                                      my_he, my_hf, my_hw, acc.stats);
             __syncwarp();
             if (since_flush >= kWarpFlush) {
@@ -1122,7 +1157,7 @@ __global__ void finalize_kernel(int cs, int ct, const double* __restrict__ s,
                                 const double* __restrict__ tt, double coef,
                                 const int64_t* __restrict__ self_pairs, Accum acc,
                                 double* __restrict__ K, double* __restrict__ L,
-                                double* __restrict__ S, int64_t* __restrict__ C) {
+                                double* __restrict__ S, int64_t* __restrict__ C, double lfac) {
     extern __shared__ __align__(16) unsigned char fsm[];
     const int nb = cs * ct;
     unsigned long long* cc = reinterpret_cast<unsigned long long*>(fsm);
@@ -1165,16 +1200,17 @@ __global__ void finalize_kernel(int cs, int ct, const double* __restrict__ s,
         }
         const double kv = coef * sv;
         if (K) K[o + i] = kv;
-        if (L) L[o + i] = sqrt(kv / (2.0 * 3.141592653589793 * tt[b])) - s[a];
+        if (L) L[o + i] = sqrt(lfac * kv / (2.0 * 3.141592653589793 * tt[b])) - s[a];
         if (S) S[o + i] = sv;
         if (C) C[o + i] = (int64_t)cc[i];
     }
 }
 
-__global__ void envelope_kernel(int m, int nbins, int ct, const double* __restrict__ K,
+__global__ void envelope_kernel(int m, int nbins, int cs, int ct, const double* __restrict__ K,
                                 const double* __restrict__ s, const double* __restrict__ tt,
                                 double* __restrict__ K_lo, double* __restrict__ K_hi,
-                                double* __restrict__ L_lo, double* __restrict__ L_hi) {
+                                double* __restrict__ L_lo, double* __restrict__ L_hi,
+                                double lfac) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nbins) return;
     double lo = K[i], hi = K[i];
@@ -1183,8 +1219,8 @@ __global__ void envelope_kernel(int m, int nbins, int ct, const double* __restri
         lo = fmin(lo, v);
         hi = fmax(hi, v);
     }
-    const int a = i / ct, b = i - (i / ct) * ct;
-    const double den = 2.0 * 3.141592653589793 * tt[b];
+    const int a = (i / ct) % cs, b = i - (i / ct) * ct;
+    const double den = 2.0 * 3.141592653589793 * tt[b] / lfac;
     K_lo[i] = lo;
     K_hi[i] = hi;
     L_lo[i] = sqrt(lo / den) - s[a];
@@ -1242,15 +1278,18 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(pair_fp64_kernel<true, false>,
+    e = cudaFuncSetAttribute(pair_fp64_kernel<true, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(pair_fp64_kernel<false, false>,
+    e = cudaFuncSetAttribute(pair_fp64_kernel<false, false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(pair_fp64_kernel<false, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     if (e != cudaSuccess) return e;
     const size_t smem_inh = std::max<size_t>(
         72 * 1024, ((sizeof(Smem64) + 15) & ~size_t(15)) + (size_t)kMaxThr * kMaxThr * 32);
-    return cudaFuncSetAttribute(pair_fp64_kernel<false, true>,
+    return cudaFuncSetAttribute(pair_fp64_kernel<false, true, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inh);
 }
 
@@ -1266,10 +1305,10 @@ int pair_fp32_blocks_per_sm(size_t smem) {
 int pair_fp64_blocks_per_sm(size_t smem, bool inh) {
     int b = 0;
     const cudaError_t e =
-        inh ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false, true>,
-                                                            kBlock, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp64_kernel<false, false>,
-                                                            kBlock, smem);
+        inh ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &b, pair_fp64_kernel<false, true, false>, kBlock, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &b, pair_fp64_kernel<false, false, false>, kBlock, smem);
     if (e != cudaSuccess) return 1;
     return b > 0 ? b : 1;
 }
@@ -1311,34 +1350,40 @@ cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum a
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
                              uint32_t* counters, Accum acc, cudaStream_t st, bool poly,
-                             bool inh) {
-    if (inh && (poly || rb.H == nullptr || acc.whole == nullptr)) return cudaErrorInvalidValue;
+                             bool inh, bool dir) {
+    if (inh && (poly || dir || rb.H == nullptr || acc.whole == nullptr))
+        return cudaErrorInvalidValue;
+    if (dir && poly) return cudaErrorInvalidValue;
+#define STK_PAIR64(P, I, D)                                                                     \
+    pair_fp64_kernel<P, I, D><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off, counters, \
+                                                          acc, reps)
     if (inh)
-        pair_fp64_kernel<false, true><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
-                                                                  counters, acc, reps);
+        STK_PAIR64(false, true, false);
+    else if (dir)
+        STK_PAIR64(false, false, true);
     else if (poly)
-        pair_fp64_kernel<true, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
-                                                                  counters, acc, reps);
+        STK_PAIR64(true, false, false);
     else
-        pair_fp64_kernel<false, false><<<grid, kBlock, smem, st>>>(d_pc, m, rb, units, unit_off,
-                                                                   counters, acc, reps);
+        STK_PAIR64(false, false, false);
+#undef STK_PAIR64
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int m, int cs, int ct, const double* s, const double* tt,
                             double coef, const int64_t* self_pairs, Accum acc, double* K,
-                            double* L, double* S, int64_t* C, cudaStream_t st) {
+                            double* L, double* S, int64_t* C, cudaStream_t st, double lfac) {
     const int nb = cs * ct;
     const size_t smem = (size_t)((nb + 1) & ~1) * 8 + (size_t)nb * 16;
-    finalize_kernel<<<m, 128, smem, st>>>(cs, ct, s, tt, coef, self_pairs, acc, K, L, S, C);
+    finalize_kernel<<<m, 128, smem, st>>>(cs, ct, s, tt, coef, self_pairs, acc, K, L, S, C,
+                                          lfac);
     return cudaGetLastError();
 }
 
-cudaError_t launch_envelope(int m, int nbins, int ct, const double* K, const double* s,
+cudaError_t launch_envelope(int m, int nbins, int cs, int ct, const double* K, const double* s,
                             const double* tt, double* K_lo, double* K_hi, double* L_lo,
-                            double* L_hi, cudaStream_t st) {
-    envelope_kernel<<<(nbins + 127) / 128, 128, 0, st>>>(m, nbins, ct, K, s, tt, K_lo, K_hi,
-                                                         L_lo, L_hi);
+                            double* L_hi, cudaStream_t st, double lfac) {
+    envelope_kernel<<<(nbins + 127) / 128, 128, 0, st>>>(m, nbins, cs, ct, K, s, tt, K_lo, K_hi,
+                                                         L_lo, L_hi, lfac);
     return cudaGetLastError();
 }
 

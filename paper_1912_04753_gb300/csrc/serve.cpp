@@ -450,7 +450,8 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
         job->ct > STK_MAX_THRESHOLDS)
         return note(STK_EINVAL, "threshold arrays must hold 1..64 entries");
     if (job->n_sims < 0 || job->n_sims > (1 << 20)) return note(STK_EINVAL, "n_sims out of range");
-    if (job->edge_mode != STK_EDGE_NONE && job->edge_mode != STK_EDGE_ISOTROPIC)
+    if (job->edge_mode != STK_EDGE_NONE && job->edge_mode != STK_EDGE_ISOTROPIC &&
+        job->edge_mode != STK_EDGE_TRANSLATION)
         return note(STK_EINVAL, "unknown edge_mode");
     if (job->prec != STK_PREC_FP64 && job->prec != STK_PREC_FP32_GUARDED)
         return note(STK_EINVAL, "unknown prec");

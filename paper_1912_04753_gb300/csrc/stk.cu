@@ -128,7 +128,8 @@ bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
 
 // The FP32-guarded pair kernel, unless the job is an inhomogeneous K (always FP64).
 bool fp32_path(const stk_handle* h, const stk_request* q) {
-    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0;
+    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0 &&
+           q->edge_mode != STK_EDGE_TRANSLATION && q->n_sectors <= 1;
 }
 
 int check_box(const stk_box* b) {
@@ -246,7 +247,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
 struct TuneKey {
     int64_t n;
     double box[6], s_max, t_max;
-    int prec, edge, method;
+    int prec, edge, method, nsec;
     bool operator<(const TuneKey& o) const {
         return memcmp(this, &o, sizeof(TuneKey)) < 0;
     }
@@ -263,6 +264,7 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
     key.t_max = q->tt[q->ct - 1];
     key.prec = q->prec;
     key.edge = q->edge_mode;
+    key.nsec = q->n_sectors;
     key.method = q->sim_method;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -325,8 +327,23 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const auto t_start = clock::now();
     int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
     if (rc) return rc;
-    if (q->edge_mode != STK_EDGE_NONE && q->edge_mode != STK_EDGE_ISOTROPIC)
+    if (q->edge_mode != STK_EDGE_NONE && q->edge_mode != STK_EDGE_ISOTROPIC &&
+        q->edge_mode != STK_EDGE_TRANSLATION)
         return fail(STK_EINVAL, "unknown edge_mode %d", q->edge_mode);
+    if (q->n_sectors < 0 || q->n_sectors > kMaxSectors)
+        return fail(STK_EINVAL, "n_sectors must be in 0..%d", kMaxSectors);
+    const int nsec = q->n_sectors > 1 ? q->n_sectors : 1;
+    const bool dir = nsec > 1 || q->edge_mode == STK_EDGE_TRANSLATION;
+    if (nsec > 1 && q->edge_mode == STK_EDGE_ISOTROPIC)
+        return fail(STK_EINVAL,
+                    "the directional K takes edge_mode NONE or TRANSLATION (the isotropic "
+                    "weight is not unbiased direction by direction)");
+    if (nsec > 1 && (int64_t)nsec * q->cs * q->ct > (int64_t)kMaxThr * kMaxThr)
+        return fail(STK_EINVAL, "n_sectors * cs * ct must be at most %d", kMaxThr * kMaxThr);
+    if (dir && (h->nv > 0 || h->inten.nix > 0 || q->labels))
+        return fail(STK_EINVAL,
+                    "the translation correction and the directional K need the rectangle, no "
+                    "intensity and no labels");
     if (q->prec != STK_PREC_FP64 && q->prec != STK_PREC_FP32_GUARDED)
         return fail(STK_EINVAL, "unknown prec %d", q->prec);
     if (q->norm != STK_NORM_N_NM1 && q->norm != STK_NORM_N2)
@@ -359,7 +376,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     if (R < 1) return fail(STK_EINVAL, "nothing to compute (no observed pattern, n_sims = 0)");
     *R_out = R;
     const int64_t n = h->n;
-    const int cs = q->cs, ct = q->ct, nbins = cs * ct;
+    // a directional K holds nsec grids of cs x ct per realization
+    const int cs = q->cs, ct = q->ct, nbins = cs * ct * nsec;
+    const double lfac = (double)nsec;
     char err[256];
     Grid g;
     // grid refinement: forced (tuner trials), STK_GRID_F (and STK_GRID_FT for the time axis),
@@ -381,6 +400,16 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     cudaStream_t st = h->stream;
     CK(cudaStreamSynchronize(st), "stream sync");  // the pinned constants are reused below
     build_pair_consts(g, n, q->s, cs, q->tt, ct, q->edge_mode, h->h_pc);
+    h->h_pc->nsec = nsec;
+    h->h_pc->nbins = nbins;
+    for (int m = 1; m < nsec; ++m) {  // sector boundaries m pi / nsec
+        const double ang = (double)m * 3.14159265358979323846 / (double)nsec;
+        h->h_pc->sec_bx[m - 1] = cos(ang);
+        h->h_pc->sec_by[m - 1] = sin(ang);
+    }
+    h->h_pc->tw = h->box[1] - h->box[0];
+    h->h_pc->th = h->box[3] - h->box[2];
+    h->h_pc->td = h->box[5] - h->box[4];
     Polygon poly;
     if (h->nv > 0) {
         poly.vx = as<double>(h->poly);
@@ -443,7 +472,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         (rc = ensure(h->acc_hi, 8 * (size_t)m_w * nbins, "histograms")) ||
         (rc = ensure(h->stats, 64, "statistics")) || (rc = ensure(h->pc, sizeof(PairConsts), "constants")) ||
         (rc = ensure(h->thr, 8 * 2 * STK_MAX_THRESHOLDS, "thresholds")) ||
-        (rc = ensure(h->self_pairs, 8 * (size_t)m_w, "self pairs")) ||
+        (rc = ensure(h->self_pairs, 8 * (size_t)m_w * nsec, "self pairs")) ||
         (rc = ensure(h->oK, 8 * (size_t)R * nbins, "K grids")) ||
         (rc = ensure(h->oL, 8 * (size_t)R * nbins, "L grids")) ||
         (rc = ensure(h->oS, 8 * (size_t)R * nbins, "S grids")) ||
@@ -636,7 +665,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         CK(cudaMemsetAsync(h->counter.p, 0, 4 * (size_t)m, st), "memset");
         if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
         // each unordered pair is evaluated once, never a point with itself
-        CK(cudaMemsetAsync(h->self_pairs.p, 0, 8 * (size_t)m, st), "memset");
+        CK(cudaMemsetAsync(h->self_pairs.p, 0, 8 * (size_t)m * nsec, st), "memset");
         RealBatch rb;
         rb.P = as<float4>(h->P);
         rb.Plo = as<float2>(h->Plo);
@@ -669,7 +698,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, st, h->nv > 0, inh),
+                                as<uint32_t>(h->counter), acc, st, h->nv > 0, inh, dir),
                "pair kernel (FP64)");
         if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
         if (fp32) {
@@ -677,9 +706,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                "FP64 queue");
         }
         const int64_t row = (int64_t)r0 * nbins;
-        CK(launch_finalize(m, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
+        CK(launch_finalize(m * nsec, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
                            as<double>(h->oK) + row, as<double>(h->oL) + row,
-                           as<double>(h->oS) + row, as<int64_t>(h->oC) + row, st),
+                           as<double>(h->oS) + row, as<int64_t>(h->oC) + row, st, lfac),
            "finalize");
         return STK_OK;
     };
@@ -699,7 +728,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         };
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
-                              q->sim_method, inh, (int64_t)h->inh_gen};
+                              q->sim_method, inh, (int64_t)h->inh_gen, nsec};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -764,22 +793,22 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     for (int gi = 0; gi < n_groups; ++gi) {
         const int g0 = plan.groups[gi].first, gn = plan.groups[gi].second;
         double* env = as<double>(h->env) + (size_t)gi * 4 * nbins;
-        CK(launch_envelope(gn, nbins, ct,
+        CK(launch_envelope(gn, nbins, cs, ct,
                            as<double>(h->oK) + (int64_t)(first_sim_row + g0) * nbins, d_s, d_tt,
-                           env, env + nbins, env + 2 * nbins, env + 3 * nbins, st),
+                           env, env + nbins, env + 2 * nbins, env + 3 * nbins, st, lfac),
            "envelope");
     }
     unsigned long long stats[8];
     CK(cudaMemcpyAsync(stats, h->stats.p, sizeof stats, cudaMemcpyDeviceToHost, st), "stats");
-    std::vector<int64_t> lastC(R);
-    for (int r = 0; r < R; ++r)
-        CK(cudaMemcpyAsync(&lastC[r], as<int64_t>(h->oC) + (int64_t)r * nbins + nbins - 1, 8,
-                           cudaMemcpyDeviceToHost, st),
-           "counts");
+    // qualifying pairs: the last cell of every grid (one per sector)
+    std::vector<int64_t> lastC((size_t)R * nsec);
+    CK(cudaMemcpy2DAsync(lastC.data(), 8, as<int64_t>(h->oC) + cs * ct - 1, 8 * (size_t)cs * ct,
+                         8, (size_t)R * nsec, cudaMemcpyDeviceToHost, st),
+       "counts");
     CK(cudaStreamSynchronize(st), "job");
     if (stats[3] != 0) return fail(STK_EDOMAIN, "a point lies outside the study box");
     h->last.qualifying_pairs = 0;
-    for (int r = 0; r < R; ++r) h->last.qualifying_pairs += lastC[r];
+    for (int64_t c : lastC) h->last.qualifying_pairs += c;
     h->last.candidate_pairs = (int64_t)stats[0];
     h->last.fp64_recomputed = (int64_t)stats[1];
     h->last.work_items = 0;
@@ -972,7 +1001,7 @@ int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
     int R = 0;
     int rc = run_job(h, req, true, default_plan(req), &R);
     if (rc) return rc;
-    const int nbins = req->cs * req->ct;
+    const int nbins = req->cs * req->ct * (req->n_sectors > 1 ? req->n_sectors : 1);
     if ((rc = copy_rows(h, h->oK, 0, 1, nbins, res->K)) ||
         (rc = copy_rows(h, h->oL, 0, 1, nbins, res->L)) ||
         (rc = copy_rows(h, h->oS, 0, 1, nbins, res->raw_sum)) ||

@@ -21,6 +21,7 @@ namespace stk {
 
 constexpr int kMaxThr = 64;   // thresholds per axis
 constexpr int kMaxPolyVertices = 128;  // vertices of a polygon study area
+constexpr int kMaxSectors = 64;        // direction sectors of the directional K
 constexpr int kTab = 1024;    // bin-table entries per axis
 constexpr int kBlock = 256;   // threads per pair-kernel block
 constexpr int kUnit = 32;      // centres per work unit (one warp)
@@ -72,6 +73,12 @@ struct PairConsts {
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
     uint8_t tab_s64[kTab], tab_t64[kTab];
+    // directional K (FP64 kernel): nsec sectors, boundary m + 1 = (sec_bx[m], sec_by[m]);
+    // histograms are [nsec][cs][ct] (nbins = nsec * cs * ct); edge 2 = translation weights
+    // with the box's sides tw, th and period td
+    int nsec;
+    double sec_bx[kMaxSectors], sec_by[kMaxSectors];
+    double tw, th, td;
 };
 
 // One unit of pair work for one warp: the centres [c_begin, c_begin + c_count) (at most 32,
@@ -206,18 +213,22 @@ cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum a
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
                              uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false,
-                             bool inh = false);
+                             bool inh = false, bool dir = false);
 size_t pair_fp32_smem(int nbins, int* replicas);
 size_t pair_fp64_smem(int nbins, int* replicas, bool inh = false);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
 int pair_fp32_blocks_per_sm(size_t smem);
 int pair_fp64_blocks_per_sm(size_t smem, bool inh = false);
+// m grids of cs x ct (a realization of a directional K holds nsec consecutive grids);
+// L = sqrt(lfac K / (2 pi t)) - s (lfac = nsec, 1 for the plain estimator)
 cudaError_t launch_finalize(int m, int cs, int ct, const double* s, const double* tt,
                             double coef, const int64_t* self_pairs, Accum acc, double* K,
-                            double* L, double* S, int64_t* C, cudaStream_t st);
-cudaError_t launch_envelope(int m, int nbins, int ct, const double* K, const double* s,
+                            double* L, double* S, int64_t* C, cudaStream_t st,
+                            double lfac = 1.0);
+// element-wise min / max over m rows of nbins (nbins a multiple of cs * ct)
+cudaError_t launch_envelope(int m, int nbins, int cs, int ct, const double* K, const double* s,
                             const double* tt, double* K_lo, double* K_hi, double* L_lo,
-                            double* L_hi, cudaStream_t st);
+                            double* L_hi, cudaStream_t st, double lfac = 1.0);
 
 // Host: derive grid and guard constants for one job.  f_req = 0 lets the planner choose the
 // refinement factor from the point density; 1 or 2 forces it.
