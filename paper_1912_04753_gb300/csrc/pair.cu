@@ -268,7 +268,7 @@ constexpr int kSpinLimit = 1 << 20;
 // wait (bounded) for the new tile.  Lane 0 works, the result is broadcast.
 __device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32_t* counter,
                                               uint32_t ubeg, uint32_t uend, int lane,
-                                              unsigned long long* stats) {
+                                              unsigned long long* stats, bool never_publish) {
     uint32_t ui = kNoUnit;
     if (lane == 0) {
         const uint32_t ntiles = (uend - ubeg + kTileUnits - 1) / kTileUnits;
@@ -287,6 +287,7 @@ __device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32
                 continue;  // past the end of the last tile: draw until someone claims anew
             }
             if (idx == kTileUnits) {
+                if (never_publish) break;  // test hook: the waiting warps' waits run out
                 const uint32_t nt = atomicAdd(counter, 1u);
                 atomicExch(cursor, ((unsigned long long)nt << 32) | 1ull);  // index 0 is ours
                 if (nt >= ntiles) break;
@@ -296,7 +297,7 @@ __device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32
             while ((uint32_t)(*reinterpret_cast<volatile unsigned long long*>(cursor) >> 32) ==
                    tile) {
                 if (++spin > kSpinLimit) {
-                    atomicAdd(&stats[2], 1ull);  // never expected: the claimer is resident
+                    atomicAdd(&stats[4], 1ull);  // never expected: the claimer is resident
                     stuck = true;
                     break;
                 }
@@ -672,7 +673,8 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
         __syncthreads();
         for (;;) {
-            const uint32_t ui = next_unit(&sm.cursor, &counters[k], ubeg, uend, lane, acc.stats);
+            const uint32_t ui = next_unit(&sm.cursor, &counters[k], ubeg, uend, lane, acc.stats,
+                                          pc.never_publish != 0);
             if (ui == kNoUnit) break;
             const WorkItem wi = units[ui];
             w.c_begin = wi.c_begin;

@@ -402,6 +402,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     build_pair_consts(g, n, q->s, cs, q->tt, ct, q->edge_mode, h->h_pc);
     h->h_pc->nsec = nsec;
     h->h_pc->nbins = nbins;
+    {  // failure-detection test hook, see PairConsts::never_publish
+        const char* np = getenv("STK_TEST_NEVER_PUBLISH");
+        h->h_pc->never_publish = (np && atoi(np) != 0) ? 1 : 0;
+    }
     for (int m = 1; m < nsec; ++m) {  // sector boundaries m pi / nsec
         const double ang = (double)m * 3.14159265358979323846 / (double)nsec;
         h->h_pc->sec_bx[m - 1] = cos(ang);
@@ -807,6 +811,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
        "counts");
     CK(cudaStreamSynchronize(st), "job");
     if (stats[3] != 0) return fail(STK_EDOMAIN, "a point lies outside the study box");
+    if (stats[4] != 0)
+        return fail(STK_ETIMEOUT,
+                    "%llu bounded waits for work in the pair kernel ran out; the job's results "
+                    "are incomplete",
+                    stats[4]);
     h->last.qualifying_pairs = 0;
     for (int64_t c : lastC) h->last.qualifying_pairs += c;
     h->last.candidate_pairs = (int64_t)stats[0];

@@ -63,6 +63,10 @@ struct PairConsts {
     // cell index ranges [lo, hi] of points at least s_max from every spatial edge (x, y) and
     // t_max from both ends of the period (t): a pair of two such points has w = v = 1
     int deep_x[2], deep_y[2], deep_t[2];
+    // failure-detection test hook (0 in normal use): a warp that should claim the next tile of
+    // work units claims none and publishes nothing, so the block's other warps wait for a tile
+    // that never comes until their bounded wait runs out
+    int never_publish;
     // polygon study area (nv = 0: the rectangle); vertex arrays in device memory
     int nv;
     int pccw;                 // 1: vertices run counter-clockwise
@@ -118,7 +122,8 @@ struct Accum {
     unsigned long long* exc_lo;  // [m][nbins]
     unsigned long long* exc_hi;  // [m][nbins]
     unsigned long long* stats;   // [0] candidates, [1] FP64 recomputes, [2] internal check
-                                 // failures, [3] out-of-box flag
+                                 // failures, [3] out-of-box flag, [4] bounded waits that ran
+                                 // out (the job fails with STK_ETIMEOUT)
     // inhomogeneous K only (null otherwise): the pair weights themselves are accumulated, in
     // units of 2^-64: sum = whole * 2^64 + exc_hi * 2^32 + exc_lo; cnt still counts pairs
     unsigned long long* whole = nullptr;  // [m][nbins]

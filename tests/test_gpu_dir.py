@@ -143,3 +143,20 @@ def test_directional_arguments(stk, orc):
         p.set_intensity(None)
         ok = p.run(S, TT, n_sectors=2, edge_mode=2)
         assert ok["K"].shape == (2, len(S), len(TT))
+
+
+def test_served_translation_k(stk, orc):
+    # the serving loop takes the translation correction as a job parameter
+    x, y, t = _pattern(1500, 17, stretch=False)
+    with stk.Server(slots=2) as sv:
+        d = sv.register(x, y, t, BOX)
+        tk = sv.submit(d, S, TT, edge_mode=stk.STK_EDGE_TRANSLATION)
+        iso = sv.submit(d, S, TT)
+        got, _ = sv.poll(tk)
+        got_iso, _ = sv.poll(iso)
+    want = orc.k_function_dir(x, y, t, BOX, S, TT, 1, edge_mode=2)
+    np.testing.assert_array_equal(got["C"], want["C"][0])
+    assert _rel(got["K"], want["K"][0]).max() <= TOL
+    # the isotropic job of the same batch is not merged with it
+    want_iso = orc.k_function(x, y, t, BOX, S, TT)
+    assert _rel(got_iso["K"], want_iso["K"]).max() <= 1e-6
