@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-             "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+             "-fno-fast-math", "-pthread", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -108,6 +108,8 @@ def _load():
         lib.oracle_pair_hist_dir.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, i32, P, P,
                                              P]
         lib.oracle_pair_hist_dir.restype = i64
+        lib.oracle_pair_hist_grid.argtypes = [i64, P, P, P, P, P, i32, P, i32, i32, P, i32, P, P]
+        lib.oracle_pair_hist_grid.restype = i64
         _lib = lib
     return _lib
 
@@ -168,6 +170,21 @@ def pair_hist(x, y, t, box, s, tt, edge_mode=1, centre_mask=None):
     m = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
     q = _load().oracle_pair_hist(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(s), cs,
                                  _ptr(tt), ct, edge_mode, _ptr(m), _ptr(cnt), _ptr(wsum))
+    return cnt.reshape(cs, ct), wsum.reshape(cs, ct), int(q)
+
+
+def pair_hist_grid(x, y, t, box, s, tt, edge_mode=1, centre_mask=None, threads=None):
+    """pair_hist over the same pairs with a grid and threads (for whole grids at large n)."""
+    x, y, t, s, tt = map(_f64, (x, y, t, s, tt))
+    b = _box(box)
+    cs, ct = len(s), len(tt)
+    cnt = np.zeros(cs * ct, np.int64)
+    wsum = np.zeros(cs * ct, np.float64)
+    m = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    nt = threads or (os.cpu_count() or 1)
+    q = _load().oracle_pair_hist_grid(len(x), _ptr(x), _ptr(y), _ptr(t), _ptr(b), _ptr(s), cs,
+                                      _ptr(tt), ct, edge_mode, _ptr(m), nt, _ptr(cnt),
+                                      _ptr(wsum))
     return cnt.reshape(cs, ct), wsum.reshape(cs, ct), int(q)
 
 

@@ -888,3 +888,175 @@ int64_t oracle_pair_hist_dir(int64_t n, const double* x, const double* y, const 
     free(comp);
     return total;
 }
+
+/* ---------------------------------------------------------------------------
+ * Grid-accelerated, multithreaded restatement of oracle_pair_hist, for checking
+ * whole grids at sizes where the O(n^2) loop is out of reach.  Every pair it
+ * evaluates goes through the same steps as oracle_pair_hist (the same
+ * separately rounded d2 and u, the same bin search, the same weight
+ * functions); it only skips pairs that cannot qualify: points are binned into
+ * a uniform grid whose cells are wider than s_max (x, y) and t_max (t), so a
+ * qualifying pair lies in the same or adjacent cells.  Centres are split over
+ * threads, each with its own compensated histograms, added in thread order.
+ * Trusted only after matching oracle_pair_hist on small inputs (tests).
+ * ------------------------------------------------------------------------- */
+#include <pthread.h>
+
+typedef struct {
+    int64_t n;
+    const double *x, *y, *t;
+    const double* box;
+    const double *s, *s2, *tt;
+    int cs, ct, edge_mode;
+    const uint8_t* centre_mask;
+    int nx, ny, nt;
+    const int64_t* start; /* [cells + 1] */
+    const int64_t* order; /* point indices sorted by cell */
+    const int* cell;      /* cell of each point */
+    int64_t i0, i1;       /* centres of this thread: order[i0 .. i1) */
+    int64_t* cnt;
+    double *wsum, *comp;
+    int64_t total;
+} grid_job;
+
+static int grid_axis(double v, double lo, double side, int nc) {
+    double f = floor((v - lo) / side);
+    if (f < 0.0) f = 0.0;
+    if (f > (double)(nc - 1)) f = (double)(nc - 1);
+    return (int)f;
+}
+
+static void* grid_worker(void* arg) {
+    grid_job* g = (grid_job*)arg;
+    const double s2max = g->s2[g->cs - 1], tmax = g->tt[g->ct - 1];
+    for (int64_t oi = g->i0; oi < g->i1; ++oi) {
+        const int64_t i = g->order[oi];
+        if (g->centre_mask && !g->centre_mask[i]) continue;
+        const int c = g->cell[i];
+        const int cx = c % g->nx, cy = (c / g->nx) % g->ny, ct = c / (g->nx * g->ny);
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int zz = ct + dz;
+            if (zz < 0 || zz >= g->nt) continue;
+            for (int dyy = -1; dyy <= 1; ++dyy) {
+                const int yy = cy + dyy;
+                if (yy < 0 || yy >= g->ny) continue;
+                for (int dxx = -1; dxx <= 1; ++dxx) {
+                    const int xx = cx + dxx;
+                    if (xx < 0 || xx >= g->nx) continue;
+                    const int nc = (zz * g->ny + yy) * g->nx + xx;
+                    for (int64_t oj = g->start[nc]; oj < g->start[nc + 1]; ++oj) {
+                        const int64_t j = g->order[oj];
+                        if (j == i) continue;
+                        const double dx = g->x[i] - g->x[j];
+                        const double dy = g->y[i] - g->y[j];
+                        const double d2 = dx * dx + dy * dy;
+                        if (d2 > s2max) continue;
+                        const double u = fabs(g->t[i] - g->t[j]);
+                        if (u > tmax) continue;
+                        int a = 0;
+                        while (d2 > g->s2[a]) ++a;
+                        int b = 0;
+                        while (u > g->tt[b]) ++b;
+                        double w = 1.0;
+                        if (g->edge_mode == 1) {
+                            const double om = oracle_spatial_weight(g->x[i], g->y[i], sqrt(d2),
+                                                                    g->box);
+                            const double v =
+                                oracle_temporal_weight(g->t[i], u, g->box[4], g->box[5]);
+                            w = 1.0 / (om * v);
+                        }
+                        const int k = a * g->ct + b;
+                        g->cnt[k] += 1;
+                        const double yk = w - g->comp[k];
+                        const double tk = g->wsum[k] + yk;
+                        g->comp[k] = (tk - g->wsum[k]) - yk;
+                        g->wsum[k] = tk;
+                        ++g->total;
+                    }
+                }
+            }
+        }
+    }
+    return NULL;
+}
+
+int64_t oracle_pair_hist_grid(int64_t n, const double* x, const double* y, const double* t,
+                              const double box[6], const double* s, int cs, const double* tt,
+                              int ct, int edge_mode, const uint8_t* centre_mask, int n_threads,
+                              int64_t* cnt, double* wsum) {
+    const int nb = cs * ct;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    /* cells strictly wider than the largest thresholds (a margin of 2^-20 absorbs the rounding
+     * of the cell index), at most 2^24 of them */
+    const double w = box[1] - box[0], h = box[3] - box[2], d = box[5] - box[4];
+    const double side_s = s[cs - 1] * (1.0 + 1.0 / 1048576.0);
+    const double side_t = tt[ct - 1] * (1.0 + 1.0 / 1048576.0);
+    int nx = (int)fmin(fmax(floor(w / side_s), 1.0), 4096.0);
+    int ny = (int)fmin(fmax(floor(h / side_s), 1.0), 4096.0);
+    int nt = (int)fmin(fmax(floor(d / side_t), 1.0), 4096.0);
+    while ((int64_t)nx * ny * nt > ((int64_t)1 << 24)) {
+        nx = nx > 1 ? nx / 2 : 1;
+        ny = ny > 1 ? ny / 2 : 1;
+        nt = nt > 1 ? nt / 2 : 1;
+    }
+    const double cw = w / nx, ch = h / ny, cd = d / nt;
+    const int64_t cells = (int64_t)nx * ny * nt;
+    int* cell = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int64_t* start = (int64_t*)calloc((size_t)cells + 1, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)cells, sizeof(int64_t));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double* s2 = (double*)malloc(sizeof(double) * (size_t)cs);
+    for (int a = 0; a < cs; ++a) s2[a] = s[a] * s[a];
+    for (int64_t i = 0; i < n; ++i) {
+        const int c = (grid_axis(t[i], box[4], cd, nt) * ny + grid_axis(y[i], box[2], ch, ny)) *
+                          nx +
+                      grid_axis(x[i], box[0], cw, nx);
+        cell[i] = c;
+        start[c + 1] += 1;
+    }
+    for (int64_t c = 0; c < cells; ++c) start[c + 1] += start[c];
+    for (int64_t i = 0; i < n; ++i) order[start[cell[i]] + fill[cell[i]]++] = i;
+    grid_job* jobs = (grid_job*)calloc((size_t)n_threads, sizeof(grid_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int k = 0; k < n_threads; ++k) {
+        grid_job* g = &jobs[k];
+        g->n = n, g->x = x, g->y = y, g->t = t, g->box = box, g->s = s, g->s2 = s2, g->tt = tt;
+        g->cs = cs, g->ct = ct, g->edge_mode = edge_mode, g->centre_mask = centre_mask;
+        g->nx = nx, g->ny = ny, g->nt = nt, g->start = start, g->order = order, g->cell = cell;
+        g->i0 = n * k / n_threads;
+        g->i1 = n * (k + 1) / n_threads;
+        g->cnt = (int64_t*)calloc((size_t)nb, sizeof(int64_t));
+        g->wsum = (double*)calloc((size_t)nb, sizeof(double));
+        g->comp = (double*)calloc((size_t)nb, sizeof(double));
+        g->total = 0;
+        if (n_threads == 1 || pthread_create(&th[k], NULL, grid_worker, g) != 0) {
+            th[k] = 0;
+            grid_worker(g); /* run inline when a thread cannot be started */
+        }
+    }
+    int64_t total = 0;
+    for (int k = 0; k < nb; ++k) {
+        cnt[k] = 0;
+        wsum[k] = 0.0;
+    }
+    for (int k = 0; k < n_threads; ++k) {
+        if (th[k]) pthread_join(th[k], NULL);
+        for (int q = 0; q < nb; ++q) {
+            cnt[q] += jobs[k].cnt[q];
+            wsum[q] += jobs[k].wsum[q];
+        }
+        total += jobs[k].total;
+        free(jobs[k].cnt);
+        free(jobs[k].wsum);
+        free(jobs[k].comp);
+    }
+    free(jobs);
+    free(th);
+    free(cell);
+    free(start);
+    free(fill);
+    free(order);
+    free(s2);
+    return total;
+}

@@ -150,6 +150,14 @@ int64_t oracle_pair_hist_dir(int64_t n, const double* x, const double* y, const 
                              int ct, int n_sec, int edge_mode, const uint8_t* centre_mask,
                              int64_t* cnt, double* wsum);
 
+/* oracle_pair_hist restricted to pairs in adjacent cells of a uniform grid wider
+ * than the largest thresholds, centres split over n_threads threads (pthreads):
+ * the same pairs and per-pair arithmetic, for whole grids at large n. */
+int64_t oracle_pair_hist_grid(int64_t n, const double* x, const double* y, const double* t,
+                              const double box[6], const double* s, int cs, const double* tt,
+                              int ct, int edge_mode, const uint8_t* centre_mask, int n_threads,
+                              int64_t* cnt, double* wsum);
+
 #ifdef __cplusplus
 }
 #endif

@@ -117,3 +117,24 @@ def test_large_config_in_waves(stk, orc):
     assert (Cs % 2 == 0).all()
     np.testing.assert_array_equal(got["K_lo"], Ks.min(axis=0))
     np.testing.assert_array_equal(got["K_hi"], Ks.max(axis=0))
+
+
+def test_full_observed_grids_against_grid_oracle(stk, orc):
+    # whole observed grids at full size: the benchmark's own job (2M points, observed + 99
+    # simulations in one batched FP32-guarded launch) and the Thomas configuration in FP64,
+    # against the grid-accelerated restatement of the oracle (all host cores)
+    from paper_1912_04753_gb300 import workloads as wl
+
+    for name, prec, tol, sims in (("thomas_n200k", stk.STK_PREC_FP64, 1e-9, 2),
+                                  ("poi_n2M", stk.STK_PREC_FP32_GUARDED, 1e-6, 99)):
+        w = wl.CONFIGS[name]()
+        with stk.Pattern(w.x, w.y, w.t, w.box) as p:
+            got = p.run(w.s, w.tt, n_sims=sims, seed=w.sim_seed, prec=prec)
+            assert p.stats()["internal_errors"] == 0
+        cnt, wsum, q = orc.pair_hist_grid(w.x, w.y, w.t, w.box, w.s, w.tt)
+        C, S, K, L = orc.finalize(w.n, w.box, w.s, w.tt, cnt, wsum)
+        assert q == C[-1, -1]
+        np.testing.assert_array_equal(got["C"], C)
+        assert _rel(got["S"], S).max() <= tol, name
+        assert _rel(got["K"], K).max() <= tol, name
+        assert _rel(got["L"] + w.s[:, None], L + w.s[:, None]).max() <= tol, name
