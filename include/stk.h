@@ -67,8 +67,9 @@ enum stk_status {
 /* NONE: weight 1.  ISOTROPIC: Section 3 (proportion of the circle's circumference inside the
  * study area, temporal weight 1 or 1/2).  TRANSLATION: the translation correction, pair weight
  * W H / ((W - |dx|)(H - |dy|)) * D / (D - u) (|A| over the area of the box intersected with
- * its copy shifted by the pair's offset, likewise in time; rectangle only, always in FP64):
- * unbiased for every direction, so the one the directional K (n_sectors > 1) takes. */
+ * its copy shifted by the pair's offset, likewise in time; rectangle only, always in FP64,
+ * needs t_ct <= (t1 - t0) / 2 so that the weight stays <= 8): unbiased for every direction,
+ * so the one the directional K (n_sectors > 1) takes. */
 enum { STK_EDGE_NONE = 0, STK_EDGE_ISOTROPIC = 1, STK_EDGE_TRANSLATION = 2 };
 /* FP64: every pair in IEEE double, bit-compatible with the reference definition.
  * FP32_GUARDED: pairs in FP32 with cell-relative coordinates; any pair whose

@@ -340,6 +340,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                     "weight is not unbiased direction by direction)");
     if (nsec > 1 && (int64_t)nsec * q->cs * q->ct > (int64_t)kMaxThr * kMaxThr)
         return fail(STK_EINVAL, "n_sectors * cs * ct must be at most %d", kMaxThr * kMaxThr);
+    if (q->edge_mode == STK_EDGE_TRANSLATION && q->ct >= 1 && q->tt &&
+        q->tt[q->ct - 1] > 0.5 * (h->box[5] - h->box[4]))
+        return fail(STK_EINVAL,
+                    "the translation correction needs t_ct <= half the study period (its "
+                    "temporal factor D / (D - u) then stays <= 2)");
     if (dir && (h->nv > 0 || h->inten.nix > 0 || q->labels))
         return fail(STK_EINVAL,
                     "the translation correction and the directional K need the rectangle, no "

@@ -136,6 +136,9 @@ def test_directional_arguments(stk, orc):
             p.run(s10, t10, n_sectors=41, edge_mode=2)
         assert e.value.code == stk.STK_EINVAL
         assert p.run(s10, t10, n_sectors=40, edge_mode=2)["C"].shape == (40, 10, 10)
+        with pytest.raises(stk.StkError) as e:  # t_max above half the period
+            p.run(S, np.array([10.0, 190.0]), edge_mode=2)
+        assert e.value.code == stk.STK_EINVAL
         p.set_intensity(np.ones((1, 2, 2)))
         with pytest.raises(stk.StkError) as e:
             p.run(S, TT, n_sectors=2, edge_mode=2)
