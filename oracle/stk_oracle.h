@@ -7,7 +7,7 @@
  * baseline / reference arm may load it.  It shares no code, header, table or
  * constant with the CUDA library, and the CUDA library never calls it.
  *
- * Conventions (readings of the paper, each also listed in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *   - ordered pairs (i, j), i != j, O(n^2), no index (Eq. 2 double sum);
  *   - indicator I = [d_ij <= s] * [u_ij <= t], both inclusive (Eq. 3);
  *     d2 = dx*dx + dy*dy with every operation rounded separately (no FMA),
