@@ -178,17 +178,63 @@ __device__ __forceinline__ int bin_even(float t, float tol, float top, int nthr,
     return a < nthr - 1 ? a : nthr - 1;
 }
 
+// Directional K: sector of the pair offset (dx, dy) among pc.nsec equal axial sectors of
+// [0, pi): the offset turned into the upper half plane (both orders of a pair agree), then the
+// number of boundaries b with b_x d_y - b_y d_x >= 0, each operation rounded separately;
+// coincident points in sector 0.
+__device__ __forceinline__ int sector_of(const PairConsts& pc, double dx, double dy) {
+    if (dx == 0.0 && dy == 0.0) return 0;
+    if (!(dy > 0.0 || (dy == 0.0 && dx > 0.0))) {
+        dx = -dx;
+        dy = -dy;
+    }
+    int k = 0;
+    for (int m = 0; m < pc.nsec - 1; ++m)
+        k += __dsub_rn(__dmul_rn(pc.sec_bx[m], dy), __dmul_rn(pc.sec_by[m], dx)) >= 0.0 ? 1 : 0;
+    return k;
+}
+
+// Translation correction of a pair at offset (dx, dy) and lag u: |A| / |A intersected with A
+// shifted by (dx, dy)| in space times D / (D - u) in time (at most 4 * 2 for thresholds within
+// half the sides and half the period).
+__device__ __forceinline__ double translation_weight(const PairConsts& pc, double dx, double dy,
+                                                     double u) {
+    const double es = (pc.tw * pc.th) / ((pc.tw - fabs(dx)) * (pc.th - fabs(dy)));
+    return es * (pc.td / (pc.td - u));
+}
+
 // Evaluates one queued entry in FP64.  Full entries (w bit 0 clear) are unordered pairs
 // {x, y}: bins, a count of (w bit 1) + (w bit 2) ordered pairs (the centre of each order may
 // be masked out) and the excess of those orders.  Weight-only entries (w bit 0 set) carry the
 // bin in w >> 2 and add the excess of the single ordered pair with centre x.
-template <bool POLY>
+// DIR: the directional / translation-corrected estimator (full entries only): the bin takes the
+// pair's sector, both orders the translation weight.
+template <bool POLY, bool DIR = false>
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
                                            int& bin, uint32_t& counts,
                                            unsigned long long& exc) {
     const int64_t base = (int64_t)q.z * rb.n;
     const double xi = rb.X[base + q.x], yi = rb.Y[base + q.x], ti = rb.T[base + q.x];
     const double xj = rb.X[base + q.y], yj = rb.Y[base + q.y], tj = rb.T[base + q.y];
+    if (DIR) {
+        const double dx = __dsub_rn(xi, xj);
+        const double dy = __dsub_rn(yi, yj);
+        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        const double u = fabs(__dsub_rn(ti, tj));
+        if (d2 > pc.s2[pc.cs - 1] || u > pc.tt[pc.ct - 1]) return false;
+        int a = 0;
+        while (a < pc.cs - 1 && d2 > pc.s2[a]) ++a;
+        int b = 0;
+        while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
+        const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
+        bin = (sector_of(pc, dx, dy) * pc.cs + a) * pc.ct + b;
+        counts = (uint32_t)act_i + (uint32_t)act_j;
+        const unsigned long long e =
+            pc.edge == STK_EDGE_TRANSLATION ? excess_fixed64(translation_weight(pc, dx, dy, u))
+                                            : 0ull;
+        exc = (act_i ? e : 0ull) + (act_j ? e : 0ull);
+        return true;
+    }
     if ((q.w & 1u) == 0u) {
         int a, b;
         unsigned long long ei, ej;
@@ -323,13 +369,13 @@ struct WarpCtx {
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
-template <bool POLY>
+template <bool POLY, bool DIR = false>
 __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, uint4 entry,
                                           uint32_t* hc, unsigned long long* he) {
     int bin;
     uint32_t counts;
     unsigned long long exc;
-    if (exact_eval<POLY>(*gpc, rb, entry, bin, counts, exc)) {
+    if (exact_eval<POLY, DIR>(*gpc, rb, entry, bin, counts, exc)) {
         if (counts) atomicAdd(&hc[bin], counts);
         if (exc) atomicAdd(&he[bin], exc);
     }
@@ -337,7 +383,7 @@ __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, u
 
 // Appends the flagged lanes' entries to the global FP64 queue.  If the queue is full the entry
 // is evaluated here instead (correct, only slower).
-template <bool POLY>
+template <bool POLY, bool DIR = false>
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
                                            const ExactQueue& xq, bool flag, uint4 entry,
                                            int lane, uint32_t lt, uint32_t* hc,
@@ -352,7 +398,7 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
     if (idx < xq.cap)
         xq.e[idx] = entry;
     else
-        exact_inline<POLY>(gpc, rb, entry, hc, he);
+        exact_inline<POLY, DIR>(gpc, rb, entry, hc, he);
 }
 
 // Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
@@ -480,7 +526,9 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
 }
 
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
-template <bool EVEN, bool EDGE, bool POLY>
+// DIR: the directional K / translation correction (EDGE and POLY false): every pair's sector and
+// weight are taken here.
+template <bool EVEN, bool EDGE, bool POLY, bool DIR>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
@@ -523,7 +571,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         aj[r] = act_j;
         const bool counted = has & !am;
         full[r] = has & am;
-        atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
+        if (!DIR) atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
         di[r] = dj[r] = wi[r] = wj[r] = false;
         if (edge) {
             const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
@@ -543,6 +591,68 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             vj[r] = vhj;
         }
         rare |= full[r] | wi[r] | wj[r] | di[r] | dj[r];
+    }
+    if (DIR) {
+        // Sector from the hi parts (their differences are exact); a cross product within its
+        // guard of a boundary, or an offset within the guard of the axis at angle 0 / pi,
+        // leaves the pair to FP64.  Translation weight in FP32 (a few ulp; no cancellation:
+        // W - |dx| >= W / 2, D - u >= D / 2).
+        bool xf[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            xf[r] = full[r];
+            if (!(r * 32 + lane < cnt) || full[r]) continue;
+            const uint32_t meta = e[r].z, j = e[r].w;
+            const int cl = (int)(meta & 31u);
+            const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
+            const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
+            const float4 ca = ws.cen_a[cl];
+            const float4 qj = w.Pk[2 * (size_t)j];
+            float dx = fmaf(dcx, pc.g.cwq, ca.x) - qj.x;
+            float dy = fmaf(dcy, pc.g.chq, ca.y) - qj.y;
+            int k = 0;
+            bool und = false;
+            if (pc.nsec > 1) {
+                und = fabsf(dy) <= pc.sec_gd;
+                if (dy < 0.0f) {
+                    dx = -dx;
+                    dy = -dy;
+                }
+                for (int m = 0; m < pc.nsec - 1; ++m) {
+                    const float cr = fmaf(pc.sec_bxf[m], dy, -(pc.sec_byf[m] * dx));
+                    und |= fabsf(cr) <= pc.sec_g;
+                    k += cr > 0.0f ? 1 : 0;
+                }
+            }
+            if (und) {
+                xf[r] = true;
+                continue;
+            }
+            const int b3 = k * (pc.cs * pc.ct) + bin[r];
+            atomicAdd(&w.hc[b3], (uint32_t)ai[r] + (uint32_t)aj[r]);
+            if (pc.edge == STK_EDGE_TRANSLATION) {
+                const float u = __uint_as_float(e[r].y);
+                const float wt = (pc.twf * __frcp_rn(pc.twf - fabsf(dx))) *
+                                 (pc.thf * __frcp_rn(pc.thf - fabsf(dy))) *
+                                 (pc.tdf * __frcp_rn(pc.tdf - u));
+                const float xs = wt - 1.0f;
+                const unsigned long long e1 =
+                    xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
+                const unsigned long long exc = (ai[r] ? e1 : 0ull) + (aj[r] ? e1 : 0ull);
+                if (exc) atomicAdd(&w.he[b3], exc);
+            }
+        }
+        if (__any_sync(0xffffffffu, xf[0] | xf[1])) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
+                push_exact<false, true>(
+                    gpc, rb, xq, xf[r],
+                    make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
+                    lane, lt, w.hc, w.he);
+            }
+        }
+        return;
     }
     if (!__any_sync(0xffffffffu, rare)) return;
     // FP64 entries: rare enough that one vote usually skips them all
@@ -590,7 +700,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
 }
 
 // Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
-template <bool EVEN, bool EDGE, bool POLY>
+template <bool EVEN, bool EDGE, bool POLY, bool DIR>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
                                           const ExactQueue& xq, uint32_t& tail, int lane,
@@ -598,7 +708,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     while (tail > 0) {
         const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
+        drain_pairs<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
         for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
@@ -617,7 +727,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
 }
 
-template <bool EVEN, bool EDGE, bool POLY>
+template <bool EVEN, bool EDGE, bool POLY, bool DIR>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
                  int m, RealBatch rb,
@@ -773,7 +883,8 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                             tail = t3 + (uint32_t)__popc(m3);
                             while (tail >= (uint32_t)kDrain) {
                                 __syncwarp();
-                                drain_pairs<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, kDrain, lane, lt, w);
+                                drain_pairs<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, kDrain, lane,
+                                                                   lt, w);
                                 __syncwarp();
                                 const uint32_t rest = tail - kDrain;
                                 uint4 v[4];
@@ -792,7 +903,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                     }
                 }
             }
-            drain_all<EVEN, EDGE, POLY>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
+            drain_all<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
             if (since_flush >= kWarpFlush) {
                 warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
                 since_flush = 0;
@@ -851,31 +962,6 @@ struct Smem64 {
     PairConsts pc;
     WarpSm64 w[kWarps];
 };
-
-// Directional K: sector of the pair offset (dx, dy) among pc.nsec equal axial sectors of
-// [0, pi): the offset turned into the upper half plane (both orders of a pair agree), then the
-// number of boundaries b with b_x d_y - b_y d_x >= 0, each operation rounded separately;
-// coincident points in sector 0.
-__device__ __forceinline__ int sector_of(const PairConsts& pc, double dx, double dy) {
-    if (dx == 0.0 && dy == 0.0) return 0;
-    if (!(dy > 0.0 || (dy == 0.0 && dx > 0.0))) {
-        dx = -dx;
-        dy = -dy;
-    }
-    int k = 0;
-    for (int m = 0; m < pc.nsec - 1; ++m)
-        k += __dsub_rn(__dmul_rn(pc.sec_bx[m], dy), __dmul_rn(pc.sec_by[m], dx)) >= 0.0 ? 1 : 0;
-    return k;
-}
-
-// Translation correction of a pair at offset (dx, dy) and lag u: |A| / |A intersected with A
-// shifted by (dx, dy)| in space times D / (D - u) in time (at most 4 * 2 for thresholds within
-// half the sides and half the period).
-__device__ __forceinline__ double translation_weight(const PairConsts& pc, double dx, double dy,
-                                                     double u) {
-    const double es = (pc.tw * pc.th) / ((pc.tw - fabs(dx)) * (pc.th - fabs(dy)));
-    return es * (pc.td / (pc.td - u));
-}
 
 // Bins and weights of `cnt` (<= 32) queued pairs, one per lane, with the reference rounding.
 template <bool POLY, bool INH, bool DIR>
@@ -1130,7 +1216,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
 
 // Evaluates the pairs the FP32 kernel queued, 32 per warp, and adds them to the global
 // accumulators (integer atomics, so the order does not matter).
-template <bool POLY>
+template <bool POLY, bool DIR>
 __global__ void __launch_bounds__(256)
 exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQueue xq) {
     const unsigned int pushed = *xq.count;
@@ -1143,7 +1229,7 @@ exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQ
         int bin;
         uint32_t counts;
         unsigned long long exc;
-        if (!exact_eval<POLY>(pc, rb, q, bin, counts, exc)) continue;
+        if (!exact_eval<POLY, DIR>(pc, rb, q, bin, counts, exc)) continue;
         const int64_t o = (int64_t)q.z * pc.nbins + bin;
         if (counts) atomicAdd(&acc.cnt[o], (unsigned long long)counts);
         if (exc & 0xffffffffull) atomicAdd(&acc.exc_lo[o], exc & 0xffffffffull);
@@ -1270,12 +1356,14 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));
     if (e != cudaSuccess) return e;
-    const void* k32[6] = {(const void*)pair_fp32_kernel<false, false, false>,
-                          (const void*)pair_fp32_kernel<false, true, false>,
-                          (const void*)pair_fp32_kernel<true, false, false>,
-                          (const void*)pair_fp32_kernel<true, true, false>,
-                          (const void*)pair_fp32_kernel<false, true, true>,
-                          (const void*)pair_fp32_kernel<true, true, true>};
+    const void* k32[8] = {(const void*)pair_fp32_kernel<false, false, false, false>,
+                          (const void*)pair_fp32_kernel<false, true, false, false>,
+                          (const void*)pair_fp32_kernel<true, false, false, false>,
+                          (const void*)pair_fp32_kernel<true, true, false, false>,
+                          (const void*)pair_fp32_kernel<false, true, true, false>,
+                          (const void*)pair_fp32_kernel<true, true, true, false>,
+                          (const void*)pair_fp32_kernel<false, false, false, true>,
+                          (const void*)pair_fp32_kernel<true, false, false, true>};
     for (const void* f : k32) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
@@ -1297,7 +1385,7 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
 
 int pair_fp32_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false, false>,
                                                       kBlock, smem) !=
         cudaSuccess)
         return 1;
@@ -1321,10 +1409,20 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st) {
     const bool poly = edge && hpc.nv > 0;
+    // directional K / translation correction: its own instantiation (no isotropic logic)
+    const bool dir = hpc.nsec > 1 || hpc.edge == STK_EDGE_TRANSLATION;
 #define STK_PAIR32(E, D, P)                                                                  \
-    pair_fp32_kernel<E, D, P><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units, unit_off, \
-                                                          counters, acc, xq, reps)
-    if (poly && even)
+    pair_fp32_kernel<E, D, P, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units,    \
+                                                                 unit_off, counters, acc, xq, \
+                                                                 reps)
+    if (dir && poly) return cudaErrorInvalidValue;
+    if (dir && even)
+        pair_fp32_kernel<true, false, false, true><<<grid, kBlock, smem, st>>>(
+            hpc, d_pc, m, rb, units, unit_off, counters, acc, xq, reps);
+    else if (dir)
+        pair_fp32_kernel<false, false, false, true><<<grid, kBlock, smem, st>>>(
+            hpc, d_pc, m, rb, units, unit_off, counters, acc, xq, reps);
+    else if (poly && even)
         STK_PAIR32(true, true, true);
     else if (poly)
         STK_PAIR32(false, true, true);
@@ -1341,11 +1439,14 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
 }
 
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
-                         ExactQueue xq, cudaStream_t st, bool poly) {
-    if (poly)
-        exact_kernel<true><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+                         ExactQueue xq, cudaStream_t st, bool poly, bool dir) {
+    if (dir && poly) return cudaErrorInvalidValue;
+    if (dir)
+        exact_kernel<false, true><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+    else if (poly)
+        exact_kernel<true, false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     else
-        exact_kernel<false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+        exact_kernel<false, false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     return cudaGetLastError();
 }
 

@@ -128,8 +128,7 @@ bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
 
 // The FP32-guarded pair kernel, unless the job is an inhomogeneous K (always FP64).
 bool fp32_path(const stk_handle* h, const stk_request* q) {
-    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0 &&
-           q->edge_mode != STK_EDGE_TRANSLATION && q->n_sectors <= 1;
+    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0;
 }
 
 int check_box(const stk_box* b) {
@@ -419,6 +418,22 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->h_pc->tw = h->box[1] - h->box[0];
     h->h_pc->th = h->box[3] - h->box[2];
     h->h_pc->td = h->box[5] - h->box[4];
+    // FP32 directional kernel: boundaries and sides rounded to FP32; the sector test's guard
+    // covers the rounding of the boundaries (2^-24 per component), of the FP32 cross product
+    // (2^-24 of each product) and the hi parts' distance from the FP64 offset (at most one
+    // quantum per axis): |cross_FP32 - cross_FP64| < 2^-22 sqrt(2) s_max + sqrt(2) q
+    for (int m = 1; m < nsec; ++m) {
+        h->h_pc->sec_bxf[m - 1] = (float)h->h_pc->sec_bx[m - 1];
+        h->h_pc->sec_byf[m - 1] = (float)h->h_pc->sec_by[m - 1];
+    }
+    h->h_pc->twf = (float)h->h_pc->tw;
+    h->h_pc->thf = (float)h->h_pc->th;
+    h->h_pc->tdf = (float)h->h_pc->td;
+    {
+        const double qm = std::max((double)g.qx, (double)g.qy);
+        h->h_pc->sec_g = (float)(5.0e-7 * q->s[cs - 1] + 2.0 * qm);
+        h->h_pc->sec_gd = (float)(2.0 * qm);
+    }
     Polygon poly;
     if (h->nv > 0) {
         poly.vx = as<double>(h->poly);
@@ -711,7 +726,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                "pair kernel (FP64)");
         if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
         if (fp32) {
-            CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st, h->nv > 0),
+            CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st, h->nv > 0,
+                            dir),
                "FP64 queue");
         }
         const int64_t row = (int64_t)r0 * nbins;

@@ -83,6 +83,12 @@ struct PairConsts {
     int nsec;
     double sec_bx[kMaxSectors], sec_by[kMaxSectors];
     double tw, th, td;
+    // the same in FP32 for the FP32-guarded directional kernel: boundaries rounded to FP32,
+    // sides, and the guards of the sector test (|cross| <= sec_g, or |d_y| <= sec_gd near the
+    // axis at angle 0 / pi: FP64 decides)
+    float sec_bxf[kMaxSectors], sec_byf[kMaxSectors];
+    float twf, thf, tdf;
+    float sec_g, sec_gd;
 };
 
 // One unit of pair work for one warp: the centres [c_begin, c_begin + c_count) (at most 32,
@@ -214,7 +220,7 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st);
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
-                         ExactQueue xq, cudaStream_t st, bool poly = false);
+                         ExactQueue xq, cudaStream_t st, bool poly = false, bool dir = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
                              uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false,
