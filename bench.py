@@ -418,31 +418,37 @@ def run_ours(args):
                    "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
                    "fp64_queue_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
 
-    # the inhomogeneous K (intensity-weighted pairs, FP64 throughout) on the Thomas pattern with
-    # a histogram intensity, observed + 99 intensity-weighted simulations
+    # the inhomogeneous K (intensity-weighted pairs; FP32-guarded and FP64) on the Thomas
+    # pattern with a histogram intensity, observed + 99 intensity-weighted simulations
     inhom = None
     if args.inhom and rank == 0:
         wi = _workload("thomas_inhom_n200k")
+        times = {}
         with stk.Pattern(wi.x, wi.y, wi.t, wi.box) as pi_:
             pi_.set_intensity(wi.meta["rho"])
             stk.stk_set_stream(pi_.h, stream)
-            pi_.run(wi.s, wi.tt, n_sims=wi.n_sims, seed=seed, exec_mode=exec_mode)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pi_.run(wi.s, wi.tt, n_sims=wi.n_sims, seed=seed, exec_mode=exec_mode)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms_i = e0.elapsed_time(e1)
-            si = pi_.stats()
+            for pname, pv in (("fp32", stk.STK_PREC_FP32_GUARDED), ("fp64", stk.STK_PREC_FP64)):
+                kw = dict(n_sims=wi.n_sims, seed=seed, exec_mode=exec_mode, prec=pv)
+                pi_.run(wi.s, wi.tt, **kw)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pi_.run(wi.s, wi.tt, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times[pname] = (e0.elapsed_time(e1), pi_.stats())
+        ms_i, si = times["fp32"]
         inhom = {"workload": wi.name, "n": wi.n, "intensity_cells": list(wi.meta["rho"].shape),
-                 "sims": wi.n_sims, "dtype": "f64", "job_s": ms_i / 1e3,
+                 "sims": wi.n_sims, "dtype": "f32 (guarded, f64 ties)", "job_s": ms_i / 1e3,
                  "sims_per_s": wi.n_sims / (ms_i / 1e3),
                  "value": si["qualifying_pairs"] / (ms_i / 1e3), "unit": UNIT,
-                 "pair_kernel_s": si["ms_pair"] / 1e3}
+                 "pair_kernel_s": si["ms_pair"] / 1e3,
+                 "fp64_recomputed": si["fp64_recomputed"],
+                 "fp64_job_s": times["fp64"][0] / 1e3}
 
-    # the directional K (8 axial sectors, translation correction, FP64) on the Thomas pattern,
-    # observed + 99 CSR simulations
+    # the directional K (8 axial sectors, translation correction; FP32-guarded and FP64) on the
+    # Thomas pattern, observed + 99 CSR simulations
     directional = None
     if args.directional and rank == 0:
         wd = _workload("thomas_n200k")

@@ -28,6 +28,10 @@ namespace stk {
 namespace {
 
 constexpr int kWarps = kBlock / 32;
+// variants of the FP32-guarded kernel and of its FP64 queue
+constexpr int kVarPlain = 0;  // Eq. 2 (isotropic correction or none, rectangle or polygon)
+constexpr int kVarDir = 1;    // directional K / translation correction
+constexpr int kVarInh = 2;    // inhomogeneous K
 
 // ---------------------------------------------------------------- exact FP64 pair (reference)
 
@@ -148,6 +152,76 @@ __device__ __forceinline__ void warp_flush(int real, int nbins, uint32_t* hc, ui
     }
 }
 
+// Inhomogeneous K: a pair weight W = h_i h_j / (w v) in fixed point, split so that every part is
+// a plain integer sum: the whole part, and the fraction in units of 2^-64 as two 32-bit halves.
+// W < 2^32 (h is at most 2^14 and 1 / (w v) at most 8).
+struct Fix96 {
+    unsigned long long whole = 0, lo = 0, hi = 0;
+};
+
+__device__ __forceinline__ void add_fix96(double W, Fix96& f) {
+    const double wh = floor(W);
+    const unsigned long long m = __double2ull_rn(__dsub_rn(W, wh) * 18446744073709551616.0);
+    f.whole += (unsigned long long)wh;
+    f.lo += m & 0xffffffffull;
+    f.hi += m >> 32;
+}
+
+// Adds a replica's sums to the global accumulators: lo (2^-64 units) and hi (2^-32 units) are
+// re-split so that each global add is below 2^32 (no overflow however many flushes).
+__device__ __forceinline__ void add_fix96_global(const Accum& acc, int64_t o,
+                                                 unsigned long long whole,
+                                                 unsigned long long lo,
+                                                 unsigned long long hi) {
+    const unsigned long long g_lo = lo & 0xffffffffull;
+    const unsigned long long g_hi = (lo >> 32) + (hi & 0xffffffffull);
+    const unsigned long long g_whole = whole + (hi >> 32);
+    if (g_lo) atomicAdd(&acc.exc_lo[o], g_lo);
+    if (g_hi) atomicAdd(&acc.exc_hi[o], g_hi);
+    if (g_whole) atomicAdd(&acc.whole[o], g_whole);
+}
+
+// Inhomogeneous K: flushes of the three fixed-point sums (see flush_hist and warp_flush).
+__device__ __forceinline__ void flush_hist_inh(int real, int nbins, int reps, uint32_t* hc,
+                                               unsigned long long* he, unsigned long long* hf,
+                                               unsigned long long* hw, const Accum& acc) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += kBlock) {
+        uint32_t c = 0;
+        unsigned long long lo = 0, hi = 0, wh = 0;
+        for (int r = 0; r < reps; ++r) {
+            const int i = r * nbins + b;
+            c += hc[i];
+            lo += he[i];
+            hi += hf[i];
+            wh += hw[i];
+            hc[i] = 0;
+            he[i] = 0;
+            hf[i] = 0;
+            hw[i] = 0;
+        }
+        const int64_t o = (int64_t)real * nbins + b;
+        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
+        add_fix96_global(acc, o, wh, lo, hi);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void warp_flush_inh(int real, int nbins, uint32_t* hc,
+                                               unsigned long long* he, unsigned long long* hf,
+                                               unsigned long long* hw, const Accum& acc,
+                                               int lane) {
+    for (int b = lane; b < nbins; b += 32) {
+        const uint32_t c = atomicExch(&hc[b], 0u);
+        const unsigned long long lo = atomicExch(&he[b], 0ull);
+        const unsigned long long hi = atomicExch(&hf[b], 0ull);
+        const unsigned long long wh = atomicExch(&hw[b], 0ull);
+        const int64_t o = (int64_t)real * nbins + b;
+        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
+        add_fix96_global(acc, o, wh, lo, hi);
+    }
+}
+
 __device__ __forceinline__ int bin_fp32(float v, float inv_h, const uint8_t* tab,
                                         const float* lo, const float* hi, int nthr, bool& amb) {
     int k = (int)(v * inv_h);
@@ -207,16 +281,40 @@ __device__ __forceinline__ double translation_weight(const PairConsts& pc, doubl
 // {x, y}: bins, a count of (w bit 1) + (w bit 2) ordered pairs (the centre of each order may
 // be masked out) and the excess of those orders.  Weight-only entries (w bit 0 set) carry the
 // bin in w >> 2 and add the excess of the single ordered pair with centre x.
-// DIR: the directional / translation-corrected estimator (full entries only): the bin takes the
-// pair's sector, both orders the translation weight.
-template <bool POLY, bool DIR = false>
+// kVarDir: the directional / translation-corrected estimator (full entries only): the bin
+// takes the pair's sector, both orders the translation weight.  kVarInh: the inhomogeneous K
+// (full entries only): the weights of both orders times h_i h_j, returned in *fx.
+template <bool POLY, int VAR = kVarPlain>
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
                                            int& bin, uint32_t& counts,
-                                           unsigned long long& exc) {
+                                           unsigned long long& exc, Fix96* fx = nullptr) {
     const int64_t base = (int64_t)q.z * rb.n;
     const double xi = rb.X[base + q.x], yi = rb.Y[base + q.x], ti = rb.T[base + q.x];
     const double xj = rb.X[base + q.y], yj = rb.Y[base + q.y], tj = rb.T[base + q.y];
-    if (DIR) {
+    if (VAR == kVarInh) {
+        int a, b;
+        unsigned long long ei, ej;
+        if (!pair_exact<false>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
+        const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
+        bin = a * pc.ct + b;
+        counts = (uint32_t)act_i + (uint32_t)act_j;
+        exc = 0;
+        const double hh = __dmul_rn(rb.H[base + q.x], rb.H[base + q.y]);
+        double wi = 1.0, wj = 1.0;
+        if (pc.edge) {
+            const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
+            const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+            const double u = fabs(__dsub_rn(ti, tj));
+            wi = 1.0 / (omega64<false>(pc, xi, yi, r) * v64(pc, ti, u));
+            wj = 1.0 / (omega64<false>(pc, xj, yj, r) * v64(pc, tj, u));
+        }
+        Fix96 f;
+        if (act_i) add_fix96(__dmul_rn(wi, hh), f);
+        if (act_j) add_fix96(__dmul_rn(wj, hh), f);
+        *fx = f;
+        return true;
+    }
+    if (VAR == kVarDir) {
         const double dx = __dsub_rn(xi, xj);
         const double dy = __dsub_rn(yi, yj);
         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
@@ -289,6 +387,7 @@ struct WarpSm {
     float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2
     float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
+    float cen_h[32];    // inhomogeneous K: h of the centres
     uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 |
                             // dcy << 8; the extra slot takes the stores of idle lanes
     uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
@@ -366,28 +465,43 @@ struct WarpCtx {
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
     const PairConsts* pa;     // shared-memory copy (indexed tables and bands)
+    // inhomogeneous K: the weights' fraction high halves and whole parts (`he` holds the low
+    // halves), and h and the low parts of the current realization's points
+    unsigned long long* hf;
+    unsigned long long* hw;
+    const double* H;
+    const float2* Plok;
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
-template <bool POLY, bool DIR = false>
+template <bool POLY, int VAR = kVarPlain>
 __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, uint4 entry,
-                                          uint32_t* hc, unsigned long long* he) {
+                                          uint32_t* hc, unsigned long long* he,
+                                          unsigned long long* hf, unsigned long long* hw) {
     int bin;
     uint32_t counts;
     unsigned long long exc;
-    if (exact_eval<POLY, DIR>(*gpc, rb, entry, bin, counts, exc)) {
+    Fix96 f;
+    if (exact_eval<POLY, VAR>(*gpc, rb, entry, bin, counts, exc, &f)) {
         if (counts) atomicAdd(&hc[bin], counts);
         if (exc) atomicAdd(&he[bin], exc);
+        if (VAR == kVarInh) {
+            if (f.lo) atomicAdd(&he[bin], f.lo);
+            if (f.hi) atomicAdd(&hf[bin], f.hi);
+            if (f.whole) atomicAdd(&hw[bin], f.whole);
+        }
     }
 }
 
 // Appends the flagged lanes' entries to the global FP64 queue.  If the queue is full the entry
 // is evaluated here instead (correct, only slower).
-template <bool POLY, bool DIR = false>
+template <bool POLY, int VAR = kVarPlain>
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
                                            const ExactQueue& xq, bool flag, uint4 entry,
                                            int lane, uint32_t lt, uint32_t* hc,
-                                           unsigned long long* he) {
+                                           unsigned long long* he,
+                                           unsigned long long* hf = nullptr,
+                                           unsigned long long* hw = nullptr) {
     const uint32_t m = __ballot_sync(0xffffffffu, flag);
     if (m == 0u) return;
     unsigned int pos = 0;
@@ -398,7 +512,7 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
     if (idx < xq.cap)
         xq.e[idx] = entry;
     else
-        exact_inline<POLY, DIR>(gpc, rb, entry, hc, he);
+        exact_inline<POLY, VAR>(gpc, rb, entry, hc, he, hf, hw);
 }
 
 // Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
@@ -525,10 +639,20 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
     w.q2n = rest;
 }
 
+// FP32 weight W (< 2^32) in the inhomogeneous fixed point (see Fix96): whole part and the
+// fraction in units of 2^-64 (exact: the fraction has 24 significant bits).
+__device__ __forceinline__ void add_fix96f(float W, Fix96& f) {
+    const float wh = floorf(W);
+    const unsigned long long m = __float2ull_rn((W - wh) * 18446744073709551616.0f);
+    f.whole += (unsigned long long)wh;
+    f.lo += m & 0xffffffffull;
+    f.hi += m >> 32;
+}
+
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
-// DIR: the directional K / translation correction (EDGE and POLY false): every pair's sector and
-// weight are taken here.
-template <bool EVEN, bool EDGE, bool POLY, bool DIR>
+// VAR kVarDir: the directional K / translation correction (EDGE and POLY false); kVarInh: the
+// inhomogeneous K (POLY false).  Both take every pair's weights here.
+template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
@@ -571,9 +695,10 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         aj[r] = act_j;
         const bool counted = has & !am;
         full[r] = has & am;
-        if (!DIR) atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
+        if (VAR == kVarPlain)
+            atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
         di[r] = dj[r] = wi[r] = wj[r] = false;
-        if (edge) {
+        if (edge && VAR == kVarPlain) {
             const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
             const float te_j = pj[r].z, rin_j = pj[r].w;
             const bool vhi = u > te_i + pc.g_v, vhj = u > te_j + pc.g_v;
@@ -592,7 +717,88 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         }
         rare |= full[r] | wi[r] | wj[r] | di[r] | dj[r];
     }
-    if (DIR) {
+    if (VAR == kVarInh) {
+        // h_i h_j times the weights of both orders, in FP32 (a few ulp); the temporal weight
+        // and the interior tests as in the rectangle path, the spatial weight inline as in
+        // phase C; anything FP32 cannot decide sends the whole pair to FP64.
+        bool xf[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            xf[r] = full[r];
+            if (!(r * 32 + lane < cnt) || full[r]) continue;
+            const uint32_t meta = e[r].z, j = e[r].w;
+            const int cl = (int)(meta & 31u);
+            const float d2 = __uint_as_float(e[r].x), u = __uint_as_float(e[r].y);
+            const float hh = ws.cen_h[cl] * (float)w.H[j];
+            float wgt[2] = {1.0f, 1.0f};
+            bool und = false;
+            if (edge) {
+                const float4 ca = ws.cen_a[cl];
+                const float4 cb = ws.cen_b[cl];
+                const float te[2] = {ws.cen_te[cl], pj[r].z};
+                const float rin[2] = {ca.w, pj[r].w};
+                const float ex[2] = {cb.z, pj[r].x}, ey[2] = {cb.w, pj[r].y};
+                float ra = -1.0f;
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const bool vh = u > te[o] + pc.g_v;
+                    und |= (u > te[o] - pc.g_v) & !vh;
+                    float wsp = 1.0f;
+                    if (!(d2 <= rin[o])) {
+                        if (ra < 0.0f) {  // accurate distance from the hi + lo parts
+                            const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
+                            const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
+                            const float4 p = w.Pk[2 * (size_t)j];
+                            const float2 lo = w.Plok[j];
+                            const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) +
+                                              (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
+                            const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) +
+                                              (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+                            ra = sqrtf(fmaf(dxa, dxa, dya * dya));
+                        }
+                        const float e1 = fminf(ex[o], ey[o]), e2 = fmaxf(ex[o], ey[o]);
+                        const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
+                        if (ra < pc.r_acc_min || fabsf(ra - e1) <= band ||
+                            fabsf(ra - e2) <= band) {
+                            und = true;
+                        } else {
+                            float a1 = 0.0f, a2 = 0.0f;
+                            if (e1 < ra) a1 = atan2f(sqrtf((ra - e1) * (ra + e1)), e1);
+                            if (e2 < ra) a2 = atan2f(sqrtf((ra - e2) * (ra + e2)), e2);
+                            const float A = (fmaf(e1, e1, e2 * e2) < ra * ra)
+                                                ? (a1 + a2 + 1.57079632679f) * 0.159154943092f
+                                                : (a1 + a2) * 0.318309886184f;
+                            wsp = 1.0f / (1.0f - A);
+                        }
+                    }
+                    wgt[o] = (vh ? 2.0f : 1.0f) * wsp;
+                }
+            }
+            if (und) {
+                xf[r] = true;
+                continue;
+            }
+            atomicAdd(&w.hc[bin[r]], (uint32_t)ai[r] + (uint32_t)aj[r]);
+            Fix96 f;
+            if (ai[r]) add_fix96f(wgt[0] * hh, f);
+            if (aj[r]) add_fix96f(wgt[1] * hh, f);
+            if (f.lo) atomicAdd(&w.he[bin[r]], f.lo);
+            if (f.hi) atomicAdd(&w.hf[bin[r]], f.hi);
+            if (f.whole) atomicAdd(&w.hw[bin[r]], f.whole);
+        }
+        if (__any_sync(0xffffffffu, xf[0] | xf[1])) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
+                push_exact<false, kVarInh>(
+                    gpc, rb, xq, xf[r],
+                    make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
+                    lane, lt, w.hc, w.he, w.hf, w.hw);
+            }
+        }
+        return;
+    }
+    if (VAR == kVarDir) {
         // Sector from the hi parts (their differences are exact); a cross product within its
         // guard of a boundary, or an offset within the guard of the axis at angle 0 / pi,
         // leaves the pair to FP64.  Translation weight in FP32 (a few ulp; no cancellation:
@@ -646,7 +852,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
-                push_exact<false, true>(
+                push_exact<false, kVarDir>(
                     gpc, rb, xq, xf[r],
                     make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
                     lane, lt, w.hc, w.he);
@@ -700,7 +906,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
 }
 
 // Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
-template <bool EVEN, bool EDGE, bool POLY, bool DIR>
+template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
                                           const ExactQueue& xq, uint32_t& tail, int lane,
@@ -708,7 +914,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     while (tail > 0) {
         const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
+        drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
         for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
@@ -727,7 +933,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
 }
 
-template <bool EVEN, bool EDGE, bool POLY, bool DIR>
+template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
                  int m, RealBatch rb,
@@ -747,18 +953,31 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
     WarpSm& ws = sm.w[warp];
     const int nbins = pc.nbins;
     const size_t hist_off = (sizeof(Smem32) + 15) & ~size_t(15);
+    // per replica: he [nbins] u64, then for the inhomogeneous K hf and hw [nbins] u64, then hc
+    // [nbins] u32 and (otherwise) hh [nbins] u32
     unsigned long long* he = reinterpret_cast<unsigned long long*>(smem_raw + hist_off);
-    uint32_t* hc = reinterpret_cast<uint32_t*>(he + (size_t)reps * nbins);
+    unsigned long long* hf = he + (size_t)reps * nbins;
+    unsigned long long* hw = hf + (size_t)reps * nbins;
+    uint32_t* hc = reinterpret_cast<uint32_t*>(VAR == kVarInh ? hw + (size_t)reps * nbins : hf);
     uint32_t* hh = hc + (size_t)reps * nbins;
     for (int i = tid; i < reps * nbins; i += kBlock) {
         hc[i] = 0;
-        hh[i] = 0;
         he[i] = 0;
+        if (VAR == kVarInh) {
+            hf[i] = 0;
+            hw[i] = 0;
+        } else {
+            hh[i] = 0;
+        }
     }
     WarpCtx w;
     w.hc = hc + (warp % reps) * nbins;
     w.hh = hh + (warp % reps) * nbins;
     w.he = he + (warp % reps) * nbins;
+    w.hf = hf + (warp % reps) * nbins;
+    w.hw = hw + (warp % reps) * nbins;
+    w.H = nullptr;
+    w.Plok = nullptr;
     w.q2n = 0;
     w.deep = false;
     w.pa = &sm.pc;
@@ -777,6 +996,8 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         const float4* Pk = rb.P + 2 * base;
         w.Pk = Pk;
         w.real = (uint32_t)k;
+        w.Plok = rb.Plo + base;
+        if (VAR == kVarInh) w.H = rb.H + base;
         w.mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
                    ? rb.mask + (rb.mask_all ? base : 0)
                    : nullptr;
@@ -799,6 +1020,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             ws.cen_a[lane] = make_float4(p.x, p.y, p.z, pe.w);
             ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
             ws.cen_te[lane] = pe.z;
+            if (VAR == kVarInh) ws.cen_h[lane] = (float)w.H[myi];
             const uint32_t fl = w.mk == nullptr ? 3u : (uint32_t)w.mk[myi];
             w.onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
             w.onB = __ballot_sync(0xffffffffu, valid && (fl & 2u));
@@ -883,7 +1105,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                             tail = t3 + (uint32_t)__popc(m3);
                             while (tail >= (uint32_t)kDrain) {
                                 __syncwarp();
-                                drain_pairs<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, kDrain, lane,
+                                drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, kDrain, lane,
                                                                    lt, w);
                                 __syncwarp();
                                 const uint32_t rest = tail - kDrain;
@@ -903,15 +1125,21 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                     }
                 }
             }
-            drain_all<EVEN, EDGE, POLY, DIR>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
+            drain_all<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
             if (since_flush >= kWarpFlush) {
-                warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
+                if (VAR == kVarInh)
+                    warp_flush_inh(k, nbins, w.hc, w.he, w.hf, w.hw, acc, lane);
+                else
+                    warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
                 since_flush = 0;
             }
         }
         __syncthreads();
         // every warp of the block is done with realization k: add its histograms
-        flush_hist(k, nbins, reps, hc, he, acc, hh);
+        if (VAR == kVarInh)
+            flush_hist_inh(k, nbins, reps, hc, he, hf, hw, acc);
+        else
+            flush_hist(k, nbins, reps, hc, he, acc, hh);
         since_flush = 0;
     }
     for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
@@ -928,35 +1156,6 @@ struct WarpSm64 {
     double ch[32];       // inhomogeneous K: h of the centres
     uint2 ring[kRing];   // (lane, neighbour)
 };
-
-// Inhomogeneous K: a pair weight W = h_i h_j / (w v) in fixed point, split so that every part is
-// a plain integer sum: the whole part, and the fraction in units of 2^-64 as two 32-bit halves.
-// W < 2^32 (h is at most 2^14 and 1 / (w v) at most 8).
-struct Fix96 {
-    unsigned long long whole = 0, lo = 0, hi = 0;
-};
-
-__device__ __forceinline__ void add_fix96(double W, Fix96& f) {
-    const double wh = floor(W);
-    const unsigned long long m = __double2ull_rn(__dsub_rn(W, wh) * 18446744073709551616.0);
-    f.whole += (unsigned long long)wh;
-    f.lo += m & 0xffffffffull;
-    f.hi += m >> 32;
-}
-
-// Adds a replica's sums to the global accumulators: lo (2^-64 units) and hi (2^-32 units) are
-// re-split so that each global add is below 2^32 (no overflow however many flushes).
-__device__ __forceinline__ void add_fix96_global(const Accum& acc, int64_t o,
-                                                 unsigned long long whole,
-                                                 unsigned long long lo,
-                                                 unsigned long long hi) {
-    const unsigned long long g_lo = lo & 0xffffffffull;
-    const unsigned long long g_hi = (lo >> 32) + (hi & 0xffffffffull);
-    const unsigned long long g_whole = whole + (hi >> 32);
-    if (g_lo) atomicAdd(&acc.exc_lo[o], g_lo);
-    if (g_hi) atomicAdd(&acc.exc_hi[o], g_hi);
-    if (g_whole) atomicAdd(&acc.whole[o], g_whole);
-}
 
 struct Smem64 {
     PairConsts pc;
@@ -1032,47 +1231,6 @@ __device__ __forceinline__ void process64(const PairConsts& pc, const WarpSm64& 
     }
     atomicAdd(&hc[bin], (uint32_t)act_i + (uint32_t)act_j);
     if (exc) atomicAdd(&he[bin], exc);
-}
-
-// Inhomogeneous K: flushes of the three fixed-point sums (see flush_hist and warp_flush).
-__device__ __forceinline__ void flush_hist_inh(int real, int nbins, int reps, uint32_t* hc,
-                                               unsigned long long* he, unsigned long long* hf,
-                                               unsigned long long* hw, const Accum& acc) {
-    __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += kBlock) {
-        uint32_t c = 0;
-        unsigned long long lo = 0, hi = 0, wh = 0;
-        for (int r = 0; r < reps; ++r) {
-            const int i = r * nbins + b;
-            c += hc[i];
-            lo += he[i];
-            hi += hf[i];
-            wh += hw[i];
-            hc[i] = 0;
-            he[i] = 0;
-            hf[i] = 0;
-            hw[i] = 0;
-        }
-        const int64_t o = (int64_t)real * nbins + b;
-        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
-        add_fix96_global(acc, o, wh, lo, hi);
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ void warp_flush_inh(int real, int nbins, uint32_t* hc,
-                                               unsigned long long* he, unsigned long long* hf,
-                                               unsigned long long* hw, const Accum& acc,
-                                               int lane) {
-    for (int b = lane; b < nbins; b += 32) {
-        const uint32_t c = atomicExch(&hc[b], 0u);
-        const unsigned long long lo = atomicExch(&he[b], 0ull);
-        const unsigned long long hi = atomicExch(&hf[b], 0ull);
-        const unsigned long long wh = atomicExch(&hw[b], 0ull);
-        const int64_t o = (int64_t)real * nbins + b;
-        if (c) atomicAdd(&acc.cnt[o], (unsigned long long)c);
-        add_fix96_global(acc, o, wh, lo, hi);
-    }
 }
 
 template <bool POLY, bool INH, bool DIR>
@@ -1216,7 +1374,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
 
 // Evaluates the pairs the FP32 kernel queued, 32 per warp, and adds them to the global
 // accumulators (integer atomics, so the order does not matter).
-template <bool POLY, bool DIR>
+template <bool POLY, int VAR>
 __global__ void __launch_bounds__(256)
 exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQueue xq) {
     const unsigned int pushed = *xq.count;
@@ -1229,11 +1387,13 @@ exact_kernel(const PairConsts* __restrict__ gpc, RealBatch rb, Accum acc, ExactQ
         int bin;
         uint32_t counts;
         unsigned long long exc;
-        if (!exact_eval<POLY, DIR>(pc, rb, q, bin, counts, exc)) continue;
+        Fix96 f;
+        if (!exact_eval<POLY, VAR>(pc, rb, q, bin, counts, exc, &f)) continue;
         const int64_t o = (int64_t)q.z * pc.nbins + bin;
         if (counts) atomicAdd(&acc.cnt[o], (unsigned long long)counts);
         if (exc & 0xffffffffull) atomicAdd(&acc.exc_lo[o], exc & 0xffffffffull);
         if (exc >> 32) atomicAdd(&acc.exc_hi[o], exc >> 32);
+        if (VAR == kVarInh) add_fix96_global(acc, o, f.whole, f.lo, f.hi);
     }
 }
 
@@ -1327,7 +1487,14 @@ size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
 
 }  // namespace
 
-size_t pair_fp32_smem(int nbins, int* reps) {
+size_t pair_fp32_smem(int nbins, int* reps, bool inh) {
+    if (inh) {  // three u64 sums and a u32 count per bin and replica
+        const size_t b = (sizeof(Smem32) + 15) & ~size_t(15);
+        int r = 8;
+        while (r > 1 && b + (size_t)r * nbins * 32 > 56 * 1024) --r;
+        *reps = r;
+        return b + (size_t)r * nbins * 32;
+    }
     return smem_with_reps(sizeof(Smem32), nbins, reps, 56 * 1024);
 }
 size_t pair_fp64_smem(int nbins, int* reps, bool inh) {
@@ -1356,16 +1523,28 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));
     if (e != cudaSuccess) return e;
-    const void* k32[8] = {(const void*)pair_fp32_kernel<false, false, false, false>,
-                          (const void*)pair_fp32_kernel<false, true, false, false>,
-                          (const void*)pair_fp32_kernel<true, false, false, false>,
-                          (const void*)pair_fp32_kernel<true, true, false, false>,
-                          (const void*)pair_fp32_kernel<false, true, true, false>,
-                          (const void*)pair_fp32_kernel<true, true, true, false>,
-                          (const void*)pair_fp32_kernel<false, false, false, true>,
-                          (const void*)pair_fp32_kernel<true, false, false, true>};
+    const void* k32[8] = {(const void*)pair_fp32_kernel<false, false, false, kVarPlain>,
+                          (const void*)pair_fp32_kernel<false, true, false, kVarPlain>,
+                          (const void*)pair_fp32_kernel<true, false, false, kVarPlain>,
+                          (const void*)pair_fp32_kernel<true, true, false, kVarPlain>,
+                          (const void*)pair_fp32_kernel<false, true, true, kVarPlain>,
+                          (const void*)pair_fp32_kernel<true, true, true, kVarPlain>,
+                          (const void*)pair_fp32_kernel<false, false, false, kVarDir>,
+                          (const void*)pair_fp32_kernel<true, false, false, kVarDir>};
     for (const void* f : k32) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        if (e != cudaSuccess) return e;
+    }
+    // inhomogeneous K: 32 bytes per bin and replica
+    const size_t smem32_inh = std::max<size_t>(
+        smem32, ((sizeof(Smem32) + 15) & ~size_t(15)) + (size_t)kMaxThr * kMaxThr * 32);
+    const void* k32i[4] = {(const void*)pair_fp32_kernel<false, false, false, kVarInh>,
+                           (const void*)pair_fp32_kernel<false, true, false, kVarInh>,
+                           (const void*)pair_fp32_kernel<true, false, false, kVarInh>,
+                           (const void*)pair_fp32_kernel<true, true, false, kVarInh>};
+    for (const void* f : k32i) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem32_inh);
         if (e != cudaSuccess) return e;
     }
     e = cudaFuncSetAttribute(pair_fp64_kernel<true, false, false>,
@@ -1385,7 +1564,7 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
 
 int pair_fp32_blocks_per_sm(size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false, false>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false, kVarPlain>,
                                                       kBlock, smem) !=
         cudaSuccess)
         return 1;
@@ -1409,19 +1588,27 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
                              ExactQueue xq, cudaStream_t st) {
     const bool poly = edge && hpc.nv > 0;
-    // directional K / translation correction: its own instantiation (no isotropic logic)
+    // directional K / translation correction and inhomogeneous K: their own instantiations
     const bool dir = hpc.nsec > 1 || hpc.edge == STK_EDGE_TRANSLATION;
-#define STK_PAIR32(E, D, P)                                                                  \
-    pair_fp32_kernel<E, D, P, false><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units,    \
-                                                                 unit_off, counters, acc, xq, \
-                                                                 reps)
-    if (dir && poly) return cudaErrorInvalidValue;
-    if (dir && even)
-        pair_fp32_kernel<true, false, false, true><<<grid, kBlock, smem, st>>>(
-            hpc, d_pc, m, rb, units, unit_off, counters, acc, xq, reps);
+    const bool inh = rb.H != nullptr;
+#define STK_PAIR32V(E, D, P, V)                                                              \
+    pair_fp32_kernel<E, D, P, V><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units,        \
+                                                             unit_off, counters, acc, xq, reps)
+#define STK_PAIR32(E, D, P) STK_PAIR32V(E, D, P, kVarPlain)
+    if ((dir && (poly || inh)) || (inh && (poly || acc.whole == nullptr)))
+        return cudaErrorInvalidValue;
+    if (inh && even && edge)
+        STK_PAIR32V(true, true, false, kVarInh);
+    else if (inh && even)
+        STK_PAIR32V(true, false, false, kVarInh);
+    else if (inh && edge)
+        STK_PAIR32V(false, true, false, kVarInh);
+    else if (inh)
+        STK_PAIR32V(false, false, false, kVarInh);
+    else if (dir && even)
+        STK_PAIR32V(true, false, false, kVarDir);
     else if (dir)
-        pair_fp32_kernel<false, false, false, true><<<grid, kBlock, smem, st>>>(
-            hpc, d_pc, m, rb, units, unit_off, counters, acc, xq, reps);
+        STK_PAIR32V(false, false, false, kVarDir);
     else if (poly && even)
         STK_PAIR32(true, true, true);
     else if (poly)
@@ -1435,18 +1622,23 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
     else
         STK_PAIR32(false, false, false);
 #undef STK_PAIR32
+#undef STK_PAIR32V
     return cudaGetLastError();
 }
 
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
                          ExactQueue xq, cudaStream_t st, bool poly, bool dir) {
-    if (dir && poly) return cudaErrorInvalidValue;
-    if (dir)
-        exact_kernel<false, true><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+    const bool inh = rb.H != nullptr;
+    if ((dir && (poly || inh)) || (inh && (poly || acc.whole == nullptr)))
+        return cudaErrorInvalidValue;
+    if (inh)
+        exact_kernel<false, kVarInh><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+    else if (dir)
+        exact_kernel<false, kVarDir><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     else if (poly)
-        exact_kernel<true, false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+        exact_kernel<true, kVarPlain><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     else
-        exact_kernel<false, false><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
+        exact_kernel<false, kVarPlain><<<grid, 256, 0, st>>>(d_pc, rb, acc, xq);
     return cudaGetLastError();
 }
 

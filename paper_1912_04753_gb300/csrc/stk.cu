@@ -126,9 +126,10 @@ namespace {
 
 bool finite_in(double v, double lo, double hi) { return v >= lo && v <= hi; }
 
-// The FP32-guarded pair kernel, unless the job is an inhomogeneous K (always FP64).
+// The FP32-guarded pair kernel (every estimator has an instantiation of it).
 bool fp32_path(const stk_handle* h, const stk_request* q) {
-    return q->prec == STK_PREC_FP32_GUARDED && h->inten.nix == 0;
+    (void)h;
+    return q->prec == STK_PREC_FP32_GUARDED;
 }
 
 int check_box(const stk_box* b) {
@@ -583,7 +584,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const bool fp32 = fp32_path(h, q);
     int reps = fp32 ? h->reps32 : h->reps64;
     size_t smem = fp32 ? h->smem32 : h->smem64;
-    if (inh) smem = pair_fp64_smem(nbins, &reps, true);
+    if (inh) smem = fp32 ? pair_fp32_smem(nbins, &reps, true) : pair_fp64_smem(nbins, &reps, true);
     const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem, inh);
     const int grid = bps * h->num_sms;
     float ms_pair = 0.0f;
