@@ -67,9 +67,9 @@ enum stk_status {
 /* NONE: weight 1.  ISOTROPIC: Section 3 (proportion of the circle's circumference inside the
  * study area, temporal weight 1 or 1/2).  TRANSLATION: the translation correction, pair weight
  * W H / ((W - |dx|)(H - |dy|)) * D / (D - u) (|A| over the area of the box intersected with
- * its copy shifted by the pair's offset, likewise in time; rectangle only, always in FP64,
- * needs t_ct <= (t1 - t0) / 2 so that the weight stays <= 8): unbiased for every direction,
- * so the one the directional K (n_sectors > 1) takes. */
+ * its copy shifted by the pair's offset, likewise in time; rectangle only; needs
+ * t_ct <= (t1 - t0) / 2 so that the weight stays <= 8): unbiased for every direction, so the
+ * one the directional K (n_sectors > 1) takes. */
 enum { STK_EDGE_NONE = 0, STK_EDGE_ISOTROPIC = 1, STK_EDGE_TRANSLATION = 2 };
 /* FP64: every pair in IEEE double, bit-compatible with the reference definition.
  * FP32_GUARDED: pairs in FP32 with cell-relative coordinates; any pair whose
@@ -120,9 +120,9 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv);
  * separately, clamped to [0, nix - 1]), and likewise along y and t.  The estimator is
  *   K_I(s, t) = n / ((n - 1) A D) * sum_{i != j} I(d_ij <= s, u_ij <= t) / (w_ij v_ij lambda_i lambda_j)
  * (1 / (A D) with STK_NORM_N2), Eq. 2 when rho is constant; raw_sum reports that sum times
- * (n / (A D))^2, so K = raw_sum * A D / (n (n - 1)) as in Eq. 2, and L follows Eq. 4.  Every
- * pair is evaluated in FP64 whatever `prec` asks (the K tolerance is that of STK_PREC_FP64;
- * counts are exact).  Simulations: STK_SIM_CSR draws n points independently with density
+ * (n / (A D))^2, so K = raw_sum * A D / (n (n - 1)) as in Eq. 2, and L follows Eq. 4.  Both
+ * precisions apply (counts exact; the weighted sums, each pair's weight times h_i h_j, are
+ * kept in 2^-64 fixed point).  Simulations: STK_SIM_CSR draws n points independently with density
  * proportional to rho (cell i of a point: the first whose running sum of rho exceeds u times
  * the total, u from Philox block (i, sim, 40, i >> 32); the position inside the cell from the
  * CSR streams 0, 1, 2: x = x0 + (x1 - x0) * ((cell x index + u_x) / nix)), and each point
@@ -197,7 +197,7 @@ typedef struct {
      * rounded separately; coincident points in sector 0).  Every grid output then holds
      * n_sectors grids, [n_sectors][cs][ct], with n_sectors * cs * ct <= 4096; L of a sector is
      * sqrt(n_sectors K / (2 pi t)) - s (zero in expectation under CSR, like Eq. 4).  Needs
-     * edge_mode NONE or TRANSLATION, the rectangle, no intensity and no labels; runs in FP64.
+     * edge_mode NONE or TRANSLATION, the rectangle, no intensity and no labels.
      * 0 or 1: no split. */
     int n_sectors;
 } stk_request;
