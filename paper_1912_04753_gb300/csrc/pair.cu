@@ -15,6 +15,11 @@
 //     to an edge) is recomputed in FP64 with the reference arithmetic, so counts are exact.
 //   * pair_fp64: the same traversal with every pair in FP64 (the plain comparison path).
 //
+// Both come in variants (template parameters): a polygon study area; the directional (sector)
+// K with the translation correction, whose histograms gain a sector axis; and the
+// inhomogeneous K, whose pair weights h_i h_j / (w v) are accumulated in 2^-64 fixed point
+// (whole part + two 32-bit fraction halves) because they are not >= 1.
+//
 // This is CUDA-core work (no dense contraction), bound by instruction issue.
 #include <stddef.h>
 #include <algorithm>
@@ -373,6 +378,8 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
 //   C (weight): 32 orders of queue 2 at a time: accurate distance from the hi + lo parts and
 //     the isotropic weight of the (at most two) cutting edges; near-tangent circles go to
 //     the FP64 queue.
+// The directional and inhomogeneous variants take every pair's sector and weights in phase B
+// itself (no queue 2); what FP32 cannot decide there goes to the FP64 queue as a whole pair.
 // Entries of the FP64 queue are evaluated with the reference arithmetic by exact_kernel.
 // FP64 runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this
 // kernel would hold a whole warp for thousands of cycles.

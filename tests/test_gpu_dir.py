@@ -190,3 +190,17 @@ def test_served_translation_k(stk, orc):
     # the isotropic job of the same batch is not merged with it
     want_iso = orc.k_function(x, y, t, BOX, S, TT)
     assert _rel(got_iso["K"], want_iso["K"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_directional_sampled_centres(stk, orc, prec):
+    # sampled-centre mode: only the masked centres count, each pair in its sector
+    x, y, t = _pattern(6000, 29)
+    rng = np.random.default_rng(8)
+    mask = (rng.random(len(x)) < 0.05).astype(np.uint8)
+    want = orc.k_function_dir(x, y, t, BOX, S, TT, 4, edge_mode=2, centre_mask=mask)
+    with stk.Pattern(x, y, t, BOX) as p:
+        got = p.run(S, TT, edge_mode=2, n_sectors=4, centre_mask=mask, prec=prec)
+        assert p.stats()["internal_errors"] == 0
+    np.testing.assert_array_equal(got["C"], want["C"])
+    assert _rel(got["K"], want["K"]).max() <= TOLP[prec]
