@@ -39,7 +39,9 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        # STK_ORACLE_LIB: a deliberately broken copy, for the tests that check that the pins
+        # catch planted mistakes
+        lib = ctypes.CDLL(os.environ.get("STK_ORACLE_LIB") or build())
         d, i64, i32, u64, u32 = (ctypes.c_double, ctypes.c_int64, ctypes.c_int,
                                  ctypes.c_uint64, ctypes.c_uint32)
         P = ctypes.c_void_p

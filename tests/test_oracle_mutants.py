@@ -1,0 +1,54 @@
+"""The pins have the power to see plausible mistakes: each mistake below is planted in a copy
+of the oracle's C source (on the CPU), the copy is compiled, and the pin files run against it
+in a subprocess must fail.  Mistakes: n^2 normalisation, no temporal weight, an open temporal
+interval, a strict threshold test, a dropped dy term, an unsigned time lag lost, the weight
+not inverted, arcs summed without their union, a wrong Philox constant, the inhomogeneous
+weight with one intensity twice, the intensity not scaled to n, a simulated coordinate scaled
+by the wrong axis's cell count, the translation correction with dx in place of dy, and the
+sector test with its operands transposed."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "stk_oracle.c")
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_inhom.py", "tests/test_oracle_dir.py"]
+
+MUTANTS = {
+    "n2_normalisation": ("nn * (nn - 1.0)", "nn * nn"),
+    "no_temporal_weight": ("return (ti - u >= t0 && ti + u <= t1) ? 1.0 : 0.5;", "return 1.0;"),
+    "open_temporal_interval": ("ti - u >= t0 && ti + u <= t1", "ti - u > t0 && ti + u < t1"),
+    "strict_threshold": ("if (d2 > s2max) continue;", "if (d2 >= s2max) continue;"),
+    "dropped_dy": ("const double d2 = dx * dx + dy * dy;", "const double d2 = dx * dx;"),
+    "signed_lag": ("fabs(t[i] - t[j])", "(t[i] - t[j])"),
+    "weight_not_inverted": ("w = 1.0 / (om * v);", "w = om * v;"),
+    "no_arc_union": ("if (arcs[k].lo <= cur_hi) {", "if (0) {"),
+    "philox_constant": ("0xD2511F53u", "0xD2511F57u"),
+    "inhom_one_intensity": ("lam[i] * lam[j]", "lam[i] * lam[i]"),
+    "inhom_not_scaled": ("lam_cell[c] = (double)n * rho[c] / mass;",
+                         "lam_cell[c] = rho[c] / mass;"),
+    "inhom_cell_axis": ("(((double)idx[a] + u) / (double)cnt[a])",
+                        "(((double)idx[a] + u) / (double)cnt[0])"),
+    "translation_index": ("((w - fabs(dx)) * (h - fabs(dy)))", "((w - fabs(dx)) * (h - fabs(dx)))"),
+    "sector_transposed": ("const double cr = bx * dy - by * dx;",
+                          "const double cr = bx * dx - by * dy;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert old in src, f"mutation {name} no longer applies"
+    mut = tmp_path / "stk_oracle.c"
+    mut.write_text(src.replace(old, new))
+    (tmp_path / "stk_oracle.h").write_text(open(SRC[:-1] + "h").read())
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-pthread", "-o", str(lib), str(mut), "-lm"])
+    env = dict(os.environ, STK_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"no pin caught {name}:\n{r.stdout[-2000:]}"
