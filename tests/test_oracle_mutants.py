@@ -4,8 +4,10 @@ in a subprocess must fail.  Mistakes: n^2 normalisation, no temporal weight, an 
 interval, a strict threshold test, a dropped dy term, an unsigned time lag lost, the weight
 not inverted, arcs summed without their union, a wrong Philox constant, the inhomogeneous
 weight with one intensity twice, the intensity not scaled to n, a simulated coordinate scaled
-by the wrong axis's cell count, the translation correction with dx in place of dy, and the
-sector test with its operands transposed."""
+by the wrong axis's cell count, the translation correction with dx in place of dy, the
+sector test with its operands transposed, a signed polygon area, an open polygon boundary, a
+ray test inclusive at both ends, an arc judged at its start instead of its midpoint, and the
+cross-K denominator of the same-label case used for two labels."""
 import os
 import subprocess
 import sys
@@ -34,6 +36,12 @@ MUTANTS = {
     "translation_index": ("((w - fabs(dx)) * (h - fabs(dy)))", "((w - fabs(dx)) * (h - fabs(dx)))"),
     "sector_transposed": ("const double cr = bx * dy - by * dx;",
                           "const double cr = bx * dx - by * dy;"),
+    "polygon_area_signed": ("return fabs(a) * 0.5;", "return a * 0.5;"),
+    "polygon_boundary_open": ("if (on_segment(px, py, ax, ay, bx, by)) return 1;", ""),
+    "polygon_ray_inclusive": ("if ((ay > py) != (by > py)) {", "if ((ay >= py) != (by > py)) {"),
+    "polygon_arc_start_not_mid": ("const double mid = 0.5 * (a0 + a1);",
+                                  "const double mid = a0;"),
+    "cross_denominator": ("(a != b) ? fa * fb", "(a != b) ? fa * (fb - 1.0)"),
 }
 
 

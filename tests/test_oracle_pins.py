@@ -553,3 +553,35 @@ def test_cross_counts_partition_all_pairs_and_are_symmetric(orc):
     np.testing.assert_array_equal(c[(0, 1)], c[(1, 0)])
     none = orc.k_cross(x, y, t, lab, 0, 1, box, s, tt, edge_mode=0)
     np.testing.assert_array_equal(none["S"], none["C"].astype(float))
+
+
+def test_point_in_polygon_at_vertex_heights(orc):
+    # the ray towards +x passes exactly through vertices: a diamond and an L shape, answers by
+    # inspection (a point is inside the diamond iff |x| + |y| <= 1)
+    dia = ([0.0, 1.0, 0.0, -1.0], [-1.0, 0.0, 1.0, 0.0])
+    for px, py in ((-0.5, 0.0), (0.25, 0.0), (0.0, 0.5), (-0.25, -0.5), (0.5, 0.25)):
+        assert orc.point_in_polygon(px, py, *dia) == (abs(px) + abs(py) <= 1.0), (px, py)
+    for px, py in ((-1.5, 0.0), (1.5, 0.0), (-2.0, 1.0), (-3.0, -1.0), (0.9, 0.5)):
+        assert not orc.point_in_polygon(px, py, *dia), (px, py)
+    ell = ([0, 4, 4, 1, 1, 0], [0, 0, 1, 1, 3, 3])
+    assert orc.point_in_polygon(0.5, 1.0, *ell)        # at the height of the reflex vertex
+    assert not orc.point_in_polygon(-1.0, 1.0, *ell)
+    assert not orc.point_in_polygon(-1.0, 3.0, *ell)   # at the height of the top edge
+    assert orc.point_in_polygon(0.5, 3.0, *ell)        # on the top edge (closed)
+
+
+def test_cross_k_normalisations_recombine_to_the_univariate_sum(orc):
+    """sum_{a != b} n_a n_b K_ab + sum_a n_a (n_a - 1) K_aa = n (n - 1) K: every ordered pair of
+    the univariate sum belongs to exactly one label pair, and each K_ab is A D / (its
+    denominator) times its part of the sum."""
+    x, y, t, lab, box = _two_types(3)
+    s, tt = np.array([20.0, 60.0]), np.array([5.0, 20.0])
+    n = len(x)
+    na = {a: int((lab == a).sum()) for a in (0, 1)}
+    total = orc.k_function(x, y, t, box, s, tt)["K"] * n * (n - 1)
+    acc = np.zeros_like(total)
+    for a in (0, 1):
+        for b in (0, 1):
+            k = orc.k_cross(x, y, t, lab, a, b, box, s, tt)["K"]
+            acc += k * (na[a] * na[b] if a != b else na[a] * (na[a] - 1))
+    np.testing.assert_allclose(acc, total, rtol=1e-12)
