@@ -6,8 +6,9 @@ not inverted, arcs summed without their union, a wrong Philox constant, the inho
 weight with one intensity twice, the intensity not scaled to n, a simulated coordinate scaled
 by the wrong axis's cell count, the translation correction with dx in place of dy, the
 sector test with its operands transposed, a signed polygon area, an open polygon boundary, a
-ray test inclusive at both ends, an arc judged at its start instead of its midpoint, and the
-cross-K denominator of the same-label case used for two labels."""
+ray test inclusive at both ends, an arc judged at its start instead of its midpoint, the
+cross-K denominator of the same-label case used for two labels, the intensity grid's x cell
+count used along y, and the grid-accelerated histogram skipping the cells on one side."""
 import os
 import subprocess
 import sys
@@ -16,7 +17,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "stk_oracle.c")
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_inhom.py", "tests/test_oracle_dir.py"]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_inhom.py", "tests/test_oracle_dir.py",
+        "tests/test_oracle_grid.py"]
 
 MUTANTS = {
     "n2_normalisation": ("nn * (nn - 1.0)", "nn * nn"),
@@ -42,6 +44,10 @@ MUTANTS = {
     "polygon_arc_start_not_mid": ("const double mid = 0.5 * (a0 + a1);",
                                   "const double mid = a0;"),
     "cross_denominator": ("(a != b) ? fa * fb", "(a != b) ? fa * (fb - 1.0)"),
+    "intensity_lookup_axis": ("axis_cell(y, box[2], box[3], niy)",
+                              "axis_cell(y, box[2], box[3], nix)"),
+    "grid_neighbours_one_side": ("for (int dxx = -1; dxx <= 1; ++dxx)",
+                                 "for (int dxx = -1; dxx <= 0; ++dxx)"),
 }
 
 
