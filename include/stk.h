@@ -328,6 +328,7 @@ typedef struct {
     uint64_t seed;
     int want_sims;       /* 1: keep per-realization K and counts for stk_poll */
     int sim_method;      /* STK_SIM_* */
+    int n_sectors;       /* directional K (as stk_request.n_sectors); grids [n_sectors][cs][ct] */
 } stk_job;
 
 typedef struct {

@@ -68,7 +68,8 @@ class stk_job(ctypes.Structure):
     _fields_ = [("dataset", ctypes.c_uint64), ("s", _P), ("cs", ctypes.c_int), ("tt", _P),
                 ("ct", ctypes.c_int), ("edge_mode", ctypes.c_int), ("prec", ctypes.c_int),
                 ("norm", ctypes.c_int), ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("want_sims", ctypes.c_int), ("sim_method", ctypes.c_int)]
+                ("want_sims", ctypes.c_int), ("sim_method", ctypes.c_int),
+                ("n_sectors", ctypes.c_int)]
 
 
 class stk_serve_stats(ctypes.Structure):
@@ -367,20 +368,21 @@ def stk_server_unregister(sv, dataset: int):
 
 def stk_submit(sv, dataset, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
                prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, want_sims=False,
-               sim_method=STK_SIM_CSR) -> int:
+               sim_method=STK_SIM_CSR, n_sectors=0) -> int:
     """Queue a K / envelope job on a registered point set; returns its ticket."""
     s, tt = _f64(s), _f64(tt)
     j = stk_job(dataset, _ptr(s), s.shape[0], _ptr(tt), tt.shape[0], edge_mode, prec, norm,
-                n_sims, seed, 1 if want_sims else 0, sim_method)
+                n_sims, seed, 1 if want_sims else 0, sim_method, n_sectors)
     tk = ctypes.c_uint64()
     _check(load().stk_submit(sv, ctypes.byref(j), ctypes.byref(tk)))
     return tk.value
 
 
-def stk_poll(sv, ticket, cs, ct, n_sims=0, want_sims=False, wait_ms=-1):
+def stk_poll(sv, ticket, cs, ct, n_sims=0, want_sims=False, wait_ms=-1, n_sectors=0):
     """Wait for a job.  Returns (grids, latency_ms), or None while it is still running after
     wait_ms; raises StkError if the job failed."""
-    nb = cs * ct
+    grid = (n_sectors, cs, ct) if n_sectors > 1 else (cs, ct)
+    nb = int(np.prod(grid))
     o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
     if n_sims > 0:
         for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
@@ -398,7 +400,7 @@ def stk_poll(sv, ticket, cs, ct, n_sims=0, want_sims=False, wait_ms=-1):
     _check(rc)
     out = {}
     for k, v in o.items():
-        out[k] = v.reshape((n_sims, cs, ct)) if k in ("K_sims", "C_sims") else v.reshape(cs, ct)
+        out[k] = v.reshape((n_sims,) + grid) if k in ("K_sims", "C_sims") else v.reshape(grid)
     return out, lat.value
 
 
@@ -433,12 +435,12 @@ class Server:
     def submit(self, dataset, s, tt, n_sims=0, seed=0, want_sims=False, **kw) -> int:
         tk = stk_submit(self.sv, dataset, s, tt, n_sims=n_sims, seed=seed, want_sims=want_sims,
                         **kw)
-        self._shape[tk] = (len(s), len(tt), n_sims, want_sims)
+        self._shape[tk] = (len(s), len(tt), n_sims, want_sims, kw.get("n_sectors", 0))
         return tk
 
     def poll(self, ticket, wait_ms=-1):
-        cs, ct, n_sims, want = self._shape[ticket]
-        r = stk_poll(self.sv, ticket, cs, ct, n_sims, want, wait_ms)
+        cs, ct, n_sims, want, nsec = self._shape[ticket]
+        r = stk_poll(self.sv, ticket, cs, ct, n_sims, want, wait_ms, nsec)
         if r is not None:
             del self._shape[ticket]
         return r

@@ -50,6 +50,7 @@ struct Job {
     uint64_t dataset = 0;
     std::vector<double> s, tt;
     int edge_mode = 0, prec = 0, norm = 0, n_sims = 0, want_sims = 0, sim_method = 0;
+    int n_sectors = 0;
     uint64_t seed = 0;
     JobState state = JobState::Queued;
     int rc = STK_OK;
@@ -72,7 +73,8 @@ struct Dataset {
 
 bool same_params(const Job& a, const Job& b) {
     return a.dataset == b.dataset && a.s == b.s && a.tt == b.tt && a.edge_mode == b.edge_mode &&
-           a.prec == b.prec && a.norm == b.norm && a.sim_method == b.sim_method;
+           a.prec == b.prec && a.norm == b.norm && a.sim_method == b.sim_method &&
+           a.n_sectors == b.n_sectors;
 }
 
 }  // namespace
@@ -157,6 +159,8 @@ bool take_batch(stk_server* sv, Batch* out) {
         q.tt = head->tt.data();
         q.ct = (int)head->tt.size();
         q.prec = head->prec;
+        q.edge_mode = head->edge_mode;
+        q.n_sectors = head->n_sectors;
         stk::Footprint fp;
         const int R = 1 + sims;
         int rc = stk::job_footprint(ds.h, &q, R, groups, &fp);
@@ -233,6 +237,7 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual) {
     q.norm = head.norm;
     q.exec = STK_EXEC_BATCHED;
     q.sim_method = head.sim_method;
+    q.n_sectors = head.n_sectors;
     stk::SimPlan plan;
     std::vector<int> group_of(b.jobs.size(), -1), first_row(b.jobs.size(), 0);
     bool any_sims = false;
@@ -253,7 +258,7 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual) {
     stk::handle_set_wave_budget(h, b.grant);
     int rc = stk::run_plan(h, &q, plan, true);
     if (rc) return rc;
-    const int nbins = q.cs * q.ct;
+    const int nbins = q.cs * q.ct * (q.n_sectors > 1 ? q.n_sectors : 1);
     const int R = 1 + (int)plan.seed.size();
     std::vector<double> K(nbins), L(nbins), S(nbins), env(4 * (size_t)nbins * plan.groups.size());
     std::vector<int64_t> C(nbins);
@@ -459,6 +464,9 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
         return note(STK_EINVAL, "unknown norm");
     if (job->sim_method < STK_SIM_CSR || job->sim_method > STK_SIM_BOOTSTRAP)
         return note(STK_EINVAL, "unknown sim_method");
+    if (job->n_sectors < 0 || job->n_sectors > 64 ||
+        (job->n_sectors > 1 && job->n_sectors * job->cs * job->ct > 4096))
+        return note(STK_EINVAL, "n_sectors out of range (n_sectors * cs * ct <= 4096)");
     auto j = std::make_shared<Job>();
     j->dataset = job->dataset;
     j->s.assign(job->s, job->s + job->cs);
@@ -470,6 +478,7 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
     j->seed = job->seed;
     j->want_sims = job->want_sims;
     j->sim_method = job->sim_method;
+    j->n_sectors = job->n_sectors;
     std::lock_guard<std::mutex> lock(sv->mu);
     auto it = sv->datasets.find(job->dataset);
     if (it == sv->datasets.end()) return note(STK_EINVAL, "unknown dataset");
@@ -482,6 +491,8 @@ int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
         q.cs = job->cs;
         q.tt = j->tt.data();
         q.ct = job->ct;
+        q.edge_mode = job->edge_mode;
+        q.n_sectors = job->n_sectors;
         const int rc = stk::job_footprint(it->second.h, &q, 1, 0, &fp);
         if (rc) return rc;
     }

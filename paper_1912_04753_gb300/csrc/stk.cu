@@ -908,7 +908,8 @@ int job_footprint(stk_handle* h, const stk_request* q, int R, int groups, Footpr
     if (const char* ft = getenv("STK_GRID_FT")) f_req = (f_req & 0xff) | (atoi(ft) << 8);
     if (build_grid(h->box, q->s[q->cs - 1], q->tt[q->ct - 1], h->n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
-    *out = footprint(h->n, g, q->cs * q->ct, R, groups, fp32_path(h, q), h->inten.nix > 0);
+    *out = footprint(h->n, g, q->cs * q->ct * (q->n_sectors > 1 ? q->n_sectors : 1), R, groups,
+                     fp32_path(h, q), h->inten.nix > 0);
     return STK_OK;
 }
 

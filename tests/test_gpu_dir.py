@@ -204,3 +204,19 @@ def test_directional_sampled_centres(stk, orc, prec):
         assert p.stats()["internal_errors"] == 0
     np.testing.assert_array_equal(got["C"], want["C"])
     assert _rel(got["K"], want["K"]).max() <= TOLP[prec]
+
+
+def test_served_directional_k(stk, orc):
+    # sectors through the serving loop: jobs with different n_sectors are not merged
+    x, y, t = _pattern(1500, 23, stretch=False)
+    with stk.Server(slots=2) as sv:
+        d = sv.register(x, y, t, BOX)
+        t4 = sv.submit(d, S, TT, edge_mode=2, n_sectors=4, n_sims=2, seed=5)
+        t1 = sv.submit(d, S, TT, edge_mode=2, n_sims=2, seed=5)
+        g4, _ = sv.poll(t4)
+        g1, _ = sv.poll(t1)
+    want = orc.k_function_dir(x, y, t, BOX, S, TT, 4, edge_mode=2)
+    assert g4["K"].shape == (4, len(S), len(TT)) and g4["K_lo"].shape == (4, len(S), len(TT))
+    np.testing.assert_array_equal(g4["C"], want["C"])
+    assert _rel(g4["K"], want["K"]).max() <= 1e-6
+    np.testing.assert_array_equal(g4["C"].sum(axis=0), g1["C"])
