@@ -356,6 +356,14 @@ int stk_server_register(stk_server* sv, const double* x, const double* y, const 
                         int64_t n, const stk_box* box, uint64_t* dataset);
 /* Releases a point set; STK_EBUSY while jobs on it are queued or running. */
 int stk_server_unregister(stk_server* sv, uint64_t dataset);
+/* A polygon study area or a relative intensity for a registered point set, as
+ * stk_set_polygon / stk_set_intensity on a handle; later jobs on it use them (jobs on one point
+ * set share them, so merged jobs agree).  Errors: those of the handle functions, STK_EINVAL
+ * (unknown dataset), STK_EBUSY while jobs on the point set are queued or running. */
+int stk_server_set_polygon(stk_server* sv, uint64_t dataset, const double* vx, const double* vy,
+                           int nv);
+int stk_server_set_intensity(stk_server* sv, uint64_t dataset, const double* rho, int nix,
+                             int niy, int nit);
 /* Queues a job; its thresholds are checked and copied here.  Errors: STK_EINVAL (unknown
  * dataset, bad thresholds or modes, n_sims < 0), STK_EBUSY (queue full). */
 int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket);

@@ -121,6 +121,8 @@ def load(build_if_missing: bool = False):
         "stk_server_register": ([_P, _P, _P, _P, i64, ctypes.POINTER(stk_box),
                                  ctypes.POINTER(u64)], i32),
         "stk_server_unregister": ([_P, u64], i32),
+        "stk_server_set_polygon": ([_P, u64, _P, _P, i32], i32),
+        "stk_server_set_intensity": ([_P, u64, _P, i32, i32, i32], i32),
         "stk_submit": ([_P, ctypes.POINTER(stk_job), ctypes.POINTER(u64)], i32),
         "stk_poll": ([_P, u64, ctypes.POINTER(stk_result), i32, ctypes.POINTER(ctypes.c_double)],
                      i32),
@@ -431,6 +433,23 @@ class Server:
 
     def unregister(self, dataset):
         stk_server_unregister(self.sv, dataset)
+
+    def set_polygon(self, dataset, vx=None, vy=None):
+        """Polygon study area of a registered point set (None: back to its box)."""
+        if vx is None:
+            _check(load().stk_server_set_polygon(self.sv, dataset, None, None, 0))
+            return
+        vx, vy = _f64(vx), _f64(vy)
+        _check(load().stk_server_set_polygon(self.sv, dataset, _ptr(vx), _ptr(vy), vx.shape[0]))
+
+    def set_intensity(self, dataset, rho=None):
+        """Relative intensity rho[nit, niy, nix] of a registered point set (None: none)."""
+        if rho is None:
+            _check(load().stk_server_set_intensity(self.sv, dataset, None, 0, 0, 0))
+            return
+        r = _rho3(rho)
+        _check(load().stk_server_set_intensity(self.sv, dataset, _ptr(r), r.shape[2],
+                                               r.shape[1], r.shape[0]))
 
     def submit(self, dataset, s, tt, n_sims=0, seed=0, want_sims=False, **kw) -> int:
         tk = stk_submit(self.sv, dataset, s, tt, n_sims=n_sims, seed=seed, want_sims=want_sims,

@@ -449,6 +449,51 @@ int stk_server_unregister(stk_server* sv, uint64_t dataset) {
     return STK_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Applies `fn` to an idle point set's handle outside the server lock (the point set is marked
+// busy meanwhile, so no batch starts on it); STK_EBUSY while jobs on it are queued or running.
+template <class F>
+int with_idle_dataset(stk_server* sv, uint64_t dataset, F fn) {
+    stk_handle* h = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        auto it = sv->datasets.find(dataset);
+        if (it == sv->datasets.end()) return note(STK_EINVAL, "unknown dataset");
+        if (it->second.busy || it->second.pending > 0)
+            return note(STK_EBUSY, "jobs on this dataset are queued or running");
+        it->second.busy = true;
+        h = it->second.h;
+    }
+    const int rc = fn(h);
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->datasets[dataset].busy = false;
+    }
+    sv->cv_work.notify_all();
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stk_server_set_polygon(stk_server* sv, uint64_t dataset, const double* vx, const double* vy,
+                           int nv) {
+    if (!sv) return note(STK_EINVAL, "server is NULL");
+    return with_idle_dataset(sv, dataset,
+                             [&](stk_handle* h) { return stk_set_polygon(h, vx, vy, nv); });
+}
+
+int stk_server_set_intensity(stk_server* sv, uint64_t dataset, const double* rho, int nix,
+                             int niy, int nit) {
+    if (!sv) return note(STK_EINVAL, "server is NULL");
+    return with_idle_dataset(
+        sv, dataset, [&](stk_handle* h) { return stk_set_intensity(h, rho, nix, niy, nit); });
+}
+
 int stk_submit(stk_server* sv, const stk_job* job, uint64_t* ticket) {
     if (!sv || !job || !ticket) return note(STK_EINVAL, "server, job and ticket must not be NULL");
     if (!job->s || !job->tt || job->cs < 1 || job->ct < 1 || job->cs > STK_MAX_THRESHOLDS ||

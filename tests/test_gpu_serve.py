@@ -164,3 +164,34 @@ def test_request_errors(stk):
         sv.unregister(d)
         with pytest.raises(stk.StkError):
             sv.submit(d, [10.0], [1.0])
+
+
+def test_served_polygon_and_intensity(stk, orc):
+    # a registered point set with a polygon study area, another with an intensity: the served
+    # grids equal the handle's own
+    from paper_1912_04753_gb300 import workloads as wl
+
+    box = (0.0, 2400.0, 0.0, 2200.0, 0.0, 365.0)
+    vx, vy = wl.star_polygon(24, 1000.0, 650.0, 1200.0, 1100.0, 3)
+    x, y, t = orc.csr_polygon_points(1500, box, vx, vy, 4, 0)
+    s, tt = wl.even_thresholds(200.0, 5), wl.even_thresholds(30.0, 4)
+    rho = wl.histogram_intensity(x, y, t, box, (2, 3, 3))
+    with stk.Server(slots=2) as sv:
+        dp = sv.register(x, y, t, box)
+        di = sv.register(x, y, t, box)
+        sv.set_polygon(dp, vx, vy)
+        sv.set_intensity(di, rho)
+        gp, _ = sv.poll(sv.submit(dp, s, tt, n_sims=2, seed=3))
+        gi, _ = sv.poll(sv.submit(di, s, tt, n_sims=2, seed=3))
+        with pytest.raises(stk.StkError) as e:
+            sv.set_polygon(999, vx, vy)
+        assert e.value.code == stk.STK_EINVAL
+    with stk.Pattern(x, y, t, box) as p:
+        p.set_polygon(vx, vy)
+        wp = p.run(s, tt, n_sims=2, seed=3)
+        p.set_polygon(None)
+        p.set_intensity(rho)
+        wi = p.run(s, tt, n_sims=2, seed=3)
+    for got, want in ((gp, wp), (gi, wi)):
+        for k in ("C", "K", "K_lo", "K_hi"):
+            np.testing.assert_array_equal(got[k], want[k])
