@@ -185,7 +185,8 @@ typedef struct {
      * neighbours labelled cross_b, weights centred at the centre, normalised by
      * n_a * n_b (the subset's univariate normalisation when cross_a == cross_b).  Simulated
      * point i keeps the label of observed point i (CSR and permutation; not bootstrap).
-     * NULL = univariate.  Not combined with centre_mask. */
+     * NULL = univariate.  Not combined with centre_mask, a polygon study area or an
+     * intensity. */
     const uint8_t* labels;
     int cross_a;
     int cross_b;

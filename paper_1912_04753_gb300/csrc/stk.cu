@@ -365,6 +365,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         return fail(STK_EINVAL, "cross labels must be in 0..255");
     if (h->inten.nix > 0 && q->labels)
         return fail(STK_EINVAL, "the inhomogeneous K takes no labels (cross K)");
+    if (h->nv > 0 && q->labels)
+        return fail(STK_EINVAL, "cross K takes the rectangle, not a polygon study area");
     if (h->inten.nix > 0 && h->inh_zero && q->sim_method == STK_SIM_PERMUTATION &&
         plan.seed.size() > 0)
         return fail(STK_EINVAL,

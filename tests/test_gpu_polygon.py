@@ -115,3 +115,6 @@ def test_polygon_arguments_checked(stk, orc):
         assert e.value.code == stk.STK_EINVAL
         p.set_polygon([0.0, 100.0, 100.0, 0.0], [0.0, 0.0, 100.0, 100.0])  # the box itself
         assert p.k(np.array([30.0]), np.array([5.0]))["C"][0, 0] >= 0
+        with pytest.raises(stk.StkError) as e:  # cross K takes the rectangle only
+            p.run(np.array([30.0]), np.array([5.0]), labels=np.zeros(3, np.uint8), cross=(0, 0))
+        assert e.value.code == stk.STK_EINVAL
