@@ -8,7 +8,10 @@ by the wrong axis's cell count, the translation correction with dx in place of d
 sector test with its operands transposed, a signed polygon area, an open polygon boundary, a
 ray test inclusive at both ends, an arc judged at its start instead of its midpoint, the
 cross-K denominator of the same-label case used for two labels, the intensity grid's x cell
-count used along y, and the grid-accelerated histogram skipping the cells on one side."""
+count used along y, the grid-accelerated histogram skipping the cells on one side, grids not
+cumulated over time, L without the factor 2 of the cylinder's height, a bootstrap that never
+draws the last point, and a permutation that maps out-of-range Feistel values to the identity
+instead of walking the cycle."""
 import os
 import subprocess
 import sys
@@ -48,6 +51,14 @@ MUTANTS = {
                               "axis_cell(y, box[2], box[3], nix)"),
     "grid_neighbours_one_side": ("for (int dxx = -1; dxx <= 1; ++dxx)",
                                  "for (int dxx = -1; dxx <= 0; ++dxx)"),
+    "no_cumulation_over_time": ("for (int b2 = 0; b2 <= b; ++b2)",
+                                "for (int b2 = b; b2 <= b; ++b2)"),
+    "l_without_factor_2": ("sqrt(kv / (2.0 * ORACLE_PI * tt[b])) - s[a]",
+                           "sqrt(kv / (ORACLE_PI * tt[b])) - s[a]"),
+    "bootstrap_never_last": ("int64_t src = (int64_t)(u * (double)n);",
+                             "int64_t src = (int64_t)(u * (double)(n - 1));"),
+    "permutation_no_cycle_walk": ("while (v >= (uint64_t)n) v = oracle_feistel(v, b, seed, sim);",
+                                  "if (v >= (uint64_t)n) v = (uint64_t)i;"),
 }
 
 

@@ -401,7 +401,12 @@ def test_bootstrap_draws_are_observed_points_uniformly(orc):
     e = sims
     chi2 = ((counts - e) ** 2 / e).sum()
     assert abs(chi2 - (n - 1)) < 6 * math.sqrt(2 * (n - 1))
+    assert counts.min() > 0  # every point is drawn (expected 200 times each)
     assert orc.bootstrap_index(1, 3, 0, 0) == 0
+    # three points: each index with probability 1/3 (5 binomial standard errors)
+    draws = np.array([orc.bootstrap_index(3, 5, k, i) for k in range(400) for i in range(3)])
+    freq = np.bincount(draws, minlength=3) / len(draws)
+    assert np.all(np.abs(freq - 1 / 3) < 5 * math.sqrt((1 / 3) * (2 / 3) / len(draws)))
 
 
 def test_bootstrap_duplicates_are_zero_distance_pairs(orc):
