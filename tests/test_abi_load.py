@@ -109,3 +109,21 @@ def test_intensity_argument_errors_need_no_device(lib):
     with pytest.raises(stk.StkError) as e:
         stk.stk_set_intensity(None, good)
     assert e.value.code == 1
+
+
+def test_null_handles_and_servers_are_rejected(lib):
+    """Every entry point that takes a handle or a server checks it on the host first."""
+    import ctypes
+
+    import paper_1912_04753_gb300 as stk
+
+    L = stk.load()
+    v = np.array([0.0, 1.0, 0.0])
+    P = ctypes.c_void_p
+    assert L.stk_set_polygon(None, v.ctypes.data_as(P), v.ctypes.data_as(P), 3) == 1
+    assert L.stk_set_intensity(None, None, 0, 0, 0) == 1
+    assert L.stk_server_set_polygon(None, 1, v.ctypes.data_as(P), v.ctypes.data_as(P), 3) == 1
+    assert L.stk_server_set_intensity(None, 1, None, 0, 0, 0) == 1
+    assert L.stk_server_unregister(None, 1) == 1
+    assert L.stk_run(None, None, None) == 1
+    assert "NULL" in stk.stk_last_error()
