@@ -21,7 +21,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "stk_oracle.c")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_inhom.py", "tests/test_oracle_dir.py",
-        "tests/test_oracle_grid.py"]
+        "tests/test_oracle_grid.py", "tests/test_oracle_properties.py"]
 
 MUTANTS = {
     "n2_normalisation": ("nn * (nn - 1.0)", "nn * nn"),
