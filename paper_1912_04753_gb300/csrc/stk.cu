@@ -321,6 +321,35 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
     return STK_OK;
 }
 
+// With STK_JOB_LOG set, every job appends one JSON line with its parameters and statistics
+// to that file (jobs of several threads are serialised).
+std::mutex g_log_mu;
+
+void log_job(const stk_handle* h, const stk_request* q, int nsec) {
+    const char* path = getenv("STK_JOB_LOG");
+    if (!path || !*path) return;
+    const stk_stats& st = h->last;
+    std::lock_guard<std::mutex> lock(g_log_mu);
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"n\": %lld, \"realizations\": %d, \"waves\": %d, \"cs\": %d, \"ct\": %d, "
+            "\"n_sectors\": %d, \"prec\": %d, \"edge_mode\": %d, \"norm\": %d, "
+            "\"sim_method\": %d, \"polygon_vertices\": %d, \"intensity_cells\": %d, "
+            "\"qualifying_pairs\": %lld, \"candidate_pairs\": %lld, \"fp64_recomputed\": %lld, "
+            "\"ms_total\": %.3f, \"ms_pair\": %.3f, \"pairs_per_s\": %.6g, "
+            "\"grid_refinement\": [%d, %d], \"graph_replays\": %d, \"kernel_launches\": %lld, "
+            "\"internal_errors\": %lld}\n",
+            (long long)h->n, st.realizations, st.waves, q->cs, q->ct, nsec, q->prec, q->edge_mode,
+            q->norm, q->sim_method, h->nv, h->inten.nix * h->inten.niy * h->inten.nit,
+            (long long)st.qualifying_pairs, (long long)st.candidate_pairs,
+            (long long)st.fp64_recomputed, st.ms_total, st.ms_pair,
+            st.ms_pair > 0 ? (double)st.qualifying_pairs / (st.ms_pair * 1e-3) : 0.0,
+            st.grid_refinement, st.grid_refinement_t, st.graph_replays,
+            (long long)st.kernel_launches, (long long)st.internal_errors);
+    fclose(f);
+}
+
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
             int* R_out, int f_force) {
     using clock = std::chrono::steady_clock;
@@ -855,6 +884,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.graph_replays = replays;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
+    log_job(h, q, nsec);
     return STK_OK;
 }
 

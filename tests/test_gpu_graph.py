@@ -50,3 +50,28 @@ def test_graph_replay_equals_direct_issue(stk, monkeypatch):
             monkeypatch.setenv("STK_GRAPHS", "1")
             p.run(s, tt, n_sims=5, seed=1, prec=prec)
             assert p.stats()["graph_replays"] == 0
+
+
+def test_job_log_lines(stk, orc, tmp_path):
+    # STK_JOB_LOG: one JSON line per job with the job's statistics
+    import json
+    import os
+
+    from paper_1912_04753_gb300 import workloads as wl
+
+    w = wl.config_csr_small(seed=2, n=1500)
+    path = tmp_path / "jobs.jsonl"
+    os.environ["STK_JOB_LOG"] = str(path)
+    try:
+        with stk.Pattern(w.x, w.y, w.t, w.box) as p:
+            p.run(w.s, w.tt, n_sims=3, seed=1)
+            st = p.stats()
+            p.run(w.s, w.tt, n_sectors=2, edge_mode=stk.STK_EDGE_TRANSLATION)
+    finally:
+        del os.environ["STK_JOB_LOG"]
+    lines = [json.loads(l) for l in path.read_text().splitlines()]
+    assert len(lines) == 2
+    a, b = lines
+    assert a["n"] == 1500 and a["realizations"] == 4 and a["cs"] == len(w.s)
+    assert a["qualifying_pairs"] == st["qualifying_pairs"]
+    assert a["internal_errors"] == 0 and b["n_sectors"] == 2 and b["edge_mode"] == 2
