@@ -237,6 +237,8 @@ typedef struct {
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);
+/* Statistics of the last job on h.  With the environment variable STK_JOB_LOG naming a file,
+ * every job also appends them, with its parameters, to that file as one JSON line. */
 int stk_last_stats(const stk_handle* h, stk_stats* out);
 
 /* One CSR realization generated by the device generator that stk_envelope
