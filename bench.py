@@ -8,8 +8,13 @@ per second (pairs with d <= s_max and u <= t_max, summed over all 100 realizatio
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a bounded sample of the
-same workload (random centres of the observed pattern against all n points).
+Prints one JSON line.  Besides the headline it carries the end-to-end time through the C ABI
+from host arrays (`e2e`), the plain FP64 comparison (`plain_fp64`), the CPU oracle on a bounded
+sample (`cpu_baseline`), the serving loop (`serve`), permutation and bootstrap simulations
+(`sim_methods`), a polygon study area (`polygon`), the inhomogeneous and the directional K
+(`inhomogeneous`, `directional`), the pair kernel's roofline and the clocks seen.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload (random
+centres of the observed pattern against all n points).
 """
 from __future__ import annotations
 
