@@ -10,8 +10,8 @@ ray test inclusive at both ends, an arc judged at its start instead of its midpo
 cross-K denominator of the same-label case used for two labels, the intensity grid's x cell
 count used along y, the grid-accelerated histogram skipping the cells on one side, grids not
 cumulated over time, L without the factor 2 of the cylinder's height, a bootstrap that never
-draws the last point, and a permutation that maps out-of-range Feistel values to the identity
-instead of walking the cycle."""
+draws the last point, a permutation that maps out-of-range Feistel values to the identity
+instead of walking the cycle, and CSR points that never reach the last tenth of each axis."""
 import os
 import subprocess
 import sys
@@ -59,6 +59,7 @@ MUTANTS = {
                              "int64_t src = (int64_t)(u * (double)(n - 1));"),
     "permutation_no_cycle_walk": ("while (v >= (uint64_t)n) v = oracle_feistel(v, b, seed, sim);",
                                   "if (v >= (uint64_t)n) v = (uint64_t)i;"),
+    "csr_short_of_the_box": ("const double span = hi - lo;", "const double span = 0.9 * (hi - lo);"),
 }
 
 

@@ -590,3 +590,25 @@ def test_cross_k_normalisations_recombine_to_the_univariate_sum(orc):
             k = orc.k_cross(x, y, t, lab, a, b, box, s, tt)["K"]
             acc += k * (na[a] * na[b] if a != b else na[a] * (na[a] - 1))
     np.testing.assert_allclose(acc, total, rtol=1e-12)
+
+
+def test_envelope_rank_under_csr(orc):
+    """Section 3's Monte Carlo test: for CSR data and m CSR simulations the observed K exceeds
+    the envelope's maximum with probability 1/(m+1), and falls below its minimum with the same
+    probability (the m+1 patterns are exchangeable).  The observed patterns are drawn with
+    numpy, independently of the oracle's generator, so a biased simulation fails this test."""
+    box = (0.0, 1.0, 0.0, 1.0, 0.0, 1.0)
+    s, tt = np.array([0.1, 0.2]), np.array([0.2, 0.4])
+    n, m, R = 150, 9, 300
+    above = below = 0
+    for r in range(R):
+        rng = np.random.default_rng(9000 + r)
+        x, y, t = rng.random(n), rng.random(n), rng.random(n)
+        obs = orc.k_function(x, y, t, box, s, tt)["K"][1, 1]
+        env = orc.envelope(n, box, s, tt, m, 500 + r)
+        above += obs > env["K_hi"][1, 1]
+        below += obs < env["K_lo"][1, 1]
+    p = 1.0 / (m + 1)
+    se = math.sqrt(p * (1 - p) / R)
+    assert abs(above / R - p) < 4 * se, above
+    assert abs(below / R - p) < 4 * se, below
