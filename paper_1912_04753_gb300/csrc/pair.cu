@@ -806,10 +806,10 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         return;
     }
     if (VAR == kVarDir) {
-        // Sector from the hi parts (their differences are exact); a cross product within its
-        // guard of a boundary, or an offset within the guard of the axis at angle 0 / pi,
-        // leaves the pair to FP64.  Translation weight in FP32 (a few ulp; no cancellation:
-        // W - |dx| >= W / 2, D - u >= D / 2).
+        // Sector from the accurate offset (exact hi-part difference plus the low parts, as in
+        // phase C); a cross product within its guard of a boundary, or an offset within the
+        // guard of the axis at angle 0 / pi, leaves the pair to FP64.  Translation weight in
+        // FP32 (a few ulp; no cancellation: W - |dx| >= W / 2, D - u >= D / 2).
         bool xf[2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -820,9 +820,11 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
             const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
             const float4 ca = ws.cen_a[cl];
+            const float4 cb = ws.cen_b[cl];
             const float4 qj = w.Pk[2 * (size_t)j];
-            float dx = fmaf(dcx, pc.g.cwq, ca.x) - qj.x;
-            float dy = fmaf(dcy, pc.g.chq, ca.y) - qj.y;
+            const float2 loj = w.Plok[j];
+            float dx = (fmaf(dcx, pc.g.cwq, ca.x) - qj.x) + (fmaf(dcx, pc.g.cwl, cb.x) - loj.x);
+            float dy = (fmaf(dcy, pc.g.chq, ca.y) - qj.y) + (fmaf(dcy, pc.g.chl, cb.y) - loj.y);
             int k = 0;
             bool und = false;
             if (pc.nsec > 1) {

@@ -450,10 +450,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->h_pc->tw = h->box[1] - h->box[0];
     h->h_pc->th = h->box[3] - h->box[2];
     h->h_pc->td = h->box[5] - h->box[4];
-    // FP32 directional kernel: boundaries and sides rounded to FP32; the sector test's guard
-    // covers the rounding of the boundaries (2^-24 per component), of the FP32 cross product
-    // (2^-24 of each product) and the hi parts' distance from the FP64 offset (at most one
-    // quantum per axis): |cross_FP32 - cross_FP64| < 2^-22 sqrt(2) s_max + sqrt(2) q
+    // FP32 directional kernel: boundaries and sides rounded to FP32.  Its offset is the exact
+    // hi-part difference plus the low parts: within 2^-24 |d| + 3 2^-24 q of the offset the
+    // points' FP64 coordinates give, which is itself within half an ulp of the largest
+    // coordinate of the FP64 offset.  With the boundaries' rounding (2^-24 per component) and
+    // the FP32 cross product's (2^-24 of each product), |cross_FP32 - cross_FP64| stays below
+    // 2^-21 s_max + 2^-22 q + 4e-16 max|coordinate|, inside sec_g; the sign of d_y is certain
+    // beyond sec_gd.
     for (int m = 1; m < nsec; ++m) {
         h->h_pc->sec_bxf[m - 1] = (float)h->h_pc->sec_bx[m - 1];
         h->h_pc->sec_byf[m - 1] = (float)h->h_pc->sec_by[m - 1];
@@ -463,8 +466,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->h_pc->tdf = (float)h->h_pc->td;
     {
         const double qm = std::max((double)g.qx, (double)g.qy);
-        h->h_pc->sec_g = (float)(5.0e-7 * q->s[cs - 1] + 2.0 * qm);
-        h->h_pc->sec_gd = (float)(2.0 * qm);
+        const double big = std::max(std::max(fabs(h->box[0]), fabs(h->box[1])),
+                                    std::max(fabs(h->box[2]), fabs(h->box[3])));
+        h->h_pc->sec_g = (float)(1.0e-6 * q->s[cs - 1] + 1.0e-6 * qm + 4.0e-16 * big + 1e-30);
+        h->h_pc->sec_gd = (float)(1.0e-6 * qm + 4.0e-16 * big + 1e-30);
     }
     Polygon poly;
     if (h->nv > 0) {
