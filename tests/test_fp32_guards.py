@@ -1,0 +1,101 @@
+"""The FP32 directional path decides a pair's sector in FP32 only outside a guard band and
+leaves the rest to FP64.  This test emulates, with numpy FP32 arithmetic, the device's point
+representation (hi part: the offset from the cell origin rounded to the quantum q = 2^-22 P,
+P the power of two >= the cell side; FP32 low part) and its sector test, on offsets placed
+adversarially close to the sector boundaries and to the axis at angle 0 / pi, at projected-size
+coordinates, and checks that whenever the FP32 test clears its guards the sector equals the
+one the reference FP64 arithmetic gives.  It also checks that the guards leave almost every
+random pair to FP32."""
+import math
+
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def _pow2_at_least(v):
+    return 2.0 ** math.ceil(math.log2(v))
+
+
+def _rep(v, lo, side, nc):
+    """Cell index, FP32 hi part and FP32 low part of coordinates v (as the scatter kernel)."""
+    c = np.clip(np.floor((v - lo) * (1.0 / side)), 0, nc - 1)
+    o = v - (lo + c * side)
+    q = _pow2_at_least(side) * 2.0 ** -22
+    hi = np.rint(o * (1.0 / q)) * q
+    return c, hi.astype(f32), (o - hi).astype(f32), q
+
+
+def _fma32(a, b, c):
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
+def _sectors(n_sec, dx, dy, bx, by):
+    flip = ~((dy > 0) | ((dy == 0) & (dx > 0)))
+    dx = np.where(flip, -dx, dx)
+    dy = np.where(flip, -dy, dy)
+    return dx, dy
+
+
+@pytest.mark.parametrize("n_sec,x0", [(8, 5.0e5), (6, 0.0), (3, 3.3e6)])
+def test_sector_guard_is_sound(n_sec, x0):
+    rng = np.random.default_rng(n_sec)
+    s_max, fs = 1000.0, 2
+    W = H = 49_999.37  # a cell side that is not a multiple of the quantum
+    y0 = x0 + 1234.5
+    nx = ny = int(W // (s_max / fs))
+    cw = W / nx
+    N = 400_000
+    m = rng.integers(0, n_sec, N)  # boundary index (0: the axis at angle 0 / pi)
+    eps = np.exp(rng.uniform(math.log(1e-13), math.log(1e-3), N)) * rng.choice([-1, 1], N)
+    eps[:2000] = 0.0
+    ang = m * math.pi / n_sec + eps + np.where(rng.random(N) < 0.5, 0.0, math.pi)
+    r = rng.uniform(0.0, s_max, N)
+    r[2000:2100] = 0.0
+    xi = x0 + s_max + rng.uniform(0, W - 2 * s_max, N)
+    yi = y0 + s_max + rng.uniform(0, H - 2 * s_max, N)
+    xj = xi - r * np.cos(ang)
+    yj = yi - r * np.sin(ang)
+    # reference: FP64 offset, upper half plane, count of boundaries with cross >= 0
+    bx64 = np.array([math.cos(k * math.pi / n_sec) for k in range(1, n_sec)])
+    by64 = np.array([math.sin(k * math.pi / n_sec) for k in range(1, n_sec)])
+    dx64, dy64 = _sectors(n_sec, xi - xj, yi - yj, bx64, by64)
+    k64 = ((bx64[None, :] * dy64[:, None] - by64[None, :] * dx64[:, None]) >= 0).sum(axis=1)
+    k64 = np.where((xi - xj == 0) & (yi - yj == 0), 0, k64)
+    # device: FP32 accurate offset from hi + lo parts, FP32 boundaries, guards
+    cxi, hxi, lxi, qx = _rep(xi, x0, cw, nx)
+    cxj, hxj, lxj, _ = _rep(xj, x0, cw, nx)
+    cyi, hyi, lyi, qy = _rep(yi, y0, cw, ny)
+    cyj, hyj, lyj, _ = _rep(yj, y0, cw, ny)
+    cwq = f32(np.rint(cw / qx) * qx)
+    cwl = f32(cw - np.rint(cw / qx) * qx)
+    dcx = (cxi - cxj).astype(f32)
+    dcy = (cyi - cyj).astype(f32)
+    cwq_v, cwl_v = np.full(N, cwq, f32), np.full(N, cwl, f32)
+    dx = ((_fma32(dcx, cwq_v, hxi) - hxj).astype(f32) + (_fma32(dcx, cwl_v, lxi) - lxj)).astype(f32)
+    dy = ((_fma32(dcy, cwq_v, hyi) - hyj).astype(f32) + (_fma32(dcy, cwl_v, lyi) - lyj)).astype(f32)
+    q = max(qx, qy)
+    big = max(abs(x0), abs(x0 + W), abs(y0), abs(y0 + H))
+    sec_g = f32(1.0e-6 * s_max + 1.0e-6 * q + 4.0e-16 * big + 1e-30)
+    sec_gd = f32(1.0e-6 * q + 4.0e-16 * big + 1e-30)
+    und = np.abs(dy) <= sec_gd
+    dxf, dyf = _sectors(n_sec, dx, dy, None, None)
+    k32 = np.zeros(N, int)
+    for bxm, bym in zip(bx64.astype(f32), by64.astype(f32)):
+        t = (bym * dxf).astype(f32)
+        cr = (bxm.astype(np.float64) * dyf.astype(np.float64) - t.astype(np.float64)).astype(f32)
+        und |= np.abs(cr) <= sec_g
+        k32 += (cr > 0).astype(int)
+    decided = ~und
+    assert decided.sum() > 0.1 * N  # many decisions close to a boundary are exercised
+    bad = np.flatnonzero(decided & (k32 != k64))
+    assert bad.size == 0, (bad[:5], k32[bad[:5]], k64[bad[:5]], eps[bad[:5]])
+    # on random (non-adversarial) offsets the guards send very few pairs to FP64
+    a2 = rng.uniform(0, 2 * math.pi, 50_000)
+    r2 = rng.uniform(1.0, s_max, 50_000)
+    c2 = np.abs(np.stack([np.cos(k * math.pi / n_sec) * r2 * np.sin(a2) -
+                          np.sin(k * math.pi / n_sec) * r2 * np.cos(a2)
+                          for k in range(1, n_sec)]))
+    frac = np.mean((c2 <= sec_g).any(axis=0) | (np.abs(r2 * np.sin(a2)) <= sec_gd))
+    assert frac < 1e-3
