@@ -40,7 +40,7 @@ UNIT = "qualifying ordered pairs/s"
 OPS_PER_CANDIDATE = 8
 OPS_PER_QUALIFYING = 12
 # DRAM bytes (read + write) of the pair kernel per realization of the 2M-point mixture, from
-# the ncu capture in profiles/pair_fp32_poi_n2M.md (2 realizations per launch there)
+# one ncu capture of the kernel as built (2 realizations per launch there)
 PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 99.7e6}
 
 
@@ -51,11 +51,6 @@ def _workload(name, sims=None):
     if sims is not None:
         w.n_sims = sims
     return w
-
-
-def rank_seed(base: int, rank: int) -> int:
-    """Simulation seed of a rank: every rank runs its own independent job (weak scaling)."""
-    return base + 7919 * rank
 
 
 def reduce_over_ranks(elapsed_ms: float, qual: float, device):
@@ -194,7 +189,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "sims": w.n_sims,
                        "thresholds": [len(w.s), len(w.tt)]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -294,14 +289,27 @@ def run_ours(args):
     w = _workload(args.config, args.sims)
     prec = stk.STK_PREC_FP32_GUARDED if args.prec == "fp32" else stk.STK_PREC_FP64
     exec_mode = stk.STK_EXEC_BATCHED if args.exec == "batched" else stk.STK_EXEC_PLAIN
-    seed = rank_seed(w.sim_seed, rank)
+    seed = w.sim_seed
     stream = torch.cuda.Stream()
     h = stk.stk_create(w.x, w.y, w.t, w.box)
     stk.stk_set_stream(h, stream)
+    dev = torch.device("cuda", local)
+
+    def run_on(handle):
+        """One whole job; with N ranks each runs its share (a block of the realizations and a
+        shard of the observed pattern's pairs) and the partial results are all-reduced."""
+        if ws == 1:
+            return stk.stk_run(handle, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
+                               exec_mode=exec_mode)
+        from types import SimpleNamespace
+
+        from paper_1912_04753_gb300 import shard
+
+        return shard.run_sharded(SimpleNamespace(h=handle), w.s, w.tt, w.n_sims, seed, ws, rank,
+                                 device=dev, prec=prec, exec_mode=exec_mode)
 
     def job():
-        return stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
-                           exec_mode=exec_mode)
+        return run_on(h)
 
     for _ in range(args.warmup):
         job()
@@ -343,12 +351,12 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         h2 = stk.stk_create(w.x, w.y, w.t, w.box)
-        stk.stk_run(h2, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec, exec_mode=exec_mode)
+        run_on(h2)
         stk.stk_destroy(h2)
         torch.cuda.synchronize()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
     e2e_ms /= e2e_steps
-    e2e_value = (qual / args.steps) / (e2e_ms / 1e3)
+    e2e_value = (qual_all / args.steps) / (e2e_ms / 1e3)
 
     # plain FP64 comparison (spec pairing): one job, one launch per realization, and the
     # per-cell error of the FP32-guarded grids against it on the same realizations
@@ -505,14 +513,16 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (guarded, f64 ties)"
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32 (guarded, f64 ties)"
         if prec == stk.STK_PREC_FP32_GUARDED else "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "sims": w.n_sims,
                    "thresholds": [len(w.s), len(w.tt)], "s_max_m": float(w.s[-1]),
                    "t_max_s": float(w.tt[-1]), "exec": args.exec, "prec": args.prec,
                    "l2": "inputs larger than L2 (100 realizations x 2M points resident)",
-                   "parallelism": f"independent jobs x{ws}"},
+                   "parallelism": (f"one job split over {ws} ranks: realization blocks + "
+                                   "observed-pattern shards, exact all-reduce"
+                                   if ws > 1 else "one job, one GPU")},
         "job_s": elapsed_ms / args.steps / 1e3,
         "sims_per_s": w.n_sims * args.steps / (elapsed_ms / 1e3),
         "candidate_pairs_per_step": cand // args.steps,

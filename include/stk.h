@@ -201,6 +201,17 @@ typedef struct {
      * edge_mode NONE or TRANSLATION, the rectangle, no intensity and no labels.
      * 0 or 1: no split. */
     int n_sectors;
+    /* Sharding of the OBSERVED pattern across processes (one GPU each; the paper partitions the
+     * points over Spark workers, Section 4.4).  With shard_count > 1 this call evaluates only
+     * shard shard_index (0 .. shard_count - 1) of the observed pattern's pairs: its work units
+     * (32 centres of one grid row each, in time-major row order) are split into shard_count
+     * contiguous ranges of equal unit count, and each unordered pair belongs to exactly one
+     * range.  The observed grids returned then hold that shard's share only; the integer
+     * accumulators of all shards (stk_last_accumulators) summed element-wise equal the whole
+     * pattern's bit for bit, and stk_merge_grids turns the sum into K, L, raw sums and counts.
+     * Simulations are not affected (shard them with first_sim / n_sims).  0 or 1: no split. */
+    int shard_count;
+    int shard_index;
 } stk_request;
 
 typedef struct {
@@ -237,6 +248,49 @@ typedef struct {
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);
+
+/* ---- Partial results and their exact merge (multi-process jobs; Section 3, Eq. 2-4) ------
+ * A job split across processes (realizations k in blocks via first_sim / n_sims, the observed
+ * pattern via shard_count / shard_index) is merged from two kinds of partial results:
+ *   - the raw integer accumulators of a realization, which add exactly: per histogram bin
+ *     (s_bin, t_bin), NOT cumulative, the count of ordered pairs and the fixed-point sum of
+ *     their weights, as four uint64 rows [4][nbins]: count, low and high 32-bit halves of the
+ *     sum of (w - 1) in units of 2^-32 (the weight excess of Eq. 2's 1 / (w v) over 1), and a
+ *     whole part (inhomogeneous K only: its sum of h_i h_j / (w v) is kept as
+ *     whole * 2^64 + high * 2^32 + low in units of 2^-64; zero otherwise).  Element-wise
+ *     sums over shards are the whole job's accumulators, whatever the order;
+ *   - per-realization K grids, whose envelope (element-wise min / max) is exact and
+ *     order-free, so local envelopes merge by a min / max reduction.
+ * nbins = n_sectors * cs * ct (n_sectors >= 1). */
+
+/* Raw accumulators of realizations row0 .. row0 + rows - 1 of the last job on h (row 0 is the
+ * observed pattern when the job had one, then the simulations in order), copied to the
+ * caller-owned host array out [rows][4][nbins] (uint64).  Errors: STK_EINVAL (NULL, rows out of
+ * range of the last job). */
+int stk_last_accumulators(stk_handle* h, int row0, int rows, uint64_t* out);
+
+/* Turns `rows` merged accumulator sets acc [rows][4][nbins] (host, as stk_last_accumulators
+ * writes them) into the cumulative grids of Eq. 2-4 with the normalisation the request q would
+ * use on h (A and D of h's study area, n or the label counts of a cross K, q->norm; L scaled by
+ * n_sectors for a directional K): K, L, raw_sum [rows][nbins] (double) and pair_count
+ * [rows][nbins] (int64), caller-owned host arrays, each may be NULL.  Computed on the device
+ * (the cumulation in 128-bit fixed point), so a merged job equals the single-process job bit
+ * for bit.  Errors: STK_EINVAL (NULL, bad sizes, request rules of stk_run), STK_ENOMEM,
+ * STK_ECUDA. */
+int stk_merge_grids(stk_handle* h, const stk_request* q, const uint64_t* acc, int rows, double* K,
+                    double* L, double* raw_sum, int64_t* pair_count);
+
+/* Envelope of `rows` K grids (host array K_rows [rows][n_sectors][cs][ct], e.g. the
+ * per-realization grids of several chunks of a job, or the local K_lo and K_hi of several
+ * processes stacked): element-wise min and max over the rows (Section 3 envelopes) and L of
+ * those (Eq. 4, sqrt(n_sectors K / (2 pi t)) - s for a directional K, n_sectors = 1 otherwise),
+ * into caller-owned host arrays [n_sectors][cs][ct], each may be NULL.  Computed on the current
+ * device.  Errors: STK_EINVAL (NULL input, rows < 1, bad sizes or thresholds), STK_ENOMEM,
+ * STK_ECUDA, STK_ENODEV. */
+int stk_envelope_merge(const double* K_rows, int rows, int cs, int ct, int n_sectors,
+                       const double* s, const double* tt, double* K_lo, double* K_hi,
+                       double* L_lo, double* L_hi);
+
 /* Statistics of the last job on h.  With the environment variable STK_JOB_LOG naming a file,
  * every job also appends them, with its parameters, to that file as one JSON line. */
 int stk_last_stats(const stk_handle* h, stk_stats* out);
@@ -276,7 +330,9 @@ int stk_sim_resample(const double* x0, const double* y0, const double* t0, int64
  * arrays; thresholds are host arrays; FP32_GUARDED precision, A*D/(n(n-1)) normalisation.
  * Every intermediate buffer lives in one static device array of 64 MiB inside the library,
  * held on every GPU that loads it until the process exits; patterns up to 262,144 points
- * and grids up to 2^20 cells are accepted, larger ones fail with STK_EINVAL.  The first call
+ * and grids up to 2^20 cells are accepted, larger ones fail with STK_EINVAL, as do NULL
+ * pointers.  STK_EDOMAIN: a point outside the box; STK_ETIMEOUT: a bounded wait inside the
+ * pair kernel ran out (outputs incomplete; the next call starts afresh).  The first call
  * on a device looks up the array's address (once per device): make it before any stream
  * capture.  All calls share the array, so calls that overlap on the GPU race; the caller
  * serialises them.  `stream` is a cudaStream_t or NULL; the call synchronises it.  Calls no

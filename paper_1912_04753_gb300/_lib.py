@@ -40,7 +40,8 @@ class stk_request(ctypes.Structure):
                 ("n_sims", ctypes.c_int), ("seed", ctypes.c_uint64), ("exec", ctypes.c_int),
                 ("centre_mask", _P), ("sim_method", ctypes.c_int), ("first_sim", ctypes.c_uint32),
                 ("labels", _P), ("cross_a", ctypes.c_int), ("cross_b", ctypes.c_int),
-                ("n_sectors", ctypes.c_int)]
+                ("n_sectors", ctypes.c_int), ("shard_count", ctypes.c_int),
+                ("shard_index", ctypes.c_int)]
 
 
 class stk_result(ctypes.Structure):
@@ -107,6 +108,9 @@ def load(build_if_missing: bool = False):
         "stk_envelope": ([_P, _P, i32, _P, i32, i32, i32, i32, i32, u64, _P, _P, _P, _P], i32),
         "stk_run": ([_P, ctypes.POINTER(stk_request), ctypes.POINTER(stk_result)], i32),
         "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
+        "stk_last_accumulators": ([_P, i32, i32, _P], i32),
+        "stk_merge_grids": ([_P, ctypes.POINTER(stk_request), _P, i32, _P, _P, _P, _P], i32),
+        "stk_envelope_merge": ([_P, i32, i32, i32, i32, _P, _P, _P, _P, _P, _P], i32),
         "stk_sim_points": ([ctypes.POINTER(stk_box), i64, u64, u32, _P, _P, _P], i32),
         "stk_sim_resample": ([_P, _P, _P, i64, i32, u64, u32, _P, _P, _P], i32),
         "stk_sim_points_polygon": ([ctypes.POINTER(stk_box), _P, _P, i32, i64, u64, u32, _P, _P,
@@ -226,21 +230,32 @@ def stk_envelope(h, s, tt, n_sims, seed, edge_mode=STK_EDGE_ISOTROPIC,
     return {k: v.reshape(sh) for k, v in zip(("K_lo", "K_hi", "L_lo", "L_hi"), out)}
 
 
+def _request(s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
+             prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
+             centre_mask=None, sim_method=STK_SIM_CSR, first_sim=0, labels=None, cross=(0, 0),
+             n_sectors=0, shard=(0, 0)):
+    """(stk_request, arrays it points to): the arrays must outlive the call."""
+    mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+    q = stk_request(_ptr(s), s.shape[0], _ptr(tt), tt.shape[0], edge_mode, prec, norm, n_sims,
+                    seed, exec_mode, _ptr(mask), sim_method, first_sim, _ptr(lab),
+                    int(cross[0]), int(cross[1]), int(n_sectors), int(shard[0]), int(shard[1]))
+    return q, (s, tt, mask, lab)
+
+
 def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
             prec=STK_PREC_FP32_GUARDED, norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED,
             centre_mask=None, want_sims=False, sim_method=STK_SIM_CSR, first_sim=0,
-            labels=None, cross=(0, 0), n_sectors=0):
+            labels=None, cross=(0, 0), n_sectors=0, shard=(0, 0)):
     """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim).
-    With n_sectors > 1 (directional K) every grid is [n_sectors, cs, ct]."""
+    With n_sectors > 1 (directional K) every grid is [n_sectors, cs, ct].  shard = (count,
+    index) evaluates only that shard of the observed pattern's pairs (see stk_request)."""
     s, tt = _f64(s), _f64(tt)
     cs, ct = s.shape[0], tt.shape[0]
     grid = (n_sectors, cs, ct) if n_sectors > 1 else (cs, ct)
     nb = int(np.prod(grid))
-    mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
-    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
-    q = stk_request(_ptr(s), cs, _ptr(tt), ct, edge_mode, prec, norm, n_sims, seed, exec_mode,
-                    _ptr(mask), sim_method, first_sim, _ptr(lab), int(cross[0]), int(cross[1]),
-                    int(n_sectors))
+    q, keep = _request(s, tt, n_sims, seed, edge_mode, prec, norm, exec_mode, centre_mask,
+                       sim_method, first_sim, labels, cross, n_sectors, shard)
     o = {"K": np.zeros(nb), "L": np.zeros(nb), "S": np.zeros(nb), "C": np.zeros(nb, np.int64)}
     if n_sims > 0:
         for k in ("K_lo", "K_hi", "L_lo", "L_hi"):
@@ -256,6 +271,55 @@ def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
     for k, v in o.items():
         out[k] = v.reshape((n_sims,) + grid) if k in ("K_sims", "C_sims") else v.reshape(grid)
     return out
+
+
+def stk_last_accumulators(h, row0=0, rows=1, n_sectors=0, cs=None, ct=None):
+    """Raw integer accumulators of realizations row0 .. row0 + rows - 1 of the last job on h
+    (row 0 = observed when the job had one): uint64 [rows, 4, nbins] (count, excess low half,
+    excess high half, whole part; per bin, not cumulative).  cs, ct: the job's grid."""
+    nb = int(cs) * int(ct) * (n_sectors if n_sectors > 1 else 1)
+    out = np.zeros((rows, 4, nb), np.uint64)
+    _check(load().stk_last_accumulators(h, row0, rows, _ptr(out)))
+    return out
+
+
+def stk_merge_grids(h, acc, s, tt, **kw):
+    """Cumulative K, L, S, C grids from merged accumulators acc [rows, 4, nbins] (uint64),
+    normalised as a request with the keywords of stk_run would be on h.  Returns the dict of
+    grids, each [rows, (n_sectors,) cs, ct]."""
+    s, tt = _f64(s), _f64(tt)
+    acc = np.ascontiguousarray(acc, dtype=np.uint64)
+    if acc.ndim != 3 or acc.shape[1] != 4:
+        raise ValueError("acc must be [rows, 4, nbins]")
+    rows, nbins = acc.shape[0], acc.shape[2]
+    nsec = kw.get("n_sectors", 0)
+    grid = (nsec, s.shape[0], tt.shape[0]) if nsec > 1 else (s.shape[0], tt.shape[0])
+    if int(np.prod(grid)) != nbins:
+        raise ValueError("acc's bin count does not match the thresholds and sectors")
+    kw.pop("want_sims", None)
+    q, keep = _request(s, tt, **kw)
+    o = {"K": np.zeros(rows * nbins), "L": np.zeros(rows * nbins), "S": np.zeros(rows * nbins),
+         "C": np.zeros(rows * nbins, np.int64)}
+    _check(load().stk_merge_grids(h, ctypes.byref(q), _ptr(acc), rows, _ptr(o["K"]),
+                                  _ptr(o["L"]), _ptr(o["S"]), _ptr(o["C"])))
+    return {k: v.reshape((rows,) + grid) for k, v in o.items()}
+
+
+def stk_envelope_merge(K_rows, s, tt, n_sectors=0):
+    """Element-wise min / max over the rows of K_rows [rows, (n_sectors,) cs, ct] and L of
+    those (computed by the library on the current device): dict K_lo, K_hi, L_lo, L_hi."""
+    s, tt = _f64(s), _f64(tt)
+    K = np.ascontiguousarray(K_rows, dtype=np.float64)
+    cs, ct = s.shape[0], tt.shape[0]
+    grid = (n_sectors, cs, ct) if n_sectors > 1 else (cs, ct)
+    nb = int(np.prod(grid))
+    if K.size % nb or K.size == 0:
+        raise ValueError("K_rows must hold whole grids of the thresholds' shape")
+    rows = K.size // nb
+    out = [np.zeros(nb) for _ in range(4)]
+    _check(load().stk_envelope_merge(_ptr(K), rows, cs, ct, int(n_sectors), _ptr(s), _ptr(tt),
+                                     *[_ptr(o) for o in out]))
+    return {k: v.reshape(grid) for k, v in zip(("K_lo", "K_hi", "L_lo", "L_hi"), out)}
 
 
 def stk_last_stats(h) -> dict:
@@ -330,10 +394,40 @@ def stk_sim_resample(x, y, t, method, seed, sim):
     return ox, oy, ot
 
 
+def _check_noalloc_tensors(x, y, t, K, L, S, C, cells, current=None):
+    """The device buffers stk_k_noalloc reads and writes, checked before the call: a wrong
+    dtype, size or device would otherwise turn into out-of-bounds device accesses.  `current`:
+    the current CUDA device index (looked up when None)."""
+    import torch
+
+    named = (("x", x, torch.float64), ("y", y, torch.float64), ("t", t, torch.float64),
+             ("K", K, torch.float64), ("L", L, torch.float64), ("S", S, torch.float64),
+             ("C", C, torch.int64))
+    for name, v, _ in named:
+        if not getattr(v, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    if current is None:
+        current = torch.cuda.current_device()
+    for name, v, dt in named:
+        if v.device.index != current:
+            raise ValueError(f"{name} must live on the current CUDA device (cuda:{current})")
+        if v.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {v.dtype}")
+        if not v.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if not (x.numel() == y.numel() == t.numel()):
+        raise ValueError("x, y and t must have the same number of points")
+    for name, v in (("K", K), ("L", L), ("S", S), ("C", C)):
+        if v.numel() < cells:
+            raise ValueError(f"{name} must hold at least cs * ct = {cells} values")
+
+
 def stk_k_noalloc(x, y, t, box, s, tt, K, L, S, C, edge_mode=STK_EDGE_ISOTROPIC, stream=None):
     """K of one pattern with no allocation inside the library.  x, y, t and the outputs K, L,
-    S (float64) and C (int64), each [cs, ct], are caller-owned contiguous CUDA tensors."""
+    S (float64) and C (int64), each [cs, ct], are caller-owned contiguous CUDA tensors on the
+    current device (checked here; ValueError otherwise)."""
     s, tt = _f64(s), _f64(tt)
+    _check_noalloc_tensors(x, y, t, K, L, S, C, s.shape[0] * tt.shape[0])
     b = _box(box)
     st = None if stream is None else _P(stream.cuda_stream)
     _check(load().stk_k_noalloc(_P(x.data_ptr()), _P(y.data_ptr()), _P(t.data_ptr()), x.numel(),

@@ -46,8 +46,8 @@ def envelope_resumable(pattern, s, tt, n_sims, seed, path, chunk=16, max_chunks=
         Ks.append(z["K"])
         Cs.append(z["C"])
     Ks, Cs = np.concatenate(Ks), np.concatenate(Cs)
-    lo, hi = Ks.min(axis=0), Ks.max(axis=0)
-    den = 2.0 * np.pi * tt[None, :]
-    obs.update(K_sims=Ks, C_sims=Cs, K_lo=lo, K_hi=hi, L_lo=np.sqrt(lo / den) - s[:, None],
-               L_hi=np.sqrt(hi / den) - s[:, None])
+    # the envelope (min / max over realizations) and its L (Eq. 4, with the sector factor of a
+    # directional K) are computed by the library
+    obs.update(K_sims=Ks, C_sims=Cs)
+    obs.update(_lib.stk_envelope_merge(Ks, s, tt, n_sectors=kw.get("n_sectors", 0)))
     return obs

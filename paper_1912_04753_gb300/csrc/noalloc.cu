@@ -17,6 +17,7 @@
 //   - no cudaMalloc, cudaFree or allocating library routine is called.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -92,7 +93,8 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
                              const stk_box* box, const double* s, int cs, const double* tt,
                              int ct, int edge_mode, double* d_K, double* d_L, double* d_S,
                              int64_t* d_C, void* stream) {
-    if (!d_x || !d_y || !d_t || !box) return nofail(STK_EINVAL, "stk_k_noalloc: NULL argument");
+    if (!d_x || !d_y || !d_t || !box || !s || !tt || !d_K || !d_L || !d_S || !d_C)
+        return nofail(STK_EINVAL, "stk_k_noalloc: NULL argument");
     if (n < 2) return nofail(STK_EINVAL, "stk_k_noalloc: need n >= 2 points");
     if (n > kMaxPoints) {
         char buf[160];
@@ -113,6 +115,10 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
         return nofail(STK_EINVAL, "stk_k_noalloc: threshold grid too fine for the fixed scratch");
     PairConsts pc;
     build_pair_consts(g, n, s, cs, tt, ct, edge_mode, &pc);
+    {  // failure-detection test hook, as in the handle's jobs (see PairConsts::never_publish)
+        const char* np = getenv("STK_TEST_NEVER_PUBLISH");
+        pc.never_publish = (np && atoi(np) != 0) ? 1 : 0;
+    }
     const int nbins = cs * ct;
     const int64_t ncells = g.ncells, nrows = (int64_t)g.ny * g.nt;
     const int64_t units_max = nrows + n / kUnit + 1;
@@ -215,5 +221,9 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
     NK(cudaStreamSynchronize(st), "synchronise");
     if (h_stats[3]) return nofail(STK_EDOMAIN, "stk_k_noalloc: a point lies outside the study box");
     if (h_stats[2]) return nofail(STK_ECUDA, "stk_k_noalloc: internal consistency check failed");
+    if (h_stats[4])
+        return nofail(STK_ETIMEOUT,
+                      "stk_k_noalloc: bounded waits for work in the pair kernel ran out; the "
+                      "outputs are incomplete");
     return STK_OK;
 }

@@ -999,7 +999,8 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
     __syncthreads();
 
     for (int k = 0; k < m; ++k) {
-        const uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        shard_units(rb, k, &ubeg, &uend);
         const int64_t base = (int64_t)k * n;
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         const float4* Pk = rb.P + 2 * base;
@@ -1289,7 +1290,8 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
     __syncthreads();
 
     for (int k = 0; k < m; ++k) {
-        const uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
+        shard_units(rb, k, &ubeg, &uend);
         const int64_t base = (int64_t)k * n;
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         const double* X = rb.X + base;

@@ -94,6 +94,8 @@ struct stk_handle {
     DevBuf X, Y, T, P, Plo, cell_start, chunks, chunk_off, items, counter;
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
+    DevBuf oA;  // raw accumulators of the last job's realizations, [R][4][nbins]
+    int last_rows = 0, last_nbins = 0;  // shape of oA
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     // pinned staging of the other per-job host inputs (graph-capturable copies)
     double* h_thr = nullptr;     // [2][STK_MAX_THRESHOLDS]
@@ -215,7 +217,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
                  8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
-    f.fixed = 32 * 8 + 32 * (size_t)R * nbins +
+    f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
               16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
     return f;
@@ -228,7 +230,7 @@ size_t workspace_bytes(const stk_handle* h) {
                             &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                             &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
                             &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh,
-                            &h->Hs, &h->acc_whole};
+                            &h->Hs, &h->acc_whole, &h->oA};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     return b;
@@ -350,10 +352,33 @@ void log_job(const stk_handle* h, const stk_request* q, int nsec) {
     fclose(f);
 }
 
+// Eq. 2 normalisation of a request on h: A * D / (n (n - 1)) (A * D / n^2 with STK_NORM_N2);
+// for a cross K the label counts take n's place: n_a n_b for two labels, n_a (n_a - 1) (or
+// n_a^2) for a label with itself.
+int job_coef(const stk_handle* h, const stk_request* q, double* coef) {
+    const double nn = (double)h->n;
+    double denom = q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0);
+    if (q->labels) {
+        int64_t n_a = 0, n_b = 0;
+        for (int64_t i = 0; i < h->n; ++i) {
+            n_a += q->labels[i] == q->cross_a ? 1 : 0;
+            n_b += q->labels[i] == q->cross_b ? 1 : 0;
+        }
+        if (n_a < 1 || n_b < 1 || (q->cross_a == q->cross_b && n_a < 2))
+            return fail(STK_EINVAL, "cross K needs points of both labels");
+        const double fa = (double)n_a, fb = (double)n_b;
+        denom = q->cross_a != q->cross_b ? fa * fb
+                                         : (q->norm == STK_NORM_N2 ? fa * fa : fa * (fa - 1.0));
+    }
+    *coef = h->area * (h->box[5] - h->box[4]) / denom;
+    return STK_OK;
+}
+
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
             int* R_out, int f_force) {
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
+    h->last_rows = 0;  // the raw accumulator rows are the new job's from here on
     int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
     if (rc) return rc;
     if (q->edge_mode != STK_EDGE_NONE && q->edge_mode != STK_EDGE_ISOTROPIC &&
@@ -380,6 +405,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                     "intensity and no labels");
     if (q->prec != STK_PREC_FP64 && q->prec != STK_PREC_FP32_GUARDED)
         return fail(STK_EINVAL, "unknown prec %d", q->prec);
+    if (q->shard_count < 0 || q->shard_count > (1 << 16) ||
+        (q->shard_count > 1 && (q->shard_index < 0 || q->shard_index >= q->shard_count)))
+        return fail(STK_EINVAL, "shard_index must be in 0 .. shard_count - 1 (shard_count <= 65536)");
     if (q->norm != STK_NORM_N_NM1 && q->norm != STK_NORM_N2)
         return fail(STK_EINVAL, "unknown norm %d", q->norm);
     if (q->exec != STK_EXEC_BATCHED && q->exec != STK_EXEC_PLAIN)
@@ -538,6 +566,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         (rc = ensure(h->oL, 8 * (size_t)R * nbins, "L grids")) ||
         (rc = ensure(h->oS, 8 * (size_t)R * nbins, "S grids")) ||
         (rc = ensure(h->oC, 8 * (size_t)R * nbins, "C grids")) ||
+        (rc = ensure(h->oA, 32 * (size_t)R * nbins, "raw accumulators")) ||
         (rc = ensure(h->env, 8 * 4 * (size_t)nbins * (size_t)(n_groups > 0 ? n_groups : 1),
                      "envelope")) ||
         (rc = ensure(h->simseed, 8 * (size_t)m_w, "simulation seeds")) ||
@@ -605,16 +634,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     }
     CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
 
-    const double area = h->area;
-    const double dur = h->box[5] - h->box[4];
-    const double nn = (double)n;
-    double denom = q->norm == STK_NORM_N2 ? nn * nn : nn * (nn - 1.0);
-    if (cross) {
-        const double fa = (double)n_a, fb = (double)n_b;
-        denom = q->cross_a != q->cross_b ? fa * fb
-                                         : (q->norm == STK_NORM_N2 ? fa * fa : fa * (fa - 1.0));
-    }
-    const double coef = area * dur / denom;
+    double coef = 0.0;
+    if ((rc = job_coef(h, q, &coef))) return rc;
     const double* d_s = as<double>(h->thr);
     const double* d_tt = as<double>(h->thr) + STK_MAX_THRESHOLDS;
     const bool fp32 = fp32_path(h, q);
@@ -739,6 +760,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         rb.n = n;
         rb.ncells = ncells;
         rb.H = inh ? as<double>(h->Hs) : nullptr;
+        if (obs_here && q->shard_count > 1) {
+            rb.shard_count = q->shard_count;
+            rb.shard_index = q->shard_index;
+        }
         Accum acc;
         acc.cnt = as<unsigned long long>(h->acc_cnt);
         acc.exc_lo = as<unsigned long long>(h->acc_lo);
@@ -767,6 +792,23 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                             dir),
                "FP64 queue");
         }
+        // the wave's raw accumulators into the job's rows [R][4][nbins] (count, excess low and
+        // high halves, whole part)
+        {
+            const size_t w8 = 8 * (size_t)nbins, pitch = 4 * w8;
+            unsigned char* dst = reinterpret_cast<unsigned char*>(h->oA.p) + (size_t)r0 * pitch;
+            const void* src[3] = {h->acc_cnt.p, h->acc_lo.p, h->acc_hi.p};
+            for (int c = 0; c < 3; ++c)
+                CK(cudaMemcpy2DAsync(dst + c * w8, pitch, src[c], w8, w8, (size_t)m,
+                                     cudaMemcpyDeviceToDevice, st),
+                   "accumulator copy");
+            if (inh)
+                CK(cudaMemcpy2DAsync(dst + 3 * w8, pitch, h->acc_whole.p, w8, w8, (size_t)m,
+                                     cudaMemcpyDeviceToDevice, st),
+                   "accumulator copy");
+            else
+                CK(cudaMemset2DAsync(dst + 3 * w8, pitch, 0, w8, (size_t)m, st), "memset");
+        }
         const int64_t row = (int64_t)r0 * nbins;
         CK(launch_finalize(m * nsec, cs, ct, d_s, d_tt, coef, as<int64_t>(h->self_pairs), acc,
                            as<double>(h->oK) + row, as<double>(h->oL) + row,
@@ -790,7 +832,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         };
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
-                              q->sim_method, inh, (int64_t)h->inh_gen, nsec};
+                              q->sim_method, inh, (int64_t)h->inh_gen, nsec, q->shard_count,
+                              q->shard_index};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -802,7 +845,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               h->oS.p, h->oC.p, h->xq_e.p, h->xq_count.p, h->simseed.p,
                               h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
                               (void*)h->ev0, (void*)h->ev1, (void*)st, h->uh.p, h->Hs.p,
-                              h->acc_whole.p, h->inh.p, h->inh_obs.p};
+                              h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p};
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
@@ -887,6 +930,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.grid_refinement = g.fs;
     h->last.grid_refinement_t = g.ft;
     h->last.graph_replays = replays;
+    h->last_rows = R;
+    h->last_nbins = nbins;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     log_job(h, q, nsec);
@@ -960,7 +1005,7 @@ void handle_trim(stk_handle* h) {
                       &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                       &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL,
                       &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh, &h->Hs,
-                      &h->acc_whole};
+                      &h->acc_whole, &h->oA};
     for (DevBuf* b : bufs) free_buf(*b);
 }
 
@@ -1556,6 +1601,142 @@ int stk_sim_points_inhom(const stk_box* box, const double* rho, int nix, int niy
     return STK_OK;
 }
 
+int stk_last_accumulators(stk_handle* h, int row0, int rows, uint64_t* out) {
+    if (!h || !out) return fail(STK_EINVAL, "handle and out must not be NULL");
+    if (h->last_rows < 1) return fail(STK_EINVAL, "no finished job on this handle");
+    if (row0 < 0 || rows < 1 || row0 + rows > h->last_rows)
+        return fail(STK_EINVAL, "rows %d .. %d are outside the last job's %d realizations", row0,
+                    row0 + rows - 1, h->last_rows);
+    const size_t per = 32 * (size_t)h->last_nbins;
+    CK(cudaMemcpyAsync(out, reinterpret_cast<char*>(h->oA.p) + per * (size_t)row0,
+                       per * (size_t)rows, cudaMemcpyDeviceToHost, h->stream),
+       "accumulator copy");
+    CK(cudaStreamSynchronize(h->stream), "accumulator copy");
+    return STK_OK;
+}
+
+int stk_merge_grids(stk_handle* h, const stk_request* q, const uint64_t* acc, int rows, double* K,
+                    double* L, double* raw_sum, int64_t* pair_count) {
+    if (!h || !q || !acc) return fail(STK_EINVAL, "handle, request and acc must not be NULL");
+    if (rows < 1 || rows > (1 << 24)) return fail(STK_EINVAL, "rows out of range");
+    int rc = check_thresholds(h, q->s, q->cs, q->tt, q->ct);
+    if (rc) return rc;
+    if (q->n_sectors < 0 || q->n_sectors > kMaxSectors)
+        return fail(STK_EINVAL, "n_sectors must be in 0..%d", kMaxSectors);
+    if (q->norm != STK_NORM_N_NM1 && q->norm != STK_NORM_N2)
+        return fail(STK_EINVAL, "unknown norm %d", q->norm);
+    const int nsec = q->n_sectors > 1 ? q->n_sectors : 1;
+    const int cs = q->cs, ct = q->ct, nb = cs * ct, nbins = nb * nsec;
+    if (nbins > kMaxThr * kMaxThr)
+        return fail(STK_EINVAL, "n_sectors * cs * ct must be at most %d", kMaxThr * kMaxThr);
+    double coef = 0.0;
+    if ((rc = job_coef(h, q, &coef))) return rc;
+    // device: accumulators [4][rows][nbins], zero self pairs, thresholds, outputs
+    const size_t cells = (size_t)rows * nbins;
+    const size_t acc_b = 32 * cells, out_b = 32 * cells;
+    DevBuf buf;
+    if ((rc = ensure(buf, acc_b + out_b + 8 * (size_t)rows * nsec + 16 * kMaxThr, "merge")))
+        return rc;
+    unsigned char* base = reinterpret_cast<unsigned char*>(buf.p);
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(base);
+    double* oK = reinterpret_cast<double*>(base + acc_b);
+    double* oL = oK + cells;
+    double* oS = oL + cells;
+    int64_t* oC = reinterpret_cast<int64_t*>(oS + cells);
+    int64_t* selfp = oC + cells;
+    double* thr = reinterpret_cast<double*>(selfp + (size_t)rows * nsec);
+    std::vector<double> hthr(2 * kMaxThr, 0.0);
+    for (int i = 0; i < cs; ++i) hthr[(size_t)i] = q->s[i];
+    for (int i = 0; i < ct; ++i) hthr[(size_t)kMaxThr + i] = q->tt[i];
+    cudaStream_t st = h->stream;
+    auto run = [&]() -> cudaError_t {
+        const size_t w8 = 8 * (size_t)nbins;
+        cudaError_t e = cudaSuccess;
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+            e = cudaMemcpy2DAsync(a + (size_t)c * cells, w8, acc + (size_t)c * nbins, 4 * w8, w8,
+                                  (size_t)rows, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(selfp, 0, 8 * (size_t)rows * nsec, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(thr, hthr.data(), 16 * kMaxThr, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        Accum ac;
+        ac.cnt = a;
+        ac.exc_lo = a + cells;
+        ac.exc_hi = a + 2 * cells;
+        ac.stats = nullptr;
+        ac.whole = h->inten.nix > 0 ? a + 3 * cells : nullptr;
+        e = launch_finalize(rows * nsec, cs, ct, thr, thr + kMaxThr, coef, selfp, ac, oK, oL, oS,
+                            oC, st, (double)nsec);
+        double* outs[3] = {K, L, raw_sum};
+        const double* srcs[3] = {oK, oL, oS};
+        for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+            if (outs[c])
+                e = cudaMemcpyAsync(outs[c], srcs[c], 8 * cells, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && pair_count)
+            e = cudaMemcpyAsync(pair_count, oC, 8 * cells, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e;
+    };
+    const cudaError_t e = run();
+    free_buf(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "grid merge");
+    return STK_OK;
+}
+
+int stk_envelope_merge(const double* K_rows, int rows, int cs, int ct, int n_sectors,
+                       const double* s, const double* tt, double* K_lo, double* K_hi,
+                       double* L_lo, double* L_hi) {
+    if (!K_rows || !s || !tt) return fail(STK_EINVAL, "K_rows, s and tt must not be NULL");
+    if (rows < 1 || rows > (1 << 24)) return fail(STK_EINVAL, "rows out of range");
+    if (cs < 1 || cs > kMaxThr || ct < 1 || ct > kMaxThr)
+        return fail(STK_EINVAL, "cs and ct must be in 1..%d", kMaxThr);
+    if (n_sectors < 0 || n_sectors > kMaxSectors)
+        return fail(STK_EINVAL, "n_sectors must be in 0..%d", kMaxSectors);
+    const int nsec = n_sectors > 1 ? n_sectors : 1;
+    const int nbins = nsec * cs * ct;
+    if (nbins > kMaxThr * kMaxThr)
+        return fail(STK_EINVAL, "n_sectors * cs * ct must be at most %d", kMaxThr * kMaxThr);
+    for (int i = 0; i < cs; ++i)
+        if (!isfinite(s[i])) return fail(STK_EINVAL, "spatial thresholds must be finite");
+    for (int i = 0; i < ct; ++i)
+        if (!(isfinite(tt[i]) && tt[i] > 0.0))
+            return fail(STK_EINVAL, "temporal thresholds must be finite and > 0");
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STK_ENODEV, "no CUDA device: %s", cudaGetErrorString(e0));
+    }
+    const size_t in_b = 8 * (size_t)rows * nbins;
+    DevBuf buf;
+    int rc = ensure(buf, in_b + 32 * (size_t)nbins + 16 * kMaxThr, "envelope merge");
+    if (rc) return rc;
+    double* dK = reinterpret_cast<double*>(buf.p);
+    double* out = dK + (size_t)rows * nbins;  // K_lo, K_hi, L_lo, L_hi
+    double* thr = out + 4 * (size_t)nbins;
+    std::vector<double> hthr(2 * kMaxThr, 0.0);
+    for (int i = 0; i < cs; ++i) hthr[(size_t)i] = s[i];
+    for (int i = 0; i < ct; ++i) hthr[(size_t)kMaxThr + i] = tt[i];
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream create");
+    cudaError_t e = cudaMemcpyAsync(dK, K_rows, in_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(thr, hthr.data(), 16 * kMaxThr, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_envelope(rows, nbins, cs, ct, dK, thr, thr + kMaxThr, out, out + nbins,
+                            out + 2 * nbins, out + 3 * nbins, st, (double)nsec);
+    double* dst[4] = {K_lo, K_hi, L_lo, L_hi};
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c)
+        if (dst[c])
+            e = cudaMemcpyAsync(dst[c], out + (size_t)c * nbins, 8 * (size_t)nbins,
+                                cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    free_buf(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "envelope merge");
+    return STK_OK;
+}
+
 int stk_last_stats(const stk_handle* h, stk_stats* out) {
     if (!h || !out) return fail(STK_EINVAL, "handle and out must not be NULL");
     *out = h->last;
@@ -1576,7 +1757,7 @@ void stk_destroy(stk_handle* h) {
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
-                      &h->oC, &h->env, &h->simseed, &h->simid};
+                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA};
     for (DevBuf* b : bufs) free_buf(*b);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_y) cudaFree(h->d_y);

@@ -118,7 +118,25 @@ struct RealBatch {
     // inhomogeneous K: per sorted point h = mean(rho) / rho(cell of the point), [m][n]; null
     // for the homogeneous estimator
     const double* H = nullptr;
+    // sharding of realization 0 of the launch (the observed pattern): its work units
+    // [ubeg, uend) are split into shard_count contiguous ranges of equal size and only range
+    // shard_index is evaluated (every unordered pair belongs to exactly one range)
+    int shard_count = 1;
+    int shard_index = 0;
 };
+
+// Work-unit range [*b, *e) of realization k of a launch: the realization's units, or for
+// realization 0 of a sharded launch its shard's share of them (equal unit counts).
+__host__ __device__ inline void shard_units(const RealBatch& rb, int k, uint32_t* b,
+                                            uint32_t* e) {
+    if (k != 0 || rb.shard_count <= 1) return;
+    const uint64_t u = (uint64_t)(*e - *b);
+    const uint32_t lo = *b + (uint32_t)(u * (uint64_t)rb.shard_index / (uint64_t)rb.shard_count);
+    const uint32_t hi =
+        *b + (uint32_t)(u * (uint64_t)(rb.shard_index + 1) / (uint64_t)rb.shard_count);
+    *b = lo;
+    *e = hi;
+}
 
 // Per-realization accumulators: counts and the fixed-point (2^-32) sum of (w - 1), the latter
 // split into the sums of the low and high 32-bit halves so that both are plain integer

@@ -12,6 +12,8 @@ numpy's PCG64 with the stated seed, so every workload is reproducible.
 """
 from __future__ import annotations
 
+import math
+
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -181,7 +183,7 @@ def serving_stream(count: int, seed: int = 0, n_datasets: int = 12, presets: int
     for d in range(n_datasets):
         n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
         kind = d % 3
-        side = float(np.sqrt(500.0 * n))
+        side = float((500.0 * n) ** 0.5)
         box = (0.0, side, 0.0, side, 0.0, 365.0)
         sub = int(rng.integers(0, 2**31))
         r = np.random.default_rng(sub)
@@ -191,7 +193,7 @@ def serving_stream(count: int, seed: int = 0, n_datasets: int = 12, presets: int
             x, y, t = thomas(n, box, max(1, n // 500), 150.0, 10.0, r)
         else:
             x, y, t = poi_mixture(n, box, max(1, n // 1000), r, sigma_s=150.0, sigma_t_s=10.0)
-        s_max = min(0.25 * side, float(np.sqrt(neighbours * 500.0 * 365.0 / (60.0 * np.pi))))
+        s_max = min(0.25 * side, float((neighbours * 500.0 * 365.0 / (60.0 * math.pi)) ** 0.5))
         mine = []
         for _ in range(presets):
             cs = int(rng.integers(5, 51))
@@ -216,7 +218,7 @@ def star_polygon(nv: int, r_out: float, r_in: float, cx: float, cy: float, seed:
     """A simple star-shaped polygon of nv vertices (alternating outer / inner radius with
     jitter, sorted angles): a stand-in for an irregular administrative outline."""
     rng = np.random.default_rng(seed)
-    th = np.sort(rng.uniform(0.0, 2.0 * np.pi, nv))
+    th = np.sort(rng.uniform(0.0, 2.0 * math.pi, nv))
     rad = np.where(np.arange(nv) % 2 == 0, r_out, r_in) * rng.uniform(0.85, 1.0, nv)
     return cx + rad * np.cos(th), cy + rad * np.sin(th)
 

@@ -127,3 +127,27 @@ def test_null_handles_and_servers_are_rejected(lib):
     assert L.stk_server_unregister(None, 1) == 1
     assert L.stk_run(None, None, None) == 1
     assert "NULL" in stk.stk_last_error()
+
+
+def test_merge_entry_points_reject_bad_arguments_without_a_device(lib):
+    """stk_last_accumulators, stk_merge_grids and stk_envelope_merge check their arguments
+    before touching a device."""
+    import paper_1912_04753_gb300 as stk
+    from paper_1912_04753_gb300 import _lib as L
+
+    P = ctypes.c_void_p
+    buf = (ctypes.c_uint64 * 16)()
+    assert lib.stk_last_accumulators(None, 0, 1, ctypes.cast(buf, P)) == stk.STK_EINVAL
+    s = np.array([1.0, 2.0])
+    q, keep = L._request(s, s)
+    assert lib.stk_merge_grids(None, ctypes.byref(q), ctypes.cast(buf, P), 1, None, None, None,
+                               None) == stk.STK_EINVAL
+    K = np.zeros(4)
+    sp = s.ctypes.data_as(P)
+    # NULL input, no rows, a grid beyond 64 thresholds, sectors x grid beyond 4096 bins,
+    # a non-positive temporal threshold
+    bad = [(None, 1, 2, 2, 0, sp, sp), (K.ctypes.data_as(P), 0, 2, 2, 0, sp, sp),
+           (K.ctypes.data_as(P), 1, 65, 2, 0, sp, sp), (K.ctypes.data_as(P), 1, 64, 64, 2, sp, sp),
+           (K.ctypes.data_as(P), 1, 2, 2, 0, sp, np.array([0.0, 1.0]).ctypes.data_as(P))]
+    for a in bad:
+        assert lib.stk_envelope_merge(*a, None, None, None, None) == stk.STK_EINVAL

@@ -48,3 +48,35 @@ def test_interrupted_job_resumes_exactly(stk, tmp_path, method):
         np.testing.assert_array_equal(got[k], whole[k], err_msg=k)
     for k in ("L_lo", "L_hi"):
         np.testing.assert_allclose(got[k], whole[k], rtol=1e-14, atol=1e-12)
+
+
+def test_resumable_directional_envelope_matches_oracle(stk, tmp_path):
+    """A directional K (4 axial sectors, translation correction) run in chunks and resumed:
+    the envelope and its L (with the sector factor of Eq. 4's directional form) come from the
+    library and match the oracle's envelope at the FP32-guarded bar."""
+    import oracle
+    from paper_1912_04753_gb300 import checkpoint, workloads as wl
+
+    oracle.build()
+    w = wl.config_csr_small(seed=9, n=1200)
+    n_sims, seed = 6, 17
+    kw = dict(n_sectors=4, edge_mode=stk.STK_EDGE_TRANSLATION,
+              prec=stk.STK_PREC_FP32_GUARDED)
+    with stk.Pattern(w.x, w.y, w.t, w.box) as p:
+        d = str(tmp_path / "ckd")
+        assert checkpoint.envelope_resumable(p, w.s, w.tt, n_sims, seed, d, chunk=4,
+                                             max_chunks=1, **kw) is None
+        got = checkpoint.envelope_resumable(p, w.s, w.tt, n_sims, seed, d, chunk=4, **kw)
+        whole = p.run(w.s, w.tt, n_sims=n_sims, seed=seed, **kw)
+    ref = oracle.envelope_of(oracle.SIM_CSR, w.x, w.y, w.t, w.box, w.s, w.tt, n_sims, seed,
+                             edge_mode=2, n_sec=4)
+    s_col = np.asarray(w.s)[None, :, None]
+    for k in ("K_lo", "K_hi"):
+        r = np.abs(got[k] - ref[k]) / np.where(ref[k] == 0, 1.0, np.abs(ref[k]))
+        assert r.max() <= 1e-6, (k, r.max())
+        np.testing.assert_array_equal(got[k], whole[k])
+    for k in ("L_lo", "L_hi"):
+        a, b = got[k] + s_col, ref[k] + s_col  # sqrt(n_sec K / (2 pi t))
+        r = np.abs(a - b) / np.where(b == 0, 1.0, np.abs(b))
+        assert r.max() <= 1e-6, (k, r.max())
+        np.testing.assert_allclose(got[k], whole[k], rtol=1e-14, atol=1e-12)
