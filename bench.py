@@ -172,6 +172,57 @@ def cpu_baseline(w, target_s=15.0, seed=123):
             "seconds": total_t}
 
 
+def host_info():
+    """CPU model and the number of host cores (the CPU baselines' machine)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def cpu_grid_baseline(w, target_s=10.0, seed=321):
+    """Time the oracle's grid restatement (FP64, the same per-pair arithmetic, pairs restricted
+    to adjacent cells of a grid wider than the thresholds) on all host cores, on random
+    centres of the observed pattern against all n points."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n, cores = w.n, os.cpu_count() or 1
+    R = min(256, n)
+    total_pairs, total_t, used = 0, 0.0, 0
+    while total_t < target_s:
+        mask = np.zeros(n, np.uint8)
+        mask[rng.choice(n, R, replace=False)] = 1
+        t0 = time.perf_counter()
+        _, _, q = oracle.pair_hist_grid(w.x, w.y, w.t, w.box, w.s, w.tt, edge_mode=1,
+                                        centre_mask=mask, threads=cores)
+        dt = time.perf_counter() - t0
+        total_pairs += q
+        total_t += dt
+        used += R
+        per = dt / R
+        R = int(max(256, min(n, (target_s - total_t) / max(per, 1e-7))))
+        if target_s - total_t < 0.5:
+            break
+    return {"value": total_pairs / total_t, "unit": UNIT, "cores": cores,
+            "kind": "oracle grid restatement, all host cores",
+            "sample": f"{used} random centres of the observed n={n} pattern x all n points "
+                      f"(grid of cells wider than the thresholds, FP64, {cores} threads, "
+                      f"{total_t:.1f} s; includes the grid build per draw)"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -194,6 +245,7 @@ def run_reference(args):
                        "thresholds": [len(w.s), len(w.tt)]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": steps[-1]["sample"] if steps else ""},
+            "host": host_info(),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -510,6 +562,7 @@ def run_ours(args):
     cb = cpu_baseline(w, target_s=args.cpu_seconds) if args.cpu_seconds > 0 else None
     if cb:
         cb.pop("seconds", None)
+    cbg = cpu_grid_baseline(w, target_s=args.cpu_seconds) if args.cpu_seconds > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -533,6 +586,8 @@ def run_ours(args):
                      "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"},
         "cpu_baseline": cb,
+        "cpu_baseline_grid": cbg,
+        "host": host_info(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -205,8 +205,8 @@ typedef struct {
      * points over Spark workers, Section 4.4).  With shard_count > 1 this call evaluates only
      * shard shard_index (0 .. shard_count - 1) of the observed pattern's pairs: its work units
      * (32 centres of one grid row each, in time-major row order) are split into shard_count
-     * contiguous ranges of equal unit count, and each unordered pair belongs to exactly one
-     * range.  The observed grids returned then hold that shard's share only; the integer
+     * contiguous ranges of whole grid rows with about equal unit counts, and each unordered
+     * pair belongs to exactly one range whatever the order of points inside a cell.  The observed grids returned then hold that shard's share only; the integer
      * accumulators of all shards (stk_last_accumulators) summed element-wise equal the whole
      * pattern's bit for bit, and stk_merge_grids turns the sum into K, L, raw sums and counts.
      * Simulations are not affected (shard them with first_sim / n_sims).  0 or 1: no split. */

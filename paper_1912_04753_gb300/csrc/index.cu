@@ -405,6 +405,8 @@ struct ScatterGrid {
     double x0, y0, t0, x1, y1, t1, cw, ch, cd;
     double inv_qx, inv_qy, inv_qt;
     double qx, qy, qt;
+    double qX, inv_qX;  // the filter's box-frame x quantum
+    int64_t nF;         // floats per realization and axis of the filter arrays
     float tan_rel, tan_abs, fast_abs;
     Polygon poly;
     int mask_all;  // role flags for every realization (indexed by the point's index in it)
@@ -419,7 +421,8 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
                                double* __restrict__ Y, double* __restrict__ T,
                                float4* __restrict__ P, float2* __restrict__ Plo,
                                uint8_t* __restrict__ mask_out,
-                               const double* __restrict__ h_in, double* __restrict__ H) {
+                               const double* __restrict__ h_in, double* __restrict__ H,
+                               float* __restrict__ F) {
     // P holds two float4 per point: (x_hi, y_hi, t_hi, cell x) and (e_x, e_y, e_t, rin2):
     // distances to the nearer x edge, y edge and end of the period, and a bound on d2 below
     // which the circle around the point stays clear of every edge (interior: weight 1)
@@ -445,6 +448,15 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         const double hy = rint(oy * g.inv_qy) * g.qy;
         const double ht = rint(ot * g.inv_qt) * g.qt;
         P[2 * pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
+        // the filter's arrays: -x_hi relative to x0 (exact multiple of qX below 2^24 qX),
+        // -y_hi, -t_hi as above
+        {
+            const double hX = rint(__dsub_rn(xi, g.x0) * g.inv_qX) * g.qX;
+            float* f = F + (int64_t)k * 3 * g.nF + (pos - (int64_t)k * n);
+            f[0] = -(float)hX;
+            f[g.nF] = -(float)hy;
+            f[2 * g.nF] = -(float)ht;
+        }
         float ex = (float)fmin(__dsub_rn(xi, g.x0), __dsub_rn(g.x1, xi));
         float ey = (float)fmin(__dsub_rn(yi, g.y0), __dsub_rn(g.y1, yi));
         const float te = (float)fmin(__dsub_rn(ti, g.t0), __dsub_rn(g.t1, ti));
@@ -619,9 +631,13 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const double* t, const uint32_t* key, const uint32_t* rank,
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
-                           float tan_rel, float tan_abs, float fast_abs, cudaStream_t st,
-                           Polygon poly, bool mask_all, const double* h_in, double* H) {
+                           float tan_rel, float tan_abs, float fast_abs, float* F, int64_t nF,
+                           cudaStream_t st, Polygon poly, bool mask_all, const double* h_in,
+                           double* H) {
     ScatterGrid s;
+    s.qX = g.qX;
+    s.inv_qX = 1.0 / (double)g.qX;
+    s.nF = nF;
     s.poly = poly;
     s.mask_all = mask_all ? 1 : 0;
     s.x1 = g.x1;
@@ -646,7 +662,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
     s.inv_qt = 1.0 / (double)g.qt;
     scatter_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
         m, n, g.ncells, s, x, y, t, key, rank, start_global, mask_in, X, Y, T, P, Plo,
-        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr);
+        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr, F);
     return cudaGetLastError();
 }
 

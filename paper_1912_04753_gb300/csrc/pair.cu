@@ -395,8 +395,9 @@ struct WarpSm {
     float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
     float cen_h[32];    // inhomogeneous K: h of the centres
-    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | dcx << 5 |
-                            // dcy << 8; the extra slot takes the stores of idle lanes
+    int cen_cx[32];     // cell x index of the centres
+    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
+                            // dcy = centre's y cell - neighbour's y cell
     uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
 };
 
@@ -579,7 +580,6 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
         const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
         const int cl = (int)(meta & 31u);
-        const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
         const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
         const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
         const bool vhalf = (meta >> 12) & 1u;
@@ -588,6 +588,8 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
         const float4 cb = ws.cen_b[cl];
         const float4 p = Pk[2 * j];
         const float2 lo = Plok[j];
+        // cells between centre and neighbour along x (at most fs for a counted pair)
+        const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
         // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
         // distance is the same for both orders
         const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
@@ -753,10 +755,10 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                     float wsp = 1.0f;
                     if (!(d2 <= rin[o])) {
                         if (ra < 0.0f) {  // accurate distance from the hi + lo parts
-                            const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
                             const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
                             const float4 p = w.Pk[2 * (size_t)j];
                             const float2 lo = w.Plok[j];
+                            const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
                             const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) +
                                               (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
                             const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) +
@@ -817,12 +819,12 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             if (!(r * 32 + lane < cnt) || full[r]) continue;
             const uint32_t meta = e[r].z, j = e[r].w;
             const int cl = (int)(meta & 31u);
-            const float dcx = (float)((int)((meta >> 5) & 7u) - pc.g.fs);
             const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
             const float4 ca = ws.cen_a[cl];
             const float4 cb = ws.cen_b[cl];
             const float4 qj = w.Pk[2 * (size_t)j];
             const float2 loj = w.Plok[j];
+            const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(qj.w));
             float dx = (fmaf(dcx, pc.g.cwq, ca.x) - qj.x) + (fmaf(dcx, pc.g.cwl, cb.x) - loj.x);
             float dy = (fmaf(dcy, pc.g.chq, ca.y) - qj.y) + (fmaf(dcy, pc.g.chl, cb.y) - loj.y);
             int k = 0;
@@ -1000,7 +1002,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
 
     for (int k = 0; k < m; ++k) {
         uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
-        shard_units(rb, k, &ubeg, &uend);
+        shard_units(rb, unit_off, nrows, k, &ubeg, &uend);
         const int64_t base = (int64_t)k * n;
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         const float4* Pk = rb.P + 2 * base;
@@ -1030,6 +1032,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             ws.cen_a[lane] = make_float4(p.x, p.y, p.z, pe.w);
             ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
             ws.cen_te[lane] = pe.z;
+            ws.cen_cx[lane] = cx;
             if (VAR == kVarInh) ws.cen_h[lane] = (float)w.H[myi];
             const uint32_t fl = w.mk == nullptr ? 3u : (uint32_t)w.mk[myi];
             w.onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
@@ -1043,94 +1046,106 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             w.deep = EDGE && max(0, cxa - fs) >= pc.deep_x[0] && wb <= pc.deep_x[1] &&
                      cy - fs >= pc.deep_y[0] && cy + fs <= pc.deep_y[1] &&
                      ct >= pc.deep_t[0] && ct + ft <= pc.deep_t[1];
+            // the filter's copy of the coordinates (negated hi parts; x relative to the box)
+            const float* NXk = rb.F + (int64_t)k * 3 * rb.nF;
+            const float* NYk = NXk + rb.nF;
+            const float* NTk = NYk + rb.nF;
+            const float xcb = -NXk[myi];  // the centre's x in the box frame
+            const float2 xc2 = make_float2(xcb, xcb);
             __syncwarp();
             uint32_t tail = 0;
-            // rows from the centres' own row onward in key order (t major, y minor)
+            // rows from the centres' own row onward in key order (t major, y minor); the cells
+            // wa .. wb of a row are one contiguous run of points in one coordinate frame (x
+            // relative to the box, y and t relative to the row's cell origin), scanned four
+            // points at a time
             for (int dt = 0; dt <= ft; ++dt) {
                 const int rt = ct + dt;
                 if (rt >= nt) break;
                 const float tc = fmaf((float)(-dt), pc.g.cdq, p.z);
+                const float2 tc2 = make_float2(tc, tc);
                 for (int dy = (dt == 0 ? 0 : -fs); dy <= fs; ++dy) {
                     const int ry = cy + dy;
                     if (ry < 0 || ry >= ny) continue;
                     const bool own = (dt == 0) & (dy == 0);
-                    // in the own row only neighbours after the centre (sorted index > myi);
-                    // cells left of the first centre's cell hold none of them
-                    const int jlo = own ? (int)myi : -1;
+                    // in the own row only neighbours after the centre (sorted index > myi),
+                    // all of them after the unit's first centre
                     const int wa = own ? cxa : max(0, cxa - fs);
-                    const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
                     const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
-                    const uint32_t mrow = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
-                    for (int cxj = wa; cxj <= wb; ++cxj) {
-                        const uint32_t j0 = cs[rowkey + cxj], j1 = cs[rowkey + cxj + 1];
-                        if (j0 == j1) continue;
-                        const int dcx = cx - cxj;
-                        const float xc = fmaf((float)dcx, pc.g.cwq, p.x);
-                        const uint32_t meta =
-                            mrow | ((uint32_t)min(max(dcx + fs, 0), 7) << 5);
-                        const float2 xc2 = make_float2(xc, xc), yc2 = make_float2(yc, yc);
-                        const float2 tc2 = make_float2(tc, tc);
-                        if (valid) n_cand += j1 - j0;
-                        since_flush += 32ull * (j1 - j0);
-                        for (uint32_t j = j0; j < j1; j += 4) {
-                            // four neighbours per step (records are padded by 8)
-                            const float4 q0 = Pk[2 * (size_t)j];
-                            const float4 q1 = Pk[2 * (size_t)j + 2];
-                            const float4 q2 = Pk[2 * (size_t)j + 4];
-                            const float4 q3 = Pk[2 * (size_t)j + 6];
-                            const float2 dxa = __fadd2_rn(xc2, make_float2(-q0.x, -q1.x));
-                            const float2 dxb = __fadd2_rn(xc2, make_float2(-q2.x, -q3.x));
-                            const float2 dya = __fadd2_rn(yc2, make_float2(-q0.y, -q1.y));
-                            const float2 dyb = __fadd2_rn(yc2, make_float2(-q2.y, -q3.y));
-                            const float2 dta = __fadd2_rn(tc2, make_float2(-q0.z, -q1.z));
-                            const float2 dtb = __fadd2_rn(tc2, make_float2(-q2.z, -q3.z));
-                            const float2 d2a = __ffma2_rn(dxa, dxa, __fmul2_rn(dya, dya));
-                            const float2 d2b = __ffma2_rn(dxb, dxb, __fmul2_rn(dyb, dyb));
-                            const bool k0 = (d2a.x <= cut2) & (fabsf(dta.x) <= ucut) & ((int)j > jlo);
-                            const bool k1 = (d2a.y <= cut2) & (fabsf(dta.y) <= ucut) &
-                                            ((int)j + 1 > jlo) & (j + 1 < j1);
-                            const bool k2 = (d2b.x <= cut2) & (fabsf(dtb.x) <= ucut) &
-                                            ((int)j + 2 > jlo) & (j + 2 < j1);
-                            const bool k3 = (d2b.y <= cut2) & (fabsf(dtb.y) <= ucut) &
-                                            ((int)j + 3 > jlo) & (j + 3 < j1);
-                            const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
-                            const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
-                            const uint32_t m2 = __ballot_sync(0xffffffffu, k2);
-                            const uint32_t m3 = __ballot_sync(0xffffffffu, k3);
-                            const uint32_t t1 = tail + (uint32_t)__popc(m0);
-                            const uint32_t t2 = t1 + (uint32_t)__popc(m1);
-                            const uint32_t t3 = t2 + (uint32_t)__popc(m2);
-                            ws.ring[k0 ? tail + __popc(m0 & lt) : (uint32_t)kRing] =
+                    const uint32_t J1 = cs[rowkey + wb + 1];
+                    const uint32_t jstart = own ? wi.c_begin + 1u : cs[rowkey + wa];
+                    if (jstart >= J1) continue;
+                    // first index this lane may pair with; from jfull on no lane's bound binds
+                    const uint32_t jmin = own ? myi + 1u : jstart;
+                    const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
+                    const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
+                    const float2 yc2 = make_float2(yc, yc);
+                    const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
+                    if (valid && J1 > jmin) n_cand += J1 - jmin;
+                    since_flush += 32ull * (J1 - jstart);
+                    for (uint32_t j = jstart & ~3u; j < J1; j += 4) {
+                        // four consecutive neighbours per step, one float4 per axis
+                        const float4 qx = *reinterpret_cast<const float4*>(NXk + j);
+                        const float4 qy = *reinterpret_cast<const float4*>(NYk + j);
+                        const float4 qt = *reinterpret_cast<const float4*>(NTk + j);
+                        const float2 dxa = __fadd2_rn(xc2, make_float2(qx.x, qx.y));
+                        const float2 dxb = __fadd2_rn(xc2, make_float2(qx.z, qx.w));
+                        const float2 dya = __fadd2_rn(yc2, make_float2(qy.x, qy.y));
+                        const float2 dyb = __fadd2_rn(yc2, make_float2(qy.z, qy.w));
+                        const float2 dta = __fadd2_rn(tc2, make_float2(qt.x, qt.y));
+                        const float2 dtb = __fadd2_rn(tc2, make_float2(qt.z, qt.w));
+                        const float2 d2a = __ffma2_rn(dxa, dxa, __fmul2_rn(dya, dya));
+                        const float2 d2b = __ffma2_rn(dxb, dxb, __fmul2_rn(dyb, dyb));
+                        bool k0 = (d2a.x <= cut2) & (fabsf(dta.x) <= ucut);
+                        bool k1 = (d2a.y <= cut2) & (fabsf(dta.y) <= ucut);
+                        bool k2 = (d2b.x <= cut2) & (fabsf(dtb.x) <= ucut);
+                        bool k3 = (d2b.y <= cut2) & (fabsf(dtb.y) <= ucut);
+                        if (j < jfull || j + 4u > J1) {  // the ends of the run
+                            k0 &= (j >= jmin) & (j < J1);
+                            k1 &= (j + 1u >= jmin) & (j + 1u < J1);
+                            k2 &= (j + 2u >= jmin) & (j + 2u < J1);
+                            k3 &= (j + 3u >= jmin) & (j + 3u < J1);
+                        }
+                        const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
+                        const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
+                        const uint32_t m2 = __ballot_sync(0xffffffffu, k2);
+                        const uint32_t m3 = __ballot_sync(0xffffffffu, k3);
+                        const uint32_t t1 = tail + (uint32_t)__popc(m0);
+                        const uint32_t t2 = t1 + (uint32_t)__popc(m1);
+                        const uint32_t t3 = t2 + (uint32_t)__popc(m2);
+                        if (k0)
+                            ws.ring[tail + __popc(m0 & lt)] =
                                 make_uint4(__float_as_uint(d2a.x), __float_as_uint(fabsf(dta.x)),
                                            meta, j);
-                            ws.ring[k1 ? t1 + __popc(m1 & lt) : (uint32_t)kRing] =
+                        if (k1)
+                            ws.ring[t1 + __popc(m1 & lt)] =
                                 make_uint4(__float_as_uint(d2a.y), __float_as_uint(fabsf(dta.y)),
                                            meta, j + 1);
-                            ws.ring[k2 ? t2 + __popc(m2 & lt) : (uint32_t)kRing] =
+                        if (k2)
+                            ws.ring[t2 + __popc(m2 & lt)] =
                                 make_uint4(__float_as_uint(d2b.x), __float_as_uint(fabsf(dtb.x)),
                                            meta, j + 2);
-                            ws.ring[k3 ? t3 + __popc(m3 & lt) : (uint32_t)kRing] =
+                        if (k3)
+                            ws.ring[t3 + __popc(m3 & lt)] =
                                 make_uint4(__float_as_uint(d2b.y), __float_as_uint(fabsf(dtb.y)),
                                            meta, j + 3);
-                            tail = t3 + (uint32_t)__popc(m3);
-                            while (tail >= (uint32_t)kDrain) {
-                                __syncwarp();
-                                drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, kDrain, lane,
-                                                                   lt, w);
-                                __syncwarp();
-                                const uint32_t rest = tail - kDrain;
-                                uint4 v[4];
+                        tail = t3 + (uint32_t)__popc(m3);
+                        while (tail >= (uint32_t)kDrain) {
+                            __syncwarp();
+                            drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, kDrain, lane,
+                                                               lt, w);
+                            __syncwarp();
+                            const uint32_t rest = tail - kDrain;
+                            uint4 v[4];
 #pragma unroll
-                                for (int c = 0; c < 4; ++c)
-                                    if ((uint32_t)(lane + 32 * c) < rest)
-                                        v[c] = ws.ring[kDrain + lane + 32 * c];
-                                __syncwarp();
+                            for (int c = 0; c < 4; ++c)
+                                if ((uint32_t)(lane + 32 * c) < rest)
+                                    v[c] = ws.ring[kDrain + lane + 32 * c];
+                            __syncwarp();
 #pragma unroll
-                                for (int c = 0; c < 4; ++c)
-                                    if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
-                                __syncwarp();
-                                tail = rest;
-                            }
+                            for (int c = 0; c < 4; ++c)
+                                if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
+                            __syncwarp();
+                            tail = rest;
                         }
                     }
                 }
@@ -1291,7 +1306,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
 
     for (int k = 0; k < m; ++k) {
         uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
-        shard_units(rb, k, &ubeg, &uend);
+        shard_units(rb, unit_off, nrows, k, &ubeg, &uend);
         const int64_t base = (int64_t)k * n;
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         const double* X = rb.X + base;

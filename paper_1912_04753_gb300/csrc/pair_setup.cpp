@@ -3,10 +3,11 @@
 // Guard derivation for the FP32 bulk path.  Every point is stored relative to the origin of
 // its own cell as hi + lo, with hi a multiple of the quantum q = 2^-22 * P (P the smallest
 // power of two >= the cell side).  The centre is moved into each neighbour cell's frame
-// (at most fs <= 2 cells away), so it lies in [-2P, 3P]: hi parts stay exact multiples of q
+// (at most fs <= 3 cells away), so it lies in [-3P, 4P]: hi parts stay exact multiples of q
 // below 2^24 q = 4P and the FP32 difference of two hi parts is exact; it differs
 // from the true coordinate difference by at most eps = 2q (+ FP64 rounding of the cell
-// origins, 2^-50 |box|).  From that:
+// origins, 2^-50 |box|).  The filter takes x instead relative to the box (quantum qX, see
+// Grid), so one grid row is one frame; there eps_x = qX.  From that:
 //   d2_hi = fl(fma(dx, dx, fl(dy*dy))) satisfies |d2_hi - d2| <= 2 r (eps_x + eps_y)
 //           + eps_x^2 + eps_y^2 + 2^-22 r^2;
 //   u_hi  = |dt_hi| satisfies |u_hi - u| <= eps_t.
@@ -127,6 +128,7 @@ int build_grid(const double box[6], double s_max, double t_max, int64_t n, int f
     g->cwl = (float)(g->cw - cwq);
     g->chl = (float)(g->ch - chq);
     g->cdl = (float)(g->cd - cdq);
+    g->qX = (float)ldexp(pow2_at_least(W), -24);
     return 0;
 }
 
@@ -191,7 +193,9 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
     pc->nbins = cs * ct;
     pc->edge = edge;
     pc->n = n;
-    const double ex = 2.0 * g.qx + ldexp(fabs(g.x0) + fabs(g.x1), -50);
+    // x: the filter's box-frame hi parts (each within qX / 2 of x - x0, which FP64 gives to
+    // 2^-53 of the box), so a difference of two is within qX of dx
+    const double ex = (double)g.qX + ldexp(fabs(g.x0) + fabs(g.x1), -50);
     const double ey = 2.0 * g.qy + ldexp(fabs(g.y0) + fabs(g.y1), -50);
     const double et = 2.0 * g.qt + ldexp(fabs(g.t0) + fabs(g.t1), -50);
     for (int a = 0; a < cs; ++a) {

@@ -95,6 +95,7 @@ struct stk_handle {
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     DevBuf oA;  // raw accumulators of the last job's realizations, [R][4][nbins]
+    DevBuf F;   // the pair filter's coordinate arrays, [m][3][filter_stride(n)]
     int last_rows = 0, last_nbins = 0;  // shape of oA
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     // pinned staging of the other per-job host inputs (graph-capturable copies)
@@ -216,6 +217,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
     f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
                  8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
+                 4 * 3 * (size_t)filter_stride(n) /* filter arrays */ +
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
@@ -230,7 +232,7 @@ size_t workspace_bytes(const stk_handle* h) {
                             &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                             &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
                             &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh,
-                            &h->Hs, &h->acc_whole, &h->oA};
+                            &h->Hs, &h->acc_whole, &h->oA, &h->F};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     return b;
@@ -551,6 +553,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         (rc = ensure(h->X, 8 * mn, "sorted x")) || (rc = ensure(h->Y, 8 * mn, "sorted y")) ||
         (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 32 * (mn + 8), "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
+        (rc = ensure(h->F, 12 * (size_t)m_w * (size_t)filter_stride(n), "filter arrays")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
         (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
         (rc = ensure(h->chunk_off, 4 * mr, "work offsets")) ||
@@ -724,7 +727,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                                                : nullptr,
                           as<double>(h->X), as<double>(h->Y), as<double>(h->T),
                           as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
-                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs, st, poly,
+                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs,
+                          as<float>(h->F), filter_stride(n), st, poly,
                           cross, inh ? as<double>(h->uh) : nullptr,
                           inh ? as<double>(h->Hs) : nullptr),
            "scatter");
@@ -760,6 +764,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         rb.n = n;
         rb.ncells = ncells;
         rb.H = inh ? as<double>(h->Hs) : nullptr;
+        rb.F = as<float>(h->F);
+        rb.nF = filter_stride(n);
         if (obs_here && q->shard_count > 1) {
             rb.shard_count = q->shard_count;
             rb.shard_index = q->shard_index;
@@ -845,7 +851,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               h->oS.p, h->oC.p, h->xq_e.p, h->xq_count.p, h->simseed.p,
                               h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
                               (void*)h->ev0, (void*)h->ev1, (void*)st, h->uh.p, h->Hs.p,
-                              h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p};
+                              h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p, h->F.p};
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
@@ -1005,7 +1011,7 @@ void handle_trim(stk_handle* h) {
                       &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                       &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL,
                       &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh, &h->Hs,
-                      &h->acc_whole, &h->oA};
+                      &h->acc_whole, &h->oA, &h->F};
     for (DevBuf* b : bufs) free_buf(*b);
 }
 
@@ -1757,7 +1763,7 @@ void stk_destroy(stk_handle* h) {
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
-                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA};
+                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA, &h->F};
     for (DevBuf* b : bufs) free_buf(*b);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_y) cudaFree(h->d_y);

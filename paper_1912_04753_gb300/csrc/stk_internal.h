@@ -8,6 +8,10 @@
 //     (x_lo, y_lo); the point is stored relative to its own cell origin: hi parts are multiples
 //     of a power-of-two quantum, so differences of hi parts are exact in FP32, and hi + lo
 //     carries the offset to ~2^-45 of the cell size;
+//   - the pair filter's copy of the coordinates, structure of arrays per realization,
+//     [3][nF] floats: -x_hi relative to the box's x0 (quantum Grid::qX), -y_hi and -t_hi in the
+//     point's cell frame (the same values as above, negated), so four consecutive points load
+//     as one float4 per axis;
 //   - cell_start[ncells + 1] per realization (offsets into that realization's n points).
 //   - work units: 32 consecutive centres of one (cy, ct) row, in realization order.
 #pragma once
@@ -38,6 +42,10 @@ struct Grid {
     float qx, qy, qt;       // quantum of the FP32 hi parts (2^-22 x a power of two >= side)
     float cwq, chq, cdq;    // cell sides rounded to a multiple of the quantum (exact FP32)
     float cwl, chl, cdl;    // cell side minus its rounded value
+    // quantum of the filter's x coordinates, which are taken relative to the box (x - x0,
+    // rounded to a multiple of qX = 2^-24 x a power of two >= the box width: exact FP32
+    // differences over the whole box, so one grid row is one coordinate frame)
+    float qX;
 };
 
 // Everything the pair kernels need for one job, built on the host (see guard derivation in
@@ -118,22 +126,46 @@ struct RealBatch {
     // inhomogeneous K: per sorted point h = mean(rho) / rho(cell of the point), [m][n]; null
     // for the homogeneous estimator
     const double* H = nullptr;
+    // the filter's coordinate arrays, [m][3][nF] (negated hi parts, see the layout above)
+    const float* F = nullptr;
+    int64_t nF = 0;
     // sharding of realization 0 of the launch (the observed pattern): its work units
-    // [ubeg, uend) are split into shard_count contiguous ranges of equal size and only range
-    // shard_index is evaluated (every unordered pair belongs to exactly one range)
+    // [ubeg, uend) are split at grid-row starts into shard_count contiguous ranges of about
+    // equal size and only range shard_index is evaluated (every unordered pair belongs to
+    // exactly one range, see shard_units)
     int shard_count = 1;
     int shard_index = 0;
 };
 
 // Work-unit range [*b, *e) of realization k of a launch: the realization's units, or for
-// realization 0 of a sharded launch its shard's share of them (equal unit counts).
-__host__ __device__ inline void shard_units(const RealBatch& rb, int k, uint32_t* b,
-                                            uint32_t* e) {
+// realization 0 of a sharded launch its shard's share of them.  Shards are cut only at the first
+// unit of a grid row (the smallest row start at or after an equal split of the unit count), so
+// that every pair a row's units evaluate stays in one shard: which unit of a row owns a pair
+// depends on the order of points inside a cell, which the counting sort does not fix from one
+// run to the next, while pairs across rows always belong to the earlier row.
+// unit_off: the launch's unit offsets [m * nrows + 1] (realization 0 first).
+__device__ inline uint32_t first_row_unit_at_or_after(const uint32_t* unit_off, int64_t nrows,
+                                                      uint32_t target) {
+    int64_t lo = 0, hi = nrows;  // unit_off[nrows] is the realization's end, >= target
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (unit_off[mid] >= target)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return unit_off[lo];
+}
+
+__device__ inline void shard_units(const RealBatch& rb, const uint32_t* unit_off, int64_t nrows,
+                                   int k, uint32_t* b, uint32_t* e) {
     if (k != 0 || rb.shard_count <= 1) return;
     const uint64_t u = (uint64_t)(*e - *b);
-    const uint32_t lo = *b + (uint32_t)(u * (uint64_t)rb.shard_index / (uint64_t)rb.shard_count);
-    const uint32_t hi =
+    const uint32_t tlo = *b + (uint32_t)(u * (uint64_t)rb.shard_index / (uint64_t)rb.shard_count);
+    const uint32_t thi =
         *b + (uint32_t)(u * (uint64_t)(rb.shard_index + 1) / (uint64_t)rb.shard_count);
+    const uint32_t lo = first_row_unit_at_or_after(unit_off, nrows, tlo);
+    const uint32_t hi = first_row_unit_at_or_after(unit_off, nrows, thi);
     *b = lo;
     *e = hi;
 }
@@ -221,8 +253,12 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
-                           cudaStream_t st, Polygon poly = Polygon(), bool mask_all = false,
-                           const double* h_in = nullptr, double* H = nullptr);
+                           float* F, int64_t nF, cudaStream_t st, Polygon poly = Polygon(),
+                           bool mask_all = false, const double* h_in = nullptr,
+                           double* H = nullptr);
+// floats per realization and axis of the filter's coordinate arrays (n plus padding for the
+// last four-point load, a multiple of 4 so that every axis starts 16-byte aligned)
+inline int64_t filter_stride(int64_t n) { return (n + 8 + 3) & ~int64_t(3); }
 cudaError_t launch_cell_starts(int m, int64_t n, int64_t ncells, const uint32_t* start_global,
                                uint32_t* cell_start, cudaStream_t st);
 // units per (realization, row) -> counts[m * nrows] (+ a zero slot for the scan total)

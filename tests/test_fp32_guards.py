@@ -99,3 +99,56 @@ def test_sector_guard_is_sound(n_sec, x0):
                           for k in range(1, n_sec)]))
     frac = np.mean((c2 <= sec_g).any(axis=0) | (np.abs(r2 * np.sin(a2)) <= sec_gd))
     assert frac < 1e-3
+
+
+@pytest.mark.parametrize("x0,W,fs", [(5.0e5, 49_999.37, 2), (0.0, 50_000.0, 2),
+                                     (3.3e6, 123_456.7, 3), (-7.5e4, 8_000.0, 1)])
+def test_filter_distance_within_guard(x0, W, fs):
+    """The pair filter's squared distance (x relative to the box, quantum qX = 2^-24 P_W, P_W
+    the power of two >= the box width; y relative to the neighbour's cell, the centre moved
+    into it; FP32 adds and a fused multiply-add, as the kernel) stays within half the guard
+    band G of the reference FP64 squared distance, so every bin FP32 decides outside the band
+    is the reference bin.  G restates the band of the job set-up: with eps_x = qX and
+    eps_y = 2 q_y (plus 2^-50 of the coordinates), sp = s (1 + 1e-6) + eps_x + eps_y,
+    G = 2 (2 sp (eps_x + eps_y) + eps_x^2 + eps_y^2 + 2^-22 sp^2) + 2^-48 sp^2."""
+    rng = np.random.default_rng(int(W) % 1000 + fs)
+    H = W * 0.8
+    y0 = x0 - 4321.0
+    s_max = min(W, H) / 20
+    ny = int(H // (s_max / fs))
+    ch = H / ny
+    N = 300_000
+    r = s_max * np.sqrt(rng.uniform(0, 1.0, N))
+    near = rng.random(N) < 0.5  # half of the pairs a hair from a threshold
+    thr = s_max * rng.integers(1, 26, N) / 25
+    r = np.where(near, thr + rng.uniform(-1e-3, 1e-3, N), r)
+    ang = rng.uniform(0, 2 * math.pi, N)
+    xi = x0 + rng.uniform(0, W, N)
+    yi = y0 + s_max + rng.uniform(0, H - 2 * s_max, N)
+    xj = np.clip(xi - r * np.cos(ang), x0, x0 + W)
+    yj = yi - r * np.sin(ang)
+    dx, dy = xi - xj, yi - yj
+    d2_ref = dx * dx + dy * dy
+    # filter representation
+    qX = _pow2_at_least(W) * 2.0 ** -24
+    hxi = (np.rint((xi - x0) / qX) * qX).astype(f32)
+    hxj = (np.rint((xj - x0) / qX) * qX).astype(f32)
+    cyi, hyi, _, qy = _rep(yi, y0, ch, ny)
+    cyj, hyj, _, _ = _rep(yj, y0, ch, ny)
+    chq = f32(np.rint(ch / qy) * qy)
+    dcell = (cyi - cyj).astype(f32)
+    keep = np.abs(dcell) <= fs
+    yc = _fma32(-(-dcell), chq, hyi)  # centre moved into the neighbour's row frame
+    dxf = (hxi + (-hxj)).astype(f32)
+    dyf = (yc + (-hyj)).astype(f32)
+    d2f = _fma32(dxf, dxf, (dyf * dyf).astype(f32))
+    ex = qX + 2.0 ** -50 * (abs(x0) + abs(x0 + W))
+    ey = 2 * qy + 2.0 ** -50 * (abs(y0) + abs(y0 + H))
+    s = np.sqrt(np.maximum(d2_ref, 0))
+    sp = s * (1 + 1e-6) + ex + ey
+    G = 2 * (2 * sp * (ex + ey) + ex * ex + ey * ey + 2.0 ** -22 * sp * sp) + 2.0 ** -48 * sp * sp
+    err = np.abs(d2f.astype(np.float64) - d2_ref)[keep]
+    assert keep.sum() > N // 2
+    assert (err <= 0.5 * G[keep]).all(), (err / G[keep]).max()
+    # the x hi parts are exact FP32 multiples of qX over the whole box
+    assert np.array_equal(hxi.astype(np.float64), np.rint((xi - x0) / qX) * qX)
