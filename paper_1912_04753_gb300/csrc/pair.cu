@@ -523,6 +523,56 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
         exact_inline<POLY, VAR>(gpc, rb, entry, hc, he, hf, hw);
 }
 
+// ---------------------------------------------------------------- FP32 isotropic weight
+
+// FP32 square root of v >= 0: the hardware reciprocal square root and one Newton step (within
+// about an ulp of the correctly rounded root); 0 for v = 0.
+__device__ __forceinline__ float sqrt_nr(float v) {
+    const float y = rsqrtf(v + 1e-30f);
+    const float s = v * y;
+    return fmaf(fmaf(-s, s, v), 0.5f * y, s);
+}
+
+// Half-angle alpha = acos(e / r) of the arc that an edge at distance e cuts from the circle of
+// radius r (inv_r = 1 / r), 0 when e >= r.  acos(x) = sqrt(1 - x) P(x), P a degree-7 least-squares
+// fit of acos(x) / sqrt(1 - x) on [0, 1] (fit_arc_poly.py; fit error below 3e-8 relative, FP32
+// evaluation within 3e-7 absolute); 1 - x is formed as (r - e) / r, whose difference is exact
+// when e is near r, so the angle stays accurate up to the tangency band.
+__device__ __forceinline__ float arc_half_angle(float e, float r, float inv_r) {
+    const float x = e * inv_r;
+    const float om = fmaxf((r - e) * inv_r, 0.0f);
+    float p = -0.0012278304202482104f;
+    p = fmaf(p, x, 0.006548574194312096f);
+    p = fmaf(p, x, -0.01692071184515953f);
+    p = fmaf(p, x, 0.030777458101511f);
+    p = fmaf(p, x, -0.05013412609696388f);
+    p = fmaf(p, x, 0.08897225558757782f);
+    p = fmaf(p, x, -0.2145983725786209f);
+    p = fmaf(p, x, 1.570796251296997f);
+    return sqrt_nr(om) * p;
+}
+
+// Share A of the circle of radius r (inv_r = 1 / r) outside the rectangle, for a centre at
+// distances e1 and e2 from its nearer x and y edges (Section 3: the weight is 1 / (1 - A)).
+// The radius is at most half of each side, so at most one x-edge and one y-edge cut the circle;
+// when the corner lies inside it the two cut arcs overlap and the outside part is
+// alpha_1 + alpha_2 + pi / 2 (of 2 pi), else 2 (alpha_1 + alpha_2).
+__device__ __forceinline__ float outside_share(float e1, float e2, float r, float inv_r) {
+    const float a1 = arc_half_angle(e1, r, inv_r);
+    const float a2 = arc_half_angle(e2, r, inv_r);
+    return (fmaf(e1, e1, e2 * e2) < r * r) ? (a1 + a2 + 1.57079632679f) * 0.159154943092f
+                                           : (a1 + a2) * 0.318309886184f;
+}
+
+// r = sqrt(r2) and 1 / r in FP32 from the hardware reciprocal square root with a Newton step
+// each (r2 = 0 gives a NaN r, which the callers' range tests send to FP64).
+__device__ __forceinline__ void radius_nr(float r2, float& r, float& inv_r) {
+    const float y = rsqrtf(r2);
+    const float s = r2 * y;
+    r = fmaf(fmaf(-s, s, r2), 0.5f * y, s);
+    inv_r = y * fmaf(-0.5f * r2 * y, y, 1.5f);
+}
+
 // Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
 // one per lane (crossings with the boundary, poly_weight_fast).  Out of line like the
 // rectangle's version, so that the rectangle path does not carry its registers.
@@ -584,37 +634,33 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
         const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
         const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
+        // the neighbour's records, issued together (the edge record is the same 32-byte
+        // sector as the coordinates; only order (j, i) uses it)
+        const float4 p = Pk[2 * j];
+        const float4 pb = Pk[2 * j + 1];
+        const float2 lo = Plok[j];
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        const float4 p = Pk[2 * j];
-        const float2 lo = Plok[j];
         // cells between centre and neighbour along x (at most fs for a counted pair)
         const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
         // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
         // distance is the same for both orders
         const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
         const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
-        const float ra = sqrtf(fmaf(dxa, dxa, dya * dya));
-        float ex = cb.z, ey = cb.w;
-        if (other) {
-            const float4 pb = Pk[2 * j + 1];
-            ex = pb.x;
-            ey = pb.y;
-        }
+        float ra, inv_r;
+        radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
+        const float ex = other ? pb.x : cb.z, ey = other ? pb.y : cb.w;
         const float e1 = fminf(ex, ey), e2 = fmaxf(ex, ey);
         const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
-        if (ra < pc.r_acc_min || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
+        if (!(ra >= pc.r_acc_min) || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
             exact = true;  // nearly tangent to an edge, or too short to resolve
             const uint32_t ci = c_begin + (uint32_t)cl;
             xe = make_uint4(other ? j : ci, other ? ci : j, real, 1u | ((uint32_t)bin << 2));
         } else {
-            float a1 = 0.0f, a2 = 0.0f;
-            if (e1 < ra) a1 = atan2f(sqrtf((ra - e1) * (ra + e1)), e1);
-            if (e2 < ra) a2 = atan2f(sqrtf((ra - e2) * (ra + e2)), e2);
-            const float A = (fmaf(e1, e1, e2 * e2) < ra * ra)
-                                ? (a1 + a2 + 1.57079632679f) * 0.159154943092f
-                                : (a1 + a2) * 0.318309886184f;
-            const float xs = vhalf ? (1.0f + A) / (1.0f - A) : A / (1.0f - A);
+            // weight 1 / ((1 - A) v) - 1 in 2^-32 units: A / (1 - A), or (1 + A) / (1 - A)
+            // when the temporal weight is 1/2
+            const float A = outside_share(e1, e2, ra, inv_r);
+            const float xs = __fdividef(vhalf ? 1.0f + A : A, 1.0f - A);
             const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
             if (exc) atomicAdd(&he[bin], exc);
         }
@@ -747,7 +793,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                 const float te[2] = {ws.cen_te[cl], pj[r].z};
                 const float rin[2] = {ca.w, pj[r].w};
                 const float ex[2] = {cb.z, pj[r].x}, ey[2] = {cb.w, pj[r].y};
-                float ra = -1.0f;
+                float ra = -1.0f, inv_r = 0.0f;
 #pragma unroll
                 for (int o = 0; o < 2; ++o) {
                     const bool vh = u > te[o] + pc.g_v;
@@ -763,21 +809,15 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                                               (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
                             const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) +
                                               (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
-                            ra = sqrtf(fmaf(dxa, dxa, dya * dya));
+                            radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
                         }
                         const float e1 = fminf(ex[o], ey[o]), e2 = fmaxf(ex[o], ey[o]);
                         const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
-                        if (ra < pc.r_acc_min || fabsf(ra - e1) <= band ||
+                        if (!(ra >= pc.r_acc_min) || fabsf(ra - e1) <= band ||
                             fabsf(ra - e2) <= band) {
                             und = true;
                         } else {
-                            float a1 = 0.0f, a2 = 0.0f;
-                            if (e1 < ra) a1 = atan2f(sqrtf((ra - e1) * (ra + e1)), e1);
-                            if (e2 < ra) a2 = atan2f(sqrtf((ra - e2) * (ra + e2)), e2);
-                            const float A = (fmaf(e1, e1, e2 * e2) < ra * ra)
-                                                ? (a1 + a2 + 1.57079632679f) * 0.159154943092f
-                                                : (a1 + a2) * 0.318309886184f;
-                            wsp = 1.0f / (1.0f - A);
+                            wsp = __fdividef(1.0f, 1.0f - outside_share(e1, e2, ra, inv_r));
                         }
                     }
                     wgt[o] = (vh ? 2.0f : 1.0f) * wsp;
