@@ -176,14 +176,23 @@ def host_info():
     """CPU model and the number of host cores (the CPU baselines' machine)."""
     model = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for ln in f:
-                key = ln.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware") and ":" in ln:
-                    model = ln.split(":", 1)[1].strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name") and ":" in ln:
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
         pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    key = ln.split(":")[0].strip().lower()
+                    if key in ("model name", "cpu model", "hardware", "cpu part") and ":" in ln:
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
     if not model:
         import platform
 

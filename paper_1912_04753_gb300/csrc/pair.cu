@@ -539,7 +539,7 @@ __device__ __forceinline__ float sqrt_nr(float v) {
 // evaluation within 3e-7 absolute); 1 - x is formed as (r - e) / r, whose difference is exact
 // when e is near r, so the angle stays accurate up to the tangency band.
 __device__ __forceinline__ float arc_half_angle(float e, float r, float inv_r) {
-    const float x = e * inv_r;
+    const float x = fminf(e * inv_r, 1.0f);  // an edge beyond the circle: no arc (P stays finite)
     const float om = fmaxf((r - e) * inv_r, 0.0f);
     float p = -0.0012278304202482104f;
     p = fmaf(p, x, 0.006548574194312096f);

@@ -44,7 +44,7 @@ def _sqrt_nr(v):
 
 
 def _arc(e, r, inv_r, c):
-    x = (e * inv_r).astype(f32)
+    x = np.minimum((e * inv_r).astype(f32), f32(1))
     om = np.maximum(((r - e).astype(f32) * inv_r).astype(f32), f32(0))
     p = np.full_like(x, c[7])
     for k in range(6, -1, -1):
@@ -115,3 +115,18 @@ def test_arc_polynomial_error_bound():
     assert math.isclose(float(_arc(np.array([r], f32), np.array([r], f32),
                                    np.array([f32(1) / r], f32), c.astype(f32))[0]), 0.0,
                         abs_tol=1e-6)
+
+
+def test_far_edges_of_tiny_circles_add_no_arc():
+    """An edge far beyond a tiny circle (e / r up to 1e9) cuts no arc: the angle is exactly 0,
+    not a NaN from the polynomial at a huge argument."""
+    sys.path.insert(0, CSRC)
+    import fit_arc_poly
+
+    c = fit_arc_poly.fit().astype(f32)
+    r = np.array([1e-6, 1e-3, 0.5, 2.0], f32)
+    e = np.array([2500.0, 2500.0, 1e4, 2.0], f32)
+    a = _arc(e, r, (f32(1) / r).astype(f32), c)
+    assert np.array_equal(a, np.zeros(4, f32))
+    w = _weight32(np.zeros(4, f32), e, r, c)
+    assert np.all(np.abs(w.astype(np.float64) - 2.0) < 1e-6)  # one edge through the centre
