@@ -386,9 +386,8 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
 
 constexpr int kRing = 192;   // per-warp queue of candidate pairs (linear, compacted on drain)
 constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
-constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders that may need an edge weight:
+constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders needing the spatial weight:
                                   // under 32 left over + up to 4 orders per lane of a pass
-constexpr uint32_t kRowDeep = 1u << 5;  // ring meta: the neighbour's whole row is deep (w = v = 1)
 static_assert(kDrain - 1 + 4 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
@@ -399,8 +398,7 @@ struct WarpSm {
     int cen_cx[32];     // cell x index of the centres
     uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
                             // dcy = centre's y cell - neighbour's y cell
-    uint4 q2[kQ2];      // orders that may need a weight other than 1: (meta | order << 11 |
-                        // bin << 13, neighbour, d2 bits, u bits)
+    uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
 };
 
 struct Smem32 {
@@ -474,7 +472,6 @@ struct WarpCtx {
     uint32_t onA, onB;        // lanes whose centre counts as a centre / as a neighbour
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
-    uint32_t cdeep;           // centres (lanes) whose every counted order has w = v = 1
     const PairConsts* pa;     // shared-memory copy (indexed tables and bands)
     // inhomogeneous K: the weights' fraction high halves and whole parts (`he` holds the low
     // halves), and h and the low parts of the current realization's points
@@ -576,131 +573,96 @@ __device__ __forceinline__ void radius_nr(float r2, float& r, float& inv_r) {
     inv_r = y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
-// Phase C in a polygon study area, for `cnt` (<= 32) queued orders: the temporal weight and the
-// interior test as in the rectangle (phase C below), then the spatial weight in FP64 from the
-// crossings with the boundary (poly_weight_fast), one order per lane.  Out of line like the
+// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
+// one per lane (crossings with the boundary, poly_weight_fast).  Out of line like the
 // rectangle's version, so that the rectangle path does not carry its registers.
 __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const PairConsts* gpc,
                                                 WarpSm* wsp, RealBatch rb, ExactQueue xq,
                                                 int off, int cnt, int lane,
                                                 unsigned long long* he, uint32_t* hc,
-                                                uint32_t* hh, uint32_t real, uint32_t c_begin) {
+                                                uint32_t real, uint32_t c_begin) {
     const PairConsts& pc = *pcs;
     WarpSm& ws = *wsp;
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint4 e = ws.q2[off + lane];
+        const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
-        const float d2 = __uint_as_float(e.z), u = __uint_as_float(e.w);
-        const int cl = (int)(meta & 31u);
         const uint32_t ci = c_begin + (meta & 31u);
         const bool other = (meta >> 11) & 1u;
+        const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
         const uint32_t a = other ? j : ci, b = other ? ci : j;  // centre, neighbour
         const int64_t base = (int64_t)real * rb.n;
-        const float4 pb = rb.P[2 * (base + j) + 1];
-        const float te = other ? pb.z : ws.cen_te[cl];
-        const float rin2 = other ? pb.w : ws.cen_a[cl].w;
-        const bool vh = u > te + pc.g_v;
-        const bool va = (u > te - pc.g_v) & !vh;
-        if (va) {  // temporal weight undecided in FP32: the whole weight in FP64
+        const double xa = rb.X[base + a], ya = rb.Y[base + a];
+        const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
+        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        const double om =
+            poly_weight_fast<false>(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        const double w = om > 0.0 ? 1.0 / (om * (vhalf ? 0.5 : 1.0)) : 0.0;
+        // undecided crossings, and weights above 8 (beyond the shared accumulators' bound),
+        // go to the FP64 queue
+        if (!(om > 0.0) || w > 8.0) {
             exact = true;
             xe = make_uint4(a, b, real, 1u | ((uint32_t)bin << 2));
-        } else if (d2 <= rin2) {  // circle inside the polygon: w = 1, weight 1 / v
-            if (vh) atomicAdd(&hh[bin], 1u);
         } else {
-            const double xa = rb.X[base + a], ya = rb.Y[base + a];
-            const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
-            const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-            const double om =
-                poly_weight_fast<false>(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
-            const double w = om > 0.0 ? 1.0 / (om * (vh ? 0.5 : 1.0)) : 0.0;
-            // undecided crossings, and weights above 8 (beyond the shared accumulators'
-            // bound), go to the FP64 queue
-            if (!(om > 0.0) || w > 8.0) {
-                exact = true;
-                xe = make_uint4(a, b, real, 1u | ((uint32_t)bin << 2));
-            } else {
-                const unsigned long long exc = excess_fixed64(w);
-                if (exc) atomicAdd(&he[bin], exc);
-            }
+            const unsigned long long exc = excess_fixed64(w);
+            if (exc) atomicAdd(&he[bin], exc);
         }
     }
     push_exact<true>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
 }
 
-// Phase C: the edge weights of `cnt` (<= 32) orders of queue 2, one per lane: orders whose
-// centre is not known to be deep.  The temporal weight (1, or 1/2 when the period's end lies
-// within u of the centre; undecided within the guard g_v: the whole weight in FP64), the
-// interior test (circle clear of every edge: spatial weight 1), else the accurate distance from
-// the hi + lo parts and the isotropic weight of the (at most two) cutting edges; circles nearly
-// tangent to an edge go to FP64.  Out of line (it runs once per 32 orders) with scalar
-// arguments, so that neither its registers nor an address-taken copy of the warp state weigh
-// on the filter loop.
+// Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.  Out of line (it
+// runs once per 32 deferred orders) with scalar arguments, so that neither its registers nor
+// an address-taken copy of the warp state weigh on the filter loop.
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
                                            WarpSm* wsp, const float4* __restrict__ Pk,
                                            const float2* __restrict__ Plok, RealBatch rb,
                                            ExactQueue xq, int off, int cnt, int lane,
-                                           unsigned long long* he, uint32_t* hc, uint32_t* hh,
+                                           unsigned long long* he, uint32_t* hc,
                                            uint32_t real, uint32_t c_begin) {
     const PairConsts& pc = *pcs;
     WarpSm& ws = *wsp;
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint4 e = ws.q2[off + lane];
+        const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
-        const float d2 = __uint_as_float(e.z), u = __uint_as_float(e.w);
         const int cl = (int)(meta & 31u);
         const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
         const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
+        const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
         // the neighbour's records, issued together (the edge record is the same 32-byte
-        // sector as the coordinates)
+        // sector as the coordinates; only order (j, i) uses it)
         const float4 p = Pk[2 * j];
         const float4 pb = Pk[2 * j + 1];
         const float2 lo = Plok[j];
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        // the order's centre: distance to the nearer end of the period, interior bound on d2,
-        // distances to the nearer x and y edges
-        const float te = other ? pb.z : ws.cen_te[cl];
-        const float rin2 = other ? pb.w : ca.w;
+        // cells between centre and neighbour along x (at most fs for a counted pair)
+        const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
+        // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
+        // distance is the same for both orders
+        const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+        float ra, inv_r;
+        radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
         const float ex = other ? pb.x : cb.z, ey = other ? pb.y : cb.w;
-        const bool vh = u > te + pc.g_v;
-        const bool va = (u > te - pc.g_v) & !vh;
-        const uint32_t ci = c_begin + (uint32_t)cl;
-        if (va) {  // temporal weight undecided in FP32: the whole weight in FP64
-            exact = true;
+        const float e1 = fminf(ex, ey), e2 = fmaxf(ex, ey);
+        const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
+        if (!(ra >= pc.r_acc_min) || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
+            exact = true;  // nearly tangent to an edge, or too short to resolve
+            const uint32_t ci = c_begin + (uint32_t)cl;
             xe = make_uint4(other ? j : ci, other ? ci : j, real, 1u | ((uint32_t)bin << 2));
-        } else if (d2 <= rin2) {  // circle clear of every edge: weight 1 / v
-            if (vh) atomicAdd(&hh[bin], 1u);
         } else {
-            // cells between centre and neighbour along x (at most fs for a counted pair);
-            // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
-            // distance is the same for both orders
-            const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
-            const float dxa =
-                (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
-            const float dya =
-                (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
-            float ra, inv_r;
-            radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
-            const float e1 = fminf(ex, ey), e2 = fmaxf(ex, ey);
-            const float band = fmaf(pc.tan_rel, ra, pc.tan_abs);
-            if (!(ra >= pc.r_acc_min) || fabsf(ra - e1) <= band || fabsf(ra - e2) <= band) {
-                exact = true;  // nearly tangent to an edge, or too short to resolve
-                xe = make_uint4(other ? j : ci, other ? ci : j, real, 1u | ((uint32_t)bin << 2));
-            } else {
-                // weight 1 / ((1 - A) v) - 1 in 2^-32 units: A / (1 - A), or (1 + A) / (1 - A)
-                // when the temporal weight is 1/2
-                const float A = outside_share(e1, e2, ra, inv_r);
-                const float xs = __fdividef(vh ? 1.0f + A : A, 1.0f - A);
-                const unsigned long long exc =
-                    xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
-                if (exc) atomicAdd(&he[bin], exc);
-            }
+            // weight 1 / ((1 - A) v) - 1 in 2^-32 units: A / (1 - A), or (1 + A) / (1 - A)
+            // when the temporal weight is 1/2
+            const float A = outside_share(e1, e2, ra, inv_r);
+            const float xs = __fdividef(vhalf ? 1.0f + A : A, 1.0f - A);
+            const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
+            if (exc) atomicAdd(&he[bin], exc);
         }
     }
     push_exact<false>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
@@ -716,15 +678,15 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
     __syncwarp();
     while (w.q2n - off >= 32) {
         if (POLY)
-            drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.hh, w.real,
+            drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
             drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, off, 32,
-                          lane, w.he, w.hc, w.hh, w.real, w.c_begin);
+                          lane, w.he, w.hc, w.real, w.c_begin);
         off += 32;
     }
     const int rest = w.q2n - off;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    uint2 v = make_uint2(0u, 0u);
     if (lane < rest) v = ws.q2[off + lane];
     __syncwarp();
     if (lane < rest) ws.q2[lane] = v;
@@ -756,12 +718,12 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
     e[1] = ws.ring[32 + lane];
     if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
     float4 pj[2];
-    if (edge && VAR == kVarInh) {  // neighbour's edge record (the weights are taken here)
+    if (edge) {  // neighbour's edge record: same 32-byte sector the filter just read
         pj[0] = w.Pk[2 * (size_t)(lane < cnt ? e[0].w : 0u) + 1];
         pj[1] = w.Pk[2 * (size_t)(32 + lane < cnt ? e[1].w : 0u) + 1];
     }
     bool rare = false;
-    bool full[2], di[2], dj[2], aj[2], ai[2];
+    bool full[2], di[2], dj[2], wi[2], wj[2], vi[2], vj[2], aj[2], ai[2];
     int bin[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -790,15 +752,25 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         full[r] = has & am;
         if (VAR == kVarPlain)
             atomicAdd(&w.hc[bin[r]], counted ? (uint32_t)act_i + (uint32_t)act_j : 0u);
-        di[r] = dj[r] = false;
+        di[r] = dj[r] = wi[r] = wj[r] = false;
         if (edge && VAR == kVarPlain) {
-            // counted orders whose centre may have a weight other than 1 go to queue 2, which
-            // takes every edge decision: order (i, j) unless centre i is deep, order (j, i)
-            // unless j's whole row is
-            di[r] = counted & act_i & !((w.cdeep >> cl) & 1u);
-            dj[r] = counted & act_j & !(e[r].z & kRowDeep);
+            const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
+            const float te_j = pj[r].z, rin_j = pj[r].w;
+            const bool vhi = u > te_i + pc.g_v, vhj = u > te_j + pc.g_v;
+            const bool vai = (u > te_i - pc.g_v) & !vhi, vaj = (u > te_j - pc.g_v) & !vhj;
+            const bool ini = d2 <= rin_i, inj = d2 <= rin_j;
+            const bool ci = counted & act_i, cj = counted & act_j;
+            const uint32_t half = (uint32_t)(ci & vhi & !vai & ini) + (uint32_t)(cj & vhj & !vaj & inj);
+            if (half) atomicAdd(&w.hh[bin[r]], half);
+            wi[r] = ci & vai;         // temporal weight undecided: FP64 weight of order (i, j)
+            wj[r] = cj & vaj;
+            di[r] = ci & !vai & !ini;  // spatial weight needed
+            dj[r] = cj & !vaj & !inj;
+
+            vi[r] = vhi;
+            vj[r] = vhj;
         }
-        rare |= full[r] | di[r] | dj[r];
+        rare |= full[r] | wi[r] | wj[r] | di[r] | dj[r];
     }
     if (VAR == kVarInh) {
         // h_i h_j times the weights of both orders, in FP32 (a few ulp); the temporal weight
@@ -940,18 +912,27 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         return;
     }
     if (!__any_sync(0xffffffffu, rare)) return;
-    // pairs whose bin FP32 cannot decide: rare enough that one vote usually skips them all
-    if (__any_sync(0xffffffffu, full[0] | full[1])) {
+    // FP64 entries: rare enough that one vote usually skips them all
+    const bool xflag = full[0] | full[1] | wi[0] | wj[0] | wi[1] | wj[1];
+    if (__any_sync(0xffffffffu, xflag)) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
+            if (edge) {
+                push_exact<POLY>(gpc, rb, xq, wi[r],
+                           make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
+                           w.hc, w.he);
+                push_exact<POLY>(gpc, rb, xq, wj[r],
+                           make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
+                           w.hc, w.he);
+            }
             push_exact<POLY>(gpc, rb, xq, full[r],
                        make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
                        lane, lt, w.hc, w.he);
         }
     }
     if (edge) {
-        // edge weights: up to four orders per lane join queue 2 in one compaction
+        // spatial weights: up to four orders per lane join queue 2 in one compaction
         const uint32_t b0 = __ballot_sync(0xffffffffu, di[0]);
         const uint32_t b1 = __ballot_sync(0xffffffffu, dj[0]);
         const uint32_t b2 = __ballot_sync(0xffffffffu, di[1]);
@@ -961,12 +942,14 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                       o3 = o2 + __popc(b2);
             const uint32_t m0 = e[0].z | ((uint32_t)bin[0] << 13);
             const uint32_t m1 = e[1].z | ((uint32_t)bin[1] << 13);
-            if (di[0]) ws.q2[o0 + __popc(b0 & lt)] = make_uint4(m0, e[0].w, e[0].x, e[0].y);
+            if (di[0]) ws.q2[o0 + __popc(b0 & lt)] = make_uint2(m0 | ((uint32_t)vi[0] << 12), e[0].w);
             if (dj[0])
-                ws.q2[o1 + __popc(b1 & lt)] = make_uint4(m0 | (1u << 11), e[0].w, e[0].x, e[0].y);
-            if (di[1]) ws.q2[o2 + __popc(b2 & lt)] = make_uint4(m1, e[1].w, e[1].x, e[1].y);
+                ws.q2[o1 + __popc(b1 & lt)] =
+                    make_uint2(m0 | (1u << 11) | ((uint32_t)vj[0] << 12), e[0].w);
+            if (di[1]) ws.q2[o2 + __popc(b2 & lt)] = make_uint2(m1 | ((uint32_t)vi[1] << 12), e[1].w);
             if (dj[1])
-                ws.q2[o3 + __popc(b3 & lt)] = make_uint4(m1 | (1u << 11), e[1].w, e[1].x, e[1].y);
+                ws.q2[o3 + __popc(b3 & lt)] =
+                    make_uint2(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w);
             w.q2n = o3 + __popc(b3);
             if (w.q2n >= 32) flush_weights<POLY>(ws, pc, gpc, rb, xq, lane, w);
         }
@@ -991,11 +974,11 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
     if (w.q2n > 0) {
         if (POLY)
-            drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.hh, w.real,
+            drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
             drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 0,
-                          w.q2n, lane, w.he, w.hc, w.hh, w.real, w.c_begin);
+                          w.q2n, lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
@@ -1103,10 +1086,6 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             w.deep = EDGE && max(0, cxa - fs) >= pc.deep_x[0] && wb <= pc.deep_x[1] &&
                      cy - fs >= pc.deep_y[0] && cy + fs <= pc.deep_y[1] &&
                      ct >= pc.deep_t[0] && ct + ft <= pc.deep_t[1];
-            // deep centres: every pair the filter passes (u <= u_cut, d2 <= s2_cut) has v = 1
-            // beyond the temporal guard (margin 2 g_v) and lies inside the interior bound
-            w.cdeep = __ballot_sync(0xffffffffu, valid && pe.z >= pc.u_cut + 2.0f * pc.g_v &&
-                                                     pe.w >= pc.s2_cut);
             // the filter's copy of the coordinates (negated hi parts; x relative to the box)
             const float* NXk = rb.F + (int64_t)k * 3 * rb.nF;
             const float* NYk = NXk + rb.nF;
@@ -1140,13 +1119,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                     const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
                     const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
                     const float2 yc2 = make_float2(yc, yc);
-                    // every neighbour of a deep row has w = v = 1 as a centre (cells at least
-                    // s_max from each spatial edge and t_max from both ends of the period)
-                    const bool row_deep = EDGE && wa >= pc.deep_x[0] && wb <= pc.deep_x[1] &&
-                                          ry >= pc.deep_y[0] && ry <= pc.deep_y[1] &&
-                                          rt >= pc.deep_t[0] && rt <= pc.deep_t[1];
-                    const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8) |
-                                          (row_deep ? kRowDeep : 0u);
+                    const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
                     if (valid && J1 > jmin) n_cand += J1 - jmin;
                     since_flush += 32ull * (J1 - jstart);
                     for (uint32_t j = jstart & ~3u; j < J1; j += 4) {
