@@ -423,9 +423,12 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
                                uint8_t* __restrict__ mask_out,
                                const double* __restrict__ h_in, double* __restrict__ H,
                                float* __restrict__ F) {
-    // P holds two float4 per point: (x_hi, y_hi, t_hi, cell x) and (e_x, e_y, e_t, rin2):
-    // distances to the nearer x edge, y edge and end of the period, and a bound on d2 below
-    // which the circle around the point stays clear of every edge (interior: weight 1)
+    // P holds two float4 per point, the coordinate record (x_hi, y_hi, t_hi, cell x) in the
+    // first half of the realization's [2n] and the edge record (e_x, e_y, e_t, rin2) in the
+    // second: distances to the nearer x edge, y edge and end of the period, and a bound on d2
+    // below which the circle around the point stays clear of every edge (interior: weight 1).
+    // Plo holds (x - x0 - X_hi, y_lo): x's remainder below the filter's box-frame hi part
+    // X_hi, and y's below its cell-frame hi part.
     const int64_t total = n * (int64_t)m;
     for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
          gi += (int64_t)gridDim.x * blockDim.x) {
@@ -447,12 +450,17 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         const double hx = rint(ox * g.inv_qx) * g.qx;
         const double hy = rint(oy * g.inv_qy) * g.qy;
         const double ht = rint(ot * g.inv_qt) * g.qt;
-        P[2 * pos] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
+        // realization k's records: [k][2n] float4, the coordinate records first, then the
+        // edge records
+        const int64_t local = pos - (int64_t)k * n;
+        float4* Pr = P + 2 * (int64_t)k * n;
+        Pr[local] = make_float4((float)hx, (float)hy, (float)ht, __int_as_float(cx));
         // the filter's arrays: -x_hi relative to x0 (exact multiple of qX below 2^24 qX),
-        // -y_hi, -t_hi as above
+        // -y_hi, -t_hi as above; x's low part is taken relative to x0 too
+        const double oX = __dsub_rn(xi, g.x0);
+        const double hX = rint(oX * g.inv_qX) * g.qX;
         {
-            const double hX = rint(__dsub_rn(xi, g.x0) * g.inv_qX) * g.qX;
-            float* f = F + (int64_t)k * 3 * g.nF + (pos - (int64_t)k * n);
+            float* f = F + (int64_t)k * 3 * g.nF + local;
             f[0] = -(float)hX;
             f[g.nF] = -(float)hy;
             f[2 * g.nF] = -(float)ht;
@@ -469,8 +477,8 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         }
         float rin = em * (1.0f - g.tan_rel) - g.tan_abs - g.fast_abs - em * 4.76837158e-7f;
         rin = fmaxf(rin, 0.0f);
-        P[2 * pos + 1] = make_float4(ex, ey, te, rin * rin * 0.99999f);
-        Plo[pos] = make_float2((float)(ox - hx), (float)(oy - hy));
+        Pr[n + local] = make_float4(ex, ey, te, rin * rin * 0.99999f);
+        Plo[pos] = make_float2((float)(oX - hX), (float)(oy - hy));
         if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)k * n];
         if (H) H[pos] = h_in[gi];
     }

@@ -391,11 +391,10 @@ constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders needing the spatia
 static_assert(kDrain - 1 + 4 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
-    float4 cen_a[32];   // x_hi, y_hi, t_hi (own cell frame), interior bound on d2
-    float4 cen_b[32];   // x_lo, y_lo, e_x, e_y
+    float4 cen_a[32];   // x_hi (box frame), y_hi, t_hi (own cell frame), interior bound on d2
+    float4 cen_b[32];   // x_lo (box frame), y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
     float cen_h[32];    // inhomogeneous K: h of the centres
-    int cen_cx[32];     // cell x index of the centres
     uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
                             // dcy = centre's y cell - neighbour's y cell
     uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
@@ -465,7 +464,10 @@ struct WarpCtx {
     uint32_t* hc;             // this warp's histogram replica: counts
     uint32_t* hh;             //   orders whose weight is exactly 2 (excess 1)
     unsigned long long* he;   //   other excess, 2^-32 units
-    const float4* Pk;         // point records of the current realization
+    const float4* Pk;         // coordinate records of the current realization
+    const float4* Ek;         // edge records of the current realization
+    const float* NX;          // the filter's x and y arrays (negated hi parts)
+    const float* NY;
     const uint8_t* mk;        // centre mask of the current realization, or null
     uint32_t real;
     uint32_t c_begin;
@@ -617,7 +619,9 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
 // runs once per 32 deferred orders) with scalar arguments, so that neither its registers nor
 // an address-taken copy of the warp state weigh on the filter loop.
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
-                                           WarpSm* wsp, const float4* __restrict__ Pk,
+                                           WarpSm* wsp, const float4* __restrict__ Ek,
+                                           const float* __restrict__ NXk,
+                                           const float* __restrict__ NYk,
                                            const float2* __restrict__ Plok, RealBatch rb,
                                            ExactQueue xq, int off, int cnt, int lane,
                                            unsigned long long* he, uint32_t* hc,
@@ -634,19 +638,18 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
         const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
         const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
-        // the neighbour's records, issued together (the edge record is the same 32-byte
-        // sector as the coordinates; only order (j, i) uses it)
-        const float4 p = Pk[2 * j];
-        const float4 pb = Pk[2 * j + 1];
+        // the neighbour's hi parts (the filter's arrays, negated: recently read), low parts and
+        // edge record (only order (j, i) uses it), issued together
+        const float nxj = NXk[j], nyj = NYk[j];
         const float2 lo = Plok[j];
+        const float4 pb = Ek[j];
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        // cells between centre and neighbour along x (at most fs for a counted pair)
-        const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
-        // centre i in j's cell frame: hi part exact, lo part carries the remainder; the
-        // distance is the same for both orders
-        const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) + (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
-        const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+        // x: box-frame hi parts (exact difference) plus low parts; y: centre i moved into j's
+        // cell frame, hi part exact, lo part carrying the remainder.  The distance is the same
+        // for both orders.
+        const float dxa = (ca.x + nxj) + (cb.x - lo.x);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
         float ra, inv_r;
         radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
         const float ex = other ? pb.x : cb.z, ey = other ? pb.y : cb.w;
@@ -681,7 +684,7 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
             drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, off, 32,
+            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
         off += 32;
     }
@@ -718,9 +721,9 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
     e[1] = ws.ring[32 + lane];
     if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
     float4 pj[2];
-    if (edge) {  // neighbour's edge record: same 32-byte sector the filter just read
-        pj[0] = w.Pk[2 * (size_t)(lane < cnt ? e[0].w : 0u) + 1];
-        pj[1] = w.Pk[2 * (size_t)(32 + lane < cnt ? e[1].w : 0u) + 1];
+    if (edge) {  // neighbour's edge record (dense array: 16 bytes per point)
+        pj[0] = w.Ek[lane < cnt ? e[0].w : 0u];
+        pj[1] = w.Ek[32 + lane < cnt ? e[1].w : 0u];
     }
     bool rare = false;
     bool full[2], di[2], dj[2], wi[2], wj[2], vi[2], vj[2], aj[2], ai[2];
@@ -802,12 +805,9 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                     if (!(d2 <= rin[o])) {
                         if (ra < 0.0f) {  // accurate distance from the hi + lo parts
                             const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
-                            const float4 p = w.Pk[2 * (size_t)j];
                             const float2 lo = w.Plok[j];
-                            const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(p.w));
-                            const float dxa = (fmaf(dcx, pc.g.cwq, ca.x) - p.x) +
-                                              (fmaf(dcx, pc.g.cwl, cb.x) - lo.x);
-                            const float dya = (fmaf(dcy, pc.g.chq, ca.y) - p.y) +
+                            const float dxa = (ca.x + w.NX[j]) + (cb.x - lo.x);
+                            const float dya = (fmaf(dcy, pc.g.chq, ca.y) + w.NY[j]) +
                                               (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
                             radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
                         }
@@ -862,11 +862,9 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
             const float4 ca = ws.cen_a[cl];
             const float4 cb = ws.cen_b[cl];
-            const float4 qj = w.Pk[2 * (size_t)j];
             const float2 loj = w.Plok[j];
-            const float dcx = (float)(ws.cen_cx[cl] - __float_as_int(qj.w));
-            float dx = (fmaf(dcx, pc.g.cwq, ca.x) - qj.x) + (fmaf(dcx, pc.g.cwl, cb.x) - loj.x);
-            float dy = (fmaf(dcy, pc.g.chq, ca.y) - qj.y) + (fmaf(dcy, pc.g.chl, cb.y) - loj.y);
+            float dx = (ca.x + w.NX[j]) + (cb.x - loj.x);
+            float dy = (fmaf(dcy, pc.g.chq, ca.y) + w.NY[j]) + (fmaf(dcy, pc.g.chl, cb.y) - loj.y);
             int k = 0;
             bool und = false;
             if (pc.nsec > 1) {
@@ -977,7 +975,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
             drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Pk, rb.Plo + (int64_t)w.real * rb.n, rb, xq, 0,
+            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
@@ -1047,6 +1045,9 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
         const float4* Pk = rb.P + 2 * base;
         w.Pk = Pk;
+        w.Ek = Pk + n;
+        w.NX = rb.F + (int64_t)k * 3 * rb.nF;
+        w.NY = w.NX + rb.nF;
         w.real = (uint32_t)k;
         w.Plok = rb.Plo + base;
         if (VAR == kVarInh) w.H = rb.H + base;
@@ -1065,14 +1066,14 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             // centres: one per lane
             const bool valid = lane < (int)wi.c_count;
             const uint32_t myi = wi.c_begin + (valid ? lane : 0);
-            const float4 p = Pk[2 * (size_t)myi];
-            const float4 pe = Pk[2 * (size_t)myi + 1];
+            const float4 p = Pk[myi];
+            const float4 pe = w.Ek[myi];
             const float2 plo = rb.Plo[base + myi];
             const int cx = __float_as_int(p.w);
-            ws.cen_a[lane] = make_float4(p.x, p.y, p.z, pe.w);
+            // x: the box-frame hi part (with plo.x its remainder); y, t: the cell frame
+            ws.cen_a[lane] = make_float4(-w.NX[myi], p.y, p.z, pe.w);
             ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
             ws.cen_te[lane] = pe.z;
-            ws.cen_cx[lane] = cx;
             if (VAR == kVarInh) ws.cen_h[lane] = (float)w.H[myi];
             const uint32_t fl = w.mk == nullptr ? 3u : (uint32_t)w.mk[myi];
             w.onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
@@ -1370,7 +1371,7 @@ pair_fp64_kernel(const PairConsts* __restrict__ gpc, int m, RealBatch rb,
             ws.cy[lane] = yi;
             ws.ct[lane] = ti;
             if (INH) ws.ch[lane] = H[ci];
-            const int cx = __float_as_int(rb.P[2 * (base + ci)].w);
+            const int cx = __float_as_int(rb.P[2 * base + ci].w);
             const uint32_t fl = mk == nullptr ? 3u : (uint32_t)mk[ci];
             const uint32_t onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
             const uint32_t onB = __ballot_sync(0xffffffffu, valid && (fl & 2u));

@@ -284,8 +284,10 @@ void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const 
         pc->top_t = round_down((double)ct - (double)pc->tol_t);
     }
 
-    // weights: accurate hi + lo differences are within acc of the truth (absolute part)
-    const double acc_x = ldexp((double)g.qx, -22) + ldexp(fabs(g.x0) + fabs(g.x1), -50);
+    // weights: accurate hi + lo differences are within acc of the truth (absolute part); x's
+    // hi part is the filter's box-frame one (quantum qX), its low part below qX / 2 rounded to
+    // FP32 (2^-25 qX each)
+    const double acc_x = ldexp((double)g.qX, -24) + ldexp(fabs(g.x0) + fabs(g.x1), -50);
     const double acc_y = ldexp((double)g.qy, -22) + ldexp(fabs(g.y0) + fabs(g.y1), -50);
     pc->tan_rel = 1e-3f;
     pc->tan_abs = round_up(4.0 * (acc_x + acc_y));

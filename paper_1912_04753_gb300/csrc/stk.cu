@@ -481,7 +481,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->h_pc->th = h->box[3] - h->box[2];
     h->h_pc->td = h->box[5] - h->box[4];
     // FP32 directional kernel: boundaries and sides rounded to FP32.  Its offset is the exact
-    // hi-part difference plus the low parts: within 2^-24 |d| + 3 2^-24 q of the offset the
+    // hi-part difference plus the low parts (x relative to the box with quantum qX, y relative
+    // to the cell with quantum q_y; q the larger): within 2^-24 |d| + 3 2^-24 q of the offset the
     // points' FP64 coordinates give, which is itself within half an ulp of the largest
     // coordinate of the FP64 offset.  With the boundaries' rounding (2^-24 per component) and
     // the FP32 cross product's (2^-24 of each product), |cross_FP32 - cross_FP64| stays below
@@ -495,7 +496,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->h_pc->thf = (float)h->h_pc->th;
     h->h_pc->tdf = (float)h->h_pc->td;
     {
-        const double qm = std::max((double)g.qx, (double)g.qy);
+        const double qm = std::max((double)g.qX, (double)g.qy);  // x: the box-frame quantum
         const double big = std::max(std::max(fabs(h->box[0]), fabs(h->box[1])),
                                     std::max(fabs(h->box[2]), fabs(h->box[3])));
         h->h_pc->sec_g = (float)(1.0e-6 * q->s[cs - 1] + 1.0e-6 * qm + 4.0e-16 * big + 1e-30);

@@ -3,11 +3,13 @@
 // Data layout in HBM (one "realization" = the observed pattern or one CSR simulation):
 //   - points sorted by grid cell (cell key = (ct*ny + cy)*nx + cx, x fastest), so the cells of
 //     one (cy, ct) row are one contiguous run;
-//   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps; two float4,
-//     (x_hi, y_hi, t_hi, cell x index) and (e_x, e_y, e_t, interior bound on d2), and a float2
-//     (x_lo, y_lo); the point is stored relative to its own cell origin: hi parts are multiples
-//     of a power-of-two quantum, so differences of hi parts are exact in FP32, and hi + lo
-//     carries the offset to ~2^-45 of the cell size;
+//   - per sorted point: FP64 x, y, t (SoA) for the exact FP64 steps; per realization [2n] float4:
+//     the coordinate records (x_hi, y_hi, t_hi, cell x index) of all n points, then their edge
+//     records (e_x, e_y, e_t, interior bound on d2), kept apart so that the edge records the
+//     weight decisions read are dense; and a float2 (x_lo, y_lo): the coordinates are relative
+//     to the point's own cell origin, hi parts multiples of a power-of-two quantum, so
+//     differences of hi parts are exact in FP32, and hi + lo carries the offset to ~2^-45 of
+//     the cell size -- except x_lo, which completes the filter's box-frame x hi part below;
 //   - the pair filter's copy of the coordinates, structure of arrays per realization,
 //     [3][nF] floats: -x_hi relative to the box's x0 (quantum Grid::qX), -y_hi and -t_hi in the
 //     point's cell frame (the same values as above, negated), so four consecutive points load
@@ -110,7 +112,7 @@ struct WorkItem {
 
 // Pointers to a batch of realizations laid out back to back ([m][n] and [m][ncells + 1]).
 struct RealBatch {
-    const float4* P;        // [2 * (realization * n + i)] and [... + 1], see above
+    const float4* P;        // [realization][2n]: coordinate records, then edge records
     const float2* Plo;
     const double* X;
     const double* Y;

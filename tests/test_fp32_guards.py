@@ -1,7 +1,8 @@
 """The FP32 directional path decides a pair's sector in FP32 only outside a guard band and
 leaves the rest to FP64.  This test emulates, with numpy FP32 arithmetic, the device's point
-representation (hi part: the offset from the cell origin rounded to the quantum q = 2^-22 P,
-P the power of two >= the cell side; FP32 low part) and its sector test, on offsets placed
+representation (x: the offset from the box's x0 rounded to the quantum qX = 2^-24 P_W, P_W the
+power of two >= the box width; y: the offset from the cell origin rounded to q = 2^-22 P, P the
+power of two >= the cell side; FP32 low parts) and its sector test, on offsets placed
 adversarially close to the sector boundaries and to the axis at angle 0 / pi, at projected-size
 coordinates, and checks that whenever the FP32 test clears its guards the sector equals the
 one the reference FP64 arithmetic gives.  It also checks that the guards leave almost every
@@ -64,18 +65,23 @@ def test_sector_guard_is_sound(n_sec, x0):
     k64 = ((bx64[None, :] * dy64[:, None] - by64[None, :] * dx64[:, None]) >= 0).sum(axis=1)
     k64 = np.where((xi - xj == 0) & (yi - yj == 0), 0, k64)
     # device: FP32 accurate offset from hi + lo parts, FP32 boundaries, guards
-    cxi, hxi, lxi, qx = _rep(xi, x0, cw, nx)
-    cxj, hxj, lxj, _ = _rep(xj, x0, cw, nx)
+    # x relative to the box (the filter's hi part, quantum qX = 2^-24 P_W, and its remainder);
+    # y relative to the point's cell, the centre moved into the neighbour's cell frame
+    qX = _pow2_at_least(W) * 2.0 ** -24
+    oxi, oxj = xi - x0, xj - x0
+    hxi = (np.rint(oxi / qX) * qX).astype(f32)
+    hxj = (np.rint(oxj / qX) * qX).astype(f32)
+    lxi = (oxi - hxi.astype(np.float64)).astype(f32)
+    lxj = (oxj - hxj.astype(np.float64)).astype(f32)
     cyi, hyi, lyi, qy = _rep(yi, y0, cw, ny)
     cyj, hyj, lyj, _ = _rep(yj, y0, cw, ny)
-    cwq = f32(np.rint(cw / qx) * qx)
-    cwl = f32(cw - np.rint(cw / qx) * qx)
-    dcx = (cxi - cxj).astype(f32)
+    cwq = f32(np.rint(cw / qy) * qy)
+    cwl = f32(cw - np.rint(cw / qy) * qy)
     dcy = (cyi - cyj).astype(f32)
     cwq_v, cwl_v = np.full(N, cwq, f32), np.full(N, cwl, f32)
-    dx = ((_fma32(dcx, cwq_v, hxi) - hxj).astype(f32) + (_fma32(dcx, cwl_v, lxi) - lxj)).astype(f32)
+    dx = ((hxi - hxj).astype(f32) + (lxi - lxj).astype(f32)).astype(f32)
     dy = ((_fma32(dcy, cwq_v, hyi) - hyj).astype(f32) + (_fma32(dcy, cwl_v, lyi) - lyj)).astype(f32)
-    q = max(qx, qy)
+    q = max(qX, qy)
     big = max(abs(x0), abs(x0 + W), abs(y0), abs(y0 + H))
     sec_g = f32(1.0e-6 * s_max + 1.0e-6 * q + 4.0e-16 * big + 1e-30)
     sec_gd = f32(1.0e-6 * q + 4.0e-16 * big + 1e-30)
