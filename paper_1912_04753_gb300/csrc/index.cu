@@ -459,10 +459,12 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         // -y_hi, -t_hi as above; x's low part is taken relative to x0 too
         const double oX = __dsub_rn(xi, g.x0);
         const double hX = rint(oX * g.inv_qX) * g.qX;
-        float* f = F + (int64_t)k * kFilterAxes * g.nF + local;
-        f[0] = -(float)hX;
-        f[g.nF] = -(float)hy;
-        f[2 * g.nF] = -(float)ht;
+        {
+            float* f = F + (int64_t)k * 3 * g.nF + local;
+            f[0] = -(float)hX;
+            f[g.nF] = -(float)hy;
+            f[2 * g.nF] = -(float)ht;
+        }
         float ex = (float)fmin(__dsub_rn(xi, g.x0), __dsub_rn(g.x1, xi));
         float ey = (float)fmin(__dsub_rn(yi, g.y0), __dsub_rn(g.y1, yi));
         const float te = (float)fmin(__dsub_rn(ti, g.t0), __dsub_rn(g.t1, ti));
@@ -475,14 +477,8 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         }
         float rin = em * (1.0f - g.tan_rel) - g.tan_abs - g.fast_abs - em * 4.76837158e-7f;
         rin = fmaxf(rin, 0.0f);
-        const float rin2 = rin * rin * 0.99999f;
-        Pr[n + local] = make_float4(ex, ey, te, rin2);
-        const float xlo = (float)(oX - hX), ylo = (float)(oy - hy);
-        Plo[pos] = make_float2(xlo, ylo);
-        f[3 * g.nF] = te;
-        f[4 * g.nF] = rin2;
-        f[5 * g.nF] = -xlo;
-        f[6 * g.nF] = -ylo;
+        Pr[n + local] = make_float4(ex, ey, te, rin * rin * 0.99999f);
+        Plo[pos] = make_float2((float)(oX - hX), (float)(oy - hy));
         if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)k * n];
         if (H) H[pos] = h_in[gi];
     }

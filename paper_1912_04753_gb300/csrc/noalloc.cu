@@ -140,7 +140,7 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
     double* T = cv.take<double>(n);
     float4* P = cv.take<float4>(2 * (n + 8));
     float2* Plo = cv.take<float2>(n);
-    float* F = cv.take<float>(kFilterAxes * filter_stride(n));
+    float* F = cv.take<float>(3 * filter_stride(n));
     uint32_t* cell_start = cv.take<uint32_t>(ncells + 1);
     uint32_t* ucount = cv.take<uint32_t>(nrows + 1);
     uint32_t* uoff = cv.take<uint32_t>(nrows + 1);

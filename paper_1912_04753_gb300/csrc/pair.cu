@@ -397,9 +397,7 @@ struct WarpSm {
     float cen_h[32];    // inhomogeneous K: h of the centres
     uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
                             // dcy = centre's y cell - neighbour's y cell
-    float4 ring2[kRing + 1];  // units near an edge: the neighbour's e_t and interior bound,
-                              // and the pair's accurate offset (dx, dy) from hi + lo parts
-    uint4 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour, dx, dy)
+    uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
 };
 
 struct Smem32 {
@@ -590,7 +588,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint4 e = ws.q2[off + lane];
+        const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
         const uint32_t ci = c_begin + (meta & 31u);
         const bool other = (meta >> 11) & 1u;
@@ -622,7 +620,9 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
 // an address-taken copy of the warp state weigh on the filter loop.
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
                                            WarpSm* wsp, const float4* __restrict__ Ek,
-                                           RealBatch rb,
+                                           const float* __restrict__ NXk,
+                                           const float* __restrict__ NYk,
+                                           const float2* __restrict__ Plok, RealBatch rb,
                                            ExactQueue xq, int off, int cnt, int lane,
                                            unsigned long long* he, uint32_t* hc,
                                            uint32_t real, uint32_t c_begin) {
@@ -631,17 +631,25 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
-        const uint4 e = ws.q2[off + lane];
+        const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
         const int cl = (int)(meta & 31u);
+        const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
         const bool other = (meta >> 11) & 1u;  // order (j, i): centre j
         const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
-        // the accurate offset the filter formed (exact hi-part difference plus the low parts'
-        // difference; the same for both orders) and, for order (j, i), j's edge record
-        const float dxa = __uint_as_float(e.z), dya = __uint_as_float(e.w);
-        const float4 pb = other ? Ek[j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // the neighbour's hi parts (the filter's arrays, negated: recently read), low parts and
+        // edge record (only order (j, i) uses it), issued together
+        const float nxj = NXk[j], nyj = NYk[j];
+        const float2 lo = Plok[j];
+        const float4 pb = Ek[j];
+        const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
+        // x: box-frame hi parts (exact difference) plus low parts; y: centre i moved into j's
+        // cell frame, hi part exact, lo part carrying the remainder.  The distance is the same
+        // for both orders.
+        const float dxa = (ca.x + nxj) + (cb.x - lo.x);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
         float ra, inv_r;
         radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
         const float ex = other ? pb.x : cb.z, ey = other ? pb.y : cb.w;
@@ -676,12 +684,12 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
             drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Ek, rb, xq, off, 32,
+            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
         off += 32;
     }
     const int rest = w.q2n - off;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    uint2 v = make_uint2(0u, 0u);
     if (lane < rest) v = ws.q2[off + lane];
     __syncwarp();
     if (lane < rest) ws.q2[lane] = v;
@@ -713,14 +721,9 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
     e[1] = ws.ring[32 + lane];
     if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
     float4 pj[2];
-    if (edge && VAR == kVarInh) {  // neighbour's edge record (dense array: 16 bytes per point)
+    if (edge) {  // neighbour's edge record (dense array: 16 bytes per point)
         pj[0] = w.Ek[lane < cnt ? e[0].w : 0u];
         pj[1] = w.Ek[32 + lane < cnt ? e[1].w : 0u];
-    }
-    float4 r2[2];  // the plain estimator: the filter's (e_t, rin2) of the neighbour and (dx, dy)
-    if (edge && VAR == kVarPlain) {
-        r2[0] = ws.ring2[lane];
-        r2[1] = ws.ring2[32 + lane];
     }
     bool rare = false;
     bool full[2], di[2], dj[2], wi[2], wj[2], vi[2], vj[2], aj[2], ai[2];
@@ -755,7 +758,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         di[r] = dj[r] = wi[r] = wj[r] = false;
         if (edge && VAR == kVarPlain) {
             const float te_i = ws.cen_te[cl], rin_i = ws.cen_a[cl].w;
-            const float te_j = r2[r].x, rin_j = r2[r].y;
+            const float te_j = pj[r].z, rin_j = pj[r].w;
             const bool vhi = u > te_i + pc.g_v, vhj = u > te_j + pc.g_v;
             const bool vai = (u > te_i - pc.g_v) & !vhi, vaj = (u > te_j - pc.g_v) & !vhj;
             const bool ini = d2 <= rin_i, inj = d2 <= rin_j;
@@ -937,20 +940,14 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                       o3 = o2 + __popc(b2);
             const uint32_t m0 = e[0].z | ((uint32_t)bin[0] << 13);
             const uint32_t m1 = e[1].z | ((uint32_t)bin[1] << 13);
-            const uint32_t x0 = __float_as_uint(r2[0].z), y0 = __float_as_uint(r2[0].w);
-            const uint32_t x1 = __float_as_uint(r2[1].z), y1 = __float_as_uint(r2[1].w);
-            if (di[0])
-                ws.q2[o0 + __popc(b0 & lt)] =
-                    make_uint4(m0 | ((uint32_t)vi[0] << 12), e[0].w, x0, y0);
+            if (di[0]) ws.q2[o0 + __popc(b0 & lt)] = make_uint2(m0 | ((uint32_t)vi[0] << 12), e[0].w);
             if (dj[0])
                 ws.q2[o1 + __popc(b1 & lt)] =
-                    make_uint4(m0 | (1u << 11) | ((uint32_t)vj[0] << 12), e[0].w, x0, y0);
-            if (di[1])
-                ws.q2[o2 + __popc(b2 & lt)] =
-                    make_uint4(m1 | ((uint32_t)vi[1] << 12), e[1].w, x1, y1);
+                    make_uint2(m0 | (1u << 11) | ((uint32_t)vj[0] << 12), e[0].w);
+            if (di[1]) ws.q2[o2 + __popc(b2 & lt)] = make_uint2(m1 | ((uint32_t)vi[1] << 12), e[1].w);
             if (dj[1])
                 ws.q2[o3 + __popc(b3 & lt)] =
-                    make_uint4(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w, x1, y1);
+                    make_uint2(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w);
             w.q2n = o3 + __popc(b3);
             if (w.q2n >= 32) flush_weights<POLY>(ws, pc, gpc, rb, xq, lane, w);
         }
@@ -969,10 +966,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
         drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
-        for (uint32_t i = lane; i < rest; i += 32) {
-            ws.ring[i] = ws.ring[cnt + i];
-            if (EDGE && VAR == kVarPlain) ws.ring2[i] = ws.ring2[cnt + i];
-        }
+        for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
         tail = rest;
     }
     __syncwarp();
@@ -981,7 +975,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
             drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Ek, rb, xq, 0,
+            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
@@ -1052,7 +1046,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         const float4* Pk = rb.P + 2 * base;
         w.Pk = Pk;
         w.Ek = Pk + n;
-        w.NX = rb.F + (int64_t)k * kFilterAxes * rb.nF;
+        w.NX = rb.F + (int64_t)k * 3 * rb.nF;
         w.NY = w.NX + rb.nF;
         w.real = (uint32_t)k;
         w.Plok = rb.Plo + base;
@@ -1094,18 +1088,11 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                      cy - fs >= pc.deep_y[0] && cy + fs <= pc.deep_y[1] &&
                      ct >= pc.deep_t[0] && ct + ft <= pc.deep_t[1];
             // the filter's copy of the coordinates (negated hi parts; x relative to the box)
-            const float* NXk = w.NX;
+            const float* NXk = rb.F + (int64_t)k * 3 * rb.nF;
             const float* NYk = NXk + rb.nF;
             const float* NTk = NYk + rb.nF;
             const float xcb = -NXk[myi];  // the centre's x in the box frame
             const float2 xc2 = make_float2(xcb, xcb);
-            // units near an edge also stream the neighbours' e_t, interior bound and low parts,
-            // and hand phase B each pair's accurate offset, so that no record is fetched there
-            const bool ew = EDGE && VAR == kVarPlain && !w.deep;
-            const float* TEk = NTk + rb.nF;
-            const float* RIk = TEk + rb.nF;
-            const float* NXLk = RIk + rb.nF;
-            const float* NYLk = NXLk + rb.nF;
             __syncwarp();
             uint32_t tail = 0;
             // rows from the centres' own row onward in key order (t major, y minor); the cells
@@ -1133,7 +1120,6 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                     const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
                     const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
                     const float2 yc2 = make_float2(yc, yc);
-                    const float ylo = fmaf((float)(-dy), pc.g.chl, plo.y);  // centre's y_lo there
                     const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
                     if (valid && J1 > jmin) n_cand += J1 - jmin;
                     since_flush += 32ull * (J1 - jstart);
@@ -1142,13 +1128,6 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                         const float4 qx = *reinterpret_cast<const float4*>(NXk + j);
                         const float4 qy = *reinterpret_cast<const float4*>(NYk + j);
                         const float4 qt = *reinterpret_cast<const float4*>(NTk + j);
-                        float4 qe, qr, qxl, qyl;  // e_t, rin2, -x_lo, -y_lo of the four
-                        if (ew) {
-                            qe = *reinterpret_cast<const float4*>(TEk + j);
-                            qr = *reinterpret_cast<const float4*>(RIk + j);
-                            qxl = *reinterpret_cast<const float4*>(NXLk + j);
-                            qyl = *reinterpret_cast<const float4*>(NYLk + j);
-                        }
                         const float2 dxa = __fadd2_rn(xc2, make_float2(qx.x, qx.y));
                         const float2 dxb = __fadd2_rn(xc2, make_float2(qx.z, qx.w));
                         const float2 dya = __fadd2_rn(yc2, make_float2(qy.x, qy.y));
@@ -1174,39 +1153,22 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                         const uint32_t t1 = tail + (uint32_t)__popc(m0);
                         const uint32_t t2 = t1 + (uint32_t)__popc(m1);
                         const uint32_t t3 = t2 + (uint32_t)__popc(m2);
-                        // accurate offset: the exact hi difference plus the low parts' difference
-                        if (k0) {
-                            const uint32_t o = tail + __popc(m0 & lt);
-                            ws.ring[o] = make_uint4(__float_as_uint(d2a.x),
-                                                    __float_as_uint(fabsf(dta.x)), meta, j);
-                            if (ew)
-                                ws.ring2[o] = make_float4(qe.x, qr.x, dxa.x + (plo.x + qxl.x),
-                                                          dya.x + (ylo + qyl.x));
-                        }
-                        if (k1) {
-                            const uint32_t o = t1 + __popc(m1 & lt);
-                            ws.ring[o] = make_uint4(__float_as_uint(d2a.y),
-                                                    __float_as_uint(fabsf(dta.y)), meta, j + 1);
-                            if (ew)
-                                ws.ring2[o] = make_float4(qe.y, qr.y, dxa.y + (plo.x + qxl.y),
-                                                          dya.y + (ylo + qyl.y));
-                        }
-                        if (k2) {
-                            const uint32_t o = t2 + __popc(m2 & lt);
-                            ws.ring[o] = make_uint4(__float_as_uint(d2b.x),
-                                                    __float_as_uint(fabsf(dtb.x)), meta, j + 2);
-                            if (ew)
-                                ws.ring2[o] = make_float4(qe.z, qr.z, dxb.x + (plo.x + qxl.z),
-                                                          dyb.x + (ylo + qyl.z));
-                        }
-                        if (k3) {
-                            const uint32_t o = t3 + __popc(m3 & lt);
-                            ws.ring[o] = make_uint4(__float_as_uint(d2b.y),
-                                                    __float_as_uint(fabsf(dtb.y)), meta, j + 3);
-                            if (ew)
-                                ws.ring2[o] = make_float4(qe.w, qr.w, dxb.y + (plo.x + qxl.w),
-                                                          dyb.y + (ylo + qyl.w));
-                        }
+                        if (k0)
+                            ws.ring[tail + __popc(m0 & lt)] =
+                                make_uint4(__float_as_uint(d2a.x), __float_as_uint(fabsf(dta.x)),
+                                           meta, j);
+                        if (k1)
+                            ws.ring[t1 + __popc(m1 & lt)] =
+                                make_uint4(__float_as_uint(d2a.y), __float_as_uint(fabsf(dta.y)),
+                                           meta, j + 1);
+                        if (k2)
+                            ws.ring[t2 + __popc(m2 & lt)] =
+                                make_uint4(__float_as_uint(d2b.x), __float_as_uint(fabsf(dtb.x)),
+                                           meta, j + 2);
+                        if (k3)
+                            ws.ring[t3 + __popc(m3 & lt)] =
+                                make_uint4(__float_as_uint(d2b.y), __float_as_uint(fabsf(dtb.y)),
+                                           meta, j + 3);
                         tail = t3 + (uint32_t)__popc(m3);
                         while (tail >= (uint32_t)kDrain) {
                             __syncwarp();
@@ -1215,20 +1177,14 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                             __syncwarp();
                             const uint32_t rest = tail - kDrain;
                             uint4 v[4];
-                            float4 v2[4];
 #pragma unroll
                             for (int c = 0; c < 4; ++c)
-                                if ((uint32_t)(lane + 32 * c) < rest) {
+                                if ((uint32_t)(lane + 32 * c) < rest)
                                     v[c] = ws.ring[kDrain + lane + 32 * c];
-                                    if (ew) v2[c] = ws.ring2[kDrain + lane + 32 * c];
-                                }
                             __syncwarp();
 #pragma unroll
                             for (int c = 0; c < 4; ++c)
-                                if ((uint32_t)(lane + 32 * c) < rest) {
-                                    ws.ring[lane + 32 * c] = v[c];
-                                    if (ew) ws.ring2[lane + 32 * c] = v2[c];
-                                }
+                                if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
                             __syncwarp();
                             tail = rest;
                         }

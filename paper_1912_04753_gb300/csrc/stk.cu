@@ -95,7 +95,7 @@ struct stk_handle {
     DevBuf acc_cnt, acc_lo, acc_hi, stats, pc, thr, self_pairs, mask_in, mask_sorted;
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     DevBuf oA;  // raw accumulators of the last job's realizations, [R][4][nbins]
-    DevBuf F;   // the pair filter's arrays, [m][kFilterAxes][filter_stride(n)]
+    DevBuf F;   // the pair filter's coordinate arrays, [m][3][filter_stride(n)]
     int last_rows = 0, last_nbins = 0;  // shape of oA
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     // pinned staging of the other per-job host inputs (graph-capturable copies)
@@ -217,7 +217,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
     f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
                  8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
-                 4 * kFilterAxes * (size_t)filter_stride(n) /* filter arrays */ +
+                 4 * 3 * (size_t)filter_stride(n) /* filter arrays */ +
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
@@ -554,8 +554,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         (rc = ensure(h->X, 8 * mn, "sorted x")) || (rc = ensure(h->Y, 8 * mn, "sorted y")) ||
         (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 32 * (mn + 8), "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
-        (rc = ensure(h->F, 4 * kFilterAxes * (size_t)m_w * (size_t)filter_stride(n),
-                     "filter arrays")) ||
+        (rc = ensure(h->F, 12 * (size_t)m_w * (size_t)filter_stride(n), "filter arrays")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
         (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
         (rc = ensure(h->chunk_off, 4 * mr, "work offsets")) ||

@@ -11,10 +11,9 @@
 //     differences of hi parts are exact in FP32, and hi + lo carries the offset to ~2^-45 of
 //     the cell size -- except x_lo, which completes the filter's box-frame x hi part below;
 //   - the pair filter's copy of the coordinates, structure of arrays per realization,
-//     [kFilterAxes][nF] floats: -x_hi relative to the box's x0 (quantum Grid::qX), -y_hi and
-//     -t_hi in the point's cell frame (the same values as above, negated), then e_t and the
-//     interior bound on d2 (the edge record's), then -x_lo (below the box-frame x_hi) and -y_lo,
-//     so four consecutive points load as one float4 per axis;
+//     [3][nF] floats: -x_hi relative to the box's x0 (quantum Grid::qX), -y_hi and -t_hi in the
+//     point's cell frame (the same values as above, negated), so four consecutive points load
+//     as one float4 per axis;
 //   - cell_start[ncells + 1] per realization (offsets into that realization's n points).
 //   - work units: 32 consecutive centres of one (cy, ct) row, in realization order.
 #pragma once
@@ -32,8 +31,6 @@ constexpr int kMaxSectors = 64;        // direction sectors of the directional K
 constexpr int kTab = 1024;    // bin-table entries per axis
 constexpr int kBlock = 256;   // threads per pair-kernel block
 constexpr int kUnit = 32;      // centres per work unit (one warp)
-// axes of the filter's arrays: -x_hi, -y_hi, -t_hi, e_t, rin2, -x_lo, -y_lo
-constexpr int kFilterAxes = 7;
 
 // Uniform grid over the study box.  Cell sides are >= s_max / fs (x, y) and >= t_max / ft (t)
 // with fs, ft in {1, 2}, so every pair within the thresholds lies in the block of
@@ -131,7 +128,7 @@ struct RealBatch {
     // inhomogeneous K: per sorted point h = mean(rho) / rho(cell of the point), [m][n]; null
     // for the homogeneous estimator
     const double* H = nullptr;
-    // the filter's arrays, [m][kFilterAxes][nF] (see the layout above)
+    // the filter's coordinate arrays, [m][3][nF] (negated hi parts, see the layout above)
     const float* F = nullptr;
     int64_t nF = 0;
     // sharding of realization 0 of the launch (the observed pattern): its work units
