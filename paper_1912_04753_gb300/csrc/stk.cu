@@ -103,8 +103,8 @@ struct stk_handle {
     uint64_t* h_seed = nullptr;  // [h_sim_cap]
     uint32_t* h_id = nullptr;
     size_t h_sim_cap = 0;
-    // the last single-wave job, captured as a CUDA graph, and what it was captured for
-    cudaGraphExec_t gexec = nullptr;
+    // the last job, captured as one CUDA graph per wave, and what it was captured for
+    std::vector<cudaGraphExec_t> gexecs;
     std::vector<unsigned char> gkey;
     stk_stats last;
     size_t smem32 = 0, smem64 = 0;
@@ -660,8 +660,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         }
         return k + 1;
     };
-    // every stream operation of the wave holding realizations r0 .. r0+m-1
-    // (in_graph: being captured; the events then bracket the whole graph launch instead)
+    // every stream operation of the wave holding realizations r0 .. r0+m-1 (in_graph: being
+    // captured; the events around the pair kernel then become event-record nodes of the graph)
     auto issue_wave = [&](int r0, int m, bool in_graph) -> int {
         const bool obs_here = include_obs && r0 == 0;
         const int first_sim_slot = obs_here ? 1 : 0;
@@ -777,7 +777,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         acc.exc_hi = as<unsigned long long>(h->acc_hi);
         acc.stats = as<unsigned long long>(h->stats);
         acc.whole = inh ? as<unsigned long long>(h->acc_whole) : nullptr;
-        if (!in_graph) CK(cudaEventRecord(h->ev0, st), "event");
+        CK(cudaEventRecordWithFlags(h->ev0, st, in_graph ? cudaEventRecordExternal : 0), "event");
         ExactQueue xq;
         xq.e = as<uint4>(h->xq_e);
         xq.count = as<unsigned int>(h->xq_count);
@@ -793,7 +793,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
                                 as<uint32_t>(h->counter), acc, st, h->nv > 0, inh, dir),
                "pair kernel (FP64)");
-        if (!in_graph) CK(cudaEventRecord(h->ev1, st), "event");
+        CK(cudaEventRecordWithFlags(h->ev1, st, in_graph ? cudaEventRecordExternal : 0), "event");
         if (fp32) {
             CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st, h->nv > 0,
                             dir),
@@ -823,14 +823,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
            "finalize");
         return STK_OK;
     };
-    // A small single-wave job without a centre mask (launch overhead matters there) is captured
-    // as a CUDA graph and replayed while the next jobs have the same shape, constants and
-    // buffers (STK_GRAPHS=0 disables it, 1 forces it for any single-wave job).  The pair-kernel
-    // time of a graph job is that of the whole graph.
+    // A batched job without role flags (centre mask, labels) is captured as one CUDA graph per
+    // wave and replayed while the next jobs have the same shape, constants and buffers
+    // (STK_GRAPHS=0 disables it).  The pair kernel is timed by event-record nodes inside the
+    // graph.
     const char* graphs_env = getenv("STK_GRAPHS");
     const int graphs = graphs_env ? atoi(graphs_env) : -1;
-    const bool use_graph = R <= m_w && !use_mask && graphs != 0 &&
-                           (graphs == 1 || (double)n * (double)R <= 1.6e7);
+    const bool use_graph = q->exec == STK_EXEC_BATCHED && !use_mask && graphs != 0;
     std::vector<unsigned char> key;
     if (use_graph) {
         auto put = [&key](const void* p, size_t b) {
@@ -856,19 +855,18 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
-    for (int r0 = 0; r0 < R; r0 += m_w) {
+    const int n_waves = (R + m_w - 1) / m_w;
+    const bool replay = use_graph && (int)h->gexecs.size() == n_waves && key == h->gkey;
+    if (use_graph && !replay) {
+        for (cudaGraphExec_t ge : h->gexecs) cudaGraphExecDestroy(ge);
+        h->gexecs.clear();
+        h->gkey.clear();
+    }
+    for (int r0 = 0, wi = 0; r0 < R; r0 += m_w, ++wi) {
         const int m = std::min(m_w, R - r0);
         const bool obs_here = include_obs && r0 == 0;
         const int first_sim_slot = obs_here ? 1 : 0;
-        if (use_graph && h->gexec && key == h->gkey) {
-            CK(cudaEventRecord(h->ev0, st), "event");
-            CK(cudaGraphLaunch(h->gexec, st), "graph launch");
-            CK(cudaEventRecord(h->ev1, st), "event");
-            ++replays;
-        } else if (use_graph) {
-            if (h->gexec) cudaGraphExecDestroy(h->gexec);
-            h->gexec = nullptr;
-            h->gkey.clear();
+        if (use_graph && !replay) {  // capture this wave (its events become graph nodes)
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture");
             const int irc = issue_wave(r0, m, true);
             cudaGraph_t graph = nullptr;
@@ -882,11 +880,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
             cudaGraphDestroy(graph);
             CK(ei, "graph instantiate");
-            h->gexec = ex;
-            h->gkey = key;
-            CK(cudaEventRecord(h->ev0, st), "event");
-            CK(cudaGraphLaunch(h->gexec, st), "graph launch");
-            CK(cudaEventRecord(h->ev1, st), "event");
+            h->gexecs.push_back(ex);
+        }
+        if (use_graph) {
+            CK(cudaGraphLaunch(h->gexecs[(size_t)wi], st), "graph launch");
+            if (replay) ++replays;
         } else {
             rc = issue_wave(r0, m, false);
             if (rc) return rc;
@@ -901,6 +899,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                     4 /* scatter, starts, counts, fill */ +
                     2 /* pair, finalize */ + (fp32 ? 1 : 0) /* FP64 queue */;
     }
+    if (use_graph && !replay) h->gkey = key;
     const int first_sim_row = include_obs ? 1 : 0;
     for (int gi = 0; gi < n_groups; ++gi) {
         const int g0 = plan.groups[gi].first, gn = plan.groups[gi].second;
@@ -1773,7 +1772,7 @@ void stk_destroy(stk_handle* h) {
     if (h->h_thr) cudaFreeHost(h->h_thr);
     if (h->h_seed) cudaFreeHost(h->h_seed);
     if (h->h_id) cudaFreeHost(h->h_id);
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (cudaGraphExec_t g : h->gexecs) cudaGraphExecDestroy(g);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
