@@ -106,6 +106,7 @@ struct stk_handle {
     // the last job, captured as one CUDA graph per wave, and what it was captured for
     std::vector<cudaGraphExec_t> gexecs;
     std::vector<unsigned char> gkey;
+    std::vector<unsigned char> last_key;  // the shape of the last batched job (captured or not)
     stk_stats last;
     size_t smem32 = 0, smem64 = 0;
     int reps32 = 1, reps64 = 1;
@@ -823,15 +824,16 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
            "finalize");
         return STK_OK;
     };
-    // A batched job without role flags (centre mask, labels) is captured as one CUDA graph per
-    // wave and replayed while the next jobs have the same shape, constants and buffers
-    // (STK_GRAPHS=0 disables it).  The pair kernel is timed by event-record nodes inside the
-    // graph.
+    // A batched job without role flags (centre mask, labels) whose shape, constants and buffers
+    // repeat those of the job before it is captured as one CUDA graph per wave and replayed for
+    // as long as they stay the same, so a one-off job pays no capture (STK_GRAPHS=1 captures a
+    // shape at its first occurrence, 0 disables graphs).  The pair kernel is timed by
+    // event-record nodes inside the graph.
     const char* graphs_env = getenv("STK_GRAPHS");
     const int graphs = graphs_env ? atoi(graphs_env) : -1;
-    const bool use_graph = q->exec == STK_EXEC_BATCHED && !use_mask && graphs != 0;
+    const bool graph_ok = q->exec == STK_EXEC_BATCHED && !use_mask && graphs != 0;
     std::vector<unsigned char> key;
-    if (use_graph) {
+    if (graph_ok) {
         auto put = [&key](const void* p, size_t b) {
             const unsigned char* c = reinterpret_cast<const unsigned char*>(p);
             key.insert(key.end(), c, c + b);
@@ -856,7 +858,9 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     }
     int replays = 0;
     const int n_waves = (R + m_w - 1) / m_w;
-    const bool replay = use_graph && (int)h->gexecs.size() == n_waves && key == h->gkey;
+    const bool replay = graph_ok && (int)h->gexecs.size() == n_waves && key == h->gkey;
+    const bool use_graph = replay || (graph_ok && (graphs == 1 || key == h->last_key));
+    if (graph_ok) h->last_key = key;
     if (use_graph && !replay) {
         for (cudaGraphExec_t ge : h->gexecs) cudaGraphExecDestroy(ge);
         h->gexecs.clear();

@@ -64,7 +64,10 @@ def test_multi_wave_graph_replay_equals_direct_issue(stk, monkeypatch):
         st = p.stats()
         assert st["waves"] >= 3 and st["graph_replays"] == 0
         monkeypatch.delenv("STK_GRAPHS")
-        p.run(w.s, w.tt, n_sims=9, seed=4, want_sims=True)  # captured
+        p.run(w.s, w.tt, n_sims=9, seed=4, want_sims=True)  # a first occurrence: issued directly
+        assert p.stats()["graph_replays"] == 0
+        p.run(w.s, w.tt, n_sims=9, seed=4, want_sims=True)  # the shape repeats: captured
+        assert p.stats()["graph_replays"] == 0
         got = p.run(w.s, w.tt, n_sims=9, seed=4, want_sims=True)  # replayed
         sg = p.stats()
     assert sg["graph_replays"] == sg["waves"] == st["waves"]
