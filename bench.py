@@ -262,53 +262,72 @@ def run_reference(args):
 
 
 def serve_bench(args, stk, seed=0):
-    """Serving loop on a synthetic request stream (Poisson arrivals, n log-uniform in
-    [1e3, 1e6], CSR / Thomas / POI-mixture point sets kept resident, 5-50 thresholds per axis,
-    0-199 simulations, own seed per request): p50 / p99 latency from submission to result and
-    jobs/s, FP32-guarded continuous batching vs a single FIFO queue running each job as the
-    plain FP64 path (one launch per realization)."""
+    """Serving loop on synthetic request streams (Poisson arrivals, n log-uniform in [1e3, 1e6],
+    CSR / Thomas / POI-mixture point sets kept resident, 5-50 thresholds per axis, 0-199
+    simulations, own seed per request), swept over arrival rates from light load to overload:
+    per rate p50 / p99 / max latency from submission to result, jobs/s, the share of jobs merged
+    into another job's batch and kernel launches per job.  Then: a sample of served results
+    against the same jobs run alone (must be identical), and the first requests of the lightest
+    stream through a single FIFO queue running each job as the plain FP64 path (one launch per
+    realization), the comparison the FP32-guarded continuous batching is measured against."""
     from paper_1912_04753_gb300 import workloads as wl
 
-    datasets, reqs = wl.serving_stream(args.serve_requests, seed=seed, rate_hz=args.serve_rate)
-    out = {"requests": len(reqs), "datasets": len(datasets),
-           "n_range": [min(d.n for d in datasets), max(d.n for d in datasets)],
-           "rate_hz": args.serve_rate, "sims_total": int(sum(r["n_sims"] for r in reqs))}
+    rates = [float(r) for r in str(args.serve_rates).split(",") if r]
+    count = args.serve_requests
+    datasets, _ = wl.serving_stream(1, seed=seed, rate_hz=rates[0])
+    out = {"requests_per_rate": count, "datasets": len(datasets),
+           "n_range": [min(d.n for d in datasets), max(d.n for d in datasets)], "sweep": []}
+    served_sample = []
     with stk.Server(slots=args.serve_slots) as sv:
         ids = [sv.register(d.x, d.y, d.t, d.box) for d in datasets]
         # warm-up: one small job per point set (workspaces, kernel attributes)
         for k, d in enumerate(datasets):
             sv.poll(sv.submit(ids[k], d.s, d.tt, n_sims=1, seed=1))
-        sv.reset_stats()
-        tickets = [None] * len(reqs)
+        for ri, rate in enumerate(rates):
+            ds2, reqs = wl.serving_stream(count, seed=seed, rate_hz=rate)
+            assert len(ds2) == len(datasets) and all(a.n == b.n for a, b in zip(ds2, datasets))
+            sv.reset_stats()
+            tickets = [None] * len(reqs)
 
-        def submit_all():
-            t0 = time.perf_counter()
-            for i, r in enumerate(reqs):
-                dt = r["arrival_s"] - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                tickets[i] = sv.submit(ids[r["dataset"]], r["s"], r["tt"], n_sims=r["n_sims"],
-                                       seed=r["seed"], want_sims=False)
+            def submit_all():
+                t0 = time.perf_counter()
+                for i, r in enumerate(reqs):
+                    dt = r["arrival_s"] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = sv.submit(ids[r["dataset"]], r["s"], r["tt"],
+                                           n_sims=r["n_sims"], seed=r["seed"], want_sims=False)
 
-        th = threading.Thread(target=submit_all)
-        th.start()
-        th.join()
-        served = [sv.poll(tk) for tk in tickets]
-        st = sv.stats()
-    out["fp32_served"] = {
-        "slots": args.serve_slots, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-        "max_ms": st["max_ms"], "jobs_per_s": st["jobs_per_s"], "sims_per_s": st["sims_per_s"],
-        "batches": st["batches"], "merged_jobs": st["merged_jobs"],
-        "max_queue_depth": st["max_queue_depth"], "peak_device_bytes": st["peak_bytes"]}
-    # a few results against the same job run alone (must be identical)
-    same = True
-    for i in range(min(3, len(reqs))):
-        r, d = reqs[i], datasets[reqs[i]["dataset"]]
+            th = threading.Thread(target=submit_all)
+            th.start()
+            th.join()
+            served = [sv.poll(tk) for tk in tickets]
+            st = sv.stats()
+            done = max(1, st["completed"])
+            out["sweep"].append({
+                "rate_hz": rate, "offered_s": reqs[-1]["arrival_s"],
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "mean_ms": st["mean_ms"], "jobs_per_s": st["jobs_per_s"],
+                "sims_per_s": st["sims_per_s"], "completed": st["completed"],
+                "failed": st["failed"], "batches": st["batches"],
+                "merged_fraction": st["merged_jobs"] / done,
+                "launches_per_job": st["kernel_launches"] / done,
+                "max_queue_depth": st["max_queue_depth"], "peak_device_bytes": st["peak_bytes"]})
+            if ri == len(rates) - 1:  # results of the heaviest stream, to check against alone
+                served_sample = [(reqs[i], served[i][0])
+                                 for i in range(0, len(reqs), max(1, len(reqs) // 20))][:20]
+        out["slots"] = args.serve_slots
+    # served = alone, bit for bit, on a sample of the heaviest stream's requests
+    same, checked = True, 0
+    for r, got in served_sample:
+        d = datasets[r["dataset"]]
         with stk.Pattern(d.x, d.y, d.t, d.box) as p:
             alone = p.run(r["s"], r["tt"], n_sims=r["n_sims"], seed=r["seed"])
-        same = same and all(np.array_equal(served[i][0][k], alone[k]) for k in alone)
-    out["served_equals_alone"] = same
-    if args.serve_fp64:
+        same = same and all(np.array_equal(got[k], alone[k]) for k in alone)
+        checked += 1
+    out["served_equals_alone"] = {"checked": checked, "identical": same}
+    if args.serve_fp64 > 0:
+        _, reqs = wl.serving_stream(args.serve_fp64, seed=seed, rate_hz=rates[0])
         handles = [stk.Pattern(d.x, d.y, d.t, d.box) for d in datasets]
         for k, d in enumerate(datasets):  # warm-up as above
             handles[k].run(d.s, d.tt, n_sims=1, seed=1, prec=stk.STK_PREC_FP64,
@@ -327,9 +346,10 @@ def serve_bench(args, stk, seed=0):
             hd.close()
         lat = np.sort(np.array(lat))
         q = lambda p: float(lat[max(0, int(np.ceil(p / 100 * len(lat))) - 1)])
-        out["fp64_plain_fifo"] = {"p50_ms": q(50), "p99_ms": q(99), "max_ms": float(lat[-1]),
+        out["fp64_plain_fifo"] = {"requests": len(reqs), "rate_hz": rates[0], "p50_ms": q(50),
+                                  "p99_ms": q(99), "max_ms": float(lat[-1]),
                                   "jobs_per_s": len(reqs) / wall,
-                                  "sims_per_s": out["sims_total"] / wall}
+                                  "sims_per_s": int(sum(r["n_sims"] for r in reqs)) / wall}
     return out
 
 
@@ -628,12 +648,14 @@ def build_parser():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--compare-fp64", type=int, default=1)
-    ap.add_argument("--serve-requests", type=int, default=48,
-                    help="requests in the serving-loop measurement (0: skip it)")
-    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests per arrival rate in the serving-loop sweep (0: skip it)")
+    ap.add_argument("--serve-rates", default="15,30,60",
+                    help="mean arrivals per second of the sweep, comma-separated")
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--serve-fp64", type=int, default=1,
-                    help="also replay the stream through a FIFO of plain FP64 jobs")
+    ap.add_argument("--serve-fp64", type=int, default=48,
+                    help="requests of the lightest stream also run through a FIFO of plain "
+                         "FP64 jobs (0: skip)")
     ap.add_argument("--methods", type=int, default=1,
                     help="also time the job with permutation and bootstrap simulations")
     ap.add_argument("--polygon", type=int, default=1,

@@ -404,6 +404,7 @@ typedef struct {
     int64_t resident_bytes;       /* point sets + workspaces held now */
     int64_t peak_bytes;           /* most held (accounted) at once */
     int64_t budget_bytes;
+    int64_t kernel_launches;      /* CUDA kernels the batches launched (graph replays included) */
 } stk_serve_stats;
 
 /* Errors: STK_EINVAL (bad config), STK_ENODEV, STK_ECUDA, STK_ENOMEM. */

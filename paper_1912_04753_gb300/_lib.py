@@ -79,7 +79,8 @@ class stk_serve_stats(ctypes.Structure):
         "merged_jobs", "simulations", "qualifying_pairs")] +
         [(k, ctypes.c_double) for k in (
             "p50_ms", "p99_ms", "max_ms", "mean_ms", "wall_s", "jobs_per_s", "sims_per_s")] +
-        [(k, ctypes.c_int64) for k in ("resident_bytes", "peak_bytes", "budget_bytes")])
+        [(k, ctypes.c_int64) for k in ("resident_bytes", "peak_bytes", "budget_bytes",
+                                        "kernel_launches")])
 
 
 _lib = None

@@ -94,7 +94,7 @@ struct stk_server {
     int running = 0;
     // statistics since the last reset
     int64_t submitted = 0, completed = 0, failed = 0, max_depth = 0, batches = 0, merged = 0;
-    int64_t sims_done = 0, pairs = 0;
+    int64_t sims_done = 0, pairs = 0, launches = 0;
     std::vector<double> lat_ms;
     bool have_first = false;
     Clock::time_point t_first, t_last;
@@ -224,7 +224,7 @@ bool take_batch(stk_server* sv, Batch* out) {
 }
 
 // Runs one batch on its point set's stream (lock not held).  Fills the jobs' results.
-int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual) {
+int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual, int64_t* launches) {
     const Job& head = *b.jobs[0];
     stk_request q;
     memset(&q, 0, sizeof q);
@@ -281,6 +281,7 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual) {
     stk_stats st;
     stk_last_stats(h, &st);
     *qual = st.qualifying_pairs;
+    *launches = st.kernel_launches;
     for (size_t j = 0; j < b.jobs.size(); ++j) {
         Job& job = *b.jobs[j];
         job.K = K;
@@ -313,8 +314,8 @@ void worker_main(stk_server* sv) {
         Dataset& ds = sv->datasets[b.dataset];
         stk_handle* h = ds.h;
         lock.unlock();
-        int64_t qual = 0;
-        const int rc = run_batch(sv, h, b, &qual);
+        int64_t qual = 0, launches = 0;
+        const int rc = run_batch(sv, h, b, &qual, &launches);
         const std::string err = rc ? std::string(stk_last_error()) : std::string();
         const auto now = Clock::now();
         lock.lock();
@@ -333,6 +334,7 @@ void worker_main(stk_server* sv) {
         sv->batches += 1;
         if (b.jobs.size() > 1) sv->merged += (int64_t)b.jobs.size();
         if (rc == STK_OK) sv->pairs += qual;
+        sv->launches += launches;
         for (auto& jp : b.jobs) {
             Job& j = *jp;
             j.t_done = now;
@@ -615,6 +617,7 @@ int stk_server_stats(stk_server* sv, stk_serve_stats* out) {
     out->merged_jobs = sv->merged;
     out->simulations = sv->sims_done;
     out->qualifying_pairs = sv->pairs;
+    out->kernel_launches = sv->launches;
     out->p50_ms = percentile(sv->lat_ms, 50.0);
     out->p99_ms = percentile(sv->lat_ms, 99.0);
     double mx = 0, sum = 0;
@@ -638,7 +641,7 @@ int stk_server_reset_stats(stk_server* sv) {
     if (!sv) return note(STK_EINVAL, "server is NULL");
     std::lock_guard<std::mutex> lock(sv->mu);
     sv->submitted = sv->completed = sv->failed = sv->max_depth = 0;
-    sv->batches = sv->merged = sv->sims_done = sv->pairs = 0;
+    sv->batches = sv->merged = sv->sims_done = sv->pairs = sv->launches = 0;
     sv->lat_ms.clear();
     sv->have_first = false;
     sv->peak = sv->accounted();
