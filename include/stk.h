@@ -245,6 +245,8 @@ typedef struct {
     int32_t grid_refinement;   /* fs: grid cells of s_max/fs x s_max/fs (1..3) */
     int32_t graph_replays;     /* waves replayed from a captured CUDA graph */
     int32_t grid_refinement_t; /* ft: grid cells of t_max/ft in time (1..3) */
+    int32_t obs_index_reused;  /* 1: the observed pattern's sorted grid index was resident (the
+                                  last job on h had the same grid), not rebuilt */
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);

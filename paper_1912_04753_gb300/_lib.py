@@ -56,7 +56,7 @@ class stk_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_pair", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("internal_errors", ctypes.c_int64),
                 ("grid_refinement", ctypes.c_int32), ("graph_replays", ctypes.c_int32),
-                ("grid_refinement_t", ctypes.c_int32)]
+                ("grid_refinement_t", ctypes.c_int32), ("obs_index_reused", ctypes.c_int32)]
 
 
 class stk_server_config(ctypes.Structure):

@@ -422,7 +422,7 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
                                float4* __restrict__ P, float2* __restrict__ Plo,
                                uint8_t* __restrict__ mask_out,
                                const double* __restrict__ h_in, double* __restrict__ H,
-                               float* __restrict__ F) {
+                               float* __restrict__ F, int slot0) {
     // P holds two float4 per point, the coordinate record (x_hi, y_hi, t_hi, cell x) in the
     // first half of the realization's [2n] and the edge record (e_x, e_y, e_t, rin2) in the
     // second: distances to the nearer x edge, y edge and end of the period, and a bound on d2
@@ -432,7 +432,9 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
     const int64_t total = n * (int64_t)m;
     for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
          gi += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(gi / n);
+        // inputs are those of slots slot0 .. slot0 + m - 1 (outputs: their slots)
+        const int kr = (int)(gi / n);
+        const int k = slot0 + kr;
         const uint32_t kk = key[gi];
         const int64_t pos = (int64_t)start[(int64_t)k * ncells + kk] + rank[gi];
         const double xi = x[gi], yi = y[gi], ti = t[gi];
@@ -479,7 +481,7 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         rin = fmaxf(rin, 0.0f);
         Pr[n + local] = make_float4(ex, ey, te, rin * rin * 0.99999f);
         Plo[pos] = make_float2((float)(oX - hX), (float)(oy - hy));
-        if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)k * n];
+        if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)kr * n];
         if (H) H[pos] = h_in[gi];
     }
 }
@@ -641,7 +643,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
                            float tan_rel, float tan_abs, float fast_abs, float* F, int64_t nF,
                            cudaStream_t st, Polygon poly, bool mask_all, const double* h_in,
-                           double* H) {
+                           double* H, int slot0) {
     ScatterGrid s;
     s.qX = g.qX;
     s.inv_qX = 1.0 / (double)g.qX;
@@ -670,7 +672,7 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
     s.inv_qt = 1.0 / (double)g.qt;
     scatter_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
         m, n, g.ncells, s, x, y, t, key, rank, start_global, mask_in, X, Y, T, P, Plo,
-        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr, F);
+        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr, F, slot0);
     return cudaGetLastError();
 }
 

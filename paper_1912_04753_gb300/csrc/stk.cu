@@ -96,6 +96,10 @@ struct stk_handle {
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     DevBuf oA;  // raw accumulators of the last job's realizations, [R][4][nbins]
     DevBuf F;   // the pair filter's coordinate arrays, [m][3][filter_stride(n)]
+    // resident index of the observed pattern: its sorted arrays, cell counts and filter arrays
+    // from the last job, reused while the grid and the record constants (obs_key) are the same
+    DevBuf obs;
+    std::vector<unsigned char> obs_key;
     int last_rows = 0, last_nbins = 0;  // shape of oA
     PairConsts* h_pc = nullptr;  // pinned host copy of the pair constants
     // pinned staging of the other per-job host inputs (graph-capturable copies)
@@ -222,7 +226,8 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
-              16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
+              16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096 +
+              80 * un + 4 * ncells + 2048 /* resident observed index */;
     return f;
 }
 
@@ -233,7 +238,7 @@ size_t workspace_bytes(const stk_handle* h) {
                             &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                             &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
                             &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh,
-                            &h->Hs, &h->acc_whole, &h->oA, &h->F};
+                            &h->Hs, &h->acc_whole, &h->oA, &h->F, &h->obs};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     return b;
@@ -647,11 +652,46 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     int reps = fp32 ? h->reps32 : h->reps64;
     size_t smem = fp32 ? h->smem32 : h->smem64;
     if (inh) smem = fp32 ? pair_fp32_smem(nbins, &reps, true) : pair_fp64_smem(nbins, &reps, true);
-    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem, inh);
+    // STK_FILTER_STAGED=1: the filter variant that bulk-copies row runs into shared memory
+    // (even thresholds, isotropic correction, rectangle, plain estimator)
+    const char* staged_env = getenv("STK_FILTER_STAGED");
+    const bool staged = fp32 && staged_env && atoi(staged_env) != 0 && h->h_pc->even_s &&
+                        h->h_pc->even_t && q->edge_mode == STK_EDGE_ISOTROPIC && h->nv == 0 &&
+                        !inh && !dir;
+    const int bps = fp32 ? (staged ? pair_fp32_tma_blocks_per_sm(smem) : pair_fp32_blocks_per_sm(smem))
+                         : pair_fp64_blocks_per_sm(smem, inh);
     const int grid = bps * h->num_sms;
     float ms_pair = 0.0f;
     int waves = 0;
     int64_t launches = 0;
+    // resident observed index: reused when the grid, the record constants and the study area
+    // are those of the cached copy (no role flags, no intensity: their per-point data differ)
+    const int64_t nF = filter_stride(n);
+    auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t oc_cnt = 0, oc_x = a256(4 * (size_t)ncells), oc_y = oc_x + a256(8 * (size_t)n),
+                 oc_t = oc_y + a256(8 * (size_t)n), oc_p = oc_t + a256(8 * (size_t)n),
+                 oc_lo = oc_p + a256(32 * (size_t)n), oc_f = oc_lo + a256(8 * (size_t)n),
+                 oc_end = oc_f + a256(12 * (size_t)nF);
+    bool obs_cacheable = include_obs && !use_mask && !inh;
+    std::vector<unsigned char> okey;
+    if (obs_cacheable) {
+        auto put = [&okey](const void* p, size_t b) {
+            const unsigned char* c = reinterpret_cast<const unsigned char*>(p);
+            okey.insert(okey.end(), c, c + b);
+        };
+        put(&g, sizeof g);
+        const float rc3[3] = {h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs};
+        put(rc3, sizeof rc3);
+        const void* pp[2] = {h->poly.p, (const void*)(intptr_t)h->nv};
+        put(pp, sizeof pp);
+    }
+    const bool obs_hit = obs_cacheable && !h->obs_key.empty() && okey == h->obs_key &&
+                         h->obs.bytes >= oc_end;
+    if (obs_cacheable && !obs_hit) {
+        h->obs_key.clear();
+        if (ensure(h->obs, oc_end, "observed index") != STK_OK) obs_cacheable = false;
+    }
+    unsigned char* oc = reinterpret_cast<unsigned char*>(h->obs.p);
     // kernels of one exclusive scan over `count` entries (tile pass + add pass per level)
     auto scan_launches = [](int64_t count) {
         int64_t k = 0;
@@ -667,7 +707,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         const bool obs_here = include_obs && r0 == 0;
         const int first_sim_slot = obs_here ? 1 : 0;
         CK(cudaMemsetAsync(h->counts.p, 0, 4 * (size_t)m * ncells, st), "memset");
-        if (obs_here) {
+        if (obs_here && obs_hit) {  // the resident index: its cell counts feed the scan
+            CK(cudaMemcpyAsync(h->counts.p, oc + oc_cnt, 4 * (size_t)ncells,
+                               cudaMemcpyDeviceToDevice, st),
+               "copy");
+        } else if (obs_here) {
             CK(cudaMemcpyAsync(h->ux.p, h->d_x, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
             CK(cudaMemcpyAsync(h->uy.p, h->d_y, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
             CK(cudaMemcpyAsync(h->ut.p, h->d_t, 8 * n, cudaMemcpyDeviceToDevice, st), "copy");
@@ -723,17 +767,40 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         CK(launch_exclusive_scan(as<uint32_t>(h->counts), as<uint32_t>(h->start),
                                  (int64_t)m * ncells, as<uint32_t>(h->scan_tmp), tmp_words, st),
            "cell scan");
-        CK(launch_scatter(m, n, g, as<double>(h->ux), as<double>(h->uy), as<double>(h->ut),
-                          as<uint32_t>(h->key), as<uint32_t>(h->rank), as<uint32_t>(h->start),
-                          (cross || (obs_here && centre_mode)) ? as<uint8_t>(h->mask_in)
-                                                               : nullptr,
-                          as<double>(h->X), as<double>(h->Y), as<double>(h->T),
-                          as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
-                          h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs,
-                          as<float>(h->F), filter_stride(n), st, poly,
-                          cross, inh ? as<double>(h->uh) : nullptr,
-                          inh ? as<double>(h->Hs) : nullptr),
-           "scatter");
+        // with the resident index the observed slot is copied, not scattered
+        const int s0 = (obs_here && obs_hit) ? 1 : 0;
+        const int64_t so = (int64_t)s0 * n;
+        if (m > s0)
+            CK(launch_scatter(m - s0, n, g, as<double>(h->ux) + so, as<double>(h->uy) + so,
+                              as<double>(h->ut) + so, as<uint32_t>(h->key) + so,
+                              as<uint32_t>(h->rank) + so, as<uint32_t>(h->start),
+                              (cross || (obs_here && centre_mode)) ? as<uint8_t>(h->mask_in)
+                                                                   : nullptr,
+                              as<double>(h->X), as<double>(h->Y), as<double>(h->T),
+                              as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
+                              h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs,
+                              as<float>(h->F), nF, st, poly, cross,
+                              inh ? as<double>(h->uh) + so : nullptr,
+                              inh ? as<double>(h->Hs) : nullptr, s0),
+               "scatter");
+        if (obs_here && (obs_hit || obs_cacheable)) {
+            // slot 0 <- resident index (hit), or resident index <- slot 0 (miss: fill it)
+            struct Span {
+                void* slot;
+                size_t off, bytes;
+            } sp[6] = {{h->X.p, oc_x, 8 * (size_t)n},       {h->Y.p, oc_y, 8 * (size_t)n},
+                       {h->T.p, oc_t, 8 * (size_t)n},       {h->P.p, oc_p, 32 * (size_t)n},
+                       {h->Plo.p, oc_lo, 8 * (size_t)n},    {h->F.p, oc_f, 12 * (size_t)nF}};
+            for (const Span& q2 : sp) {
+                void* dst = obs_hit ? q2.slot : (void*)(oc + q2.off);
+                const void* src = obs_hit ? (const void*)(oc + q2.off) : q2.slot;
+                CK(cudaMemcpyAsync(dst, src, q2.bytes, cudaMemcpyDeviceToDevice, st), "copy");
+            }
+            if (!obs_hit)
+                CK(cudaMemcpyAsync(oc + oc_cnt, h->counts.p, 4 * (size_t)ncells,
+                                   cudaMemcpyDeviceToDevice, st),
+                   "copy");
+        }
         CK(launch_cell_starts(m, n, ncells, as<uint32_t>(h->start), as<uint32_t>(h->cell_start),
                               st),
            "cell starts");
@@ -787,7 +854,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             CK(launch_pair_fp32(*h->h_pc, as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
                                 h->h_pc->edge != 0, smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, xq, st),
+                                as<uint32_t>(h->counter), acc, xq, st, staged),
                "pair kernel (FP32)");
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
@@ -841,7 +908,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
                               q->sim_method, inh, (int64_t)h->inh_gen, nsec, q->shard_count,
-                              q->shard_index};
+                              q->shard_index, staged, obs_hit, obs_cacheable};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -853,7 +920,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               h->oS.p, h->oC.p, h->xq_e.p, h->xq_count.p, h->simseed.p,
                               h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
                               (void*)h->ev0, (void*)h->ev1, (void*)st, h->uh.p, h->Hs.p,
-                              h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p, h->F.p};
+                              h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p, h->F.p,
+                              h->obs.p};
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
@@ -898,9 +966,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event timing");
         ms_pair += ms;
         ++waves;
-        launches += (obs_here ? 1 : 0) + (m > first_sim_slot ? 1 : 0) +
+        launches += (obs_here && !obs_hit ? 1 : 0) + (m > first_sim_slot ? 1 : 0) +
                     scan_launches((int64_t)m * ncells) + scan_launches((int64_t)m * nrows + 1) +
-                    4 /* scatter, starts, counts, fill */ +
+                    4 /* scatter, starts, counts, fill */ -
+                    (obs_here && obs_hit && m == 1 ? 1 : 0) /* no scatter */ +
                     2 /* pair, finalize */ + (fp32 ? 1 : 0) /* FP64 queue */;
     }
     if (use_graph && !replay) h->gkey = key;
@@ -942,6 +1011,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.graph_replays = replays;
     h->last_rows = R;
     h->last_nbins = nbins;
+    if (obs_cacheable && !obs_hit) h->obs_key = okey;
+    h->last.obs_index_reused = obs_hit ? 1 : 0;
     h->last.ms_total =
         std::chrono::duration<double, std::milli>(clock::now() - t_start).count();
     log_job(h, q, nsec);
@@ -1009,6 +1080,8 @@ size_t handle_workspace_bytes(const stk_handle* h) { return workspace_bytes(h); 
 
 void handle_trim(stk_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
+    free_buf(h->obs);
+    h->obs_key.clear();
     DevBuf* bufs[] = {&h->xq_e, &h->xq_count, &h->ux, &h->uy, &h->ut, &h->key, &h->rank,
                       &h->counts, &h->start, &h->scan_tmp, &h->X, &h->Y, &h->T, &h->P,
                       &h->Plo, &h->cell_start, &h->chunks, &h->chunk_off, &h->items,
@@ -1767,7 +1840,7 @@ void stk_destroy(stk_handle* h) {
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
-                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA, &h->F};
+                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA, &h->F, &h->obs};
     for (DevBuf* b : bufs) free_buf(*b);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_y) cudaFree(h->d_y);

@@ -257,7 +257,9 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
                            float* F, int64_t nF, cudaStream_t st, Polygon poly = Polygon(),
                            bool mask_all = false, const double* h_in = nullptr,
-                           double* H = nullptr);
+                           double* H = nullptr, int slot0 = 0);
+// (slot0: the m realizations scattered are slots slot0 .. slot0 + m - 1 of the sorted arrays;
+// the inputs x, y, t, key, rank, mask_in and h_in start at slot slot0's points)
 // floats per realization and axis of the filter's coordinate arrays (n plus padding for the
 // last four-point load, a multiple of 4 so that every axis starts 16-byte aligned)
 inline int64_t filter_stride(int64_t n) { return (n + 8 + 3) & ~int64_t(3); }
@@ -270,11 +272,15 @@ cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
 cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
                              const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
 // hpc: host copy of *d_pc, passed by value (its scalars are read from the constant bank)
+// staged: the filter variant that bulk-copies row runs to shared memory (even thresholds,
+// isotropic correction, rectangle, plain estimator only)
 cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool even, bool edge,
                              size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
-                             ExactQueue xq, cudaStream_t st);
+                             ExactQueue xq, cudaStream_t st, bool staged = false);
+size_t stage_bytes();
+int pair_fp32_tma_blocks_per_sm(size_t smem);
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
                          ExactQueue xq, cudaStream_t st, bool poly = false, bool dir = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
