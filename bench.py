@@ -469,24 +469,6 @@ def run_ours(args):
                                   "p99_rel_err_K": float(np.quantile(rel, 0.99)),
                                   "median_rel_err_K": float(np.median(rel))}}
 
-    # the filter variant that stages row runs in shared memory with bulk copies (TMA), timed on
-    # the same job against the default filter (reads through L1)
-    staging = None
-    if args.staged and rank == 0:
-        times = {}
-        for name, flag in (("default_l1", "0"), ("bulk_staged", "1")):
-            os.environ["STK_FILTER_STAGED"] = flag
-            stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec, exec_mode=exec_mode)
-            ms = []
-            for _ in range(2):
-                stk.stk_run(h, w.s, w.tt, n_sims=w.n_sims, seed=seed, prec=prec,
-                            exec_mode=exec_mode)
-                ms.append(stk.stk_last_stats(h)["ms_pair"])
-            times[name] = min(ms)
-        os.environ.pop("STK_FILTER_STAGED", None)
-        staging = {"pair_kernel_ms": times,
-                   "staged_over_default": times["bulk_staged"] / times["default_l1"]}
-
     serve = serve_bench(args, stk) if (args.serve_requests > 0 and rank == 0) else None
 
     # the other two simulation methods of Section 3 on the same job shape
@@ -640,7 +622,6 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "plain_fp64": plain,
-        "filter_staging": staging,
         "serve": serve,
         "sim_methods": methods,
         "polygon": polygon,
@@ -681,8 +662,6 @@ def build_parser():
                     help="also time a job over an 85-vertex polygon study area")
     ap.add_argument("--inhom", type=int, default=1,
                     help="also time an inhomogeneous-K job (intensity-weighted, FP64)")
-    ap.add_argument("--staged", type=int, default=1,
-                    help="also time the job with the bulk-staged filter variant")
     ap.add_argument("--directional", type=int, default=1,
                     help="also time a directional-K job (8 sectors, translation correction)")
     return ap

@@ -409,81 +409,6 @@ struct Smem32 {
 };
 
 constexpr uint32_t kTileUnits = 2 * kWarps;  // consecutive units a block claims at once
-
-// ---------------------------------------------------------------- bulk staging of row runs
-//
-// Alternative filter source (pair_fp32_kernel<..., TMA = true>): each warp copies the row runs
-// of the three filter arrays into shared memory with 1-D bulk copies (cp.async.bulk, one lane
-// issues them, completion counted in bytes on an mbarrier), in chunks of kStage points, double
-// buffered and prefetched across rows, and the filter reads the chunks from shared memory.
-// No cluster multicast: every copy is this GPU's global memory into the issuing CTA.
-constexpr uint32_t kStage = 192;          // points per chunk (a multiple of 4: 16-byte copies)
-constexpr int kStageSpin = 1 << 18;       // bound on the polls of one chunk's barrier
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// The issuing lane's arrival, announcing `bytes` of bulk-copy completions for this phase.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-        ::"r"(smem_addr(bar)), "r"(bytes)
-        : "memory");
-}
-
-// 1-D bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
-// this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar) {
-    uint64_t gsrc;
-    asm("cvta.to.global.u64 %0, %1;" : "=l"(gsrc) : "l"(src));
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_addr(dst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Orders this thread's earlier shared-memory reads before later bulk writes into the buffer.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Lane 0 of a warp bulk-copies points [c, e) (c and e multiples of 4, e - c <= kStage) of the
-// three filter arrays into the warp's staging buffer b (3 x kStage floats), completing on that
-// buffer's mbarrier.  The warp's lanes are done reading the buffer (a __syncwarp before).
-__device__ __forceinline__ void stage_issue(float* stage, uint64_t* bars, const float* nx,
-                                            const float* ny, const float* nt, uint32_t c,
-                                            uint32_t e, uint32_t b, int lane, bool ok) {
-    if (lane != 0 || !ok) return;
-    const uint32_t bytes = (e - c) * (uint32_t)sizeof(float);
-    float* dst = stage + (size_t)b * 3 * kStage;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[b], 3u * bytes);
-    bulk_copy_g2s(dst, nx + c, bytes, &bars[b]);
-    bulk_copy_g2s(dst + kStage, ny + c, bytes, &bars[b]);
-    bulk_copy_g2s(dst + 2 * kStage, nt + c, bytes, &bars[b]);
-}
 constexpr uint32_t kNoUnit = 0xffffffffu;
 constexpr int kSpinLimit = 1 << 20;
 
@@ -534,45 +459,6 @@ __device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32
         }
     }
     return __shfl_sync(0xffffffffu, ui, 0);
-}
-
-// A run of neighbour candidates of a unit: grid row (dt, dy) relative to the centres' row, its
-// cells from the window's first (the own row: from the first centre's cell) to wb, as the
-// contiguous sorted indices [jstart, J1) (the own row: after the unit's first centre).
-struct RowRun {
-    int dt, dy;
-    uint32_t jstart, J1;
-    bool valid;
-};
-
-// The first row at or after (dt, dy), in key order (dt = 0: dy = 0 .. fs; dt > 0: dy = -fs ..
-// fs), that lies in the grid and holds candidates for the unit.
-__device__ __forceinline__ RowRun find_run(int dt, int dy, int cy, int ct, int cxa, int wb,
-                                           int fs, int ft, int nx, int ny, int nt,
-                                           const uint32_t* __restrict__ cs, uint32_t c_begin) {
-    RowRun r;
-    r.valid = false;
-    for (; dt <= ft; ++dt, dy = -fs) {
-        const int rt = ct + dt;
-        if (rt >= nt) break;
-        for (; dy <= fs; ++dy) {
-            const int ry = cy + dy;
-            if (ry < 0 || ry >= ny) continue;
-            const bool own = (dt == 0) & (dy == 0);
-            const int wa = own ? cxa : max(0, cxa - fs);
-            const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
-            const uint32_t J1 = cs[rowkey + wb + 1];
-            const uint32_t js = own ? c_begin + 1u : cs[rowkey + wa];
-            if (js >= J1) continue;
-            r.dt = dt;
-            r.dy = dy;
-            r.jstart = js;
-            r.J1 = J1;
-            r.valid = true;
-            return r;
-        }
-    }
-    return r;
 }
 
 struct WarpCtx {
@@ -1097,7 +983,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
 }
 
-template <bool EVEN, bool EDGE, bool POLY, int VAR, bool TMA = false>
+template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __global__ void __launch_bounds__(kBlock, 2)
 pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
                  int m, RealBatch rb,
@@ -1124,24 +1010,6 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
     unsigned long long* hw = hf + (size_t)reps * nbins;
     uint32_t* hc = reinterpret_cast<uint32_t*>(VAR == kVarInh ? hw + (size_t)reps * nbins : hf);
     uint32_t* hh = hc + (size_t)reps * nbins;
-    // bulk staging (TMA): per warp 2 buffers x 3 axes x kStage floats, then 2 mbarriers per
-    // warp, after the histograms (plain estimator: 16 bytes per bin and replica)
-    float* stage = nullptr;
-    uint64_t* bars = nullptr;
-    uint32_t sb = 0, sphase = 0;  // buffer being filled or read next; parity per buffer
-    bool stage_ok = true;
-    if (TMA) {
-        const size_t off = (hist_off + (size_t)reps * nbins * 16 + 15) & ~size_t(15);
-        stage = reinterpret_cast<float*>(smem_raw + off) + (size_t)warp * 6 * kStage;
-        bars = reinterpret_cast<uint64_t*>(smem_raw + off +
-                                           (size_t)kWarps * 6 * kStage * sizeof(float)) +
-               2 * warp;
-        if (lane == 0) {
-            mbar_init(&bars[0], 1u);
-            mbar_init(&bars[1], 1u);
-            mbar_init_fence();
-        }
-    }
     for (int i = tid; i < reps * nbins; i += kBlock) {
         hc[i] = 0;
         he[i] = 0;
@@ -1231,75 +1099,36 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             // rows from the centres' own row onward in key order (t major, y minor); the cells
             // wa .. wb of a row are one contiguous run of points in one coordinate frame (x
             // relative to the box, y and t relative to the row's cell origin), scanned four
-            // points at a time (with bulk staging: from chunks copied to shared memory, the next
-            // chunk of the run, or the first of the next run, in flight meanwhile)
-            RowRun rr = find_run(0, 0, cy, ct, cxa, wb, fs, ft, nx, ny, nt, cs, wi.c_begin);
-            if (TMA && rr.valid) {
-                const uint32_t c = rr.jstart & ~3u;
-                stage_issue(stage, bars, NXk, NYk, NTk, c, (min(c + kStage, rr.J1) + 3u) & ~3u,
-                            sb, lane, stage_ok);
-            }
-            while (rr.valid) {
-                const int dt = rr.dt, dy = rr.dy;
-                int ndt = dt, ndy = dy;
-                if (++ndy > fs) {
-                    ++ndt;
-                    ndy = -fs;
-                }
-                RowRun nxt;
-                nxt.valid = false;
-                if (TMA)
-                    nxt = find_run(ndt, ndy, cy, ct, cxa, wb, fs, ft, nx, ny, nt, cs, wi.c_begin);
-                const bool own = (dt == 0) & (dy == 0);
+            // points at a time
+            for (int dt = 0; dt <= ft; ++dt) {
+                const int rt = ct + dt;
+                if (rt >= nt) break;
                 const float tc = fmaf((float)(-dt), pc.g.cdq, p.z);
                 const float2 tc2 = make_float2(tc, tc);
-                const uint32_t jstart = rr.jstart, J1 = rr.J1;
-                // first index this lane may pair with; from jfull on no lane's bound binds
-                const uint32_t jmin = own ? myi + 1u : jstart;
-                const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
-                const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
-                const float2 yc2 = make_float2(yc, yc);
-                const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
-                if (valid && J1 > jmin) n_cand += J1 - jmin;
-                since_flush += 32ull * (J1 - jstart);
-                // one chunk per run without staging
-                const uint32_t K = TMA ? kStage : 0x7fffffffu;
-                for (uint32_t c0 = jstart & ~3u; c0 < J1; c0 += K) {
-                    const uint32_t c1 = min(c0 + K, J1);
-                    const float* sx = nullptr;
-                    if (TMA) {
-                        // prefetch the following chunk (of this run, else the next run) into the
-                        // other buffer, then wait for this one (bounded)
-                        if (c1 < J1) {
-                            stage_issue(stage, bars, NXk, NYk, NTk, c1,
-                                        (min(c1 + K, J1) + 3u) & ~3u, sb ^ 1u, lane, stage_ok);
-                        } else if (nxt.valid) {
-                            const uint32_t c = nxt.jstart & ~3u;
-                            stage_issue(stage, bars, NXk, NYk, NTk, c,
-                                        (min(c + K, nxt.J1) + 3u) & ~3u, sb ^ 1u, lane, stage_ok);
-                        }
-                        int spin = 0;
-                        while (stage_ok && !mbar_try_wait(&bars[sb], (sphase >> sb) & 1u)) {
-                            if (++spin > kStageSpin) {
-                                stage_ok = false;  // never expected: the job fails, no hang
-                                if (lane == 0) atomicAdd(&acc.stats[4], 1ull);
-                            }
-                        }
-                        sphase ^= 1u << sb;
-                        sx = stage + (size_t)sb * 3 * kStage;
-                    }
-                    for (uint32_t j = c0; j < c1; j += 4) {
+                for (int dy = (dt == 0 ? 0 : -fs); dy <= fs; ++dy) {
+                    const int ry = cy + dy;
+                    if (ry < 0 || ry >= ny) continue;
+                    const bool own = (dt == 0) & (dy == 0);
+                    // in the own row only neighbours after the centre (sorted index > myi),
+                    // all of them after the unit's first centre
+                    const int wa = own ? cxa : max(0, cxa - fs);
+                    const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
+                    const uint32_t J1 = cs[rowkey + wb + 1];
+                    const uint32_t jstart = own ? wi.c_begin + 1u : cs[rowkey + wa];
+                    if (jstart >= J1) continue;
+                    // first index this lane may pair with; from jfull on no lane's bound binds
+                    const uint32_t jmin = own ? myi + 1u : jstart;
+                    const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
+                    const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
+                    const float2 yc2 = make_float2(yc, yc);
+                    const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
+                    if (valid && J1 > jmin) n_cand += J1 - jmin;
+                    since_flush += 32ull * (J1 - jstart);
+                    for (uint32_t j = jstart & ~3u; j < J1; j += 4) {
                         // four consecutive neighbours per step, one float4 per axis
-                        float4 qx, qy, qt;
-                        if (TMA) {
-                            qx = *reinterpret_cast<const float4*>(sx + (j - c0));
-                            qy = *reinterpret_cast<const float4*>(sx + kStage + (j - c0));
-                            qt = *reinterpret_cast<const float4*>(sx + 2 * kStage + (j - c0));
-                        } else {
-                            qx = *reinterpret_cast<const float4*>(NXk + j);
-                            qy = *reinterpret_cast<const float4*>(NYk + j);
-                            qt = *reinterpret_cast<const float4*>(NTk + j);
-                        }
+                        const float4 qx = *reinterpret_cast<const float4*>(NXk + j);
+                        const float4 qy = *reinterpret_cast<const float4*>(NYk + j);
+                        const float4 qt = *reinterpret_cast<const float4*>(NTk + j);
                         const float2 dxa = __fadd2_rn(xc2, make_float2(qx.x, qx.y));
                         const float2 dxb = __fadd2_rn(xc2, make_float2(qx.z, qx.w));
                         const float2 dya = __fadd2_rn(yc2, make_float2(qy.x, qy.y));
@@ -1350,13 +1179,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                             head += (uint32_t)kDrain;
                         }
                     }
-                    if (TMA) {
-                        __syncwarp();  // every lane is done with buffer sb before its refill
-                        sb ^= 1u;
-                    }
                 }
-                rr = TMA ? nxt : find_run(ndt, ndy, cy, ct, cxa, wb, fs, ft, nx, ny, nt, cs,
-                                          wi.c_begin);
             }
             drain_all<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, tail, head, lane, lt, w);
             if (since_flush >= kWarpFlush) {
@@ -1711,14 +1534,6 @@ __global__ void envelope_kernel(int m, int nbins, int cs, int ct, const double* 
 
 size_t hist_bytes(int nbins, int reps) { return (size_t)reps * nbins * 16; }
 
-}  // namespace
-
-// Shared memory the bulk-staging filter adds per block: the warps' double buffers of three
-// axes and their two mbarriers (plus alignment).
-size_t stage_bytes() { return (size_t)kWarps * (6 * kStage * sizeof(float) + 16) + 16; }
-
-namespace {
-
 size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
     const size_t b = (base + 15) & ~size_t(15);
     int r = 8;
@@ -1777,10 +1592,6 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
     }
-    e = cudaFuncSetAttribute(pair_fp32_kernel<true, true, false, kVarPlain, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(smem32 + stage_bytes()));
-    if (e != cudaSuccess) return e;
     // inhomogeneous K: 32 bytes per bin and replica
     const size_t smem32_inh = std::max<size_t>(
         smem32, ((sizeof(Smem32) + 15) & ~size_t(15)) + (size_t)kMaxThr * kMaxThr * 32);
@@ -1808,15 +1619,6 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inh);
 }
 
-int pair_fp32_tma_blocks_per_sm(size_t smem) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &b, pair_fp32_kernel<true, true, false, kVarPlain, true>, kBlock,
-            smem + stage_bytes()) != cudaSuccess)
-        return 1;
-    return b > 0 ? b : 1;
-}
-
 int pair_fp32_blocks_per_sm(size_t smem) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false, kVarPlain>,
@@ -1841,7 +1643,7 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
-                             ExactQueue xq, cudaStream_t st, bool staged) {
+                             ExactQueue xq, cudaStream_t st) {
     const bool poly = edge && hpc.nv > 0;
     // directional K / translation correction and inhomogeneous K: their own instantiations
     const bool dir = hpc.nsec > 1 || hpc.edge == STK_EDGE_TRANSLATION;
@@ -1852,12 +1654,7 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
 #define STK_PAIR32(E, D, P) STK_PAIR32V(E, D, P, kVarPlain)
     if ((dir && (poly || inh)) || (inh && (poly || acc.whole == nullptr)))
         return cudaErrorInvalidValue;
-    if (staged && !(even && edge && !poly && !dir && !inh)) return cudaErrorInvalidValue;
-    if (staged)
-        pair_fp32_kernel<true, true, false, kVarPlain, true>
-            <<<grid, kBlock, smem + stage_bytes(), st>>>(hpc, d_pc, m, rb, units, unit_off,
-                                                         counters, acc, xq, reps);
-    else if (inh && even && edge)
+    if (inh && even && edge)
         STK_PAIR32V(true, true, false, kVarInh);
     else if (inh && even)
         STK_PAIR32V(true, false, false, kVarInh);

@@ -652,14 +652,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     int reps = fp32 ? h->reps32 : h->reps64;
     size_t smem = fp32 ? h->smem32 : h->smem64;
     if (inh) smem = fp32 ? pair_fp32_smem(nbins, &reps, true) : pair_fp64_smem(nbins, &reps, true);
-    // STK_FILTER_STAGED=1: the filter variant that bulk-copies row runs into shared memory
-    // (even thresholds, isotropic correction, rectangle, plain estimator)
-    const char* staged_env = getenv("STK_FILTER_STAGED");
-    const bool staged = fp32 && staged_env && atoi(staged_env) != 0 && h->h_pc->even_s &&
-                        h->h_pc->even_t && q->edge_mode == STK_EDGE_ISOTROPIC && h->nv == 0 &&
-                        !inh && !dir;
-    const int bps = fp32 ? (staged ? pair_fp32_tma_blocks_per_sm(smem) : pair_fp32_blocks_per_sm(smem))
-                         : pair_fp64_blocks_per_sm(smem, inh);
+    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem, inh);
     const int grid = bps * h->num_sms;
     float ms_pair = 0.0f;
     int waves = 0;
@@ -672,7 +665,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                  oc_t = oc_y + a256(8 * (size_t)n), oc_p = oc_t + a256(8 * (size_t)n),
                  oc_lo = oc_p + a256(32 * (size_t)n), oc_f = oc_lo + a256(8 * (size_t)n),
                  oc_end = oc_f + a256(12 * (size_t)nF);
-    bool obs_cacheable = include_obs && !use_mask && !inh;
+    // (STK_RESIDENT=0 rebuilds the index every job)
+    const char* resident_env = getenv("STK_RESIDENT");
+    bool obs_cacheable = include_obs && !use_mask && !inh &&
+                         !(resident_env && atoi(resident_env) == 0);
     std::vector<unsigned char> okey;
     if (obs_cacheable) {
         auto put = [&okey](const void* p, size_t b) {
@@ -854,7 +850,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             CK(launch_pair_fp32(*h->h_pc, as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
                                 h->h_pc->edge != 0, smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, xq, st, staged),
+                                as<uint32_t>(h->counter), acc, xq, st),
                "pair kernel (FP32)");
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
@@ -908,7 +904,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
                               q->sim_method, inh, (int64_t)h->inh_gen, nsec, q->shard_count,
-                              q->shard_index, staged, obs_hit, obs_cacheable};
+                              q->shard_index, obs_hit, obs_cacheable};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));

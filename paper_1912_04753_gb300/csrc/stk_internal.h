@@ -272,15 +272,11 @@ cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
 cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
                              const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
 // hpc: host copy of *d_pc, passed by value (its scalars are read from the constant bank)
-// staged: the filter variant that bulk-copies row runs to shared memory (even thresholds,
-// isotropic correction, rectangle, plain estimator only)
 cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool even, bool edge,
                              size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
-                             ExactQueue xq, cudaStream_t st, bool staged = false);
-size_t stage_bytes();
-int pair_fp32_tma_blocks_per_sm(size_t smem);
+                             ExactQueue xq, cudaStream_t st);
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
                          ExactQueue xq, cudaStream_t st, bool poly = false, bool dir = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,

@@ -35,6 +35,9 @@ def test_graph_replay_equals_direct_issue(stk, monkeypatch):
             monkeypatch.setenv("STK_GRAPHS", "1")
             first = p.run(s, tt, n_sims=7, seed=11, prec=prec, want_sims=True)
             assert p.stats()["graph_replays"] == 0  # captured, launched once
+            # the observed index is resident from now on: another graph, captured once more
+            p.run(s, tt, n_sims=7, seed=11, prec=prec, want_sims=True)
+            assert p.stats()["obs_index_reused"] == 1 and p.stats()["graph_replays"] == 0
             runs = {}
             for seed in (11, 12, 13):
                 runs[seed] = p.run(s, tt, n_sims=7, seed=seed, prec=prec, want_sims=True)
