@@ -384,19 +384,18 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
 // FP64 runs at 1/64 of the FP32 rate on this part: a handful of such pairs inside this
 // kernel would hold a whole warp for thousands of cycles.
 
-constexpr int kRing = 256;   // per-warp ring of candidate pairs (indices taken modulo kRing)
+constexpr int kRing = 192;   // per-warp queue of candidate pairs (linear, compacted on drain)
 constexpr int kDrain = 64;   // phase-B batch: two pairs per lane
 constexpr int kQ2 = 32 + 4 * 32;  // per-warp queue of orders needing the spatial weight:
                                   // under 32 left over + up to 4 orders per lane of a pass
-static_assert(kDrain - 1 + 4 * 32 <= kRing, "ring must hold a batch plus one step");
-static_assert((kRing & (kRing - 1)) == 0, "ring size must be a power of two");
+static_assert(kDrain - 1 + 4 * 32 <= kRing, "queue must hold a batch plus one step");
 
 struct WarpSm {
     float4 cen_a[32];   // x_hi (box frame), y_hi, t_hi (own cell frame), interior bound on d2
     float4 cen_b[32];   // x_lo (box frame), y_lo, e_x, e_y
     float cen_te[32];   // distance to the nearer end of the study period
     float cen_h[32];    // inhomogeneous K: h of the centres
-    uint4 ring[kRing];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
+    uint4 ring[kRing + 1];  // (d2 bits, u bits, meta, neighbour)  meta: lane | (fs + dcy) << 8,
                             // dcy = centre's y cell - neighbour's y cell
     uint2 q2[kQ2];      // (meta | order << 11 | vhalf << 12 | bin << 13, neighbour)
 };
@@ -647,10 +646,11 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
         // x: box-frame hi parts (exact difference) plus low parts; y: centre i moved into j's
-        // cell frame, hi part exact, lo part carrying the remainder.  The distance is the same
-        // for both orders.
+        // cell frame, hi part exact, the low parts' difference and the cell sides' remainder
+        // rounded once.  Both are exact negations of the offset taken the other way round, so
+        // the distance does not depend on which point of the pair is the centre.
         const float dxa = (ca.x + nxj) + (cb.x - lo.x);
-        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + fmaf(dcy, pc.g.chl, cb.y - lo.y);
         float ra, inv_r;
         radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
         const float ex = other ? pb.x : cb.z, ey = other ? pb.y : cb.w;
@@ -708,19 +708,18 @@ __device__ __forceinline__ void add_fix96f(float W, Fix96& f) {
     f.hi += m >> 32;
 }
 
-// Phase B for `cnt` (<= 64) ring entries starting at index `head` (modulo kRing): two per
-// lane, loaded together.
+// Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
 // VAR kVarDir: the directional K / translation correction (EDGE and POLY false); kVarInh: the
 // inhomogeneous K (POLY false).  Both take every pair's weights here.
 template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
-                                            uint32_t lt, WarpCtx& w, uint32_t head) {
+                                            uint32_t lt, WarpCtx& w) {
     const bool edge = EDGE && !w.deep;  // uniform
     uint4 e[2];
-    e[0] = ws.ring[(head + (uint32_t)lane) & (kRing - 1)];
-    e[1] = ws.ring[(head + 32u + (uint32_t)lane) & (kRing - 1)];
+    e[0] = ws.ring[lane];
+    e[1] = ws.ring[32 + lane];
     if (32 + lane >= cnt) e[1] = make_uint4(0u, 0u, 0u, 0u);  // stale slot: keep values sane
     float4 pj[2];
     if (edge) {  // neighbour's edge record (dense array: 16 bytes per point)
@@ -810,7 +809,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                             const float2 lo = w.Plok[j];
                             const float dxa = (ca.x + w.NX[j]) + (cb.x - lo.x);
                             const float dya = (fmaf(dcy, pc.g.chq, ca.y) + w.NY[j]) +
-                                              (fmaf(dcy, pc.g.chl, cb.y) - lo.y);
+                                              fmaf(dcy, pc.g.chl, cb.y - lo.y);
                             radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
                         }
                         const float e1 = fminf(ex[o], ey[o]), e2 = fmaxf(ex[o], ey[o]);
@@ -866,7 +865,7 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
             const float4 cb = ws.cen_b[cl];
             const float2 loj = w.Plok[j];
             float dx = (ca.x + w.NX[j]) + (cb.x - loj.x);
-            float dy = (fmaf(dcy, pc.g.chq, ca.y) + w.NY[j]) + (fmaf(dcy, pc.g.chl, cb.y) - loj.y);
+            float dy = (fmaf(dcy, pc.g.chq, ca.y) + w.NY[j]) + fmaf(dcy, pc.g.chl, cb.y - loj.y);
             int k = 0;
             bool und = false;
             if (pc.nsec > 1) {
@@ -960,15 +959,16 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
 template <bool EVEN, bool EDGE, bool POLY, int VAR>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
-                                          const ExactQueue& xq, uint32_t tail, uint32_t& head,
-                                          int lane, uint32_t lt, WarpCtx& w) {
-    while (tail != head) {
-        const uint32_t left = tail - head;
-        const int cnt = left < (uint32_t)kDrain ? (int)left : kDrain;
+                                          const ExactQueue& xq, uint32_t& tail, int lane,
+                                          uint32_t lt, WarpCtx& w) {
+    while (tail > 0) {
+        const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w, head);
+        drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
-        head += (uint32_t)cnt;
+        const uint32_t rest = tail - (uint32_t)cnt;
+        for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
+        tail = rest;
     }
     __syncwarp();
     if (w.q2n > 0) {
@@ -1095,7 +1095,7 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
             const float xcb = -NXk[myi];  // the centre's x in the box frame
             const float2 xc2 = make_float2(xcb, xcb);
             __syncwarp();
-            uint32_t tail = 0, head = 0;  // ring entries written and taken by phase B
+            uint32_t tail = 0;
             // rows from the centres' own row onward in key order (t major, y minor); the cells
             // wa .. wb of a row are one contiguous run of points in one coordinate frame (x
             // relative to the box, y and t relative to the row's cell origin), scanned four
@@ -1155,33 +1155,44 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
                         const uint32_t t2 = t1 + (uint32_t)__popc(m1);
                         const uint32_t t3 = t2 + (uint32_t)__popc(m2);
                         if (k0)
-                            ws.ring[(tail + __popc(m0 & lt)) & (kRing - 1)] =
+                            ws.ring[tail + __popc(m0 & lt)] =
                                 make_uint4(__float_as_uint(d2a.x), __float_as_uint(fabsf(dta.x)),
                                            meta, j);
                         if (k1)
-                            ws.ring[(t1 + __popc(m1 & lt)) & (kRing - 1)] =
+                            ws.ring[t1 + __popc(m1 & lt)] =
                                 make_uint4(__float_as_uint(d2a.y), __float_as_uint(fabsf(dta.y)),
                                            meta, j + 1);
                         if (k2)
-                            ws.ring[(t2 + __popc(m2 & lt)) & (kRing - 1)] =
+                            ws.ring[t2 + __popc(m2 & lt)] =
                                 make_uint4(__float_as_uint(d2b.x), __float_as_uint(fabsf(dtb.x)),
                                            meta, j + 2);
                         if (k3)
-                            ws.ring[(t3 + __popc(m3 & lt)) & (kRing - 1)] =
+                            ws.ring[t3 + __popc(m3 & lt)] =
                                 make_uint4(__float_as_uint(d2b.y), __float_as_uint(fabsf(dtb.y)),
                                            meta, j + 3);
                         tail = t3 + (uint32_t)__popc(m3);
-                        while (tail - head >= (uint32_t)kDrain) {
+                        while (tail >= (uint32_t)kDrain) {
                             __syncwarp();
                             drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, kDrain, lane,
-                                                               lt, w, head);
-                            __syncwarp();  // the batch is read before its slots are refilled
-                            head += (uint32_t)kDrain;
+                                                               lt, w);
+                            __syncwarp();
+                            const uint32_t rest = tail - kDrain;
+                            uint4 v[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if ((uint32_t)(lane + 32 * c) < rest)
+                                    v[c] = ws.ring[kDrain + lane + 32 * c];
+                            __syncwarp();
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
+                            __syncwarp();
+                            tail = rest;
                         }
                     }
                 }
             }
-            drain_all<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, tail, head, lane, lt, w);
+            drain_all<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
             if (since_flush >= kWarpFlush) {
                 if (VAR == kVarInh)
                     warp_flush_inh(k, nbins, w.hc, w.he, w.hf, w.hw, acc, lane);

@@ -226,8 +226,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
-              16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096 +
-              80 * un + 4 * ncells + 2048 /* resident observed index */;
+              16 * kMaxThr + 2 * un + ((size_t)1 << 16) * 16 + 4096;
     return f;
 }
 
@@ -533,6 +532,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const bool inh = h->inten.nix > 0;
     const Footprint fp = footprint(n, g, nbins, R, n_groups, fp32_path(h, q), inh);
     int m_w = 1;
+    size_t budget_job = 0;  // device bytes this job may hold (batched jobs)
     if (q->exec == STK_EXEC_BATCHED) {
         size_t budget = h->wave_budget;
         if (budget == 0) {
@@ -546,6 +546,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         if (fit < 1) fit = 1;
         const int64_t cap_idx = ((int64_t)1 << 31) / (n > 0 ? n : 1);  // 32-bit sorted offsets
         m_w = (int)std::min<int64_t>(std::min<int64_t>(fit, cap_idx > 0 ? cap_idx : 1), R);
+        budget_job = budget;
     }
     const int64_t mn = (int64_t)m_w * n;
     const int64_t mc = (int64_t)m_w * ncells;
@@ -680,6 +681,13 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         put(rc3, sizeof rc3);
         const void* pp[2] = {h->poly.p, (const void*)(intptr_t)h->nv};
         put(pp, sizeof pp);
+    }
+    // the resident index is kept only beside a job's workspace that leaves room for it
+    if (obs_cacheable && budget_job > 0 &&
+        fp.fixed + fp.per_real * (size_t)m_w + oc_end > budget_job) {
+        obs_cacheable = false;
+        free_buf(h->obs);
+        h->obs_key.clear();
     }
     const bool obs_hit = obs_cacheable && !h->obs_key.empty() && okey == h->obs_key &&
                          h->obs.bytes >= oc_end;

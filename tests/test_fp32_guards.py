@@ -80,7 +80,8 @@ def test_sector_guard_is_sound(n_sec, x0):
     dcy = (cyi - cyj).astype(f32)
     cwq_v, cwl_v = np.full(N, cwq, f32), np.full(N, cwl, f32)
     dx = ((hxi - hxj).astype(f32) + (lxi - lxj).astype(f32)).astype(f32)
-    dy = ((_fma32(dcy, cwq_v, hyi) - hyj).astype(f32) + (_fma32(dcy, cwl_v, lyi) - lyj)).astype(f32)
+    dy = ((_fma32(dcy, cwq_v, hyi) - hyj).astype(f32) +
+          _fma32(dcy, cwl_v, (lyi - lyj).astype(f32))).astype(f32)
     q = max(qX, qy)
     big = max(abs(x0), abs(x0 + W), abs(y0), abs(y0 + H))
     sec_g = f32(1.0e-6 * s_max + 1.0e-6 * q + 4.0e-16 * big + 1e-30)
@@ -158,3 +159,41 @@ def test_filter_distance_within_guard(x0, W, fs):
     assert (err <= 0.5 * G[keep]).all(), (err / G[keep]).max()
     # the x hi parts are exact FP32 multiples of qX over the whole box
     assert np.array_equal(hxi.astype(np.float64), np.rint((xi - x0) / qX) * qX)
+
+
+def test_accurate_offset_is_antisymmetric():
+    """The accurate offset of a pair (x: box-frame hi difference plus low difference; y: the
+    other point moved into the neighbour's cell frame, the low parts' difference and the cell
+    side's remainder rounded once) is the exact negation of the offset taken the other way
+    round, so a weight does not depend on which point of the pair the traversal makes the
+    centre (the counting sort does not fix the order of points inside a cell)."""
+    rng = np.random.default_rng(4)
+    N = 200_000
+    qX, qy = 2.0 ** -8, 2.0 ** -12
+    hxi, hxj = (rng.integers(0, 2**23, N) * qX).astype(f32), (rng.integers(0, 2**23, N) * qX).astype(f32)
+    lxi, lxj = (rng.uniform(-qX / 2, qX / 2, N)).astype(f32), (rng.uniform(-qX / 2, qX / 2, N)).astype(f32)
+    # close pairs across cell boundaries (the hi part of the offset is small), where the low
+    # parts decide the last bits
+    dcy = rng.integers(-3, 4, N).astype(f32)
+    chq = np.full(N, f32(2.0 ** 21 * qy / 4))
+    hyi = (rng.integers(0, 2**19, N) * qy).astype(f32)
+    hyj = (hyi.astype(np.float64) + dcy.astype(np.float64) * chq + rng.integers(-64, 65, N) * qy
+           ).astype(f32)
+    lyi, lyj = (rng.uniform(-qy / 2, qy / 2, N)).astype(f32), (rng.uniform(-qy / 2, qy / 2, N)).astype(f32)
+    chl = rng.uniform(-qy / 2, qy / 2, N).astype(f32)  # the cell side's remainder
+
+    def off(hxa, lxa, hya, lya, hxb, lxb, hyb, lyb, dc, fused=True):
+        dx = ((hxa + (-hxb)).astype(f32) + (lxa - lxb).astype(f32)).astype(f32)
+        lo = (_fma32(dc, chl, (lya - lyb).astype(f32)) if fused else
+              (_fma32(dc, chl, lya) - lyb).astype(f32))
+        dy = ((_fma32(dc, chq, hya) + (-hyb)).astype(f32) + lo).astype(f32)
+        return dx, dy
+
+    dx1, dy1 = off(hxi, lxi, hyi, lyi, hxj, lxj, hyj, lyj, dcy)
+    dx2, dy2 = off(hxj, lxj, hyj, lyj, hxi, lxi, hyi, lyi, -dcy)
+    assert np.array_equal(dx1, -dx2) and np.array_equal(dy1, -dy2)
+    # rounding the low part in two steps (each point's remainder moved separately) is not
+    # antisymmetric: the reason for the single rounding
+    _, e1 = off(hxi, lxi, hyi, lyi, hxj, lxj, hyj, lyj, dcy, fused=False)
+    _, e2 = off(hxj, lxj, hyj, lyj, hxi, lxi, hyi, lyi, -dcy, fused=False)
+    assert not np.array_equal(e1, -e2)
