@@ -318,14 +318,20 @@ def serve_bench(args, stk, seed=0):
                                  for i in range(0, len(reqs), max(1, len(reqs) // 20))][:20]
         out["slots"] = args.serve_slots
     # served = alone, bit for bit, on a sample of the heaviest stream's requests
-    same, checked = True, 0
+    same, counts, checked, worst = True, True, 0, 0.0
     for r, got in served_sample:
         d = datasets[r["dataset"]]
         with stk.Pattern(d.x, d.y, d.t, d.box) as p:
             alone = p.run(r["s"], r["tt"], n_sims=r["n_sims"], seed=r["seed"])
         same = same and all(np.array_equal(got[k], alone[k]) for k in alone)
+        counts = counts and np.array_equal(got["C"], alone["C"])
+        for k in ("K", "K_lo", "K_hi"):
+            if k in alone:
+                den = np.where(alone[k] == 0, 1.0, np.abs(alone[k]))
+                worst = max(worst, float((np.abs(got[k] - alone[k]) / den).max()))
         checked += 1
-    out["served_equals_alone"] = {"checked": checked, "identical": same}
+    out["served_equals_alone"] = {"checked": checked, "identical": same,
+                                  "counts_identical": counts, "max_rel_diff_K": worst}
     if args.serve_fp64 > 0:
         _, reqs = wl.serving_stream(args.serve_fp64, seed=seed, rate_hz=rates[0])
         handles = [stk.Pattern(d.x, d.y, d.t, d.box) for d in datasets]

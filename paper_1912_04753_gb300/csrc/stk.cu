@@ -264,7 +264,8 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 
-int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
+// The problem shape of a job, for the tuner's table.
+TuneKey tune_key(const stk_handle* h, const stk_request* q) {
     TuneKey key;
     memset(&key, 0, sizeof key);
     key.n = h->n;
@@ -275,6 +276,19 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
     key.edge = q->edge_mode;
     key.nsec = q->n_sectors;
     key.method = q->sim_method;
+    return key;
+}
+
+// The refinement tuned for this problem shape, if any (0: none yet).
+int tuned_lookup(const stk_handle* h, const stk_request* q) {
+    const TuneKey key = tune_key(h, q);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
+    const TuneKey key = tune_key(h, q);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -465,6 +479,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     if (tune) {
         rc = tuned_refinement(h, q, &f_req);
         if (rc) return rc;
+    } else if (f_req == 0 && q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0)) {
+        // a smaller job of a shape tuned before takes the same refinement, so that its grids
+        // do not depend on the jobs it shares a batch with (a served job equals it alone)
+        f_req = tuned_lookup(h, q);
     }
     if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
