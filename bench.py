@@ -41,7 +41,7 @@ OPS_PER_CANDIDATE = 8
 OPS_PER_QUALIFYING = 12
 # DRAM bytes (read + write) of the pair kernel per realization of the 2M-point mixture, from
 # one ncu capture of the kernel as built (2 realizations per launch there)
-PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 99.7e6}
+PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 130.2e6}
 
 
 def _workload(name, sims=None):
