@@ -617,6 +617,12 @@ def run_ours(args):
         "qualifying_pairs_per_step": qual // args.steps,
         "fp64_recomputed_per_step": st["fp64_recomputed"],
         "pair_kernel_ms_per_step": pair_ms / args.steps,
+        "launch_shape": {"grid_refinement": [st["grid_refinement"], st["grid_refinement_t"]],
+                         "tile_units": st["tile_units"], "blocks_per_sm": st["blocks_per_sm"],
+                         "chosen_by": ("environment" if any(
+                             os.environ.get(v) for v in ("STK_GRID_F", "STK_TILE_UNITS",
+                                                         "STK_BLOCKS_PER_SM"))
+                             else "launch-shape tuner (process-wide, per job shape)")},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"},

@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 #define STK_MAX_THRESHOLDS 64
+#define STK_MAX_FUSED_JOBS 256
 
 typedef struct stk_handle stk_handle;
 
@@ -247,9 +248,35 @@ typedef struct {
     int32_t grid_refinement_t; /* ft: grid cells of t_max/ft in time (1..3) */
     int32_t obs_index_reused;  /* 1: the observed pattern's sorted grid index was resident (the
                                   last job on h had the same grid), not rebuilt */
+    int32_t tile_units;        /* launch shape of the FP32 pair kernel: work units a block
+                                  claims at once (the refinement tuner's choice, else 16) */
+    int32_t blocks_per_sm;     /* resident blocks per SM of the pair kernel's launch (the FP32
+                                  kernel: 2, or 3 where the tuner chose its 85-register build) */
 } stk_stats;
 
 int stk_run(stk_handle* h, const stk_request* req, stk_result* res);
+
+/* Several jobs, each on its own handle (point set), whose FP32 pair kernels run as ONE
+ * persistent launch (the batched path of Section 3's envelope over small problems at once):
+ * job i is reqs[i] on hs[i] with results into results[i], exactly as stk_run(hs[i], &reqs[i],
+ * &results[i]) would compute them (bit for bit: the sums are exact fixed-point integers, and a
+ * job of this size takes its problem shape's tuned or planned grid either way).  Each job's
+ * simulation generation and grid index run on its handle's stream; the fused pair launch runs
+ * on hs[0]'s stream (or the first fused job's) once every index is built, with each job's
+ * constants, grid and accumulators taken from a per-job descriptor; each job's FP64 queue,
+ * finalisation and envelope follow on its own stream.  Jobs that cannot share the launch run
+ * alone, in order, after it: FP64 precision, the translation correction or sectors, labels, a
+ * centre mask, shards, a polygon or an intensity on the handle, more than 2e7
+ * point-realizations (n x (1 + n_sims)), or too large to fit one wave.  Jobs whose thresholds
+ * differ in kind (evenly spaced or not, edge correction or not) share one launch per kind.
+ * hs: njobs distinct handles (1 <= njobs <= STK_MAX_FUSED_JOBS); reqs, results: njobs each,
+ * caller-owned, result pointers as for stk_run.  pair_launches (may be NULL): pair-kernel
+ * launches the fused jobs took (1 when all share one kind).  Errors: STK_EINVAL (NULL arrays,
+ * a repeated handle, njobs or n_sims out of range, any request error of stk_run), STK_ENOMEM,
+ * STK_ECUDA, STK_EDOMAIN, STK_ETIMEOUT; on an error the jobs' results are unspecified and
+ * every handle remains usable. */
+int stk_run_fused(stk_handle* const* hs, const stk_request* reqs, stk_result* results, int njobs,
+                  int* pair_launches);
 
 /* ---- Partial results and their exact merge (multi-process jobs; Section 3, Eq. 2-4) ------
  * A job split across processes (realizations k in blocks via first_sim / n_sims, the observed

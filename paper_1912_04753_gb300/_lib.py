@@ -56,7 +56,8 @@ class stk_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_pair", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("internal_errors", ctypes.c_int64),
                 ("grid_refinement", ctypes.c_int32), ("graph_replays", ctypes.c_int32),
-                ("grid_refinement_t", ctypes.c_int32), ("obs_index_reused", ctypes.c_int32)]
+                ("grid_refinement_t", ctypes.c_int32), ("obs_index_reused", ctypes.c_int32),
+                ("tile_units", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 class stk_server_config(ctypes.Structure):
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
         "stk_k": ([_P, _P, i32, _P, i32, i32, i32, i32, _P, _P, _P, _P], i32),
         "stk_envelope": ([_P, _P, i32, _P, i32, i32, i32, i32, i32, u64, _P, _P, _P, _P], i32),
         "stk_run": ([_P, ctypes.POINTER(stk_request), ctypes.POINTER(stk_result)], i32),
+        "stk_run_fused": ([ctypes.POINTER(_P), ctypes.POINTER(stk_request),
+                           ctypes.POINTER(stk_result), i32, ctypes.POINTER(i32)], i32),
         "stk_last_stats": ([_P, ctypes.POINTER(stk_stats)], i32),
         "stk_last_accumulators": ([_P, i32, i32, _P], i32),
         "stk_merge_grids": ([_P, ctypes.POINTER(stk_request), _P, i32, _P, _P, _P, _P], i32),
@@ -251,6 +254,18 @@ def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
     """A whole job: observed grids plus the n_sims CSR envelope (and optionally every sim).
     With n_sectors > 1 (directional K) every grid is [n_sectors, cs, ct].  shard = (count,
     index) evaluates only that shard of the observed pattern's pairs (see stk_request)."""
+    q, keep, o, r, shape = _job(s, tt, n_sims, seed, edge_mode, prec, norm, exec_mode,
+                                centre_mask, want_sims, sim_method, first_sim, labels, cross,
+                                n_sectors, shard)
+    _check(load().stk_run(h, ctypes.byref(q), ctypes.byref(r)))
+    return _shaped(o, shape)
+
+
+def _job(s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC, prec=STK_PREC_FP32_GUARDED,
+         norm=STK_NORM_N_NM1, exec_mode=STK_EXEC_BATCHED, centre_mask=None, want_sims=False,
+         sim_method=STK_SIM_CSR, first_sim=0, labels=None, cross=(0, 0), n_sectors=0,
+         shard=(0, 0)):
+    """Request and result structures of one job, with the arrays they point to."""
     s, tt = _f64(s), _f64(tt)
     cs, ct = s.shape[0], tt.shape[0]
     grid = (n_sectors, cs, ct) if n_sectors > 1 else (cs, ct)
@@ -267,11 +282,29 @@ def stk_run(h, s, tt, n_sims=0, seed=0, edge_mode=STK_EDGE_ISOTROPIC,
     r = stk_result(_ptr(o["K"]), _ptr(o["L"]), _ptr(o["S"]), _ptr(o["C"]), _ptr(o.get("K_lo")),
                    _ptr(o.get("K_hi")), _ptr(o.get("L_lo")), _ptr(o.get("L_hi")),
                    _ptr(o.get("K_sims")), _ptr(o.get("C_sims")))
-    _check(load().stk_run(h, ctypes.byref(q), ctypes.byref(r)))
-    out = {}
-    for k, v in o.items():
-        out[k] = v.reshape((n_sims,) + grid) if k in ("K_sims", "C_sims") else v.reshape(grid)
-    return out
+    return q, keep, o, r, (n_sims, grid)
+
+
+def _shaped(o, shape):
+    n_sims, grid = shape
+    return {k: v.reshape((n_sims,) + grid) if k in ("K_sims", "C_sims") else v.reshape(grid)
+            for k, v in o.items()}
+
+
+def stk_run_fused(handles, jobs):
+    """Several jobs, job i on handles[i] (distinct point sets) with the keywords of stk_run in
+    the dict jobs[i] (s and tt included), their pair kernels in one persistent launch (see
+    stk_run_fused in stk.h).  Returns (list of result dicts as stk_run's, pair launches)."""
+    if len(handles) != len(jobs) or not handles:
+        raise ValueError("one job per handle, at least one")
+    built = [_job(**j) for j in jobs]
+    nj = len(built)
+    hs = (_P * nj)(*handles)
+    qs = (stk_request * nj)(*[b[0] for b in built])
+    rs = (stk_result * nj)(*[b[3] for b in built])
+    launches = ctypes.c_int32(0)
+    _check(load().stk_run_fused(hs, qs, rs, nj, ctypes.byref(launches)))
+    return [_shaped(b[2], b[4]) for b in built], int(launches.value)
 
 
 def stk_last_accumulators(h, row0=0, rows=1, n_sectors=0, cs=None, ct=None):

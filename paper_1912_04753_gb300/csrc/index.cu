@@ -412,32 +412,60 @@ struct ScatterGrid {
     int mask_all;  // role flags for every realization (indexed by the point's index in it)
 };
 
-__global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
-                               const double* __restrict__ x, const double* __restrict__ y,
-                               const double* __restrict__ t, const uint32_t* __restrict__ key,
-                               const uint32_t* __restrict__ rank,
-                               const uint32_t* __restrict__ start,
+// The counting sort's scatter in two passes.  Points arrive in random order, so writing each
+// per-point array at the point's sorted position is a store of 4-16 bytes into a random DRAM
+// sector for each of nine arrays, most of them partial sectors that the memory system merges
+// by read-modify-write.  Instead pass 1 moves each point as one 32-byte record (FP64
+// coordinates, cell key, index within its realization: one whole sector) to its sorted
+// position in a staging array, and pass 2 reads the records in sorted order and writes every
+// per-point array with coalesced stores.
+
+// Pass 1: inputs of slots slot0 .. slot0 + m - 1; the record of the point that goes to sorted
+// position pos lands at S[pos - slot0 * n] (two double2: (x, y) and (t, key | src << 32)).
+__global__ void stage_kernel(int m, int64_t n, int64_t ncells, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ t,
+                             const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                             const uint32_t* __restrict__ start, int slot0,
+                             double2* __restrict__ S) {
+    const int64_t total = n * (int64_t)m;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int kr = (int)(gi / n);
+        const int k = slot0 + kr;
+        const uint32_t kk = key[gi];
+        const int64_t q = (int64_t)start[(int64_t)k * ncells + kk] + rank[gi] - (int64_t)slot0 * n;
+        const uint32_t src = (uint32_t)(gi - (int64_t)kr * n);
+        const unsigned long long tag = (unsigned long long)kk | ((unsigned long long)src << 32);
+        S[2 * q] = make_double2(x[gi], y[gi]);
+        S[2 * q + 1] = make_double2(t[gi], __longlong_as_double((long long)tag));
+    }
+}
+
+// Pass 2: sorted position pos = slot0 * n + q of realization (slot) k = pos / n.
+// P holds two float4 per point, the coordinate record (x_hi, y_hi, t_hi, cell x) in the
+// first half of the realization's [2n] and the edge record (e_x, e_y, e_t, rin2) in the
+// second: distances to the nearer x edge, y edge and end of the period, and a bound on d2
+// below which the circle around the point stays clear of every edge (interior: weight 1).
+// Plo holds (x - x0 - X_hi, y_lo): x's remainder below the filter's box-frame hi part
+// X_hi, and y's below its cell-frame hi part.  The role flags and h of a point come from its
+// input slot (index src within the realization).
+__global__ void records_kernel(int m, int64_t n, ScatterGrid g, const double2* __restrict__ S,
                                const uint8_t* __restrict__ mask_in, double* __restrict__ X,
                                double* __restrict__ Y, double* __restrict__ T,
                                float4* __restrict__ P, float2* __restrict__ Plo,
                                uint8_t* __restrict__ mask_out,
                                const double* __restrict__ h_in, double* __restrict__ H,
                                float* __restrict__ F, int slot0) {
-    // P holds two float4 per point, the coordinate record (x_hi, y_hi, t_hi, cell x) in the
-    // first half of the realization's [2n] and the edge record (e_x, e_y, e_t, rin2) in the
-    // second: distances to the nearer x edge, y edge and end of the period, and a bound on d2
-    // below which the circle around the point stays clear of every edge (interior: weight 1).
-    // Plo holds (x - x0 - X_hi, y_lo): x's remainder below the filter's box-frame hi part
-    // X_hi, and y's below its cell-frame hi part.
     const int64_t total = n * (int64_t)m;
-    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
-         gi += (int64_t)gridDim.x * blockDim.x) {
-        // inputs are those of slots slot0 .. slot0 + m - 1 (outputs: their slots)
-        const int kr = (int)(gi / n);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int kr = (int)(q / n);
         const int k = slot0 + kr;
-        const uint32_t kk = key[gi];
-        const int64_t pos = (int64_t)start[(int64_t)k * ncells + kk] + rank[gi];
-        const double xi = x[gi], yi = y[gi], ti = t[gi];
+        const int64_t pos = (int64_t)slot0 * n + q;
+        const double2 r0 = S[2 * q], r1 = S[2 * q + 1];
+        const double xi = r0.x, yi = r0.y, ti = r1.x;
+        const unsigned long long tag = (unsigned long long)__double_as_longlong(r1.y);
+        const uint32_t kk = (uint32_t)tag, src = (uint32_t)(tag >> 32);
         X[pos] = xi;
         Y[pos] = yi;
         T[pos] = ti;
@@ -481,8 +509,8 @@ __global__ void scatter_kernel(int m, int64_t n, int64_t ncells, ScatterGrid g,
         rin = fmaxf(rin, 0.0f);
         Pr[n + local] = make_float4(ex, ey, te, rin * rin * 0.99999f);
         Plo[pos] = make_float2((float)(oX - hX), (float)(oy - hy));
-        if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[gi - (int64_t)kr * n];
-        if (H) H[pos] = h_in[gi];
+        if (mask_out && (g.mask_all || k == 0)) mask_out[pos] = mask_in[src];
+        if (H) H[pos] = h_in[(int64_t)kr * n + src];
     }
 }
 
@@ -642,8 +670,9 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in, double* X,
                            double* Y, double* T, float4* P, float2* Plo, uint8_t* mask_out,
                            float tan_rel, float tan_abs, float fast_abs, float* F, int64_t nF,
-                           cudaStream_t st, Polygon poly, bool mask_all, const double* h_in,
-                           double* H, int slot0) {
+                           double2* stage, cudaStream_t st, Polygon poly, bool mask_all,
+                           const double* h_in, double* H, int slot0) {
+    if (stage == nullptr) return cudaErrorInvalidValue;
     ScatterGrid s;
     s.qX = g.qX;
     s.inv_qX = 1.0 / (double)g.qX;
@@ -670,9 +699,11 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
     s.inv_qx = 1.0 / (double)g.qx;
     s.inv_qy = 1.0 / (double)g.qy;
     s.inv_qt = 1.0 / (double)g.qt;
-    scatter_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
-        m, n, g.ncells, s, x, y, t, key, rank, start_global, mask_in, X, Y, T, P, Plo,
-        mask_in ? mask_out : nullptr, h_in, h_in ? H : nullptr, F, slot0);
+    stage_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        m, n, g.ncells, x, y, t, key, rank, start_global, slot0, stage);
+    records_kernel<<<grid_for(n * (int64_t)m, kThreads), kThreads, 0, st>>>(
+        m, n, s, stage, mask_in, X, Y, T, P, Plo, mask_in ? mask_out : nullptr, h_in,
+        h_in ? H : nullptr, F, slot0);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,7 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
     float4* P = cv.take<float4>(2 * (n + 8));
     float2* Plo = cv.take<float2>(n);
     float* F = cv.take<float>(3 * filter_stride(n));
+    double2* stage = cv.take<double2>(2 * n);
     uint32_t* cell_start = cv.take<uint32_t>(ncells + 1);
     uint32_t* ucount = cv.take<uint32_t>(nrows + 1);
     uint32_t* uoff = cv.take<uint32_t>(nrows + 1);
@@ -177,7 +178,8 @@ extern "C" int stk_k_noalloc(const double* d_x, const double* d_y, const double*
                             reinterpret_cast<int*>(stats + 3), st), "cell keys");
     NK(launch_exclusive_scan(counts, start, ncells, scan_tmp, tmp_words, st), "cell scan");
     NK(launch_scatter(1, n, g, d_x, d_y, d_t, key, rank, start, nullptr, X, Y, T, P, Plo, nullptr,
-                      pc.tan_rel, pc.tan_abs, pc.fast_abs, F, filter_stride(n), st), "scatter");
+                      pc.tan_rel, pc.tan_abs, pc.fast_abs, F, filter_stride(n), stage, st),
+       "scatter");
     NK(launch_cell_starts(1, n, ncells, start, cell_start, st), "cell starts");
     NK(launch_work_counts(1, g, cell_start, ucount, st), "work counts");
     NK(launch_exclusive_scan(ucount, uoff, nrows + 1, scan_tmp, tmp_words, st), "work scan");

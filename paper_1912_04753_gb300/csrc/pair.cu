@@ -82,7 +82,7 @@ __device__ __forceinline__ unsigned long long excess_fixed64(double w) {
 // centre i, and (j, i), with centre j.  d2 and u are the same for both orders (the FP64
 // difference of two numbers is exactly the negation of the reversed difference).  Returns
 // false when the pair does not qualify.
-template <bool POLY>
+template <bool POLY, int CALLER = 0>
 __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double yi, double ti,
                                         double xj, double yj, double tj, int& a, int& b,
                                         unsigned long long& exc_i, unsigned long long& exc_j) {
@@ -289,7 +289,7 @@ __device__ __forceinline__ double translation_weight(const PairConsts& pc, doubl
 // kVarDir: the directional / translation-corrected estimator (full entries only): the bin
 // takes the pair's sector, both orders the translation weight.  kVarInh: the inhomogeneous K
 // (full entries only): the weights of both orders times h_i h_j, returned in *fx.
-template <bool POLY, int VAR = kVarPlain>
+template <bool POLY, int VAR = kVarPlain, int CALLER = 0>
 __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch& rb, uint4 q,
                                            int& bin, uint32_t& counts,
                                            unsigned long long& exc, Fix96* fx = nullptr) {
@@ -299,7 +299,7 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
     if (VAR == kVarInh) {
         int a, b;
         unsigned long long ei, ej;
-        if (!pair_exact<false>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
+        if (!pair_exact<false, CALLER>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
         const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
         bin = a * pc.ct + b;
         counts = (uint32_t)act_i + (uint32_t)act_j;
@@ -341,7 +341,7 @@ __device__ __forceinline__ bool exact_eval(const PairConsts& pc, const RealBatch
     if ((q.w & 1u) == 0u) {
         int a, b;
         unsigned long long ei, ej;
-        if (!pair_exact<POLY>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
+        if (!pair_exact<POLY, CALLER>(pc, xi, yi, ti, xj, yj, tj, a, b, ei, ej)) return false;
         const bool act_i = (q.w >> 1) & 1u, act_j = (q.w >> 2) & 1u;
         bin = a * pc.ct + b;
         counts = (uint32_t)act_i + (uint32_t)act_j;
@@ -401,53 +401,52 @@ struct WarpSm {
 };
 
 struct Smem32 {
-    PairConsts pc;      // only the part before `s2` is copied
+    PairConsts pc;      // the single-job kernel copies only the part before `s2`
     WarpSm w[kWarps];
     unsigned long long cursor;  // (tile << 32) | next index in the tile, see next_unit
     // histograms follow (dynamic size)
 };
 
-constexpr uint32_t kTileUnits = 2 * kWarps;  // consecutive units a block claims at once
 constexpr uint32_t kNoUnit = 0xffffffffu;
 constexpr int kSpinLimit = 1 << 20;
 
 // Next work unit of the current realization for the calling warp, or kNoUnit when none is
-// left.  The block claims tiles of kTileUnits consecutive units (neighbouring centres of one
-// row, so its warps walk the same neighbour cells and share them in L1) from the
-// realization's global counter; its warps draw units from the current tile through a shared
-// cursor, with no block barrier, so a warp with a cheap unit never waits for one with a dear
-// unit.  The warp that draws index kTileUnits claims the next tile; warps that draw past it
-// wait (bounded) for the new tile.  Lane 0 works, the result is broadcast.
+// left.  The block claims tiles of `tile` consecutive units (neighbouring centres of one row,
+// so its warps walk the same neighbour cells and share them in L1; `ntiles` tiles in
+// [ubeg, uend)) from the realization's global counter; its warps draw units from the current
+// tile through a shared cursor, with no block barrier, so a warp with a cheap unit never waits
+// for one with a dear unit.  The warp that draws index `tile` claims the next tile; warps that
+// draw past it wait (bounded) for the new tile.  Lane 0 works, the result is broadcast.
 __device__ __forceinline__ uint32_t next_unit(unsigned long long* cursor, uint32_t* counter,
-                                              uint32_t ubeg, uint32_t uend, int lane,
+                                              uint32_t ubeg, uint32_t uend, uint32_t tile,
+                                              uint32_t ntiles, int lane,
                                               unsigned long long* stats, bool never_publish) {
     uint32_t ui = kNoUnit;
     if (lane == 0) {
-        const uint32_t ntiles = (uend - ubeg + kTileUnits - 1) / kTileUnits;
         int spin = 0;
         bool stuck = false;
         while (!stuck) {
             const unsigned long long old = atomicAdd(cursor, 1ull);
-            const uint32_t tile = (uint32_t)(old >> 32), idx = (uint32_t)old;
-            if (tile >= ntiles) break;
-            if (idx < kTileUnits) {
-                const uint32_t u = ubeg + tile * kTileUnits + idx;
+            const uint32_t t = (uint32_t)(old >> 32), idx = (uint32_t)old;  // tile index
+            if (t >= ntiles) break;
+            if (idx < tile) {
+                const uint32_t u = ubeg + t * tile + idx;
                 if (u < uend) {
                     ui = u;
                     break;
                 }
                 continue;  // past the end of the last tile: draw until someone claims anew
             }
-            if (idx == kTileUnits) {
+            if (idx == tile) {
                 if (never_publish) break;  // test hook: the waiting warps' waits run out
                 const uint32_t nt = atomicAdd(counter, 1u);
                 atomicExch(cursor, ((unsigned long long)nt << 32) | 1ull);  // index 0 is ours
                 if (nt >= ntiles) break;
-                ui = ubeg + nt * kTileUnits;  // < uend: nt < ntiles
+                ui = ubeg + nt * tile;  // < uend: nt < ntiles
                 break;
             }
             while ((uint32_t)(*reinterpret_cast<volatile unsigned long long*>(cursor) >> 32) ==
-                   tile) {
+                   t) {
                 if (++spin > kSpinLimit) {
                     atomicAdd(&stats[4], 1ull);  // never expected: the claimer is resident
                     stuck = true;
@@ -484,7 +483,10 @@ struct WarpCtx {
 };
 
 // Evaluates an entry in FP64 inside the pair kernel (only when the FP64 queue is full).
-template <bool POLY, int VAR = kVarPlain>
+// CALLER: 0 for the single-job kernels, 1 for the fused kernel, which gets its own instances of
+// the out-of-line helpers (a callee shared with the fused kernel changed the single-job
+// kernel's register allocation and cost it 2%).
+template <bool POLY, int VAR = kVarPlain, int CALLER = 0>
 __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, uint4 entry,
                                           uint32_t* hc, unsigned long long* he,
                                           unsigned long long* hf, unsigned long long* hw) {
@@ -492,7 +494,7 @@ __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, u
     uint32_t counts;
     unsigned long long exc;
     Fix96 f;
-    if (exact_eval<POLY, VAR>(*gpc, rb, entry, bin, counts, exc, &f)) {
+    if (exact_eval<POLY, VAR, CALLER>(*gpc, rb, entry, bin, counts, exc, &f)) {
         if (counts) atomicAdd(&hc[bin], counts);
         if (exc) atomicAdd(&he[bin], exc);
         if (VAR == kVarInh) {
@@ -505,7 +507,7 @@ __device__ __noinline__ void exact_inline(const PairConsts* gpc, RealBatch rb, u
 
 // Appends the flagged lanes' entries to the global FP64 queue.  If the queue is full the entry
 // is evaluated here instead (correct, only slower).
-template <bool POLY, int VAR = kVarPlain>
+template <bool POLY, int VAR = kVarPlain, int CALLER = 0>
 __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatch& rb,
                                            const ExactQueue& xq, bool flag, uint4 entry,
                                            int lane, uint32_t lt, uint32_t* hc,
@@ -522,7 +524,7 @@ __device__ __forceinline__ void push_exact(const PairConsts* gpc, const RealBatc
     if (idx < xq.cap)
         xq.e[idx] = entry;
     else
-        exact_inline<POLY, VAR>(gpc, rb, entry, hc, he, hf, hw);
+        exact_inline<POLY, VAR, CALLER>(gpc, rb, entry, hc, he, hf, hw);
 }
 
 // ---------------------------------------------------------------- FP32 isotropic weight
@@ -618,6 +620,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
 // Phase C: isotropic spatial weight for `cnt` (<= 32) entries of queue 2.  Out of line (it
 // runs once per 32 deferred orders) with scalar arguments, so that neither its registers nor
 // an address-taken copy of the warp state weigh on the filter loop.
+template <int CALLER = 0>
 __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairConsts* gpc,
                                            WarpSm* wsp, const float4* __restrict__ Ek,
                                            const float* __restrict__ NXk,
@@ -669,12 +672,13 @@ __device__ __noinline__ void drain_weights(const PairConsts* pcs, const PairCons
             if (exc) atomicAdd(&he[bin], exc);
         }
     }
-    push_exact<false>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
+    push_exact<false, kVarPlain, CALLER>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc,
+                                         he);
 }
 
 // Evaluates queue 2 in batches of 32 while it holds that many, and moves the rest (fewer than
 // 32) to its front.
-template <bool POLY>
+template <bool POLY, int CALLER = 0>
 __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
                                               const PairConsts* gpc, const RealBatch& rb,
                                               const ExactQueue& xq, int lane, WarpCtx& w) {
@@ -685,7 +689,7 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
             drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
+            drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
         off += 32;
     }
@@ -711,7 +715,7 @@ __device__ __forceinline__ void add_fix96f(float W, Fix96& f) {
 // Phase B for `cnt` (<= 64) ring entries starting at index 0: two per lane, loaded together.
 // VAR kVarDir: the directional K / translation correction (EDGE and POLY false); kVarInh: the
 // inhomogeneous K (POLY false).  Both take every pair's weights here.
-template <bool EVEN, bool EDGE, bool POLY, int VAR>
+template <bool EVEN, bool EDGE, bool POLY, int VAR, int CALLER = 0>
 __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairConsts* gpc,
                                             WarpSm& ws, const RealBatch& rb,
                                             const ExactQueue& xq, int cnt, int lane,
@@ -918,14 +922,14 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
         for (int r = 0; r < 2; ++r) {
             const uint32_t ci = w.c_begin + (e[r].z & 31u), j = e[r].w;
             if (edge) {
-                push_exact<POLY>(gpc, rb, xq, wi[r],
+                push_exact<POLY, kVarPlain, CALLER>(gpc, rb, xq, wi[r],
                            make_uint4(ci, j, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
                            w.hc, w.he);
-                push_exact<POLY>(gpc, rb, xq, wj[r],
+                push_exact<POLY, kVarPlain, CALLER>(gpc, rb, xq, wj[r],
                            make_uint4(j, ci, w.real, 1u | ((uint32_t)bin[r] << 2)), lane, lt,
                            w.hc, w.he);
             }
-            push_exact<POLY>(gpc, rb, xq, full[r],
+            push_exact<POLY, kVarPlain, CALLER>(gpc, rb, xq, full[r],
                        make_uint4(ci, j, w.real, ((uint32_t)ai[r] << 1) | ((uint32_t)aj[r] << 2)),
                        lane, lt, w.hc, w.he);
         }
@@ -950,13 +954,13 @@ __device__ __forceinline__ void drain_pairs(const PairConsts& pc, const PairCons
                 ws.q2[o3 + __popc(b3 & lt)] =
                     make_uint2(m1 | (1u << 11) | ((uint32_t)vj[1] << 12), e[1].w);
             w.q2n = o3 + __popc(b3);
-            if (w.q2n >= 32) flush_weights<POLY>(ws, pc, gpc, rb, xq, lane, w);
+            if (w.q2n >= 32) flush_weights<POLY, CALLER>(ws, pc, gpc, rb, xq, lane, w);
         }
     }
 }
 
 // Drains the warp's queues completely (end of a work unit: the centre data is replaced next).
-template <bool EVEN, bool EDGE, bool POLY, int VAR>
+template <bool EVEN, bool EDGE, bool POLY, int VAR, int CALLER = 0>
 __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts* gpc,
                                           WarpSm& ws, const RealBatch& rb,
                                           const ExactQueue& xq, uint32_t& tail, int lane,
@@ -964,7 +968,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     while (tail > 0) {
         const int cnt = tail < (uint32_t)kDrain ? (int)tail : kDrain;
         __syncwarp();
-        drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
+        drain_pairs<EVEN, EDGE, POLY, VAR, CALLER>(pc, gpc, ws, rb, xq, cnt, lane, lt, w);
         __syncwarp();
         const uint32_t rest = tail - (uint32_t)cnt;
         for (uint32_t i = lane; i < rest; i += 32) ws.ring[i] = ws.ring[cnt + i];
@@ -976,15 +980,22 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
             drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
                                w.c_begin);
         else
-            drain_weights(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
+            drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);
         w.q2n = 0;
     }
     __syncwarp();
 }
 
-template <bool EVEN, bool EDGE, bool POLY, int VAR>
-__global__ void __launch_bounds__(kBlock, 2)
+// One job's realizations [0, m) in a block of the FP32 pair kernel: pc is the job's constants
+// (the kernel parameters themselves in the single-job kernel, so that its scalars are
+// constant-bank operands; a shared-memory copy in the fused kernel), the shared Smem32's pc
+// holds at least the indexed tables and bands before `s2`.  Adds the job's candidate count to
+// acc.stats[0].
+// BPS: resident blocks per SM the register allocation is made for (2: 128 registers per
+// thread; 3: 85, the launch shape the tuner may choose for the plain rectangle kernels).
+template <bool EVEN, bool EDGE, bool POLY, int VAR, int BPS = 2>
+__global__ void __launch_bounds__(kBlock, BPS)
 pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __restrict__ gpc,
                  int m, RealBatch rb,
                  const WorkItem* __restrict__ units, const uint32_t* __restrict__ unit_off,
@@ -1000,217 +1011,57 @@ pair_fp32_kernel(const __grid_constant__ PairConsts pk, const PairConsts* __rest
         for (int i = tid; i < words; i += kBlock) dst[i] = src[i];
     }
     __syncthreads();
-    WarpSm& ws = sm.w[warp];
-    const int nbins = pc.nbins;
-    const size_t hist_off = (sizeof(Smem32) + 15) & ~size_t(15);
-    // per replica: he [nbins] u64, then for the inhomogeneous K hf and hw [nbins] u64, then hc
-    // [nbins] u32 and (otherwise) hh [nbins] u32
-    unsigned long long* he = reinterpret_cast<unsigned long long*>(smem_raw + hist_off);
-    unsigned long long* hf = he + (size_t)reps * nbins;
-    unsigned long long* hw = hf + (size_t)reps * nbins;
-    uint32_t* hc = reinterpret_cast<uint32_t*>(VAR == kVarInh ? hw + (size_t)reps * nbins : hf);
-    uint32_t* hh = hc + (size_t)reps * nbins;
-    for (int i = tid; i < reps * nbins; i += kBlock) {
-        hc[i] = 0;
-        he[i] = 0;
-        if (VAR == kVarInh) {
-            hf[i] = 0;
-            hw[i] = 0;
-        } else {
-            hh[i] = 0;
-        }
-    }
-    WarpCtx w;
-    w.hc = hc + (warp % reps) * nbins;
-    w.hh = hh + (warp % reps) * nbins;
-    w.he = he + (warp % reps) * nbins;
-    w.hf = hf + (warp % reps) * nbins;
-    w.hw = hw + (warp % reps) * nbins;
-    w.H = nullptr;
-    w.Plok = nullptr;
-    w.q2n = 0;
-    w.deep = false;
-    w.pa = &sm.pc;
-    const int64_t n = rb.n;
-    const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
-    const int64_t nrows = (int64_t)ny * nt;
-    const uint32_t lt = (1u << lane) - 1u;
-    unsigned long long n_cand = 0;
-    uint64_t since_flush = 0;  // candidates this warp added since it last flushed (uniform)
-    __syncthreads();
+    constexpr int CALLER = 0;
+#include "pair_fp32_body.cuh"
+}
 
-    for (int k = 0; k < m; ++k) {
-        uint32_t ubeg = unit_off[(int64_t)k * nrows], uend = unit_off[(int64_t)(k + 1) * nrows];
-        shard_units(rb, unit_off, nrows, k, &ubeg, &uend);
-        const int64_t base = (int64_t)k * n;
-        const uint32_t* cs = rb.cell_start + (int64_t)k * (rb.ncells + 1);
-        const float4* Pk = rb.P + 2 * base;
-        w.Pk = Pk;
-        w.Ek = Pk + n;
-        w.NX = rb.F + (int64_t)k * 3 * rb.nF;
-        w.NY = w.NX + rb.nF;
-        w.real = (uint32_t)k;
-        w.Plok = rb.Plo + base;
-        if (VAR == kVarInh) w.H = rb.H + base;
-        w.mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
-                   ? rb.mask + (rb.mask_all ? base : 0)
-                   : nullptr;
-        if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
-        __syncthreads();
-        for (;;) {
-            const uint32_t ui = next_unit(&sm.cursor, &counters[k], ubeg, uend, lane, acc.stats,
-                                          pc.never_publish != 0);
-            if (ui == kNoUnit) break;
-            const WorkItem wi = units[ui];
-            w.c_begin = wi.c_begin;
-            const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
-            // centres: one per lane
-            const bool valid = lane < (int)wi.c_count;
-            const uint32_t myi = wi.c_begin + (valid ? lane : 0);
-            const float4 p = Pk[myi];
-            const float4 pe = w.Ek[myi];
-            const float2 plo = rb.Plo[base + myi];
-            const int cx = __float_as_int(p.w);
-            // x: the box-frame hi part (with plo.x its remainder); y, t: the cell frame
-            ws.cen_a[lane] = make_float4(-w.NX[myi], p.y, p.z, pe.w);
-            ws.cen_b[lane] = make_float4(plo.x, plo.y, pe.x, pe.y);
-            ws.cen_te[lane] = pe.z;
-            if (VAR == kVarInh) ws.cen_h[lane] = (float)w.H[myi];
-            const uint32_t fl = w.mk == nullptr ? 3u : (uint32_t)w.mk[myi];
-            w.onA = __ballot_sync(0xffffffffu, valid && (fl & 1u));
-            w.onB = __ballot_sync(0xffffffffu, valid && (fl & 2u));
-            const float cut2 = valid ? pc.s2_cut : -1.0f;  // idle lanes never qualify
-            const float ucut = pc.u_cut;
-            const int cxa = __reduce_min_sync(0xffffffffu, valid ? cx : 0x7fffffff);
-            const int cxb = __reduce_max_sync(0xffffffffu, valid ? cx : -1);
-            const int wb = min(nx - 1, cxb + fs);
-            // units whose whole neighbourhood is deep inside the box skip the weight logic
-            w.deep = EDGE && max(0, cxa - fs) >= pc.deep_x[0] && wb <= pc.deep_x[1] &&
-                     cy - fs >= pc.deep_y[0] && cy + fs <= pc.deep_y[1] &&
-                     ct >= pc.deep_t[0] && ct + ft <= pc.deep_t[1];
-            // the filter's copy of the coordinates (negated hi parts; x relative to the box)
-            const float* NXk = rb.F + (int64_t)k * 3 * rb.nF;
-            const float* NYk = NXk + rb.nF;
-            const float* NTk = NYk + rb.nF;
-            const float xcb = -NXk[myi];  // the centre's x in the box frame
-            const float2 xc2 = make_float2(xcb, xcb);
-            __syncwarp();
-            uint32_t tail = 0;
-            // rows from the centres' own row onward in key order (t major, y minor); the cells
-            // wa .. wb of a row are one contiguous run of points in one coordinate frame (x
-            // relative to the box, y and t relative to the row's cell origin), scanned four
-            // points at a time
-            for (int dt = 0; dt <= ft; ++dt) {
-                const int rt = ct + dt;
-                if (rt >= nt) break;
-                const float tc = fmaf((float)(-dt), pc.g.cdq, p.z);
-                const float2 tc2 = make_float2(tc, tc);
-                for (int dy = (dt == 0 ? 0 : -fs); dy <= fs; ++dy) {
-                    const int ry = cy + dy;
-                    if (ry < 0 || ry >= ny) continue;
-                    const bool own = (dt == 0) & (dy == 0);
-                    // in the own row only neighbours after the centre (sorted index > myi),
-                    // all of them after the unit's first centre
-                    const int wa = own ? cxa : max(0, cxa - fs);
-                    const int64_t rowkey = ((int64_t)rt * ny + ry) * nx;
-                    const uint32_t J1 = cs[rowkey + wb + 1];
-                    const uint32_t jstart = own ? wi.c_begin + 1u : cs[rowkey + wa];
-                    if (jstart >= J1) continue;
-                    // first index this lane may pair with; from jfull on no lane's bound binds
-                    const uint32_t jmin = own ? myi + 1u : jstart;
-                    const uint32_t jfull = own ? wi.c_begin + (uint32_t)kUnit : jstart;
-                    const float yc = fmaf((float)(-dy), pc.g.chq, p.y);
-                    const float2 yc2 = make_float2(yc, yc);
-                    const uint32_t meta = (uint32_t)lane | ((uint32_t)(fs - dy) << 8);
-                    if (valid && J1 > jmin) n_cand += J1 - jmin;
-                    since_flush += 32ull * (J1 - jstart);
-                    for (uint32_t j = jstart & ~3u; j < J1; j += 4) {
-                        // four consecutive neighbours per step, one float4 per axis
-                        const float4 qx = *reinterpret_cast<const float4*>(NXk + j);
-                        const float4 qy = *reinterpret_cast<const float4*>(NYk + j);
-                        const float4 qt = *reinterpret_cast<const float4*>(NTk + j);
-                        const float2 dxa = __fadd2_rn(xc2, make_float2(qx.x, qx.y));
-                        const float2 dxb = __fadd2_rn(xc2, make_float2(qx.z, qx.w));
-                        const float2 dya = __fadd2_rn(yc2, make_float2(qy.x, qy.y));
-                        const float2 dyb = __fadd2_rn(yc2, make_float2(qy.z, qy.w));
-                        const float2 dta = __fadd2_rn(tc2, make_float2(qt.x, qt.y));
-                        const float2 dtb = __fadd2_rn(tc2, make_float2(qt.z, qt.w));
-                        const float2 d2a = __ffma2_rn(dxa, dxa, __fmul2_rn(dya, dya));
-                        const float2 d2b = __ffma2_rn(dxb, dxb, __fmul2_rn(dyb, dyb));
-                        bool k0 = (d2a.x <= cut2) & (fabsf(dta.x) <= ucut);
-                        bool k1 = (d2a.y <= cut2) & (fabsf(dta.y) <= ucut);
-                        bool k2 = (d2b.x <= cut2) & (fabsf(dtb.x) <= ucut);
-                        bool k3 = (d2b.y <= cut2) & (fabsf(dtb.y) <= ucut);
-                        if (j < jfull || j + 4u > J1) {  // the ends of the run
-                            k0 &= (j >= jmin) & (j < J1);
-                            k1 &= (j + 1u >= jmin) & (j + 1u < J1);
-                            k2 &= (j + 2u >= jmin) & (j + 2u < J1);
-                            k3 &= (j + 3u >= jmin) & (j + 3u < J1);
-                        }
-                        const uint32_t m0 = __ballot_sync(0xffffffffu, k0);
-                        const uint32_t m1 = __ballot_sync(0xffffffffu, k1);
-                        const uint32_t m2 = __ballot_sync(0xffffffffu, k2);
-                        const uint32_t m3 = __ballot_sync(0xffffffffu, k3);
-                        const uint32_t t1 = tail + (uint32_t)__popc(m0);
-                        const uint32_t t2 = t1 + (uint32_t)__popc(m1);
-                        const uint32_t t3 = t2 + (uint32_t)__popc(m2);
-                        if (k0)
-                            ws.ring[tail + __popc(m0 & lt)] =
-                                make_uint4(__float_as_uint(d2a.x), __float_as_uint(fabsf(dta.x)),
-                                           meta, j);
-                        if (k1)
-                            ws.ring[t1 + __popc(m1 & lt)] =
-                                make_uint4(__float_as_uint(d2a.y), __float_as_uint(fabsf(dta.y)),
-                                           meta, j + 1);
-                        if (k2)
-                            ws.ring[t2 + __popc(m2 & lt)] =
-                                make_uint4(__float_as_uint(d2b.x), __float_as_uint(fabsf(dtb.x)),
-                                           meta, j + 2);
-                        if (k3)
-                            ws.ring[t3 + __popc(m3 & lt)] =
-                                make_uint4(__float_as_uint(d2b.y), __float_as_uint(fabsf(dtb.y)),
-                                           meta, j + 3);
-                        tail = t3 + (uint32_t)__popc(m3);
-                        while (tail >= (uint32_t)kDrain) {
-                            __syncwarp();
-                            drain_pairs<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, kDrain, lane,
-                                                               lt, w);
-                            __syncwarp();
-                            const uint32_t rest = tail - kDrain;
-                            uint4 v[4];
-#pragma unroll
-                            for (int c = 0; c < 4; ++c)
-                                if ((uint32_t)(lane + 32 * c) < rest)
-                                    v[c] = ws.ring[kDrain + lane + 32 * c];
-                            __syncwarp();
-#pragma unroll
-                            for (int c = 0; c < 4; ++c)
-                                if ((uint32_t)(lane + 32 * c) < rest) ws.ring[lane + 32 * c] = v[c];
-                            __syncwarp();
-                            tail = rest;
-                        }
-                    }
-                }
-            }
-            drain_all<EVEN, EDGE, POLY, VAR>(pc, gpc, ws, rb, xq, tail, lane, lt, w);
-            if (since_flush >= kWarpFlush) {
-                if (VAR == kVarInh)
-                    warp_flush_inh(k, nbins, w.hc, w.he, w.hf, w.hw, acc, lane);
-                else
-                    warp_flush(k, nbins, w.hc, w.hh, w.he, acc, lane);
-                since_flush = 0;
-            }
+// Several jobs (point sets, grids, thresholds) in one persistent launch: the blocks take the
+// jobs in order, each job's realizations and units as the single-job kernel does; at a job
+// switch every block copies the job's whole constants and its descriptor into shared memory
+// (block barriers on both sides), so the body reads them from there.  The jobs share the
+// kernel class (even thresholds, edge correction; the plain rectangle estimator).  The
+// histogram replicas are laid out for the largest job (nbins_max bins) and cleared once:
+// every flush clears what it moves, so each job starts on zeros whatever its bin count.
+template <bool EVEN, bool EDGE>
+__global__ void __launch_bounds__(kBlock, 2)
+pair_fp32_fused_kernel(const FusedJob* __restrict__ jobs, int njobs, int reps, int nbins_max) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem32& sm = *reinterpret_cast<Smem32*>(smem_raw);
+    __shared__ FusedJob job;  // the current job's descriptor
+    {
+        const size_t hist_off = (sizeof(Smem32) + 15) & ~size_t(15);
+        uint32_t* hist = reinterpret_cast<uint32_t*>(smem_raw + hist_off);
+        const int words = 4 * reps * nbins_max;  // he (u64), hc and hh (u32) per replica
+        for (int i = threadIdx.x; i < words; i += kBlock) hist[i] = 0u;
+    }
+    for (int j = 0; j < njobs; ++j) {
+        __syncthreads();  // every warp is done with the previous job's constants
+        {
+            const int words = (int)(sizeof(PairConsts) / 4);
+            const int* src = reinterpret_cast<const int*>(jobs[j].pc);
+            int* dst = reinterpret_cast<int*>(&sm.pc);
+            for (int i = threadIdx.x; i < words; i += kBlock) dst[i] = src[i];
+            const int dwords = (int)(sizeof(FusedJob) / 4);
+            const int* dsrc = reinterpret_cast<const int*>(&jobs[j]);
+            int* ddst = reinterpret_cast<int*>(&job);
+            for (int i = threadIdx.x; i < dwords; i += kBlock) ddst[i] = dsrc[i];
         }
         __syncthreads();
-        // every warp of the block is done with realization k: add its histograms
-        if (VAR == kVarInh)
-            flush_hist_inh(k, nbins, reps, hc, he, hf, hw, acc);
-        else
-            flush_hist(k, nbins, reps, hc, he, acc, hh);
-        since_flush = 0;
+        constexpr bool POLY = false;
+        constexpr int VAR = kVarPlain;
+        constexpr int CALLER = 1;
+        const PairConsts& pc = sm.pc;
+        const PairConsts* gpc = job.pc;
+        const int m = job.m;
+        const RealBatch& rb = job.rb;
+        const WorkItem* __restrict__ units = job.units;
+        const uint32_t* __restrict__ unit_off = job.unit_off;
+        uint32_t* __restrict__ counters = job.counters;
+        const Accum& acc = job.acc;
+        const ExactQueue& xq = job.xq;
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#include "pair_fp32_body.cuh"
     }
-    for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
-    if (lane == 0) atomicAdd(&acc.stats[0], n_cand);
 }
 
 // ---------------------------------------------------------------- FP64 plain kernel
@@ -1591,14 +1442,22 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxThr * kMaxThr * 24 + 16));
     if (e != cudaSuccess) return e;
-    const void* k32[8] = {(const void*)pair_fp32_kernel<false, false, false, kVarPlain>,
+    const void* k32[16] = {(const void*)pair_fp32_kernel<false, false, false, kVarPlain>,
                           (const void*)pair_fp32_kernel<false, true, false, kVarPlain>,
                           (const void*)pair_fp32_kernel<true, false, false, kVarPlain>,
                           (const void*)pair_fp32_kernel<true, true, false, kVarPlain>,
                           (const void*)pair_fp32_kernel<false, true, true, kVarPlain>,
                           (const void*)pair_fp32_kernel<true, true, true, kVarPlain>,
                           (const void*)pair_fp32_kernel<false, false, false, kVarDir>,
-                          (const void*)pair_fp32_kernel<true, false, false, kVarDir>};
+                          (const void*)pair_fp32_kernel<true, false, false, kVarDir>,
+                          (const void*)pair_fp32_kernel<false, false, false, kVarPlain, 3>,
+                          (const void*)pair_fp32_kernel<false, true, false, kVarPlain, 3>,
+                          (const void*)pair_fp32_kernel<true, false, false, kVarPlain, 3>,
+                          (const void*)pair_fp32_kernel<true, true, false, kVarPlain, 3>,
+                          (const void*)pair_fp32_fused_kernel<false, false>,
+                          (const void*)pair_fp32_fused_kernel<false, true>,
+                          (const void*)pair_fp32_fused_kernel<true, false>,
+                          (const void*)pair_fp32_fused_kernel<true, true>};
     for (const void* f : k32) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
@@ -1630,13 +1489,46 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inh);
 }
 
-int pair_fp32_blocks_per_sm(size_t smem) {
+int pair_fp32_blocks_per_sm(size_t smem, int bps) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_kernel<true, true, false, kVarPlain>,
-                                                      kBlock, smem) !=
-        cudaSuccess)
+    const cudaError_t e =
+        bps == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       &b, pair_fp32_kernel<true, true, false, kVarPlain, 3>, kBlock, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       &b, pair_fp32_kernel<true, true, false, kVarPlain>, kBlock, smem);
+    if (e != cudaSuccess) return 1;
+    return b > 0 ? b : 1;
+}
+
+int pair_fp32_fused_blocks_per_sm(size_t smem) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_fp32_fused_kernel<true, true>,
+                                                      kBlock, smem) != cudaSuccess)
         return 1;
     return b > 0 ? b : 1;
+}
+
+cudaError_t launch_pair_fp32_fused(bool even, bool edge, size_t smem, int reps, int nbins_max,
+                                   int grid, const FusedJob* d_jobs, int njobs, cudaStream_t st) {
+    if (njobs < 1 || reps < 1 || nbins_max < 1) return cudaErrorInvalidValue;
+    if (even && edge)
+        pair_fp32_fused_kernel<true, true><<<grid, kBlock, smem, st>>>(d_jobs, njobs, reps,
+                                                                      nbins_max);
+    else if (even)
+        pair_fp32_fused_kernel<true, false><<<grid, kBlock, smem, st>>>(d_jobs, njobs, reps,
+                                                                       nbins_max);
+    else if (edge)
+        pair_fp32_fused_kernel<false, true><<<grid, kBlock, smem, st>>>(d_jobs, njobs, reps,
+                                                                       nbins_max);
+    else
+        pair_fp32_fused_kernel<false, false><<<grid, kBlock, smem, st>>>(d_jobs, njobs, reps,
+                                                                        nbins_max);
+    return cudaGetLastError();
+}
+
+bool pair_fp32_shape_tunable(const PairConsts& hpc, bool inh) {
+    const bool dir = hpc.nsec > 1 || hpc.edge == STK_EDGE_TRANSLATION;
+    return !(hpc.nv > 0) && !dir && !inh;
 }
 
 int pair_fp64_blocks_per_sm(size_t smem, bool inh) {
@@ -1654,7 +1546,8 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
                              size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
-                             ExactQueue xq, cudaStream_t st) {
+                             ExactQueue xq, cudaStream_t st, int bps) {
+    if (hpc.tile_units < 1) return cudaErrorInvalidValue;
     const bool poly = edge && hpc.nv > 0;
     // directional K / translation correction and inhomogeneous K: their own instantiations
     const bool dir = hpc.nsec > 1 || hpc.edge == STK_EDGE_TRANSLATION;
@@ -1663,6 +1556,12 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
     pair_fp32_kernel<E, D, P, V><<<grid, kBlock, smem, st>>>(hpc, d_pc, m, rb, units,        \
                                                              unit_off, counters, acc, xq, reps)
 #define STK_PAIR32(E, D, P) STK_PAIR32V(E, D, P, kVarPlain)
+#define STK_PAIR32S(E, D)                                                                     \
+    if (bps == 3)                                                                             \
+        pair_fp32_kernel<E, D, false, kVarPlain, 3><<<grid, kBlock, smem, st>>>(               \
+            hpc, d_pc, m, rb, units, unit_off, counters, acc, xq, reps);                      \
+    else                                                                                      \
+        STK_PAIR32(E, D, false)
     if ((dir && (poly || inh)) || (inh && (poly || acc.whole == nullptr)))
         return cudaErrorInvalidValue;
     if (inh && even && edge)
@@ -1682,13 +1581,14 @@ cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool
     else if (poly)
         STK_PAIR32(false, true, true);
     else if (even && edge)
-        STK_PAIR32(true, true, false);
+        STK_PAIR32S(true, true);
     else if (even)
-        STK_PAIR32(true, false, false);
+        STK_PAIR32S(true, false);
     else if (edge)
-        STK_PAIR32(false, true, false);
+        STK_PAIR32S(false, true);
     else
-        STK_PAIR32(false, false, false);
+        STK_PAIR32S(false, false);
+#undef STK_PAIR32S
 #undef STK_PAIR32
 #undef STK_PAIR32V
     return cudaGetLastError();

@@ -187,6 +187,7 @@ void deep_range(double w, int nc, double extent, double req, int out[2]) {
 void build_pair_consts(const Grid& g, int64_t n, const double* s, int cs, const double* tt,
                        int ct, int edge, PairConsts* pc) {
     memset(pc, 0, sizeof(*pc));
+    pc->tile_units = kTileUnitsDefault;
     pc->g = g;
     pc->cs = cs;
     pc->ct = ct;

@@ -96,6 +96,8 @@ struct stk_handle {
     DevBuf oK, oL, oS, oC, env, xq_e, xq_count, simseed, simid;
     DevBuf oA;  // raw accumulators of the last job's realizations, [R][4][nbins]
     DevBuf F;   // the pair filter's coordinate arrays, [m][3][filter_stride(n)]
+    DevBuf stg; // the scatter's staging records, [m][n] x 32 bytes
+    DevBuf fused;  // descriptors of a fused pair launch issued on this handle's stream
     // resident index of the observed pattern: its sorted arrays, cell counts and filter arrays
     // from the last job, reused while the grid and the record constants (obs_key) are the same
     DevBuf obs;
@@ -223,6 +225,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
                  8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
                  4 * 3 * (size_t)filter_stride(n) /* filter arrays */ +
+                 32 * un /* scatter staging */ +
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
     f.fixed = 32 * 8 + 64 * (size_t)R * nbins +
               32 * (size_t)nbins * (size_t)(groups > 0 ? groups : 1) + sizeof(PairConsts) +
@@ -237,7 +240,7 @@ size_t workspace_bytes(const stk_handle* h) {
                             &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                             &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK,
                             &h->oL, &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh,
-                            &h->Hs, &h->acc_whole, &h->oA, &h->F, &h->obs};
+                            &h->Hs, &h->acc_whole, &h->oA, &h->F, &h->stg, &h->fused, &h->obs};
     size_t b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     return b;
@@ -246,8 +249,23 @@ size_t workspace_bytes(const stk_handle* h) {
 // Runs the observed pattern (optional) and the simulations of `plan`; leaves per-realization
 // K, L, S, C rows in h->oK/oL/oS/oC ([R][nbins], observed first) and one envelope per group of
 // the plan in h->env ([groups][4][nbins]).
+// Part of a fused pair launch (run_plans_fused): Prepare issues a job's generation and grid
+// index, stops before its pair kernel and describes that kernel's work in `job`; Finish (the
+// same job, after the fused launch) issues only what follows the pair kernel.
+enum class FusePhase { Prepare, Finish };
+struct FuseCtx {
+    FusePhase phase = FusePhase::Prepare;
+    FusedJob job{};
+    bool even = false, edge = false;
+    int nbins = 0;
+    float ms_pair = 0.0f;            // Finish: the fused launch's time
+    bool count_pair_launch = false;  // Finish: the fused launch counts in this job's launches
+    int shape = 0;  // Prepare's launch shape (shape_code), which Finish repeats
+};
+constexpr int kNotFusable = -1000;  // run_job with a FuseCtx: the job cannot be fused
+
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
-            int* R_out, int f_force = 0);
+            int* R_out, int f_force = 0, FuseCtx* fuse = nullptr);
 
 // Grid refinement tuner: for batched jobs large enough to amortise it, times the pair kernel
 // on a few CSR realizations for (fs, ft) = (f, f), f = 1..3, then the best fs with ft one step
@@ -261,8 +279,15 @@ struct TuneKey {
         return memcmp(this, &o, sizeof(TuneKey)) < 0;
     }
 };
+// A launch shape: grid refinement (fs | ft << 8), work units per tile claim and blocks per SM
+// of the FP32 pair kernel; 0 = not chosen (planner / defaults).
+struct TuneChoice {
+    int f = 0, tile = 0, bps = 0;
+};
+// run_job's forced shape for the tuner's trials: f | tile << 16 | bps << 24
+inline int shape_code(const TuneChoice& c) { return c.f | (c.tile << 16) | (c.bps << 24); }
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tuned;
+std::map<TuneKey, TuneChoice> g_tuned;
 
 // The problem shape of a job, for the tuner's table.
 TuneKey tune_key(const stk_handle* h, const stk_request* q) {
@@ -280,20 +305,26 @@ TuneKey tune_key(const stk_handle* h, const stk_request* q) {
 }
 
 // The refinement tuned for this problem shape, if any (0: none yet).
-int tuned_lookup(const stk_handle* h, const stk_request* q) {
+TuneChoice tuned_lookup(const stk_handle* h, const stk_request* q) {
     const TuneKey key = tune_key(h, q);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
-    return it == g_tuned.end() ? 0 : it->second;
+    return it == g_tuned.end() ? TuneChoice() : it->second;
 }
 
-int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
+// Launch shape for a job shape, timed once per process on a few CSR realizations and kept:
+// first the grid refinement (fs = ft = 1, 2, 3, then the time axis one step either side), then
+// with it the tile of work units a block claims (8, 32, 64 against 16), then, for the plain
+// rectangle kernels, three blocks per SM (85 registers) against two.  The incumbent of each
+// step (the planner's refinement, tile 16, two blocks) is replaced only by a shape 3% faster:
+// trial timings of a few realizations differ by about 1% from run to run.
+int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
     const TuneKey key = tune_key(h, q);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            *f_out = it->second;
+            *out = it->second;
             return STK_OK;
         }
     }
@@ -306,41 +337,61 @@ int tuned_refinement(stk_handle* h, const stk_request* q, int* f_out) {
     }
     stk_request tq = *q;
     tq.centre_mask = nullptr;
-    float best = 0.0f;
-    int best_f = 0;
-    // the planner's choice is the incumbent; another refinement must be faster by 3% (trial
-    // timings of a few realizations differ by about 1% from run to run)
     Grid gp;
     char err[256];
     if (build_grid(h->box, key.s_max, key.t_max, h->n, 0, &gp, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
-    const int planned = gp.fs | (gp.ft << 8);
-    auto trial_run = [&](int fs, int ft) -> int {
+    TuneChoice best;
+    best.f = gp.fs | (gp.ft << 8);
+    best.tile = (int)kTileUnitsDefault;
+    best.bps = 2;
+    float best_ms = -1.0f;
+    // times shape c; `incumbent`: the step's default, which others must beat by 3%
+    auto trial_run = [&](TuneChoice c, bool incumbent) -> int {
         int R = 0;
-        const int f = fs | (ft << 8);
-        const int rc = run_job(h, &tq, false, trial, &R, f);
-        if (rc == STK_ENOMEM) return STK_OK;  // a finer grid that does not fit is no candidate
+        const int rc = run_job(h, &tq, false, trial, &R, shape_code(c));
+        if (rc == STK_ENOMEM) return STK_OK;  // a shape that does not fit is no candidate
         if (rc) return rc;
         float ms = (float)h->last.ms_pair;
-        if (f != planned) ms *= 1.03f;
-        if (best_f == 0 || ms < best) best = ms, best_f = f;
+        if (!incumbent) ms *= 1.03f;
+        if (best_ms < 0.0f || ms < best_ms) best_ms = ms, best = c;
         return STK_OK;
     };
-    // the same refinement on both axes first, then the time axis one step either side
+    const int planned = best.f;
     for (int f = 1; f <= 3; ++f) {
-        const int rc = trial_run(f, f);
+        TuneChoice c = best;
+        c.f = f | (f << 8);
+        const int rc = trial_run(c, c.f == planned);
         if (rc) return rc;
     }
-    if (best_f == 0) best_f = 1 | (1 << 8);
-    const int fs0 = best_f & 0xff;
+    const int fs0 = best.f & 0xff;
     for (int ft = fs0 - 1; ft <= fs0 + 1; ft += 2) {
         if (ft < 1 || ft > 3) continue;
-        const int rc = trial_run(fs0, ft);
+        TuneChoice c = best;
+        c.f = fs0 | (ft << 8);
+        const int rc = trial_run(c, c.f == planned);
         if (rc) return rc;
     }
+    // the refinement's own time with the default shape is the incumbent of the next steps
+    {
+        const TuneChoice base = best;
+        best_ms = -1.0f;
+        int rc = trial_run(base, true);
+        if (rc) return rc;
+        for (int tile : {8, 32, 64}) {
+            TuneChoice c = base;
+            c.tile = tile;
+            if ((rc = trial_run(c, false))) return rc;
+        }
+        if (fp32_path(h, q) && pair_fp32_shape_tunable(*h->h_pc, h->inten.nix > 0)) {
+            TuneChoice c = best;
+            c.bps = 3;
+            if ((rc = trial_run(c, false))) return rc;
+        }
+    }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[key] = best_f;
-    *f_out = best_f;
+    g_tuned[key] = best;
+    *out = best;
     return STK_OK;
 }
 
@@ -396,7 +447,9 @@ int job_coef(const stk_handle* h, const stk_request* q, double* coef) {
 }
 
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
-            int* R_out, int f_force) {
+            int* R_out, int f_force, FuseCtx* fuse) {
+    const bool finish = fuse && fuse->phase == FusePhase::Finish;
+    if (finish) f_force = fuse->shape;  // the grid and tile Prepare built
     using clock = std::chrono::steady_clock;
     const auto t_start = clock::now();
     h->last_rows = 0;  // the raw accumulator rows are the new job's from here on
@@ -466,31 +519,45 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     const double lfac = (double)nsec;
     char err[256];
     Grid g;
-    // grid refinement: forced (tuner trials), STK_GRID_F (and STK_GRID_FT for the time axis),
-    // the tuner (STK_TUNE=0 disables it) or the density planner
-    int f_req = f_force;
-    if (f_req == 0) {
+    // launch shape: forced (tuner trials: shape_code), STK_GRID_F (and STK_GRID_FT for the time
+    // axis), STK_TILE_UNITS, STK_BLOCKS_PER_SM, the tuner (STK_TUNE=0 disables it), or the
+    // density planner with the default tile and two blocks per SM
+    int f_req = f_force & 0xffff;
+    int tile_req = (f_force >> 16) & 0xff, bps_req = (f_force >> 24) & 0xf;
+    if (f_force == 0) {
         if (const char* fe = getenv("STK_GRID_F")) f_req = atoi(fe);
         if (const char* ft = getenv("STK_GRID_FT")) f_req |= atoi(ft) << 8;
+        if (const char* te = getenv("STK_TILE_UNITS")) tile_req = atoi(te);
+        if (const char* be = getenv("STK_BLOCKS_PER_SM")) bps_req = atoi(be);
     }
     const char* tune_env = getenv("STK_TUNE");
-    const bool tune = f_req == 0 && q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0) &&
-                      (double)n * (double)R >= 2.0e7;
-    if (tune) {
-        rc = tuned_refinement(h, q, &f_req);
-        if (rc) return rc;
-    } else if (f_req == 0 && q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0)) {
-        // a smaller job of a shape tuned before takes the same refinement, so that its grids
-        // do not depend on the jobs it shares a batch with (a served job equals it alone)
-        f_req = tuned_lookup(h, q);
+    const bool tune_on = q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0) &&
+                         f_req == 0 && tile_req == 0 && bps_req == 0;
+    if (tune_on) {
+        TuneChoice c;
+        if ((double)n * (double)R >= 2.0e7 && !fuse) {
+            rc = tuned_refinement(h, q, &c);
+            if (rc) return rc;
+        } else {
+            // a smaller job of a shape tuned before takes the same shape, so that its grids do
+            // not depend on the jobs it shares a batch with (a served job equals it alone)
+            c = tuned_lookup(h, q);
+        }
+        f_req = c.f;
+        tile_req = c.tile;
+        bps_req = c.bps;
     }
+    if (tile_req < 1 || tile_req > 255) tile_req = (int)kTileUnitsDefault;
+    if (bps_req != 3 || fuse) bps_req = 2;  // the fused kernel has the 2-block shape only
     if (build_grid(h->box, q->s[cs - 1], q->tt[ct - 1], n, f_req, &g, err, sizeof err))
         return fail(STK_EINVAL, "%s", err);
+    if (fuse && !finish) fuse->shape = (g.fs | (g.ft << 8)) | (tile_req << 16) | (bps_req << 24);
     cudaStream_t st = h->stream;
     CK(cudaStreamSynchronize(st), "stream sync");  // the pinned constants are reused below
     build_pair_consts(g, n, q->s, cs, q->tt, ct, q->edge_mode, h->h_pc);
     h->h_pc->nsec = nsec;
     h->h_pc->nbins = nbins;
+    h->h_pc->tile_units = (uint32_t)tile_req;
     {  // failure-detection test hook, see PairConsts::never_publish
         const char* np = getenv("STK_TEST_NEVER_PUBLISH");
         h->h_pc->never_publish = (np && atoi(np) != 0) ? 1 : 0;
@@ -580,6 +647,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         (rc = ensure(h->T, 8 * mn, "sorted t")) || (rc = ensure(h->P, 32 * (mn + 8), "FP32 points")) ||
         (rc = ensure(h->Plo, 8 * mn, "FP32 low parts")) ||
         (rc = ensure(h->F, 12 * (size_t)m_w * (size_t)filter_stride(n), "filter arrays")) ||
+        (rc = ensure(h->stg, stage_bytes(m_w, n), "scatter staging")) ||
         (rc = ensure(h->cell_start, 4 * (mc + m_w), "cell starts")) ||
         (rc = ensure(h->chunks, 4 * mr, "work counts")) ||
         (rc = ensure(h->chunk_off, 4 * mr, "work offsets")) ||
@@ -661,7 +729,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         h->h_seed[k] = plan.seed[(size_t)k];
         h->h_id[k] = plan.id[(size_t)k];
     }
-    CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
+    if (!finish) CK(cudaMemsetAsync(h->stats.p, 0, 64, st), "memset");
 
     double coef = 0.0;
     if ((rc = job_coef(h, q, &coef))) return rc;
@@ -671,8 +739,14 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     int reps = fp32 ? h->reps32 : h->reps64;
     size_t smem = fp32 ? h->smem32 : h->smem64;
     if (inh) smem = fp32 ? pair_fp32_smem(nbins, &reps, true) : pair_fp64_smem(nbins, &reps, true);
-    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem) : pair_fp64_blocks_per_sm(smem, inh);
+    // the launch shape's blocks per SM: 3 only where the kernel has that instantiation
+    const int shape_bps = fp32 && bps_req == 3 && pair_fp32_shape_tunable(*h->h_pc, inh) ? 3 : 2;
+    const int bps = fp32 ? pair_fp32_blocks_per_sm(smem, shape_bps)
+                         : pair_fp64_blocks_per_sm(smem, inh);
     const int grid = bps * h->num_sms;
+    if (fuse && (!fp32 || q->exec != STK_EXEC_BATCHED || use_mask || inh || h->nv > 0 || dir ||
+                 q->shard_count > 1 || (R + m_w - 1) / m_w != 1))
+        return kNotFusable;  // fused jobs: plain FP32 rectangle kernels, one wave
     float ms_pair = 0.0f;
     int waves = 0;
     int64_t launches = 0;
@@ -728,6 +802,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     auto issue_wave = [&](int r0, int m, bool in_graph) -> int {
         const bool obs_here = include_obs && r0 == 0;
         const int first_sim_slot = obs_here ? 1 : 0;
+        if (!finish) {  // generation, grid index, work list, cleared accumulators
         CK(cudaMemsetAsync(h->counts.p, 0, 4 * (size_t)m * ncells, st), "memset");
         if (obs_here && obs_hit) {  // the resident index: its cell counts feed the scan
             CK(cudaMemcpyAsync(h->counts.p, oc + oc_cnt, 4 * (size_t)ncells,
@@ -801,7 +876,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               as<double>(h->X), as<double>(h->Y), as<double>(h->T),
                               as<float4>(h->P), as<float2>(h->Plo), as<uint8_t>(h->mask_sorted),
                               h->h_pc->tan_rel, h->h_pc->tan_abs, h->h_pc->fast_abs,
-                              as<float>(h->F), nF, st, poly, cross,
+                              as<float>(h->F), nF, as<double2>(h->stg), st, poly, cross,
                               inh ? as<double>(h->uh) + so : nullptr,
                               inh ? as<double>(h->Hs) : nullptr, s0),
                "scatter");
@@ -843,6 +918,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         if (fp32) CK(cudaMemsetAsync(h->xq_count.p, 0, 16, st), "memset");
         // each unordered pair is evaluated once, never a point with itself
         CK(cudaMemsetAsync(h->self_pairs.p, 0, 8 * (size_t)m * nsec, st), "memset");
+        }
         RealBatch rb;
         rb.P = as<float4>(h->P);
         rb.Plo = as<float2>(h->Plo);
@@ -867,23 +943,42 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         acc.exc_hi = as<unsigned long long>(h->acc_hi);
         acc.stats = as<unsigned long long>(h->stats);
         acc.whole = inh ? as<unsigned long long>(h->acc_whole) : nullptr;
-        CK(cudaEventRecordWithFlags(h->ev0, st, in_graph ? cudaEventRecordExternal : 0), "event");
         ExactQueue xq;
         xq.e = as<uint4>(h->xq_e);
         xq.count = as<unsigned int>(h->xq_count);
         xq.cap = xq_cap;
-        if (fp32)
+        if (fuse && !finish) {  // the fused launch runs this job's pair kernel
+            fuse->job.pc = as<PairConsts>(h->pc);
+            fuse->job.rb = rb;
+            fuse->job.units = as<WorkItem>(h->items);
+            fuse->job.unit_off = as<uint32_t>(h->chunk_off);
+            fuse->job.counters = as<uint32_t>(h->counter);
+            fuse->job.acc = acc;
+            fuse->job.xq = xq;
+            fuse->job.m = m;
+            fuse->even = h->h_pc->even_s && h->h_pc->even_t;
+            fuse->edge = h->h_pc->edge != 0;
+            fuse->nbins = nbins;
+            return STK_OK;
+        }
+        if (!finish)
+            CK(cudaEventRecordWithFlags(h->ev0, st, in_graph ? cudaEventRecordExternal : 0),
+               "event");
+        if (finish) {
+        } else if (fp32)
             CK(launch_pair_fp32(*h->h_pc, as<PairConsts>(h->pc), h->h_pc->even_s && h->h_pc->even_t,
                                 h->h_pc->edge != 0, smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
-                                as<uint32_t>(h->counter), acc, xq, st),
+                                as<uint32_t>(h->counter), acc, xq, st, shape_bps),
                "pair kernel (FP32)");
         else
             CK(launch_pair_fp64(as<PairConsts>(h->pc), smem, reps, grid, m, rb,
                                 as<WorkItem>(h->items), as<uint32_t>(h->chunk_off),
                                 as<uint32_t>(h->counter), acc, st, h->nv > 0, inh, dir),
                "pair kernel (FP64)");
-        CK(cudaEventRecordWithFlags(h->ev1, st, in_graph ? cudaEventRecordExternal : 0), "event");
+        if (!finish)
+            CK(cudaEventRecordWithFlags(h->ev1, st, in_graph ? cudaEventRecordExternal : 0),
+               "event");
         if (fp32) {
             CK(launch_exact(as<PairConsts>(h->pc), 4 * h->num_sms, rb, acc, xq, st, h->nv > 0,
                             dir),
@@ -920,7 +1015,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     // event-record nodes inside the graph.
     const char* graphs_env = getenv("STK_GRAPHS");
     const int graphs = graphs_env ? atoi(graphs_env) : -1;
-    const bool graph_ok = q->exec == STK_EXEC_BATCHED && !use_mask && graphs != 0;
+    const bool graph_ok = q->exec == STK_EXEC_BATCHED && !use_mask && graphs != 0 && !fuse;
     std::vector<unsigned char> key;
     if (graph_ok) {
         auto put = [&key](const void* p, size_t b) {
@@ -930,7 +1025,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         const int64_t sc[] = {n, R, include_obs, fp32, q->edge_mode, q->norm, cs, ct, grid,
                               (int64_t)smem, reps, (int64_t)xq_cap, tmp_words, ncells, nrows,
                               q->sim_method, inh, (int64_t)h->inh_gen, nsec, q->shard_count,
-                              q->shard_index, obs_hit, obs_cacheable};
+                              q->shard_index, obs_hit, obs_cacheable, shape_bps};
         put(sc, sizeof sc);
         put(&coef, sizeof coef);
         put(h->h_pc, sizeof(PairConsts));
@@ -943,7 +1038,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                               h->simid.p, h->d_x, h->d_y, h->d_t, h->h_seed, h->h_id,
                               (void*)h->ev0, (void*)h->ev1, (void*)st, h->uh.p, h->Hs.p,
                               h->acc_whole.p, h->inh.p, h->inh_obs.p, h->oA.p, h->F.p,
-                              h->obs.p};
+                              h->obs.p, h->stg.p};
         put(ptrs, sizeof ptrs);
     }
     int replays = 0;
@@ -983,11 +1078,17 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
             rc = issue_wave(r0, m, false);
             if (rc) return rc;
         }
-        CK(cudaEventSynchronize(h->ev1), "pair kernel");
+        if (fuse && !finish) return STK_OK;  // Prepare ends before the pair kernel (one wave)
         float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event timing");
+        if (finish) {
+            ms = fuse->ms_pair;
+        } else {
+            CK(cudaEventSynchronize(h->ev1), "pair kernel");
+            CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1), "event timing");
+        }
         ms_pair += ms;
         ++waves;
+        if (finish && !fuse->count_pair_launch) --launches;  // counted with another job
         launches += (obs_here && !obs_hit ? 1 : 0) + (m > first_sim_slot ? 1 : 0) +
                     scan_launches((int64_t)m * ncells) + scan_launches((int64_t)m * nrows + 1) +
                     4 /* scatter, starts, counts, fill */ -
@@ -1030,6 +1131,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     h->last.internal_errors = (int64_t)stats[2];
     h->last.grid_refinement = g.fs;
     h->last.grid_refinement_t = g.ft;
+    h->last.tile_units = fp32 ? tile_req : 0;
+    h->last.blocks_per_sm = bps;
     h->last.graph_replays = replays;
     h->last_rows = R;
     h->last_nbins = nbins;
@@ -1066,6 +1169,117 @@ namespace stk {
 int run_plan(stk_handle* h, const stk_request* q, const SimPlan& plan, bool include_obs) {
     int R = 0;
     return run_job(h, q, include_obs, plan, &R);
+}
+
+bool fusable_job(const stk_handle* h, const stk_request* q, int64_t R) {
+    return q->exec == STK_EXEC_BATCHED && q->prec == STK_PREC_FP32_GUARDED &&
+           (q->edge_mode == STK_EDGE_NONE || q->edge_mode == STK_EDGE_ISOTROPIC) &&
+           q->n_sectors <= 1 && q->labels == nullptr && q->centre_mask == nullptr &&
+           q->shard_count <= 1 && h->nv == 0 && h->inten.nix == 0 &&
+           (double)h->n * (double)R < kFuseMaxPointRealizations;
+}
+
+int run_plans_fused(const std::vector<FusePart>& parts, int* fused_launches) {
+    const size_t np = parts.size();
+    if (fused_launches) *fused_launches = 0;
+    std::vector<FuseCtx> ctx(np);
+    std::vector<char> in_launch(np, 0);
+    int rc = STK_OK;
+    // 1. each part's generation and grid index on its own stream
+    for (size_t i = 0; i < np; ++i) {
+        int R = 0;
+        if (!fusable_job(parts[i].h, parts[i].q, 1 + (int64_t)parts[i].plan->seed.size()))
+            continue;  // runs alone below
+        ctx[i].phase = FusePhase::Prepare;
+        rc = run_job(parts[i].h, parts[i].q, true, *parts[i].plan, &R, 0, &ctx[i]);
+        if (rc == kNotFusable) continue;  // runs alone below
+        if (rc) return rc;
+        in_launch[i] = 1;
+    }
+    // 2. one persistent pair launch per kernel class present (usually one), on the first
+    // part's stream once every part's index is built; the parts' streams wait for it
+    std::vector<cudaEvent_t> evs;
+    auto new_event = [&evs](unsigned flags) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, flags) != cudaSuccess) return (cudaEvent_t) nullptr;
+        evs.push_back(e);
+        return e;
+    };
+    auto cleanup = [&evs]() {
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+        evs.clear();
+    };
+    for (int cls = 0; cls < 4 && rc == STK_OK; ++cls) {
+        std::vector<size_t> members;
+        for (size_t i = 0; i < np; ++i)
+            if (in_launch[i] && (ctx[i].even ? 2 : 0) + (ctx[i].edge ? 1 : 0) == cls)
+                members.push_back(i);
+        if (members.empty()) continue;
+        stk_handle* h0 = parts[members[0]].h;
+        cudaStream_t st0 = h0->stream;
+        int nbins_max = 0;
+        std::vector<FusedJob> jobs;
+        for (size_t i : members) {
+            nbins_max = std::max(nbins_max, ctx[i].nbins);
+            jobs.push_back(ctx[i].job);
+            cudaEvent_t built = new_event(cudaEventDisableTiming);
+            if (!built || cudaEventRecord(built, parts[i].h->stream) != cudaSuccess ||
+                cudaStreamWaitEvent(st0, built, 0) != cudaSuccess) {
+                cleanup();
+                return fail(STK_ECUDA, "fused launch: event");
+            }
+        }
+        int reps = 1, reps64 = 1;
+        const size_t smem = pair_fp32_smem(nbins_max, &reps);
+        if (pair_kernels_configure(smem, pair_fp64_smem(nbins_max, &reps64)) != cudaSuccess ||
+            ensure(h0->fused, sizeof(FusedJob) * jobs.size(), "fused launch") != STK_OK) {
+            cleanup();
+            return fail(STK_ECUDA, "fused launch: set-up");
+        }
+        cudaEvent_t t0 = new_event(cudaEventDefault), t1 = new_event(cudaEventDefault);
+        cudaEvent_t done = new_event(cudaEventDisableTiming);
+        const int grid = pair_fp32_fused_blocks_per_sm(smem) * h0->num_sms;
+        cudaError_t e = (t0 && t1 && done) ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h0->fused.p, jobs.data(), sizeof(FusedJob) * jobs.size(),
+                                cudaMemcpyHostToDevice, st0);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, st0);
+        if (e == cudaSuccess)
+            e = launch_pair_fp32_fused(ctx[members[0]].even, ctx[members[0]].edge, smem, reps,
+                                       nbins_max, grid, as<FusedJob>(h0->fused),
+                                       (int)jobs.size(), st0);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, st0);
+        if (e == cudaSuccess) e = cudaEventRecord(done, st0);
+        for (size_t i : members)
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(parts[i].h->stream, done, 0);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) {
+            cleanup();
+            return fail(STK_ECUDA, "fused pair launch: %s", cudaGetErrorString(e));
+        }
+        for (size_t k = 0; k < members.size(); ++k) {
+            ctx[members[k]].ms_pair = ms;
+            ctx[members[k]].count_pair_launch = k == 0;
+        }
+        if (fused_launches) *fused_launches += 1;
+    }
+    cleanup();
+    // 3. what follows each part's pair kernel, on its own stream
+    for (size_t i = 0; i < np && rc == STK_OK; ++i) {
+        if (!in_launch[i]) continue;
+        int R = 0;
+        ctx[i].phase = FusePhase::Finish;
+        rc = run_job(parts[i].h, parts[i].q, true, *parts[i].plan, &R, 0, &ctx[i]);
+    }
+    // 4. parts that could not join the launch run alone
+    for (size_t i = 0; i < np && rc == STK_OK; ++i) {
+        if (in_launch[i]) continue;
+        int R = 0;
+        rc = run_job(parts[i].h, parts[i].q, true, *parts[i].plan, &R);
+    }
+    return rc;
 }
 
 int fetch_rows(stk_handle* h, int what, int row0, int rows, void* dst) {
@@ -1110,7 +1324,7 @@ void handle_trim(stk_handle* h) {
                       &h->counter, &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc,
                       &h->thr, &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL,
                       &h->oS, &h->oC, &h->env, &h->simseed, &h->simid, &h->uh, &h->Hs,
-                      &h->acc_whole, &h->oA, &h->F};
+                      &h->acc_whole, &h->oA, &h->F, &h->stg, &h->fused};
     for (DevBuf* b : bufs) free_buf(*b);
 }
 
@@ -1214,12 +1428,10 @@ int stk_set_stream(stk_handle* h, void* stream) {
     return STK_OK;
 }
 
-int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
-    if (!h || !req || !res) return fail(STK_EINVAL, "handle, request and result must not be NULL");
-    if (req->n_sims < 0 || req->n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
-    int R = 0;
-    int rc = run_job(h, req, true, default_plan(req), &R);
-    if (rc) return rc;
+// Copies the last job's observed grids, envelope and per-simulation grids into res (the
+// pointers that are not NULL) and waits for the copies.
+int download_result(stk_handle* h, const stk_request* req, stk_result* res) {
+    int rc = STK_OK;
     const int nbins = req->cs * req->ct * (req->n_sectors > 1 ? req->n_sectors : 1);
     if ((rc = copy_rows(h, h->oK, 0, 1, nbins, res->K)) ||
         (rc = copy_rows(h, h->oL, 0, 1, nbins, res->L)) ||
@@ -1236,6 +1448,43 @@ int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
             return rc;
     }
     CK(cudaStreamSynchronize(h->stream), "result copy");
+    return STK_OK;
+}
+
+int stk_run(stk_handle* h, const stk_request* req, stk_result* res) {
+    if (!h || !req || !res) return fail(STK_EINVAL, "handle, request and result must not be NULL");
+    if (req->n_sims < 0 || req->n_sims > (1 << 24)) return fail(STK_EINVAL, "n_sims out of range");
+    int R = 0;
+    const int rc = run_job(h, req, true, default_plan(req), &R);
+    if (rc) return rc;
+    return download_result(h, req, res);
+}
+
+int stk_run_fused(stk_handle* const* hs, const stk_request* reqs, stk_result* results, int njobs,
+                  int* pair_launches) {
+    if (pair_launches) *pair_launches = 0;
+    if (!hs || !reqs || !results || njobs < 1 || njobs > STK_MAX_FUSED_JOBS)
+        return fail(STK_EINVAL, "handles, requests and results must not be NULL and njobs must "
+                                "be in 1..%d", STK_MAX_FUSED_JOBS);
+    for (int i = 0; i < njobs; ++i) {
+        if (!hs[i]) return fail(STK_EINVAL, "handle %d is NULL", i);
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return fail(STK_EINVAL, "handle %d appears twice", i);
+        if (reqs[i].n_sims < 0 || reqs[i].n_sims > (1 << 24))
+            return fail(STK_EINVAL, "n_sims out of range (job %d)", i);
+    }
+    std::vector<SimPlan> plans(njobs);
+    std::vector<FusePart> parts;
+    for (int i = 0; i < njobs; ++i) {
+        plans[i] = default_plan(&reqs[i]);
+        parts.push_back({hs[i], &reqs[i], &plans[i]});
+    }
+    int launches = 0;
+    int rc = run_plans_fused(parts, &launches);
+    if (rc) return rc;
+    for (int i = 0; i < njobs; ++i)
+        if ((rc = download_result(hs[i], &reqs[i], &results[i]))) return rc;
+    if (pair_launches) *pair_launches = launches;
     return STK_OK;
 }
 
@@ -1862,7 +2111,7 @@ void stk_destroy(stk_handle* h) {
                       &h->chunks, &h->chunk_off, &h->items, &h->counter,
                       &h->acc_cnt, &h->acc_lo, &h->acc_hi, &h->stats, &h->pc, &h->thr,
                       &h->self_pairs, &h->mask_in, &h->mask_sorted, &h->oK, &h->oL, &h->oS,
-                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA, &h->F, &h->obs};
+                      &h->oC, &h->env, &h->simseed, &h->simid, &h->oA, &h->F, &h->stg, &h->fused, &h->obs};
     for (DevBuf* b : bufs) free_buf(*b);
     if (h->d_x) cudaFree(h->d_x);
     if (h->d_y) cudaFree(h->d_y);

@@ -77,6 +77,9 @@ struct PairConsts {
     // work units claims none and publishes nothing, so the block's other warps wait for a tile
     // that never comes until their bounded wait runs out
     int never_publish;
+    // consecutive work units a block of the FP32 pair kernel claims at once (>= 1; the launch
+    // shape's tile, kTileUnitsDefault unless tuned)
+    uint32_t tile_units;
     // polygon study area (nv = 0: the rectangle); vertex arrays in device memory
     int nv;
     int pccw;                 // 1: vertices run counter-clockwise
@@ -146,7 +149,7 @@ struct RealBatch {
 // depends on the order of points inside a cell, which the counting sort does not fix from one
 // run to the next, while pairs across rows always belong to the earlier row.
 // unit_off: the launch's unit offsets [m * nrows + 1] (realization 0 first).
-__device__ inline uint32_t first_row_unit_at_or_after(const uint32_t* unit_off, int64_t nrows,
+__device__ __forceinline__ uint32_t first_row_unit_at_or_after(const uint32_t* unit_off, int64_t nrows,
                                                       uint32_t target) {
     int64_t lo = 0, hi = nrows;  // unit_off[nrows] is the realization's end, >= target
     while (lo < hi) {
@@ -159,7 +162,7 @@ __device__ inline uint32_t first_row_unit_at_or_after(const uint32_t* unit_off, 
     return unit_off[lo];
 }
 
-__device__ inline void shard_units(const RealBatch& rb, const uint32_t* unit_off, int64_t nrows,
+__device__ __forceinline__ void shard_units(const RealBatch& rb, const uint32_t* unit_off, int64_t nrows,
                                    int k, uint32_t* b, uint32_t* e) {
     if (k != 0 || rb.shard_count <= 1) return;
     const uint64_t u = (uint64_t)(*e - *b);
@@ -194,6 +197,20 @@ struct ExactQueue {
     uint4* e;
     unsigned int* count;  // entries pushed (may exceed cap; the excess ran in the pair kernel)
     unsigned int cap;
+};
+
+// One job of a fused FP32 pair launch (several jobs, each with its own point set, grid and
+// thresholds, in one persistent launch; an array of these in device memory).
+struct FusedJob {
+    const PairConsts* pc;       // the job's whole constants (device)
+    RealBatch rb;
+    const WorkItem* units;
+    const uint32_t* unit_off;   // [m * nrows + 1]
+    uint32_t* counters;         // [m]
+    Accum acc;
+    ExactQueue xq;
+    int m;                      // realizations
+    int pad;
 };
 
 // ---------------------------------------------------------------- host-side launchers
@@ -255,11 +272,13 @@ cudaError_t launch_scatter(int m, int64_t n, const Grid& g, const double* x, con
                            const uint32_t* start_global, const uint8_t* mask_in,
                            double* X, double* Y, double* T, float4* P, float2* Plo,
                            uint8_t* mask_out, float tan_rel, float tan_abs, float fast_abs,
-                           float* F, int64_t nF, cudaStream_t st, Polygon poly = Polygon(),
-                           bool mask_all = false, const double* h_in = nullptr,
-                           double* H = nullptr, int slot0 = 0);
+                           float* F, int64_t nF, double2* stage, cudaStream_t st,
+                           Polygon poly = Polygon(), bool mask_all = false,
+                           const double* h_in = nullptr, double* H = nullptr, int slot0 = 0);
 // (slot0: the m realizations scattered are slots slot0 .. slot0 + m - 1 of the sorted arrays;
-// the inputs x, y, t, key, rank, mask_in and h_in start at slot slot0's points)
+// the inputs x, y, t, key, rank, mask_in and h_in start at slot slot0's points.  stage:
+// scratch of 32 bytes per scattered point, stage_bytes(m, n), 16-byte aligned)
+inline size_t stage_bytes(int64_t m, int64_t n) { return 32 * (size_t)m * (size_t)n; }
 // floats per realization and axis of the filter's coordinate arrays (n plus padding for the
 // last four-point load, a multiple of 4 so that every axis starts 16-byte aligned)
 inline int64_t filter_stride(int64_t n) { return (n + 8 + 3) & ~int64_t(3); }
@@ -271,12 +290,25 @@ cudaError_t launch_work_counts(int m, const Grid& g, const uint32_t* cell_start,
 // units[unit_off[k*nrows + r] ...] for every (k, r); unit_off has m * nrows + 1 entries
 cudaError_t launch_work_fill(int m, const Grid& g, const uint32_t* cell_start,
                              const uint32_t* unit_off, WorkItem* units, cudaStream_t st);
-// hpc: host copy of *d_pc, passed by value (its scalars are read from the constant bank)
+// hpc: host copy of *d_pc, passed by value (its scalars are read from the constant bank).
+// bps: the launch shape's blocks per SM (2, or 3 for the kernels pair_fp32_shape_tunable
+// admits; grid = SMs x pair_fp32_blocks_per_sm(smem, bps))
 cudaError_t launch_pair_fp32(const PairConsts& hpc, const PairConsts* d_pc, bool even, bool edge,
                              size_t smem, int reps,
                              int grid, int m, RealBatch rb, const WorkItem* units,
                              const uint32_t* unit_off, uint32_t* counters, Accum acc,
-                             ExactQueue xq, cudaStream_t st);
+                             ExactQueue xq, cudaStream_t st, int bps = 2);
+// One persistent launch over njobs jobs (d_jobs: device array) of one kernel class: even
+// thresholds or not, edge correction or not (the plain rectangle estimator); smem and reps for
+// the largest job's bin count nbins_max (pair_fp32_smem); grid = SMs x
+// pair_fp32_fused_blocks_per_sm(smem).
+cudaError_t launch_pair_fp32_fused(bool even, bool edge, size_t smem, int reps, int nbins_max,
+                                   int grid, const FusedJob* d_jobs, int njobs, cudaStream_t st);
+int pair_fp32_fused_blocks_per_sm(size_t smem);
+// whether the FP32 pair kernel of a job has the 3-blocks-per-SM launch shape (the plain
+// rectangle kernels: no polygon, no directional or inhomogeneous variant)
+bool pair_fp32_shape_tunable(const PairConsts& hpc, bool inh);
+constexpr uint32_t kTileUnitsDefault = 16;
 cudaError_t launch_exact(const PairConsts* d_pc, int grid, RealBatch rb, Accum acc,
                          ExactQueue xq, cudaStream_t st, bool poly = false, bool dir = false);
 cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int grid, int m,
@@ -286,7 +318,7 @@ cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int 
 size_t pair_fp32_smem(int nbins, int* replicas, bool inh = false);
 size_t pair_fp64_smem(int nbins, int* replicas, bool inh = false);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
-int pair_fp32_blocks_per_sm(size_t smem);
+int pair_fp32_blocks_per_sm(size_t smem, int bps = 2);
 int pair_fp64_blocks_per_sm(size_t smem, bool inh = false);
 // m grids of cs x ct (a realization of a directional K holds nsec consecutive grids);
 // L = sqrt(lfac K / (2 pi t)) - s (lfac = nsec, 1 for the plain estimator)
@@ -336,6 +368,22 @@ struct SimPlan {
 
 // Runs the observed pattern (when include_obs) and the simulations of `plan` on h's stream.
 int run_plan(stk_handle* h, const stk_request* q, const SimPlan& plan, bool include_obs);
+// Jobs (observed pattern + plan) on several handles whose FP32 pair kernels run as one
+// persistent launch per kernel class: each part's generation and grid index are built on its
+// handle's stream, the fused launch runs on the first part's stream once all are built, then
+// each part's FP64 queue, finalisation and envelopes follow on its own stream.  The results
+// equal run_plan's bit for bit (exact fixed-point sums).  A part that turns out not to fit
+// one wave runs alone afterwards.  fused_launches: pair launches issued for the fused parts.
+struct FusePart {
+    stk_handle* h;
+    const stk_request* q;
+    const SimPlan* plan;
+};
+// below this many point-realizations a job is small enough to share a launch (and is never
+// tuned, so its launch shape is the tuned or planned one of its problem shape)
+constexpr double kFuseMaxPointRealizations = 2.0e7;
+bool fusable_job(const stk_handle* h, const stk_request* q, int64_t R);
+int run_plans_fused(const std::vector<FusePart>& parts, int* fused_launches);
 // Copies rows of the last job's grids to host: what = 0 K, 1 L, 2 raw sum, 3 count (int64),
 // 4 envelope rows (K_lo, K_hi, L_lo, L_hi of each group, 4 rows per group).
 int fetch_rows(stk_handle* h, int what, int row0, int rows, void* dst);

@@ -127,6 +127,15 @@ def test_null_handles_and_servers_are_rejected(lib):
     assert L.stk_server_unregister(None, 1) == 1
     assert L.stk_run(None, None, None) == 1
     assert "NULL" in stk.stk_last_error()
+    # fused jobs: NULL arrays and a job count outside 1 .. STK_MAX_FUSED_JOBS
+    assert L.stk_run_fused(None, None, None, 1, None) == 1
+    hs = (P * 1)(None)
+    qs = (stk._lib.stk_request * 1)()
+    rs = (stk._lib.stk_result * 1)()
+    assert L.stk_run_fused(hs, qs, rs, 0, None) == 1
+    assert L.stk_run_fused(hs, qs, rs, 257, None) == 1
+    assert L.stk_run_fused(hs, qs, rs, 1, None) == 1  # a NULL handle
+    assert "NULL" in stk.stk_last_error()
 
 
 def test_merge_entry_points_reject_bad_arguments_without_a_device(lib):

@@ -212,6 +212,29 @@ def test_every_grid_refinement(stk, orc, wl, prec, fs, ft, monkeypatch):
         assert st["internal_errors"] == 0
 
 
+@pytest.mark.parametrize("tile,bps", [(8, 2), (32, 2), (64, 2), (1, 2), (16, 3), (64, 3)])
+def test_every_launch_shape(stk, orc, wl, tile, bps, monkeypatch):
+    # the FP32 kernel's launch shape (units per tile claim, blocks per SM with the matching
+    # register allocation) changes only the schedule: the accumulators are exact integers, so
+    # every shape gives the default shape's grids bit for bit, and the oracle's
+    c = _refine_case(orc, wl)
+    with stk.Pattern(c["x"], c["y"], c["t"], c["box"]) as p:
+        monkeypatch.setenv("STK_GRID_F", "2")
+        ref = p.run(c["s"], c["tt"], n_sims=3, seed=11, prec=1, want_sims=True)
+        st0 = p.stats()
+        assert (st0["tile_units"], st0["blocks_per_sm"]) == (16, 2)
+        monkeypatch.setenv("STK_TILE_UNITS", str(tile))
+        monkeypatch.setenv("STK_BLOCKS_PER_SM", str(bps))
+        got = p.run(c["s"], c["tt"], n_sims=3, seed=11, prec=1, want_sims=True)
+        st = p.stats()
+    assert st["tile_units"] == tile
+    assert st["blocks_per_sm"] in ((3,) if bps == 3 else (2,))
+    assert st["internal_errors"] == 0
+    for key in ("K", "L", "S", "C", "K_sims", "C_sims", "K_lo", "K_hi"):
+        np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
+    assert_grids(got, c["want"], 1, f"tile={tile}, bps={bps}")
+
+
 def test_tuned_refinement_gives_the_same_job(stk, wl, monkeypatch):
     # a batched job large enough to be tuned: the tuner's choice (1..3) must not change counts,
     # and K stays within the FP32 tolerance of the planner's grid
@@ -226,7 +249,13 @@ def test_tuned_refinement_gives_the_same_job(stk, wl, monkeypatch):
         monkeypatch.setenv("STK_TUNE", "1")
         got = p.run(s, tt, n_sims=80, seed=5, want_sims=True)
         st = p.stats()
+        # a job of the same shape too small to be tuned takes the tuned launch shape
+        p.run(s, tt, n_sims=2, seed=6)
+        st_small = p.stats()
     assert st["grid_refinement"] in (1, 2, 3) and st["grid_refinement_t"] in (1, 2, 3)
+    assert st["tile_units"] in (8, 16, 32, 64) and st["blocks_per_sm"] in (2, 3)
+    shape = ("grid_refinement", "grid_refinement_t", "tile_units", "blocks_per_sm")
+    assert [st_small[k] for k in shape] == [st[k] for k in shape]
     assert f_plan in (1, 2)
     np.testing.assert_array_equal(got["C"], ref["C"])
     np.testing.assert_array_equal(got["C_sims"], ref["C_sims"])
