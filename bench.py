@@ -261,6 +261,40 @@ def run_reference(args):
     return 0
 
 
+def _serve_stream(sv, ids, reqs, rate):
+    """Submits `reqs` at their arrival times from another thread, waits for every result;
+    returns (the rate's row of statistics, the served results)."""
+    sv.reset_stats()
+    tickets = [None] * len(reqs)
+
+    def submit_all():
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            dt = r["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = sv.submit(ids[r["dataset"]], r["s"], r["tt"],
+                                   n_sims=r["n_sims"], seed=r["seed"], want_sims=False)
+
+    th = threading.Thread(target=submit_all)
+    th.start()
+    th.join()
+    served = [sv.poll(tk) for tk in tickets]
+    st = sv.stats()
+    done = max(1, st["completed"])
+    row = {
+        "rate_hz": rate, "offered_s": reqs[-1]["arrival_s"],
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+        "mean_ms": st["mean_ms"], "jobs_per_s": st["jobs_per_s"],
+        "sims_per_s": st["sims_per_s"], "completed": st["completed"],
+        "failed": st["failed"], "batches": st["batches"],
+        "merged_fraction": st["merged_jobs"] / done,
+        "fused_fraction": st["fused_jobs"] / done,
+        "launches_per_job": st["kernel_launches"] / done,
+        "max_queue_depth": st["max_queue_depth"], "peak_device_bytes": st["peak_bytes"]}
+    return row, served
+
+
 def serve_bench(args, stk, seed=0):
     """Serving loop on synthetic request streams (Poisson arrivals, n log-uniform in [1e3, 1e6],
     CSR / Thomas / POI-mixture point sets kept resident, 5-50 thresholds per axis, 0-199
@@ -286,37 +320,54 @@ def serve_bench(args, stk, seed=0):
         for ri, rate in enumerate(rates):
             ds2, reqs = wl.serving_stream(count, seed=seed, rate_hz=rate)
             assert len(ds2) == len(datasets) and all(a.n == b.n for a, b in zip(ds2, datasets))
-            sv.reset_stats()
-            tickets = [None] * len(reqs)
-
-            def submit_all():
-                t0 = time.perf_counter()
-                for i, r in enumerate(reqs):
-                    dt = r["arrival_s"] - (time.perf_counter() - t0)
-                    if dt > 0:
-                        time.sleep(dt)
-                    tickets[i] = sv.submit(ids[r["dataset"]], r["s"], r["tt"],
-                                           n_sims=r["n_sims"], seed=r["seed"], want_sims=False)
-
-            th = threading.Thread(target=submit_all)
-            th.start()
-            th.join()
-            served = [sv.poll(tk) for tk in tickets]
-            st = sv.stats()
-            done = max(1, st["completed"])
-            out["sweep"].append({
-                "rate_hz": rate, "offered_s": reqs[-1]["arrival_s"],
-                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-                "mean_ms": st["mean_ms"], "jobs_per_s": st["jobs_per_s"],
-                "sims_per_s": st["sims_per_s"], "completed": st["completed"],
-                "failed": st["failed"], "batches": st["batches"],
-                "merged_fraction": st["merged_jobs"] / done,
-                "launches_per_job": st["kernel_launches"] / done,
-                "max_queue_depth": st["max_queue_depth"], "peak_device_bytes": st["peak_bytes"]})
+            row, served = _serve_stream(sv, ids, reqs, rate)
+            out["sweep"].append(row)
             if ri == len(rates) - 1:  # results of the heaviest stream, to check against alone
                 served_sample = [(reqs[i], served[i][0])
                                  for i in range(0, len(reqs), max(1, len(reqs) // 20))][:20]
         out["slots"] = args.serve_slots
+    # small jobs on different point sets sharing pair launches (cfg.fuse): the heaviest stream
+    # again, and a stream of tiny jobs (n in [1e3, 1e4], at most 20 simulations) with and
+    # without it
+    def fused_vs_not(dsets, reqs, rate):
+        rows = {}
+        for fuse in (True, False):
+            with stk.Server(slots=args.serve_slots, fuse=fuse) as sv:
+                ids = [sv.register(d.x, d.y, d.t, d.box) for d in dsets]
+                for k, d in enumerate(dsets):
+                    sv.poll(sv.submit(ids[k], d.s, d.tt, n_sims=1, seed=1))
+                rows["fused" if fuse else "not_fused"], _ = _serve_stream(sv, ids, reqs, rate)
+        return rows
+
+    _, reqs = wl.serving_stream(count, seed=seed, rate_hz=rates[-1])
+    out["heaviest_with_fusing"] = fused_vs_not(datasets, reqs, rates[-1])["fused"]
+    tiny_rate = 2000.0
+    tiny_sets, tiny_reqs = wl.serving_stream(3 * count, seed=seed + 1, rate_hz=tiny_rate,
+                                             n_lo=1000, n_hi=10000, max_sims=20)
+    out["tiny_jobs"] = {"requests": len(tiny_reqs), "rate_hz": tiny_rate,
+                        "n_range": [min(d.n for d in tiny_sets), max(d.n for d in tiny_sets)],
+                        **fused_vs_not(tiny_sets, tiny_reqs, tiny_rate)}
+    # the fused launch itself, one thread: 12 tiny jobs (one per point set, 20 simulations
+    # each) in one stk_run_fused call against the same jobs through stk_run one after another
+    pats = [stk.Pattern(d.x, d.y, d.t, d.box) for d in tiny_sets]
+    jobs = [dict(s=d.s, tt=d.tt, n_sims=20, seed=7 + k) for k, d in enumerate(tiny_sets)]
+    for p_, j in zip(pats, jobs):  # warm-up (tuning, workspaces)
+        p_.run(**j)
+    stk.stk_run_fused([p_.h for p_ in pats], jobs)
+    reps = 20
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for p_, j in zip(pats, jobs):
+            p_.run(**j)
+    t_seq = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, fl = stk.stk_run_fused([p_.h for p_ in pats], jobs)
+    t_fused = (time.perf_counter() - t0) / reps
+    for p_ in pats:
+        p_.close()
+    out["fused_call"] = {"jobs": len(jobs), "sims_each": 20, "ms_one_by_one": 1e3 * t_seq,
+                         "ms_fused": 1e3 * t_fused, "pair_launches_fused": fl}
     # served = alone, bit for bit, on a sample of the heaviest stream's requests
     same, counts, checked, worst = True, True, 0, 0.0
     for r, got in served_sample:

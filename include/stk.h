@@ -249,7 +249,8 @@ typedef struct {
     int32_t obs_index_reused;  /* 1: the observed pattern's sorted grid index was resident (the
                                   last job on h had the same grid), not rebuilt */
     int32_t tile_units;        /* launch shape of the FP32 pair kernel: work units a block
-                                  claims at once (the refinement tuner's choice, else 16) */
+                                  claims at once (the launch-shape tuner's choice for the
+                                  job's problem shape, made by its first job; 16 untuned) */
     int32_t blocks_per_sm;     /* resident blocks per SM of the pair kernel's launch (the FP32
                                   kernel: 2, or 3 where the tuner chose its 85-register build) */
 } stk_stats;
@@ -260,7 +261,7 @@ int stk_run(stk_handle* h, const stk_request* req, stk_result* res);
  * persistent launch (the batched path of Section 3's envelope over small problems at once):
  * job i is reqs[i] on hs[i] with results into results[i], exactly as stk_run(hs[i], &reqs[i],
  * &results[i]) would compute them (bit for bit: the sums are exact fixed-point integers, and a
- * job of this size takes its problem shape's tuned or planned grid either way).  Each job's
+ * job takes its problem shape's tuned launch shape either way).  Each job's
  * simulation generation and grid index run on its handle's stream; the fused pair launch runs
  * on hs[0]'s stream (or the first fused job's) once every index is built, with each job's
  * constants, grid and accumulators taken from a per-job descriptor; each job's FP64 queue,
@@ -388,7 +389,15 @@ int stk_k_noalloc(const double* d_x, const double* d_y, const double* d_t, int64
  *     their simulations go through the same launches, each job's under its own seed:
  *     realization k of a job is Philox realization k under the job's seed, exactly as in
  *     stk_envelope, and every realization is accumulated on its own, so a job's results do
- *     not depend on the jobs it ran with.
+ *     not depend on the jobs it ran with;
+ *   - fused launches (cfg.fuse): when a slot takes a small batch (FP32-guarded, rectangle,
+ *     isotropic or no edge correction, no sectors, below 2e7 point-realizations) it also takes
+ *     the next admissible such batches on other idle point sets (up to 16, 2e7
+ *     point-realizations in all) and runs their pair kernels as one persistent launch, as
+ *     stk_run_fused does; each job's results are those it would have alone, bit for bit.  It
+ *     pays where launches and host work dominate (streams of tiny jobs); where the slots'
+ *     concurrent streams already keep the GPU busy it adds latency (a group finishes
+ *     together), so it is off by default.
  * A server is thread-safe; handles created with stk_create are unaffected by it. */
 typedef struct stk_server stk_server;
 
@@ -401,6 +410,8 @@ typedef struct {
     int max_queue;            /* queued jobs beyond which stk_submit returns STK_EBUSY;
                                  0 = 65536 */
     int no_merge;             /* 1: run every job on its own (no continuous batching) */
+    int fuse;                 /* 1: let small batches on different point sets share a pair
+                                 launch (see stk_run_fused); 0: every batch launches its own */
 } stk_server_config;
 
 typedef struct {
@@ -434,6 +445,8 @@ typedef struct {
     int64_t peak_bytes;           /* most held (accounted) at once */
     int64_t budget_bytes;
     int64_t kernel_launches;      /* CUDA kernels the batches launched (graph replays included) */
+    int64_t fused_jobs;           /* jobs whose pair kernel ran in one launch with jobs on other
+                                     point sets */
 } stk_serve_stats;
 
 /* Errors: STK_EINVAL (bad config), STK_ENODEV, STK_ECUDA, STK_ENOMEM. */

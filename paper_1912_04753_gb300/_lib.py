@@ -63,7 +63,7 @@ class stk_stats(ctypes.Structure):
 class stk_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int),
                 ("mem_budget_bytes", ctypes.c_int64), ("max_batch_sims", ctypes.c_int),
-                ("max_queue", ctypes.c_int), ("no_merge", ctypes.c_int)]
+                ("max_queue", ctypes.c_int), ("no_merge", ctypes.c_int), ("fuse", ctypes.c_int)]
 
 
 class stk_job(ctypes.Structure):
@@ -81,7 +81,7 @@ class stk_serve_stats(ctypes.Structure):
         [(k, ctypes.c_double) for k in (
             "p50_ms", "p99_ms", "max_ms", "mean_ms", "wall_s", "jobs_per_s", "sims_per_s")] +
         [(k, ctypes.c_int64) for k in ("resident_bytes", "peak_bytes", "budget_bytes",
-                                        "kernel_launches")])
+                                        "kernel_launches", "fused_jobs")])
 
 
 _lib = None
@@ -471,10 +471,10 @@ def stk_k_noalloc(x, y, t, box, s, tt, K, L, S, C, edge_mode=STK_EDGE_ISOTROPIC,
 
 
 def stk_server_create(device=0, slots=0, mem_budget_bytes=0, max_batch_sims=0, max_queue=0,
-                      no_merge=False):
+                      no_merge=False, fuse=False):
     """Start a serving loop on `device` (returns an opaque server)."""
     cfg = stk_server_config(device, slots, int(mem_budget_bytes), max_batch_sims, max_queue,
-                            1 if no_merge else 0)
+                            1 if no_merge else 0, 1 if fuse else 0)
     sv = _P()
     _check(load().stk_server_create(ctypes.byref(cfg), ctypes.byref(sv)))
     return sv

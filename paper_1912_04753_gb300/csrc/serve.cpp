@@ -71,6 +71,24 @@ struct Dataset {
     int pending = 0;        // queued + running jobs
 };
 
+// The request of a batch headed by `head` (thresholds, modes; n_sims and seeds come from the
+// batch's plan).
+stk_request head_request(const Job& head) {
+    stk_request q;
+    memset(&q, 0, sizeof q);
+    q.s = head.s.data();
+    q.cs = (int)head.s.size();
+    q.tt = head.tt.data();
+    q.ct = (int)head.tt.size();
+    q.edge_mode = head.edge_mode;
+    q.prec = head.prec;
+    q.norm = head.norm;
+    q.exec = STK_EXEC_BATCHED;
+    q.sim_method = head.sim_method;
+    q.n_sectors = head.n_sectors;
+    return q;
+}
+
 bool same_params(const Job& a, const Job& b) {
     return a.dataset == b.dataset && a.s == b.s && a.tt == b.tt && a.edge_mode == b.edge_mode &&
            a.prec == b.prec && a.norm == b.norm && a.sim_method == b.sim_method &&
@@ -94,7 +112,7 @@ struct stk_server {
     int running = 0;
     // statistics since the last reset
     int64_t submitted = 0, completed = 0, failed = 0, max_depth = 0, batches = 0, merged = 0;
-    int64_t sims_done = 0, pairs = 0, launches = 0;
+    int64_t sims_done = 0, pairs = 0, launches = 0, fused_jobs = 0;
     std::vector<double> lat_ms;
     bool have_first = false;
     Clock::time_point t_first, t_last;
@@ -128,14 +146,32 @@ struct Batch {
     size_t grant = 0;
 };
 
+// A fused group being formed: its point sets and the point-realizations it may still take.
+struct FuseGroup {
+    std::vector<uint64_t> datasets;
+    double room = 0.0;
+};
+
 // Picks the next batch and admits it (lock held).  Returns false when nothing can start now.
-bool take_batch(stk_server* sv, Batch* out) {
+// fuse: a fused group being formed; then only a batch on another point set that can share the
+// group's pair launch (a small job that fits one wave now and the group's room) is taken, and
+// nothing is failed or waited for.
+bool take_batch(stk_server* sv, Batch* out, FuseGroup* fuse = nullptr) {
     for (size_t qi = 0; qi < sv->queue.size(); ++qi) {
         auto jt = sv->jobs.find(sv->queue[qi]);
         if (jt == sv->jobs.end()) continue;
         std::shared_ptr<Job> head = jt->second;
         Dataset& ds = sv->datasets[head->dataset];
         if (ds.busy) continue;
+        if (fuse) {
+            if (std::find(fuse->datasets.begin(), fuse->datasets.end(), head->dataset) !=
+                fuse->datasets.end())
+                continue;
+            const stk_request hq = head_request(*head);
+            if (!stk::fusable_job(ds.h, &hq, 1 + (int64_t)head->n_sims) ||
+                (double)ds.n * (1.0 + head->n_sims) > fuse->room)
+                continue;
+        }
         // the batch: the head plus compatible queued jobs, in arrival order
         std::vector<size_t> take{qi};
         int sims = head->n_sims;
@@ -152,15 +188,7 @@ bool take_batch(stk_server* sv, Batch* out) {
         }
         int groups = 0;
         for (size_t k : take) groups += sv->jobs[sv->queue[k]]->n_sims > 0 ? 1 : 0;
-        stk_request q;
-        memset(&q, 0, sizeof q);
-        q.s = head->s.data();
-        q.cs = (int)head->s.size();
-        q.tt = head->tt.data();
-        q.ct = (int)head->tt.size();
-        q.prec = head->prec;
-        q.edge_mode = head->edge_mode;
-        q.n_sectors = head->n_sectors;
+        const stk_request q = head_request(*head);
         stk::Footprint fp;
         const int R = 1 + sims;
         int rc = stk::job_footprint(ds.h, &q, R, groups, &fp);
@@ -178,6 +206,13 @@ bool take_batch(stk_server* sv, Batch* out) {
             const size_t free_now =
                 sv->budget > sv->accounted() ? sv->budget - sv->accounted() : 0;
             if (stk::handle_workspace_bytes(ds.h) > free_now) stk::handle_trim(ds.h);
+            if (fuse && ((double)ds.n * R > fuse->room ||
+                         fp.fixed + fp.per_real * (size_t)R > free_now)) {
+                const size_t still = stk::handle_workspace_bytes(ds.h);
+                sv->idle_total += still;  // not now: it would not run in one wave
+                ds.idle_bytes = still;
+                continue;
+            }
             if (need_min > free_now) {
                 const size_t still = stk::handle_workspace_bytes(ds.h);
                 sv->idle_total += still;
@@ -223,23 +258,22 @@ bool take_batch(stk_server* sv, Batch* out) {
     return false;
 }
 
-// Runs one batch on its point set's stream (lock not held).  Fills the jobs' results.
-int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual, int64_t* launches) {
-    const Job& head = *b.jobs[0];
+// A batch's request and simulation plan: every job's simulations under its own seed, its
+// envelope group and first row.
+struct BatchRun {
     stk_request q;
-    memset(&q, 0, sizeof q);
-    q.s = head.s.data();
-    q.cs = (int)head.s.size();
-    q.tt = head.tt.data();
-    q.ct = (int)head.tt.size();
-    q.edge_mode = head.edge_mode;
-    q.prec = head.prec;
-    q.norm = head.norm;
-    q.exec = STK_EXEC_BATCHED;
-    q.sim_method = head.sim_method;
-    q.n_sectors = head.n_sectors;
     stk::SimPlan plan;
-    std::vector<int> group_of(b.jobs.size(), -1), first_row(b.jobs.size(), 0);
+    std::vector<int> group_of, first_row;
+    bool any_sims = false;
+};
+
+void plan_batch(const Batch& b, BatchRun* br) {
+    br->q = head_request(*b.jobs[0]);
+    stk::SimPlan& plan = br->plan;
+    std::vector<int>& group_of = br->group_of;
+    std::vector<int>& first_row = br->first_row;
+    group_of.assign(b.jobs.size(), -1);
+    first_row.assign(b.jobs.size(), 0);
     bool any_sims = false;
     for (size_t j = 0; j < b.jobs.size(); ++j) {
         const Job& job = *b.jobs[j];
@@ -254,10 +288,18 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual, int64_t* l
             any_sims = any_sims || job.want_sims;
         }
     }
-    (void)sv;
-    stk::handle_set_wave_budget(h, b.grant);
-    int rc = stk::run_plan(h, &q, plan, true);
-    if (rc) return rc;
+    br->any_sims = any_sims;
+}
+
+// Copies the batch's results (the last job run on h) into its jobs.
+int collect_batch(stk_handle* h, Batch& b, const BatchRun& br, int64_t* qual,
+                  int64_t* launches) {
+    const stk_request& q = br.q;
+    const stk::SimPlan& plan = br.plan;
+    const std::vector<int>& group_of = br.group_of;
+    const std::vector<int>& first_row = br.first_row;
+    const bool any_sims = br.any_sims;
+    int rc = STK_OK;
     const int nbins = q.cs * q.ct * (q.n_sectors > 1 ? q.n_sectors : 1);
     const int R = 1 + (int)plan.seed.size();
     std::vector<double> K(nbins), L(nbins), S(nbins), env(4 * (size_t)nbins * plan.groups.size());
@@ -302,55 +344,133 @@ int run_batch(stk_server* sv, stk_handle* h, Batch& b, int64_t* qual, int64_t* l
     return STK_OK;
 }
 
+// Runs one batch on its point set's stream (lock not held).  Fills the jobs' results.
+int run_batch(stk_handle* h, Batch& b, int64_t* qual, int64_t* launches) {
+    BatchRun br;
+    plan_batch(b, &br);
+    stk::handle_set_wave_budget(h, b.grant);
+    const int rc = stk::run_plan(h, &br.q, br.plan, true);
+    if (rc) return rc;
+    return collect_batch(h, b, br, qual, launches);
+}
+
+// Runs batches on different point sets with their pair kernels in shared launches (lock not
+// held); per batch its status, qualifying pairs and kernel launches.
+void run_fused_group(std::vector<Batch>& group, const std::vector<stk_handle*>& hs,
+                     std::vector<int>* rcs, std::vector<int64_t>* quals,
+                     std::vector<int64_t>* launches) {
+    const size_t ng = group.size();
+    std::vector<BatchRun> brs(ng);
+    std::vector<stk::FusePart> parts;
+    for (size_t i = 0; i < ng; ++i) {
+        plan_batch(group[i], &brs[i]);
+        stk::handle_set_wave_budget(hs[i], group[i].grant);
+        parts.push_back({hs[i], &brs[i].q, &brs[i].plan});
+    }
+    int fused = 0;
+    const int rc = stk::run_plans_fused(parts, &fused);
+    rcs->assign(ng, rc);
+    quals->assign(ng, 0);
+    launches->assign(ng, 0);
+    if (rc) return;
+    for (size_t i = 0; i < ng; ++i)
+        (*rcs)[i] = collect_batch(hs[i], group[i], brs[i], &(*quals)[i], &(*launches)[i]);
+}
+
+// Bookkeeping after a batch ran (lock held).
+void finish_batch(stk_server* sv, Batch& b, int rc, const std::string& err, int64_t qual,
+                  int64_t launches, Clock::time_point now) {
+    stk_handle* h = sv->datasets[b.dataset].h;
+    sv->granted -= b.grant;
+    sv->running -= 1;
+    Dataset& d2 = sv->datasets[b.dataset];
+    d2.busy = false;
+    d2.pending -= (int)b.jobs.size();
+    d2.idle_bytes = stk::handle_workspace_bytes(h);
+    sv->idle_total += d2.idle_bytes;
+    if (sv->accounted() > sv->budget) {  // the runner held more than granted: give it back
+        sv->idle_total -= d2.idle_bytes;
+        stk::handle_trim(h);
+        d2.idle_bytes = 0;
+    }
+    sv->batches += 1;
+    if (b.jobs.size() > 1) sv->merged += (int64_t)b.jobs.size();
+    if (rc == STK_OK) sv->pairs += qual;
+    sv->launches += launches;
+    for (auto& jp : b.jobs) {
+        Job& j = *jp;
+        j.t_done = now;
+        if (rc == STK_OK) {
+            j.state = JobState::Done;
+            sv->completed += 1;
+            sv->sims_done += j.n_sims;
+            sv->lat_ms.push_back(
+                std::chrono::duration<double, std::milli>(now - j.t_submit).count());
+            sv->t_last = now;
+        } else {
+            j.state = JobState::Failed;
+            j.rc = rc;
+            j.err = err;
+            sv->failed += 1;
+        }
+    }
+}
+
+constexpr size_t kMaxFusedBatches = 16;
+
 void worker_main(stk_server* sv) {
     cudaSetDevice(sv->cfg.device);
     std::unique_lock<std::mutex> lock(sv->mu);
     while (!sv->stop) {
-        Batch b;
-        if (!take_batch(sv, &b)) {
+        std::vector<Batch> group(1);
+        if (!take_batch(sv, &group[0])) {
             sv->cv_work.wait(lock);
             continue;
         }
-        Dataset& ds = sv->datasets[b.dataset];
-        stk_handle* h = ds.h;
+        // a small batch takes the next small batches on other idle point sets into its launch
+        if (sv->cfg.fuse) {
+            int sims = 0;
+            for (const auto& j : group[0].jobs) sims += j->n_sims;
+            const stk_request hq = head_request(*group[0].jobs[0]);
+            const Dataset& d0 = sv->datasets[group[0].dataset];
+            if (stk::fusable_job(d0.h, &hq, 1 + (int64_t)sims)) {
+                // a group holds about as much work as one job that is just too large to fuse,
+                // so that fusing gathers small jobs without starving the other slots
+                FuseGroup fg;
+                fg.datasets.push_back(group[0].dataset);
+                fg.room = stk::kFuseMaxPointRealizations - (double)d0.n * (1.0 + sims);
+                while (group.size() < kMaxFusedBatches) {
+                    Batch bk;
+                    if (!take_batch(sv, &bk, &fg)) break;
+                    int bs = 0;
+                    for (const auto& j : bk.jobs) bs += j->n_sims;
+                    fg.datasets.push_back(bk.dataset);
+                    fg.room -= (double)sv->datasets[bk.dataset].n * (1.0 + bs);
+                    group.push_back(std::move(bk));
+                }
+            }
+        }
+        std::vector<stk_handle*> hs;
+        for (const Batch& b : group) hs.push_back(sv->datasets[b.dataset].h);
         lock.unlock();
-        int64_t qual = 0, launches = 0;
-        const int rc = run_batch(sv, h, b, &qual, &launches);
-        const std::string err = rc ? std::string(stk_last_error()) : std::string();
+        std::vector<int> rcs;
+        std::vector<int64_t> quals, launches;
+        if (group.size() == 1) {
+            int64_t qual = 0, nl = 0;
+            rcs.push_back(run_batch(hs[0], group[0], &qual, &nl));
+            quals.push_back(qual);
+            launches.push_back(nl);
+        } else {
+            run_fused_group(group, hs, &rcs, &quals, &launches);
+        }
+        std::string err;
+        for (int rc : rcs)
+            if (rc) err = stk_last_error();
         const auto now = Clock::now();
         lock.lock();
-        sv->granted -= b.grant;
-        sv->running -= 1;
-        Dataset& d2 = sv->datasets[b.dataset];
-        d2.busy = false;
-        d2.pending -= (int)b.jobs.size();
-        d2.idle_bytes = stk::handle_workspace_bytes(h);
-        sv->idle_total += d2.idle_bytes;
-        if (sv->accounted() > sv->budget) {  // the runner held more than granted: give it back
-            sv->idle_total -= d2.idle_bytes;
-            stk::handle_trim(h);
-            d2.idle_bytes = 0;
-        }
-        sv->batches += 1;
-        if (b.jobs.size() > 1) sv->merged += (int64_t)b.jobs.size();
-        if (rc == STK_OK) sv->pairs += qual;
-        sv->launches += launches;
-        for (auto& jp : b.jobs) {
-            Job& j = *jp;
-            j.t_done = now;
-            if (rc == STK_OK) {
-                j.state = JobState::Done;
-                sv->completed += 1;
-                sv->sims_done += j.n_sims;
-                sv->lat_ms.push_back(
-                    std::chrono::duration<double, std::milli>(now - j.t_submit).count());
-                sv->t_last = now;
-            } else {
-                j.state = JobState::Failed;
-                j.rc = rc;
-                j.err = err;
-                sv->failed += 1;
-            }
+        for (size_t i = 0; i < group.size(); ++i) {
+            finish_batch(sv, group[i], rcs[i], err, quals[i], launches[i], now);
+            if (group.size() > 1) sv->fused_jobs += (int64_t)group[i].jobs.size();
         }
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
@@ -618,6 +738,7 @@ int stk_server_stats(stk_server* sv, stk_serve_stats* out) {
     out->simulations = sv->sims_done;
     out->qualifying_pairs = sv->pairs;
     out->kernel_launches = sv->launches;
+    out->fused_jobs = sv->fused_jobs;
     out->p50_ms = percentile(sv->lat_ms, 50.0);
     out->p99_ms = percentile(sv->lat_ms, 99.0);
     double mx = 0, sum = 0;
@@ -641,7 +762,7 @@ int stk_server_reset_stats(stk_server* sv) {
     if (!sv) return note(STK_EINVAL, "server is NULL");
     std::lock_guard<std::mutex> lock(sv->mu);
     sv->submitted = sv->completed = sv->failed = sv->max_depth = 0;
-    sv->batches = sv->merged = sv->sims_done = sv->pairs = sv->launches = 0;
+    sv->batches = sv->merged = sv->sims_done = sv->pairs = sv->launches = sv->fused_jobs = 0;
     sv->lat_ms.clear();
     sv->have_first = false;
     sv->peak = sv->accounted();

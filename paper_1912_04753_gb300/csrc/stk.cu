@@ -267,10 +267,11 @@ constexpr int kNotFusable = -1000;  // run_job with a FuseCtx: the job cannot be
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
             int* R_out, int f_force = 0, FuseCtx* fuse = nullptr);
 
-// Grid refinement tuner: for batched jobs large enough to amortise it, times the pair kernel
-// on a few CSR realizations for (fs, ft) = (f, f), f = 1..3, then the best fs with ft one step
-// finer and coarser, and keeps the fastest per problem shape (n, box, largest thresholds,
-// precision, edge mode) for the life of the process.
+// Launch-shape tuner: the first batched job of a problem shape (n, box, largest thresholds,
+// precision, edge mode, simulation method, sectors) times the pair kernel on a few CSR
+// realizations (about 4e6 point-realizations) for the grid refinement, the unit tile and the
+// blocks per SM (tuned_refinement), and every later job of the shape takes that choice for the
+// life of the process.
 struct TuneKey {
     int64_t n;
     double box[6], s_max, t_max;
@@ -288,6 +289,7 @@ struct TuneChoice {
 inline int shape_code(const TuneChoice& c) { return c.f | (c.tile << 16) | (c.bps << 24); }
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tuned;
+thread_local bool t_tuning = false;  // the tuner's trial jobs are running (not logged)
 
 // The problem shape of a job, for the tuner's table.
 TuneKey tune_key(const stk_handle* h, const stk_request* q) {
@@ -305,13 +307,6 @@ TuneKey tune_key(const stk_handle* h, const stk_request* q) {
 }
 
 // The refinement tuned for this problem shape, if any (0: none yet).
-TuneChoice tuned_lookup(const stk_handle* h, const stk_request* q) {
-    const TuneKey key = tune_key(h, q);
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tuned.find(key);
-    return it == g_tuned.end() ? TuneChoice() : it->second;
-}
-
 // Launch shape for a job shape, timed once per process on a few CSR realizations and kept:
 // first the grid refinement (fs = ft = 1, 2, 3, then the time axis one step either side), then
 // with it the tile of work units a block claims (8, 32, 64 against 16), then, for the plain
@@ -337,6 +332,7 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
     }
     stk_request tq = *q;
     tq.centre_mask = nullptr;
+    tq.exec = STK_EXEC_BATCHED;  // the shape serves plain jobs too; trials run batched
     Grid gp;
     char err[256];
     if (build_grid(h->box, key.s_max, key.t_max, h->n, 0, &gp, err, sizeof err))
@@ -349,7 +345,9 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
     // times shape c; `incumbent`: the step's default, which others must beat by 3%
     auto trial_run = [&](TuneChoice c, bool incumbent) -> int {
         int R = 0;
+        t_tuning = true;
         const int rc = run_job(h, &tq, false, trial, &R, shape_code(c));
+        t_tuning = false;
         if (rc == STK_ENOMEM) return STK_OK;  // a shape that does not fit is no candidate
         if (rc) return rc;
         float ms = (float)h->last.ms_pair;
@@ -389,9 +387,9 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
             if ((rc = trial_run(c, false))) return rc;
         }
     }
+    // a shape tuned meanwhile by another thread keeps its first choice
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned[key] = best;
-    *out = best;
+    *out = g_tuned.emplace(key, best).first->second;
     return STK_OK;
 }
 
@@ -400,6 +398,7 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
 std::mutex g_log_mu;
 
 void log_job(const stk_handle* h, const stk_request* q, int nsec) {
+    if (t_tuning) return;
     const char* path = getenv("STK_JOB_LOG");
     if (!path || !*path) return;
     const stk_stats& st = h->last;
@@ -531,18 +530,15 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         if (const char* be = getenv("STK_BLOCKS_PER_SM")) bps_req = atoi(be);
     }
     const char* tune_env = getenv("STK_TUNE");
-    const bool tune_on = q->exec == STK_EXEC_BATCHED && !(tune_env && atoi(tune_env) == 0) &&
-                         f_req == 0 && tile_req == 0 && bps_req == 0;
+    const bool tune_on = !(tune_env && atoi(tune_env) == 0) && f_req == 0 && tile_req == 0 &&
+                         bps_req == 0;
     if (tune_on) {
+        // the first job of a problem shape tunes it, whatever its size, and every later job of
+        // the shape takes that choice: a job's grids then never depend on which jobs came
+        // before it or shared its batch (a served job equals the same job run alone)
         TuneChoice c;
-        if ((double)n * (double)R >= 2.0e7 && !fuse) {
-            rc = tuned_refinement(h, q, &c);
-            if (rc) return rc;
-        } else {
-            // a smaller job of a shape tuned before takes the same shape, so that its grids do
-            // not depend on the jobs it shares a batch with (a served job equals it alone)
-            c = tuned_lookup(h, q);
-        }
+        rc = tuned_refinement(h, q, &c);
+        if (rc) return rc;
         f_req = c.f;
         tile_req = c.tile;
         bps_req = c.bps;

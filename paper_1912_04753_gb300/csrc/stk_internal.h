@@ -379,8 +379,7 @@ struct FusePart {
     const stk_request* q;
     const SimPlan* plan;
 };
-// below this many point-realizations a job is small enough to share a launch (and is never
-// tuned, so its launch shape is the tuned or planned one of its problem shape)
+// below this many point-realizations a job is small enough to share a launch
 constexpr double kFuseMaxPointRealizations = 2.0e7;
 bool fusable_job(const stk_handle* h, const stk_request* q, int64_t R);
 int run_plans_fused(const std::vector<FusePart>& parts, int* fused_launches);

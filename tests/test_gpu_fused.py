@@ -160,3 +160,35 @@ def test_fused_arguments_checked(stk):
         # both handles still compute correctly
         res, _ = stk.stk_run_fused([p.h, q.h], [jobs[0], jobs[1]])
         _same(res[0], _alone(stk, sets[0], jobs[0])[0], "after errors")
+
+
+@pytest.mark.parametrize("fuse", [True, False])
+def test_served_jobs_on_several_point_sets_share_a_launch(stk, fuse):
+    """One slot: while an FP64 job (never fused) holds it, small jobs on four point sets queue;
+    the slot then takes them as one group with shared pair launches.  Every served result
+    equals the job alone, and the statistics count the fused jobs (none without fuse)."""
+    from paper_1912_04753_gb300 import workloads as wl
+
+    sets, jobs = _sets(), _jobs(stk)
+    alone = [_alone(stk, pts, job)[0] for pts, job in zip(sets, jobs)]
+    with stk.Server(slots=1, fuse=fuse) as sv:
+        ids = [sv.register(*p) for p in sets]
+        blocker = sv.submit(ids[2], wl.even_thresholds(500.0, 10),
+                            wl.even_thresholds(30.0 * 86400.0, 10), n_sims=60, seed=5,
+                            prec=stk.STK_PREC_FP64)
+        tickets = []
+        for i, j in enumerate(jobs):
+            kw = {k: v for k, v in j.items() if k not in ("s", "tt", "n_sims", "seed")}
+            tickets.append(sv.submit(ids[i], j["s"], j["tt"], n_sims=j["n_sims"],
+                                     seed=j["seed"], **kw))
+        served = [sv.poll(tk, wait_ms=120000) for tk in tickets]
+        assert sv.poll(blocker, wait_ms=120000) is not None
+        st = sv.stats()
+    assert st["completed"] == 5 and st["failed"] == 0
+    if not fuse:
+        assert st["fused_jobs"] == 0
+    else:
+        assert st["fused_jobs"] >= 2, st
+    for i, (got, _lat) in enumerate(served):
+        want = {k: v for k, v in alone[i].items() if k in got}
+        _same(got, want, f"served job {i}")
