@@ -577,42 +577,184 @@ __device__ __forceinline__ void radius_nr(float r2, float& r, float& inv_r) {
     inv_r = y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
-// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders in FP64,
-// one per lane (crossings with the boundary, poly_weight_fast).  Out of line like the
+// Share of the circle of radius r (FP32, inv_r = 1 / r; within 2^-22 r of the reference radius)
+// around the point (cx, cy) (FP64, inside the polygon) that lies inside the polygon, in FP32
+// with an error bound (Section 3's isotropic weight is 1 / inside).  For each edge whose
+// bounding box meets the circle's, the line's signed distance h = (a - c) x u and the
+// centre's projection u0 = (c - a) . u (u the edge's unit direction) are taken in FP64 (six
+// operations); the rest is FP32.  The line meets the circle at u0 -+ t along the edge,
+// t = sqrt((r - h)(r + h)), and the crossings' polar angles are phi_m +- psi, phi_m the angle
+// of the direction from the centre to the line (phi of the edge's normal, + pi when h < 0,
+// exact in FP64) and psi = acos(|h| / r) (the fitted arc polynomial): they depend on h, r and
+// the edge's direction only, not on how far its vertices lie.  Inside arcs run from an
+// entering crossing to the next (counter-clockwise); the larger root enters when the vertices
+// run counter-clockwise.  Each crossing carries a bound on its angle's error: the polynomial's
+// 4e-7 and the rounding of h / r (5 2^-24) amplified by 1 / sin(psi) = r / t.  Returns false
+// (the order goes to FP64) for a line within 2^-19 r of tangency, a crossing within its
+// position error of a vertex, more than 8 crossings, an odd count, crossings that do not
+// alternate or lie closer than their errors, or when the bounds add up to more than 8.5e-7 of
+// the inside share; else inside and outside (their relative errors below that bound).
+constexpr int kPolyCrossF32 = 8;
+
+__device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, double cx, double cy,
+                                               float r, float inv_r, float& inside,
+                                               float& outside) {
+    const float cxf = (float)cx, cyf = (float)cy;
+    const float m = r * 1e-4f + 1e-6f * (fabsf(cxf) + fabsf(cyf)) + 1e-30f;
+    const float x0 = cxf - r - m, x1 = cxf + r + m, y0 = cyf - r - m, y1 = cyf + r + m;
+    const float band = ldexpf(r, -19);
+    double th[kPolyCrossF32];
+    float key[kPolyCrossF32], er[kPolyCrossF32];
+    bool ent[kPolyCrossF32];
+    int na = 0;
+    const float cmag = fabsf(cxf) + fabsf(cyf);
+    for (int k = 0; k < pc.nv; ++k) {
+        const float4 eb = pc.pebox[k];
+        if (eb.x > x1 || eb.y < x0 || eb.z > y1 || eb.w < y0) continue;
+        // FP32 pre-test of the line's distance: the vertex, the centre and the direction are
+        // rounded to FP32, so |h32 - h| <= 2^-22 (|a| + |c| + |h32|) (components summed)
+        const float4 e32 = pc.pef32[k];
+        const float h32 = fabsf(fmaf(e32.x - cxf, e32.w, -((e32.y - cyf) * e32.z)));
+        if (h32 > r + band + 2.4e-7f * (fabsf(e32.x) + fabsf(e32.y) + cmag + h32)) continue;
+        const EdgeDir ed = pc.pedir[k];
+        if (!(ed.len > 0.0)) continue;
+        const double fx = pc.pvx[k] - cx, fy = pc.pvy[k] - cy;
+        const double hd = fx * ed.uy - fy * ed.ux;
+        const float h = fabsf((float)hd);
+        if (h >= r + band) continue;   // the line misses the circle
+        if (h > r - band) return false;  // nearly tangent
+        const float t = sqrt_nr((r - h) * (r + h));
+        const float psi = arc_half_angle(h, r, inv_r);
+        const float u0 = (float)(-(fx * ed.ux + fy * ed.uy));
+        const float len = (float)ed.len;
+        const float rt = r / t;
+        const float err = 4.2e-7f + 3.0e-7f * rt;
+        const float uerr = 1.2e-7f * (fabsf(u0) + len + t) + 3.0e-7f * r * rt + 1.5e-7f * t;
+        const double phi = ed.phi + (hd < 0.0 ? 3.141592653589793 : 0.0);
+        const double sgn = hd < 0.0 ? -1.0 : 1.0;
+        for (int q = -1; q <= 1; q += 2) {
+            const float u = fmaf((float)q, t, u0);
+            if (fabsf(u) <= uerr || fabsf(u - len) <= uerr) return false;  // at a vertex
+            if (u < 0.0f || u >= len) continue;
+            if (na == kPolyCrossF32) return false;
+            double a = fma((double)q * sgn, (double)psi, phi);
+            a = a < 0.0 ? a + 6.283185307179586 : (a >= 6.283185307179586 ? a - 6.283185307179586 : a);
+            th[na] = a;
+            key[na] = (float)a;
+            er[na] = err;
+            ent[na] = (q > 0) == (pc.pccw != 0);
+            ++na;
+        }
+    }
+    if (na == 0) {  // the centre is inside and no crossing: the whole circle is
+        inside = 1.0f;
+        outside = 0.0f;
+        return true;
+    }
+    if (na & 1) return false;
+    // insertion sort by the angles rounded to FP32 (an order they get wrong leaves a
+    // negative gap below, which refuses the circle)
+    for (int i = 1; i < na; ++i) {
+        const double v = th[i];
+        const float kv = key[i], e = er[i];
+        const bool g = ent[i];
+        int j = i - 1;
+        while (j >= 0 && key[j] > kv) {
+            th[j + 1] = th[j];
+            key[j + 1] = key[j];
+            er[j + 1] = er[j];
+            ent[j + 1] = ent[j];
+            --j;
+        }
+        th[j + 1] = v;
+        key[j + 1] = kv;
+        er[j + 1] = e;
+        ent[j + 1] = g;
+    }
+    double in = 0.0;
+    float bound = 0.0f;
+    for (int k = 0; k < na; ++k) {
+        const int k1 = k + 1 < na ? k + 1 : 0;
+        const double gap = k + 1 < na ? th[k1] - th[k] : th[0] + 6.283185307179586 - th[k];
+        if (!(gap > (double)(er[k] + er[k1]))) return false;  // order within the errors
+        if (ent[k] == ent[k1]) return false;                   // must alternate
+        if (ent[k]) in += gap;
+        bound += er[k];
+    }
+    inside = (float)(in * 0.15915494309189535);
+    outside = (float)((6.283185307179586 - in) * 0.15915494309189535);
+    return bound * 0.15915494309189535f <= 8.5e-7f * inside;
+}
+
+// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders, the
+// inside share in FP32 with its error bound (poly_share_f32) from the accurate FP32 distance
+// of the pair (as in the rectangle's drain_weights) when the job's outline allows it
+// (pc.poly_f32), else from the crossings' directions with FP64 crossing points
+// (poly_weight_fast); what neither decides, and weights above 8 (beyond the shared
+// accumulators' bound), go to the FP64 queue.  Out of line like the
 // rectangle's version, so that the rectangle path does not carry its registers.
 __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const PairConsts* gpc,
-                                                WarpSm* wsp, RealBatch rb, ExactQueue xq,
-                                                int off, int cnt, int lane,
+                                                WarpSm* wsp, const float4* __restrict__ Ek,
+                                                const float* __restrict__ NXk,
+                                                const float* __restrict__ NYk,
+                                                const float2* __restrict__ Plok, RealBatch rb,
+                                                ExactQueue xq, int off, int cnt, int lane,
                                                 unsigned long long* he, uint32_t* hc,
                                                 uint32_t real, uint32_t c_begin) {
     const PairConsts& pc = *pcs;
     WarpSm& ws = *wsp;
+    (void)Ek;
     bool exact = false;
     uint4 xe = make_uint4(0u, 0u, 0u, 0u);
     if (lane < cnt) {
         const uint2 e = ws.q2[off + lane];
         const uint32_t meta = e.x, j = e.y;
-        const uint32_t ci = c_begin + (meta & 31u);
+        const int cl = (int)(meta & 31u);
+        const uint32_t ci = c_begin + (uint32_t)cl;
+        const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
         const bool other = (meta >> 11) & 1u;
         const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
         const uint32_t a = other ? j : ci, b = other ? ci : j;  // centre, neighbour
+        const float nxj = NXk[j], nyj = NYk[j];
+        const float2 lo = Plok[j];
+        const float4 ca = ws.cen_a[cl];
+        const float4 cb = ws.cen_b[cl];
+        const float dxa = (ca.x + nxj) + (cb.x - lo.x);
+        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + fmaf(dcy, pc.g.chl, cb.y - lo.y);
+        float ra, inv_r;
+        radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
         const int64_t base = (int64_t)real * rb.n;
         const double xa = rb.X[base + a], ya = rb.Y[base + a];
-        const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
-        const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-        const double om =
-            poly_weight_fast<false>(xa, ya, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
-        const double w = om > 0.0 ? 1.0 / (om * (vhalf ? 0.5 : 1.0)) : 0.0;
-        // undecided crossings, and weights above 8 (beyond the shared accumulators' bound),
-        // go to the FP64 queue
-        if (!(om > 0.0) || w > 8.0) {
-            exact = true;
-            xe = make_uint4(a, b, real, 1u | ((uint32_t)bin << 2));
+        float in = 0.0f, out = 0.0f;
+        if (pc.poly_f32 && ra >= pc.r_acc_min && poly_share_f32(pc, xa, ya, ra, inv_r, in, out)) {
+            // weight 1 / (inside v) - 1: outside / inside, or (1 + outside) / inside when the
+            // temporal weight is 1/2 (correctly rounded division)
+            const float xs = __fdiv_rn(vhalf ? 1.0f + out : out, in);
+            if (!(xs <= 7.0f)) {
+                exact = true;
+            } else {
+                const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
+                if (exc) atomicAdd(&he[bin], exc);
+            }
         } else {
-            const unsigned long long exc = excess_fixed64(w);
-            if (exc) atomicAdd(&he[bin], exc);
+            const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
+            const double r64 = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+            const double in64 =
+                poly_weight_fast<false>(xa, ya, r64, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+            if (in64 > 0.0) {
+                const double w = 1.0 / (in64 * (vhalf ? 0.5 : 1.0));
+                if (w > 8.0) {
+                    exact = true;
+                } else {
+                    const unsigned long long exc = excess_fixed64(w);
+                    if (exc) atomicAdd(&he[bin], exc);
+                }
+            } else {
+                exact = true;
+            }
         }
+        if (exact) xe = make_uint4(a, b, real, 1u | ((uint32_t)bin << 2));
     }
     push_exact<true>(gpc, rb, xq, exact, xe, lane, (1u << lane) - 1u, hc, he);
 }
@@ -686,8 +828,8 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
     __syncwarp();
     while (w.q2n - off >= 32) {
         if (POLY)
-            drain_weights_poly(&pc, gpc, &ws, rb, xq, off, 32, lane, w.he, w.hc, w.real,
-                               w.c_begin);
+            drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32, lane,
+                               w.he, w.hc, w.real, w.c_begin);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
@@ -977,8 +1119,8 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     __syncwarp();
     if (w.q2n > 0) {
         if (POLY)
-            drain_weights_poly(&pc, gpc, &ws, rb, xq, 0, w.q2n, lane, w.he, w.hc, w.real,
-                               w.c_begin);
+            drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0, w.q2n, lane,
+                               w.he, w.hc, w.real, w.c_begin);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);

@@ -223,6 +223,18 @@ def star_polygon(nv: int, r_out: float, r_in: float, cx: float, cy: float, seed:
     return cx + rad * np.cos(th), cy + rad * np.sin(th)
 
 
+def smooth_polygon(nv: int, r_mean: float, cx: float, cy: float, seed: int):
+    """A simple polygon of nv vertices whose radius varies slowly with the angle (a few low
+    harmonics of 5-15% and 1% jitter): a stand-in for an administrative outline without
+    spikes."""
+    rng = np.random.default_rng(seed)
+    ang = np.sort(rng.uniform(0.0, 2.0 * np.pi, nv))
+    ph = rng.uniform(0.0, 2.0 * np.pi, 3)
+    rad = r_mean * (1.0 + 0.15 * np.sin(2.0 * ang + ph[0]) + 0.08 * np.sin(3.0 * ang + ph[1]) +
+                    0.05 * np.sin(5.0 * ang + ph[2]) + 0.01 * rng.uniform(-1.0, 1.0, nv))
+    return cx + rad * np.cos(ang), cy + rad * np.sin(ang)
+
+
 def inside_polygon(px, py, vx, vy):
     """Vectorised even-odd test (input generation only; boundary cases are immaterial)."""
     inside = np.zeros(np.shape(px), bool)
@@ -257,6 +269,25 @@ def config_polygon(seed: int = 0, n: int = 200_000) -> Workload:
                     {"time_unit": "day", "polygon": (vx, vy)})
 
 
+def config_polygon_smooth(seed: int = 0, n: int = 200_000) -> Workload:
+    """As config_polygon, inside an 85-vertex outline without spikes (smooth_polygon, mean
+    radius 3800 m)."""
+    rng = np.random.default_rng(seed)
+    box = (0.0, 10_000.0, 0.0, 10_000.0, 0.0, 730.0)
+    vx, vy = smooth_polygon(85, 3800.0, 5000.0, 5000.0, seed + 2)
+    xs, ys, ts = [], [], []
+    have = 0
+    while have < n:
+        x, y, t = thomas(n, box, 400, 150.0, 10.0, rng)
+        keep = inside_polygon(x, y, vx, vy)
+        xs.append(x[keep]), ys.append(y[keep]), ts.append(t[keep])
+        have += int(keep.sum())
+    x, y, t = (np.concatenate(a)[:n] for a in (xs, ys, ts))
+    return Workload("thomas_smooth85_n200k", x, y, t, box, even_thresholds(1000.0, 20),
+                    even_thresholds(60.0, 20), 99, seed,
+                    {"time_unit": "day", "polygon": (vx, vy)})
+
+
 def histogram_intensity(x, y, t, box, shape, floor: float = 0.05) -> np.ndarray:
     """A relative intensity for the inhomogeneous K: the point counts on `shape` = (nit, niy,
     nix) equal cells of the box plus `floor` times the mean count, so that every cell is
@@ -286,5 +317,6 @@ CONFIGS = {
     "poi_n2M": config_poi,
     "poi_n10M": config_large,
     "thomas_polygon85_n200k": config_polygon,
+    "thomas_smooth85_n200k": config_polygon_smooth,
     "thomas_inhom_n200k": config_inhom,
 }

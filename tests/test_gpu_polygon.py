@@ -118,3 +118,27 @@ def test_polygon_arguments_checked(stk, orc):
         with pytest.raises(stk.StkError) as e:  # cross K takes the rectangle only
             p.run(np.array([30.0]), np.array([5.0]), labels=np.zeros(3, np.uint8), cross=(0, 0))
         assert e.value.code == stk.STK_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_k_and_envelope_in_smooth_outline(stk, orc, prec):
+    """An outline without spikes (about two boundary crossings per circle), where the FP32
+    kernel takes its FP32-guarded polygon weights (poly_share_f32) rather than FP64 ones."""
+    from paper_1912_04753_gb300 import workloads as wl
+
+    vx, vy = wl.smooth_polygon(60, 800.0, 1200.0, 1100.0, 4)
+    box = (0.0, 2400.0, 0.0, 2200.0, 0.0, 365.0)
+    x, y, t = _pattern(orc, box, vx, vy, 3000, 21)
+    s, tt = np.linspace(40.0, 320.0, 8), np.linspace(5.0, 40.0, 6)
+    want = orc.k_function_polygon(x, y, t, box, vx, vy, s, tt)
+    sims, seed = 4, 29
+    env = orc.envelope_of(0, x, y, t, box, s, tt, sims, seed, polygon=(vx, vy))
+    with stk.Pattern(x, y, t, box) as p:
+        p.set_polygon(vx, vy)
+        got = p.run(s, tt, n_sims=sims, seed=seed, prec=prec, want_sims=True)
+        assert p.stats()["internal_errors"] == 0
+    np.testing.assert_array_equal(got["C"], want["C"])
+    assert _rel(got["S"], want["S"]).max() <= TOL[prec]
+    assert _rel(got["K"], want["K"]).max() <= TOL[prec]
+    for k in range(sims):
+        assert _rel(got["K_sims"][k], env["K_all"][k]).max() <= TOL[prec]
