@@ -549,11 +549,11 @@ def run_ours(args):
                              "value": sm["qualifying_pairs"] / (ms_m / 1e3), "unit": UNIT,
                              "qualifying_pairs": sm["qualifying_pairs"]}
 
-    # a polygon study area (85-vertex outline, Thomas process, CSR simulations in it); its
-    # weights near the boundary are all FP64, so the job is kept to 9 simulations
-    polygon = None
-    if args.polygon and rank == 0:
-        wp = _workload("thomas_polygon85_n200k", sims=9)
+    # polygon study areas (85-vertex outlines, Thomas process, CSR simulations in them): a
+    # spiky star, whose circles cross the boundary six times on average and keep FP64 weights,
+    # and a smooth outline, which takes the FP32-guarded ones; 9 simulations each
+    def polygon_job(name):
+        wp = _workload(name, sims=9)
         with stk.Pattern(wp.x, wp.y, wp.t, wp.box) as pp:
             pp.set_polygon(*wp.meta["polygon"])
             stk.stk_set_stream(pp.h, stream)
@@ -566,11 +566,17 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms_p = e0.elapsed_time(e1)
             sp = pp.stats()
-        polygon = {"workload": wp.name, "n": wp.n, "vertices": len(wp.meta["polygon"][0]),
-                   "sims": wp.n_sims, "job_s": ms_p / 1e3,
-                   "sims_per_s": wp.n_sims / (ms_p / 1e3),
-                   "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
-                   "fp64_queue_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
+        return {"workload": wp.name, "n": wp.n, "vertices": len(wp.meta["polygon"][0]),
+                "sims": wp.n_sims, "job_s": ms_p / 1e3,
+                "sims_per_s": wp.n_sims / (ms_p / 1e3),
+                "value": sp["qualifying_pairs"] / (ms_p / 1e3), "unit": UNIT,
+                "pair_kernel_s": sp["ms_pair"] / 1e3,
+                "fp64_queue_share": sp["fp64_recomputed"] / max(1, sp["qualifying_pairs"])}
+
+    polygon = polygon_smooth = None
+    if args.polygon and rank == 0:
+        polygon = polygon_job("thomas_polygon85_n200k")
+        polygon_smooth = polygon_job("thomas_smooth85_n200k")
 
     # the inhomogeneous K (intensity-weighted pairs; FP32-guarded and FP64) on the Thomas
     # pattern with a histogram intensity, observed + 99 intensity-weighted simulations
@@ -688,6 +694,7 @@ def run_ours(args):
         "serve": serve,
         "sim_methods": methods,
         "polygon": polygon,
+        "polygon_smooth": polygon_smooth,
         "inhomogeneous": inhom,
         "directional": directional,
     }
