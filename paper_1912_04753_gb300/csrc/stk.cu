@@ -422,8 +422,9 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
         const int rc = trial_run(c, c.f == planned);
         if (rc) return rc;
     }
-    // the refinement's own time with the default shape is the incumbent of the next steps
-    {
+    // the refinement's own time with the default shape is the incumbent of the next steps;
+    // the tile and the block shape are the FP32 kernel's (the FP64 kernel has neither)
+    if (fp32_path(h, q)) {
         const TuneChoice base = best;
         best_ms = -1.0f;
         int rc = trial_run(base, true);
@@ -433,7 +434,7 @@ int tuned_refinement(stk_handle* h, const stk_request* q, TuneChoice* out) {
             c.tile = tile;
             if ((rc = trial_run(c, false))) return rc;
         }
-        if (fp32_path(h, q) && pair_fp32_shape_tunable(*h->h_pc, h->inten.nix > 0)) {
+        if (pair_fp32_shape_tunable(*h->h_pc, h->inten.nix > 0)) {
             TuneChoice c = best;
             c.bps = 3;
             if ((rc = trial_run(c, false))) return rc;
