@@ -40,8 +40,9 @@ UNIT = "qualifying ordered pairs/s"
 OPS_PER_CANDIDATE = 8
 OPS_PER_QUALIFYING = 12
 # DRAM bytes (read + write) of the pair kernel per realization of the 2M-point mixture, from
-# one ncu capture of the kernel as built (2 realizations per launch there)
-PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 130.2e6}
+# one ncu capture of the kernel as built (a launch of 2 CSR realizations; the clustered observed
+# realization is one of the job's hundred)
+PAIR_DRAM_BYTES_PER_REALIZATION = {"poi_n2M": 123.9e6}
 
 
 def _workload(name, sims=None):
