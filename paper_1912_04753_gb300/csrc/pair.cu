@@ -470,6 +470,7 @@ struct WarpCtx {
     const uint8_t* mk;        // centre mask of the current realization, or null
     uint32_t real;
     uint32_t c_begin;
+    int cy;                   // the unit's cell row (set in polygon study areas only)
     uint32_t onA, onB;        // lanes whose centre counts as a centre / as a neighbour
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
@@ -577,122 +578,229 @@ __device__ __forceinline__ void radius_nr(float r2, float& r, float& inv_r) {
     inv_r = y * fmaf(-0.5f * r2 * y, y, 1.5f);
 }
 
-// Share of the circle of radius r (FP32, inv_r = 1 / r; within 2^-22 r of the reference radius)
-// around the point (cx, cy) (FP64, inside the polygon) that lies inside the polygon, in FP32
-// with an error bound (Section 3's isotropic weight is 1 / inside).  For each edge whose
-// bounding box meets the circle's, the line's signed distance h = (a - c) x u and the
-// centre's projection u0 = (c - a) . u (u the edge's unit direction) are taken in FP64 (six
-// operations); the rest is FP32.  The line meets the circle at u0 -+ t along the edge,
-// t = sqrt((r - h)(r + h)), and the crossings' polar angles are phi_m +- psi, phi_m the angle
-// of the direction from the centre to the line (phi of the edge's normal, + pi when h < 0,
-// exact in FP64) and psi = acos(|h| / r) (the fitted arc polynomial): they depend on h, r and
-// the edge's direction only, not on how far its vertices lie.  Inside arcs run from an
-// entering crossing to the next (counter-clockwise); the larger root enters when the vertices
-// run counter-clockwise.  Each crossing carries a bound on its angle's error: the polynomial's
-// 4e-7 and the rounding of h / r (5 2^-24) amplified by 1 / sin(psi) = r / t.  Returns false
-// (the order goes to FP64) for a line within 2^-19 r of tangency, a crossing within its
-// position error of a vertex, more than 8 crossings, an odd count, crossings that do not
-// alternate or lie closer than their errors, or when the bounds add up to more than 8.5e-7 of
-// the inside share; else inside and outside (their relative errors below that bound).
-constexpr int kPolyCrossF32 = 8;
+// ------------------------------------------------- FP32 polygon weight (pairs of FP32 numbers)
+// Values that need more than FP32 precision are carried as unevaluated sums hi + lo of two FP32
+// numbers (error-free sums and products; every step stays on the FP32 pipe).
 
-__device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, double cx, double cy,
-                                               float r, float inv_r, float& inside,
-                                               float& outside) {
-    const float cxf = (float)cx, cyf = (float)cy;
-    const float m = r * 1e-4f + 1e-6f * (fabsf(cxf) + fabsf(cyf)) + 1e-30f;
-    const float x0 = cxf - r - m, x1 = cxf + r + m, y0 = cyf - r - m, y1 = cyf + r + m;
-    const float band = ldexpf(r, -19);
-    double th[kPolyCrossF32];
-    float key[kPolyCrossF32], er[kPolyCrossF32];
-    bool ent[kPolyCrossF32];
-    int na = 0;
-    const float cmag = fabsf(cxf) + fabsf(cyf);
+// s + e = a + b exactly (s = a + b rounded).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// p + e = a * b exactly (p = a * b rounded).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Arc half-angle psi = acos(h / r) as a pair, from d = r - h (pair, 0 < d <= r) and r (pair):
+// om = d / r and x = 1 - om to about 2^-46, acos(x) = sqrt(om) P(x) with P a degree-9 fit of
+// acos(x) / sqrt(1 - x) on [0, 1] (fit_arc_poly.py, fit error below 1e-9 relative), its
+// constant term and last Horner step and the product with sqrt(om) as pairs.  Measured error
+// below 1e-8 absolute; the weight's bound takes 3e-8 (kArcErrF32).
+constexpr float kArcErrF32 = 3.0e-8f;
+
+__device__ __forceinline__ void arc_half_angle_pair(float dh, float dl, float rh, float rl,
+                                                    float& ph, float& pl) {
+    const float y = __frcp_rn(rh);
+    const float om0 = dh * y;
+    float res = __fmaf_rn(-om0, rh, dh);
+    res = __fsub_rn(__fadd_rn(res, dl), om0 * rl);
+    const float om1 = res * y;
+    const float ys = rsqrtf(om0);
+    float s0 = om0 * ys;
+    s0 = __fmaf_rn(__fmaf_rn(-s0, s0, om0), 0.5f * ys, s0);
+    const float s1 = __fadd_rn(__fmaf_rn(-s0, s0, om0), om1) * (0.5f * ys);
+    const float x = __fsub_rn(__fsub_rn(1.0f, om0), om1);
+    float p = -0.0004011530545540154f;
+    p = __fmaf_rn(p, x, 0.002504516625776887f);
+    p = __fmaf_rn(p, x, -0.007419043220579624f);
+    p = __fmaf_rn(p, x, 0.014548846520483494f);
+    p = __fmaf_rn(p, x, -0.02282850071787834f);
+    p = __fmaf_rn(p, x, 0.03330930322408676f);
+    p = __fmaf_rn(p, x, -0.050739698112010956f);
+    p = __fmaf_rn(p, x, 0.08904469013214111f);
+    p = __fmaf_rn(p, x, -0.21460172533988953f);
+    float m, me, Ph, Pe;
+    two_prod(p, x, m, me);
+    two_sum(1.5707963705062866f, m, Ph, Pe);
+    const float Pl = __fadd_rn(__fadd_rn(Pe, me), -4.4270890953157505e-08f);
+    ph = s0 * Ph;
+    pl = __fadd_rn(__fmaf_rn(s0, Ph, -ph), __fmaf_rn(s0, Pl, s1 * Ph));
+}
+
+// Share of the circle of radius r = rh + rl around the point c (box frame: c - (x0, y0) =
+// (cxh + cxl, cyh + cyl)) that lies inside the polygon, for a centre inside it (Section 3's
+// isotropic weight is 1 / inside).  For each edge whose box meets the circle's: f = a - c
+// (a the edge's start vertex), the line's signed distance h = f x u and d = r - |h| as pairs
+// (u the unit direction); a line with |d| within the band is too close to tangency to call.
+// A crossing line meets the circle at u0 -+ t along the edge (u0 = -(f . u),
+// t = sqrt(d (r + |h|))); those on the edge, away from its vertices by more than their
+// position error, are crossings at polar angle phi_m +- psi (phi_m the normal's direction
+// towards the line, psi = acos(|h| / r)), a pair in [0, 2 pi).  Going round the circle from angle
+// 0 the inside indicator starts at I0 and steps by +1 at an entering crossing, -1 at a leaving
+// one, so the inside measure is 2 pi I0 - sum(delta_c theta_c) in any order of the crossings, and
+// I0 = 1 when the crossing of least angle leaves.  Each angle is within
+// kArcErrF32 + 2 poly_eh / t (the arc's error and the positions' error eh through dpsi = dh / t)
+// of the true one; the result is refused (false: the order goes to FP64) when the least angle
+// lies within its error of 0, the largest within the largest error of 2 pi, or the second least
+// within both errors of the least (the choice of I0 would be in doubt), when entering and
+// leaving crossings do not balance, or when the errors add up to more than 8.5e-7 of the inside
+// share.  No crossing: the whole circle is inside unless it might enclose the polygon
+// (2 r >= the polygon's larger bounding-box side: refused).  inv_r = 1 / rh.
+__device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, float cxl,
+                                               float cyh, float cyl, float rh, float rl,
+                                               float& inside, float& outside) {
+    const float kPiH = 3.1415927410125732f, kPiL = -8.742277657347586e-08f;
+    const float k2PiH = 6.2831854820251465f, k2PiL = -1.7484555314695172e-07f;
+    const float eh = pc.poly_eh;
+    const float m = rh * 1e-5f + 1e-6f * (fabsf(cxh) + fabsf(cyh)) + eh;
+    const float x0 = cxh - rh - m, x1 = cxh + rh + m, y0 = cyh - rh - m, y1 = cyh + rh + m;
+    const float band = 4.0f * eh + rh * 1e-12f;
+    float Sh = 0.0f, Sl = 0.0f;              // sum of delta_c theta_c
+    float a1h = 4.0e1f, a1l = 0.0f, a1e = 0.0f;  // least angle, its error
+    bool a1in = false;                       // ... and whether it enters
+    float a2h = 4.0e1f, a2l = 0.0f;          // second least angle
+    float zh = -1.0f, zl = 0.0f;             // largest angle
+    float esum = 0.0f, emax = 0.0f;
+    int bal = 0, na = 0;
     for (int k = 0; k < pc.nv; ++k) {
-        const float4 eb = pc.pebox[k];
+        const float4* E = pc.pe32 + 4 * k;
+        const float4 eb = E[3];
         if (eb.x > x1 || eb.y < x0 || eb.z > y1 || eb.w < y0) continue;
-        // FP32 pre-test of the line's distance: the vertex, the centre and the direction are
-        // rounded to FP32, so |h32 - h| <= 2^-22 (|a| + |c| + |h32|) (components summed)
-        const float4 e32 = pc.pef32[k];
-        const float h32 = fabsf(fmaf(e32.x - cxf, e32.w, -((e32.y - cyf) * e32.z)));
-        if (h32 > r + band + 2.4e-7f * (fabsf(e32.x) + fabsf(e32.y) + cmag + h32)) continue;
-        const EdgeDir ed = pc.pedir[k];
-        if (!(ed.len > 0.0)) continue;
-        const double fx = pc.pvx[k] - cx, fy = pc.pvy[k] - cy;
-        const double hd = fx * ed.uy - fy * ed.ux;
-        const float h = fabsf((float)hd);
-        if (h >= r + band) continue;   // the line misses the circle
-        if (h > r - band) return false;  // nearly tangent
-        const float t = sqrt_nr((r - h) * (r + h));
-        const float psi = arc_half_angle(h, r, inv_r);
-        const float u0 = (float)(-(fx * ed.ux + fy * ed.uy));
-        const float len = (float)ed.len;
-        const float rt = r / t;
-        const float err = 4.2e-7f + 3.0e-7f * rt;
-        const float uerr = 1.2e-7f * (fabsf(u0) + len + t) + 3.0e-7f * r * rt + 1.5e-7f * t;
-        const double phi = ed.phi + (hd < 0.0 ? 3.141592653589793 : 0.0);
-        const double sgn = hd < 0.0 ? -1.0 : 1.0;
+        const float4 e0 = E[0], e1 = E[1];
+        float fxh, fxe, fyh, fye;
+        two_sum(e0.x, -cxh, fxh, fxe);
+        two_sum(e0.z, -cyh, fyh, fye);
+        const float fxl = __fadd_rn(fxe, __fsub_rn(e0.y, cxl));
+        const float fyl = __fadd_rn(fye, __fsub_rn(e0.w, cyl));
+        // h = fx uy - fy ux
+        float p1, q1, p2, q2, hs, he;
+        two_prod(fxh, e1.z, p1, q1);
+        two_prod(fyh, e1.x, p2, q2);
+        two_sum(p1, -p2, hs, he);
+        const float hl0 = __fadd_rn(__fadd_rn(he, __fsub_rn(q1, q2)),
+                                    __fsub_rn(__fmaf_rn(fxh, e1.w, fxl * e1.z),
+                                              __fmaf_rn(fyh, e1.y, fyl * e1.x)));
+        float hh, hl;
+        two_sum(hs, hl0, hh, hl);
+        const bool neg = hh < 0.0f;
+        if (neg) {
+            hh = -hh;
+            hl = -hl;
+        }
+        float dh, de, dl;
+        two_sum(rh, -hh, dh, de);
+        dl = __fadd_rn(de, __fsub_rn(rl, hl));
+        two_sum(dh, dl, dh, dl);
+        if (dh < -band) continue;   // the line misses the circle
+        if (dh <= band) return false;  // nearly tangent
+        const float t = sqrt_nr(dh * (rh + hh));
+        const float u0 = -__fmaf_rn(fxh, e1.x, fyh * e1.z);
+        const float4 e2 = E[2];
+        const float len = e2.z;
+        const float eang = kArcErrF32 + 2.0f * eh / t;
+        const float uerr = 2.5e-7f * (fabsf(fxh) + fabsf(fyh)) + 1.5e-7f * t + 6.0e-8f * len +
+                           2.0f * eh * (rh / t + 1.0f);
+        bool have_psi = false;
+        float ph = 0.0f, pl = 0.0f, bh = 0.0f, bl = 0.0f;
         for (int q = -1; q <= 1; q += 2) {
             const float u = fmaf((float)q, t, u0);
             if (fabsf(u) <= uerr || fabsf(u - len) <= uerr) return false;  // at a vertex
             if (u < 0.0f || u >= len) continue;
-            if (na == kPolyCrossF32) return false;
-            double a = fma((double)q * sgn, (double)psi, phi);
-            a = a < 0.0 ? a + 6.283185307179586 : (a >= 6.283185307179586 ? a - 6.283185307179586 : a);
-            th[na] = a;
-            key[na] = (float)a;
-            er[na] = err;
-            ent[na] = (q > 0) == (pc.pccw != 0);
+            if (!have_psi) {
+                arc_half_angle_pair(dh, dl, rh, rl, ph, pl);
+                float be;
+                if (neg) {
+                    two_sum(e2.x, kPiH, bh, be);
+                    bl = __fadd_rn(be, __fadd_rn(e2.y, kPiL));
+                } else {
+                    bh = e2.x;
+                    bl = e2.y;
+                }
+                have_psi = true;
+            }
+            // theta = phi_m + q sgn psi, sgn = -1 when h < 0
+            const bool plus = (q > 0) != neg;
+            float th, te;
+            two_sum(bh, plus ? ph : -ph, th, te);
+            float tl = __fadd_rn(te, __fadd_rn(bl, plus ? pl : -pl));
+            two_sum(th, tl, th, tl);
+            // into [0, 2 pi), comparing the whole pair (a hi part equal to 2 pi's may carry
+            // a negative low part)
+            if (th < 0.0f || (th == 0.0f && tl < 0.0f)) {
+                two_sum(th, k2PiH, th, te);
+                tl = __fadd_rn(te, __fadd_rn(tl, k2PiL));
+                two_sum(th, tl, th, tl);
+            } else if (th > k2PiH || (th == k2PiH && tl >= k2PiL)) {
+                two_sum(th, -k2PiH, th, te);
+                tl = __fadd_rn(te, __fsub_rn(tl, k2PiL));
+                two_sum(th, tl, th, tl);
+            }
+            const bool enter = (q > 0) == (pc.pccw != 0);
+            float sh, se;
+            two_sum(Sh, enter ? th : -th, sh, se);
+            Sl = __fadd_rn(Sl, __fadd_rn(se, enter ? tl : -tl));
+            Sh = sh;
+            bal += enter ? 1 : -1;
             ++na;
+            esum += eang;
+            emax = fmaxf(emax, eang);
+            if (th < a1h || (th == a1h && tl < a1l)) {
+                a2h = a1h;
+                a2l = a1l;
+                a1h = th;
+                a1l = tl;
+                a1e = eang;
+                a1in = enter;
+            } else if (th < a2h || (th == a2h && tl < a2l)) {
+                a2h = th;
+                a2l = tl;
+            }
+            if (th > zh || (th == zh && tl > zl)) {
+                zh = th;
+                zl = tl;
+            }
         }
     }
-    if (na == 0) {  // the centre is inside and no crossing: the whole circle is
+    if (na == 0) {  // the centre is inside and no crossing
+        if (!(2.0f * rh * (1.0f + 1e-6f) < pc.poly_span)) return false;
         inside = 1.0f;
         outside = 0.0f;
         return true;
     }
-    if (na & 1) return false;
-    // insertion sort by the angles rounded to FP32 (an order they get wrong leaves a
-    // negative gap below, which refuses the circle)
-    for (int i = 1; i < na; ++i) {
-        const double v = th[i];
-        const float kv = key[i], e = er[i];
-        const bool g = ent[i];
-        int j = i - 1;
-        while (j >= 0 && key[j] > kv) {
-            th[j + 1] = th[j];
-            key[j + 1] = key[j];
-            er[j + 1] = er[j];
-            ent[j + 1] = ent[j];
-            --j;
-        }
-        th[j + 1] = v;
-        key[j + 1] = kv;
-        er[j + 1] = e;
-        ent[j + 1] = g;
-    }
-    double in = 0.0;
-    float bound = 0.0f;
-    for (int k = 0; k < na; ++k) {
-        const int k1 = k + 1 < na ? k + 1 : 0;
-        const double gap = k + 1 < na ? th[k1] - th[k] : th[0] + 6.283185307179586 - th[k];
-        if (!(gap > (double)(er[k] + er[k1]))) return false;  // order within the errors
-        if (ent[k] == ent[k1]) return false;                   // must alternate
-        if (ent[k]) in += gap;
-        bound += er[k];
-    }
-    inside = (float)(in * 0.15915494309189535);
-    outside = (float)((6.283185307179586 - in) * 0.15915494309189535);
-    return bound * 0.15915494309189535f <= 8.5e-7f * inside;
+    if (bal != 0) return false;
+    // I0's choice: the least angle clear of 0, of the second least and (largest) of 2 pi
+    if (!(__fadd_rn(a1h, a1l) > a1e * 1.0001f)) return false;
+    if (!(__fadd_rn(__fsub_rn(a2h, a1h), __fsub_rn(a2l, a1l)) > (a1e + emax) * 1.0001f))
+        return false;
+    if (!(__fadd_rn(__fsub_rn(k2PiH, zh), __fsub_rn(k2PiL, zl)) > emax * 1.0001f)) return false;
+    // inside measure 2 pi I0 - S and outside measure 2 pi (1 - I0) + S, each times 1 / (2 pi)
+    const float kInvH = 0.15915493667125702f, kInvL = 6.4206382432985265e-09f;
+    const bool i0 = !a1in;
+    float ih, ie, oh, oe;
+    two_sum(i0 ? k2PiH : 0.0f, -Sh, ih, ie);
+    const float il = __fadd_rn(ie, __fsub_rn(i0 ? k2PiL : 0.0f, Sl));
+    two_sum(i0 ? 0.0f : k2PiH, Sh, oh, oe);
+    const float ol = __fadd_rn(oe, __fadd_rn(i0 ? 0.0f : k2PiL, Sl));
+    float vh, ve;
+    two_prod(ih, kInvH, vh, ve);
+    inside = __fadd_rn(vh, __fadd_rn(ve, __fmaf_rn(ih, kInvL, il * kInvH)));
+    two_prod(oh, kInvH, vh, ve);
+    outside = __fadd_rn(vh, __fadd_rn(ve, __fmaf_rn(oh, kInvL, ol * kInvH)));
+    return inside > 0.0f && esum * kInvH <= 8.5e-7f * inside;
 }
 
-// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders, the
-// inside share in FP32 with its error bound (poly_share_f32) from the accurate FP32 distance
-// of the pair (as in the rectangle's drain_weights) when the job's outline allows it
-// (pc.poly_f32), else from the crossings' directions with FP64 crossing points
-// (poly_weight_fast); what neither decides, and weights above 8 (beyond the shared
-// accumulators' bound), go to the FP64 queue.  Out of line like the
-// rectangle's version, so that the rectangle path does not carry its registers.
+// Phase C in a polygon study area: the weight of each of `cnt` (<= 32) queued orders.  The
+// inside share comes from poly_share_f32 when the job allows it (pc.poly_f32): the pair's
+// radius and the centre's box-frame position as pairs of FP32 numbers (the records' hi and
+// low parts; y from the centre's cell row cy_u = the unit's row, or the neighbour's), else, or
+// when it refuses, from the crossings' directions with FP64 crossing points
+// (poly_weight_fast).  What neither decides, and weights above 8 (beyond the shared
+// accumulators' bound), go to the FP64 queue.  Out of line like the rectangle's version, so
+// that the rectangle path does not carry its registers.
 __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const PairConsts* gpc,
                                                 WarpSm* wsp, const float4* __restrict__ Ek,
                                                 const float* __restrict__ NXk,
@@ -700,7 +808,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
                                                 const float2* __restrict__ Plok, RealBatch rb,
                                                 ExactQueue xq, int off, int cnt, int lane,
                                                 unsigned long long* he, uint32_t* hc,
-                                                uint32_t real, uint32_t c_begin) {
+                                                uint32_t real, uint32_t c_begin, int cy_u) {
     const PairConsts& pc = *pcs;
     WarpSm& ws = *wsp;
     (void)Ek;
@@ -711,7 +819,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
         const uint32_t meta = e.x, j = e.y;
         const int cl = (int)(meta & 31u);
         const uint32_t ci = c_begin + (uint32_t)cl;
-        const float dcy = (float)((int)((meta >> 8) & 7u) - pc.g.fs);
+        const int dcy = (int)((meta >> 8) & 7u) - pc.g.fs;  // centre i's row - j's row
         const bool other = (meta >> 11) & 1u;
         const bool vhalf = (meta >> 12) & 1u;
         const int bin = (int)(meta >> 13);
@@ -720,24 +828,53 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
         const float2 lo = Plok[j];
         const float4 ca = ws.cen_a[cl];
         const float4 cb = ws.cen_b[cl];
-        const float dxa = (ca.x + nxj) + (cb.x - lo.x);
-        const float dya = (fmaf(dcy, pc.g.chq, ca.y) + nyj) + fmaf(dcy, pc.g.chl, cb.y - lo.y);
-        float ra, inv_r;
-        radius_nr(fmaf(dxa, dxa, dya * dya), ra, inv_r);
-        const int64_t base = (int64_t)real * rb.n;
-        const double xa = rb.X[base + a], ya = rb.Y[base + a];
         float in = 0.0f, out = 0.0f;
-        if (pc.poly_f32 && ra >= pc.r_acc_min && poly_share_f32(pc, xa, ya, ra, inv_r, in, out)) {
-            // weight 1 / (inside v) - 1: outside / inside, or (1 + outside) / inside when the
-            // temporal weight is 1/2 (correctly rounded division)
-            const float xs = __fdiv_rn(vhalf ? 1.0f + out : out, in);
-            if (!(xs <= 7.0f)) {
-                exact = true;
-            } else {
-                const unsigned long long exc = xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
-                if (exc) atomicAdd(&he[bin], exc);
+        bool done = false;
+        if (pc.poly_f32) {
+            // offset i - j: hi parts exact (x in the box frame, y with i moved into j's row),
+            // low parts rounded once; r^2 and r as pairs
+            const float dxh = ca.x + nxj, dxl = cb.x - lo.x;
+            const float dyh = fmaf((float)dcy, pc.g.chq, ca.y) + nyj;
+            const float dyl = fmaf((float)dcy, pc.g.chl, cb.y - lo.y);
+            float p1, e1, p2, e2, s, es;
+            two_prod(dxh, dxh, p1, e1);
+            two_prod(dyh, dyh, p2, e2);
+            two_sum(p1, p2, s, es);
+            const float r2l = __fadd_rn(__fadd_rn(es, __fadd_rn(e1, e2)),
+                                        __fmaf_rn(2.0f * dxh, dxl,
+                                                  __fmaf_rn(2.0f * dyh, dyl,
+                                                            dxl * dxl + dyl * dyl)));
+            const float ys = rsqrtf(s);
+            float rh = s * ys;
+            rh = __fmaf_rn(__fmaf_rn(-rh, rh, s), 0.5f * ys, rh);
+            const float rl = __fadd_rn(__fmaf_rn(-rh, rh, s), r2l) * (0.5f * ys);
+            // the centre's box-frame position: x hi + low; y = its row's origin
+            // row (chq + chl) plus its offset in the cell
+            const int row = other ? cy_u - dcy : cy_u;
+            const float cxh = other ? -nxj : ca.x, cxl = other ? lo.x : cb.x;
+            const float cyr = other ? -nyj : ca.y, cyrl = other ? lo.y : cb.y;
+            float ro, roe, cyh, cye;
+            two_prod((float)row, pc.g.chq, ro, roe);
+            two_sum(ro, cyr, cyh, cye);
+            const float cyl = __fadd_rn(__fadd_rn(cye, roe),
+                                        __fmaf_rn((float)row, pc.g.chl, cyrl));
+            if (rh > 0.0f && poly_share_f32(pc, cxh, cxl, cyh, cyl, rh, rl, in, out)) {
+                done = true;
+                // weight 1 / (inside v) - 1: outside / inside, or (1 + outside) / inside when
+                // the temporal weight is 1/2 (correctly rounded division)
+                const float xs = __fdiv_rn(vhalf ? 1.0f + out : out, in);
+                if (!(xs <= 7.0f)) {
+                    exact = true;
+                } else {
+                    const unsigned long long exc =
+                        xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
+                    if (exc) atomicAdd(&he[bin], exc);
+                }
             }
-        } else {
+        }
+        if (!done) {
+            const int64_t base = (int64_t)real * rb.n;
+            const double xa = rb.X[base + a], ya = rb.Y[base + a];
             const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
             const double r64 = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
             const double in64 =
@@ -829,7 +966,7 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
     while (w.q2n - off >= 32) {
         if (POLY)
             drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32, lane,
-                               w.he, w.hc, w.real, w.c_begin);
+                               w.he, w.hc, w.real, w.c_begin, w.cy);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
@@ -1120,7 +1257,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     if (w.q2n > 0) {
         if (POLY)
             drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0, w.q2n, lane,
-                               w.he, w.hc, w.real, w.c_begin);
+                               w.he, w.hc, w.real, w.c_begin, w.cy);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);

@@ -76,6 +76,7 @@
             const WorkItem wi = units[ui];
             w.c_begin = wi.c_begin;
             const int cy = (int)(wi.row % (uint32_t)ny), ct = (int)(wi.row / (uint32_t)ny);
+            if (POLY) w.cy = cy;
             // centres: one per lane
             const bool valid = lane < (int)wi.c_count;
             const uint32_t myi = wi.c_begin + (valid ? lane : 0);

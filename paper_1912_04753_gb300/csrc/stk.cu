@@ -120,12 +120,10 @@ struct stk_handle {
     int configured_nbins = -1;
     size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
     // polygon study area (nv = 0: the box), vertices in device memory, and the area A of Eq. 2
-    DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4), [nv] EdgeDir, [nv] float4
+    DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4), [4 nv] float4 (pe32)
     int nv = 0;
     int poly_ccw = 1;
-    std::vector<double> poly_hx, poly_hy;  // host copy of the vertices
-    double poly_f32_smax = -1.0;           // s_max of the cached choice below
-    int poly_f32 = 0;
+    double poly_span = 0.0;  // larger side of the polygon's bounding box
     double area = 0.0;
     // inhomogeneous K: the relative intensity (device tables hcell and cum, [2][cells]), h of
     // the observed points in input order, and the per-wave h arrays (unsorted, sorted) and
@@ -270,54 +268,6 @@ constexpr int kNotFusable = -1000;  // run_job with a FuseCtx: the job cannot be
 
 int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan& plan,
             int* R_out, int f_force = 0, FuseCtx* fuse = nullptr);
-
-// Mean number of boundary crossings of circles of radius r centred on a 12 x 12 lattice of
-// points inside the polygon (those whose circle meets the boundary), in FP64 on the host.  The
-// FP32-guarded polygon weight bounds its error per crossing, so circles with many crossings
-// (spiky outlines) mostly end in its FP64 fallback and cost more than the FP64 weight alone:
-// above five crossings on average the FP32 kernel takes FP64 weights for the job.
-double poly_mean_crossings(const std::vector<double>& vx, const std::vector<double>& vy,
-                           double r) {
-    const int nv = (int)vx.size();
-    if (nv < 3 || !(r > 0.0)) return 0.0;
-    const double x0 = *std::min_element(vx.begin(), vx.end());
-    const double x1 = *std::max_element(vx.begin(), vx.end());
-    const double y0 = *std::min_element(vy.begin(), vy.end());
-    const double y1 = *std::max_element(vy.begin(), vy.end());
-    double total = 0.0;
-    int circles = 0;
-    for (int i = 0; i < 12; ++i) {
-        for (int j = 0; j < 12; ++j) {
-            const double cx = x0 + (i + 0.5) / 12.0 * (x1 - x0);
-            const double cy = y0 + (j + 0.5) / 12.0 * (y1 - y0);
-            bool inside = false;  // even-odd test
-            for (int k = 0; k < nv; ++k) {
-                const int k1 = (k + 1) % nv;
-                if ((vy[k] > cy) != (vy[k1] > cy) &&
-                    cx < vx[k] + (cy - vy[k]) * (vx[k1] - vx[k]) / (vy[k1] - vy[k]))
-                    inside = !inside;
-            }
-            if (!inside) continue;
-            int n = 0;
-            for (int k = 0; k < nv; ++k) {
-                const int k1 = (k + 1) % nv;
-                const double ax = vx[k] - cx, ay = vy[k] - cy;
-                const double dx = vx[k1] - vx[k], dy = vy[k1] - vy[k];
-                const double A = dx * dx + dy * dy, hb = ax * dx + ay * dy;
-                const double disc = hb * hb - A * (ax * ax + ay * ay - r * r);
-                if (!(A > 0.0) || !(disc > 0.0)) continue;
-                const double sq = sqrt(disc);
-                n += ((-hb - sq) / A >= 0.0 && (-hb - sq) / A < 1.0) ? 1 : 0;
-                n += ((-hb + sq) / A >= 0.0 && (-hb + sq) / A < 1.0) ? 1 : 0;
-            }
-            if (n > 0) {
-                total += n;
-                ++circles;
-            }
-        }
-    }
-    return circles > 0 ? total / circles : 0.0;
-}
 
 // Launch-shape tuner: the first batched job of a problem shape (n, box, largest thresholds,
 // precision, edge mode, simulation method, sectors) times the pair kernel on a few CSR
@@ -651,13 +601,20 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         h->h_pc->pvx = poly.vx;
         h->h_pc->pvy = poly.vy;
         h->h_pc->pebox = reinterpret_cast<const float4*>(as<double>(h->poly) + 2 * h->nv);
-        h->h_pc->pedir = reinterpret_cast<const EdgeDir*>(as<double>(h->poly) + 4 * h->nv);
-        h->h_pc->pef32 = reinterpret_cast<const float4*>(as<double>(h->poly) + 8 * h->nv);
-        if (h->poly_f32_smax != q->s[cs - 1]) {
-            h->poly_f32 = poly_mean_crossings(h->poly_hx, h->poly_hy, 0.75 * q->s[cs - 1]) <= 5.0;
-            h->poly_f32_smax = q->s[cs - 1];
-        }
-        h->h_pc->poly_f32 = h->poly_f32;
+        h->h_pc->pe32 = reinterpret_cast<const float4*>(as<double>(h->poly) + 4 * h->nv);
+        h->h_pc->poly_f32 = 1;
+        // bound on the error of the FP32 pair positions the polygon weight works with (box
+        // frame): the records' hi + low parts (acc_x, acc_y, as for the pair offsets; they
+        // bound one point's position and the vertices' FP64 box-frame values too), a row
+        // origin row (chq + chl) (chl rounded: up to ny q_y 2^-24) and the pair arithmetic on
+        // box-frame lengths (2^-44 of the box's extent each step); doubled
+        const double acc_x = ldexp((double)g.qX, -24) + ldexp(fabs(g.x0) + fabs(g.x1), -50);
+        const double acc_y = ldexp((double)g.qy, -22) + ldexp(fabs(g.y0) + fabs(g.y1), -50);
+        const double ext = (g.x1 - g.x0) + (g.y1 - g.y0);
+        const double eh = 2.0 * (2.0 * (acc_x + acc_y) + ldexp((double)g.ny * g.qy, -23) +
+                                 ldexp(ext, -43));
+        h->h_pc->poly_eh = (float)(eh * 1.001);
+        h->h_pc->poly_span = (float)(h->poly_span * (1.0 - 1e-6));
         // the deep-unit shortcut is derived for the rectangle: none in a polygon
         for (int a = 0; a < 2; ++a) {
             h->h_pc->deep_x[a] = 1 - a;
@@ -1802,28 +1759,46 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
             ebox[4 * (size_t)k + 2 * c + 1] = u;
         }
     }
-    // edge directions and lengths in FP64 for the FP32-guarded weight (poly_share_f32), and
-    // the start vertices and directions rounded to FP32 for its pre-test
-    std::vector<double> edir(4 * (size_t)nv, 0.0);
-    std::vector<float> ef32(4 * (size_t)nv, 0.0f);
+    // the FP32 polygon weight's edge table (poly_share_f32): per edge in the box frame the
+    // start vertex, the unit direction and the normal's polar angle as pairs hi + lo of FP32
+    // numbers (from FP64), the length, and the edge's box rounded outwards
+    std::vector<float> pe32(16 * (size_t)nv, 0.0f);
+    auto split = [](double v, float* o) {
+        o[0] = (float)v;
+        o[1] = (float)(v - (double)o[0]);
+    };
+    const double two_pi = 6.283185307179586;
     for (int k = 0; k < nv; ++k) {
         const int k1 = (k + 1) % nv;
+        float* E = &pe32[16 * (size_t)k];
+        const double ax = vx[k] - h->box[0], ay = vy[k] - h->box[2];
+        const double bx = vx[k1] - h->box[0], by = vy[k1] - h->box[2];
+        split(ax, E);
+        split(ay, E + 2);
         const double dx = vx[k1] - vx[k], dy = vy[k1] - vy[k];
         const double len = sqrt(dx * dx + dy * dy);
         if (len > 0.0) {
-            edir[4 * (size_t)k] = dx / len;
-            edir[4 * (size_t)k + 1] = dy / len;
-            edir[4 * (size_t)k + 2] = len;
-            edir[4 * (size_t)k + 3] = atan2(-dx / len, dy / len);
+            const double ux = dx / len, uy = dy / len;
+            split(ux, E + 4);
+            split(uy, E + 6);
+            double phi = atan2(-ux, uy);
+            if (phi < 0.0) phi += two_pi;
+            split(phi, E + 8);
+            E[10] = (float)len;
         }
-        ef32[4 * (size_t)k] = (float)vx[k];
-        ef32[4 * (size_t)k + 1] = (float)vy[k];
-        ef32[4 * (size_t)k + 2] = (float)edir[4 * (size_t)k];
-        ef32[4 * (size_t)k + 3] = (float)edir[4 * (size_t)k + 1];
+        const double lo[2] = {fmin(ax, bx), fmin(ay, by)};
+        const double hi[2] = {fmax(ax, bx), fmax(ay, by)};
+        for (int c = 0; c < 2; ++c) {
+            float l = (float)lo[c], u = (float)hi[c];
+            if ((double)l > lo[c]) l = nextafterf(l, -INFINITY);
+            if ((double)u < hi[c]) u = nextafterf(u, INFINITY);
+            E[12 + 2 * c] = l;
+            E[13 + 2 * c] = u;
+        }
     }
     int rc;
     DevBuf pv;
-    if ((rc = ensure(pv, 80 * (size_t)nv, "polygon"))) return rc;
+    if ((rc = ensure(pv, 96 * (size_t)nv, "polygon"))) return rc;
     cudaStream_t st = h->stream;
     int bad = 0;
     DevBuf flag;
@@ -1842,13 +1817,10 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
         e = cudaMemcpyAsync(as<double>(pv) + 2 * nv, ebox.data(), 16 * (size_t)nv,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(as<double>(pv) + 4 * nv, edir.data(), 32 * (size_t)nv,
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(as<double>(pv) + 8 * nv, ef32.data(), 16 * (size_t)nv,
+        e = cudaMemcpyAsync(as<double>(pv) + 4 * nv, pe32.data(), 64 * (size_t)nv,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 4, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ebox, edir, ef32 are read
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ebox and pe32 are read
     if (e == cudaSuccess) e = launch_poly_validate(h->d_x, h->d_y, h->n, poly, as<int>(flag), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag.p, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1864,9 +1836,8 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     free_buf(h->poly);
     h->poly = pv;
     h->nv = nv;
-    h->poly_hx.assign(vx, vx + nv);
-    h->poly_hy.assign(vy, vy + nv);
-    h->poly_f32_smax = -1.0;
+    h->poly_span = std::max(*std::max_element(vx, vx + nv) - *std::min_element(vx, vx + nv),
+                            *std::max_element(vy, vy + nv) - *std::min_element(vy, vy + nv));
     h->poly_ccw = area2 > 0.0 ? 1 : 0;
     h->area = area;
     return STK_OK;

@@ -50,13 +50,6 @@ struct Grid {
     float qX;
 };
 
-// A polygon edge a -> b for the FP32-guarded weight, in FP64: the unit direction
-// u = (b - a) / |b - a|, the length |b - a| and the polar angle of the normal (u_y, -u_x)
-// (all zero for an edge of length 0).
-struct __align__(16) EdgeDir {
-    double ux, uy, len, phi;
-};
-
 // Everything the pair kernels need for one job, built on the host (see guard derivation in
 // pair_setup.cpp).  The FP32 kernel copies the part before `s2` into shared memory.
 struct PairConsts {
@@ -91,11 +84,16 @@ struct PairConsts {
     int nv;
     int pccw;                 // 1: vertices run counter-clockwise
     int poly_f32;             // 1: FP32-guarded weights in the FP32 kernel (else FP64 ones)
+    float poly_eh;            // bound on the FP32 pair positions' error (box frame, length)
+    float poly_span;          // larger side of the polygon's bounding box, rounded down
     const double* pvx;
     const double* pvy;
     const float4* pebox;      // per-edge bounding boxes, FP32 rounded outwards
-    const struct EdgeDir* pedir;  // per edge: unit direction and length (FP64)
-    const float4* pef32;          // per edge: start vertex and unit direction rounded to FP32
+    // per edge, 4 float4 in the box frame (coordinates minus (x0, y0)), each value a pair
+    // hi + lo of FP32 numbers: (start vertex x, y), (unit direction x, y), (polar angle in
+    // [0, 2 pi) of the normal (u_y, -u_x), length rounded to FP32, 0), and the edge's bounding
+    // box (x_min, x_max, y_min, y_max) rounded outwards
+    const float4* pe32;
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;

@@ -36,6 +36,26 @@ def test_kernel_coefficients_are_the_fit():
     assert np.array_equal(got, c)
 
 
+def test_pair_coefficients_are_the_fit():
+    """arc_half_angle_pair (the polygon weight): c9 .. c1 in its Horner steps and c0 as a pair
+    hi + lo are the degree-9 fit's."""
+    sys.path.insert(0, CSRC)
+    import fit_arc_poly
+
+    src = open(os.path.join(CSRC, "pair.cu")).read()
+    body = src[src.index("void arc_half_angle_pair("):]
+    body = body[:body.index("ph = s0 * Ph;")]
+    horner = [float(v) for v in re.findall(r"p = [^;]*?(-?\d+\.\d+(?:e-?\d+)?)f\)?;", body)]
+    c0 = [float(v) for v in
+          re.findall(r"two_sum\((-?\d+\.\d+(?:e-?\d+)?)f, m", body)]
+    c0l = [float(v) for v in re.findall(r"Pe, me\), (-?\d+\.\d+(?:e-?\d+)?)f\)", body)]
+    c = fit_arc_poly.fit(fit_arc_poly.PAIR_DEGREE)
+    want = c.astype(f32)
+    assert np.array_equal(np.array(horner[::-1], f32), want[1:])
+    hi = f32(c[0])
+    assert c0 == [float(hi)] and c0l == [float(f32(c[0] - float(hi)))]
+
+
 def _sqrt_nr(v):
     y = (1.0 / np.sqrt(v.astype(np.float64) + 1e-30)).astype(f32)
     s = (v * y).astype(f32)
