@@ -618,6 +618,44 @@ cudaError_t launch_poly_validate(const double* x, const double* y, int64_t n, Po
     return cudaGetLastError();
 }
 
+// One thread per bucket: the edges whose closest point lies within `reach` of the bucket's
+// centre, in edge order (FP64).  A circle of radius r around a point of the bucket meets only
+// edges within r + half the bucket's diagonal of that centre, so with reach above the largest
+// pair radius plus half the diagonal the list holds every edge the bucket's circles can cross.
+__global__ void poly_bucket_kernel(Polygon poly, double x0, double y0, double ox, double oy,
+                                   double bs, int nx, int ny, double reach,
+                                   uint8_t* __restrict__ list) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nx * ny) return;
+    const double cx = x0 + ox + ((b % nx) + 0.5) * bs, cy = y0 + oy + ((b / nx) + 0.5) * bs;
+    uint8_t* L = list + (size_t)b * kPolyBucketBytes;
+    int cnt = 0;
+    for (int k = 0; k < poly.nv; ++k) {
+        const int k1 = k + 1 < poly.nv ? k + 1 : 0;
+        const double ax = poly.vx[k] - cx, ay = poly.vy[k] - cy;
+        const double dx = poly.vx[k1] - poly.vx[k], dy = poly.vy[k1] - poly.vy[k];
+        const double len2 = dx * dx + dy * dy;
+        const double s = len2 > 0.0 ? fmin(1.0, fmax(0.0, -(ax * dx + ay * dy) / len2)) : 0.0;
+        const double ex = ax + s * dx, ey = ay + s * dy;
+        if (ex * ex + ey * ey <= reach * reach) {
+            if (cnt == kPolyBucketCap) {
+                cnt = 255;
+                break;
+            }
+            L[1 + cnt++] = (uint8_t)k;
+        }
+    }
+    L[0] = (uint8_t)cnt;
+}
+
+cudaError_t launch_poly_buckets(Polygon poly, double x0, double y0, double ox, double oy,
+                                double bs, int nx, int ny, double reach, uint8_t* list,
+                                cudaStream_t st) {
+    poly_bucket_kernel<<<(nx * ny + 127) / 128, 128, 0, st>>>(poly, x0, y0, ox, oy, bs, nx, ny,
+                                                              reach, list);
+    return cudaGetLastError();
+}
+
 int feistel_bits(int64_t n) {
     int b = 2;
     while (((int64_t)1 << b) < n) b += 2;

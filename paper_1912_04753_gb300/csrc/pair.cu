@@ -644,7 +644,9 @@ __device__ __forceinline__ void arc_half_angle_pair(float dh, float dl, float rh
 // one, so the inside measure is 2 pi I0 - sum(delta_c theta_c) in any order of the crossings, and
 // I0 = 1 when the crossing of least angle leaves.  Each angle is within
 // kArcErrF32 + 2 poly_eh / t (the arc's error and the positions' error eh through dpsi = dh / t)
-// of the true one; the result is refused (false: the order goes to FP64) when the least angle
+// of the true one (edges that cannot meet the circle are skipped: those outside its centre's
+// bucket list, PairConsts::pb_list, and those whose box misses the circle's); the result is
+// refused (false: the order goes to FP64) when the least angle
 // lies within its error of 0, the largest within the largest error of 2 pi, or the second least
 // within both errors of the least (the choice of I0 would be in doubt), when entering and
 // leaving crossings do not balance, or when the errors add up to more than 8.5e-7 of the inside
@@ -666,7 +668,16 @@ __device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, 
     float zh = -1.0f, zl = 0.0f;             // largest angle
     float esum = 0.0f, emax = 0.0f;
     int bal = 0, na = 0;
-    for (int k = 0; k < pc.nv; ++k) {
+    // the edges the circle can meet: its centre's bucket list (every edge when the list
+    // overflowed or the radius is beyond the lists' reach)
+    const int bi = min(max((int)((cxh - pc.pb_ox) * pc.pb_inv), 0), pc.pb_nx - 1);
+    const int bj = min(max((int)((cyh - pc.pb_oy) * pc.pb_inv), 0), pc.pb_ny - 1);
+    const uint8_t* L = pc.pb_list + kPolyBucketBytes * (bj * pc.pb_nx + bi);
+    const int lc = L[0];
+    const bool all = lc > kPolyBucketCap || !(rh <= pc.pb_rmax);
+    const int ne = all ? pc.nv : lc;
+    for (int i = 0; i < ne; ++i) {
+        const int k = all ? i : (int)L[1 + i];
         const float4* E = pc.pe32 + 4 * k;
         const float4 eb = E[3];
         if (eb.x > x1 || eb.y < x0 || eb.z > y1 || eb.w < y0) continue;

@@ -120,10 +120,12 @@ struct stk_handle {
     int configured_nbins = -1;
     size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
     // polygon study area (nv = 0: the box), vertices in device memory, and the area A of Eq. 2
-    DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4), [4 nv] float4 (pe32)
+    DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4), [4 nv] float4 (pe32),
+                  // the bucket lists (kPolyBucketsMax^2 x kPolyBucketBytes)
     int nv = 0;
     int poly_ccw = 1;
     double poly_span = 0.0;  // larger side of the polygon's bounding box
+    double poly_bb[4] = {0.0, 0.0, 0.0, 0.0};  // its bounding box in the box frame
     double area = 0.0;
     // inhomogeneous K: the relative intensity (device tables hcell and cum, [2][cells]), h of
     // the observed points in input order, and the per-wave h arrays (unsorted, sorted) and
@@ -592,6 +594,8 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         h->h_pc->sec_gd = (float)(1.0e-6 * qm + 4.0e-16 * big + 1e-30);
     }
     Polygon poly;
+    double pb_bs = 0.0, pb_reach = 0.0;
+    int pb_nx = 0, pb_ny = 0;
     if (h->nv > 0) {
         poly.vx = as<double>(h->poly);
         poly.vy = as<double>(h->poly) + h->nv;
@@ -615,6 +619,23 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
                                  ldexp(ext, -43));
         h->h_pc->poly_eh = (float)(eh * 1.001);
         h->h_pc->poly_span = (float)(h->poly_span * (1.0 - 1e-6));
+        // bucket grid over the polygon's bounding box: side at least half the largest pair
+        // radius, at most 64 buckets a side; a bucket lists the edges within the largest radius
+        // plus half its diagonal of its centre, with a margin for the FP32 bucket index
+        const double r_max = sqrt((double)h->h_pc->s2_cut) * (1.0 + 1e-6);
+        const double bw = h->poly_bb[1] - h->poly_bb[0], bh = h->poly_bb[3] - h->poly_bb[2];
+        pb_bs = std::max(0.5 * r_max, std::max(bw, bh) / (kPolyBucketsMax - 0.5));
+        pb_nx = std::max(1, std::min(kPolyBucketsMax, (int)ceil(bw / pb_bs)));
+        pb_ny = std::max(1, std::min(kPolyBucketsMax, (int)ceil(bh / pb_bs)));
+        pb_reach = r_max + 0.5 * sqrt(2.0) * pb_bs * 1.001 +
+                   1e-5 * (fabs(h->poly_bb[0]) + fabs(h->poly_bb[2]) + bw + bh);
+        h->h_pc->pb_ox = (float)h->poly_bb[0];
+        h->h_pc->pb_oy = (float)h->poly_bb[2];
+        h->h_pc->pb_inv = (float)(1.0 / pb_bs);
+        h->h_pc->pb_rmax = (float)(r_max * (1.0 - 1e-6));
+        h->h_pc->pb_nx = pb_nx;
+        h->h_pc->pb_ny = pb_ny;
+        h->h_pc->pb_list = as<uint8_t>(h->poly) + 96 * (size_t)h->nv;
         // the deep-unit shortcut is derived for the rectangle: none in a polygon
         for (int a = 0; a < 2; ++a) {
             h->h_pc->deep_x[a] = 1 - a;
@@ -722,6 +743,11 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     }
     CK(cudaMemcpyAsync(h->pc.p, h->h_pc, sizeof(PairConsts), cudaMemcpyHostToDevice, st),
        "constants upload");
+    if (h->nv > 0)
+        CK(launch_poly_buckets(poly, h->box[0], h->box[2], h->poly_bb[0], h->poly_bb[2], pb_bs,
+                               pb_nx, pb_ny, pb_reach, as<uint8_t>(h->poly) + 96 * (size_t)h->nv,
+                               st),
+           "polygon buckets");
     for (int a = 0; a < 2 * STK_MAX_THRESHOLDS; ++a) h->h_thr[a] = 0.0;
     for (int a = 0; a < cs; ++a) h->h_thr[a] = q->s[a];
     for (int b = 0; b < ct; ++b) h->h_thr[STK_MAX_THRESHOLDS + b] = q->tt[b];
@@ -762,7 +788,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         return kNotFusable;  // fused jobs: plain FP32 rectangle kernels, one wave
     float ms_pair = 0.0f;
     int waves = 0;
-    int64_t launches = 0;
+    int64_t launches = h->nv > 0 ? 1 : 0;  // the polygon's bucket lists
     // resident observed index: reused when the grid, the record constants and the study area
     // are those of the cached copy (no role flags, no intensity: their per-point data differ)
     const int64_t nF = filter_stride(n);
@@ -1798,7 +1824,10 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     }
     int rc;
     DevBuf pv;
-    if ((rc = ensure(pv, 96 * (size_t)nv, "polygon"))) return rc;
+    if ((rc = ensure(pv, 96 * (size_t)nv + (size_t)kPolyBucketsMax * kPolyBucketsMax *
+                                              kPolyBucketBytes,
+                     "polygon")))
+        return rc;
     cudaStream_t st = h->stream;
     int bad = 0;
     DevBuf flag;
@@ -1836,8 +1865,11 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     free_buf(h->poly);
     h->poly = pv;
     h->nv = nv;
-    h->poly_span = std::max(*std::max_element(vx, vx + nv) - *std::min_element(vx, vx + nv),
-                            *std::max_element(vy, vy + nv) - *std::min_element(vy, vy + nv));
+    h->poly_bb[0] = *std::min_element(vx, vx + nv) - h->box[0];
+    h->poly_bb[1] = *std::max_element(vx, vx + nv) - h->box[0];
+    h->poly_bb[2] = *std::min_element(vy, vy + nv) - h->box[2];
+    h->poly_bb[3] = *std::max_element(vy, vy + nv) - h->box[2];
+    h->poly_span = std::max(h->poly_bb[1] - h->poly_bb[0], h->poly_bb[3] - h->poly_bb[2]);
     h->poly_ccw = area2 > 0.0 ? 1 : 0;
     h->area = area;
     return STK_OK;

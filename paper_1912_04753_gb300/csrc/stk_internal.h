@@ -27,6 +27,11 @@ namespace stk {
 
 constexpr int kMaxThr = 64;   // thresholds per axis
 constexpr int kMaxPolyVertices = 128;  // vertices of a polygon study area
+// bucket grid over a polygon's bounding box for the FP32 polygon weight: at most 64 x 64
+// buckets, each a count (255: too many, scan every edge) and up to 47 edge indices
+constexpr int kPolyBucketsMax = 64;
+constexpr int kPolyBucketCap = 47;
+constexpr int kPolyBucketBytes = 48;
 constexpr int kMaxSectors = 64;        // direction sectors of the directional K
 constexpr int kTab = 1024;    // bin-table entries per axis
 constexpr int kBlock = 256;   // threads per pair-kernel block
@@ -94,6 +99,12 @@ struct PairConsts {
     // [0, 2 pi) of the normal (u_y, -u_x), length rounded to FP32, 0), and the edge's bounding
     // box (x_min, x_max, y_min, y_max) rounded outwards
     const float4* pe32;
+    // bucket grid (box frame): bucket (i, j) = [pb_ox + i / pb_inv, ...) x [pb_oy + j / pb_inv,
+    // ...), i < pb_nx, j < pb_ny; its edge list at pb_list + kPolyBucketBytes (j pb_nx + i)
+    float pb_ox, pb_oy, pb_inv;
+    float pb_rmax;            // the lists hold every edge circles up to this radius can meet
+    int pb_nx, pb_ny;
+    const uint8_t* pb_list;
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
@@ -269,6 +280,12 @@ cudaError_t launch_gen_csr(int64_t n, int m, const uint64_t* seeds, const uint32
                            const Grid& g, double* x, double* y, double* t, uint32_t* key,
                            uint32_t* rank, uint32_t* cell_count, cudaStream_t st,
                            Polygon poly = Polygon(), unsigned long long* err = nullptr);
+// bucket lists of the FP32 polygon weight: in a grid of nx x ny buckets of side bs at (ox, oy)
+// (box frame, the box's corner at (x0, y0)), bucket b lists the edges within `reach` of its
+// centre (list[b kPolyBucketBytes] = count or 255, then the indices)
+cudaError_t launch_poly_buckets(Polygon poly, double x0, double y0, double ox, double oy,
+                                double bs, int nx, int ny, double reach, uint8_t* list,
+                                cudaStream_t st);
 // flags (bad = 1) any of the n points outside the polygon (closed)
 cudaError_t launch_poly_validate(const double* x, const double* y, int64_t n, Polygon poly,
                                  int* bad, cudaStream_t st);

@@ -152,14 +152,58 @@ def tables(vx, vy, frame):
     return out, span
 
 
+class Buckets:
+    """The bucket lists (stk.cu, run_job; index.cu, poly_bucket_kernel): a grid over the
+    polygon's bounding box (box frame) with side max(r_max / 2, larger side / 63.5), each bucket
+    listing the edges within r_max + half its diagonal (plus margins) of its centre; 255 when
+    more than 47 (then every edge is scanned)."""
+
+    def __init__(self, vx, vy, frame, r_max):
+        bb = (vx.min() - frame.x0, vx.max() - frame.x0, vy.min() - frame.y0, vy.max() - frame.y0)
+        r_max = r_max * (1.0 + 1e-6)
+        bw, bh = bb[1] - bb[0], bb[3] - bb[2]
+        bs = max(0.5 * r_max, max(bw, bh) / 63.5)
+        self.nx = max(1, min(64, math.ceil(bw / bs)))
+        self.ny = max(1, min(64, math.ceil(bh / bs)))
+        reach = r_max + 0.5 * math.sqrt(2.0) * bs * 1.001 + 1e-5 * (abs(bb[0]) + abs(bb[2]) +
+                                                                   bw + bh)
+        self.ox, self.oy, self.inv = f32(bb[0]), f32(bb[2]), f32(1.0 / bs)
+        self.rmax = f32(r_max * (1.0 - 1e-6))
+        nv = len(vx)
+        self.lists = []
+        for b in range(self.nx * self.ny):
+            cx = frame.x0 + bb[0] + (b % self.nx + 0.5) * bs
+            cy = frame.y0 + bb[2] + (b // self.nx + 0.5) * bs
+            lst = []
+            for k in range(nv):
+                k1 = (k + 1) % nv
+                ax, ay = vx[k] - cx, vy[k] - cy
+                dx, dy = vx[k1] - vx[k], vy[k1] - vy[k]
+                len2 = dx * dx + dy * dy
+                t = min(1.0, max(0.0, -(ax * dx + ay * dy) / len2)) if len2 > 0 else 0.0
+                ex, ey = ax + t * dx, ay + t * dy
+                if ex * ex + ey * ey <= reach * reach:
+                    lst.append(k)
+            self.lists.append(lst if len(lst) <= 47 else None)
+
+    def edges(self, cxh, cyh, rh, nv):
+        bi = min(max(int(f32(f32(cxh - self.ox) * self.inv)), 0), self.nx - 1)
+        bj = min(max(int(f32(f32(cyh - self.oy) * self.inv)), 0), self.ny - 1)
+        lst = self.lists[bj * self.nx + bi]
+        if lst is None or not rh <= self.rmax:
+            return range(nv)
+        return lst
+
+
 def _sqrt_nr(v):
     y = _rsqrt(float(v) + 1e-30)
     s = f32(v * y)
     return _fma(_fma(-s, s, v), f32(f32(0.5) * y), s)
 
 
-def share_f32(c, rh, rl, edges, span, ccw, eh, coef):
-    """Emulation of poly_share_f32: (inside, outside, error bound) or None where it refuses."""
+def share_f32(c, rh, rl, edges, span, ccw, eh, coef, buckets=None):
+    """Emulation of poly_share_f32: (inside, outside, error bound) or None where it refuses
+    (the edges of the centre's bucket list when `buckets` is given, else all)."""
     cxh, cxl, cyh, cyl = c
     k2h, k2l = f32(6.2831854820251465), f32(-1.7484555314695172e-07)
     kph, kpl = f32(3.1415927410125732), f32(-8.742277657347586e-08)
@@ -171,7 +215,9 @@ def share_f32(c, rh, rl, edges, span, ccw, eh, coef):
     a1, a1e, a1in, a2, z = (f32(40), f32(0)), f32(0), False, (f32(40), f32(0)), (f32(-1), f32(0))
     esum = emax = f32(0)
     bal = na = 0
-    for e in edges:
+    scan = range(len(edges)) if buckets is None else buckets.edges(cxh, cyh, rh, len(edges))
+    for k in scan:
+        e = edges[k]
         bx0, bx1, by0, by1 = e["box"]
         if bx0 > x1 or bx1 < x0 or by0 > y1 or by1 < y0:
             continue
@@ -342,10 +388,12 @@ def test_fp32_polygon_share_within_its_bound(orc, name):
     rng = np.random.default_rng(11)
     decided = cut = crossed = 0
     worst = 0.0
+    buckets = Buckets(vx, vy, frame, r_max)
     for px, py, r in _circles(orc, vx, vy, r_max, 1500, 7):
         want = orc.polygon_weight(px, py, r, vx, vy)
         rh, rl = _radius(r, frame, rng)
-        got = share_f32(frame.centre(px, py), rh, rl, edges, span, ccw, frame.eh, coef)
+        got = share_f32(frame.centre(px, py), rh, rl, edges, span, ccw, frame.eh, coef,
+                        buckets)
         if got is None:
             cut += 1
             continue
@@ -361,6 +409,31 @@ def test_fp32_polygon_share_within_its_bound(orc, name):
     # nearly every circle is decided, many crossings included
     assert decided >= 0.97 * (decided + cut), (decided, cut)
     assert crossed > 200 and worst > 0
+
+
+@pytest.mark.parametrize("name", ["star85", "projected40"])
+def test_bucket_lists_hold_every_edge_a_circle_meets(orc, name):
+    """For circles of radius up to the lists' reach around points of the polygon, every edge
+    that comes within r of the centre (FP64 point-segment distance) is in the list the kernel
+    picks for it; and the lists are far shorter than the edge count."""
+    vx, vy, r_max, frame, edges, span, ccw = _setup(name)
+    buckets = Buckets(vx, vy, frame, r_max)
+    nv = len(vx)
+    rng = np.random.default_rng(23)
+    listed = []
+    for px, py, _ in _circles(orc, vx, vy, r_max, 800, 29):
+        c = frame.centre(px, py)
+        r = float(buckets.rmax) * rng.uniform(0.5, 1.0)
+        scan = set(buckets.edges(c[0], c[2], f32(r), nv))
+        listed.append(len(scan))
+        for k in range(nv):
+            k1 = (k + 1) % nv
+            ax, ay = vx[k] - px, vy[k] - py
+            dx, dy = vx[k1] - vx[k], vy[k1] - vy[k]
+            t = min(1.0, max(0.0, -(ax * dx + ay * dy) / (dx * dx + dy * dy)))
+            if math.hypot(ax + t * dx, ay + t * dy) <= r:
+                assert k in scan, (name, px, py, r, k)
+    assert np.mean(listed) < 0.5 * nv, np.mean(listed)
 
 
 def test_arc_pair_error_bound():
