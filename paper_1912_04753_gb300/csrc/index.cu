@@ -157,7 +157,8 @@ __global__ void gen_csr_kernel(int64_t n, int m, const uint64_t* __restrict__ se
                 double py = __dadd_rn(g.y0, __dmul_rn(sy, u01(w.z, w.w)));
                 px = px > x1 ? x1 : px;
                 py = py > y1 ? y1 : py;
-                if (poly_contains(px, py, poly.vx, poly.vy, poly.nv)) {
+                if (poly.band ? poly_contains_banded(px, py, poly)
+                              : poly_contains(px, py, poly.vx, poly.vy, poly.nv)) {
                     xi = px;
                     yi = py;
                     found = true;

@@ -595,7 +595,8 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     e = __fmaf_rn(a, b, -p);
 }
 
-// Arc half-angle psi = acos(h / r) as a pair, from d = r - h (pair, 0 < d <= r) and r (pair):
+// Arc half-angle psi = acos(h / r) as a pair, from d = r - h (pair, 0 < d <= r), r (pair) and
+// y ~ 1 / rh (within a few ulps; the correction step makes om insensitive to it):
 // om = d / r and x = 1 - om to about 2^-46, acos(x) = sqrt(om) P(x) with P a degree-9 fit of
 // acos(x) / sqrt(1 - x) on [0, 1] (fit_arc_poly.py, fit error below 1e-9 relative), its
 // constant term and last Horner step and the product with sqrt(om) as pairs.  Measured error
@@ -603,8 +604,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 constexpr float kArcErrF32 = 3.0e-8f;
 
 __device__ __forceinline__ void arc_half_angle_pair(float dh, float dl, float rh, float rl,
-                                                    float& ph, float& pl) {
-    const float y = __frcp_rn(rh);
+                                                    float y, float& ph, float& pl) {
     const float om0 = dh * y;
     float res = __fmaf_rn(-om0, rh, dh);
     res = __fsub_rn(__fadd_rn(res, dl), om0 * rl);
@@ -651,10 +651,10 @@ __device__ __forceinline__ void arc_half_angle_pair(float dh, float dl, float rh
 // within both errors of the least (the choice of I0 would be in doubt), when entering and
 // leaving crossings do not balance, or when the errors add up to more than 8.5e-7 of the inside
 // share.  No crossing: the whole circle is inside unless it might enclose the polygon
-// (2 r >= the polygon's larger bounding-box side: refused).  inv_r = 1 / rh.
+// (2 r >= the polygon's larger bounding-box side: refused).  inv_r ~ 1 / rh (a few ulps).
 __device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, float cxl,
                                                float cyh, float cyl, float rh, float rl,
-                                               float& inside, float& outside) {
+                                               float inv_r, float& inside, float& outside) {
     const float kPiH = 3.1415927410125732f, kPiL = -8.742277657347586e-08f;
     const float k2PiH = 6.2831854820251465f, k2PiL = -1.7484555314695172e-07f;
     const float eh = pc.poly_eh;
@@ -708,13 +708,19 @@ __device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, 
         two_sum(dh, dl, dh, dl);
         if (dh < -band) continue;   // the line misses the circle
         if (dh <= band) return false;  // nearly tangent
-        const float t = sqrt_nr(dh * (rh + hh));
+        // t = sqrt(v) and 1 / t from the hardware reciprocal square root (within 2^-21 of
+        // 1 / t: the bounds below scale it by 1 + 1e-6)
+        const float v = dh * (rh + hh);
+        const float yt = rsqrtf(v);
+        const float t0 = v * yt;
+        const float t = __fmaf_rn(__fmaf_rn(-t0, t0, v), 0.5f * yt, t0);
+        const float inv_t = yt * 1.000001f;
         const float u0 = -__fmaf_rn(fxh, e1.x, fyh * e1.z);
         const float4 e2 = E[2];
         const float len = e2.z;
-        const float eang = kArcErrF32 + 2.0f * eh / t;
+        const float eang = kArcErrF32 + 2.0f * eh * inv_t;
         const float uerr = 2.5e-7f * (fabsf(fxh) + fabsf(fyh)) + 1.5e-7f * t + 6.0e-8f * len +
-                           2.0f * eh * (rh / t + 1.0f);
+                           2.0f * eh * (rh * inv_t + 1.0f);
         bool have_psi = false;
         float ph = 0.0f, pl = 0.0f, bh = 0.0f, bl = 0.0f;
         for (int q = -1; q <= 1; q += 2) {
@@ -722,7 +728,7 @@ __device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, 
             if (fabsf(u) <= uerr || fabsf(u - len) <= uerr) return false;  // at a vertex
             if (u < 0.0f || u >= len) continue;
             if (!have_psi) {
-                arc_half_angle_pair(dh, dl, rh, rl, ph, pl);
+                arc_half_angle_pair(dh, dl, rh, rl, inv_r, ph, pl);
                 float be;
                 if (neg) {
                     two_sum(e2.x, kPiH, bh, be);
@@ -859,6 +865,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
             float rh = s * ys;
             rh = __fmaf_rn(__fmaf_rn(-rh, rh, s), 0.5f * ys, rh);
             const float rl = __fadd_rn(__fmaf_rn(-rh, rh, s), r2l) * (0.5f * ys);
+            const float inv_r = ys * __fmaf_rn(-0.5f * s * ys, ys, 1.5f);  // Newton step
             // the centre's box-frame position: x hi + low; y = its row's origin
             // row (chq + chl) plus its offset in the cell
             const int row = other ? cy_u - dcy : cy_u;
@@ -869,7 +876,7 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
             two_sum(ro, cyr, cyh, cye);
             const float cyl = __fadd_rn(__fadd_rn(cye, roe),
                                         __fmaf_rn((float)row, pc.g.chl, cyrl));
-            if (rh > 0.0f && poly_share_f32(pc, cxh, cxl, cyh, cyl, rh, rl, in, out)) {
+            if (rh > 0.0f && poly_share_f32(pc, cxh, cxl, cyh, cyl, rh, rl, inv_r, in, out)) {
                 done = true;
                 // weight 1 / (inside v) - 1: outside / inside, or (1 + outside) / inside when
                 // the temporal weight is 1/2 (correctly rounded division)

@@ -38,7 +38,32 @@ static __device__ __forceinline__ bool poly_contains(double px, double py, const
     return inside;
 }
 
-// Distance from (px, py) to the polygon's boundary.
+// poly_contains over the edges of py's band only (Polygon::band): the same decisions, since
+// an edge whose y-range misses py neither holds the point nor straddles the ray's height, and
+// a point outside the vertices' y-range meets no edge at all.
+static __device__ __forceinline__ bool poly_contains_banded(double px, double py,
+                                                            const Polygon& poly) {
+    if (!(py >= poly.band_ylo && py <= poly.band_yhi)) return false;
+    const int b = min(max((int)((py - poly.band_ylo) * poly.band_inv), 0), kPolyBands - 1);
+    const uint8_t* L = poly.band + (size_t)b * kPolyBandBytes;
+    const int cnt = L[0];
+    bool inside = false;
+    for (int i = 0; i < cnt; ++i) {
+        const int k = L[1 + i];
+        const int k1 = k + 1 < poly.nv ? k + 1 : 0;
+        const double ax = poly.vx[k], ay = poly.vy[k], bx = poly.vx[k1], by = poly.vy[k1];
+        if (poly_on_segment(px, py, ax, ay, bx, by)) return true;
+        if ((ay > py) != (by > py)) {
+            const double xc = __dadd_rn(
+                ax, __ddiv_rn(__dmul_rn(__dsub_rn(py, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
+            if (px < xc) inside = !inside;
+        }
+    }
+    return inside;
+}
+
+// Distance from (px, py) to the polygon's boundary (the root of the least squared distance:
+// the same value as the least root, the rounded root being monotone).
 static __device__ __forceinline__ double poly_boundary_distance(double px, double py,
                                                                 const double* vx,
                                                                 const double* vy, int nv) {
@@ -52,9 +77,9 @@ static __device__ __forceinline__ double poly_boundary_distance(double px, doubl
         double s = len2 > 0.0 ? (fx * dx + fy * dy) / len2 : 0.0;
         s = fmin(1.0, fmax(0.0, s));
         const double ex = fx - s * dx, ey = fy - s * dy;
-        best = fmin(best, sqrt(ex * ex + ey * ey));
+        best = fmin(best, ex * ex + ey * ey);
     }
-    return best;
+    return sqrt(best);
 }
 
 

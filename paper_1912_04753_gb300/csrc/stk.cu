@@ -70,9 +70,43 @@ T* as(DevBuf& b) {
     return reinterpret_cast<T*>(b.p);
 }
 
+// byte offset of a polygon's band lists in its device buffer (after the vertices, the edge
+// boxes, the FP32 edge table and the bucket lists)
+size_t poly_band_offset(int nv) {
+    return 96 * (size_t)nv + (size_t)kPolyBucketsMax * kPolyBucketsMax * kPolyBucketBytes;
+}
+
 }  // namespace
 
 namespace stk {
+// The y-band edge lists of a polygon (Polygon::band): band b of kPolyBands equal bands over the
+// vertices' y-range lists the edges whose closed y-range meets the band widened by eps, far
+// above the rounding of the band index on the device.
+void build_poly_bands(const double* vx, const double* vy, int nv, uint8_t* out, double* ylo,
+                      double* yhi) {
+    (void)vx;
+    double lo = vy[0], hi = vy[0];
+    for (int k = 1; k < nv; ++k) {
+        lo = std::min(lo, vy[k]);
+        hi = std::max(hi, vy[k]);
+    }
+    const double bh = (hi - lo) / kPolyBands;
+    const double eps = 1e-9 * (hi - lo) + 1e-12 * (fabs(lo) + fabs(hi));
+    for (int b = 0; b < kPolyBands; ++b) {
+        const double blo = lo + b * bh - eps, bhi = lo + (b + 1) * bh + eps;
+        uint8_t* L = out + (size_t)b * kPolyBandBytes;
+        int c = 0;
+        for (int k = 0; k < nv; ++k) {
+            const int k1 = (k + 1) % nv;
+            if (std::min(vy[k], vy[k1]) <= bhi && std::max(vy[k], vy[k1]) >= blo)
+                L[1 + c++] = (uint8_t)k;
+        }
+        L[0] = (uint8_t)c;
+    }
+    *ylo = lo;
+    *yhi = hi;
+}
+
 void stk_note_error(int code, const char* msg) {
     (void)code;
     snprintf(g_err, sizeof g_err, "%s", msg);
@@ -121,11 +155,12 @@ struct stk_handle {
     size_t wave_budget = 0;  // device bytes a job may hold (0: a share of the free memory)
     // polygon study area (nv = 0: the box), vertices in device memory, and the area A of Eq. 2
     DevBuf poly;  // [nv] x, [nv] y (FP64), [nv] edge boxes (float4), [4 nv] float4 (pe32),
-                  // the bucket lists (kPolyBucketsMax^2 x kPolyBucketBytes)
+                  // the bucket lists (kPolyBucketsMax^2 x kPolyBucketBytes), the band lists
     int nv = 0;
     int poly_ccw = 1;
     double poly_span = 0.0;  // larger side of the polygon's bounding box
     double poly_bb[4] = {0.0, 0.0, 0.0, 0.0};  // its bounding box in the box frame
+    double band_ylo = 0.0, band_yhi = 0.0;     // the band lists' y-range
     double area = 0.0;
     // inhomogeneous K: the relative intensity (device tables hcell and cum, [2][cells]), h of
     // the observed points in input order, and the per-wave h arrays (unsorted, sorted) and
@@ -600,6 +635,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         poly.vx = as<double>(h->poly);
         poly.vy = as<double>(h->poly) + h->nv;
         poly.nv = h->nv;
+        poly.band = as<uint8_t>(h->poly) + poly_band_offset(h->nv);
+        poly.band_ylo = h->band_ylo;
+        poly.band_yhi = h->band_yhi;
+        poly.band_inv = kPolyBands / (h->band_yhi - h->band_ylo);
         h->h_pc->nv = h->nv;
         h->h_pc->pccw = h->poly_ccw;
         h->h_pc->pvx = poly.vx;
@@ -1602,7 +1641,8 @@ int stk_sim_points_polygon(const stk_box* box, const double* vx, const double* v
     if ((rc = ensure(bx, b8, "x")) || (rc = ensure(by, b8, "y")) || (rc = ensure(bt, b8, "t")) ||
         (rc = ensure(bk, b4, "keys")) || (rc = ensure(br, b4, "ranks")) ||
         (rc = ensure(bc, 16, "counts")) || (rc = ensure(bs, 16, "seed")) ||
-        (rc = ensure(bp, 16 * (size_t)nv, "polygon")) || (rc = ensure(be, 16, "status"))) {
+        (rc = ensure(bp, 16 * (size_t)nv + (size_t)kPolyBands * kPolyBandBytes, "polygon")) ||
+        (rc = ensure(be, 16, "status"))) {
         release();
         return rc;
     }
@@ -1610,15 +1650,22 @@ int stk_sim_points_polygon(const stk_box* box, const double* vx, const double* v
         uint64_t seed;
         uint32_t sim, pad;
     } key_sim = {seed, sim, 0};
+    std::vector<uint8_t> bands((size_t)kPolyBands * kPolyBandBytes, 0);
     Polygon poly;
     poly.vx = as<double>(bp);
     poly.vy = as<double>(bp) + nv;
     poly.nv = nv;
+    poly.band = as<uint8_t>(bp) + 16 * (size_t)nv;
+    build_poly_bands(vx, vy, nv, bands.data(), &poly.band_ylo, &poly.band_yhi);
+    poly.band_inv = kPolyBands / (poly.band_yhi - poly.band_ylo);
     cudaStream_t st = nullptr;
     unsigned long long miss = 0;
     cudaError_t e = cudaMemcpyAsync(bp.p, vx, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(as<double>(bp) + nv, vy, 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(as<uint8_t>(bp) + 16 * (size_t)nv, bands.data(), bands.size(),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bc.p, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(be.p, 0, 16, st);
     if (e == cudaSuccess)
@@ -1824,10 +1871,10 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     }
     int rc;
     DevBuf pv;
-    if ((rc = ensure(pv, 96 * (size_t)nv + (size_t)kPolyBucketsMax * kPolyBucketsMax *
-                                              kPolyBucketBytes,
-                     "polygon")))
-        return rc;
+    std::vector<uint8_t> bands((size_t)kPolyBands * kPolyBandBytes, 0);
+    double band_ylo = 0.0, band_yhi = 0.0;
+    build_poly_bands(vx, vy, nv, bands.data(), &band_ylo, &band_yhi);
+    if ((rc = ensure(pv, poly_band_offset(nv) + bands.size(), "polygon"))) return rc;
     cudaStream_t st = h->stream;
     int bad = 0;
     DevBuf flag;
@@ -1848,6 +1895,9 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(as<double>(pv) + 4 * nv, pe32.data(), 64 * (size_t)nv,
                             cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(as<uint8_t>(pv) + poly_band_offset(nv), bands.data(), bands.size(),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(flag.p, 0, 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ebox and pe32 are read
     if (e == cudaSuccess) e = launch_poly_validate(h->d_x, h->d_y, h->n, poly, as<int>(flag), st);
@@ -1865,6 +1915,8 @@ int stk_set_polygon(stk_handle* h, const double* vx, const double* vy, int nv) {
     free_buf(h->poly);
     h->poly = pv;
     h->nv = nv;
+    h->band_ylo = band_ylo;
+    h->band_yhi = band_yhi;
     h->poly_bb[0] = *std::min_element(vx, vx + nv) - h->box[0];
     h->poly_bb[1] = *std::max_element(vx, vx + nv) - h->box[0];
     h->poly_bb[2] = *std::min_element(vy, vy + nv) - h->box[2];

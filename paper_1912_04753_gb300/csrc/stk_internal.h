@@ -252,7 +252,18 @@ struct Polygon {
     const double* vx = nullptr;
     const double* vy = nullptr;
     int nv = 0;
+    // optional y-band edge lists for the point-in-polygon test (poly_contains_banded):
+    // kPolyBands bands of equal height over [band_ylo, band_yhi] (the vertices' y-range), band b
+    // at band + b (1 + kMaxPolyVertices): its count, then the edges whose y-range meets the band
+    // (widened by a margin); null: every edge is tested
+    const uint8_t* band = nullptr;
+    double band_ylo = 0.0, band_yhi = 0.0, band_inv = 0.0;
 };
+constexpr int kPolyBands = 32;
+constexpr int kPolyBandBytes = 1 + kMaxPolyVertices;
+// host: the band lists of a polygon (kPolyBands x kPolyBandBytes bytes) and the y-range
+void build_poly_bands(const double* vx, const double* vy, int nv, uint8_t* out, double* ylo,
+                      double* yhi);
 // Relative intensity of the inhomogeneous K: rho on nix x niy x nit equal cells of the box
 // ([nit][niy][nix], x fastest), in device memory.
 struct Intensity {

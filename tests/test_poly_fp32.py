@@ -57,10 +57,18 @@ def _rsqrt(v):
     return f32(1.0 / math.sqrt(float(v)))
 
 
-def arc_pair(dh, dl, rh, rl, coef):
-    """Emulation of arc_half_angle_pair: psi = acos(1 - d / r) as (hi, lo)."""
+def _inv(v):
+    """1 / v as the kernel forms it from the reciprocal square root of v^2 and a Newton step
+    (the hardware's approximation taken as correctly rounded here)."""
+    s = f32(v * v)
+    ys = _rsqrt(s)
+    return f32(ys * _fma(f32(f32(f32(-0.5) * s) * ys), ys, f32(1.5)))
+
+
+def arc_pair(dh, dl, rh, rl, coef, y=None):
+    """Emulation of arc_half_angle_pair: psi = acos(1 - d / r) as (hi, lo); y ~ 1 / rh."""
     c, c0h, c0l = coef
-    y = f32(1.0 / float(rh))  # __frcp_rn
+    y = _inv(rh) if y is None else y
     om0 = f32(dh * y)
     res = _fma(-om0, rh, dh)
     res = f32(f32(res + dl) - f32(om0 * rl))
@@ -205,6 +213,7 @@ def share_f32(c, rh, rl, edges, span, ccw, eh, coef, buckets=None):
     """Emulation of poly_share_f32: (inside, outside, error bound) or None where it refuses
     (the edges of the centre's bucket list when `buckets` is given, else all)."""
     cxh, cxl, cyh, cyl = c
+    inv_r = _inv(rh)
     k2h, k2l = f32(6.2831854820251465), f32(-1.7484555314695172e-07)
     kph, kpl = f32(3.1415927410125732), f32(-8.742277657347586e-08)
     m = f32(f32(f32(rh * f32(1e-5)) + f32(f32(1e-6) * f32(abs(cxh) + abs(cyh)))) + eh)
@@ -243,12 +252,17 @@ def share_f32(c, rh, rl, edges, span, ccw, eh, coef, buckets=None):
             continue
         if dh <= band:
             return None
-        t = _sqrt_nr(f32(dh * f32(rh + hh)))
+        v = f32(dh * f32(rh + hh))
+        yt = _rsqrt(v)
+        t0 = f32(v * yt)
+        t = _fma(_fma(-t0, t0, v), f32(f32(0.5) * yt), t0)
+        inv_t = f32(yt * f32(1.000001))
         u0 = -_fma(fxh, uxh, f32(fyh * uyh))
         ln = e["len"]
-        eang = f32(f32(ARC_ERR) + f32(f32(f32(2.0) * eh) / t))
+        eang = f32(f32(ARC_ERR) + f32(f32(f32(2.0) * eh) * inv_t))
         uerr = f32(f32(f32(f32(2.5e-7) * f32(abs(fxh) + abs(fyh))) + f32(f32(1.5e-7) * t)) +
-                   f32(f32(f32(6.0e-8) * ln) + f32(f32(f32(2.0) * eh) * f32(f32(rh / t) + 1))))
+                   f32(f32(f32(6.0e-8) * ln) +
+                       f32(f32(f32(2.0) * eh) * f32(f32(rh * inv_t) + f32(1)))))
         psi = None
         for q in (-1, 1):
             u = _fma(f32(q), t, u0)
@@ -257,7 +271,7 @@ def share_f32(c, rh, rl, edges, span, ccw, eh, coef, buckets=None):
             if u < 0 or u >= ln:
                 continue
             if psi is None:
-                psi = arc_pair(dh, dl, rh, rl, coef)
+                psi = arc_pair(dh, dl, rh, rl, coef, inv_r)
                 ph0, pl0 = e["phi"]
                 if neg:
                     bh, be = _two_sum(ph0, kph)
