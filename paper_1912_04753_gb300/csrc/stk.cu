@@ -244,11 +244,13 @@ int configure_kernels(stk_handle* h, int nbins) {
     return STK_OK;
 }
 
-// FP64 queue entries for a wave of `points` points (about one undecided pair per point is the
-// worst seen; an overflow is still evaluated exactly, inside the pair kernel)
+// FP64 queue entries for a wave of `points` points: four per point (the workloads measured
+// push at most two per point), at most 2^27 (2 GiB).  An overflow is still evaluated exactly,
+// but inside the pair kernel, where its FP64 work holds up the warp that meets it: the 2M-point
+// job's 1.3e8 entries overflowing a queue of 2^24 cost its pair kernel 18%.
 unsigned int exact_queue_cap(int64_t points) {
     int64_t c = 1 << 16;
-    while (c < points && c < (int64_t(1) << 24)) c <<= 1;
+    while (c < 4 * points && c < (int64_t(1) << 27)) c <<= 1;
     return (unsigned int)c;
 }
 
@@ -262,7 +264,7 @@ Footprint footprint(int64_t n, const Grid& g, int nbins, int R, int groups, bool
     // starts, scan scratch; work counts/offsets and units; histograms; seeds; FP64 queue
     f.per_real = un * (24 + 8 + 24 + 32 + 8) + ncells * 12 + ncells / 256 + 8 +
                  (nrows + 1) * 8 + (nrows + un / kUnit + 1) * 16 + 4 + (size_t)nbins * 24 +
-                 8 + 12 + (fp32 ? 16 * un : 0) + un /* role flags */ +
+                 8 + 12 + (fp32 ? 64 * un : 0) + un /* role flags */ +
                  4 * 3 * (size_t)filter_stride(n) /* filter arrays */ +
                  32 * un /* scatter staging */ +
                  (inh ? 16 * un + 8 * (size_t)nbins : 0);
