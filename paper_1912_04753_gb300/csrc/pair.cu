@@ -77,6 +77,13 @@ __device__ __forceinline__ unsigned long long excess_fixed64(double w) {
     return e > 0.0 ? __double2ull_rn(e * 4294967296.0) : 0ull;
 }
 
+// excess_fixed64(1 / (om v)) without the division when om = 1 (v is 1 or 1/2: the weight is
+// exactly 1 or 2, as the division gives it)
+__device__ __forceinline__ unsigned long long excess_of_weights(double om, double v) {
+    if (om == 1.0) return v == 1.0 ? 0ull : 4294967296ull;
+    return excess_fixed64(1.0 / (om * v));
+}
+
 // Exact evaluation of the unordered pair {i, j} with the reference rounding (every operation
 // rounded separately): its bin and the fixed-point excess of both ordered pairs (i, j), with
 // centre i, and (j, i), with centre j.  d2 and u are the same for both orders (the FP64
@@ -92,16 +99,21 @@ __device__ __noinline__ bool pair_exact(const PairConsts& pc, double xi, double 
     if (d2 > pc.s2[pc.cs - 1]) return false;
     const double u = fabs(__dsub_rn(ti, tj));
     if (u > pc.tt[pc.ct - 1]) return false;
-    a = 0;
+    // bins: the tables' start (never past the answer) and exact comparisons from there
+    int ks = (int)(d2 * pc.inv_hs2_64);
+    ks = ks < kTab - 1 ? ks : kTab - 1;
+    a = pc.tab_s64[ks];
     while (a < pc.cs - 1 && d2 > pc.s2[a]) ++a;
-    b = 0;
+    int kt = (int)(u * pc.inv_ht_64);
+    kt = kt < kTab - 1 ? kt : kTab - 1;
+    b = pc.tab_t64[kt];
     while (b < pc.ct - 1 && u > pc.tt[b]) ++b;
     exc_i = 0;
     exc_j = 0;
     if (pc.edge) {
         const double r = __dsqrt_rn(d2);
-        exc_i = excess_fixed64(1.0 / (omega64<POLY>(pc, xi, yi, r) * v64(pc, ti, u)));
-        exc_j = excess_fixed64(1.0 / (omega64<POLY>(pc, xj, yj, r) * v64(pc, tj, u)));
+        exc_i = excess_of_weights(omega64<POLY>(pc, xi, yi, r), v64(pc, ti, u));
+        exc_j = excess_of_weights(omega64<POLY>(pc, xj, yj, r), v64(pc, tj, u));
     }
     return true;
 }
