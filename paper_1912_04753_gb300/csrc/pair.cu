@@ -40,6 +40,37 @@ constexpr int kVarInh = 2;    // inhomogeneous K
 
 // ---------------------------------------------------------------- exact FP64 pair (reference)
 
+// The job's polygon with its band lists.
+__device__ __forceinline__ Polygon poly_of(const PairConsts& pc) {
+    Polygon p;
+    p.vx = pc.pvx;
+    p.vy = pc.pvy;
+    p.nv = pc.nv;
+    p.band = pc.pband;
+    p.band_ylo = pc.band_ylo;
+    p.band_yhi = pc.band_yhi;
+    p.band_inv = pc.band_inv;
+    return p;
+}
+
+// The edges a circle of radius r around (xi, yi) can meet: its centre's bucket list (ne
+// indices), or null (every edge, ne = nv) when the radius is beyond the lists' reach or the
+// list overflowed.  The bucket index comes from the FP32 box-frame position; the lists' margin
+// covers its rounding.
+__device__ __forceinline__ const uint8_t* poly_edges_of(const PairConsts& pc, double xi,
+                                                        double yi, double r, int& ne) {
+    ne = pc.nv;
+    if (!(r <= (double)pc.pb_rmax)) return nullptr;
+    const float fx = (float)__dsub_rn(xi, pc.g.x0), fy = (float)__dsub_rn(yi, pc.g.y0);
+    const int bi = min(max((int)((fx - pc.pb_ox) * pc.pb_inv), 0), pc.pb_nx - 1);
+    const int bj = min(max((int)((fy - pc.pb_oy) * pc.pb_inv), 0), pc.pb_ny - 1);
+    const uint8_t* L = pc.pb_list + kPolyBucketBytes * (bj * pc.pb_nx + bi);
+    const int lc = L[0];
+    if (lc > kPolyBucketCap) return nullptr;
+    ne = lc;
+    return L + 1;
+}
+
 // Section 3 isotropic weight for a rectangle when the radius is at most half of each side:
 // at most one x-edge and one y-edge cut the circle.  An edge at distance e < r removes an arc
 // of half-angle acos(e/r) around its normal; when the corner lies inside the circle the two
@@ -51,8 +82,10 @@ __device__ __forceinline__ double omega64(const PairConsts& pc, double xi, doubl
                                           double r) {
     if (r == 0.0) return 1.0;
     if (POLY && pc.nv > 0) {
-        const double w =
-            poly_weight_fast<true>(xi, yi, r, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+        int ne;
+        const uint8_t* list = poly_edges_of(pc, xi, yi, r, ne);
+        const double w = poly_weight_fast<true>(xi, yi, r, poly_of(pc), pc.pebox, pc.pccw,
+                                                list, ne);
         return w >= 0.0 ? w : poly_weight(xi, yi, r, pc.pvx, pc.pvy, pc.nv);
     }
     const double ex = fmin(__dsub_rn(xi, pc.g.x0), __dsub_rn(pc.g.x1, xi));
@@ -907,8 +940,10 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
             const double xa = rb.X[base + a], ya = rb.Y[base + a];
             const double dx = __dsub_rn(xa, rb.X[base + b]), dy = __dsub_rn(ya, rb.Y[base + b]);
             const double r64 = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-            const double in64 =
-                poly_weight_fast<false>(xa, ya, r64, pc.pvx, pc.pvy, pc.pebox, pc.nv, pc.pccw);
+            int ne;
+            const uint8_t* list = poly_edges_of(pc, xa, ya, r64, ne);
+            const double in64 = poly_weight_fast<false>(xa, ya, r64, poly_of(pc), pc.pebox,
+                                                        pc.pccw, list, ne);
             if (in64 > 0.0) {
                 const double w = 1.0 / (in64 * (vhalf ? 0.5 : 1.0));
                 if (w > 8.0) {

@@ -152,10 +152,16 @@ static __device__ __noinline__ double poly_weight(double xi, double yi, double r
 // then uses poly_weight.
 // F64: arc lengths in FP64 (the FP64 paths); else in FP32 from FP64 end vectors (relative
 // error ~1e-7 of each arc: the FP32-guarded path).
+// `list` (ne increasing edge indices, or null: every edge) restricts the scan to the edges that
+// can meet the circle (a bucket list): the same crossings in the same order.  The no-crossing
+// case tests a point of the circle with poly_contains_banded.
 template <bool F64>
 static __device__ __noinline__ double poly_weight_fast(double xi, double yi, double r,
-                                                       const double* vx, const double* vy,
-                                                       const float4* ebox, int nv, int ccw) {
+                                                       const Polygon& poly, const float4* ebox,
+                                                       int ccw, const uint8_t* list, int ne) {
+    const double* vx = poly.vx;
+    const double* vy = poly.vy;
+    const int nv = poly.nv;
     if (r <= 0.0) return 1.0;
     // crossing points relative to the centre (FP64), an FP32 angle to sort them by, and
     // whether the circle enters the polygon there
@@ -167,7 +173,8 @@ static __device__ __noinline__ double poly_weight_fast(double xi, double yi, dou
     const float x0 = (float)(xi - r) - m, x1 = (float)(xi + r) + m;
     const float y0 = (float)(yi - r) - m, y1 = (float)(yi + r) + m;
     const double r2 = r * r;
-    for (int k = 0; k < nv; ++k) {
+    for (int i = 0; i < ne; ++i) {
+        const int k = list ? (int)list[i] : i;
         const float4 eb = ebox[k];
         if (eb.x > x1 || eb.y < x0 || eb.z > y1 || eb.w < y0) continue;
         const int k1 = k + 1 < nv ? k + 1 : 0;
@@ -193,7 +200,7 @@ static __device__ __noinline__ double poly_weight_fast(double xi, double yi, dou
             enter[na++] = (q == 1) == (ccw != 0);
         }
     }
-    if (na == 0) return poly_contains(xi + r, yi, vx, vy, nv) ? 1.0 : 0.0;
+    if (na == 0) return poly_contains_banded(xi + r, yi, poly) ? 1.0 : 0.0;
     if (na & 1) return -1.0;
     for (int a = 1; a < na; ++a) {  // insertion sort by angle: a handful of crossings
         const float kv = key[a];

@@ -641,6 +641,10 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
         poly.band_ylo = h->band_ylo;
         poly.band_yhi = h->band_yhi;
         poly.band_inv = kPolyBands / (h->band_yhi - h->band_ylo);
+        h->h_pc->pband = poly.band;
+        h->h_pc->band_ylo = poly.band_ylo;
+        h->h_pc->band_yhi = poly.band_yhi;
+        h->h_pc->band_inv = poly.band_inv;
         h->h_pc->nv = h->nv;
         h->h_pc->pccw = h->poly_ccw;
         h->h_pc->pvx = poly.vx;

@@ -105,6 +105,9 @@ struct PairConsts {
     float pb_rmax;            // the lists hold every edge circles up to this radius can meet
     int pb_nx, pb_ny;
     const uint8_t* pb_list;
+    // the polygon's y-band lists (Polygon::band)
+    const uint8_t* pband;
+    double band_ylo, band_yhi, band_inv;
     // FP64 path: exact thresholds (s_a*s_a rounded once) and a table over d^2 and u.
     double s2[kMaxThr], tt[kMaxThr];
     double inv_hs2_64, inv_ht_64;
