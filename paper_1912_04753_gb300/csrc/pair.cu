@@ -449,6 +449,11 @@ struct Smem32 {
     PairConsts pc;      // the single-job kernel copies only the part before `s2`
     WarpSm w[kWarps];
     unsigned long long cursor;  // (tile << 32) | next index in the tile, see next_unit
+    // polygon study areas (no block barrier between realizations): the cursors of realizations
+    // of either parity, the warps done with the realization in each slot, and the realization
+    // each slot is ready for
+    unsigned long long pcur[2];
+    int pdone[2], pready[2];
     // histograms follow (dynamic size)
 };
 
@@ -1750,6 +1755,8 @@ size_t smem_with_reps(size_t base, int nbins, int* reps, size_t budget) {
 
 }  // namespace
 
+size_t pair_fp32_poly_extra(int nbins, int reps) { return hist_bytes(nbins, reps); }
+
 size_t pair_fp32_smem(int nbins, int* reps, bool inh) {
     if (inh) {  // three u64 sums and a u32 count per bin and replica
         const size_t b = (sizeof(Smem32) + 15) & ~size_t(15);
@@ -1809,6 +1816,13 @@ cudaError_t pair_kernels_configure(size_t smem32, size_t smem64) {
     // inhomogeneous K: 32 bytes per bin and replica
     const size_t smem32_inh = std::max<size_t>(
         smem32, ((sizeof(Smem32) + 15) & ~size_t(15)) + (size_t)kMaxThr * kMaxThr * 32);
+    // polygon study areas: two histogram sets (pair_fp32_poly_extra), within the same cap
+    for (const void* f : {(const void*)pair_fp32_kernel<false, true, true, kVarPlain>,
+                          (const void*)pair_fp32_kernel<true, true, true, kVarPlain>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem32_inh);
+        if (e != cudaSuccess) return e;
+    }
     const void* k32i[4] = {(const void*)pair_fp32_kernel<false, false, false, kVarInh>,
                            (const void*)pair_fp32_kernel<false, true, false, kVarInh>,
                            (const void*)pair_fp32_kernel<true, false, false, kVarInh>,

@@ -30,6 +30,24 @@
             hh[i] = 0;
         }
     }
+    // In a polygon study area the cost of a work unit varies so much (units along the outline
+    // weigh many times the others) that a block barrier at the end of each realization left its
+    // warps waiting for the slowest: there, realizations of either parity have their own
+    // histogram set (a second set follows the first) and cursor, the last warp done with a
+    // realization flushes its set, claims the block's first tile of the realization two on and
+    // marks the slot ready for it, and a warp waits only for its next realization's slot.
+    const size_t set_bytes = (size_t)reps * nbins * 16;
+    if (POLY) {
+        uint32_t* s1 = reinterpret_cast<uint32_t*>(smem_raw + hist_off + set_bytes);
+        for (size_t i = tid; i < set_bytes / 4; i += kBlock) s1[i] = 0u;
+        if (tid == 0) {
+            sm.pcur[0] = (unsigned long long)atomicAdd(&counters[0], 1u) << 32;
+            sm.pcur[1] = m > 1 ? (unsigned long long)atomicAdd(&counters[1], 1u) << 32 : 0ull;
+            sm.pdone[0] = sm.pdone[1] = 0;
+            sm.pready[0] = 0;
+            sm.pready[1] = 1;
+        }
+    }
     WarpCtx w;
     w.hc = hc + (warp % reps) * nbins;
     w.hh = hh + (warp % reps) * nbins;
@@ -67,10 +85,36 @@
         w.mk = (rb.mask != nullptr && (rb.mask_all || k == 0))
                    ? rb.mask + (rb.mask_all ? base : 0)
                    : nullptr;
-        if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
-        __syncthreads();
+        if (POLY) {
+            // wait (bounded) until this realization's slot is flushed and its cursor claimed
+            const int slot = k & 1;
+            if (lane == 0) {
+                int spin = 0;
+                while (*reinterpret_cast<volatile int*>(&sm.pready[slot]) != k) {
+                    if (++spin > kSpinLimit) {
+                        atomicAdd(&acc.stats[4], 1ull);  // never expected: the flusher runs
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __syncwarp();
+            __threadfence_block();
+            const size_t so = slot ? set_bytes : 0;
+            unsigned long long* hes = reinterpret_cast<unsigned long long*>(
+                smem_raw + hist_off + so);
+            uint32_t* hcs = reinterpret_cast<uint32_t*>(hes + (size_t)reps * nbins);
+            w.he = hes + (warp % reps) * nbins;
+            w.hc = hcs + (warp % reps) * nbins;
+            w.hh = hcs + (size_t)reps * nbins + (warp % reps) * nbins;
+            since_flush = 0;
+        } else {
+            if (tid == 0) sm.cursor = (unsigned long long)atomicAdd(&counters[k], 1u) << 32;
+            __syncthreads();
+        }
+        unsigned long long* cursor = POLY ? &sm.pcur[k & 1] : &sm.cursor;
         for (;;) {
-            const uint32_t ui = next_unit(&sm.cursor, &counters[k], ubeg, uend, tile, ntiles,
+            const uint32_t ui = next_unit(cursor, &counters[k], ubeg, uend, tile, ntiles,
                                           lane, acc.stats, pc.never_publish != 0);
             if (ui == kNoUnit) break;
             const WorkItem wi = units[ui];
@@ -214,13 +258,41 @@
                 since_flush = 0;
             }
         }
-        __syncthreads();
-        // every warp of the block is done with realization k: add its histograms
-        if (VAR == kVarInh)
-            flush_hist_inh(k, nbins, reps, hc, he, hf, hw, acc);
-        else
-            flush_hist(k, nbins, reps, hc, he, acc, hh);
-        since_flush = 0;
+        if (POLY) {
+            // done with realization k; the last warp of the block flushes the slot's set
+            const int slot = k & 1;
+            __threadfence_block();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&sm.pdone[slot], 1) == kWarps - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                const size_t so = slot ? set_bytes : 0;
+                unsigned long long* hes = reinterpret_cast<unsigned long long*>(
+                    smem_raw + hist_off + so);
+                uint32_t* hcs = reinterpret_cast<uint32_t*>(hes + (size_t)reps * nbins);
+                for (int r = 0; r < reps; ++r)
+                    warp_flush(k, nbins, hcs + r * nbins, hcs + (size_t)(reps + r) * nbins,
+                               hes + r * nbins, acc, lane);
+                __syncwarp();
+                if (lane == 0) {
+                    sm.pdone[slot] = 0;
+                    if (k + 2 < m)
+                        sm.pcur[slot] = (unsigned long long)atomicAdd(&counters[k + 2], 1u) << 32;
+                    __threadfence_block();
+                    *reinterpret_cast<volatile int*>(&sm.pready[slot]) = k + 2;
+                }
+                __syncwarp();
+            }
+        } else {
+            __syncthreads();
+            // every warp of the block is done with realization k: add its histograms
+            if (VAR == kVarInh)
+                flush_hist_inh(k, nbins, reps, hc, he, hf, hw, acc);
+            else
+                flush_hist(k, nbins, reps, hc, he, acc, hh);
+            since_flush = 0;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
     if (lane == 0) atomicAdd(&acc.stats[0], n_cand);

@@ -823,6 +823,7 @@ int run_job(stk_handle* h, const stk_request* q, bool include_obs, const SimPlan
     int reps = fp32 ? h->reps32 : h->reps64;
     size_t smem = fp32 ? h->smem32 : h->smem64;
     if (inh) smem = fp32 ? pair_fp32_smem(nbins, &reps, true) : pair_fp64_smem(nbins, &reps, true);
+    if (fp32 && !inh && h->nv > 0) smem += pair_fp32_poly_extra(nbins, reps);
     // the launch shape's blocks per SM: 3 only where the kernel has that instantiation
     const int shape_bps = fp32 && bps_req == 3 && pair_fp32_shape_tunable(*h->h_pc, inh) ? 3 : 2;
     const int bps = fp32 ? pair_fp32_blocks_per_sm(smem, shape_bps)

@@ -354,6 +354,9 @@ cudaError_t launch_pair_fp64(const PairConsts* d_pc, size_t smem, int reps, int 
                              RealBatch rb, const WorkItem* units, const uint32_t* unit_off,
                              uint32_t* counters, Accum acc, cudaStream_t st, bool poly = false,
                              bool inh = false, bool dir = false);
+// dynamic shared memory a polygon job's FP32 kernel adds to pair_fp32_smem: its second
+// histogram set (the realizations of either parity have their own)
+size_t pair_fp32_poly_extra(int nbins, int reps);
 size_t pair_fp32_smem(int nbins, int* replicas, bool inh = false);
 size_t pair_fp64_smem(int nbins, int* replicas, bool inh = false);
 cudaError_t pair_kernels_configure(size_t smem32, size_t smem64);
