@@ -521,6 +521,9 @@ struct WarpCtx {
     uint32_t real;
     uint32_t c_begin;
     int cy;                   // the unit's cell row (set in polygon study areas only)
+    // polygon study areas: the global excess accumulators, for weights above 8
+    unsigned long long* exlo;
+    unsigned long long* exhi;
     uint32_t onA, onB;        // lanes whose centre counts as a centre / as a neighbour
     int q2n;                  // queue 2 fill (warp-uniform)
     bool deep;                // every point the unit meets has w = v = 1 for counted pairs
@@ -865,8 +868,9 @@ __device__ __forceinline__ bool poly_share_f32(const PairConsts& pc, float cxh, 
 // radius and the centre's box-frame position as pairs of FP32 numbers (the records' hi and
 // low parts; y from the centre's cell row cy_u = the unit's row, or the neighbour's), else, or
 // when it refuses, from the crossings' directions with FP64 crossing points
-// (poly_weight_fast).  What neither decides, and weights above 8 (beyond the shared
-// accumulators' bound), go to the FP64 queue.  Out of line like the rectangle's version, so
+// (poly_weight_fast).  FP32-tier weights above 8 (beyond the shared accumulators' bound) are
+// added to the realization's global sums (exlo, exhi); what neither tier decides, and FP64
+// weights above 8, go to the FP64 queue.  Out of line like the rectangle's version, so
 // that the rectangle path does not carry its registers.
 __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const PairConsts* gpc,
                                                 WarpSm* wsp, const float4* __restrict__ Ek,
@@ -875,7 +879,9 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
                                                 const float2* __restrict__ Plok, RealBatch rb,
                                                 ExactQueue xq, int off, int cnt, int lane,
                                                 unsigned long long* he, uint32_t* hc,
-                                                uint32_t real, uint32_t c_begin, int cy_u) {
+                                                uint32_t real, uint32_t c_begin, int cy_u,
+                                                unsigned long long* exlo,
+                                                unsigned long long* exhi) {
     const PairConsts& pc = *pcs;
     WarpSm& ws = *wsp;
     (void)Ek;
@@ -931,12 +937,19 @@ __device__ __noinline__ void drain_weights_poly(const PairConsts* pcs, const Pai
                 // weight 1 / (inside v) - 1: outside / inside, or (1 + outside) / inside when
                 // the temporal weight is 1/2 (correctly rounded division)
                 const float xs = __fdiv_rn(vhalf ? 1.0f + out : out, in);
-                if (!(xs <= 7.0f)) {
-                    exact = true;
-                } else {
+                if (xs <= 7.0f) {
                     const unsigned long long exc =
                         xs > 0.0f ? __float2ull_rn(xs * 4294967296.0f) : 0ull;
                     if (exc) atomicAdd(&he[bin], exc);
+                } else if (xs < 1048576.0f) {
+                    // above the shared accumulators' bound: straight to the realization's
+                    // global sums (the same fixed point, split into its 32-bit halves)
+                    const unsigned long long exc = __float2ull_rn(xs * 4294967296.0f);
+                    const int64_t o = (int64_t)real * pc.nbins + bin;
+                    atomicAdd(&exlo[o], exc & 0xffffffffull);
+                    atomicAdd(&exhi[o], exc >> 32);
+                } else {
+                    exact = true;
                 }
             }
         }
@@ -1036,7 +1049,7 @@ __device__ __forceinline__ void flush_weights(WarpSm& ws, const PairConsts& pc,
     while (w.q2n - off >= 32) {
         if (POLY)
             drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32, lane,
-                               w.he, w.hc, w.real, w.c_begin, w.cy);
+                               w.he, w.hc, w.real, w.c_begin, w.cy, w.exlo, w.exhi);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, off, 32,
                           lane, w.he, w.hc, w.real, w.c_begin);
@@ -1327,7 +1340,7 @@ __device__ __forceinline__ void drain_all(const PairConsts& pc, const PairConsts
     if (w.q2n > 0) {
         if (POLY)
             drain_weights_poly(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0, w.q2n, lane,
-                               w.he, w.hc, w.real, w.c_begin, w.cy);
+                               w.he, w.hc, w.real, w.c_begin, w.cy, w.exlo, w.exhi);
         else
             drain_weights<CALLER>(&pc, gpc, &ws, w.Ek, w.NX, w.NY, w.Plok, rb, xq, 0,
                           w.q2n, lane, w.he, w.hc, w.real, w.c_begin);

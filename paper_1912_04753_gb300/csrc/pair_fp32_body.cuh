@@ -59,6 +59,10 @@
     w.q2n = 0;
     w.deep = false;
     w.pa = &sm.pc;
+    if (POLY) {
+        w.exlo = acc.exc_lo;
+        w.exhi = acc.exc_hi;
+    }
     const int64_t n = rb.n;
     const int nx = pc.g.nx, ny = pc.g.ny, nt = pc.g.nt, fs = pc.g.fs, ft = pc.g.ft;
     const int64_t nrows = (int64_t)ny * nt;
