@@ -142,3 +142,25 @@ def test_k_and_envelope_in_smooth_outline(stk, orc, prec):
     assert _rel(got["K"], want["K"]).max() <= TOL[prec]
     for k in range(sims):
         assert _rel(got["K_sims"][k], env["K_all"][k]).max() <= TOL[prec]
+
+
+def test_largest_threshold_grid_in_polygon(stk, orc):
+    """The largest threshold grid (64 x 64 bins) in a polygon, FP32-guarded, with simulations:
+    the polygon kernel keeps a second histogram set in shared memory (realizations of either
+    parity have their own), which at this grid takes it to one block per SM; every
+    realization's K at the parity bar against the oracle, the observed counts exact."""
+    vx, vy = _star(85, 1000.0, 600.0, 1200.0, 1100.0, 85)
+    box = (0.0, 2400.0, 0.0, 2200.0, 0.0, 365.0)
+    x, y, t = _pattern(orc, box, vx, vy, 1500, 5)
+    s, tt = np.linspace(5.0, 320.0, 64), np.linspace(0.7, 45.0, 64)
+    sims, seed = 5, 23
+    want = orc.envelope_of(0, x, y, t, box, s, tt, sims, seed, polygon=(vx, vy))
+    obs = orc.k_function_polygon(x, y, t, box, vx, vy, s, tt)
+    with stk.Pattern(x, y, t, box) as p:
+        p.set_polygon(vx, vy)
+        got = p.run(s, tt, n_sims=sims, seed=seed, want_sims=True)
+        assert p.stats()["internal_errors"] == 0
+    np.testing.assert_array_equal(got["C"], obs["C"])
+    assert _rel(got["K"], obs["K"]).max() <= TOL[1]
+    for k in range(sims):
+        assert _rel(got["K_sims"][k], want["K_all"][k]).max() <= TOL[1]
