@@ -103,8 +103,10 @@ int stk_create_device(const double* d_x, const double* d_y, const double* d_t, i
 /* Polygon study area (the paper's experiments use an 85-vertex outline, Sections 3 and 6):
  * subsequent jobs on h take the closed simple polygon of nv vertices (vx[k], vy[k]), either
  * orientation, as the study region: A in Eq. 2 is its area, the spatial weight is the
- * proportion of the circle's circumference inside it (computed in FP64 whenever the circle
- * reaches the boundary), and CSR simulations are uniform in it (each point the first of its
+ * proportion of the circle's circumference inside it (whenever the circle reaches the
+ * boundary: in FP64 on the FP64 path; on the FP32-guarded path in FP32 with an error bound
+ * per circle, FP64 for what that bound cannot decide), and CSR simulations are uniform in it
+ * (each point the first of its
  * draws in the bounding box, Philox streams 32, 33, ..., that falls inside).  The period stays
  * the box's.  Requires 3 <= nv <= 128, every vertex inside the handle's box, an area of at
  * least 1/64 of the box's, and every point of the handle inside the polygon (else
