@@ -106,9 +106,8 @@ int stk_create_device(const double* d_x, const double* d_y, const double* d_t, i
  * proportion of the circle's circumference inside it (whenever the circle reaches the
  * boundary: in FP64 on the FP64 path; on the FP32-guarded path in FP32 with an error bound
  * per circle, FP64 for what that bound cannot decide), and CSR simulations are uniform in it
- * (each point the first of its
- * draws in the bounding box, Philox streams 32, 33, ..., that falls inside).  The period stays
- * the box's.  Requires 3 <= nv <= 128, every vertex inside the handle's box, an area of at
+ * (each point the first of its draws in the bounding box, Philox streams 32, 33, ..., that
+ * falls inside).  The period stays the box's.  Requires 3 <= nv <= 128, every vertex inside the handle's box, an area of at
  * least 1/64 of the box's, and every point of the handle inside the polygon (else
  * STK_EDOMAIN, the study area unchanged).  nv = 0 restores the box.  Errors: STK_EINVAL,
  * STK_EDOMAIN, STK_ENOMEM, STK_ECUDA. */
